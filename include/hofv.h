@@ -1,0 +1,240 @@
+/*
+ * hofv.h -- C ABI of the GB300 (sm_103a) high-order finite-volume JFNK
+ * library for solid mechanics.
+ *
+ * The method is the cell-centred finite-volume discretisation of
+ * Batistic, Castrillo & Cardiff, "High-order finite volume solid mechanics
+ * with Jacobian-free Newton-Krylov" (arXiv 2601.18417): point values at
+ * cell centroids, least-squares Taylor reconstruction of the displacement
+ * gradient at face Gauss points, Gaussian face quadrature of the traction,
+ * alpha stabilisation, a Jacobian-free Newton-Krylov solver and the
+ * compact-stencil approximate Jacobian as preconditioner.
+ *
+ * Conventions (all entry points)
+ *   - Return value: 0 OK; > 0 warning (HOFV_WNOTCONV); < 0 error.  Errors
+ *     never abort the process; hofv_last_error() gives the message.
+ *   - Vectors over cells are FP64, component-major: x[c * n_cells + cell].
+ *   - "device" pointers are CUDA global-memory addresses on the context's
+ *     device, owned by the caller; the library never frees them.  The
+ *     library owns mesh, stencil, coefficient, preconditioner and Krylov
+ *     storage, allocated by the set-up calls; the evaluation calls
+ *     (residual, jvp, precondition) allocate nothing.
+ *   - Asynchrony: evaluation calls enqueue work on the context stream and
+ *     return; set-up calls and hofv_newton_solve synchronise that stream.
+ *   - Faces: internal faces first, ordered by (owner, owner local face) with
+ *     owner < neighbour; then displacement faces, then traction faces, each
+ *     in the order of the boundary-face list given to hofv_set_mesh.  Local
+ *     faces of a cell are x-, x+, y-, y+ (, z-, z+) of its reference element.
+ *   - Gradients: grad[i][j] = d u_j / d x_i, the paper's sum of c (x) u
+ *     (Sec. 3.5.4, eq. faceQuadGrad).
+ */
+#ifndef HOFV_H
+#define HOFV_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define HOFV_OK 0
+#define HOFV_WNOTCONV 1      /* solver stopped before reaching its tolerance */
+#define HOFV_EINVAL (-1)     /* bad argument */
+#define HOFV_ENOMEM (-2)     /* device or host allocation failed */
+#define HOFV_ECUDA (-3)      /* CUDA runtime error */
+#define HOFV_EILLCOND (-4)   /* singular / ill-conditioned reconstruction */
+#define HOFV_ENAN (-5)       /* non-finite value met */
+#define HOFV_ENOTSUP (-6)    /* feature not supported */
+#define HOFV_ESTATE (-7)     /* call out of order (e.g. residual before set-up) */
+
+/* laws (App. A) */
+#define HOFV_LAW_LINEAR 0       /* small-strain Hooke's law, eq. (linearElastic) */
+#define HOFV_LAW_NEOHOOKEAN 1   /* total-Lagrangian neo-Hookean, eq. (neoHook) */
+
+/* preconditioners for hofv_precondition / hofv_newton_solve */
+#define HOFV_PC_NONE (-1)
+#define HOFV_PC_AJ64 0   /* compact approximate Jacobian, FP64 inner solve */
+#define HOFV_PC_AJ32 1   /* same operator stored and applied in FP32 */
+#define HOFV_PC_GNN 2    /* learned graph network on top of AJ32 */
+
+/* point sets for hofv_get_points */
+#define HOFV_PTS_CELL_CENTROID 0   /* [n_cells][dim] */
+#define HOFV_PTS_DISP_QP 1         /* [n_disp][Q][dim]  displacement-face Gauss points */
+#define HOFV_PTS_DISP_CENTRE 2     /* [n_disp][dim]     displacement-face centres */
+#define HOFV_PTS_TRAC_QP 3         /* [n_trac][Q][dim]  traction-face Gauss points */
+#define HOFV_PTS_CELL_QP 4         /* [n_cells][QC][dim] cell Gauss points */
+#define HOFV_PTS_FACE_CENTRE 5     /* [n_faces][dim] all face centres */
+#define HOFV_PTS_FACE_QP 6         /* [n_faces][Q][dim] all face Gauss points */
+#define HOFV_PTS_FACE_AREA 7       /* [n_faces][Q][dim] vector area of each Gauss point */
+#define HOFV_PTS_CELL_VOLUME 8     /* [n_cells] */
+
+typedef struct hofv_ctx hofv_ctx;
+
+typedef struct {
+  int32_t dim;
+  int32_t p;            /* reconstruction degree */
+  int32_t stencil;      /* |S| = N_t + n_plus */
+  int32_t n_t;          /* number of Taylor terms N_t = (d+p)! / (d! p!) */
+  int32_t q_face;       /* Gauss points per face Q */
+  int32_t q_cell;       /* Gauss points per cell QC */
+  int64_t n_cells, n_faces, n_internal, n_disp, n_trac;
+  double max_cond;      /* largest 2-norm condition-number estimate of the
+                           scaled, weighted LSQ matrix W^1/2 Q^T seen at set-up */
+  double setup_seconds; /* wall time of hofv_build_stencils */
+  int64_t device_bytes; /* device memory held by the context */
+} hofv_layout;
+
+typedef struct {
+  int32_t max_newton;      /* Newton iterations per call (default 30) */
+  double rtol;             /* stop when ||R|| <= rtol * ||R(u_in)|| (default 1e-8) */
+  double atol;             /* ... or ||R|| <= atol (default 0) */
+  int32_t restart;         /* FGMRES restart length m (default 30, max 100) */
+  int32_t max_krylov;      /* Krylov iterations per Newton step (default 300) */
+  double eta_max;          /* forcing term cap (default 1e-2) */
+  int32_t precond;         /* HOFV_PC_* (default HOFV_PC_AJ32) */
+  int32_t inner_iters;     /* AJ inner CG iterations per apply (default 30) */
+  int32_t line_search_max; /* backtracking halvings (default 10) */
+  int32_t verbose;         /* 1: one line per Newton step on stderr */
+} hofv_solve_opts;
+
+typedef struct {
+  int32_t newton_iters;
+  int32_t krylov_iters;    /* total over the call */
+  int32_t residual_evals;  /* R evaluations incl. those inside Jv */
+  int32_t precond_applies;
+  int32_t gnn_fallbacks;   /* learned-preconditioner cycles replaced by AJ */
+  double r0, r_final;      /* ||R|| at entry and exit */
+  double seconds;
+  int32_t status;          /* same as the return value */
+} hofv_stats;
+
+/* ---- context --------------------------------------------------------- */
+
+/* Create a context on CUDA device `device`; `cuda_stream` is a cudaStream_t
+   (NULL = the legacy default stream) on which all work is enqueued. */
+int hofv_create(hofv_ctx** out, int device, void* cuda_stream);
+void hofv_destroy(hofv_ctx* ctx);
+/* Message of the last error on this context (never NULL). */
+const char* hofv_last_error(const hofv_ctx* ctx);
+/* Library version string. */
+const char* hofv_version(void);
+
+/* ---- set-up ------------------------------------------------------------ */
+
+/* Mesh of straight-edged quads (dim 2, unit depth, nodes counter-clockwise)
+   or hexahedra (dim 3, bottom face counter-clockwise seen from +z, then the
+   top face).  All arrays are HOST arrays, copied in:
+     xyz         [n_nodes][dim]
+     cell_nodes  [n_cells][2^dim]
+     bface_nodes [n_bfaces][2^(dim-1)]   every boundary face exactly once
+     bface_tag   [n_bfaces]  0 = prescribed displacement, 1 = prescribed
+                             traction (2 = symmetry: HOFV_ENOTSUP)
+   Face sets of Sec. 3.1.  Errors: EINVAL if a boundary face is missing,
+   duplicated or not on the boundary. */
+int hofv_set_mesh(hofv_ctx* ctx, int dim, int64_t n_nodes, const double* xyz,
+                  int64_t n_cells, const int64_t* cell_nodes, int64_t n_bfaces,
+                  const int64_t* bface_nodes, const int32_t* bface_tag);
+
+/* Scheme (Sec. 3.5): reconstruction degree p in 1..3, surplus stencil nodes
+   n_plus (|S| = N_t + n_plus; the paper uses 10 in 2-D and 45/55/65 in 3-D),
+   Gauss points per face direction q_per_dir in 1..4 (faces are bilinear
+   patches with q_per_dir^(dim-1) tensor Gauss-Legendre points), weight shape
+   k_weight (eq. weightFunc, paper: 6) and stabilisation factor alpha
+   (eq. alpha, paper: 0.1). */
+int hofv_set_scheme(hofv_ctx* ctx, int p, int n_plus, int q_per_dir,
+                    double k_weight, double alpha);
+
+/* Build everything that depends only on the mesh, on the device: geometry
+   and quadrature, nearest-neighbour stencils (Sec. 3.5.2), the
+   least-squares reconstruction coefficients by Householder QR (eqs. ls-lsA),
+   the alpha-stabilisation extrapolation weights (eq. alphaJump, App. B) and
+   the compact approximate Jacobian (Sec. 4.1).  Synchronises.
+   Errors: ESTATE before set_mesh/set_scheme, ENOMEM, EILLCOND. */
+int hofv_build_stencils(hofv_ctx* ctx);
+
+int hofv_get_layout(const hofv_ctx* ctx, hofv_layout* out);
+
+/* Copy a point set (HOFV_PTS_*) to the HOST array `out` (layouts above),
+   so the caller can evaluate boundary data and body forces. */
+int hofv_get_points(hofv_ctx* ctx, int kind, double* out);
+
+/* Material (App. A).  For neo-Hookean the bulk modulus is
+   kappa = lambda + 2 mu / 3; the stabilisation stiffness is
+   Kbar = 2 mu + lambda in both laws (Sec. 3.4). */
+int hofv_set_material(hofv_ctx* ctx, int law, double mu, double lambda);
+
+/* Boundary data and sources, DEVICE arrays copied into the context (any may
+   be NULL = zero):
+     u_bq  [n_disp][Q][dim]  prescribed displacement at displacement-face Gauss points
+     u_bf  [n_disp][dim]     prescribed displacement at displacement-face centres
+     t_bq  [n_trac][Q][dim]  prescribed traction at traction-face Gauss points
+     body  [dim][n_cells]    integrated body force per cell (eq. bodyTerm) */
+int hofv_set_bc(hofv_ctx* ctx, const double* u_bq, const double* u_bf,
+                const double* t_bq, const double* body);
+
+/* Gauss quadrature over each cell, eq. (bodyTerm): f_qp [n_cells][QC][dim]
+   (DEVICE) -> b [dim][n_cells] (DEVICE). */
+int hofv_integrate_cells(hofv_ctx* ctx, const double* f_qp, double* b);
+
+/* ---- evaluation (hot path) -------------------------------------------- */
+
+/* R(u) = sum of face tractions (Gauss quadrature, eq. divStressDiscret) +
+   alpha stabilisation (eq. alpha) + traction-boundary and body sources.
+   u, R: DEVICE [dim][n_cells].  Enqueued on the context stream. */
+int hofv_residual(hofv_ctx* ctx, const double* u, double* R);
+
+/* Jacobian-vector product by forward difference (Sec. 4.1):
+   Jv = (R(u + eps v) - R(u)) / eps with
+   eps = sqrt(2^-52) (1 + ||u||_2) / ||v||_2 computed on the device.
+   Ru must hold R(u).  u, Ru, v, Jv: DEVICE [dim][n_cells].  eps_used: HOST
+   pointer or NULL; when non-NULL the call synchronises to return eps. */
+int hofv_jvp(hofv_ctx* ctx, const double* u, const double* Ru, const double* v,
+             double* Jv, double* eps_used);
+
+/* z ~= P^{-1} v with the compact approximate Jacobian P (Sec. 4.1) applied
+   to every displacement component: HOFV_PC_AJ64 / AJ32 run `inner_iters`
+   Jacobi-preconditioned CG iterations in FP64 / FP32; HOFV_PC_GNN adds the
+   learned correction (needs hofv_gnn_load or hofv_gnn_train first).
+   v, z: DEVICE [dim][n_cells]. */
+int hofv_precondition(hofv_ctx* ctx, int kind, int inner_iters, const double* v, double* z);
+
+/* Newton-Krylov solve of R(u) = 0 from the DEVICE vector u (updated in
+   place): flexible GMRES(m), right preconditioned, Jv by forward
+   differences, backtracking line search on ||R||_2.  opts/stats are HOST
+   pointers (opts NULL = defaults).  Returns 0, HOFV_WNOTCONV, or an error.
+   Synchronises. */
+int hofv_newton_solve(hofv_ctx* ctx, double* u, const hofv_solve_opts* opts,
+                      hofv_stats* stats);
+
+/* Fill `opts` with the defaults listed in hofv_solve_opts. */
+void hofv_default_opts(hofv_solve_opts* opts);
+
+/* ---- inspection (tests) -------------------------------------------------- */
+
+/* Face data for faces [first, first + count) to HOST arrays (any may be NULL):
+     stencil [count][S]        int32 cell ids (internal and displacement faces)
+     coef    [count][Q][S+1][dim]  gradient coefficients; slot S = ghost node
+   Traction faces have no stencil; their rows are left untouched. */
+int hofv_get_face_data(hofv_ctx* ctx, int64_t first, int64_t count, int32_t* stencil,
+                       double* coef);
+
+/* Cell data for cells [first, first + count) to HOST arrays (any may be NULL):
+     stencil [count][S] int32;  ext [count][2 dim][S] weights e with
+     u*_{f,P} = u_P + sum_N e_N u_N (eq. alphaJump). */
+int hofv_get_cell_data(hofv_ctx* ctx, int64_t first, int64_t count, int32_t* stencil,
+                       double* ext);
+
+/* Faces: owner, neighbour (-1 on the boundary), owner local face, tag
+   (-1 internal, 0 displacement, 1 traction); HOST arrays [n_faces]. */
+int hofv_get_faces(hofv_ctx* ctx, int64_t* owner, int64_t* neighbour, int32_t* local_face,
+                   int32_t* tag);
+
+/* Approximate Jacobian (Sec. 4.1) in FP64: diag [n_cells], off [n_internal]
+   (entry coupling owner and neighbour of internal face f); HOST arrays. */
+int hofv_get_aj(hofv_ctx* ctx, double* diag, double* off);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HOFV_H */

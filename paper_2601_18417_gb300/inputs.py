@@ -1,0 +1,488 @@
+"""Seeded synthetic inputs: meshes, manufactured fields and random vectors.
+
+This module holds no arithmetic of the finite-volume method itself.  It builds
+structured quad/hex meshes (optionally with seeded interior-node jitter),
+evaluates closed-form displacement fields together with their exact
+derivatives and the matching body force of linear elasticity, and draws
+seeded random vectors.  Both the CUDA path and the oracle consume these inputs;
+neither imports the other.
+
+Random numbers come from SplitMix64 (Steele, Lea & Flood, "Fast splittable
+pseudorandom number generators", OOPSLA 2014), used as a counter-based
+generator: value i of stream s is splitmix64(seed_mix(s) + i * golden_gamma).
+
+Workloads follow the paper's manufactured-solution case (Section 5.1.1, Case 1)
+and the block-compression loading used for the neo-Hookean runs; the dataclass
+``Workload`` records each one's mesh, order and material.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+_GAMMA = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def splitmix64(counter: np.ndarray) -> np.ndarray:
+    """SplitMix64 finaliser applied to 64-bit counters (vectorised)."""
+    with np.errstate(over="ignore"):
+        z = counter.astype(np.uint64) + _GAMMA
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        return z ^ (z >> np.uint64(31))
+
+
+def uniform(seed: int, n: int, stream: int = 0) -> np.ndarray:
+    """n doubles in [0, 1) from counter-based SplitMix64 (53 high bits)."""
+    base = splitmix64(np.array([seed * 1_000_003 + stream], dtype=np.uint64))[0]
+    with np.errstate(over="ignore"):
+        ctr = base + np.arange(n, dtype=np.uint64) * _GAMMA
+    bits = splitmix64(ctr) >> np.uint64(11)
+    return bits.astype(np.float64) * (1.0 / 9007199254740992.0)
+
+
+def normal(seed: int, n: int, stream: int = 0) -> np.ndarray:
+    """n standard normal doubles (Box-Muller on two uniform streams)."""
+    u1 = uniform(seed, n, 2 * stream + 1)
+    u2 = uniform(seed, n, 2 * stream + 2)
+    u1 = np.maximum(u1, 1e-300)
+    return np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * math.pi * u2)
+
+
+# --------------------------------------------------------------------------
+# meshes
+# --------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class Mesh:
+    """Unstructured description of a structured quad (d=2) or hex (d=3) grid.
+
+    xyz          [n_nodes, d] node coordinates
+    cell_nodes   [n_cells, 2**d] node ids; quads counter-clockwise, hexes with
+                 the bottom face (z-) counter-clockwise seen from +z, then top
+    bface_nodes  [n_bfaces, 2**(d-1)] node ids of boundary faces, outward order
+    bface_side   [n_bfaces] domain side: 0 x-, 1 x+, 2 y-, 3 y+, 4 z-, 5 z+
+    """
+
+    dim: int
+    n: int
+    xyz: np.ndarray
+    cell_nodes: np.ndarray
+    bface_nodes: np.ndarray
+    bface_side: np.ndarray
+    length: float = 1.0
+
+    @property
+    def n_cells(self) -> int:
+        return int(self.cell_nodes.shape[0])
+
+    @property
+    def n_nodes(self) -> int:
+        return int(self.xyz.shape[0])
+
+
+def structured_mesh(dim: int, n: int, length: float = 1.0, jitter: float = 0.0,
+                    seed: int = 0) -> Mesh:
+    """n^d cells on [0, length]^d; interior nodes moved by U(-jitter*h, jitter*h)
+    per coordinate, boundary nodes fixed (boundary-normal motion would change
+    the domain; tangential motion of boundary nodes is also left out)."""
+    h = length / n
+    m = n + 1
+    if dim == 2:
+        j, i = np.meshgrid(np.arange(m), np.arange(m), indexing="ij")
+        xyz = np.stack([i.ravel() * h, j.ravel() * h], axis=1).astype(np.float64)
+        nid = lambda i, j: i + m * j  # noqa: E731
+        cj, ci = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+        ci, cj = ci.ravel(), cj.ravel()
+        cell_nodes = np.stack([nid(ci, cj), nid(ci + 1, cj), nid(ci + 1, cj + 1),
+                               nid(ci, cj + 1)], axis=1)
+        interior = (i.ravel() > 0) & (i.ravel() < n) & (j.ravel() > 0) & (j.ravel() < n)
+        r = np.arange(n)
+        faces, sides = [], []
+        # x- (i=0): outward order (0,3) -> nodes (0,j+1),(0,j)
+        faces.append(np.stack([nid(0, r + 1), nid(0, r)], 1)); sides.append(np.full(n, 0))
+        faces.append(np.stack([nid(n, r), nid(n, r + 1)], 1)); sides.append(np.full(n, 1))
+        faces.append(np.stack([nid(r, 0), nid(r + 1, 0)], 1)); sides.append(np.full(n, 2))
+        faces.append(np.stack([nid(r + 1, n), nid(r, n)], 1)); sides.append(np.full(n, 3))
+    elif dim == 3:
+        k, j, i = np.meshgrid(np.arange(m), np.arange(m), np.arange(m), indexing="ij")
+        xyz = np.stack([i.ravel() * h, j.ravel() * h, k.ravel() * h], axis=1).astype(np.float64)
+        nid = lambda i, j, k: i + m * (j + m * k)  # noqa: E731
+        ck, cj, ci = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+        ci, cj, ck = ci.ravel(), cj.ravel(), ck.ravel()
+        cell_nodes = np.stack([
+            nid(ci, cj, ck), nid(ci + 1, cj, ck), nid(ci + 1, cj + 1, ck), nid(ci, cj + 1, ck),
+            nid(ci, cj, ck + 1), nid(ci + 1, cj, ck + 1), nid(ci + 1, cj + 1, ck + 1),
+            nid(ci, cj + 1, ck + 1)], axis=1)
+        iv, jv, kv = i.ravel(), j.ravel(), k.ravel()
+        interior = ((iv > 0) & (iv < n) & (jv > 0) & (jv < n) & (kv > 0) & (kv < n))
+        b, a = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+        a, b = a.ravel(), b.ravel()
+        faces, sides = [], []
+        nf = n * n
+        # outward node orders mirror the hex's local faces
+        faces.append(np.stack([nid(0, a, b), nid(0, a, b + 1), nid(0, a + 1, b + 1), nid(0, a + 1, b)], 1)); sides.append(np.full(nf, 0))
+        faces.append(np.stack([nid(n, a, b), nid(n, a + 1, b), nid(n, a + 1, b + 1), nid(n, a, b + 1)], 1)); sides.append(np.full(nf, 1))
+        faces.append(np.stack([nid(a, 0, b), nid(a + 1, 0, b), nid(a + 1, 0, b + 1), nid(a, 0, b + 1)], 1)); sides.append(np.full(nf, 2))
+        faces.append(np.stack([nid(a, n, b), nid(a, n, b + 1), nid(a + 1, n, b + 1), nid(a + 1, n, b)], 1)); sides.append(np.full(nf, 3))
+        faces.append(np.stack([nid(a, b, 0), nid(a, b + 1, 0), nid(a + 1, b + 1, 0), nid(a + 1, b, 0)], 1)); sides.append(np.full(nf, 4))
+        faces.append(np.stack([nid(a, b, n), nid(a + 1, b, n), nid(a + 1, b + 1, n), nid(a, b + 1, n)], 1)); sides.append(np.full(nf, 5))
+    else:
+        raise ValueError("dim must be 2 or 3")
+    if jitter > 0.0:
+        nn = xyz.shape[0]
+        shift = (2.0 * uniform(seed, nn * dim, stream=7) - 1.0).reshape(nn, dim) * (jitter * h)
+        xyz = xyz + np.where(interior[:, None], shift, 0.0)
+    return Mesh(dim=dim, n=n, xyz=np.ascontiguousarray(xyz),
+                cell_nodes=np.ascontiguousarray(cell_nodes.astype(np.int64)),
+                bface_nodes=np.ascontiguousarray(np.concatenate(faces).astype(np.int64)),
+                bface_side=np.concatenate(sides).astype(np.int32), length=length)
+
+
+# --------------------------------------------------------------------------
+# material constants
+# --------------------------------------------------------------------------
+
+def lame_from_young(E: float, nu: float) -> tuple[float, float]:
+    """(mu, lambda) from Young's modulus and Poisson's ratio (Appendix A)."""
+    return E / (2.0 * (1.0 + nu)), E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu))
+
+
+# --------------------------------------------------------------------------
+# closed-form displacement fields: value, gradient, Hessian
+# grad[..., i, j] = d u_j / d x_i ; hess[..., j, a, b] = d^2 u_j / dx_a dx_b
+# --------------------------------------------------------------------------
+
+class Field:
+    dim: int
+
+    def value(self, x):  # pragma: no cover - interface
+        raise NotImplementedError
+
+    def grad(self, x):  # pragma: no cover
+        raise NotImplementedError
+
+    def hess(self, x):  # pragma: no cover
+        raise NotImplementedError
+
+    def body_force(self, x, mu, lam):
+        """f_b = -div(sigma(u)) for linear elasticity:
+        -(mu * lap(u) + (mu + lam) * grad(div u))."""
+        H = self.hess(x)
+        lap = np.einsum("...jaa->...j", H)
+        grad_div = np.einsum("...iji->...j", H)
+        return -(mu * lap + (mu + lam) * grad_div)
+
+
+class Trig2D(Field):
+    """u = a sin(4 pi x) sin(2 pi y): the paper's 3-D trigonometric field
+    (Case 1) with the z factor dropped, a = (2, 4) micrometres."""
+    dim = 2
+
+    def __init__(self, a=(2e-6, 4e-6)):
+        self.a = np.asarray(a, dtype=np.float64)
+
+    def _parts(self, x):
+        X, Y = x[..., 0], x[..., 1]
+        kx, ky = 4 * math.pi, 2 * math.pi
+        return X, Y, kx, ky
+
+    def value(self, x):
+        X, Y, kx, ky = self._parts(x)
+        s = np.sin(kx * X) * np.sin(ky * Y)
+        return s[..., None] * self.a
+
+    def grad(self, x):
+        X, Y, kx, ky = self._parts(x)
+        dx = kx * np.cos(kx * X) * np.sin(ky * Y)
+        dy = ky * np.sin(kx * X) * np.cos(ky * Y)
+        g = np.stack([dx, dy], axis=-1)  # d s / d x_i
+        return g[..., :, None] * self.a[None, :]
+
+    def hess(self, x):
+        X, Y, kx, ky = self._parts(x)
+        sxx = -kx * kx * np.sin(kx * X) * np.sin(ky * Y)
+        syy = -ky * ky * np.sin(kx * X) * np.sin(ky * Y)
+        sxy = kx * ky * np.cos(kx * X) * np.cos(ky * Y)
+        Hs = np.stack([np.stack([sxx, sxy], -1), np.stack([sxy, syy], -1)], -2)
+        return self.a[:, None, None] * Hs[..., None, :, :]
+
+
+class Mixed2D(Field):
+    """The paper's 2-D manufactured field (Case 1):
+    u_x = exp(x^2) sin(y),  u_y = ln(3 + y) cos(x) + sin(y)."""
+    dim = 2
+
+    def value(self, x):
+        X, Y = x[..., 0], x[..., 1]
+        return np.stack([np.exp(X * X) * np.sin(Y),
+                         np.log(3 + Y) * np.cos(X) + np.sin(Y)], axis=-1)
+
+    def grad(self, x):
+        X, Y = x[..., 0], x[..., 1]
+        e = np.exp(X * X)
+        dux_dx = 2 * X * e * np.sin(Y)
+        dux_dy = e * np.cos(Y)
+        duy_dx = -np.log(3 + Y) * np.sin(X)
+        duy_dy = np.cos(X) / (3 + Y) + np.cos(Y)
+        g = np.empty(x.shape[:-1] + (2, 2))
+        g[..., 0, 0], g[..., 1, 0] = dux_dx, dux_dy
+        g[..., 0, 1], g[..., 1, 1] = duy_dx, duy_dy
+        return g
+
+    def hess(self, x):
+        X, Y = x[..., 0], x[..., 1]
+        e = np.exp(X * X)
+        H = np.empty(x.shape[:-1] + (2, 2, 2))
+        H[..., 0, 0, 0] = (2 + 4 * X * X) * e * np.sin(Y)
+        H[..., 0, 0, 1] = H[..., 0, 1, 0] = 2 * X * e * np.cos(Y)
+        H[..., 0, 1, 1] = -e * np.sin(Y)
+        H[..., 1, 0, 0] = -np.log(3 + Y) * np.cos(X)
+        H[..., 1, 0, 1] = H[..., 1, 1, 0] = -np.sin(X) / (3 + Y)
+        H[..., 1, 1, 1] = -np.cos(X) / (3 + Y) ** 2 - np.sin(Y)
+        return H
+
+
+class Trig3D(Field):
+    """The paper's 3-D manufactured field (Case 1):
+    u = a sin(4 pi x) sin(2 pi y) sin(pi z), a = (2, 4, 6) micrometres."""
+    dim = 3
+
+    def __init__(self, a=(2e-6, 4e-6, 6e-6)):
+        self.a = np.asarray(a, dtype=np.float64)
+        self.k = np.array([4 * math.pi, 2 * math.pi, math.pi])
+
+    def _sc(self, x):
+        s = np.sin(self.k * x)
+        c = np.cos(self.k * x)
+        return s, c
+
+    def value(self, x):
+        s, _ = self._sc(x)
+        return np.prod(s, axis=-1)[..., None] * self.a
+
+    def grad(self, x):
+        s, c = self._sc(x)
+        k = self.k
+        g = np.stack([k[0] * c[..., 0] * s[..., 1] * s[..., 2],
+                      k[1] * s[..., 0] * c[..., 1] * s[..., 2],
+                      k[2] * s[..., 0] * s[..., 1] * c[..., 2]], axis=-1)
+        return g[..., :, None] * self.a
+
+    def hess(self, x):
+        s, c = self._sc(x)
+        k = self.k
+        Hs = np.empty(x.shape[:-1] + (3, 3))
+        for a_ in range(3):
+            for b_ in range(3):
+                f = np.ones(x.shape[:-1])
+                for m in range(3):
+                    if m == a_ and m == b_:
+                        f = f * (-k[m] * k[m] * s[..., m])
+                    elif m == a_ or m == b_:
+                        f = f * (k[m] * c[..., m])
+                    else:
+                        f = f * s[..., m]
+                Hs[..., a_, b_] = f
+        return self.a[:, None, None] * Hs[..., None, :, :]
+
+
+def monomial_exponents(dim: int, p: int) -> list[tuple[int, ...]]:
+    """Exponent tuples of all monomials of total degree <= p, graded order."""
+    out = []
+    for deg in range(p + 1):
+        if dim == 2:
+            for a in range(deg, -1, -1):
+                out.append((a, deg - a))
+        else:
+            for a in range(deg, -1, -1):
+                for b in range(deg - a, -1, -1):
+                    out.append((a, b, deg - a - b))
+    return out
+
+
+class Polynomial(Field):
+    """Vector polynomial field with seeded coefficients of total degree <= p.
+    coef[m, j] multiplies monomial m in component j."""
+
+    def __init__(self, dim: int, p: int, seed: int = 0, scale: float = 1.0,
+                 center=None):
+        self.dim = dim
+        self.exps = monomial_exponents(dim, p)
+        self.coef = (2.0 * uniform(seed, len(self.exps) * dim, stream=11) - 1.0).reshape(
+            len(self.exps), dim) * scale
+        self.center = np.zeros(dim) if center is None else np.asarray(center, float)
+
+    def _mono(self, x, deriv):
+        y = x - self.center
+        out = []
+        for e in self.exps:
+            f = np.ones(x.shape[:-1])
+            for ax in range(self.dim):
+                n_d = deriv.count(ax)
+                ee = e[ax]
+                if n_d > ee:
+                    f = f * 0.0
+                    continue
+                fac = 1.0
+                for t in range(n_d):
+                    fac *= (ee - t)
+                f = f * fac * y[..., ax] ** (ee - n_d)
+            out.append(f)
+        return np.stack(out, axis=-1)
+
+    def value(self, x):
+        return self._mono(x, ()) @ self.coef
+
+    def grad(self, x):
+        return np.stack([self._mono(x, (i,)) @ self.coef for i in range(self.dim)], axis=-2)
+
+    def hess(self, x):
+        d = self.dim
+        H = np.empty(x.shape[:-1] + (d, d, d))
+        for a in range(d):
+            for b in range(d):
+                H[..., :, a, b] = self._mono(x, (a, b)) @ self.coef
+        return H
+
+
+class RigidBody(Field):
+    """u = c + W x with W skew-symmetric (an infinitesimal rigid motion)."""
+
+    def __init__(self, dim: int, seed: int = 0, scale: float = 1e-3):
+        self.dim = dim
+        r = 2.0 * uniform(seed, 4, stream=13) - 1.0
+        self.c = r[:dim] * scale
+        W = np.zeros((dim, dim))
+        if dim == 2:
+            W[0, 1], W[1, 0] = r[3] * scale, -r[3] * scale
+        else:
+            w = r[1:4] * scale
+            W = np.array([[0, -w[2], w[1]], [w[2], 0, -w[0]], [-w[1], w[0], 0]])
+        self.W = W
+
+    def value(self, x):
+        return self.c + x @ self.W.T
+
+    def grad(self, x):
+        return np.broadcast_to(self.W.T, x.shape[:-1] + (self.dim, self.dim)).copy()
+
+    def hess(self, x):
+        return np.zeros(x.shape[:-1] + (self.dim,) * 3)
+
+
+class FiniteRotation(Field):
+    """u = (Q - I) x for a proper rotation Q (a finite rigid motion)."""
+
+    def __init__(self, dim: int, angle: float = 0.3, axis=(1.0, 2.0, 2.0)):
+        self.dim = dim
+        if dim == 2:
+            c, s = math.cos(angle), math.sin(angle)
+            Q = np.array([[c, -s], [s, c]])
+        else:
+            a = np.asarray(axis, float)
+            a = a / np.linalg.norm(a)
+            K = np.array([[0, -a[2], a[1]], [a[2], 0, -a[0]], [-a[1], a[0], 0]])
+            Q = np.eye(3) + math.sin(angle) * K + (1 - math.cos(angle)) * (K @ K)
+        self.Q = Q
+
+    def value(self, x):
+        return x @ (self.Q - np.eye(self.dim)).T
+
+    def grad(self, x):
+        return np.broadcast_to((self.Q - np.eye(self.dim)).T,
+                               x.shape[:-1] + (self.dim, self.dim)).copy()
+
+    def hess(self, x):
+        return np.zeros(x.shape[:-1] + (self.dim,) * 3)
+
+
+# --------------------------------------------------------------------------
+# workloads (the paper's Case 1 fields; the block-compression loading)
+# --------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    dim: int
+    n: int
+    p: int
+    n_plus: int
+    q1: int
+    jitter: float
+    law: int            # 0 linear elastic, 1 neo-Hookean
+    mu: float
+    lam: float
+    problem: str        # "mms-trig2d", "mms-mixed2d", "mms-trig3d", "block"
+    mesh_seed: int
+    load_steps: int = 1
+    alpha: float = 0.1
+    k_weight: float = 6.0
+
+    @property
+    def n_cells(self) -> int:
+        return self.n ** self.dim
+
+    @property
+    def n_t(self) -> int:
+        return math.comb(self.dim + self.p, self.dim)
+
+    @property
+    def stencil(self) -> int:
+        return self.n_t + self.n_plus
+
+
+_MU_S, _LAM_S = lame_from_young(200e9, 0.3)
+_MU_1G, _LAM_1G = lame_from_young(1e9, 0.3)
+
+WORKLOADS = {
+    # 2-D plane strain, E=200 GPa, nu=0.3, 32x32 quads, quadratic LSQ, 2 Gauss pts/face
+    "quad32-p2-trig": Workload("quad32-p2-trig", 2, 32, 2, 10, 2, 0.0, 0, _MU_S, _LAM_S,
+                               "mms-trig2d", 1234),
+    # 2-D, cubic LSQ, 3 Gauss pts/face, 512x512 quads jittered 25 %
+    "quad512j-p3-mixed": Workload("quad512j-p3-mixed", 2, 512, 3, 10, 3, 0.25, 0, _MU_S,
+                                  _LAM_S, "mms-mixed2d", 1235),
+    # 3-D linear elastic cube, 96^3 hexes, cubic LSQ, 3x3 Gauss pts/face, E=1 GPa
+    "hex96-p3-trig": Workload("hex96-p3-trig", 3, 96, 3, 65, 3, 0.0, 0, _MU_1G, _LAM_1G,
+                              "mms-trig3d", 1236),
+    # 3-D neo-Hookean block mu=1 MPa lambda=4 MPa, 64^3 hexes jittered 20 %, quadratic LSQ
+    "hex64j-p2-nh": Workload("hex64j-p2-nh", 3, 64, 2, 55, 2, 0.20, 1, 1e6, 4e6, "block",
+                             1237, load_steps=10),
+    # 3-D neo-Hookean, 128^3 jittered hexes, cubic LSQ
+    "hex128j-p3-nh": Workload("hex128j-p3-nh", 3, 128, 3, 65, 3, 0.20, 1, 1e6, 4e6, "block",
+                              1238, load_steps=10),
+}
+
+
+def field_for(problem: str, dim: int) -> Field | None:
+    if problem == "mms-trig2d":
+        return Trig2D()
+    if problem == "mms-mixed2d":
+        return Mixed2D()
+    if problem == "mms-trig3d":
+        return Trig3D()
+    return None
+
+
+def side_tags(problem: str, dim: int) -> np.ndarray:
+    """Boundary condition tag per domain side: 0 displacement, 1 traction.
+    Manufactured cases prescribe displacement on every side; the block has a
+    fixed bottom (z-), a displaced top (z+) and traction-free sides."""
+    if problem == "block":
+        t = np.ones(2 * dim, dtype=np.int32)
+        t[2 * dim - 2] = 0
+        t[2 * dim - 1] = 0
+        return t
+    return np.zeros(2 * dim, dtype=np.int32)
+
+
+def block_top_displacement(step: int, n_steps: int, dim: int, total: float = 0.3) -> np.ndarray:
+    """Prescribed top-face displacement at load step `step` of `n_steps`:
+    a compression of `total` of the unit height, in equal increments."""
+    u = np.zeros(dim)
+    u[dim - 1] = -total * step / n_steps
+    return u
