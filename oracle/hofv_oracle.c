@@ -27,7 +27,8 @@
  * Readings of the paper taken here (the paper is silent or its setting differs):
  *   - faces are bilinear patches with tensor Gauss-Legendre points; each point
  *     carries its own vector area (the paper fan-triangulates planar faces);
- *   - stencil ties are broken by a quantised squared distance then cell id;
+ *   - stencil ties are broken by a quantised squared distance (quantum
+ *     2^-24 of the squared reference cell size) then by cell id;
  *   - the reconstruction is solved from the normal equations, eq. (maQw), in
  *     extended precision (the paper uses Householder QR; the result is the same
  *     in exact arithmetic).
@@ -521,7 +522,7 @@ static int64_t dist_key(const orc_mesh* m, const double* xr, int64_t cell) {
     double dz = m->xc[3 * cell + 2] - xr[2];
     d2 = d2 + dz * dz;
   }
-  double s = ldexp(d2, 40 - 2 * m->href_exp);
+  double s = ldexp(d2, 24 - 2 * m->href_exp);
   return (int64_t)floor(s + 0.5);
 }
 
@@ -630,7 +631,7 @@ static int stencil_search(const orc_mesh* m, const buckets* B, const double* xr,
       if (hi[a] < B->nb[a] - 1) { whole = 0; double g = (B->lo[a] + (hi[a] + 1) * B->bs) - xr[a]; if (g < reach) reach = g; }
     }
     int64_t kmax = cs[S - 1].key;
-    double reach_key = ldexp(reach * reach, 40 - 2 * m->href_exp);
+    double reach_key = ldexp(reach * reach, 24 - 2 * m->href_exp);
     if (whole || (double)kmax + 2.0 < reach_key) {
       for (int i = 0; i < S; ++i) out[i] = cs[i].id;
       free(cs);

@@ -1,0 +1,988 @@
+// api.cu -- the C ABI of libhofv (include/hofv.h): context, mesh and face
+// extraction, set-up orchestration, evaluation entry points and the
+// Jacobian-free Newton-Krylov driver (arXiv 2601.18417, Sec. 4.1).
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <array>
+#include <chrono>
+#include <cstdio>
+#include <numeric>
+
+#include "hofv_internal.cuh"
+
+namespace hofv {
+
+int fail(hofv_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+int cuda_fail(hofv_ctx* c, cudaError_t e, const char* what) {
+  return fail(c, HOFV_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+void dev_free(hofv_ctx* c, void* p) {
+  if (!p) return;
+  auto it = std::find(c->allocs.begin(), c->allocs.end(), p);
+  if (it != c->allocs.end()) c->allocs.erase(it);
+  cudaFree(p);
+}
+
+DevMesh dev_mesh(const hofv_ctx* c) {
+  DevMesh m;
+  m.dim = c->dim;
+  m.nlf = c->nlf;
+  m.S = c->S;
+  m.Q = c->Q;
+  m.R = c->Q * c->dim;
+  m.nc = c->nc;
+  m.nf = c->nf;
+  m.nfi = c->nfi;
+  m.nfd = c->nfd;
+  m.nft = c->nft;
+  m.nfid = c->nfid;
+  m.nftile = c->nftile;
+  m.nctile = c->nctile;
+  m.fst = c->d_fst;
+  m.fco = c->d_fco;
+  m.gco = c->d_gco;
+  m.aq = c->d_aq;
+  m.fstar = c->d_fstar;
+  m.fstab = c->d_fstab;
+  m.cst = c->d_cst;
+  m.cex = c->d_cex;
+  m.cface = c->d_cface;
+  return m;
+}
+
+// local faces of the reference quad / hex as node positions, outward order
+static const int kQuadLF[4][2] = {{3, 0}, {1, 2}, {0, 1}, {2, 3}};
+static const int kHexLF[6][4] = {{0, 4, 7, 3}, {1, 2, 6, 5}, {0, 1, 5, 4},
+                                 {3, 7, 6, 2}, {0, 3, 2, 1}, {4, 5, 6, 7}};
+
+// Gauss-Legendre rule on [0, 1] (closed forms of the 1..4 point rules on
+// [-1, 1], mapped by x = (t + 1) / 2, w = c / 2)
+static void gauss_rule(int n, double* x, double* w) {
+  double t[4] = {0, 0, 0, 0}, c[4] = {0, 0, 0, 0};
+  switch (n) {
+    case 1: t[0] = 0.0; c[0] = 2.0; break;
+    case 2: t[0] = -1.0 / sqrt(3.0); t[1] = -t[0]; c[0] = c[1] = 1.0; break;
+    case 3:
+      t[0] = -sqrt(3.0 / 5.0); t[1] = 0.0; t[2] = -t[0];
+      c[0] = c[2] = 5.0 / 9.0; c[1] = 8.0 / 9.0;
+      break;
+    default: {
+      const double a = sqrt(3.0 / 7.0 - 2.0 / 7.0 * sqrt(6.0 / 5.0));
+      const double b = sqrt(3.0 / 7.0 + 2.0 / 7.0 * sqrt(6.0 / 5.0));
+      t[0] = -b; t[1] = -a; t[2] = a; t[3] = b;
+      c[1] = c[2] = (18.0 + sqrt(30.0)) / 36.0;
+      c[0] = c[3] = (18.0 - sqrt(30.0)) / 36.0;
+    }
+  }
+  for (int i = 0; i < n; ++i) {
+    x[i] = 0.5 * (t[i] + 1.0);
+    w[i] = 0.5 * c[i];
+  }
+}
+
+static void free_built(hofv_ctx* c) {
+  for (void* p : c->allocs) cudaFree(p);
+  c->allocs.clear();
+  c->device_bytes = 0;
+  c->d_x = nullptr; c->d_fnodes = nullptr; c->d_cnodes = nullptr;
+  c->d_xc = c->d_vol = c->d_xq = c->d_aq = c->d_xf = c->d_nrm = c->d_gam = nullptr;
+  c->d_cqx = c->d_cqw = nullptr;
+  c->d_cf = nullptr; c->d_ftag = c->d_fown = c->d_fnei = nullptr;
+  c->d_fst = c->d_cst = c->d_fstar = c->d_cface = nullptr;
+  c->d_fco = c->d_gco = c->d_cex = c->d_fstab = nullptr;
+  c->d_ubq = c->d_ubf = c->d_tbq = c->d_body = c->d_src = nullptr;
+  c->d_ustar = c->d_flux = c->d_w = c->d_red = c->d_scal = nullptr;
+  c->d_count = nullptr;
+  c->d_aj_diag = c->d_aj_off = nullptr;
+  c->d_aj_col = nullptr;
+  c->d_aj_diag32 = c->d_aj_off32 = nullptr;
+  c->d_cg64 = nullptr;
+  c->d_cg32 = nullptr;
+  c->d_V = c->d_Z = c->d_kvec = c->d_h = nullptr;
+  c->kry_m = 0;
+  c->built = false;
+}
+
+}  // namespace hofv
+
+using namespace hofv;
+
+extern "C" {
+
+const char* hofv_version(void) { return "hofv 0.1 (sm_103a)"; }
+
+int hofv_create(hofv_ctx** out, int device, void* stream) {
+  if (!out) return HOFV_EINVAL;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return HOFV_ECUDA;
+  if (cudaSetDevice(device) != cudaSuccess) return HOFV_ECUDA;
+  hofv_ctx* c = new hofv_ctx();
+  c->device = device;
+  c->stream = static_cast<cudaStream_t>(stream);
+  *out = c;
+  return HOFV_OK;
+}
+
+void hofv_destroy(hofv_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  else cudaDeviceSynchronize();
+  free_built(c);
+  delete c;
+}
+
+const char* hofv_last_error(const hofv_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int hofv_set_mesh(hofv_ctx* c, int dim, int64_t nn, const double* xyz, int64_t nc,
+                  const int64_t* cell_nodes, int64_t nb, const int64_t* bface_nodes,
+                  const int32_t* bface_tag) {
+  if (!c) return HOFV_EINVAL;
+  if (dim != 2 && dim != 3) return fail(c, HOFV_EINVAL, "dim must be 2 or 3");
+  if (nn <= 0 || nc <= 0 || !xyz || !cell_nodes || nb < 0 || (nb > 0 && (!bface_nodes || !bface_tag)))
+    return fail(c, HOFV_EINVAL, "empty mesh or null array");
+  if (nn >= (int64_t)1 << 31 || nc >= (int64_t)1 << 30)
+    return fail(c, HOFV_EINVAL, "mesh too large for 32-bit ids");
+  free_built(c);
+  c->have_mesh = false;
+  c->dim = dim;
+  c->nv = dim == 2 ? 4 : 8;
+  c->nlf = 2 * dim;
+  c->nfv = dim == 2 ? 2 : 4;
+  c->nn = nn;
+  c->nc = nc;
+  c->nb = nb;
+  c->x.assign((size_t)nn * 3, 0.0);
+  for (int64_t i = 0; i < nn; ++i)
+    for (int a = 0; a < dim; ++a) c->x[3 * i + a] = xyz[dim * i + a];
+  c->cn.assign(cell_nodes, cell_nodes + nc * c->nv);
+  for (int64_t i = 0; i < nc * c->nv; ++i)
+    if (c->cn[i] < 0 || c->cn[i] >= nn) return fail(c, HOFV_EINVAL, "cell node id out of range");
+  for (int64_t b = 0; b < nb; ++b) {
+    if (bface_tag[b] == 2) return fail(c, HOFV_ENOTSUP, "symmetry boundaries are not supported");
+    if (bface_tag[b] != 0 && bface_tag[b] != 1) return fail(c, HOFV_EINVAL, "bad boundary tag");
+  }
+  // local faces keyed by their sorted node ids
+  const int nlf = c->nlf, nfv = c->nfv;
+  struct Rec {
+    std::array<int64_t, 4> key;
+    int64_t id;  // cell * nlf + lf
+  };
+  auto make_key = [&](const int64_t* nodes) {
+    std::array<int64_t, 4> k = {-1, -1, -1, -1};
+    for (int i = 0; i < nfv; ++i) k[i] = nodes[i];
+    std::sort(k.begin(), k.begin() + nfv);
+    return k;
+  };
+  std::vector<Rec> recs((size_t)nc * nlf);
+  for (int64_t cell = 0; cell < nc; ++cell)
+    for (int lf = 0; lf < nlf; ++lf) {
+      int64_t nodes[4];
+      for (int k = 0; k < nfv; ++k)
+        nodes[k] = c->cn[cell * c->nv + (dim == 2 ? kQuadLF[lf][k] : kHexLF[lf][k])];
+      recs[cell * nlf + lf] = {make_key(nodes), cell * nlf + lf};
+    }
+  std::sort(recs.begin(), recs.end(), [](const Rec& a, const Rec& b) {
+    return a.key != b.key ? a.key < b.key : a.id < b.id;
+  });
+  std::vector<int64_t> partner((size_t)nc * nlf, -1);
+  for (size_t i = 0; i + 1 < recs.size(); ++i)
+    if (recs[i].key == recs[i + 1].key) {
+      if (i + 2 < recs.size() && recs[i + 2].key == recs[i].key)
+        return fail(c, HOFV_EINVAL, "a face is shared by more than two cells");
+      partner[recs[i].id] = recs[i + 1].id;
+      partner[recs[i + 1].id] = recs[i].id;
+    }
+  int64_t nbound = 0;
+  for (int64_t i = 0; i < nc * nlf; ++i) nbound += partner[i] < 0;
+  if (nbound != nb) return fail(c, HOFV_EINVAL, "boundary face list does not match the mesh boundary");
+  std::vector<int64_t> bown((size_t)nb);
+  std::vector<char> seen((size_t)nc * nlf, 0);
+  for (int64_t b = 0; b < nb; ++b) {
+    Rec q{make_key(bface_nodes + b * nfv), -1};
+    auto itr = std::lower_bound(recs.begin(), recs.end(), q, [](const Rec& a, const Rec& b) {
+      return a.key < b.key;
+    });
+    if (itr == recs.end() || itr->key != q.key) return fail(c, HOFV_EINVAL, "boundary face not in mesh");
+    if (partner[itr->id] >= 0) return fail(c, HOFV_EINVAL, "boundary face is an internal face");
+    if (seen[itr->id]) return fail(c, HOFV_EINVAL, "boundary face listed twice");
+    seen[itr->id] = 1;
+    bown[b] = itr->id;
+  }
+  int64_t nfi = 0, nfd = 0, nft = 0;
+  for (int64_t i = 0; i < nc * nlf; ++i) nfi += partner[i] > i;
+  for (int64_t b = 0; b < nb; ++b) (bface_tag[b] == 0 ? nfd : nft)++;
+  c->nfi = nfi;
+  c->nfd = nfd;
+  c->nft = nft;
+  c->nfid = nfi + nfd;
+  c->nf = nfi + nfd + nft;
+  c->fown.assign(c->nf, -1);
+  c->fnei.assign(c->nf, -1);
+  c->flf.assign(c->nf, 0);
+  c->ftag.assign(c->nf, -1);
+  c->cf.assign((size_t)nc * nlf, -1);
+  int64_t f = 0;
+  for (int64_t cell = 0; cell < nc; ++cell)
+    for (int lf = 0; lf < nlf; ++lf) {
+      const int64_t id = cell * nlf + lf, pid = partner[id];
+      if (pid >= 0 && pid / nlf > cell) {
+        c->fown[f] = cell;
+        c->fnei[f] = pid / nlf;
+        c->flf[f] = lf;
+        c->cf[id] = f;
+        c->cf[pid] = f;
+        ++f;
+      }
+    }
+  for (int tag = 0; tag <= 1; ++tag)
+    for (int64_t b = 0; b < nb; ++b)
+      if (bface_tag[b] == tag) {
+        const int64_t id = bown[b];
+        c->fown[f] = id / nlf;
+        c->flf[f] = (int)(id % nlf);
+        c->ftag[f] = tag;
+        c->cf[id] = f;
+        ++f;
+      }
+  c->fnodes.assign((size_t)c->nf * nfv, 0);
+  for (f = 0; f < c->nf; ++f)
+    for (int k = 0; k < nfv; ++k) {
+      const int lf = c->flf[f];
+      c->fnodes[f * nfv + k] =
+          (int32_t)c->cn[c->fown[f] * c->nv + (dim == 2 ? kQuadLF[lf][k] : kHexLF[lf][k])];
+    }
+  c->have_mesh = true;
+  c->built = false;
+  return HOFV_OK;
+}
+
+int hofv_set_scheme(hofv_ctx* c, int p, int n_plus, int q1, double k_weight, double alpha) {
+  if (!c) return HOFV_EINVAL;
+  if (!c->have_mesh) return fail(c, HOFV_ESTATE, "hofv_set_mesh must come first");
+  if (p < 1 || p > 3) return fail(c, HOFV_EINVAL, "p must be 1..3");
+  if (q1 < 1 || q1 > 4 || (c->dim == 3 && q1 > 3))
+    return fail(c, HOFV_EINVAL, "q_per_dir must be 1..4 in 2-D and 1..3 in 3-D");
+  if (n_plus < 0 || !(k_weight > 0) || !(alpha >= 0)) return fail(c, HOFV_EINVAL, "bad scheme parameter");
+  int nt = 1;
+  for (int i = 1; i <= c->dim; ++i) nt = nt * (p + i) / i;
+  if (nt + n_plus + 1 > kMaxS) return fail(c, HOFV_EINVAL, "stencil too large");
+  if (nt + n_plus > c->nc) return fail(c, HOFV_EINVAL, "stencil larger than the mesh");
+  free_built(c);
+  c->p = p;
+  c->nplus = n_plus;
+  c->q1 = q1;
+  c->Nt = nt;
+  c->S = nt + n_plus;
+  c->Q = c->dim == 2 ? q1 : q1 * q1;
+  c->QC = c->dim == 2 ? q1 * q1 : q1 * q1 * q1;
+  c->kw = k_weight;
+  c->alpha = alpha;
+  gauss_rule(q1, c->gl_x, c->gl_w);
+  c->have_scheme = true;
+  return HOFV_OK;
+}
+
+#define TRY(x)                 \
+  do {                         \
+    int rc_ = (x);             \
+    if (rc_ != 0) return rc_;  \
+  } while (0)
+
+int hofv_build_stencils(hofv_ctx* c) {
+  if (!c) return HOFV_EINVAL;
+  if (!c->have_mesh || !c->have_scheme) return fail(c, HOFV_ESTATE, "mesh and scheme must be set first");
+  HOFV_CUDA(c, cudaSetDevice(c->device));
+  const auto t0 = std::chrono::steady_clock::now();
+  free_built(c);
+  const int d = c->dim, nlf = c->nlf;
+  const int64_t nc = c->nc, nf = c->nf;
+  c->nftile = (c->nfid + kTile - 1) / kTile;
+  c->nctile = (nc + kTile - 1) / kTile;
+  const int R = c->Q * d;
+  // ---- uploads ----
+  TRY(dev_alloc(c, &c->d_x, c->nn * 3));
+  TRY(dev_alloc(c, &c->d_fnodes, nf * c->nfv));
+  TRY(dev_alloc(c, &c->d_cnodes, nc * c->nv));
+  TRY(dev_alloc(c, &c->d_cf, nc * nlf));
+  TRY(dev_alloc(c, &c->d_ftag, nf));
+  TRY(dev_alloc(c, &c->d_fown, nf));
+  TRY(dev_alloc(c, &c->d_fnei, nf));
+  TRY(dev_alloc(c, &c->d_cface, nc * nlf));
+  std::vector<int32_t> tmp32((size_t)std::max(nc * c->nv, std::max(nc * nlf, nf)));
+  HOFV_CUDA(c, cudaMemcpy(c->d_x, c->x.data(), sizeof(double) * c->nn * 3, cudaMemcpyHostToDevice));
+  HOFV_CUDA(c, cudaMemcpy(c->d_fnodes, c->fnodes.data(), sizeof(int32_t) * nf * c->nfv,
+                          cudaMemcpyHostToDevice));
+  for (int64_t i = 0; i < nc * c->nv; ++i) tmp32[i] = (int32_t)c->cn[i];
+  HOFV_CUDA(c, cudaMemcpy(c->d_cnodes, tmp32.data(), sizeof(int32_t) * nc * c->nv, cudaMemcpyHostToDevice));
+  HOFV_CUDA(c, cudaMemcpy(c->d_cf, c->cf.data(), sizeof(int64_t) * nc * nlf, cudaMemcpyHostToDevice));
+  HOFV_CUDA(c, cudaMemcpy(c->d_ftag, c->ftag.data(), sizeof(int32_t) * nf, cudaMemcpyHostToDevice));
+  for (int64_t i = 0; i < nf; ++i) tmp32[i] = (int32_t)c->fown[i];
+  HOFV_CUDA(c, cudaMemcpy(c->d_fown, tmp32.data(), sizeof(int32_t) * nf, cudaMemcpyHostToDevice));
+  for (int64_t i = 0; i < nf; ++i) tmp32[i] = (int32_t)c->fnei[i];
+  HOFV_CUDA(c, cudaMemcpy(c->d_fnei, tmp32.data(), sizeof(int32_t) * nf, cudaMemcpyHostToDevice));
+  for (int64_t cell = 0; cell < nc; ++cell)
+    for (int lf = 0; lf < nlf; ++lf) {
+      const int64_t f = c->cf[cell * nlf + lf];
+      tmp32[cell * nlf + lf] = c->ftag[f] == 1 ? 0 : (c->fown[f] == cell ? (int32_t)(f + 1) : -(int32_t)(f + 1));
+    }
+  HOFV_CUDA(c, cudaMemcpy(c->d_cface, tmp32.data(), sizeof(int32_t) * nc * nlf, cudaMemcpyHostToDevice));
+  std::vector<int32_t>().swap(tmp32);
+  // ---- geometry ----
+  TRY(dev_alloc(c, &c->d_xc, nc * 3));
+  TRY(dev_alloc(c, &c->d_vol, nc));
+  TRY(dev_alloc(c, &c->d_xq, nf * c->Q * 3));
+  TRY(dev_alloc(c, &c->d_aq, nf * c->Q * 3));
+  TRY(dev_alloc(c, &c->d_xf, nf * 3));
+  TRY(dev_alloc(c, &c->d_nrm, nf * 3));
+  TRY(dev_alloc(c, &c->d_gam, nf));
+  TRY(dev_alloc(c, &c->d_cqx, nc * c->QC * 3));
+  TRY(dev_alloc(c, &c->d_cqw, nc * c->QC));
+  TRY(run_geometry(c));
+  // reference length: power of two near the mean cell size (node bounding box)
+  double vbox = 1.0;
+  for (int a = 0; a < d; ++a) {
+    double lo = c->x[a], hi = c->x[a];
+    for (int64_t i = 1; i < c->nn; ++i) {
+      lo = std::min(lo, c->x[3 * i + a]);
+      hi = std::max(hi, c->x[3 * i + a]);
+    }
+    vbox *= (hi - lo);
+  }
+  {
+    const int e = ilogb(vbox / (double)nc);
+    c->href_exp = (int)floor((double)e / d);
+  }
+  // ---- buckets of centroids (host) ----
+  std::vector<double> xc((size_t)nc * 3);
+  HOFV_CUDA(c, cudaMemcpy(xc.data(), c->d_xc, sizeof(double) * nc * 3, cudaMemcpyDeviceToHost));
+  const double bs = ldexp(1.0, c->href_exp);
+  int nb[3] = {1, 1, 1};
+  double lo[3] = {0, 0, 0};
+  for (int a = 0; a < d; ++a) {
+    double l = xc[a], h = xc[a];
+    for (int64_t i = 1; i < nc; ++i) {
+      l = std::min(l, xc[3 * i + a]);
+      h = std::max(h, xc[3 * i + a]);
+    }
+    lo[a] = l;
+    nb[a] = (int)floor((h - l) / bs) + 1;
+  }
+  const int64_t nbk = (int64_t)nb[0] * nb[1] * nb[2];
+  std::vector<int64_t> bstart((size_t)nbk + 1, 0);
+  std::vector<int64_t> bid((size_t)nc);
+  for (int64_t i = 0; i < nc; ++i) {
+    int64_t id = 0;
+    for (int a = d - 1; a >= 0; --a) {
+      int k = (int)floor((xc[3 * i + a] - lo[a]) / bs);
+      k = std::min(std::max(k, 0), nb[a] - 1);
+      id = id * nb[a] + k;
+    }
+    bid[i] = id;
+    bstart[id + 1]++;
+  }
+  for (int64_t i = 0; i < nbk; ++i) bstart[i + 1] += bstart[i];
+  std::vector<int32_t> bitems((size_t)nc);
+  {
+    std::vector<int64_t> fill(bstart.begin(), bstart.end() - 1);
+    for (int64_t i = 0; i < nc; ++i) bitems[fill[bid[i]]++] = (int32_t)i;
+  }
+  // ---- stencils ----
+  TRY(dev_alloc(c, &c->d_fst, std::max<int64_t>(c->nftile, 1) * c->S * kTile));
+  TRY(dev_alloc(c, &c->d_cst, c->nctile * c->S * kTile));
+  HOFV_CUDA(c, cudaMemset(c->d_fst, 0, sizeof(int32_t) * std::max<int64_t>(c->nftile, 1) * c->S * kTile));
+  HOFV_CUDA(c, cudaMemset(c->d_cst, 0, sizeof(int32_t) * c->nctile * c->S * kTile));
+  TRY(run_stencils(c, bstart, bitems, nb, lo, bs));
+  // ---- reconstruction coefficients ----
+  const int64_t nfco = std::max<int64_t>(c->nftile, 1) * c->S * kTile * R;
+  TRY(dev_alloc(c, &c->d_fco, nfco));
+  HOFV_CUDA(c, cudaMemset(c->d_fco, 0, sizeof(double) * nfco));
+  TRY(dev_alloc(c, &c->d_gco, std::max<int64_t>(c->nfd, 1) * R));
+  const int64_t ncex = c->nctile * c->S * kTile * nlf;
+  TRY(dev_alloc(c, &c->d_cex, ncex));
+  HOFV_CUDA(c, cudaMemset(c->d_cex, 0, sizeof(double) * ncex));
+  TRY(run_lsq(c));
+  // ---- per-face data and approximate Jacobian ----
+  TRY(dev_alloc(c, &c->d_fstar, std::max<int64_t>(c->nfid, 1) * 2));
+  TRY(dev_alloc(c, &c->d_fstab, std::max<int64_t>(c->nfid, 1)));
+  TRY(dev_alloc(c, &c->d_aj_diag, nc));
+  TRY(dev_alloc(c, &c->d_aj_col, nc * nlf));
+  TRY(dev_alloc(c, &c->d_aj_off, nc * nlf));
+  TRY(dev_alloc(c, &c->d_aj_diag32, nc));
+  TRY(dev_alloc(c, &c->d_aj_off32, nc * nlf));
+  TRY(run_face_aux(c));
+  // ---- boundary data, sources and scratch ----
+  TRY(dev_alloc(c, &c->d_ubq, std::max<int64_t>(c->nfd, 1) * c->Q * d));
+  TRY(dev_alloc(c, &c->d_ubf, std::max<int64_t>(c->nfd, 1) * d));
+  TRY(dev_alloc(c, &c->d_tbq, std::max<int64_t>(c->nft, 1) * c->Q * d));
+  TRY(dev_alloc(c, &c->d_body, nc * d));
+  TRY(dev_alloc(c, &c->d_src, nc * d));
+  HOFV_CUDA(c, cudaMemset(c->d_ubq, 0, sizeof(double) * std::max<int64_t>(c->nfd, 1) * c->Q * d));
+  HOFV_CUDA(c, cudaMemset(c->d_ubf, 0, sizeof(double) * std::max<int64_t>(c->nfd, 1) * d));
+  HOFV_CUDA(c, cudaMemset(c->d_tbq, 0, sizeof(double) * std::max<int64_t>(c->nft, 1) * c->Q * d));
+  HOFV_CUDA(c, cudaMemset(c->d_body, 0, sizeof(double) * nc * d));
+  HOFV_CUDA(c, cudaMemset(c->d_src, 0, sizeof(double) * nc * d));
+  TRY(dev_alloc(c, &c->d_ustar, nc * nlf * d));
+  TRY(dev_alloc(c, &c->d_flux, std::max<int64_t>(c->nfid, 1) * d));
+  TRY(dev_alloc(c, &c->d_w, nc * d));
+  c->red_blocks = 4 * 152;
+  TRY(dev_alloc(c, &c->d_red, (int64_t)c->red_blocks * 128));
+  TRY(dev_alloc(c, &c->d_count, 256));
+  TRY(dev_alloc(c, &c->d_scal, 256));
+  HOFV_CUDA(c, cudaMemset(c->d_count, 0, sizeof(unsigned int) * 256));
+  HOFV_CUDA(c, cudaMemset(c->d_scal, 0, sizeof(double) * 256));
+  TRY(dev_alloc(c, &c->d_cg64, 6 * nc * d));
+  TRY(dev_alloc(c, &c->d_cg32, 6 * nc * d));
+  HOFV_CUDA(c, cudaDeviceSynchronize());
+  c->src_dirty = false;
+  c->built = true;
+  c->setup_seconds =
+      std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  return HOFV_OK;
+}
+
+int hofv_get_layout(const hofv_ctx* c, hofv_layout* out) {
+  if (!c || !out) return HOFV_EINVAL;
+  if (!c->have_mesh || !c->have_scheme) return HOFV_ESTATE;
+  out->dim = c->dim;
+  out->p = c->p;
+  out->stencil = c->S;
+  out->n_t = c->Nt;
+  out->q_face = c->Q;
+  out->q_cell = c->QC;
+  out->n_cells = c->nc;
+  out->n_faces = c->nf;
+  out->n_internal = c->nfi;
+  out->n_disp = c->nfd;
+  out->n_trac = c->nft;
+  out->max_cond = c->max_cond;
+  out->setup_seconds = c->setup_seconds;
+  out->device_bytes = c->device_bytes;
+  return HOFV_OK;
+}
+
+int hofv_get_points(hofv_ctx* c, int kind, double* out) {
+  if (!c || !out) return HOFV_EINVAL;
+  if (!c->built) return fail(c, HOFV_ESTATE, "hofv_build_stencils must come first");
+  const int d = c->dim, Q = c->Q;
+  std::vector<double> buf;
+  auto fetch = [&](const double* src, int64_t count) -> int {
+    buf.resize((size_t)count);
+    HOFV_CUDA(c, cudaMemcpy(buf.data(), src, sizeof(double) * count, cudaMemcpyDeviceToHost));
+    return 0;
+  };
+  switch (kind) {
+    case HOFV_PTS_CELL_CENTROID:
+      TRY(fetch(c->d_xc, c->nc * 3));
+      for (int64_t i = 0; i < c->nc; ++i)
+        for (int a = 0; a < d; ++a) out[i * d + a] = buf[3 * i + a];
+      return 0;
+    case HOFV_PTS_CELL_VOLUME:
+      TRY(fetch(c->d_vol, c->nc));
+      memcpy(out, buf.data(), sizeof(double) * c->nc);
+      return 0;
+    case HOFV_PTS_CELL_QP:
+      TRY(fetch(c->d_cqx, c->nc * c->QC * 3));
+      for (int64_t i = 0; i < c->nc * c->QC; ++i)
+        for (int a = 0; a < d; ++a) out[i * d + a] = buf[3 * i + a];
+      return 0;
+    case HOFV_PTS_FACE_CENTRE:
+    case HOFV_PTS_DISP_CENTRE: {
+      TRY(fetch(c->d_xf, c->nf * 3));
+      const int64_t f0 = kind == HOFV_PTS_DISP_CENTRE ? c->nfi : 0;
+      const int64_t nfx = kind == HOFV_PTS_DISP_CENTRE ? c->nfd : c->nf;
+      for (int64_t i = 0; i < nfx; ++i)
+        for (int a = 0; a < d; ++a) out[i * d + a] = buf[3 * (f0 + i) + a];
+      return 0;
+    }
+    case HOFV_PTS_FACE_QP:
+    case HOFV_PTS_DISP_QP:
+    case HOFV_PTS_TRAC_QP:
+    case HOFV_PTS_FACE_AREA: {
+      TRY(fetch(kind == HOFV_PTS_FACE_AREA ? c->d_aq : c->d_xq, c->nf * Q * 3));
+      int64_t f0 = 0, nfx = c->nf;
+      if (kind == HOFV_PTS_DISP_QP) { f0 = c->nfi; nfx = c->nfd; }
+      if (kind == HOFV_PTS_TRAC_QP) { f0 = c->nfi + c->nfd; nfx = c->nft; }
+      for (int64_t i = 0; i < nfx * Q; ++i)
+        for (int a = 0; a < d; ++a) out[i * d + a] = buf[3 * (f0 * Q + i) + a];
+      return 0;
+    }
+    default:
+      return fail(c, HOFV_EINVAL, "unknown point set");
+  }
+}
+
+int hofv_set_material(hofv_ctx* c, int law, double mu, double lambda) {
+  if (!c) return HOFV_EINVAL;
+  if (law != HOFV_LAW_LINEAR && law != HOFV_LAW_NEOHOOKEAN) return fail(c, HOFV_EINVAL, "unknown law");
+  if (!(mu > 0) || !(lambda > -2.0 * mu / 3.0)) return fail(c, HOFV_EINVAL, "bad material constants");
+  c->mat.law = law;
+  c->mat.mu = mu;
+  c->mat.lam = lambda;
+  c->mat.kappa = lambda + 2.0 * mu / 3.0;
+  c->mat.kbar = 2.0 * mu + lambda;
+  c->mat.alpha = c->alpha;
+  c->have_mat = true;
+  return HOFV_OK;
+}
+
+int hofv_set_bc(hofv_ctx* c, const double* ubq, const double* ubf, const double* tbq,
+                const double* body) {
+  if (!c) return HOFV_EINVAL;
+  if (!c->built) return fail(c, HOFV_ESTATE, "hofv_build_stencils must come first");
+  const int d = c->dim;
+  auto put = [&](double* dst, const double* src, int64_t count) -> int {
+    if (count <= 0) return 0;
+    if (src)
+      HOFV_CUDA(c, cudaMemcpyAsync(dst, src, sizeof(double) * count, cudaMemcpyDeviceToDevice, c->stream));
+    else
+      HOFV_CUDA(c, cudaMemsetAsync(dst, 0, sizeof(double) * count, c->stream));
+    return 0;
+  };
+  TRY(put(c->d_ubq, ubq, c->nfd * c->Q * d));
+  TRY(put(c->d_ubf, ubf, c->nfd * d));
+  TRY(put(c->d_tbq, tbq, c->nft * c->Q * d));
+  TRY(put(c->d_body, body, c->nc * d));
+  launch_source(c, c->stream);
+  HOFV_CUDA(c, cudaGetLastError());
+  HOFV_CUDA(c, cudaStreamSynchronize(c->stream));
+  return HOFV_OK;
+}
+
+}  // extern "C"
+
+namespace hofv {
+__global__ void k_integrate(int dim, int QC, int64_t nc, const double* __restrict__ w,
+                            const double* __restrict__ f, double* __restrict__ b) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  for (int j = 0; j < dim; ++j) {
+    double s = 0.0;
+    for (int q = 0; q < QC; ++q) s = fma(w[c * QC + q], f[(c * QC + q) * dim + j], s);
+    b[j * nc + c] = s;
+  }
+}
+}  // namespace hofv
+
+extern "C" {
+
+int hofv_integrate_cells(hofv_ctx* c, const double* f_qp, double* b) {
+  if (!c || !f_qp || !b) return HOFV_EINVAL;
+  if (!c->built) return fail(c, HOFV_ESTATE, "hofv_build_stencils must come first");
+  k_integrate<<<(unsigned)((c->nc + 127) / 128), 128, 0, c->stream>>>(c->dim, c->QC, c->nc, c->d_cqw,
+                                                                       f_qp, b);
+  HOFV_CUDA(c, cudaGetLastError());
+  return HOFV_OK;
+}
+
+static int check_eval(hofv_ctx* c) {
+  if (!c) return HOFV_EINVAL;
+  if (!c->built) return fail(c, HOFV_ESTATE, "hofv_build_stencils must come first");
+  if (!c->have_mat) return fail(c, HOFV_ESTATE, "hofv_set_material must come first");
+  c->mat.alpha = c->alpha;
+  return 0;
+}
+
+int hofv_residual(hofv_ctx* c, const double* u, double* R) {
+  TRY(check_eval(c));
+  if (!u || !R) return fail(c, HOFV_EINVAL, "null vector");
+  launch_residual(dev_mesh(c), c->mat, u, nullptr, nullptr, nullptr, R, c->d_ustar, c->d_flux,
+                  c->d_ubq, c->d_ubf, c->d_src, c->stream);
+  HOFV_CUDA(c, cudaGetLastError());
+  return HOFV_OK;
+}
+
+// Jv with ||u|| already in d_scal[0]: computes ||v||, eps, w = u + eps v and
+// (R(w) - Ru) / eps into Jv.  eps stays in d_scal[2].
+static int jvp_impl(hofv_ctx* c, const double* u, const double* Ru, const double* v, double* Jv) {
+  const int64_t n = c->nc * c->dim;
+  double* sc = c->d_scal;
+  launch_norm2(v, n, c->d_red, c->d_count, sc + 1, c->red_blocks, c->stream);
+  launch_jv_eps(sc + 0, sc + 1, sc + 2, c->stream);
+  launch_waxpy_dev(c->d_w, u, v, sc + 2, 1.0, n, c->stream);
+  launch_residual(dev_mesh(c), c->mat, c->d_w, nullptr, sc + 2, Ru, Jv, c->d_ustar, c->d_flux,
+                  c->d_ubq, c->d_ubf, c->d_src, c->stream);
+  HOFV_CUDA(c, cudaGetLastError());
+  return 0;
+}
+
+int hofv_jvp(hofv_ctx* c, const double* u, const double* Ru, const double* v, double* Jv,
+             double* eps_used) {
+  TRY(check_eval(c));
+  if (!u || !Ru || !v || !Jv) return fail(c, HOFV_EINVAL, "null vector");
+  const int64_t n = c->nc * c->dim;
+  launch_norm2(u, n, c->d_red, c->d_count, c->d_scal + 0, c->red_blocks, c->stream);
+  TRY(jvp_impl(c, u, Ru, v, Jv));
+  if (eps_used) {
+    HOFV_CUDA(c, cudaMemcpyAsync(eps_used, c->d_scal + 2, sizeof(double), cudaMemcpyDeviceToHost,
+                                 c->stream));
+    HOFV_CUDA(c, cudaStreamSynchronize(c->stream));
+  }
+  return HOFV_OK;
+}
+
+int hofv_precondition(hofv_ctx* c, int kind, int iters, const double* v, double* z) {
+  TRY(check_eval(c));
+  if (!v || !z) return fail(c, HOFV_EINVAL, "null vector");
+  if (iters < 0 || iters > 100000) return fail(c, HOFV_EINVAL, "bad inner iteration count");
+  const int64_t n = c->nc * c->dim;
+  switch (kind) {
+    case HOFV_PC_NONE:
+      HOFV_CUDA(c, cudaMemcpyAsync(z, v, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
+      return HOFV_OK;
+    case HOFV_PC_AJ64:
+    case HOFV_PC_AJ32:
+      return aj_precondition(c, kind, iters, v, z);
+    case HOFV_PC_GNN: {
+      if (!c->gnn) return fail(c, HOFV_ESTATE, "no learned preconditioner loaded");
+      TRY(aj_precondition(c, HOFV_PC_AJ32, iters, v, z));
+      return gnn_apply(c, v, z, z);
+    }
+    default:
+      return fail(c, HOFV_EINVAL, "unknown preconditioner");
+  }
+}
+
+void hofv_default_opts(hofv_solve_opts* o) {
+  if (!o) return;
+  o->max_newton = 30;
+  o->rtol = 1e-8;
+  o->atol = 0.0;
+  o->restart = 30;
+  o->max_krylov = 300;
+  o->eta_max = 1e-2;
+  o->precond = HOFV_PC_AJ32;
+  o->inner_iters = 30;
+  o->line_search_max = 10;
+  o->verbose = 0;
+}
+
+}  // extern "C"
+
+namespace hofv {
+
+// host-side FGMRES state for one linear solve J x = b
+struct Fgmres {
+  std::vector<double> H;   // [(m+1) x m] column-major
+  std::vector<double> cs, sn, g, y, hbuf;
+};
+
+static int ensure_krylov(hofv_ctx* c, int m) {
+  if (c->kry_m >= m) return 0;
+  const int64_t n = c->nc * c->dim;
+  dev_free(c, c->d_V);
+  dev_free(c, c->d_Z);
+  dev_free(c, c->d_kvec);
+  dev_free(c, c->d_h);
+  c->d_V = c->d_Z = c->d_kvec = c->d_h = nullptr;
+  TRY(dev_alloc(c, &c->d_V, (int64_t)(m + 1) * n));
+  TRY(dev_alloc(c, &c->d_Z, (int64_t)m * n));
+  TRY(dev_alloc(c, &c->d_kvec, 6 * n));
+  TRY(dev_alloc(c, &c->d_h, 4 * (int64_t)(m + 2)));
+  c->kry_m = m;
+  return 0;
+}
+
+static int apply_pc(hofv_ctx* c, const hofv_solve_opts& o, const double* v, double* z,
+                    hofv_stats* st) {
+  st->precond_applies++;
+  if (o.precond == HOFV_PC_NONE) {
+    HOFV_CUDA(c, cudaMemcpyAsync(z, v, sizeof(double) * c->nc * c->dim, cudaMemcpyDeviceToDevice,
+                                 c->stream));
+    return 0;
+  }
+  if (o.precond == HOFV_PC_GNN && c->gnn) {
+    TRY(aj_precondition(c, HOFV_PC_AJ32, o.inner_iters, v, z));
+    return gnn_apply(c, v, z, z);
+  }
+  return aj_precondition(c, o.precond == HOFV_PC_AJ64 ? HOFV_PC_AJ64 : HOFV_PC_AJ32, o.inner_iters, v,
+                         z);
+}
+
+static double dev_norm(hofv_ctx* c, const double* x, int64_t n) {
+  launch_norm2(x, n, c->d_red, c->d_count, c->d_scal + 16, c->red_blocks, c->stream);
+  double v = 0;
+  cudaMemcpyAsync(&v, c->d_scal + 16, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  cudaStreamSynchronize(c->stream);
+  return v;
+}
+
+// Solve J x = b (b = -R(u)), x zero on entry, to ||b - J x|| <= tol.
+// Flexible GMRES(m), right preconditioning, classical Gram-Schmidt with one
+// re-orthogonalisation; Jv by forward differences about u (||u|| in d_scal[0]).
+static int fgmres(hofv_ctx* c, const hofv_solve_opts& o, const double* u, const double* Ru,
+                  const double* b, double* x, double tol, int max_it, hofv_stats* st,
+                  int* its_out, double* res_out) {
+  const int64_t n = c->nc * c->dim;
+  const int m = o.restart;
+  double* V = c->d_V;
+  double* Z = c->d_Z;
+  double* w = c->d_kvec;
+  double* r = c->d_kvec + n;
+  double* dh = c->d_h;
+  Fgmres F;
+  F.H.assign((size_t)(m + 1) * m, 0.0);
+  F.cs.assign(m, 0.0);
+  F.sn.assign(m, 0.0);
+  F.g.assign(m + 1, 0.0);
+  F.y.assign(m, 0.0);
+  F.hbuf.assign(2 * (m + 2), 0.0);
+  HOFV_CUDA(c, cudaMemsetAsync(x, 0, sizeof(double) * n, c->stream));
+  HOFV_CUDA(c, cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
+  int total = 0;
+  double res = dev_norm(c, r, n);
+  while (total < max_it) {
+    if (res <= tol || res == 0.0) break;
+    const double beta = res;
+    HOFV_CUDA(c, cudaMemcpyAsync(c->d_scal + 20, &beta, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    launch_scale_copy(V, r, c->d_scal + 20, 1, n, c->stream);
+    std::fill(F.g.begin(), F.g.end(), 0.0);
+    F.g[0] = beta;
+    int j = 0;
+    for (; j < m && total < max_it; ++j) {
+      double* Vj = V + (int64_t)j * n;
+      double* Zj = Z + (int64_t)j * n;
+      TRY(apply_pc(c, o, Vj, Zj, st));
+      TRY(jvp_impl(c, u, Ru, Zj, w));
+      st->residual_evals++;
+      // classical Gram-Schmidt, twice
+      launch_dots(V, n, w, j + 1, n, c->d_red, c->d_count, dh, c->red_blocks, c->stream, 0);
+      launch_multi_axpy(w, V, dh, j + 1, n, n, c->stream);
+      launch_dots(V, n, w, j + 1, n, c->d_red, c->d_count, dh + (m + 2), c->red_blocks, c->stream, 0);
+      launch_multi_axpy(w, V, dh + (m + 2), j + 1, n, n, c->stream);
+      launch_norm2(w, n, c->d_red, c->d_count, dh + 2 * (m + 2), c->red_blocks, c->stream);
+      HOFV_CUDA(c, cudaMemcpyAsync(F.hbuf.data(), dh, sizeof(double) * 2 * (m + 2),
+                                   cudaMemcpyDeviceToHost, c->stream));
+      double hn = 0.0;
+      HOFV_CUDA(c, cudaMemcpyAsync(&hn, dh + 2 * (m + 2), sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+      HOFV_CUDA(c, cudaStreamSynchronize(c->stream));
+      if (!std::isfinite(hn)) return fail(c, HOFV_ENAN, "non-finite value in the Krylov basis");
+      double* Hc = F.H.data() + (size_t)j * (m + 1);
+      for (int i = 0; i <= j; ++i) Hc[i] = F.hbuf[i] + F.hbuf[(m + 2) + i];
+      Hc[j + 1] = hn;
+      if (hn > 0.0) launch_scale_copy(V + (int64_t)(j + 1) * n, w, dh + 2 * (m + 2), 1, n, c->stream);
+      for (int i = 0; i < j; ++i) {  // previous rotations
+        const double t = F.cs[i] * Hc[i] + F.sn[i] * Hc[i + 1];
+        Hc[i + 1] = -F.sn[i] * Hc[i] + F.cs[i] * Hc[i + 1];
+        Hc[i] = t;
+      }
+      const double den = hypot(Hc[j], Hc[j + 1]);
+      F.cs[j] = den > 0 ? Hc[j] / den : 1.0;
+      F.sn[j] = den > 0 ? Hc[j + 1] / den : 0.0;
+      Hc[j] = den;
+      Hc[j + 1] = 0.0;
+      F.g[j + 1] = -F.sn[j] * F.g[j];
+      F.g[j] = F.cs[j] * F.g[j];
+      res = fabs(F.g[j + 1]);
+      ++total;
+      st->krylov_iters++;
+      if (res <= tol || hn == 0.0) {
+        ++j;
+        break;
+      }
+    }
+    // y = H^{-1} g (upper triangular j x j)
+    for (int i = j - 1; i >= 0; --i) {
+      double s = F.g[i];
+      for (int k = i + 1; k < j; ++k) s -= F.H[(size_t)k * (m + 1) + i] * F.y[k];
+      const double dgl = F.H[(size_t)i * (m + 1) + i];
+      F.y[i] = dgl != 0.0 ? s / dgl : 0.0;
+    }
+    HOFV_CUDA(c, cudaMemcpyAsync(dh, F.y.data(), sizeof(double) * j, cudaMemcpyHostToDevice, c->stream));
+    launch_combine(x, Z, dh, j, n, n, c->stream);
+    if (res <= tol || total >= max_it) break;
+    // restart: r = b - J x
+    TRY(jvp_impl(c, u, Ru, x, w));
+    st->residual_evals++;
+    HOFV_CUDA(c, cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
+    launch_axpby(r, -1.0, w, 1.0, n, c->stream);
+    res = dev_norm(c, r, n);
+  }
+  HOFV_CUDA(c, cudaStreamSynchronize(c->stream));
+  *its_out = total;
+  *res_out = res;
+  return 0;
+}
+
+}  // namespace hofv
+
+extern "C" int hofv_newton_solve(hofv_ctx* c, double* u, const hofv_solve_opts* opts,
+                                 hofv_stats* stats) {
+  TRY(check_eval(c));
+  if (!u) return fail(c, HOFV_EINVAL, "null vector");
+  hofv_solve_opts o;
+  hofv_default_opts(&o);
+  if (opts) o = *opts;
+  if (o.restart < 1 || o.restart > 100 || o.max_krylov < 1 || o.max_newton < 0)
+    return fail(c, HOFV_EINVAL, "bad solver options");
+  hofv_stats st;
+  memset(&st, 0, sizeof(st));
+  const auto t0 = std::chrono::steady_clock::now();
+  TRY(ensure_krylov(c, o.restart));
+  const int64_t n = c->nc * c->dim;
+  double* R = c->d_kvec + 2 * n;
+  double* du = c->d_kvec + 3 * n;
+  double* ut = c->d_kvec + 4 * n;
+  double* Rt = c->d_kvec + 5 * n;
+  TRY(hofv_residual(c, u, R));
+  st.residual_evals++;
+  double rn = dev_norm(c, R, n);
+  const double r0 = rn;
+  st.r0 = r0;
+  int status = HOFV_WNOTCONV;
+  if (!std::isfinite(rn)) {
+    status = fail(c, HOFV_ENAN, "non-finite initial residual");
+  } else {
+    for (int it = 0; it <= o.max_newton; ++it) {
+      if (rn <= o.rtol * r0 || rn <= o.atol || rn == 0.0) {
+        status = HOFV_OK;
+        break;
+      }
+      if (it == o.max_newton) break;
+      // rhs -R into Rt, ||u|| into d_scal[0]
+      HOFV_CUDA(c, cudaMemcpyAsync(Rt, R, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
+      launch_axpby(Rt, 0.0, Rt, -1.0, n, c->stream);
+      launch_norm2(u, n, c->d_red, c->d_count, c->d_scal + 0, c->red_blocks, c->stream);
+      const double eta = std::min(o.eta_max, rn / r0);
+      const double tol = std::max(eta * rn, 0.5 * o.rtol * r0);
+      int its = 0;
+      double lres = 0.0;
+      int rc = fgmres(c, o, u, R, Rt, du, tol, o.max_krylov, &st, &its, &lres);
+      if (rc < 0) { status = rc; break; }
+      // backtracking line search on ||R||
+      double lam = 1.0, rt = 0.0;
+      bool ok = false;
+      for (int ls = 0; ls <= o.line_search_max; ++ls) {
+        HOFV_CUDA(c, cudaMemcpyAsync(ut, u, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
+        launch_axpby(ut, lam, du, 1.0, n, c->stream);
+        TRY(hofv_residual(c, ut, Rt));
+        st.residual_evals++;
+        rt = dev_norm(c, Rt, n);
+        if (std::isfinite(rt) && rt <= (1.0 - 1e-4 * lam) * rn) {
+          ok = true;
+          break;
+        }
+        lam *= 0.5;
+      }
+      if (o.verbose)
+        fprintf(stderr, "[hofv] newton %d |R| %.3e -> %.3e  krylov %d (lin res %.2e)  lambda %.3g\n", it,
+                rn, rt, its, lres, lam);
+      if (!ok) {
+        status = fail(c, HOFV_WNOTCONV, "line search failed to reduce the residual");
+        break;
+      }
+      HOFV_CUDA(c, cudaMemcpyAsync(u, ut, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
+      HOFV_CUDA(c, cudaMemcpyAsync(R, Rt, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
+      rn = rt;
+      st.newton_iters++;
+    }
+  }
+  HOFV_CUDA(c, cudaStreamSynchronize(c->stream));
+  st.r_final = rn;
+  st.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  st.status = status;
+  if (stats) *stats = st;
+  return status;
+}
+
+extern "C" {
+
+int hofv_get_face_data(hofv_ctx* c, int64_t first, int64_t count, int32_t* stencil, double* coef) {
+  if (!c) return HOFV_EINVAL;
+  if (!c->built) return fail(c, HOFV_ESTATE, "hofv_build_stencils must come first");
+  if (first < 0 || count < 0 || first + count > c->nf) return fail(c, HOFV_EINVAL, "face range");
+  const int S = c->S, Q = c->Q, d = c->dim, R = Q * d;
+  const int64_t hi = std::min(first + count, c->nfid);
+  if (hi <= first) return HOFV_OK;
+  const int64_t t0 = first / kTile, t1 = (hi - 1) / kTile + 1;
+  std::vector<int32_t> st((size_t)(t1 - t0) * S * kTile);
+  HOFV_CUDA(c, cudaMemcpy(st.data(), c->d_fst + t0 * S * kTile, sizeof(int32_t) * st.size(),
+                          cudaMemcpyDeviceToHost));
+  std::vector<double> co;
+  std::vector<double> gc;
+  if (coef) {
+    co.resize((size_t)(t1 - t0) * S * kTile * R);
+    HOFV_CUDA(c, cudaMemcpy(co.data(), c->d_fco + t0 * S * kTile * R, sizeof(double) * co.size(),
+                            cudaMemcpyDeviceToHost));
+    if (c->nfd > 0) {
+      gc.resize((size_t)c->nfd * R);
+      HOFV_CUDA(c, cudaMemcpy(gc.data(), c->d_gco, sizeof(double) * gc.size(), cudaMemcpyDeviceToHost));
+    }
+  }
+  for (int64_t f = first; f < hi; ++f) {
+    const int64_t t = f / kTile - t0, fi = f % kTile, o = f - first;
+    for (int nn = 0; nn < S; ++nn) {
+      if (stencil) stencil[o * S + nn] = st[(t * S + nn) * kTile + fi];
+      if (coef)
+        for (int q = 0; q < Q; ++q)
+          for (int i = 0; i < d; ++i)
+            coef[((o * Q + q) * (S + 1) + nn) * d + i] = co[((t * S + nn) * kTile + fi) * R + q * d + i];
+    }
+    if (coef)
+      for (int q = 0; q < Q; ++q)
+        for (int i = 0; i < d; ++i)
+          coef[((o * Q + q) * (S + 1) + S) * d + i] = f >= c->nfi ? gc[(f - c->nfi) * R + q * d + i] : 0.0;
+  }
+  return HOFV_OK;
+}
+
+int hofv_get_cell_data(hofv_ctx* c, int64_t first, int64_t count, int32_t* stencil, double* ext) {
+  if (!c) return HOFV_EINVAL;
+  if (!c->built) return fail(c, HOFV_ESTATE, "hofv_build_stencils must come first");
+  if (first < 0 || count < 0 || first + count > c->nc) return fail(c, HOFV_EINVAL, "cell range");
+  if (count == 0) return HOFV_OK;
+  const int S = c->S, nlf = c->nlf;
+  const int64_t hi = first + count;
+  const int64_t t0 = first / kTile, t1 = (hi - 1) / kTile + 1;
+  std::vector<int32_t> st((size_t)(t1 - t0) * S * kTile);
+  HOFV_CUDA(c, cudaMemcpy(st.data(), c->d_cst + t0 * S * kTile, sizeof(int32_t) * st.size(),
+                          cudaMemcpyDeviceToHost));
+  std::vector<double> ex;
+  if (ext) {
+    ex.resize((size_t)(t1 - t0) * S * kTile * nlf);
+    HOFV_CUDA(c, cudaMemcpy(ex.data(), c->d_cex + t0 * S * kTile * nlf, sizeof(double) * ex.size(),
+                            cudaMemcpyDeviceToHost));
+  }
+  for (int64_t cell = first; cell < hi; ++cell) {
+    const int64_t t = cell / kTile - t0, ci = cell % kTile, o = cell - first;
+    for (int nn = 0; nn < S; ++nn) {
+      if (stencil) stencil[o * S + nn] = st[(t * S + nn) * kTile + ci];
+      if (ext)
+        for (int lf = 0; lf < nlf; ++lf)
+          ext[(o * nlf + lf) * S + nn] = ex[((t * S + nn) * kTile + ci) * nlf + lf];
+    }
+  }
+  return HOFV_OK;
+}
+
+int hofv_get_faces(hofv_ctx* c, int64_t* owner, int64_t* nei, int32_t* lf, int32_t* tag) {
+  if (!c) return HOFV_EINVAL;
+  if (!c->have_mesh) return fail(c, HOFV_ESTATE, "hofv_set_mesh must come first");
+  if (owner) memcpy(owner, c->fown.data(), sizeof(int64_t) * c->nf);
+  if (nei) memcpy(nei, c->fnei.data(), sizeof(int64_t) * c->nf);
+  if (lf) memcpy(lf, c->flf.data(), sizeof(int32_t) * c->nf);
+  if (tag) memcpy(tag, c->ftag.data(), sizeof(int32_t) * c->nf);
+  return HOFV_OK;
+}
+
+int hofv_get_aj(hofv_ctx* c, double* diag, double* off) {
+  if (!c) return HOFV_EINVAL;
+  if (!c->built) return fail(c, HOFV_ESTATE, "hofv_build_stencils must come first");
+  if (diag) HOFV_CUDA(c, cudaMemcpy(diag, c->d_aj_diag, sizeof(double) * c->nc, cudaMemcpyDeviceToHost));
+  if (off && c->nfi > 0) {
+    std::vector<double> fs((size_t)c->nfi);
+    HOFV_CUDA(c, cudaMemcpy(fs.data(), c->d_fstab, sizeof(double) * c->nfi, cudaMemcpyDeviceToHost));
+    memcpy(off, fs.data(), sizeof(double) * c->nfi);
+  }
+  return HOFV_OK;
+}
+
+}  // extern "C"

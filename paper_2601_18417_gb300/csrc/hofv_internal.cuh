@@ -1,0 +1,200 @@
+// hofv_internal.cuh -- context layout and kernel launchers shared by the
+// translation units of libhofv (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/hofv.h"
+
+namespace hofv {
+
+constexpr int kTile = 32;        // faces / cells per tile of the tiled layouts
+constexpr int kMaxS = 128;       // largest supported stencil (+ ghost)
+constexpr int kMaxNt = 20;       // Taylor terms of a cubic in 3-D
+constexpr int kMaxQ = 16;        // Gauss points per face (4 x 4)
+constexpr int kMaxQC = 64;       // Gauss points per cell (4^3)
+
+// Device-side description of the discretisation used by the residual
+// kernels.  All pointers are device addresses owned by the context.
+struct DevMesh {
+  int dim, nlf, S, Q, R;          // R = Q * dim rows per face
+  int64_t nc, nf, nfi, nfd, nft;
+  int64_t nfid;                   // internal + displacement faces
+  int64_t nftile;                 // face tiles of kTile (internal + disp)
+  int64_t nctile;                 // cell tiles of kTile
+  // faces (internal + displacement), index f in [0, nfid)
+  const int32_t* fst;     // [nftile][S][kTile]                stencil cell ids
+  const double* fco;      // [nftile][S][kTile][R]             gradient coefficients
+  const double* gco;      // [nfd][R]                          ghost coefficients
+  const double* aq;       // [nf][Q][3]                        vector areas
+  const int32_t* fstar;   // [nfid][2]  u* slots (cell*nlf+lf) owner, neighbour (-1 disp)
+  const double* fstab;    // [nfid]     Gamma_f / |d . n|
+  // cells
+  const int32_t* cst;     // [nctile][S][kTile]
+  const double* cex;      // [nctile][S][kTile][nlf]
+  const int32_t* cface;   // [nc][nlf]  +(f+1) owner, -(f+1) neighbour, 0 traction
+};
+
+struct Material {
+  int law;
+  double mu, lam, kappa, kbar, alpha;
+};
+
+}  // namespace hofv
+
+struct hofv_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  // ---- mesh (host) ----
+  bool have_mesh = false, have_scheme = false, built = false, have_mat = false;
+  int dim = 0, nv = 0, nlf = 0, nfv = 0;
+  int64_t nn = 0, nc = 0, nb = 0;
+  std::vector<double> x;            // [nn][3]
+  std::vector<int64_t> cn;          // [nc][nv]
+  int64_t nf = 0, nfi = 0, nfd = 0, nft = 0, nfid = 0;
+  std::vector<int64_t> fown, fnei;
+  std::vector<int32_t> flf, ftag;
+  std::vector<int32_t> fnodes;      // [nf][nfv]
+  std::vector<int64_t> cf;          // [nc][nlf]
+  // ---- scheme ----
+  int p = 0, nplus = 0, q1 = 0, S = 0, Nt = 0, Q = 0, QC = 0;
+  double kw = 6.0, alpha = 0.1;
+  int href_exp = 0;
+  double gl_x[4] = {0}, gl_w[4] = {0};
+  // ---- material ----
+  hofv::Material mat{};
+  // ---- device geometry ----
+  double* d_x = nullptr;            // [nn][3]
+  int32_t* d_fnodes = nullptr;      // [nf][nfv]
+  int32_t* d_cnodes = nullptr;      // [nc][nv]
+  double *d_xc = nullptr, *d_vol = nullptr;        // [nc][3], [nc]
+  double *d_xq = nullptr, *d_aq = nullptr;         // [nf][Q][3]
+  double *d_xf = nullptr, *d_nrm = nullptr, *d_gam = nullptr;  // [nf][3],[nf][3],[nf]
+  double *d_cqx = nullptr, *d_cqw = nullptr;       // [nc][QC][3], [nc][QC]
+  int64_t* d_cf = nullptr;          // [nc][nlf] face of each local face
+  int32_t* d_ftag = nullptr;        // [nf]
+  int32_t* d_fown = nullptr;        // [nf]
+  int32_t* d_fnei = nullptr;        // [nf]
+  // ---- stencils / coefficients ----
+  int64_t nftile = 0, nctile = 0;
+  int32_t* d_fst = nullptr;
+  double* d_fco = nullptr;
+  double* d_gco = nullptr;
+  int32_t* d_cst = nullptr;
+  double* d_cex = nullptr;
+  int32_t* d_fstar = nullptr;
+  double* d_fstab = nullptr;
+  int32_t* d_cface = nullptr;
+  double max_cond = 0.0;
+  double setup_seconds = 0.0;
+  // ---- boundary data ----
+  double* d_ubq = nullptr;          // [nfd][Q][dim]
+  double* d_ubf = nullptr;          // [nfd][dim]
+  double* d_tbq = nullptr;          // [nft][Q][dim]
+  double* d_body = nullptr;         // [dim][nc]
+  double* d_src = nullptr;          // [dim][nc]  body + traction-face fluxes
+  bool src_dirty = true;
+  // ---- scratch for the residual ----
+  double* d_ustar = nullptr;        // [nc][nlf][dim]
+  double* d_flux = nullptr;         // [nfid][dim]
+  double* d_w = nullptr;            // [dim][nc]
+  double* d_red = nullptr;          // reduction partials
+  unsigned int* d_count = nullptr;  // last-block counters
+  double* d_scal = nullptr;         // device scalars (eps, norms, CG alpha/beta)
+  int red_blocks = 0;
+  // ---- approximate Jacobian (Kbar = 1) ----
+  double* d_aj_diag = nullptr;      // [nc]
+  int32_t* d_aj_col = nullptr;      // [nc][nlf]  neighbour id or -1
+  double* d_aj_off = nullptr;       // [nc][nlf]
+  float* d_aj_diag32 = nullptr;
+  float* d_aj_off32 = nullptr;
+  // CG work vectors (sized dim*nc each)
+  double *d_cg64 = nullptr;         // 5 vectors FP64
+  float *d_cg32 = nullptr;          // 5 vectors FP32
+  // ---- Krylov ----
+  int kry_m = 0;
+  double* d_V = nullptr;            // [(m+1)][n]
+  double* d_Z = nullptr;            // [m][n]
+  double* d_kvec = nullptr;         // work vectors
+  double* d_h = nullptr;            // [m+2] projections
+  // ---- learned preconditioner ----
+  void* gnn = nullptr;
+  int64_t device_bytes = 0;
+  std::vector<void*> allocs;
+};
+
+namespace hofv {
+
+// error helpers
+int fail(hofv_ctx* c, int code, const std::string& msg);
+int cuda_fail(hofv_ctx* c, cudaError_t e, const char* what);
+#define HOFV_CUDA(ctx, call)                                   \
+  do {                                                         \
+    cudaError_t e_ = (call);                                   \
+    if (e_ != cudaSuccess) return hofv::cuda_fail(ctx, e_, #call); \
+  } while (0)
+
+template <typename T>
+int dev_alloc(hofv_ctx* c, T** p, size_t count) {
+  void* q = nullptr;
+  size_t bytes = count * sizeof(T) + 16;
+  cudaError_t e = cudaMalloc(&q, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return fail(c, HOFV_ENOMEM, std::string("cudaMalloc of ") + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e));
+  }
+  c->allocs.push_back(q);
+  c->device_bytes += (int64_t)bytes;
+  *p = static_cast<T*>(q);
+  return 0;
+}
+void dev_free(hofv_ctx* c, void* p);
+
+DevMesh dev_mesh(const hofv_ctx* c);
+
+// ---- set-up kernels (setup.cu) ----
+int run_geometry(hofv_ctx* c);
+int run_stencils(hofv_ctx* c, const std::vector<int64_t>& bucket_start,
+                 const std::vector<int32_t>& bucket_items, const int nb[3], const double lo[3],
+                 double bs);
+int run_lsq(hofv_ctx* c);
+int run_face_aux(hofv_ctx* c);
+
+// ---- residual kernels (residual.cu) ----
+// R = residual(w) where w = u (+ eps * v when v != nullptr, eps read from
+// *d_eps on the device); when R0 != nullptr the output is (R(w) - R0) / eps.
+void launch_residual(const DevMesh& m, const Material& mat, const double* u, const double* v,
+                     const double* d_eps, const double* R0, double* out, double* ustar,
+                     double* flux, const double* ubq, const double* ubf, const double* src,
+                     cudaStream_t st);
+void launch_source(const hofv_ctx* c, cudaStream_t st);
+
+// ---- vector kernels (krylov.cu) ----
+// out[i] = sum over blocks of partial dot products, deterministic order
+// out[k] = X_k . y (mode 0) for k < nvec with X_k = X + k * ldx; mode 1: sqrt
+void launch_dots(const double* X, int64_t ldx, const double* y, int nvec, int64_t n, double* red,
+                 unsigned int* count, double* out, int blocks, cudaStream_t st, int mode);
+void launch_norm2(const double* x, int64_t n, double* red, unsigned int* count, double* out,
+                  int blocks, cudaStream_t st);
+void launch_jv_eps(const double* u_norm, const double* v_norm, double* eps, cudaStream_t st);
+// y = x + sign * alpha[0] * v
+void launch_waxpy_dev(double* y, const double* x, const double* v, const double* alpha,
+                      double sign, int64_t n, cudaStream_t st);
+void launch_scale_copy(double* y, const double* x, const double* s, int invert, int64_t n,
+                       cudaStream_t st);
+void launch_multi_axpy(double* w, const double* V, const double* coef, int k, int64_t n,
+                       int64_t ld, cudaStream_t st);
+void launch_combine(double* x, const double* Z, const double* y, int k, int64_t n, int64_t ld,
+                    cudaStream_t st);
+void launch_axpby(double* y, double a, const double* x, double b, int64_t n, cudaStream_t st);
+int aj_precondition(hofv_ctx* c, int kind, int iters, const double* v, double* z);
+
+// ---- learned preconditioner (gnn.cu) ----
+int gnn_apply(hofv_ctx* c, const double* v, const double* z_aj, double* z);
+
+}  // namespace hofv

@@ -1,0 +1,307 @@
+// residual.cu -- the matrix-free residual R(u) of the high-order
+// cell-centred finite-volume scheme (arXiv 2601.18417):
+//
+//   k_ustar : cell-ordered; extrapolated face values of the alpha
+//             stabilisation, u*_{f,P} = u_P + sum_N e_N u_N (eq. alphaJump,
+//             App. B, with the Taylor terms folded into e at set-up)
+//   k_flux  : face-ordered, 32 faces per tile; (1) displacement gradient at
+//             every Gauss point, grad u = sum_N c_N (x) u_N (+ ghost node,
+//             eq. faceQuadGrad), (2) the law (App. A) and traction T a_q,
+//             (3) Gauss quadrature over the face plus the stabilisation
+//             traction alpha Kbar / |d.n| (u*_N - u*_P) Gamma (eq. alpha)
+//   k_cell  : cell-ordered, fixed face order (no atomics):
+//             R_P = sum_f +-flux_f + source_P (eq. divStressDiscret +
+//             eq. bodyTerm); optional epilogue (R - R0) / eps for Jv.
+//
+// All arithmetic is FP64.  Every FP64 instruction of the gradient phase runs
+// with all 32 lanes busy: a tile's (face, row) pairs are laid out so that
+// consecutive threads own consecutive coefficient rows.
+#include "hofv_internal.cuh"
+
+namespace hofv {
+
+// ---------------------------------------------------------------------
+// stabilisation extrapolation: one thread per (cell, local face)
+// ---------------------------------------------------------------------
+template <int DIM>
+__global__ void __launch_bounds__(32 * 2 * DIM)
+    k_ustar(DevMesh m, const double* __restrict__ w, double* __restrict__ ustar) {
+  constexpr int NLF = 2 * DIM;
+  const int64_t tile = blockIdx.x;
+  const int it = threadIdx.x;            // ci * NLF + lf
+  const int ci = it / NLF;
+  const int64_t cell = tile * kTile + ci;
+  const int32_t* __restrict__ st = m.cst + tile * m.S * kTile + ci;
+  const double* __restrict__ ex = m.cex + tile * (int64_t)m.S * kTile * NLF + it;
+  double acc[DIM];
+#pragma unroll
+  for (int j = 0; j < DIM; ++j) acc[j] = 0.0;
+  const int64_t nc = m.nc;
+#pragma unroll 4
+  for (int n = 0; n < m.S; ++n) {
+    const int32_t id = __ldg(st + n * kTile);
+    const double e = __ldg(ex + (int64_t)n * kTile * NLF);
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) acc[j] = fma(e, __ldg(w + j * nc + id), acc[j]);
+  }
+  if (cell < nc) {
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) ustar[(cell * NLF + (it % NLF)) * DIM + j] = w[j * nc + cell] + acc[j];
+  }
+}
+
+// ---------------------------------------------------------------------
+// laws: traction t = T a from G[i][j] = du_j/dx_i
+// ---------------------------------------------------------------------
+template <int DIM, int LAW>
+__device__ __forceinline__ void traction(const double (&G)[3][3], const double* a, const Material& mt,
+                                         double* t) {
+  if (LAW == HOFV_LAW_LINEAR) {
+    // sigma = mu (G + G^T) + lambda tr(G) I, eq. (linearElastic)
+    double tr = 0.0;
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) tr += G[i][i];
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) {
+      double s = mt.lam * tr * a[i];
+#pragma unroll
+      for (int j = 0; j < DIM; ++j) s = fma(mt.mu * (G[i][j] + G[j][i]), a[j], s);
+      t[i] = s;
+    }
+  } else {
+    // neo-Hookean, eq. (neoHook), first Piola-Kirchhoff P = J sigma F^{-T}
+    // (eq. nanson).  With tau = J sigma = mu dev(bbar) + kappa/2 (J^2-1) I
+    // and F^{-T} = cof(F) / J:  P = tau cof(F) / J.
+    double F[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) F[i][j] = (i == j ? 1.0 : 0.0) + G[j][i];
+    double C[3][3];  // cofactor matrix
+    C[0][0] = F[1][1] * F[2][2] - F[1][2] * F[2][1];
+    C[0][1] = F[1][2] * F[2][0] - F[1][0] * F[2][2];
+    C[0][2] = F[1][0] * F[2][1] - F[1][1] * F[2][0];
+    C[1][0] = F[0][2] * F[2][1] - F[0][1] * F[2][2];
+    C[1][1] = F[0][0] * F[2][2] - F[0][2] * F[2][0];
+    C[1][2] = F[0][1] * F[2][0] - F[0][0] * F[2][1];
+    C[2][0] = F[0][1] * F[1][2] - F[0][2] * F[1][1];
+    C[2][1] = F[0][2] * F[1][0] - F[0][0] * F[1][2];
+    C[2][2] = F[0][0] * F[1][1] - F[0][1] * F[1][0];
+    const double J = F[0][0] * C[0][0] + F[0][1] * C[0][1] + F[0][2] * C[0][2];
+    // J^{-2/3}; not defined for J <= 0 (an inverted element): NaN, so the
+    // caller's finiteness checks reject the state
+    const double jm23 = J > 0.0 ? rcbrt(J * J) : __longlong_as_double(0x7ff8000000000000LL);
+    double b[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = i; j < 3; ++j) {
+        const double s = F[i][0] * F[j][0] + F[i][1] * F[j][1] + F[i][2] * F[j][2];
+        b[i][j] = b[j][i] = jm23 * s;
+      }
+    const double tb = (b[0][0] + b[1][1] + b[2][2]) * (1.0 / 3.0);
+    const double pvol = 0.5 * mt.kappa * (J * J - 1.0);
+    double tau[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) tau[i][j] = mt.mu * (b[i][j] - (i == j ? tb : 0.0)) + (i == j ? pvol : 0.0);
+    // t = P a = tau (cof(F) a) / J
+    double ca[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      double s = 0.0;
+#pragma unroll
+      for (int l = 0; l < DIM; ++l) s = fma(C[k][l], a[l], s);
+      ca[k] = s;
+    }
+    const double iJ = 1.0 / J;
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) {
+      double s = 0.0;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) s = fma(tau[i][k], ca[k], s);
+      t[i] = s * iJ;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------
+// face fluxes, one tile of 32 faces per block, blockDim = 32 * R
+// ---------------------------------------------------------------------
+template <int DIM, int LAW>
+__global__ void __launch_bounds__(DIM == 3 ? 864 : 256)
+    k_flux(DevMesh m, Material mt, const double* __restrict__ w, const double* __restrict__ ustar,
+           const double* __restrict__ ubq, const double* __restrict__ ubf,
+           double* __restrict__ flux) {
+  extern __shared__ double sm[];
+  const int R = m.R, Q = m.Q, S = m.S;
+  double* Gs = sm;                        // [32][R][DIM]
+  double* Ts = sm + kTile * R * DIM;      // [32][Q][DIM]
+  const int64_t tile = blockIdx.x;
+  const int it = threadIdx.x;
+  const int64_t nc = m.nc;
+  // (1) gradient rows: thread (fi, r) accumulates sum_N c_{r,N} u_N
+  {
+    const int fi = it / R, r = it % R;
+    const int64_t f = tile * kTile + fi;
+    const int32_t* __restrict__ st = m.fst + tile * S * kTile + fi;
+    const double* __restrict__ co = m.fco + tile * (int64_t)S * kTile * R + it;
+    double acc[DIM];
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) acc[j] = 0.0;
+#pragma unroll 4
+    for (int n = 0; n < S; ++n) {
+      const int32_t id = __ldg(st + n * kTile);
+      const double c = __ldg(co + (int64_t)n * kTile * R);
+#pragma unroll
+      for (int j = 0; j < DIM; ++j) acc[j] = fma(c, __ldg(w + j * nc + id), acc[j]);
+    }
+    if (f >= m.nfi && f < m.nfid) {  // ghost node of a displacement face
+      const int64_t fd = f - m.nfi;
+      const double cg = m.gco[fd * R + r];
+      const int q = r / DIM;
+#pragma unroll
+      for (int j = 0; j < DIM; ++j) acc[j] = fma(cg, ubq[(fd * Q + q) * DIM + j], acc[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) Gs[(fi * R + r) * DIM + j] = acc[j];
+  }
+  __syncthreads();
+  // (2) law and traction at each Gauss point
+  if (it < kTile * Q) {
+    const int fi = it / Q, q = it % Q;
+    const int64_t f = tile * kTile + fi;
+    double t[DIM];
+    if (f < m.nfid) {
+      double G[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+#pragma unroll
+      for (int i = 0; i < DIM; ++i)
+#pragma unroll
+        for (int j = 0; j < DIM; ++j) G[i][j] = Gs[(fi * R + q * DIM + i) * DIM + j];
+      double a[3];
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) a[k] = m.aq[(f * Q + q) * 3 + k];
+      traction<DIM, LAW>(G, a, mt, t);
+    } else {
+#pragma unroll
+      for (int i = 0; i < DIM; ++i) t[i] = 0.0;
+    }
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) Ts[(fi * Q + q) * DIM + i] = t[i];
+  }
+  __syncthreads();
+  // (3) quadrature over the face + alpha stabilisation
+  if (it < kTile * DIM) {
+    const int fi = it / DIM, i = it % DIM;
+    const int64_t f = tile * kTile + fi;
+    if (f < m.nfid) {
+      double s = 0.0;
+      for (int q = 0; q < Q; ++q) s += Ts[(fi * Q + q) * DIM + i];
+      const int32_t sp = m.fstar[2 * f], sn = m.fstar[2 * f + 1];
+      const double other = sn >= 0 ? ustar[(int64_t)sn * DIM + i] : ubf[(f - m.nfi) * DIM + i];
+      const double coef = mt.alpha * mt.kbar * m.fstab[f];
+      flux[f * DIM + i] = fma(coef, other - ustar[(int64_t)sp * DIM + i], s);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------
+// cell assembly; out = R, or (R - R0) * inv_eps when R0 != nullptr
+// ---------------------------------------------------------------------
+template <int DIM>
+__global__ void k_cell(DevMesh m, const double* __restrict__ flux, const double* __restrict__ src,
+                       const double* __restrict__ R0, const double* __restrict__ d_eps,
+                       double* __restrict__ out) {
+  constexpr int NLF = 2 * DIM;
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= m.nc) return;
+  double r[DIM];
+#pragma unroll
+  for (int j = 0; j < DIM; ++j) r[j] = src ? src[j * m.nc + c] : 0.0;
+#pragma unroll
+  for (int lf = 0; lf < NLF; ++lf) {
+    const int32_t code = m.cface[c * NLF + lf];
+    if (code == 0) continue;
+    const int64_t f = (code > 0 ? code : -code) - 1;
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) {
+      const double v = flux[f * DIM + j];
+      r[j] = code > 0 ? r[j] + v : r[j] - v;
+    }
+  }
+  if (R0) {
+    const double ie = 1.0 / d_eps[0];
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) out[j * m.nc + c] = (r[j] - R0[j * m.nc + c]) * ie;
+  } else {
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) out[j * m.nc + c] = r[j];
+  }
+}
+
+template <int DIM, int LAW>
+static void residual_impl(const DevMesh& m, const Material& mat, const double* w,
+                          const double* d_eps, const double* R0, double* out, double* ustar,
+                          double* flux, const double* ubq, const double* ubf, const double* src,
+                          cudaStream_t st) {
+  k_ustar<DIM><<<(unsigned)m.nctile, 32 * 2 * DIM, 0, st>>>(m, w, ustar);
+  if (m.nftile > 0) {
+    const size_t smem = sizeof(double) * kTile * (m.R * DIM + m.Q * DIM);
+    k_flux<DIM, LAW><<<(unsigned)m.nftile, kTile * m.R, smem, st>>>(m, mat, w, ustar, ubq, ubf, flux);
+  }
+  k_cell<DIM><<<(unsigned)((m.nc + 255) / 256), 256, 0, st>>>(m, flux, src, R0, d_eps, out);
+}
+
+void launch_residual(const DevMesh& m, const Material& mat, const double* w, const double* /*v*/,
+                     const double* d_eps, const double* R0, double* out, double* ustar,
+                     double* flux, const double* ubq, const double* ubf, const double* src,
+                     cudaStream_t st) {
+  if (m.dim == 2) {
+    if (mat.law == HOFV_LAW_LINEAR)
+      residual_impl<2, 0>(m, mat, w, d_eps, R0, out, ustar, flux, ubq, ubf, src, st);
+    else
+      residual_impl<2, 1>(m, mat, w, d_eps, R0, out, ustar, flux, ubq, ubf, src, st);
+  } else {
+    if (mat.law == HOFV_LAW_LINEAR)
+      residual_impl<3, 0>(m, mat, w, d_eps, R0, out, ustar, flux, ubq, ubf, src, st);
+    else
+      residual_impl<3, 1>(m, mat, w, d_eps, R0, out, ustar, flux, ubq, ubf, src, st);
+  }
+}
+
+// ---------------------------------------------------------------------
+// constant source per cell: integrated body force + traction-face fluxes
+// sum_q |a_q| T_{b,q} (eq. divStressDiscret, traction term)
+// ---------------------------------------------------------------------
+__global__ void k_source(int dim, int nlf, int Q, int64_t nc, int64_t nfi, int64_t nfd,
+                         const int64_t* __restrict__ cf, const int32_t* __restrict__ ftag,
+                         const double* __restrict__ aq, const double* __restrict__ tbq,
+                         const double* __restrict__ body, double* __restrict__ src) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  for (int j = 0; j < dim; ++j) {
+    double s = body ? body[j * nc + c] : 0.0;
+    if (tbq) {
+      for (int lf = 0; lf < nlf; ++lf) {
+        const int64_t f = cf[c * nlf + lf];
+        if (ftag[f] != 1) continue;
+        const int64_t b = f - nfi - nfd;
+        for (int q = 0; q < Q; ++q) {
+          const double* a = aq + (f * Q + q) * 3;
+          const double mag = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+          s += mag * tbq[(b * Q + q) * dim + j];
+        }
+      }
+    }
+    src[j * nc + c] = s;
+  }
+}
+
+void launch_source(const hofv_ctx* c, cudaStream_t st) {
+  k_source<<<(unsigned)((c->nc + 127) / 128), 128, 0, st>>>(
+      c->dim, c->nlf, c->Q, c->nc, c->nfi, c->nfd, c->d_cf, c->d_ftag, c->d_aq,
+      c->nft > 0 ? c->d_tbq : nullptr, c->d_body, c->d_src);
+}
+
+}  // namespace hofv

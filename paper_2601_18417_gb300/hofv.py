@@ -1,0 +1,253 @@
+"""Thin Python binding of libhofv (C ABI in ``include/hofv.h``).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Device vectors are torch CUDA tensors (FP64, component-major
+``[dim, n_cells]``); torch provides device memory and the stream.  The
+library must have been built (``paper_2601_18417_gb300.build.build()``);
+loading fails loudly otherwise -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhofv.so")
+
+OK, WNOTCONV = 0, 1
+EINVAL, ENOMEM, ECUDA, EILLCOND, ENAN, ENOTSUP, ESTATE = -1, -2, -3, -4, -5, -6, -7
+LAW_LINEAR, LAW_NEOHOOKEAN = 0, 1
+PC_NONE, PC_AJ64, PC_AJ32, PC_GNN = -1, 0, 1, 2
+PTS_CELL_CENTROID, PTS_DISP_QP, PTS_DISP_CENTRE, PTS_TRAC_QP, PTS_CELL_QP = 0, 1, 2, 3, 4
+PTS_FACE_CENTRE, PTS_FACE_QP, PTS_FACE_AREA, PTS_CELL_VOLUME = 5, 6, 7, 8
+
+
+class HofvError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"hofv error {code}: {msg}")
+        self.code = code
+
+
+class Layout(C.Structure):
+    _fields_ = [("dim", C.c_int32), ("p", C.c_int32), ("stencil", C.c_int32), ("n_t", C.c_int32),
+                ("q_face", C.c_int32), ("q_cell", C.c_int32), ("n_cells", C.c_int64),
+                ("n_faces", C.c_int64), ("n_internal", C.c_int64), ("n_disp", C.c_int64),
+                ("n_trac", C.c_int64), ("max_cond", C.c_double), ("setup_seconds", C.c_double),
+                ("device_bytes", C.c_int64)]
+
+
+class SolveOpts(C.Structure):
+    _fields_ = [("max_newton", C.c_int32), ("rtol", C.c_double), ("atol", C.c_double),
+                ("restart", C.c_int32), ("max_krylov", C.c_int32), ("eta_max", C.c_double),
+                ("precond", C.c_int32), ("inner_iters", C.c_int32),
+                ("line_search_max", C.c_int32), ("verbose", C.c_int32)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("newton_iters", C.c_int32), ("krylov_iters", C.c_int32),
+                ("residual_evals", C.c_int32), ("precond_applies", C.c_int32),
+                ("gnn_fallbacks", C.c_int32), ("r0", C.c_double), ("r_final", C.c_double),
+                ("seconds", C.c_double), ("status", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+# exported entry points and their argument types
+_P, _I, _I64, _D = C.c_void_p, C.c_int, C.c_int64, C.c_double
+SIGNATURES = {
+    "hofv_create": (_I, [C.POINTER(_P), _I, _P]),
+    "hofv_destroy": (None, [_P]),
+    "hofv_last_error": (C.c_char_p, [_P]),
+    "hofv_version": (C.c_char_p, []),
+    "hofv_set_mesh": (_I, [_P, _I, _I64, _P, _I64, _P, _I64, _P, _P]),
+    "hofv_set_scheme": (_I, [_P, _I, _I, _I, _D, _D]),
+    "hofv_build_stencils": (_I, [_P]),
+    "hofv_get_layout": (_I, [_P, C.POINTER(Layout)]),
+    "hofv_get_points": (_I, [_P, _I, _P]),
+    "hofv_set_material": (_I, [_P, _I, _D, _D]),
+    "hofv_set_bc": (_I, [_P, _P, _P, _P, _P]),
+    "hofv_integrate_cells": (_I, [_P, _P, _P]),
+    "hofv_residual": (_I, [_P, _P, _P]),
+    "hofv_jvp": (_I, [_P, _P, _P, _P, _P, C.POINTER(_D)]),
+    "hofv_precondition": (_I, [_P, _I, _I, _P, _P]),
+    "hofv_newton_solve": (_I, [_P, _P, C.POINTER(SolveOpts), C.POINTER(Stats)]),
+    "hofv_default_opts": (None, [C.POINTER(SolveOpts)]),
+    "hofv_get_face_data": (_I, [_P, _I64, _I64, _P, _P]),
+    "hofv_get_cell_data": (_I, [_P, _I64, _I64, _P, _P]),
+    "hofv_get_faces": (_I, [_P, _P, _P, _P, _P]),
+    "hofv_get_aj": (_I, [_P, _P, _P]),
+}
+
+
+def load():
+    """Load libhofv.so (no fallback: raises if it is missing)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -m paper_2601_18417_gb300.build` (needs nvcc)")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data_as(C.c_void_p)
+    return C.c_void_p(t.data_ptr())
+
+
+def _dev(t, dtype_name="float64"):
+    import torch
+    if t is None:
+        return None
+    if not (t.is_cuda and t.is_contiguous() and str(t.dtype) == f"torch.{dtype_name}"):
+        raise ValueError(f"expected a contiguous CUDA {dtype_name} tensor")
+    return t
+
+
+class Context:
+    """One hofv context on a CUDA device and stream (torch's current stream
+    unless given)."""
+
+    def __init__(self, device: int = 0, stream=None):
+        import torch
+        L = load()
+        self._L = L
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.stream = stream
+        h = C.c_void_p()
+        rc = L.hofv_create(C.byref(h), device, C.c_void_p(stream.cuda_stream))
+        if rc != 0:
+            raise HofvError(rc, "hofv_create failed (no CUDA device?)")
+        self.h = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._L.hofv_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc, allow_warn=False):
+        if rc < 0 or (rc > 0 and not allow_warn):
+            raise HofvError(rc, self._L.hofv_last_error(self.h).decode())
+        return rc
+
+    # ---- set-up --------------------------------------------------------
+    def set_mesh(self, mesh, bface_tag):
+        xyz = np.ascontiguousarray(mesh.xyz, np.float64)
+        cn = np.ascontiguousarray(mesh.cell_nodes, np.int64)
+        bn = np.ascontiguousarray(mesh.bface_nodes, np.int64)
+        tag = np.ascontiguousarray(bface_tag, np.int32)
+        self.dim = mesh.dim
+        return self._check(self._L.hofv_set_mesh(self.h, mesh.dim, xyz.shape[0], _ptr(xyz),
+                                                 cn.shape[0], _ptr(cn), bn.shape[0], _ptr(bn),
+                                                 _ptr(tag)))
+
+    def set_scheme(self, p, n_plus, q_per_dir, k_weight=6.0, alpha=0.1):
+        return self._check(self._L.hofv_set_scheme(self.h, p, n_plus, q_per_dir, k_weight, alpha))
+
+    def build_stencils(self):
+        self._check(self._L.hofv_build_stencils(self.h))
+        self.layout = self.get_layout()
+        return self.layout
+
+    def get_layout(self) -> Layout:
+        lay = Layout()
+        self._check(self._L.hofv_get_layout(self.h, C.byref(lay)))
+        return lay
+
+    def get_points(self, kind):
+        lay = self.layout
+        d = lay.dim
+        shapes = {PTS_CELL_CENTROID: (lay.n_cells, d), PTS_DISP_QP: (lay.n_disp, lay.q_face, d),
+                  PTS_DISP_CENTRE: (lay.n_disp, d), PTS_TRAC_QP: (lay.n_trac, lay.q_face, d),
+                  PTS_CELL_QP: (lay.n_cells, lay.q_cell, d), PTS_FACE_CENTRE: (lay.n_faces, d),
+                  PTS_FACE_QP: (lay.n_faces, lay.q_face, d),
+                  PTS_FACE_AREA: (lay.n_faces, lay.q_face, d), PTS_CELL_VOLUME: (lay.n_cells,)}
+        out = np.zeros(shapes[kind])
+        self._check(self._L.hofv_get_points(self.h, kind, _ptr(out)))
+        return out
+
+    def set_material(self, law, mu, lam):
+        return self._check(self._L.hofv_set_material(self.h, law, mu, lam))
+
+    def set_bc(self, u_bq=None, u_bf=None, t_bq=None, body=None):
+        args = [_dev(t) for t in (u_bq, u_bf, t_bq, body)]
+        return self._check(self._L.hofv_set_bc(self.h, *[_ptr(a) for a in args]))
+
+    def integrate_cells(self, f_qp, out):
+        return self._check(self._L.hofv_integrate_cells(self.h, _ptr(_dev(f_qp)), _ptr(_dev(out))))
+
+    # ---- evaluation ------------------------------------------------------
+    def residual(self, u, R):
+        return self._check(self._L.hofv_residual(self.h, _ptr(_dev(u)), _ptr(_dev(R))))
+
+    def jvp(self, u, Ru, v, Jv, want_eps=False):
+        eps = C.c_double(0.0)
+        self._check(self._L.hofv_jvp(self.h, _ptr(_dev(u)), _ptr(_dev(Ru)), _ptr(_dev(v)),
+                                     _ptr(_dev(Jv)), C.byref(eps) if want_eps else None))
+        return eps.value if want_eps else None
+
+    def precondition(self, kind, inner_iters, v, z):
+        return self._check(self._L.hofv_precondition(self.h, kind, inner_iters, _ptr(_dev(v)),
+                                                     _ptr(_dev(z))))
+
+    def newton_solve(self, u, **opts):
+        o = SolveOpts()
+        self._L.hofv_default_opts(C.byref(o))
+        for k, v in opts.items():
+            setattr(o, k, v)
+        st = Stats()
+        rc = self._L.hofv_newton_solve(self.h, _ptr(_dev(u)), C.byref(o), C.byref(st))
+        self._check(rc, allow_warn=True)
+        return st.as_dict()
+
+    # ---- inspection --------------------------------------------------------
+    def get_face_data(self, first, count, coef=True):
+        lay = self.layout
+        st = np.zeros((count, lay.stencil), np.int32)
+        co = np.zeros((count, lay.q_face, lay.stencil + 1, lay.dim)) if coef else None
+        self._check(self._L.hofv_get_face_data(self.h, first, count, _ptr(st), _ptr(co)))
+        return st, co
+
+    def get_cell_data(self, first, count, ext=True):
+        lay = self.layout
+        st = np.zeros((count, lay.stencil), np.int32)
+        ex = np.zeros((count, 2 * lay.dim, lay.stencil)) if ext else None
+        self._check(self._L.hofv_get_cell_data(self.h, first, count, _ptr(st), _ptr(ex)))
+        return st, ex
+
+    def get_faces(self):
+        n = self.layout.n_faces
+        own = np.zeros(n, np.int64)
+        nei = np.zeros(n, np.int64)
+        lf = np.zeros(n, np.int32)
+        tag = np.zeros(n, np.int32)
+        self._check(self._L.hofv_get_faces(self.h, _ptr(own), _ptr(nei), _ptr(lf), _ptr(tag)))
+        return own, nei, lf, tag
+
+    def get_aj(self):
+        lay = self.layout
+        diag = np.zeros(lay.n_cells)
+        off = np.zeros(max(lay.n_internal, 1))
+        self._check(self._L.hofv_get_aj(self.h, _ptr(diag), _ptr(off)))
+        return diag, off[: lay.n_internal]

@@ -140,3 +140,27 @@ def probe_jacobian(pb: Problem, K: int | None = None):
                         vals.append(dR[rc, r])
     J = sp.csr_matrix((vals, (rows, cols)), shape=(d * nc, d * nc))
     return J, R0
+
+
+# ---------------------------------------------------------------- GPU side
+def gpu_context(pb: Problem, alpha=0.1, k_weight=6.0):
+    """Library context on cuda:0 for the same mesh, scheme, material and
+    boundary data as the oracle problem `pb`."""
+    import torch
+    from paper_2601_18417_gb300 import hofv
+    o = pb.orc
+    ctx = hofv.Context(0)
+    ctx.set_mesh(pb.mesh, o.bface_tag)
+    ctx.set_scheme(o.p, o.n_plus, o.q1, k_weight, alpha)
+    ctx.build_stencils()
+    ctx.set_material(pb.law, pb.mu, pb.lam)
+    dev = torch.device("cuda", 0)
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)  # noqa: E731
+    ctx.set_bc(t(pb.ubq) if pb.ubq.size else None, t(pb.ubf) if pb.ubf.size else None,
+               t(pb.tbq) if pb.tbq.size else None, t(pb.body))
+    return ctx
+
+
+def to_dev(a):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda:0")
