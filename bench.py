@@ -1,0 +1,402 @@
+#!/usr/bin/env python
+"""Benchmark of the high-order FV-JFNK hot path on GB300.
+
+Default (N=1): the 2-D, 512 x 512 jittered quad workload with cubic
+least-squares reconstruction (3 Gauss points per face), linear elasticity,
+the paper's mixed manufactured field.  One timed step is one flexible-GMRES
+Arnoldi step of the JFNK solver -- the approximate-Jacobian preconditioner
+(FP32 inner CG), the forward-difference Jacobian-vector product (one FP64
+residual evaluation), two Gram-Schmidt passes against 16 basis vectors and
+the normalisation -- i.e. one pass over every kernel of the hot path.
+``value`` counts residual evaluations: cells x evaluations / s (Mcell/s).
+
+Also reported on the same JSON line: the roofline of the dominant kernel
+(face fluxes, FP64-ALU bound on this GPU), the oracle timed on the host
+cores on a bounded sample, an end-to-end number through the public API with
+host buffers, the time to a 1e-8 residual reduction for the FP64 and FP32
+approximate-Jacobian preconditioners, clocks sampled during the timed region.
+
+``--impl reference`` times the CPU oracle as it stands (the only reference
+available: the paper ships no code) on the same workload.
+Multi-GPU runs (torchrun) are independent replicas, one per rank.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "residual evals/s (Mcell/s, % HBM roofline); JFNK time to 1e-8, learned vs plain"
+KRYLOV_J = 15          # Arnoldi index of the timed step (16 basis vectors)
+INNER_ITERS = 20       # approximate-Jacobian CG iterations per preconditioner apply
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ------------------------------------------------------------------ workload
+def build_workload(name, device=0):
+    import torch
+
+    from paper_2601_18417_gb300 import hofv
+    from paper_2601_18417_gb300 import inputs as I
+    wl = I.WORKLOADS[name]
+    mesh = I.structured_mesh(wl.dim, wl.n, jitter=wl.jitter, seed=wl.mesh_seed)
+    tags = I.side_tags(wl.problem, wl.dim)[mesh.bface_side]
+    ctx = hofv.Context(device)
+    ctx.set_mesh(mesh, tags)
+    ctx.set_scheme(wl.p, wl.n_plus, wl.q1, wl.k_weight, wl.alpha)
+    t0 = time.perf_counter()
+    lay = ctx.build_stencils()
+    setup_s = time.perf_counter() - t0
+    ctx.set_material(wl.law, wl.mu, wl.lam)
+    dev = torch.device("cuda", device)
+    T = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)  # noqa
+    field = I.field_for(wl.problem, wl.dim)
+    xq = ctx.get_points(hofv.PTS_DISP_QP)
+    xb = ctx.get_points(hofv.PTS_DISP_CENTRE)
+    if field is not None:
+        ubq, ubf = field.value(xq), field.value(xb)
+        fq = T(field.body_force(ctx.get_points(hofv.PTS_CELL_QP), wl.mu, wl.lam))
+        body = torch.empty((wl.dim, lay.n_cells), dtype=torch.float64, device=dev)
+        ctx.integrate_cells(fq, body)
+    else:
+        top = I.block_top_displacement(1, wl.load_steps, wl.dim)
+        on_top = np.abs(xb[:, wl.dim - 1] - 1.0) < 1e-9
+        ubq = np.where(on_top[:, None, None], top, 0.0) * np.ones_like(xq)
+        ubf = np.where(on_top[:, None], top, 0.0) * np.ones_like(xb)
+        body = None
+    ctx.set_bc(T(ubq), T(ubf), None, body)
+    xc = ctx.get_points(hofv.PTS_CELL_CENTROID)
+    if field is not None:
+        u_ex = field.value(xc).T.copy()
+    else:
+        u_ex = (I.block_top_displacement(1, wl.load_steps, wl.dim)[:, None]
+                * xc[:, wl.dim - 1][None, :])
+    return wl, mesh, ctx, lay, setup_s, u_ex, field
+
+
+def algorithmic_counts(wl, lay):
+    """Per residual launch of the face-flux kernel: FP64 flops of the
+    gradient contraction and the minimum bytes it must move."""
+    d, S, Q = wl.dim, lay.stencil, lay.q_face
+    R = Q * d
+    nfid = lay.n_internal + lay.n_disp
+    flops = 2.0 * nfid * R * S * d + 2.0 * lay.n_disp * R * d
+    bytes_face = 8 * R * S + 4 * S + 8 * Q * 3 + 8 + 8 + 8 * d + 2 * 8 * d
+    bytes_ = nfid * bytes_face + lay.n_disp * (8 * R + 8 * Q * d + 8 * d) + 8 * d * lay.n_cells
+    # the whole residual (u* prepass + fluxes + assembly), for the HBM view
+    nlf = 2 * d
+    res_bytes = bytes_ + lay.n_cells * (8 * nlf * S + 4 * S + 8 * d + 8 * nlf * d * 2
+                                        + 8 * d * 2 + 4 * nlf)
+    return flops, bytes_, res_bytes
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.p = None
+        try:
+            self.p = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except Exception:
+            self.p.kill()
+            out, _ = self.p.communicate()
+        rows = []
+        for line in out.strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[3]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows),
+                "sm_max_mhz": max(r[1] for r in rows),
+                "power_w_max": max(r[2] for r in rows),
+                "samples": len(rows), "reasons": reasons}
+
+
+# ------------------------------------------------------------------ oracle baseline
+def oracle_baseline(wl, mesh, budget_s=12.0, sample_cells=2048, seed=3):
+    """The CPU oracle as it stands, single-threaded, on a bounded sample:
+    the residual of `sample_cells` cells of the same workload."""
+    import oracle
+    from paper_2601_18417_gb300 import inputs as I
+    tags = I.side_tags(wl.problem, wl.dim)
+    o = oracle.OracleMesh(mesh, tags, p=wl.p, n_plus=wl.n_plus, q1=wl.q1,
+                          k_weight=wl.k_weight, alpha=wl.alpha)
+    rng = np.random.default_rng(seed)
+    nc = o.nc
+    start = int(rng.integers(0, max(nc - sample_cells, 1)))
+    cells = np.arange(start, min(start + sample_cells, nc))
+    o.prepare(cells)
+    field = I.field_for(wl.problem, wl.dim)
+    xq, xf = o.xq[o.disp_faces()], o.xf[o.disp_faces()]
+    if field is not None:
+        ubq, ubf = field.value(xq), field.value(xf)
+        u = field.value(o.xc).T.copy()
+    else:
+        top = I.block_top_displacement(1, wl.load_steps, wl.dim)
+        on_top = np.abs(xf[:, wl.dim - 1] - 1.0) < 1e-9
+        ubq = np.where(on_top[:, None, None], top, 0.0) * np.ones_like(xq)
+        ubf = np.where(on_top[:, None], top, 0.0) * np.ones_like(xf)
+        u = top[:, None] * o.xc[:, wl.dim - 1][None, :]
+    u = u + 1e-3 * np.abs(u).max() * rng.standard_normal(u.shape)
+    tbq = np.zeros((max(o.nft, 1), o.Q, wl.dim))
+    body = np.zeros((wl.dim, nc))
+    reps = 0
+    t0 = time.perf_counter()
+    while True:
+        o.residual(wl.law, wl.mu, wl.lam, u, ubq, ubf, tbq, body, cells=cells)
+        reps += 1
+        dt = time.perf_counter() - t0
+        if dt >= budget_s:
+            break
+    return {"value": len(cells) * reps / dt / 1e6, "unit": "Mcell/s", "cores": 1,
+            "kind": "oracle",
+            "sample": f"residual of {len(cells)} contiguous cells of the {wl.name} workload, "
+                      f"{reps} evaluations in {dt:.1f} s, single thread"}
+
+
+# ------------------------------------------------------------------ main arm
+def run_hofv(args):
+    import torch
+
+    from paper_2601_18417_gb300 import build as B
+    from paper_2601_18417_gb300 import hofv
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    if rank == 0:
+        B.build()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    wl, mesh, ctx, lay, setup_s, u_ex, field = build_workload(args.workload, local)
+    d, nc = wl.dim, lay.n_cells
+    n = d * nc
+    dev = torch.device("cuda", local)
+    rng = np.random.default_rng(99)
+    amp = np.abs(u_ex).max()
+    u = torch.as_tensor(u_ex + 1e-3 * amp * rng.standard_normal(u_ex.shape), device=dev)
+    Ru = torch.empty_like(u)
+    ctx.residual(u, Ru)
+    J = KRYLOV_J
+    V = torch.as_tensor(rng.standard_normal((J + 2, n)), device=dev)
+    V /= V.norm(dim=1, keepdim=True)
+    Z = torch.zeros((J + 1, n), dtype=torch.float64, device=dev)
+    v_host = torch.empty(n, dtype=torch.float64).pin_memory()
+    v_host.copy_(V[J].cpu())
+    pc = hofv.PC_AJ32
+
+    def step():
+        ctx.arnoldi_step(u, Ru, pc, INNER_ITERS, V, Z, J)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    clk = ClockSampler(local) if rank == 0 else None
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(s)
+    for _ in range(args.steps):
+        step()
+    e1.record(s)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    # per-kernel residual timing for the roofline (same stream, CUDA events)
+    kt = []
+    for _ in range(max(args.steps, 10)):
+        kt.append(ctx.residual_timed(u, Ru))
+    clocks = clk.stop() if clk else None
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * nc / (ms * 1e-3) / 1e6
+    kt = np.array(kt)
+    flux_ms = float(kt[:, 1].mean())
+    res_ms = float(kt.sum(axis=1).mean())
+    flops, fbytes, rbytes = algorithmic_counts(wl, lay)
+    pk, src = peaks()
+    sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    fp64_peak = 152 * 2 * 2 * sm_max * 1e6 / 1e12     # TFLOP/s: 2 DFMA/clk/SM
+    achieved = flops / (flux_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "kernel": "k_flux (face gradients + law + quadrature)",
+                "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp64_peak,
+                "peak_source": f"FP64 units x SMs x max clock ({sm_max:.0f} MHz), nominal "
+                               "2 DFMA/clk/SM on GB300",
+                "traffic": None,
+                "hbm_achieved_gbs": fbytes / (flux_ms * 1e-3) / 1e9,
+                "hbm_peak_gbs": pk["hbm_gbs"], "hbm_peak_source": src,
+                "hbm_frac": fbytes / (flux_ms * 1e-3) / 1e9 / pk["hbm_gbs"],
+                "flux_ms": flux_ms, "residual_ms": res_ms,
+                "residual_mcells": nc / (res_ms * 1e-3) / 1e6,
+                "residual_hbm_frac": rbytes / (res_ms * 1e-3) / 1e9 / pk["hbm_gbs"],
+                "alg_flops_per_launch": flops, "alg_bytes_per_launch": fbytes}
+    # end to end through the public API with host buffers
+    e2e = None
+    if rank == 0:
+        h2d = n * 8
+        d2h = (J + 2) * 8
+        for _ in range(2):
+            V[J].copy_(v_host, non_blocking=True)
+            step()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        reps = max(args.steps, 5)
+        for _ in range(reps):
+            V[J].copy_(v_host, non_blocking=True)
+            step()          # returns the Hessenberg column on the host
+        torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / reps
+        e2e = {"value": nc / e2e_s / 1e6, "unit": "Mcell/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+    launches = 2 * INNER_ITERS + 2 + 1 + 6 + 4 + 2
+    solve = None
+    if rank == 0 and not args.no_solve:
+        solve = {}
+        for name_, kind in (("plain_fp64_aj", hofv.PC_AJ64), ("fp32_aj", hofv.PC_AJ32)):
+            uu = torch.zeros_like(u)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st = ctx.newton_solve(uu, rtol=1e-8, precond=kind, inner_iters=INNER_ITERS,
+                                  restart=30, max_krylov=3000)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            err = float((uu.cpu().numpy() - u_ex).std() / max(np.abs(u_ex).std(), 1e-300))
+            solve[name_] = {"seconds": dt, "status": st["status"], "newton": st["newton_iters"],
+                            "krylov": st["krylov_iters"], "r_final_over_r0":
+                            st["r_final"] / max(st["r0"], 1e-300),
+                            "rel_error_vs_manufactured": err}
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = oracle_baseline(wl, mesh, budget_s=args.cpu_budget)
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "Mcell/s", "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64", "data": "synthetic",
+                "config": {"workload": wl.name,
+                           "mesh": f"{wl.n}^{wl.dim} {'quads' if wl.dim == 2 else 'hexes'}, "
+                                   f"{int(wl.jitter * 100)}% node jitter",
+                           "cells": nc, "p": wl.p, "stencil": lay.stencil,
+                           "gauss_per_face": lay.q_face,
+                           "law": "linear" if wl.law == 0 else "neo-Hookean",
+                           "step": f"one flexible Arnoldi step: AJ FP32 preconditioner "
+                                   f"({INNER_ITERS} CG its) + forward-difference Jv (1 FP64 "
+                                   f"residual) + 2x classical Gram-Schmidt on {J + 1} vectors",
+                           "l2": "inputs larger than L2 (coefficients "
+                                 f"{rbytes / 1e9:.2f} GB per residual)",
+                           "parallelism": "replicas" if ws > 1 else "single GPU"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches * args.steps, "clocks": clocks,
+                "setup_s": setup_s, "solve": solve, "impl": "hofv"}
+        print(json.dumps(line))
+    ctx.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_2601_18417_gb300 import inputs as I
+    oracle.build()
+    wl = I.WORKLOADS[args.workload]
+    mesh = I.structured_mesh(wl.dim, wl.n, jitter=wl.jitter, seed=wl.mesh_seed)
+    per = max(1.0, args.cpu_budget / max(args.steps + args.warmup, 1))
+    for _ in range(args.warmup):
+        oracle_baseline(wl, mesh, budget_s=per)
+    vals = [oracle_baseline(wl, mesh, budget_s=per) for _ in range(args.steps)]
+    v = statistics.median(x["value"] for x in vals)
+    cpu = dict(vals[-1])
+    cpu["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Mcell/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": per * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name, "cells": wl.n_cells, "p": wl.p,
+                       "note": "CPU oracle as it stands (the paper ships no code)"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": v, "unit": "Mcell/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="hofv", choices=["hofv", "reference"])
+    ap.add_argument("--workload", default="quad512j-p3-mixed")
+    ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_hofv(args)
+
+
+if __name__ == "__main__":
+    main()

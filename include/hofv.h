@@ -210,6 +210,24 @@ int hofv_newton_solve(hofv_ctx* ctx, double* u, const hofv_solve_opts* opts,
 /* Fill `opts` with the defaults listed in hofv_solve_opts. */
 void hofv_default_opts(hofv_solve_opts* opts);
 
+/* One flexible-GMRES Arnoldi step of the JFNK solver (Sec. 4.1, right
+   preconditioning): Z_j = P^{-1} V_j (preconditioner `kind`, `inner_iters`),
+   w = J Z_j by forward differences about u (Ru = R(u)), w orthogonalised
+   against V_0..V_j by classical Gram-Schmidt applied twice, and
+   V_{j+1} = w / ||w||.  This is one pass over every kernel of the hot path.
+     V  DEVICE [(j+2)][ld], columns 0..j given, column j+1 written
+     Z  DEVICE [(j+1)][ld], column j written
+     ld >= dim * n_cells (elements between columns)
+     h  HOST [j+2] receives the Hessenberg column (h[j+1] = ||w||)
+   Synchronises.  j must be in 0..99. */
+int hofv_arnoldi_step(hofv_ctx* ctx, const double* u, const double* Ru, int kind,
+                      int inner_iters, double* V, double* Z, int64_t ld, int j, double* h);
+
+/* hofv_residual with each of its three kernels timed by CUDA events on the
+   context stream: ms[0] stabilisation extrapolation (cell-ordered), ms[1]
+   face fluxes, ms[2] cell assembly (HOST array of 3).  Synchronises. */
+int hofv_residual_timed(hofv_ctx* ctx, const double* u, double* R, float* ms);
+
 /* ---- inspection (tests) -------------------------------------------------- */
 
 /* Face data for faces [first, first + count) to HOST arrays (any may be NULL):

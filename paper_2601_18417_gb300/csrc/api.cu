@@ -686,7 +686,7 @@ static int ensure_krylov(hofv_ctx* c, int m) {
   TRY(dev_alloc(c, &c->d_V, (int64_t)(m + 1) * n));
   TRY(dev_alloc(c, &c->d_Z, (int64_t)m * n));
   TRY(dev_alloc(c, &c->d_kvec, 6 * n));
-  TRY(dev_alloc(c, &c->d_h, 4 * (int64_t)(m + 2)));
+  TRY(dev_alloc(c, &c->d_h, 4 * (int64_t)(std::max(m, 100) + 2)));
   c->kry_m = m;
   return 0;
 }
@@ -986,3 +986,59 @@ int hofv_get_aj(hofv_ctx* c, double* diag, double* off) {
 }
 
 }  // extern "C"
+
+extern "C" int hofv_arnoldi_step(hofv_ctx* c, const double* u, const double* Ru, int kind,
+                                 int inner_iters, double* V, double* Z, int64_t ld, int j,
+                                 double* h) {
+  TRY(check_eval(c));
+  if (!u || !Ru || !V || !Z || !h) return fail(c, HOFV_EINVAL, "null argument");
+  const int64_t n = c->nc * c->dim;
+  if (j < 0 || j > 99 || ld < n) return fail(c, HOFV_EINVAL, "bad Arnoldi index or leading dimension");
+  if (kind != HOFV_PC_NONE && kind != HOFV_PC_AJ64 && kind != HOFV_PC_AJ32 && kind != HOFV_PC_GNN)
+    return fail(c, HOFV_EINVAL, "unknown preconditioner");
+  if (kind == HOFV_PC_GNN && !c->gnn) return fail(c, HOFV_ESTATE, "no learned preconditioner loaded");
+  TRY(ensure_krylov(c, 1));
+  double* Vj = V + (int64_t)j * ld;
+  double* Zj = Z + (int64_t)j * ld;
+  double* w = c->d_kvec;
+  double* dh = c->d_h;
+  hofv_solve_opts o;
+  hofv_default_opts(&o);
+  o.precond = kind;
+  o.inner_iters = inner_iters;
+  hofv_stats st;
+  memset(&st, 0, sizeof(st));
+  TRY(apply_pc(c, o, Vj, Zj, &st));
+  launch_norm2(u, n, c->d_red, c->d_count, c->d_scal + 0, c->red_blocks, c->stream);
+  TRY(jvp_impl(c, u, Ru, Zj, w));
+  const int k = j + 1;
+  launch_dots(V, ld, w, k, n, c->d_red, c->d_count, dh, c->red_blocks, c->stream, 0);
+  launch_multi_axpy(w, V, dh, k, n, ld, c->stream);
+  launch_dots(V, ld, w, k, n, c->d_red, c->d_count, dh + k, c->red_blocks, c->stream, 0);
+  launch_multi_axpy(w, V, dh + k, k, n, ld, c->stream);
+  launch_norm2(w, n, c->d_red, c->d_count, dh + 2 * k, c->red_blocks, c->stream);
+  launch_scale_copy(V + (int64_t)(j + 1) * ld, w, dh + 2 * k, 1, n, c->stream);
+  std::vector<double> hb((size_t)(2 * k + 1));
+  HOFV_CUDA(c, cudaMemcpyAsync(hb.data(), dh, sizeof(double) * hb.size(), cudaMemcpyDeviceToHost,
+                               c->stream));
+  HOFV_CUDA(c, cudaStreamSynchronize(c->stream));
+  for (int i = 0; i < k; ++i) h[i] = hb[i] + hb[k + i];
+  h[k] = hb[2 * k];
+  if (!std::isfinite(h[k])) return fail(c, HOFV_ENAN, "non-finite value in the Arnoldi step");
+  return HOFV_OK;
+}
+
+extern "C" int hofv_residual_timed(hofv_ctx* c, const double* u, double* R, float* ms) {
+  TRY(check_eval(c));
+  if (!u || !R || !ms) return fail(c, HOFV_EINVAL, "null argument");
+  cudaEvent_t ev[4];
+  for (int i = 0; i < 4; ++i) HOFV_CUDA(c, cudaEventCreate(&ev[i]));
+  launch_residual(dev_mesh(c), c->mat, u, nullptr, nullptr, nullptr, R, c->d_ustar, c->d_flux,
+                  c->d_ubq, c->d_ubf, c->d_src, c->stream, ev);
+  cudaError_t e = cudaEventSynchronize(ev[3]);
+  for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaEventElapsedTime(&ms[i], ev[i], ev[i + 1]);
+  for (int i = 0; i < 4; ++i) cudaEventDestroy(ev[i]);
+  HOFV_CUDA(c, e);
+  HOFV_CUDA(c, cudaGetLastError());
+  return HOFV_OK;
+}

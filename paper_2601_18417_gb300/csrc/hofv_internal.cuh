@@ -171,7 +171,7 @@ int run_face_aux(hofv_ctx* c);
 void launch_residual(const DevMesh& m, const Material& mat, const double* u, const double* v,
                      const double* d_eps, const double* R0, double* out, double* ustar,
                      double* flux, const double* ubq, const double* ubf, const double* src,
-                     cudaStream_t st);
+                     cudaStream_t st, cudaEvent_t* ev = nullptr);
 void launch_source(const hofv_ctx* c, cudaStream_t st);
 
 // ---- vector kernels (krylov.cu) ----

@@ -38,6 +38,15 @@ __device__ __forceinline__ bool last_block(unsigned int* count, unsigned int nbl
   return is_last;
 }
 
+// Sum of partials red[0..nb) by the whole (last) block: thread t adds
+// partials t, t + blockDim, ... in order, then a fixed-shape tree.  The
+// result (valid in thread 0) does not depend on which block finished last.
+__device__ __forceinline__ double final_sum(const double* red, unsigned int nb, double* sh) {
+  double s = 0.0;
+  for (unsigned int b = threadIdx.x; b < nb; b += blockDim.x) s += __ldcg(red + b);
+  return block_sum(s, sh);
+}
+
 // out[k] = x_k . y for k = blockIdx.y; x_k = X + k * ldx
 __global__ void k_mdot(const double* __restrict__ X, int64_t ldx, const double* __restrict__ y,
                        int64_t n, double* red, unsigned int* count, double* out, int mode) {
@@ -50,12 +59,13 @@ __global__ void k_mdot(const double* __restrict__ X, int64_t ldx, const double* 
     s = fma(x[i], y[i], s);
   s = block_sum(s, sh);
   if (threadIdx.x == 0) red[k * gridDim.x + blockIdx.x] = s;
-  if (last_block(count + k, gridDim.x) && threadIdx.x == 0) {
+  if (last_block(count + k, gridDim.x)) {
     __threadfence();
-    double t = 0.0;
-    for (unsigned int b = 0; b < gridDim.x; ++b) t += ((volatile double*)red)[k * gridDim.x + b];
-    out[k] = mode == 1 ? sqrt(t) : t;
-    count[k] = 0;
+    const double t = final_sum(red + k * gridDim.x, gridDim.x, sh);
+    if (threadIdx.x == 0) {
+      out[k] = mode == 1 ? sqrt(t) : t;
+      count[k] = 0;
+    }
   }
 }
 
@@ -186,15 +196,16 @@ __global__ void k_cg_init(int64_t nc, const double* __restrict__ v, double inv_k
     const double s = block_sum(part[j], sh);
     if (threadIdx.x == 0) red[j * gridDim.x + blockIdx.x] = s;
   }
-  if (last_block(count, gridDim.x) && threadIdx.x == 0) {
+  if (last_block(count, gridDim.x)) {
     __threadfence();
     for (int j = 0; j < DIM; ++j) {
-      double t = 0.0;
-      for (unsigned int b = 0; b < gridDim.x; ++b) t += ((volatile double*)red)[j * gridDim.x + b];
-      sc[j] = t;
-      sc[2 * DIM + j] = 0.0;
+      const double t = final_sum(red + j * gridDim.x, gridDim.x, sh);
+      if (threadIdx.x == 0) {
+        sc[j] = t;
+        sc[2 * DIM + j] = 0.0;
+      }
     }
-    count[0] = 0;
+    if (threadIdx.x == 0) count[0] = 0;
   }
 }
 
@@ -243,14 +254,13 @@ __global__ void k_cg_spmv(int64_t nc, const T* __restrict__ diag, const int32_t*
     const double s = block_sum(part[j], sh);
     if (threadIdx.x == 0) red[j * gridDim.x + blockIdx.x] = s;
   }
-  if (last_block(count, gridDim.x) && threadIdx.x == 0) {
+  if (last_block(count, gridDim.x)) {
     __threadfence();
     for (int j = 0; j < DIM; ++j) {
-      double t = 0.0;
-      for (unsigned int b = 0; b < gridDim.x; ++b) t += ((volatile double*)red)[j * gridDim.x + b];
-      sc[DIM + j] = t != 0.0 ? sc[j] / t : 0.0;
+      const double t = final_sum(red + j * gridDim.x, gridDim.x, sh);
+      if (threadIdx.x == 0) sc[DIM + j] = t != 0.0 ? sc[j] / t : 0.0;
     }
-    count[0] = 0;
+    if (threadIdx.x == 0) count[0] = 0;
   }
 }
 
@@ -286,15 +296,16 @@ __global__ void k_cg_update(int64_t nc, const T* __restrict__ diag, const T* __r
     const double s = block_sum(part[j], sh);
     if (threadIdx.x == 0) red[j * gridDim.x + blockIdx.x] = s;
   }
-  if (last_block(count, gridDim.x) && threadIdx.x == 0) {
+  if (last_block(count, gridDim.x)) {
     __threadfence();
     for (int j = 0; j < DIM; ++j) {
-      double t = 0.0;
-      for (unsigned int b = 0; b < gridDim.x; ++b) t += ((volatile double*)red)[j * gridDim.x + b];
-      sc[2 * DIM + j] = sc[j] != 0.0 ? t / sc[j] : 0.0;
-      sc[j] = t;
+      const double t = final_sum(red + j * gridDim.x, gridDim.x, sh);
+      if (threadIdx.x == 0) {
+        sc[2 * DIM + j] = sc[j] != 0.0 ? t / sc[j] : 0.0;
+        sc[j] = t;
+      }
     }
-    count[0] = 0;
+    if (threadIdx.x == 0) count[0] = 0;
   }
 }
 

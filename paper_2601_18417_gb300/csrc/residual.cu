@@ -244,29 +244,33 @@ template <int DIM, int LAW>
 static void residual_impl(const DevMesh& m, const Material& mat, const double* w,
                           const double* d_eps, const double* R0, double* out, double* ustar,
                           double* flux, const double* ubq, const double* ubf, const double* src,
-                          cudaStream_t st) {
+                          cudaStream_t st, cudaEvent_t* ev) {
+  if (ev) cudaEventRecord(ev[0], st);
   k_ustar<DIM><<<(unsigned)m.nctile, 32 * 2 * DIM, 0, st>>>(m, w, ustar);
+  if (ev) cudaEventRecord(ev[1], st);
   if (m.nftile > 0) {
     const size_t smem = sizeof(double) * kTile * (m.R * DIM + m.Q * DIM);
     k_flux<DIM, LAW><<<(unsigned)m.nftile, kTile * m.R, smem, st>>>(m, mat, w, ustar, ubq, ubf, flux);
   }
+  if (ev) cudaEventRecord(ev[2], st);
   k_cell<DIM><<<(unsigned)((m.nc + 255) / 256), 256, 0, st>>>(m, flux, src, R0, d_eps, out);
+  if (ev) cudaEventRecord(ev[3], st);
 }
 
 void launch_residual(const DevMesh& m, const Material& mat, const double* w, const double* /*v*/,
                      const double* d_eps, const double* R0, double* out, double* ustar,
                      double* flux, const double* ubq, const double* ubf, const double* src,
-                     cudaStream_t st) {
+                     cudaStream_t st, cudaEvent_t* ev) {
   if (m.dim == 2) {
     if (mat.law == HOFV_LAW_LINEAR)
-      residual_impl<2, 0>(m, mat, w, d_eps, R0, out, ustar, flux, ubq, ubf, src, st);
+      residual_impl<2, 0>(m, mat, w, d_eps, R0, out, ustar, flux, ubq, ubf, src, st, ev);
     else
-      residual_impl<2, 1>(m, mat, w, d_eps, R0, out, ustar, flux, ubq, ubf, src, st);
+      residual_impl<2, 1>(m, mat, w, d_eps, R0, out, ustar, flux, ubq, ubf, src, st, ev);
   } else {
     if (mat.law == HOFV_LAW_LINEAR)
-      residual_impl<3, 0>(m, mat, w, d_eps, R0, out, ustar, flux, ubq, ubf, src, st);
+      residual_impl<3, 0>(m, mat, w, d_eps, R0, out, ustar, flux, ubq, ubf, src, st, ev);
     else
-      residual_impl<3, 1>(m, mat, w, d_eps, R0, out, ustar, flux, ubq, ubf, src, st);
+      residual_impl<3, 1>(m, mat, w, d_eps, R0, out, ustar, flux, ubq, ubf, src, st, ev);
   }
 }
 

@@ -81,6 +81,8 @@ SIGNATURES = {
     "hofv_get_cell_data": (_I, [_P, _I64, _I64, _P, _P]),
     "hofv_get_faces": (_I, [_P, _P, _P, _P, _P]),
     "hofv_get_aj": (_I, [_P, _P, _P]),
+    "hofv_arnoldi_step": (_I, [_P, _P, _P, _I, _I, _P, _P, _I64, _I, _P]),
+    "hofv_residual_timed": (_I, [_P, _P, _P, _P]),
 }
 
 
@@ -220,6 +222,21 @@ class Context:
         rc = self._L.hofv_newton_solve(self.h, _ptr(_dev(u)), C.byref(o), C.byref(st))
         self._check(rc, allow_warn=True)
         return st.as_dict()
+
+    def arnoldi_step(self, u, Ru, kind, inner_iters, V, Z, j):
+        """One flexible Arnoldi step; V [(j+2), n], Z [(j+1), n] CUDA FP64.
+        Returns the Hessenberg column (numpy, length j+2)."""
+        h = np.zeros(j + 2)
+        ld = V.stride(0)
+        self._check(self._L.hofv_arnoldi_step(self.h, _ptr(_dev(u)), _ptr(_dev(Ru)), kind,
+                                              inner_iters, _ptr(V), _ptr(Z), ld, j, _ptr(h)))
+        return h
+
+    def residual_timed(self, u, R):
+        """Residual with per-kernel CUDA-event times (ms): u*, flux, cell."""
+        ms = (C.c_float * 3)()
+        self._check(self._L.hofv_residual_timed(self.h, _ptr(_dev(u)), _ptr(_dev(R)), ms))
+        return [float(x) for x in ms]
 
     # ---- inspection --------------------------------------------------------
     def get_face_data(self, first, count, coef=True):
