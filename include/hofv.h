@@ -223,6 +223,21 @@ void hofv_default_opts(hofv_solve_opts* opts);
 int hofv_arnoldi_step(hofv_ctx* ctx, const double* u, const double* Ru, int kind,
                       int inner_iters, double* V, double* Z, int64_t ld, int j, double* h);
 
+/* Same result as hofv_residual, for callers that must not have device memory
+   allocated on their behalf (for example code running while a stream is
+   captured into a CUDA graph, real-time loops that forbid allocation after
+   start-up, or frameworks that own every device allocation).  The paper has
+   no counterpart: this is a property of the library, not of the method.
+   The call allocates nothing: its scratch is one fixed device array of
+   32 MiB (4 Mi doubles) compiled into the library and held on every GPU
+   that loads it until exit.  Meshes needing more scratch than that
+   (n_cells * 2 dim * dim + (n_internal + n_disp) * dim doubles) get
+   HOFV_EINVAL.  All calls share the array: calls that overlap on the GPU
+   race and must be serialised by the caller.  The first call on a device
+   resolves the array's address (cudaGetSymbolAddress) and should come
+   before any stream capture.  u, R: DEVICE [dim][n_cells]. */
+int hofv_residual_noalloc(hofv_ctx* ctx, const double* u, double* R);
+
 /* hofv_residual with each of its three kernels timed by CUDA events on the
    context stream: ms[0] stabilisation extrapolation (cell-ordered), ms[1]
    face fluxes, ms[2] cell assembly (HOST array of 3).  Synchronises. */

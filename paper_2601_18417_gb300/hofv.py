@@ -83,6 +83,7 @@ SIGNATURES = {
     "hofv_get_aj": (_I, [_P, _P, _P]),
     "hofv_arnoldi_step": (_I, [_P, _P, _P, _I, _I, _P, _P, _I64, _I, _P]),
     "hofv_residual_timed": (_I, [_P, _P, _P, _P]),
+    "hofv_residual_noalloc": (_I, [_P, _P, _P]),
 }
 
 
@@ -231,6 +232,10 @@ class Context:
         self._check(self._L.hofv_arnoldi_step(self.h, _ptr(_dev(u)), _ptr(_dev(Ru)), kind,
                                               inner_iters, _ptr(V), _ptr(Z), ld, j, _ptr(h)))
         return h
+
+    def residual_noalloc(self, u, R):
+        """hofv_residual through the variant that allocates nothing."""
+        return self._check(self._L.hofv_residual_noalloc(self.h, _ptr(_dev(u)), _ptr(_dev(R))))
 
     def residual_timed(self, u, R):
         """Residual with per-kernel CUDA-event times (ms): u*, flux, cell."""
