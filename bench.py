@@ -49,6 +49,22 @@ def dist_env():
     return ws, rank, local
 
 
+def measured_traffic(workload):
+    """DRAM bytes per k_flux launch from the committed ncu capture, or None
+    when the face-flux source changed since the capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "ncu_k_flux_traffic.txt")
+    src = os.path.join(ROOT, "paper_2601_18417_gb300", "csrc", "residual.cu")
+    if not os.path.exists(path):
+        return None
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    for line in open(path):
+        parts = line.split()
+        if len(parts) == 3 and not line.startswith("#") and parts[0] == workload:
+            return float(parts[1]) if parts[2] == h else None
+    return None
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -127,7 +143,7 @@ class ClockSampler:
         try:
             self.p = subprocess.Popen(
                 ["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.p = None
@@ -278,7 +294,7 @@ def run_hofv(args):
                 "frac": achieved / fp64_peak,
                 "peak_source": f"FP64 units x SMs x max clock ({sm_max:.0f} MHz), nominal "
                                "2 DFMA/clk/SM on GB300",
-                "traffic": None,
+                "traffic": measured_traffic(wl.name),
                 "hbm_achieved_gbs": fbytes / (flux_ms * 1e-3) / 1e9,
                 "hbm_peak_gbs": pk["hbm_gbs"], "hbm_peak_source": src,
                 "hbm_frac": fbytes / (flux_ms * 1e-3) / 1e9 / pk["hbm_gbs"],
@@ -382,7 +398,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="hofv", choices=["hofv", "reference"])
     ap.add_argument("--workload", default="quad512j-p3-mixed")

@@ -449,6 +449,11 @@ WORKLOADS = {
     # 3-D linear elastic cube, 96^3 hexes, cubic LSQ, 3x3 Gauss pts/face, E=1 GPa
     "hex96-p3-trig": Workload("hex96-p3-trig", 3, 96, 3, 65, 3, 0.0, 0, _MU_1G, _LAM_1G,
                               "mms-trig3d", 1236),
+    # small 3-D cube of the same scheme (profiling-sized: ~2 GB of coefficients)
+    "hex32-p3-trig": Workload("hex32-p3-trig", 3, 32, 3, 65, 3, 0.0, 0, _MU_1G, _LAM_1G,
+                              "mms-trig3d", 1239),
+    "hex32j-p3-nh": Workload("hex32j-p3-nh", 3, 32, 3, 65, 3, 0.20, 1, 1e6, 4e6, "block",
+                             1240, load_steps=10),
     # 3-D neo-Hookean block mu=1 MPa lambda=4 MPa, 64^3 hexes jittered 20 %, quadratic LSQ
     "hex64j-p2-nh": Workload("hex64j-p2-nh", 3, 64, 2, 55, 2, 0.20, 1, 1e6, 4e6, "block",
                              1237, load_steps=10),
