@@ -89,6 +89,9 @@ typedef struct {
   int32_t max_newton;      /* Newton iterations per call (default 30) */
   double rtol;             /* stop when ||R|| <= rtol * ||R(u_in)|| (default 1e-8) */
   double atol;             /* ... or ||R|| <= atol (default 0) */
+  double ftol;             /* ... or ||R|| <= ftol * F_s * sqrt(dim * n_cells), F_s the force
+                              scale of the entry state (hofv_force_scale): a floor for the
+                              rounding noise of the FP64 residual (default 0 = off) */
   int32_t restart;         /* FGMRES restart length m (default 30, max 100) */
   int32_t max_krylov;      /* Krylov iterations per Newton step (default 300) */
   double eta_max;          /* forcing term cap (default 1e-2) */
@@ -96,6 +99,8 @@ typedef struct {
   int32_t inner_iters;     /* AJ inner CG iterations per apply (default 30) */
   int32_t line_search_max; /* backtracking halvings (default 10) */
   int32_t verbose;         /* 1: one line per Newton step on stderr */
+  int32_t record_pairs;    /* 1: keep (-R(u_k), du_k) of every Newton step as a training
+                              pair of the learned preconditioner (hofv_gnn_train) */
 } hofv_solve_opts;
 
 typedef struct {
@@ -207,8 +212,68 @@ int hofv_precondition(hofv_ctx* ctx, int kind, int inner_iters, const double* v,
 int hofv_newton_solve(hofv_ctx* ctx, double* u, const hofv_solve_opts* opts,
                       hofv_stats* stats);
 
+/* ---- learned preconditioner ---------------------------------------------
+   A graph network over the cell adjacency (no counterpart in the paper):
+   nodes are cells, neighbours are face neighbours weighted by the
+   normalised compact approximate Jacobian, w_ij = a_ij / sqrt(D_i D_j).
+   Inputs per cell: v / rms(v), z / rms(z) with z = P_AJ^{-1} v, and the
+   fractions of displacement and traction faces (16 features, zero-padded);
+   encoder 16 -> 64 (ReLU), four message-passing layers
+   h += ReLU(W [h ; sum_j w_ij h_j] + b) with W 64 x 128, decoder 64 -> dim.
+   The preconditioned vector is z + rms(z) * y.  Node-wise products run on
+   the tensor cores in BF16 with FP32 accumulation; parameters are FP32.
+   Parameter order (flat): W0 [64][16], b0 [64], then per layer W [64][128],
+   b [64], then Wd [dim][64], bd [dim].  Training minimises
+   |z + rms(z) y - delta|^2 / |delta|^2 over recorded (residual, Newton
+   correction) pairs with Adam.  All entry points need hofv_build_stencils;
+   changing the mesh or scheme discards the network. */
+
+typedef struct {
+  int32_t epochs;       /* passes over the recorded pairs */
+  int32_t batch;        /* pairs per Adam step */
+  double lr;            /* Adam learning rate */
+  int32_t inner_iters;  /* CG iterations of the AJ preconditioner feeding the network */
+  uint64_t seed;        /* shuffling seed */
+  int32_t verbose;
+} hofv_train_opts;
+
+typedef struct {
+  int32_t pairs, epochs;
+  double loss_first, loss_last;  /* mean loss of the first and last epoch */
+  double seconds;
+} hofv_train_stats;
+
+/* Random initialisation (seeded); the output layer is scaled by out_scale
+   (0 gives the identity correction z_out = z). */
+int hofv_gnn_init(hofv_ctx* ctx, uint64_t seed, double out_scale);
+int hofv_gnn_num_params(hofv_ctx* ctx, int64_t* n);
+/* Copy the FP32 parameters to / from a HOST array of hofv_gnn_num_params. */
+int hofv_gnn_get_params(hofv_ctx* ctx, float* host, int64_t n);
+int hofv_gnn_set_params(hofv_ctx* ctx, const float* host, int64_t n);
+/* Save / load the parameters (binary file with a dimension check). */
+int hofv_gnn_save(hofv_ctx* ctx, const char* path);
+int hofv_gnn_load(hofv_ctx* ctx, const char* path);
+/* zout = z + rms(z) G(v, z): DEVICE [dim][n_cells]; zout may alias z. */
+int hofv_gnn_forward(hofv_ctx* ctx, const double* v, const double* z, double* zout);
+/* Loss of one sample (v, z, delta DEVICE) and its gradient (HOST float
+   array of hofv_gnn_num_params, may be NULL); *loss HOST.  Synchronises. */
+int hofv_gnn_loss_grad(hofv_ctx* ctx, const double* v, const double* z, const double* delta,
+                       double* loss, float* grad);
+/* Record one training pair (r, delta), DEVICE vectors copied in. */
+int hofv_gnn_record(hofv_ctx* ctx, const double* r, const double* delta);
+int hofv_gnn_pairs(hofv_ctx* ctx, int32_t* count);
+int hofv_gnn_clear_pairs(hofv_ctx* ctx);
+/* Train on the recorded pairs (Adam, FP32 master weights).  Synchronises. */
+int hofv_gnn_train(hofv_ctx* ctx, const hofv_train_opts* opts, hofv_train_stats* stats);
+
 /* Fill `opts` with the defaults listed in hofv_solve_opts. */
 void hofv_default_opts(hofv_solve_opts* opts);
+
+/* Force scale F_s = max over cells of the sum over the cell's internal and
+   displacement faces of |flux_f| at the state u (DEVICE [dim][n_cells]); the
+   magnitude against which the rounding error of R(u) is measured.  *fs is
+   a HOST pointer.  Synchronises. */
+int hofv_force_scale(hofv_ctx* ctx, const double* u, double* fs);
 
 /* One flexible-GMRES Arnoldi step of the JFNK solver (Sec. 4.1, right
    preconditioning): Z_j = P^{-1} V_j (preconditioner `kind`, `inner_iters`),

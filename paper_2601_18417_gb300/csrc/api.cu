@@ -88,6 +88,7 @@ static void gauss_rule(int n, double* x, double* w) {
 }
 
 static void free_built(hofv_ctx* c) {
+  gnn_release(c);
   for (void* p : c->allocs) cudaFree(p);
   c->allocs.clear();
   c->device_bytes = 0;
@@ -656,6 +657,7 @@ void hofv_default_opts(hofv_solve_opts* o) {
   o->max_newton = 30;
   o->rtol = 1e-8;
   o->atol = 0.0;
+  o->ftol = 0.0;
   o->restart = 30;
   o->max_krylov = 300;
   o->eta_max = 1e-2;
@@ -663,6 +665,7 @@ void hofv_default_opts(hofv_solve_opts* o) {
   o->inner_iters = 30;
   o->line_search_max = 10;
   o->verbose = 0;
+  o->record_pairs = 0;
 }
 
 }  // extern "C"
@@ -739,9 +742,15 @@ static int fgmres(hofv_ctx* c, const hofv_solve_opts& o, const double* u, const 
   HOFV_CUDA(c, cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
   int total = 0;
   double res = dev_norm(c, r, n);
+  // the learned preconditioner stays on only while its restart cycles reduce
+  // the residual at least as fast per iteration as the last AJ cycle did
+  hofv_solve_opts oc = o;
+  if (oc.precond == HOFV_PC_GNN && !c->gnn) oc.precond = HOFV_PC_AJ32;
   while (total < max_it) {
     if (res <= tol || res == 0.0) break;
     const double beta = res;
+    const bool cycle_gnn = oc.precond == HOFV_PC_GNN;
+    bool broken = false;
     HOFV_CUDA(c, cudaMemcpyAsync(c->d_scal + 20, &beta, sizeof(double), cudaMemcpyHostToDevice, c->stream));
     launch_scale_copy(V, r, c->d_scal + 20, 1, n, c->stream);
     std::fill(F.g.begin(), F.g.end(), 0.0);
@@ -750,7 +759,7 @@ static int fgmres(hofv_ctx* c, const hofv_solve_opts& o, const double* u, const 
     for (; j < m && total < max_it; ++j) {
       double* Vj = V + (int64_t)j * n;
       double* Zj = Z + (int64_t)j * n;
-      TRY(apply_pc(c, o, Vj, Zj, st));
+      TRY(apply_pc(c, oc, Vj, Zj, st));
       TRY(jvp_impl(c, u, Ru, Zj, w));
       st->residual_evals++;
       // classical Gram-Schmidt, twice
@@ -764,6 +773,13 @@ static int fgmres(hofv_ctx* c, const hofv_solve_opts& o, const double* u, const 
       double hn = 0.0;
       HOFV_CUDA(c, cudaMemcpyAsync(&hn, dh + 2 * (m + 2), sizeof(double), cudaMemcpyDeviceToHost, c->stream));
       HOFV_CUDA(c, cudaStreamSynchronize(c->stream));
+      if (!std::isfinite(hn) && cycle_gnn) {
+        // learned preconditioner failed: drop this cycle, continue with AJ
+        oc.precond = HOFV_PC_AJ32;
+        st->gnn_fallbacks++;
+        broken = true;
+        break;
+      }
       if (!std::isfinite(hn)) return fail(c, HOFV_ENAN, "non-finite value in the Krylov basis");
       double* Hc = F.H.data() + (size_t)j * (m + 1);
       for (int i = 0; i <= j; ++i) Hc[i] = F.hbuf[i] + F.hbuf[(m + 2) + i];
@@ -787,6 +803,27 @@ static int fgmres(hofv_ctx* c, const hofv_solve_opts& o, const double* u, const 
       if (res <= tol || hn == 0.0) {
         ++j;
         break;
+      }
+    }
+    if (broken) {
+      // restart from the current x without the failed cycle
+      TRY(jvp_impl(c, u, Ru, x, w));
+      st->residual_evals++;
+      HOFV_CUDA(c, cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
+      launch_axpby(r, -1.0, w, 1.0, n, c->stream);
+      res = dev_norm(c, r, n);
+      continue;
+    }
+    if (j > 0 && beta > 0.0) {
+      const double rate = pow(std::max(res, 1e-300) / beta, 1.0 / j);
+      if (!cycle_gnn && oc.precond != HOFV_PC_NONE) {
+        c->aj_rate = rate;
+      } else if (cycle_gnn) {
+        const double judge = c->aj_rate > 0.0 ? c->aj_rate : 0.98;
+        if (!(rate <= judge)) {
+          oc.precond = HOFV_PC_AJ32;
+          st->gnn_fallbacks++;
+        }
       }
     }
     // y = H^{-1} g (upper triangular j x j)
@@ -832,17 +869,25 @@ extern "C" int hofv_newton_solve(hofv_ctx* c, double* u, const hofv_solve_opts* 
   double* du = c->d_kvec + 3 * n;
   double* ut = c->d_kvec + 4 * n;
   double* Rt = c->d_kvec + 5 * n;
+  double atol = o.atol;
+  if (o.ftol > 0.0) {
+    double fs = 0.0;
+    TRY(hofv_force_scale(c, u, &fs));
+    st.residual_evals++;
+    atol = std::max(atol, o.ftol * fs * sqrt((double)n));
+  }
   TRY(hofv_residual(c, u, R));
   st.residual_evals++;
   double rn = dev_norm(c, R, n);
   const double r0 = rn;
   st.r0 = r0;
+  if (o.verbose) fprintf(stderr, "[hofv] |R0| %.6e  absolute floor %.3e\n", r0, atol);
   int status = HOFV_WNOTCONV;
   if (!std::isfinite(rn)) {
     status = fail(c, HOFV_ENAN, "non-finite initial residual");
   } else {
     for (int it = 0; it <= o.max_newton; ++it) {
-      if (rn <= o.rtol * r0 || rn <= o.atol || rn == 0.0) {
+      if (rn <= o.rtol * r0 || rn <= atol || rn == 0.0) {
         status = HOFV_OK;
         break;
       }
@@ -857,6 +902,20 @@ extern "C" int hofv_newton_solve(hofv_ctx* c, double* u, const hofv_solve_opts* 
       double lres = 0.0;
       int rc = fgmres(c, o, u, R, Rt, du, tol, o.max_krylov, &st, &its, &lres);
       if (rc < 0) { status = rc; break; }
+      if (o.record_pairs) {
+        rc = hofv_gnn_record(c, Rt, du);  // (-R(u_k), du_k)
+        if (rc < 0) { status = rc; break; }
+      }
+      if (o.verbose >= 2) {
+        // true linear residual ||R + J du|| and its FD estimate with a 100x larger step
+        double* w = c->d_kvec;
+        TRY(jvp_impl(c, u, R, du, w));
+        launch_axpby(w, 1.0, R, 1.0, n, c->stream);
+        const double tr = dev_norm(c, w, n);
+        const double dn = dev_norm(c, du, n);
+        fprintf(stderr, "[hofv]   true linear residual %.3e (estimate %.3e, tol %.3e)  |du| %.3e\n", tr,
+                lres, tol, dn);
+      }
       // backtracking line search on ||R||
       double lam = 1.0, rt = 0.0;
       bool ok = false;
@@ -1040,5 +1099,22 @@ extern "C" int hofv_residual_timed(hofv_ctx* c, const double* u, double* R, floa
   for (int i = 0; i < 4; ++i) cudaEventDestroy(ev[i]);
   HOFV_CUDA(c, e);
   HOFV_CUDA(c, cudaGetLastError());
+  return HOFV_OK;
+}
+
+extern "C" int hofv_force_scale(hofv_ctx* c, const double* u, double* fs) {
+  TRY(check_eval(c));
+  if (!u || !fs) return fail(c, HOFV_EINVAL, "null argument");
+  launch_residual(dev_mesh(c), c->mat, u, nullptr, nullptr, nullptr, c->d_w, c->d_ustar, c->d_flux,
+                  c->d_ubq, c->d_ubf, c->d_src, c->stream);
+  launch_flux_scale(dev_mesh(c), c->d_flux, c->d_w, c->stream);
+  std::vector<double> per((size_t)c->nc);
+  HOFV_CUDA(c, cudaMemcpyAsync(per.data(), c->d_w, sizeof(double) * c->nc, cudaMemcpyDeviceToHost,
+                               c->stream));
+  HOFV_CUDA(c, cudaStreamSynchronize(c->stream));
+  double m = 0.0;
+  for (double v : per) m = std::isnan(v) ? v : std::max(m, v);
+  *fs = m;
+  if (!std::isfinite(m)) return fail(c, HOFV_ENAN, "non-finite face flux");
   return HOFV_OK;
 }

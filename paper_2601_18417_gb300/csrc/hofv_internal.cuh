@@ -124,6 +124,7 @@ struct hofv_ctx {
   double* d_h = nullptr;            // [m+2] projections
   // ---- learned preconditioner ----
   void* gnn = nullptr;
+  double aj_rate = -1.0;            // mean per-iteration residual reduction of the last AJ cycle
   int64_t device_bytes = 0;
   std::vector<void*> allocs;
 };
@@ -173,6 +174,8 @@ void launch_residual(const DevMesh& m, const Material& mat, const double* u, con
                      double* flux, const double* ubq, const double* ubf, const double* src,
                      cudaStream_t st, cudaEvent_t* ev = nullptr);
 void launch_source(const hofv_ctx* c, cudaStream_t st);
+// out[cell] = sum over the cell's internal/displacement faces of |flux_f|
+void launch_flux_scale(const DevMesh& m, const double* flux, double* out, cudaStream_t st);
 
 // ---- vector kernels (krylov.cu) ----
 // out[i] = sum over blocks of partial dot products, deterministic order
@@ -196,5 +199,6 @@ int aj_precondition(hofv_ctx* c, int kind, int iters, const double* v, double* z
 
 // ---- learned preconditioner (gnn.cu) ----
 int gnn_apply(hofv_ctx* c, const double* v, const double* z_aj, double* z);
+void gnn_release(hofv_ctx* c);
 
 }  // namespace hofv

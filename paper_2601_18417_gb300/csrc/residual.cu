@@ -309,3 +309,33 @@ void launch_source(const hofv_ctx* c, cudaStream_t st) {
 }
 
 }  // namespace hofv
+
+namespace hofv {
+// per-cell sum of |flux_f| over the cell's internal and displacement faces
+// (the force scale F_s = max over cells), from the last residual's fluxes
+template <int DIM>
+__global__ void k_flux_scale(DevMesh m, const double* __restrict__ flux, double* __restrict__ out) {
+  constexpr int NLF = 2 * DIM;
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= m.nc) return;
+  double s = 0.0;
+#pragma unroll
+  for (int lf = 0; lf < NLF; ++lf) {
+    const int32_t code = m.cface[c * NLF + lf];
+    if (code == 0) continue;
+    const int64_t f = (code > 0 ? code : -code) - 1;
+    double q = 0.0;
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) q += flux[f * DIM + j] * flux[f * DIM + j];
+    s += sqrt(q);
+  }
+  out[c] = s;
+}
+
+void launch_flux_scale(const DevMesh& m, const double* flux, double* out, cudaStream_t st) {
+  if (m.dim == 2)
+    k_flux_scale<2><<<(unsigned)((m.nc + 255) / 256), 256, 0, st>>>(m, flux, out);
+  else
+    k_flux_scale<3><<<(unsigned)((m.nc + 255) / 256), 256, 0, st>>>(m, flux, out);
+}
+}  // namespace hofv

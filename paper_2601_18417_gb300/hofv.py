@@ -40,9 +40,24 @@ class Layout(C.Structure):
 
 class SolveOpts(C.Structure):
     _fields_ = [("max_newton", C.c_int32), ("rtol", C.c_double), ("atol", C.c_double),
+                ("ftol", C.c_double),
                 ("restart", C.c_int32), ("max_krylov", C.c_int32), ("eta_max", C.c_double),
                 ("precond", C.c_int32), ("inner_iters", C.c_int32),
-                ("line_search_max", C.c_int32), ("verbose", C.c_int32)]
+                ("line_search_max", C.c_int32), ("verbose", C.c_int32),
+                ("record_pairs", C.c_int32)]
+
+
+class TrainOpts(C.Structure):
+    _fields_ = [("epochs", C.c_int32), ("batch", C.c_int32), ("lr", C.c_double),
+                ("inner_iters", C.c_int32), ("seed", C.c_uint64), ("verbose", C.c_int32)]
+
+
+class TrainStats(C.Structure):
+    _fields_ = [("pairs", C.c_int32), ("epochs", C.c_int32), ("loss_first", C.c_double),
+                ("loss_last", C.c_double), ("seconds", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class Stats(C.Structure):
@@ -84,6 +99,19 @@ SIGNATURES = {
     "hofv_arnoldi_step": (_I, [_P, _P, _P, _I, _I, _P, _P, _I64, _I, _P]),
     "hofv_residual_timed": (_I, [_P, _P, _P, _P]),
     "hofv_residual_noalloc": (_I, [_P, _P, _P]),
+    "hofv_force_scale": (_I, [_P, _P, C.POINTER(_D)]),
+    "hofv_gnn_init": (_I, [_P, C.c_uint64, _D]),
+    "hofv_gnn_num_params": (_I, [_P, C.POINTER(_I64)]),
+    "hofv_gnn_get_params": (_I, [_P, _P, _I64]),
+    "hofv_gnn_set_params": (_I, [_P, _P, _I64]),
+    "hofv_gnn_save": (_I, [_P, C.c_char_p]),
+    "hofv_gnn_load": (_I, [_P, C.c_char_p]),
+    "hofv_gnn_forward": (_I, [_P, _P, _P, _P]),
+    "hofv_gnn_loss_grad": (_I, [_P, _P, _P, _P, C.POINTER(_D), _P]),
+    "hofv_gnn_record": (_I, [_P, _P, _P]),
+    "hofv_gnn_pairs": (_I, [_P, C.POINTER(C.c_int32)]),
+    "hofv_gnn_clear_pairs": (_I, [_P]),
+    "hofv_gnn_train": (_I, [_P, C.POINTER(TrainOpts), C.POINTER(TrainStats)]),
 }
 
 
@@ -233,6 +261,12 @@ class Context:
                                               inner_iters, _ptr(V), _ptr(Z), ld, j, _ptr(h)))
         return h
 
+    def force_scale(self, u):
+        """F_s = max over cells of the sum of |face flux| at state u."""
+        fs = C.c_double(0.0)
+        self._check(self._L.hofv_force_scale(self.h, _ptr(_dev(u)), C.byref(fs)))
+        return fs.value
+
     def residual_noalloc(self, u, R):
         """hofv_residual through the variant that allocates nothing."""
         return self._check(self._L.hofv_residual_noalloc(self.h, _ptr(_dev(u)), _ptr(_dev(R))))
@@ -242,6 +276,58 @@ class Context:
         ms = (C.c_float * 3)()
         self._check(self._L.hofv_residual_timed(self.h, _ptr(_dev(u)), _ptr(_dev(R)), ms))
         return [float(x) for x in ms]
+
+    # ---- learned preconditioner -------------------------------------------
+    def gnn_init(self, seed=0, out_scale=0.0):
+        return self._check(self._L.hofv_gnn_init(self.h, seed, out_scale))
+
+    def gnn_num_params(self):
+        n = C.c_int64(0)
+        self._check(self._L.hofv_gnn_num_params(self.h, C.byref(n)))
+        return n.value
+
+    def gnn_get_params(self):
+        out = np.zeros(self.gnn_num_params(), np.float32)
+        self._check(self._L.hofv_gnn_get_params(self.h, _ptr(out), out.size))
+        return out
+
+    def gnn_set_params(self, theta):
+        theta = np.ascontiguousarray(theta, np.float32)
+        return self._check(self._L.hofv_gnn_set_params(self.h, _ptr(theta), theta.size))
+
+    def gnn_save(self, path):
+        return self._check(self._L.hofv_gnn_save(self.h, str(path).encode()))
+
+    def gnn_load(self, path):
+        return self._check(self._L.hofv_gnn_load(self.h, str(path).encode()))
+
+    def gnn_forward(self, v, z, zout):
+        return self._check(self._L.hofv_gnn_forward(self.h, _ptr(_dev(v)), _ptr(_dev(z)),
+                                                    _ptr(_dev(zout))))
+
+    def gnn_loss_grad(self, v, z, delta):
+        loss = C.c_double(0.0)
+        g = np.zeros(self.gnn_num_params(), np.float32)
+        self._check(self._L.hofv_gnn_loss_grad(self.h, _ptr(_dev(v)), _ptr(_dev(z)),
+                                               _ptr(_dev(delta)), C.byref(loss), _ptr(g)))
+        return loss.value, g
+
+    def gnn_record(self, r, delta):
+        return self._check(self._L.hofv_gnn_record(self.h, _ptr(_dev(r)), _ptr(_dev(delta))))
+
+    def gnn_pairs(self):
+        n = C.c_int32(0)
+        self._check(self._L.hofv_gnn_pairs(self.h, C.byref(n)))
+        return n.value
+
+    def gnn_clear_pairs(self):
+        return self._check(self._L.hofv_gnn_clear_pairs(self.h))
+
+    def gnn_train(self, epochs=20, batch=4, lr=1e-3, inner_iters=20, seed=0, verbose=0):
+        o = TrainOpts(epochs, batch, lr, inner_iters, seed, verbose)
+        st = TrainStats()
+        self._check(self._L.hofv_gnn_train(self.h, C.byref(o), C.byref(st)))
+        return st.as_dict()
 
     # ---- inspection --------------------------------------------------------
     def get_face_data(self, first, count, coef=True):
