@@ -367,6 +367,117 @@ def run_hofv(args):
         dist.destroy_process_group()
 
 
+def block_load_steps(ctx, wl, lay, steps, **opts):
+    """Neo-Hookean block: `steps` load increments of the top-face compression,
+    each started from the previous state plus the uniform increment (an
+    admissible predictor), solved to opts' tolerance.  Returns u and stats."""
+    import torch
+
+    from paper_2601_18417_gb300 import hofv
+    from paper_2601_18417_gb300 import inputs as I
+    d = wl.dim
+    xq = ctx.get_points(hofv.PTS_DISP_QP)
+    xb = ctx.get_points(hofv.PTS_DISP_CENTRE)
+    on_top = np.abs(xb[:, d - 1] - 1.0) < 1e-9
+    dev = torch.device("cuda", ctx.device)
+    T = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)  # noqa
+    xc = T(ctx.get_points(hofv.PTS_CELL_CENTROID))
+    inc = T(I.block_top_displacement(1, wl.load_steps, d))
+    u = torch.zeros((d, lay.n_cells), dtype=torch.float64, device=dev)
+    out = []
+    for s in range(1, steps + 1):
+        top = I.block_top_displacement(s, wl.load_steps, d)
+        ctx.set_bc(T(np.where(on_top[:, None, None], top, 0.0) * np.ones_like(xq)),
+                   T(np.where(on_top[:, None], top, 0.0) * np.ones_like(xb)), None, None)
+        u += inc[:, None] * xc[:, d - 1][None, :]
+        out.append(ctx.newton_solve(u, **opts))
+    torch.cuda.synchronize()
+    return u, out
+
+
+def summarize(stats, seconds):
+    return {"seconds": seconds, "load_steps": len(stats),
+            "newton": sum(s["newton_iters"] for s in stats),
+            "krylov": sum(s["krylov_iters"] for s in stats),
+            "residual_evals": sum(s["residual_evals"] for s in stats),
+            "gnn_fallbacks": sum(s["gnn_fallbacks"] for s in stats),
+            "all_converged": all(s["status"] == 0 for s in stats),
+            "worst_r_final_over_r0": max(s["r_final"] / max(s["r0"], 1e-300) for s in stats)}
+
+
+def run_learned(args):
+    """Learned preconditioner: train on (residual, correction) pairs recorded
+    by the solver on one neo-Hookean block, then time load-stepped solves to
+    1e-8 with the plain FP64 AJ, the FP32 AJ and the learned + FP32 AJ
+    preconditioners on held-out meshes."""
+    import dataclasses
+    import tempfile
+
+    import torch
+
+    from paper_2601_18417_gb300 import build as B
+    from paper_2601_18417_gb300 import hofv
+    from paper_2601_18417_gb300 import inputs as I
+    B.build()
+    t_start = time.perf_counter()
+    opts = dict(rtol=1e-8, ftol=1e-13, inner_iters=INNER_ITERS, restart=30, max_krylov=3000,
+                max_newton=20)
+    tw = I.WORKLOADS[args.train_workload]
+    wl, mesh, ctx, lay, setup_s, _, _ = build_workload(tw.name)
+    t0 = time.perf_counter()
+    _, st = block_load_steps(ctx, wl, lay, tw.load_steps, precond=hofv.PC_AJ32,
+                             record_pairs=args.record, **opts)
+    gen_s = time.perf_counter() - t0
+    ctx.gnn_init(seed=args.seed, out_scale=0.0)
+    tr = ctx.gnn_train(epochs=args.epochs, batch=4, lr=args.lr, inner_iters=INNER_ITERS,
+                       seed=args.seed)
+    print(f"[learned] trained: {tr}", file=sys.stderr, flush=True)
+    wpath = os.path.join(tempfile.gettempdir(), f"hofv_gnn_{os.getpid()}.bin")
+    ctx.gnn_save(wpath)
+    result = {"mode": "learned", "train": {"workload": tw.name, "pairs": tr["pairs"],
+                                           "epochs": tr["epochs"], "loss_first": tr["loss_first"],
+                                           "loss_last": tr["loss_last"], "train_s": tr["seconds"],
+                                           "pair_generation_s": gen_s}, "eval": {}}
+    ctx.close()
+    del ctx
+    torch.cuda.empty_cache()
+    held = dataclasses.replace(tw, name=tw.name + "-heldout", mesh_seed=tw.mesh_seed + 100)
+    I.WORKLOADS[held.name] = held
+    evals = [(held.name, held.load_steps)]
+    if args.eval_workload:
+        evals.append((args.eval_workload, args.eval_steps))
+    for name, steps in evals:
+        wl, mesh, ctx, lay, setup_s, _, _ = build_workload(name)
+        res = {"cells": lay.n_cells, "setup_s": setup_s}
+        sols = {}
+        variants = (("plain_fp64_aj", hofv.PC_AJ64, 1, steps), ("fp32_aj", hofv.PC_AJ32, 1, steps),
+                    ("learned", hofv.PC_GNN, 1, steps),
+                    ("learned_no_judge", hofv.PC_GNN, 0, min(steps, 2)))
+        for label, pc, judge, nsteps in variants:
+            if time.perf_counter() - t_start > args.budget_s:
+                res[label] = {"skipped": "time budget"}
+                continue
+            if pc == hofv.PC_GNN:
+                ctx.gnn_load(wpath)
+            capped = dict(opts, max_krylov=600 if judge else 300, max_newton=12 if judge else 6)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            u, st = block_load_steps(ctx, wl, lay, nsteps, precond=pc, gnn_judge=judge, **capped)
+            res[label] = summarize(st, time.perf_counter() - t0)
+            sols[label] = u
+            print(f"[learned] {name} {label}: {res[label]}", file=sys.stderr, flush=True)
+        ref = sols.get("plain_fp64_aj")
+        for label in ("fp32_aj", "learned"):
+            if ref is not None and label in sols:
+                res[label]["rel_diff_vs_plain"] = float((sols[label] - ref).norm() / ref.norm())
+        result["eval"][name] = res
+        ctx.close()
+        del ctx, sols
+        torch.cuda.empty_cache()
+    os.remove(wpath)
+    print(json.dumps(result))
+
+
 def run_reference(args):
     ws, rank, local = dist_env()
     if rank != 0:
@@ -405,11 +516,24 @@ def main():
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--learned", action="store_true",
+                    help="train the learned preconditioner and compare solve times")
+    ap.add_argument("--train-workload", default="hex64j-p2-nh")
+    ap.add_argument("--eval-workload", default="")
+    ap.add_argument("--eval-steps", type=int, default=10)
+    ap.add_argument("--epochs", type=int, default=40)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--record", type=int, default=2, help="1: Newton pairs, 2: + Krylov pairs")
+    ap.add_argument("--budget-s", type=float, default=420.0,
+                    help="wall-clock budget of the learned comparison; later variants are skipped")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.learned:
+        run_learned(args)
     else:
         run_hofv(args)
 

@@ -100,7 +100,13 @@ typedef struct {
   int32_t line_search_max; /* backtracking halvings (default 10) */
   int32_t verbose;         /* 1: one line per Newton step on stderr */
   int32_t record_pairs;    /* 1: keep (-R(u_k), du_k) of every Newton step as a training
-                              pair of the learned preconditioner (hofv_gnn_train) */
+                              pair of the learned preconditioner (hofv_gnn_train); 2: also
+                              keep (J z, z) for the preconditioned Krylov vectors z of a few
+                              Arnoldi steps (exact inverse-Jacobian pairs, one Jv each) */
+  int32_t gnn_judge;       /* 1 (default): a learned-preconditioner restart cycle whose mean
+                              per-iteration residual reduction is worse than that of the last
+                              FGMRES solve preconditioned by AJ alone switches the rest of the
+                              Newton solve to AJ; 0: never switch (non-finite output still does) */
 } hofv_solve_opts;
 
 typedef struct {

@@ -666,6 +666,7 @@ void hofv_default_opts(hofv_solve_opts* o) {
   o->line_search_max = 10;
   o->verbose = 0;
   o->record_pairs = 0;
+  o->gnn_judge = 1;
 }
 
 }  // extern "C"
@@ -742,6 +743,7 @@ static int fgmres(hofv_ctx* c, const hofv_solve_opts& o, const double* u, const 
   HOFV_CUDA(c, cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
   int total = 0;
   double res = dev_norm(c, r, n);
+  const double res0 = res;
   // the learned preconditioner stays on only while its restart cycles reduce
   // the residual at least as fast per iteration as the last AJ cycle did
   hofv_solve_opts oc = o;
@@ -762,6 +764,10 @@ static int fgmres(hofv_ctx* c, const hofv_solve_opts& o, const double* u, const 
       TRY(apply_pc(c, oc, Vj, Zj, st));
       TRY(jvp_impl(c, u, Ru, Zj, w));
       st->residual_evals++;
+      // (J z, z) is an exact pair of the inverse Jacobian: keep a few from
+      // the Krylov space as training data for the learned preconditioner
+      if (o.record_pairs >= 2 && !cycle_gnn && (j == 0 || j == 3 || j == 8 || j == 15 || j == 24))
+        TRY(hofv_gnn_record(c, w, Zj));
       // classical Gram-Schmidt, twice
       launch_dots(V, n, w, j + 1, n, c->d_red, c->d_count, dh, c->red_blocks, c->stream, 0);
       launch_multi_axpy(w, V, dh, j + 1, n, n, c->stream);
@@ -814,16 +820,12 @@ static int fgmres(hofv_ctx* c, const hofv_solve_opts& o, const double* u, const 
       res = dev_norm(c, r, n);
       continue;
     }
-    if (j > 0 && beta > 0.0) {
+    if (j > 0 && beta > 0.0 && cycle_gnn && o.gnn_judge) {
       const double rate = pow(std::max(res, 1e-300) / beta, 1.0 / j);
-      if (!cycle_gnn && oc.precond != HOFV_PC_NONE) {
-        c->aj_rate = rate;
-      } else if (cycle_gnn) {
-        const double judge = c->aj_rate > 0.0 ? c->aj_rate : 0.98;
-        if (!(rate <= judge)) {
-          oc.precond = HOFV_PC_AJ32;
-          st->gnn_fallbacks++;
-        }
+      const double judge = c->aj_rate > 0.0 ? c->aj_rate : 0.98;
+      if (!(rate <= judge)) {
+        oc.precond = HOFV_PC_AJ32;
+        st->gnn_fallbacks++;
       }
     }
     // y = H^{-1} g (upper triangular j x j)
@@ -844,6 +846,8 @@ static int fgmres(hofv_ctx* c, const hofv_solve_opts& o, const double* u, const 
     res = dev_norm(c, r, n);
   }
   HOFV_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (o.precond != HOFV_PC_GNN && o.precond != HOFV_PC_NONE && total > 0 && res0 > 0.0)
+    c->aj_rate = pow(std::max(res, 1e-300) / res0, 1.0 / total);
   *its_out = total;
   *res_out = res;
   return 0;
@@ -864,6 +868,7 @@ extern "C" int hofv_newton_solve(hofv_ctx* c, double* u, const hofv_solve_opts* 
   memset(&st, 0, sizeof(st));
   const auto t0 = std::chrono::steady_clock::now();
   TRY(ensure_krylov(c, o.restart));
+  hofv_solve_opts on = o;
   const int64_t n = c->nc * c->dim;
   double* R = c->d_kvec + 2 * n;
   double* du = c->d_kvec + 3 * n;
@@ -900,7 +905,10 @@ extern "C" int hofv_newton_solve(hofv_ctx* c, double* u, const hofv_solve_opts* 
       const double tol = std::max(eta * rn, 0.5 * o.rtol * r0);
       int its = 0;
       double lres = 0.0;
-      int rc = fgmres(c, o, u, R, Rt, du, tol, o.max_krylov, &st, &its, &lres);
+      // once the learned preconditioner has lost to AJ in this solve, keep AJ
+      const int fb0 = st.gnn_fallbacks;
+      int rc = fgmres(c, on, u, R, Rt, du, tol, o.max_krylov, &st, &its, &lres);
+      if (st.gnn_fallbacks > fb0) on.precond = HOFV_PC_AJ32;
       if (rc < 0) { status = rc; break; }
       if (o.record_pairs) {
         rc = hofv_gnn_record(c, Rt, du);  // (-R(u_k), du_k)

@@ -44,7 +44,7 @@ class SolveOpts(C.Structure):
                 ("restart", C.c_int32), ("max_krylov", C.c_int32), ("eta_max", C.c_double),
                 ("precond", C.c_int32), ("inner_iters", C.c_int32),
                 ("line_search_max", C.c_int32), ("verbose", C.c_int32),
-                ("record_pairs", C.c_int32)]
+                ("record_pairs", C.c_int32), ("gnn_judge", C.c_int32)]
 
 
 class TrainOpts(C.Structure):
