@@ -1,0 +1,109 @@
+"""Parity at the full workload sizes, in the configuration the benchmark
+times.  The oracle cannot hold these meshes' coefficients, so it builds the
+stencils and reconstructions of a sample of cells (random interior cells
+plus corner and edge cells) and evaluates the residual there; the GPU
+evaluates the whole mesh.  Bars as in test_gpu_parity: bit-exact stencils,
+residual |R_gpu - R_orc| <= 1e-12 F_s on the sample (F_s over the sample's
+faces), and properties of the timed Arnoldi step that hold at any size."""
+import numpy as np
+import pytest
+
+import bench
+import oracle
+from paper_2601_18417_gb300 import hofv
+from paper_2601_18417_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def sample_cells(n, dim, k=40, seed=0):
+    rng = np.random.default_rng(seed)
+    nc = n ** dim
+    corners = []
+    for a in (0, n - 1):
+        for b in (0, n - 1):
+            if dim == 2:
+                corners.append(a + n * b)
+            else:
+                for c in (0, n - 1):
+                    corners.append(a + n * (b + n * c))
+    edge = [n // 2, n * (n // 2)] if dim == 2 else [n // 2, n * n * (n // 2) + n // 3]
+    return np.unique(np.concatenate([rng.integers(0, nc, k), corners, edge])).astype(np.int64)
+
+
+def state(wl, xc, u_ex, seed=1):
+    rng = np.random.default_rng(seed)
+    amp = np.abs(u_ex).max()
+    return u_ex + 1e-3 * amp * rng.standard_normal(u_ex.shape)
+
+
+@pytest.mark.parametrize("name", ["quad512j-p3-mixed", "hex96-p3-trig", "hex64j-p2-nh",
+                                  "hex128j-p3-nh"])
+def test_full_size_residual_on_sampled_cells(name):
+    import torch
+    wl, mesh, ctx, lay, setup_s, u_ex, field = bench.build_workload(name)
+    xc = ctx.get_points(hofv.PTS_CELL_CENTROID)
+    u = state(wl, xc, u_ex)
+    ud = torch.as_tensor(u, device="cuda:0")
+    R = torch.empty_like(ud)
+    ctx.residual(ud, R)
+    Rg = R.cpu().numpy()
+    cells = sample_cells(wl.n, wl.dim)
+    # stencils of the sampled cells and of their faces, from the GPU
+    st_gpu = {int(c): ctx.get_cell_data(int(c), 1, ext=False)[0][0] for c in cells}
+    o = oracle.OracleMesh(mesh, I.side_tags(wl.problem, wl.dim), p=wl.p, n_plus=wl.n_plus,
+                          q1=wl.q1, k_weight=wl.k_weight, alpha=wl.alpha)
+    o.prepare(cells)
+    for c in cells:
+        assert np.array_equal(st_gpu[int(c)], o.cell_stencil(c)), c
+    # boundary data from the oracle's own points (same definition)
+    if field is not None:
+        ubq = field.value(o.xq[o.disp_faces()])
+        ubf = field.value(o.xf[o.disp_faces()])
+        body = o.integrate_cells(field.body_force(o.cell_qp, wl.mu, wl.lam))
+    else:
+        top = I.block_top_displacement(1, wl.load_steps, wl.dim)
+        xf = o.xf[o.disp_faces()]
+        on_top = np.abs(xf[:, wl.dim - 1] - 1.0) < 1e-9
+        ubq = np.where(on_top[:, None, None], top, 0.0) * np.ones_like(o.xq[o.disp_faces()])
+        ubf = np.where(on_top[:, None], top, 0.0) * np.ones_like(xf)
+        body = None
+    tbq = np.zeros((max(o.nft, 1), o.Q, wl.dim))
+    Ro = o.residual(wl.law, wl.mu, wl.lam, u, ubq, ubf, tbq, body, cells=cells)
+    fl = o.face_fluxes(wl.law, wl.mu, wl.lam, u, ubq, ubf, tbq)
+    cf = o.cell_faces()
+    Fs = float(max(np.linalg.norm(fl[cf[c]], axis=1).sum() for c in cells))
+    err = np.abs(Rg[:, cells] - Ro).max()
+    assert err <= 1e-12 * Fs, (name, err, Fs, err / Fs)
+    ctx.close()
+
+
+def test_full_size_arnoldi_step_properties():
+    """The benchmark's step on the 512x512 workload: the new basis vector is
+    unit length and orthogonal to the previous ones, the Hessenberg column
+    reproduces w = J z_j, and J z_j matches a forward difference formed here
+    from two library residuals with the same step."""
+    import torch
+    wl, mesh, ctx, lay, setup_s, u_ex, field = bench.build_workload("quad512j-p3-mixed")
+    n = wl.dim * lay.n_cells
+    xc = ctx.get_points(hofv.PTS_CELL_CENTROID)
+    u = torch.as_tensor(state(wl, xc, u_ex), device="cuda:0")
+    Ru = torch.empty_like(u)
+    ctx.residual(u, Ru)
+    J = bench.KRYLOV_J
+    rng = np.random.default_rng(0)
+    V = torch.as_tensor(rng.standard_normal((J + 2, n)), device="cuda:0")
+    V[: J + 1] = torch.linalg.qr(V[: J + 1].T)[0].T
+    Z = torch.zeros((J + 1, n), dtype=torch.float64, device="cuda:0")
+    h = ctx.arnoldi_step(u, Ru, hofv.PC_AJ32, bench.INNER_ITERS, V, Z, J)
+    torch.cuda.synchronize()
+    assert abs(float(V[J + 1].norm()) - 1.0) < 1e-12
+    assert float((V[: J + 1] @ V[J + 1]).abs().max()) < 1e-10
+    w = (V[: J + 2].T @ torch.as_tensor(h, device="cuda:0"))
+    z = Z[J]
+    eps = 1.4901161193847656e-08 * (1 + float(u.norm())) / float(z.norm())
+    R1 = torch.empty_like(u)
+    ctx.residual((u.reshape(-1) + eps * z).reshape(u.shape).contiguous(), R1)
+    fd = (R1 - Ru).reshape(-1) / eps
+    assert float((w - fd).norm() / fd.norm()) < 1e-6
+    ctx.close()
