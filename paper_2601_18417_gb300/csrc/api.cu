@@ -104,6 +104,9 @@ static void free_built(hofv_ctx* c) {
   c->d_aj_diag = c->d_aj_off = nullptr;
   c->d_aj_col = nullptr;
   c->d_aj_diag32 = c->d_aj_off32 = nullptr;
+  c->d_aj_invd = nullptr;
+  c->d_aj_invd32 = nullptr;
+  c->d_bar = nullptr;
   c->d_cg64 = nullptr;
   c->d_cg32 = nullptr;
   c->d_V = c->d_Z = c->d_kvec = c->d_h = nullptr;
@@ -419,6 +422,10 @@ int hofv_build_stencils(hofv_ctx* c) {
   TRY(dev_alloc(c, &c->d_aj_off, nc * nlf));
   TRY(dev_alloc(c, &c->d_aj_diag32, nc));
   TRY(dev_alloc(c, &c->d_aj_off32, nc * nlf));
+  TRY(dev_alloc(c, &c->d_aj_invd, nc));
+  TRY(dev_alloc(c, &c->d_bar, 4));
+  HOFV_CUDA(c, cudaMemset(c->d_bar, 0, 4 * sizeof(unsigned int)));
+  TRY(dev_alloc(c, &c->d_aj_invd32, nc));
   TRY(run_face_aux(c));
   // ---- boundary data, sources and scratch ----
   TRY(dev_alloc(c, &c->d_ubq, std::max<int64_t>(c->nfd, 1) * c->Q * d));
@@ -440,8 +447,8 @@ int hofv_build_stencils(hofv_ctx* c) {
   TRY(dev_alloc(c, &c->d_scal, 256));
   HOFV_CUDA(c, cudaMemset(c->d_count, 0, sizeof(unsigned int) * 256));
   HOFV_CUDA(c, cudaMemset(c->d_scal, 0, sizeof(double) * 256));
-  TRY(dev_alloc(c, &c->d_cg64, 6 * nc * d));
-  TRY(dev_alloc(c, &c->d_cg32, 6 * nc * d));
+  TRY(dev_alloc(c, &c->d_cg64, 8 * nc * d));
+  TRY(dev_alloc(c, &c->d_cg32, 8 * nc * d));
   HOFV_CUDA(c, cudaDeviceSynchronize());
   c->src_dirty = false;
   c->built = true;
@@ -779,6 +786,7 @@ static int fgmres(hofv_ctx* c, const hofv_solve_opts& o, const double* u, const 
       double hn = 0.0;
       HOFV_CUDA(c, cudaMemcpyAsync(&hn, dh + 2 * (m + 2), sizeof(double), cudaMemcpyDeviceToHost, c->stream));
       HOFV_CUDA(c, cudaStreamSynchronize(c->stream));
+      TRY(check_pc_barrier(c));
       if (!std::isfinite(hn) && cycle_gnn) {
         // learned preconditioner failed: drop this cycle, continue with AJ
         oc.precond = HOFV_PC_AJ32;
@@ -1089,6 +1097,7 @@ extern "C" int hofv_arnoldi_step(hofv_ctx* c, const double* u, const double* Ru,
   HOFV_CUDA(c, cudaMemcpyAsync(hb.data(), dh, sizeof(double) * hb.size(), cudaMemcpyDeviceToHost,
                                c->stream));
   HOFV_CUDA(c, cudaStreamSynchronize(c->stream));
+  TRY(check_pc_barrier(c));
   for (int i = 0; i < k; ++i) h[i] = hb[i] + hb[k + i];
   h[k] = hb[2 * k];
   if (!std::isfinite(h[k])) return fail(c, HOFV_ENAN, "non-finite value in the Arnoldi step");
@@ -1126,3 +1135,16 @@ extern "C" int hofv_force_scale(hofv_ctx* c, const double* u, double* fs) {
   if (!std::isfinite(m)) return fail(c, HOFV_ENAN, "non-finite face flux");
   return HOFV_OK;
 }
+
+namespace hofv {
+int check_pc_barrier(hofv_ctx* c) {
+  if (!c->d_bar) return 0;
+  int err = 0;
+  HOFV_CUDA(c, cudaMemcpy(&err, c->d_bar + 2, sizeof(int), cudaMemcpyDeviceToHost));
+  if (err) {
+    HOFV_CUDA(c, cudaMemset(c->d_bar, 0, 4 * sizeof(unsigned int)));
+    return fail(c, HOFV_ECUDA, "approximate-Jacobian solve: grid barrier timed out");
+  }
+  return 0;
+}
+}  // namespace hofv

@@ -113,6 +113,9 @@ struct hofv_ctx {
   double* d_aj_off = nullptr;       // [nc][nlf]
   float* d_aj_diag32 = nullptr;
   float* d_aj_off32 = nullptr;
+  unsigned int* d_bar = nullptr;    // grid barrier of the persistent CG: count, generation, error
+  double* d_aj_invd = nullptr;      // 1 / (-diag), FP64 and FP32
+  float* d_aj_invd32 = nullptr;
   // CG work vectors (sized dim*nc each)
   double *d_cg64 = nullptr;         // 5 vectors FP64
   float *d_cg32 = nullptr;          // 5 vectors FP32
@@ -196,6 +199,9 @@ void launch_combine(double* x, const double* Z, const double* y, int k, int64_t 
                     cudaStream_t st);
 void launch_axpby(double* y, double a, const double* x, double b, int64_t n, cudaStream_t st);
 int aj_precondition(hofv_ctx* c, int kind, int iters, const double* v, double* z);
+// error of a timed-out persistent-CG grid barrier since the last check
+// (reads the flag: call after a stream synchronisation), then clears it
+int check_pc_barrier(hofv_ctx* c);
 
 // ---- learned preconditioner (gnn.cu) ----
 int gnn_apply(hofv_ctx* c, const double* v, const double* z_aj, double* z);

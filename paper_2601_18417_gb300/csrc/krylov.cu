@@ -7,6 +7,8 @@
 // block order and publishes the result to device memory, where the next
 // kernel on the stream reads it.  No host round trip is needed inside Jv or
 // inside the preconditioner.
+#include <stdlib.h>
+
 #include "hofv_internal.cuh"
 
 namespace hofv {
@@ -24,6 +26,38 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   }
   __syncthreads();
   return s;  // valid in thread 0
+}
+
+// Block sum in the precision of the values (FP32 stays on the FP32 pipe);
+// the per-warp results are added by warp 0 in double.  Valid in thread 0.
+// FP64 warp instructions cost 16 cycles of the SM's FP64 pipe on this GPU,
+// so FP64 reductions are kept to one warp wherever possible.
+template <typename T>
+__device__ __forceinline__ double block_sum_t(T v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) sh[wid] = (double)v;
+  __syncthreads();
+  double s = 0.0;
+  if (wid == 0) {
+    s = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  }
+  __syncthreads();
+  return s;
+}
+
+// Sum of partials red[0..nb) by warp 0 of the block (fixed order: lane l adds
+// partials l, l+32, ..., then a fixed shuffle tree), accumulated in A.
+// Valid in thread 0.
+template <typename A = double>
+__device__ __forceinline__ double warp0_sum(const double* red, unsigned int nb) {
+  A s = (A)0;
+  if (threadIdx.x < 32) {
+    for (unsigned int b = threadIdx.x; b < nb; b += 32) s += (A)__ldcg(red + b);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  }
+  return (double)s;
 }
 
 // Returns true in thread 0 of the block that finished last.
@@ -61,7 +95,7 @@ __global__ void k_mdot(const double* __restrict__ X, int64_t ldx, const double* 
   if (threadIdx.x == 0) red[k * gridDim.x + blockIdx.x] = s;
   if (last_block(count + k, gridDim.x)) {
     __threadfence();
-    const double t = final_sum(red + k * gridDim.x, gridDim.x, sh);
+    const double t = warp0_sum(red + k * gridDim.x, gridDim.x);
     if (threadIdx.x == 0) {
       out[k] = mode == 1 ? sqrt(t) : t;
       count[k] = 0;
@@ -71,6 +105,8 @@ __global__ void k_mdot(const double* __restrict__ X, int64_t ldx, const double* 
 
 void launch_dots(const double* X, int64_t ldx, const double* y, int nvec, int64_t n, double* red,
                  unsigned int* count, double* out, int blocks, cudaStream_t st, int mode) {
+  // few blocks per vector: every block ends in FP64 warp reductions
+  blocks = (int)std::min<int64_t>(std::max(blocks / 4, 1), (n + kRedThreads - 1) / kRedThreads);
   dim3 grid((unsigned)blocks, (unsigned)nvec);
   k_mdot<<<grid, kRedThreads, 0, st>>>(X, ldx, y, n, red, count, out, mode);
 }
@@ -162,198 +198,480 @@ void launch_axpby(double* y, double a, const double* x, double b, int64_t n, cud
 
 // ---------------------------------------------------------------------
 // approximate Jacobian A = Kbar * A1 (Sec. 4.1), A1 negative definite with
-// Kbar = 1.  z = A^{-1} v solves B z = -v / Kbar with B = -A1 (SPD),
-// by a fixed number of Jacobi-preconditioned CG iterations on all `dim`
-// right-hand sides at once.  T = float (FP32 storage and arithmetic) or
-// double.  Scalars: sc[0..d) rz, sc[d..2d) alpha, sc[2d..3d) beta.
+// Kbar = 1.  z = A^{-1} v solves B z = -v / Kbar with B = -A1 (SPD), by a
+// fixed number of Jacobi-preconditioned conjugate-gradient iterations on
+// all `dim` right-hand sides at once, in the single-reduction form of
+// Chronopoulos & Gear (J. Comput. Appl. Math. 25, 1989): per iteration one
+// product w = B u (u = D^{-1} r) and the two inner products (r,u), (w,u),
+// with s = B p carried by recurrence.  One kernel per iteration: the vector
+// updates of iteration i-1 are recomputed on the fly for the neighbours
+// that the product of iteration i reads (r, w and s are double-buffered),
+// so no grid-wide synchronisation is needed.  T = float or double.
+// Scalars (double): sc[0..d) gamma_prev, sc[d..2d) alpha, sc[2d..3d) beta.
 // ---------------------------------------------------------------------
 template <typename T, int DIM>
-__global__ void k_cg_init(int64_t nc, const double* __restrict__ v, double inv_kbar,
-                          const T* __restrict__ diag, T* __restrict__ x, T* __restrict__ r,
-                          T* __restrict__ z, T* __restrict__ p, double* red,
-                          unsigned int* count, double* sc) {
-  __shared__ double sh[32];
-  double part[DIM];
-#pragma unroll
-  for (int j = 0; j < DIM; ++j) part[j] = 0.0;
-  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc;
-       c += (int64_t)gridDim.x * blockDim.x) {
-    const T dg = -diag[c];
-#pragma unroll
-    for (int j = 0; j < DIM; ++j) {
-      const int64_t i = j * nc + c;
-      const T rr = (T)(-v[i] * inv_kbar);
-      const T zz = rr / dg;
-      r[i] = rr;
-      z[i] = zz;
-      x[i] = (T)0;
-      p[i] = (T)0;
-      part[j] += (double)rr * (double)zz;
-    }
-  }
-#pragma unroll
+__device__ __forceinline__ void cg_finalize(const double* red, unsigned int nb, double* sh,
+                                            double* sc, bool first) {
   for (int j = 0; j < DIM; ++j) {
-    const double s = block_sum(part[j], sh);
-    if (threadIdx.x == 0) red[j * gridDim.x + blockIdx.x] = s;
-  }
-  if (last_block(count, gridDim.x)) {
-    __threadfence();
-    for (int j = 0; j < DIM; ++j) {
-      const double t = final_sum(red + j * gridDim.x, gridDim.x, sh);
-      if (threadIdx.x == 0) {
-        sc[j] = t;
-        sc[2 * DIM + j] = 0.0;
+    const double gamma = warp0_sum<T>(red + (2 * j) * nb, nb);
+    const double delta = warp0_sum<T>(red + (2 * j + 1) * nb, nb);
+    if (threadIdx.x == 0) {
+      double alpha, beta;
+      if (first) {
+        beta = 0.0;
+        alpha = delta != 0.0 ? gamma / delta : 0.0;
+      } else {
+        const double gp = sc[j], ap = sc[DIM + j];
+        beta = gp != 0.0 ? gamma / gp : 0.0;
+        const double den = ap != 0.0 ? delta - beta * gamma / ap : 0.0;
+        alpha = den != 0.0 ? gamma / den : 0.0;
       }
+      sc[j] = gamma;
+      sc[DIM + j] = alpha;
+      sc[2 * DIM + j] = beta;
     }
-    if (threadIdx.x == 0) count[0] = 0;
   }
 }
 
-// p_new = z + beta p_old (own and neighbours, on the fly); q = B p_new;
-// partial p.q -> alpha = rz / pq
+// r0 = b = -v/Kbar, w0 = B D^{-1} r0; x = p = 0, s_{-1} = 0; alpha0 = gamma0/delta0
 template <typename T, int DIM>
-__global__ void k_cg_spmv(int64_t nc, const T* __restrict__ diag, const int32_t* __restrict__ col,
-                          const T* __restrict__ off, const T* __restrict__ z,
-                          const T* __restrict__ p_old, T* __restrict__ p_new, T* __restrict__ q,
-                          double* red, unsigned int* count, double* sc) {
+__global__ void k_cg_init(int64_t nc, const double* __restrict__ v, double inv_kbar,
+                          const T* __restrict__ diag, const T* __restrict__ invd,
+                          const int32_t* __restrict__ col,
+                          const T* __restrict__ off, T* __restrict__ r0, T* __restrict__ w0,
+                          T* __restrict__ sm1, T* __restrict__ x, T* __restrict__ p, double* red,
+                          unsigned int* count, double* sc) {
   constexpr int NLF = 2 * DIM;
   __shared__ double sh[32];
-  double part[DIM];
-  T beta[DIM];
+  T pg[DIM], pd[DIM];  // per-thread partials in the vector precision
 #pragma unroll
-  for (int j = 0; j < DIM; ++j) {
-    part[j] = 0.0;
-    beta[j] = (T)sc[2 * DIM + j];
-  }
+  for (int j = 0; j < DIM; ++j) pg[j] = pd[j] = (T)0;
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc;
        c += (int64_t)gridDim.x * blockDim.x) {
-    const T dg = -diag[c];
-    T pc[DIM], qc[DIM];
+    const T D = -diag[c], iD = invd[c];
+    T u[DIM], w[DIM];
 #pragma unroll
     for (int j = 0; j < DIM; ++j) {
-      pc[j] = z[j * nc + c] + beta[j] * p_old[j * nc + c];
-      qc[j] = dg * pc[j];
+      const T b = (T)(-v[j * nc + c] * inv_kbar);
+      r0[j * nc + c] = b;
+      u[j] = b * iD;
+      w[j] = D * u[j];
+      x[j * nc + c] = (T)0;
+      p[j * nc + c] = (T)0;
+      sm1[j * nc + c] = (T)0;
+      pg[j] += b * u[j];
     }
 #pragma unroll
     for (int lf = 0; lf < NLF; ++lf) {
       const int32_t nb = col[c * NLF + lf];
       if (nb < 0) continue;
-      const T o = off[c * NLF + lf];
+      const T o = off[c * NLF + lf] * invd[nb];
 #pragma unroll
-      for (int j = 0; j < DIM; ++j) qc[j] -= o * (z[j * nc + nb] + beta[j] * p_old[j * nc + nb]);
+      for (int j = 0; j < DIM; ++j) w[j] -= o * (T)(-v[j * nc + nb] * inv_kbar);
     }
 #pragma unroll
     for (int j = 0; j < DIM; ++j) {
-      p_new[j * nc + c] = pc[j];
-      q[j * nc + c] = qc[j];
-      part[j] += (double)pc[j] * (double)qc[j];
+      w0[j * nc + c] = w[j];
+      pd[j] += w[j] * u[j];
     }
   }
 #pragma unroll
   for (int j = 0; j < DIM; ++j) {
-    const double s = block_sum(part[j], sh);
-    if (threadIdx.x == 0) red[j * gridDim.x + blockIdx.x] = s;
+    const double a = block_sum_t(pg[j], sh);
+    const double b = block_sum_t(pd[j], sh);
+    if (threadIdx.x == 0) {
+      red[(2 * j) * gridDim.x + blockIdx.x] = a;
+      red[(2 * j + 1) * gridDim.x + blockIdx.x] = b;
+    }
   }
   if (last_block(count, gridDim.x)) {
     __threadfence();
-    for (int j = 0; j < DIM; ++j) {
-      const double t = final_sum(red + j * gridDim.x, gridDim.x, sh);
-      if (threadIdx.x == 0) sc[DIM + j] = t != 0.0 ? sc[j] / t : 0.0;
-    }
+    cg_finalize<T, DIM>(red, gridDim.x, sh, sc, true);
     if (threadIdx.x == 0) count[0] = 0;
   }
 }
 
-// x += alpha p; r -= alpha q; z = r / D; partial r.z -> beta, rz
+// iteration i: from r_{i-1}, w_{i-1}, s_{i-2} and alpha_{i-1}, beta_{i-1}:
+//   s_{i-1} = w_{i-1} + beta s_{i-2};  r_i = r_{i-1} - alpha s_{i-1}
+//   p_{i-1} = u_{i-1} + beta p_{i-2};  x += alpha p_{i-1}
+//   w_i = B u_i, u_i = D^{-1} r_i;  partial (r_i, u_i), (w_i, u_i)
 template <typename T, int DIM>
-__global__ void k_cg_update(int64_t nc, const T* __restrict__ diag, const T* __restrict__ p,
-                            const T* __restrict__ q, T* __restrict__ x, T* __restrict__ r,
-                            T* __restrict__ z, double* red, unsigned int* count, double* sc) {
+__global__ void k_cg_iter(int64_t nc, const T* __restrict__ diag, const T* __restrict__ invd,
+                          const int32_t* __restrict__ col,
+                          const T* __restrict__ off, const T* __restrict__ r_old,
+                          const T* __restrict__ w_old, const T* __restrict__ s_oldold,
+                          T* __restrict__ r_new, T* __restrict__ w_new, T* __restrict__ s_new,
+                          T* __restrict__ x, T* __restrict__ p, double* red, unsigned int* count,
+                          double* sc) {
+  constexpr int NLF = 2 * DIM;
   __shared__ double sh[32];
-  double part[DIM];
-  T alpha[DIM];
+  T alpha[DIM], beta[DIM];
+  T pg[DIM], pd[DIM];  // per-thread partials in the vector precision
 #pragma unroll
   for (int j = 0; j < DIM; ++j) {
-    part[j] = 0.0;
     alpha[j] = (T)sc[DIM + j];
+    beta[j] = (T)sc[2 * DIM + j];
+    pg[j] = pd[j] = 0.0;
   }
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc;
        c += (int64_t)gridDim.x * blockDim.x) {
-    const T dg = -diag[c];
+    const T D = -diag[c], iD = invd[c];
+    T un[DIM], w[DIM];
 #pragma unroll
     for (int j = 0; j < DIM; ++j) {
       const int64_t i = j * nc + c;
-      x[i] += alpha[j] * p[i];
-      const T rr = r[i] - alpha[j] * q[i];
-      const T zz = rr / dg;
-      r[i] = rr;
-      z[i] = zz;
-      part[j] += (double)rr * (double)zz;
+      const T ro = r_old[i];
+      const T s1 = w_old[i] + beta[j] * s_oldold[i];
+      const T rn = ro - alpha[j] * s1;
+      const T pp = ro * iD + beta[j] * p[i];
+      p[i] = pp;
+      x[i] += alpha[j] * pp;
+      s_new[i] = s1;
+      r_new[i] = rn;
+      un[j] = rn * iD;
+      w[j] = D * un[j];
+      pg[j] += rn * un[j];
+    }
+#pragma unroll
+    for (int lf = 0; lf < NLF; ++lf) {
+      const int32_t nb = col[c * NLF + lf];
+      if (nb < 0) continue;
+      const T o = off[c * NLF + lf] * invd[nb];
+#pragma unroll
+      for (int j = 0; j < DIM; ++j) {
+        const int64_t i = j * nc + nb;
+        const T rn = r_old[i] - alpha[j] * (w_old[i] + beta[j] * s_oldold[i]);
+        w[j] -= o * rn;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) {
+      w_new[j * nc + c] = w[j];
+      pd[j] += w[j] * un[j];
     }
   }
 #pragma unroll
   for (int j = 0; j < DIM; ++j) {
-    const double s = block_sum(part[j], sh);
-    if (threadIdx.x == 0) red[j * gridDim.x + blockIdx.x] = s;
+    const double a = block_sum_t(pg[j], sh);
+    const double b = block_sum_t(pd[j], sh);
+    if (threadIdx.x == 0) {
+      red[(2 * j) * gridDim.x + blockIdx.x] = a;
+      red[(2 * j + 1) * gridDim.x + blockIdx.x] = b;
+    }
   }
   if (last_block(count, gridDim.x)) {
     __threadfence();
-    for (int j = 0; j < DIM; ++j) {
-      const double t = final_sum(red + j * gridDim.x, gridDim.x, sh);
-      if (threadIdx.x == 0) {
-        sc[2 * DIM + j] = sc[j] != 0.0 ? t / sc[j] : 0.0;
-        sc[j] = t;
-      }
-    }
+    cg_finalize<T, DIM>(red, gridDim.x, sh, sc, false);
     if (threadIdx.x == 0) count[0] = 0;
   }
 }
 
-template <typename T>
-__global__ void k_to_double(int64_t n, const T* __restrict__ x, double* __restrict__ z) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    z[i] = (double)x[i];
+// z = x + alpha (u + beta p), u = D^{-1} r (the last step's update), in FP64
+template <typename T, int DIM>
+__global__ void k_cg_finish(int64_t nc, const T* __restrict__ invd, const T* __restrict__ r,
+                            const T* __restrict__ x, const T* __restrict__ p,
+                            const double* __restrict__ sc, double* __restrict__ z) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  const T iD = invd[c];
+#pragma unroll
+  for (int j = 0; j < DIM; ++j) {
+    const int64_t i = j * nc + c;
+    const T alpha = (T)sc[DIM + j], beta = (T)sc[2 * DIM + j];
+    z[i] = (double)(x[i] + alpha * (r[i] * iD + beta * p[i]));
+  }
+}
+
+// ---------------------------------------------------------------------
+// The same iteration in one persistent cooperative launch: the blocks are
+// co-resident (cudaLaunchCooperativeKernel) and meet at one grid barrier
+// per iteration, after which every block forms the scalars from the
+// per-block partial sums in the same fixed order.  The barrier's spin is
+// bounded: on time-out the kernel sets an error flag and returns, and the
+// host reports the error at its next synchronisation.
+// ---------------------------------------------------------------------
+constexpr unsigned int kBarrierSpinLimit = 1u << 24;  // x ~64 ns sleeps: ~1 s
+
+struct GridBarrier {
+  unsigned int* count;
+  unsigned int* gen;
+  int* err;
+};
+
+__device__ __forceinline__ bool grid_barrier(const GridBarrier& gb, unsigned int nblocks) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int* vgen = gb.gen;
+    volatile int* verr = gb.err;
+    const unsigned int g = *vgen;
+    __threadfence();
+    int ok = 1;
+    if (atomicAdd(gb.count, 1u) == nblocks - 1) {
+      atomicExch(gb.count, 0u);
+      __threadfence();
+      atomicAdd(gb.gen, 1u);
+    } else {
+      unsigned int spins = 0;
+      while (*vgen == g) {
+        if (++spins > kBarrierSpinLimit || *verr) {
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    if (!ok) atomicExch(gb.err, 1);
+    __threadfence();
+    s_ok = ok && !*verr;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+constexpr int kPersistThreads = 1024;
+
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kPersistThreads)
+    k_cg_persist(int64_t nc, int iters, const double* __restrict__ v, double inv_kbar,
+                 const T* __restrict__ diag, const T* __restrict__ invd,
+                 const int32_t* __restrict__ col, const T* __restrict__ off, T* x, T* p, T* r0,
+                 T* r1, T* w0, T* w1, T* s0, T* s1, double* part, GridBarrier gb,
+                 double* __restrict__ zout) {
+  constexpr int NLF = 2 * DIM;
+  __shared__ double sh[32];
+  __shared__ double s_sc[3 * DIM];  // gamma_prev, alpha, beta
+  __shared__ T s_ab[2 * DIM];       // alpha, beta in the vector precision
+  const unsigned int nb = gridDim.x;
+  T* r[2] = {r0, r1};
+  T* w[2] = {w0, w1};
+  T* s[2] = {s0, s1};
+  T pg[DIM], pd[DIM];  // per-thread partials in the vector precision
+  // ---- iteration 0: r0 = b, w0 = B D^-1 r0, x = p = 0, s_{-1} = 0
+#pragma unroll
+  for (int j = 0; j < DIM; ++j) pg[j] = pd[j] = (T)0;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const T D = -diag[c], iD = invd[c];
+    T u[DIM], ww[DIM];
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) {
+      const T b = (T)(-v[j * nc + c] * inv_kbar);
+      r[0][j * nc + c] = b;
+      u[j] = b * iD;
+      ww[j] = D * u[j];
+      x[j * nc + c] = (T)0;
+      p[j * nc + c] = (T)0;
+      s[1][j * nc + c] = (T)0;
+      pg[j] += b * u[j];
+    }
+#pragma unroll
+    for (int lf = 0; lf < NLF; ++lf) {
+      const int32_t n2 = col[c * NLF + lf];
+      if (n2 < 0) continue;
+      const T o = off[c * NLF + lf] * invd[n2];
+#pragma unroll
+      for (int j = 0; j < DIM; ++j) ww[j] -= o * (T)(-v[j * nc + n2] * inv_kbar);
+    }
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) {
+      w[0][j * nc + c] = ww[j];
+      pd[j] += ww[j] * u[j];
+    }
+  }
+  for (int it = 0; it < iters; ++it) {
+    // partial sums of this block -> part[parity][2j(+1)][block]
+    double* pp = part + (int64_t)(it & 1) * 2 * DIM * nb;
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) {
+      const double a = block_sum_t(pg[j], sh);
+      const double b = block_sum_t(pd[j], sh);
+      if (threadIdx.x == 0) {
+        pp[(2 * j) * nb + blockIdx.x] = a;
+        pp[(2 * j + 1) * nb + blockIdx.x] = b;
+      }
+    }
+    if (!grid_barrier(gb, nb)) return;
+    // every block forms the same scalars in the same order
+    for (int j = 0; j < DIM; ++j) {
+      const double gamma = warp0_sum<T>(pp + (2 * j) * nb, nb);
+      const double delta = warp0_sum<T>(pp + (2 * j + 1) * nb, nb);
+      if (threadIdx.x == 0) {
+        double alpha, beta;
+        if (it == 0) {
+          beta = 0.0;
+          alpha = delta != 0.0 ? gamma / delta : 0.0;
+        } else {
+          const double gp = s_sc[j], ap = s_sc[DIM + j];
+          beta = gp != 0.0 ? gamma / gp : 0.0;
+          const double den = ap != 0.0 ? delta - beta * gamma / ap : 0.0;
+          alpha = den != 0.0 ? gamma / den : 0.0;
+        }
+        s_sc[j] = gamma;
+        s_sc[DIM + j] = alpha;
+        s_sc[2 * DIM + j] = beta;
+        s_ab[j] = (T)alpha;
+        s_ab[DIM + j] = (T)beta;
+      }
+    }
+    __syncthreads();
+    T alpha[DIM], beta[DIM];
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) {
+      alpha[j] = s_ab[j];
+      beta[j] = s_ab[DIM + j];
+    }
+    const int i = it + 1;  // the iteration this pass computes
+    const T* ro_ = r[(i - 1) & 1];
+    const T* wo_ = w[(i - 1) & 1];
+    const T* so_ = s[i & 1];
+    if (i == iters) {
+      // last step: z = x + alpha (u + beta p), u = D^-1 r
+      for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc;
+           c += (int64_t)gridDim.x * blockDim.x) {
+        const T iD = invd[c];
+#pragma unroll
+        for (int j = 0; j < DIM; ++j) {
+          const int64_t k = j * nc + c;
+          zout[k] = (double)(x[k] + alpha[j] * (ro_[k] * iD + beta[j] * p[k]));
+        }
+      }
+      return;
+    }
+    T* rn_ = r[i & 1];
+    T* wn_ = w[i & 1];
+    T* sn_ = s[(i - 1) & 1];
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) pg[j] = pd[j] = (T)0;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc;
+         c += (int64_t)gridDim.x * blockDim.x) {
+      const T D = -diag[c], iD = invd[c];
+      T un[DIM], ww[DIM];
+#pragma unroll
+      for (int j = 0; j < DIM; ++j) {
+        const int64_t k = j * nc + c;
+        const T ro = ro_[k];
+        const T s1 = wo_[k] + beta[j] * so_[k];
+        const T rn = ro - alpha[j] * s1;
+        const T pv = ro * iD + beta[j] * p[k];
+        p[k] = pv;
+        x[k] += alpha[j] * pv;
+        sn_[k] = s1;
+        rn_[k] = rn;
+        un[j] = rn * iD;
+        ww[j] = D * un[j];
+        pg[j] += rn * un[j];
+      }
+#pragma unroll
+      for (int lf = 0; lf < NLF; ++lf) {
+        const int32_t n2 = col[c * NLF + lf];
+        if (n2 < 0) continue;
+        const T o = off[c * NLF + lf] * invd[n2];
+#pragma unroll
+        for (int j = 0; j < DIM; ++j) {
+          const int64_t k = j * nc + n2;
+          ww[j] -= o * (ro_[k] - alpha[j] * (wo_[k] + beta[j] * so_[k]));
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < DIM; ++j) {
+        wn_[j * nc + c] = ww[j];
+        pd[j] += ww[j] * un[j];
+      }
+    }
+  }
 }
 
 template <typename T, int DIM>
-static void cg_run(hofv_ctx* c, const T* diag, const T* off, T* work, int iters, const double* v,
-                   double* zout) {
+static bool cg_persist_run(hofv_ctx* c, const T* diag, const T* invd, const T* off, T* work,
+                           int iters, const double* v, double* zout) {
+  static int max_blocks[2][2] = {{-1, -1}, {-1, -1}};
+  int& mb = max_blocks[sizeof(T) == 8][DIM == 3];
+  if (mb < 0) {
+    int per_sm = 0, dev = 0, nsm = 0, coop = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (!coop ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg_persist<T, DIM>,
+                                                      kPersistThreads, 0) != cudaSuccess)
+      per_sm = 0;
+    mb = std::min(per_sm, 1) * nsm;
+    const char* env = getenv("HOFV_CG_PERSISTENT");
+    if (env && env[0] == '0') mb = 0;
+  }
+  if (mb <= 0 || !c->d_bar) return false;
   const int64_t nc = c->nc, n = DIM * nc;
   T* x = work;
-  T* r = work + n;
-  T* z = work + 2 * n;
-  T* p0 = work + 3 * n;
-  T* p1 = work + 4 * n;
-  T* q = work + 5 * n;
+  T* p = work + n;
+  int64_t nc_ = nc;
+  int iters_ = std::max(iters, 1);
+  double inv_kbar = 1.0 / c->mat.kbar;
+  T *r0 = work + 2 * n, *r1 = work + 3 * n, *w0 = work + 4 * n, *w1 = work + 5 * n;
+  T *s0 = work + 6 * n, *s1 = work + 7 * n;
+  double* part = c->d_red;
+  GridBarrier gb{c->d_bar, c->d_bar + 1, reinterpret_cast<int*>(c->d_bar + 2)};
+  void* args[] = {&nc_, &iters_, (void*)&v, &inv_kbar, (void*)&diag, (void*)&invd,
+                  (void*)&c->d_aj_col, (void*)&off, &x, &p, &r0, &r1, &w0, &w1, &s0, &s1, &part,
+                  &gb, &zout};
+  const cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_cg_persist<T, DIM>, dim3(mb),
+                                                    dim3(kPersistThreads), args, 0, c->stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return true;
+}
+
+template <typename T, int DIM>
+static void cg_run(hofv_ctx* c, const T* diag, const T* invd, const T* off, T* work, int iters,
+                   const double* v, double* zout) {
+  const int64_t nc = c->nc, n = DIM * nc;
+  T* x = work;
+  T* p = work + n;
+  T* r[2] = {work + 2 * n, work + 3 * n};
+  T* w[2] = {work + 4 * n, work + 5 * n};
+  T* s[2] = {work + 6 * n, work + 7 * n};
   const int blocks = c->red_blocks;
   double* red = c->d_red;
   unsigned int* cnt = c->d_count;
-  double* sc = c->d_scal + 32;  // slots 32..40: CG rz, alpha, beta per component
+  double* sc = c->d_scal + 32;  // slots 32..40
   cudaStream_t st = c->stream;
-  k_cg_init<T, DIM><<<blocks, kRedThreads, 0, st>>>(nc, v, 1.0 / c->mat.kbar, diag, x, r, z, p0,
-                                                   red, cnt, sc);
-  for (int it = 0; it < iters; ++it) {
-    T* po = (it & 1) ? p1 : p0;
-    T* pn = (it & 1) ? p0 : p1;
-    k_cg_spmv<T, DIM><<<blocks, kRedThreads, 0, st>>>(nc, diag, c->d_aj_col, off, z, po, pn, q, red,
-                                                     cnt, sc);
-    k_cg_update<T, DIM><<<blocks, kRedThreads, 0, st>>>(nc, diag, pn, q, x, r, z, red, cnt, sc);
-  }
-  k_to_double<T><<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, st>>>(n, x, zout);
+  if (iters < 1) iters = 1;
+  k_cg_init<T, DIM><<<blocks, kRedThreads, 0, st>>>(nc, v, 1.0 / c->mat.kbar, diag, invd, c->d_aj_col,
+                                                   off, r[0], w[0], s[1], x, p, red, cnt, sc);
+  for (int i = 1; i < iters; ++i)
+    k_cg_iter<T, DIM><<<blocks, kRedThreads, 0, st>>>(nc, diag, invd, c->d_aj_col, off, r[(i - 1) & 1],
+                                                     w[(i - 1) & 1], s[i & 1], r[i & 1], w[i & 1],
+                                                     s[(i - 1) & 1], x, p, red, cnt, sc);
+  k_cg_finish<T, DIM><<<(unsigned)((nc + 255) / 256), 256, 0, st>>>(nc, invd, r[(iters - 1) & 1], x,
+                                                                     p, sc, zout);
 }
 
 int aj_precondition(hofv_ctx* c, int kind, int iters, const double* v, double* z) {
+  bool done = false;
+  if (kind == HOFV_PC_AJ64)
+    done = c->dim == 2
+               ? cg_persist_run<double, 2>(c, c->d_aj_diag, c->d_aj_invd, c->d_aj_off, c->d_cg64, iters, v, z)
+               : cg_persist_run<double, 3>(c, c->d_aj_diag, c->d_aj_invd, c->d_aj_off, c->d_cg64, iters, v, z);
+  else
+    done = c->dim == 2
+               ? cg_persist_run<float, 2>(c, c->d_aj_diag32, c->d_aj_invd32, c->d_aj_off32, c->d_cg32, iters, v, z)
+               : cg_persist_run<float, 3>(c, c->d_aj_diag32, c->d_aj_invd32, c->d_aj_off32, c->d_cg32, iters, v, z);
+  if (done) {
+    HOFV_CUDA(c, cudaGetLastError());
+    return 0;
+  }
   if (kind == HOFV_PC_AJ64) {
     if (c->dim == 2)
-      cg_run<double, 2>(c, c->d_aj_diag, c->d_aj_off, c->d_cg64, iters, v, z);
+      cg_run<double, 2>(c, c->d_aj_diag, c->d_aj_invd, c->d_aj_off, c->d_cg64, iters, v, z);
     else
-      cg_run<double, 3>(c, c->d_aj_diag, c->d_aj_off, c->d_cg64, iters, v, z);
+      cg_run<double, 3>(c, c->d_aj_diag, c->d_aj_invd, c->d_aj_off, c->d_cg64, iters, v, z);
   } else {
     if (c->dim == 2)
-      cg_run<float, 2>(c, c->d_aj_diag32, c->d_aj_off32, c->d_cg32, iters, v, z);
+      cg_run<float, 2>(c, c->d_aj_diag32, c->d_aj_invd32, c->d_aj_off32, c->d_cg32, iters, v, z);
     else
-      cg_run<float, 3>(c, c->d_aj_diag32, c->d_aj_off32, c->d_cg32, iters, v, z);
+      cg_run<float, 3>(c, c->d_aj_diag32, c->d_aj_invd32, c->d_aj_off32, c->d_cg32, iters, v, z);
   }
   HOFV_CUDA(c, cudaGetLastError());
   return 0;

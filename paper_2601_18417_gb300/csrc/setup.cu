@@ -507,7 +507,8 @@ __global__ void k_face_aux(int dim, int nlf, int64_t nfid, int64_t nfi,
 __global__ void k_aj_rows(int nlf, int64_t nc, const int32_t* __restrict__ cface,
                           const int32_t* __restrict__ fown, const int32_t* __restrict__ fnei,
                           int64_t nfi, const double* __restrict__ fstab, double* diag,
-                          int32_t* col, double* off, float* diag32, float* off32) {
+                          int32_t* col, double* off, float* diag32, float* off32, double* invd,
+                          float* invd32) {
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= nc) return;
   double dg = 0.0;
@@ -530,6 +531,8 @@ __global__ void k_aj_rows(int nlf, int64_t nc, const int32_t* __restrict__ cface
   }
   diag[c] = dg;
   diag32[c] = (float)dg;
+  invd[c] = -1.0 / dg;
+  invd32[c] = (float)(-1.0 / dg);
 }
 
 int run_face_aux(hofv_ctx* c) {
@@ -542,7 +545,7 @@ int run_face_aux(hofv_ctx* c) {
   }
   k_aj_rows<<<(unsigned)((c->nc + T - 1) / T), T, 0, c->stream>>>(
       c->nlf, c->nc, c->d_cface, c->d_fown, c->d_fnei, c->nfi, c->d_fstab, c->d_aj_diag,
-      c->d_aj_col, c->d_aj_off, c->d_aj_diag32, c->d_aj_off32);
+      c->d_aj_col, c->d_aj_off, c->d_aj_diag32, c->d_aj_off32, c->d_aj_invd, c->d_aj_invd32);
   HOFV_CUDA(c, cudaGetLastError());
   HOFV_CUDA(c, cudaStreamSynchronize(c->stream));
   return 0;
