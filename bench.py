@@ -320,15 +320,58 @@ def run_hofv(args):
         e2e_s = (time.perf_counter() - t0) / reps
         e2e = {"value": nc / e2e_s / 1e6, "unit": "Mcell/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
-    launches = 2 * INNER_ITERS + 2 + 1 + 6 + 4 + 2
-    solve = None
-    if rank == 0 and not args.no_solve:
-        solve = {}
-        for name_, kind in (("plain_fp64_aj", hofv.PC_AJ64), ("fp32_aj", hofv.PC_AJ32)):
+    # the linear law in contracted form (law and quadrature folded into one
+    # d x d matrix per face and stencil cell), same step and solve
+    contracted = None
+    if rank == 0 and wl.law == 0:
+        ctx.set_contraction(True)
+        kc = np.array([ctx.residual_timed(u, Ru) for _ in range(max(args.steps // 10, 10))])
+        for _ in range(3):
+            step()
+        torch.cuda.synchronize()
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record(s)
+        for _ in range(args.steps):
+            step()
+        c1.record(s)
+        torch.cuda.synchronize()
+        cms = c0.elapsed_time(c1) / args.steps
+        tf_ms = float(kc[:, 1].mean())
+        d_, S_ = wl.dim, lay.stencil
+        nfid = lay.n_internal + lay.n_disp
+        t_flops = 2.0 * nfid * S_ * d_ * d_
+        t_bytes = nfid * (8 * S_ * d_ * d_ + 4 * S_ + 16 + 24 * d_) + 8 * d_ * lay.n_cells
+        contracted = {"step_ms": cms, "value": nc / (cms * 1e-3) / 1e6,
+                      "residual_ms": float(kc.sum(axis=1).mean()),
+                      "residual_mcells": nc / (float(kc.sum(axis=1).mean()) * 1e-3) / 1e6,
+                      "tflux_ms": tf_ms, "tflux_tflops": t_flops / (tf_ms * 1e-3) / 1e12,
+                      "tflux_fp64_frac": t_flops / (tf_ms * 1e-3) / 1e12 / fp64_peak,
+                      "tflux_hbm_gbs": t_bytes / (tf_ms * 1e-3) / 1e9,
+                      "tflux_hbm_frac": t_bytes / (tf_ms * 1e-3) / 1e9 / pk["hbm_gbs"]}
+        if not args.no_solve:
             uu = torch.zeros_like(u)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            st = ctx.newton_solve(uu, rtol=1e-8, precond=kind, inner_iters=INNER_ITERS,
+            st = ctx.newton_solve(uu, rtol=1e-8, precond=hofv.PC_AJ32, inner_iters=40,
+                                  restart=30, max_krylov=3000)
+            torch.cuda.synchronize()
+            contracted["solve_fp32_aj_inner40"] = {
+                "seconds": time.perf_counter() - t0, "status": st["status"],
+                "newton": st["newton_iters"], "krylov": st["krylov_iters"]}
+        ctx.set_contraction(False)
+    # per step: persistent AJ CG (1) + norm (1) + Jv (norm, eps, axpy, 3 residual kernels)
+    # + CGS2 (2 multi-dots, 2 multi-axpys) + norm + scale
+    launches = 1 + 1 + 6 + 4 + 2
+    solve = None
+    if rank == 0 and not args.no_solve:
+        solve = {}
+        for name_, kind, inner in (("plain_fp64_aj", hofv.PC_AJ64, INNER_ITERS),
+                                   ("fp32_aj", hofv.PC_AJ32, INNER_ITERS),
+                                   ("fp32_aj_inner40", hofv.PC_AJ32, 40)):
+            uu = torch.zeros_like(u)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st = ctx.newton_solve(uu, rtol=1e-8, precond=kind, inner_iters=inner,
                                   restart=30, max_krylov=3000)
             torch.cuda.synchronize()
             dt = time.perf_counter() - t0
@@ -359,7 +402,7 @@ def run_hofv(args):
                            "parallelism": "replicas" if ws > 1 else "single GPU"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches * args.steps, "clocks": clocks,
-                "setup_s": setup_s, "solve": solve, "impl": "hofv"}
+                "setup_s": setup_s, "solve": solve, "contracted": contracted, "impl": "hofv"}
         print(json.dumps(line))
     ctx.close()
     if ws > 1:

@@ -175,6 +175,16 @@ int hofv_get_points(hofv_ctx* ctx, int kind, double* out);
    Kbar = 2 mu + lambda in both laws (Sec. 3.4). */
 int hofv_set_material(hofv_ctx* ctx, int law, double mu, double lambda);
 
+/* Evaluate the linear-elastic flux in contracted form (on = 1) or per Gauss
+   point (on = 0, default).  With Hooke's law the traction of a face is linear
+   in the stencil values, so the law and the Gauss quadrature of
+   eq. divStressDiscret fold exactly into one d x d matrix per face and
+   stencil cell, T_N = sum_q mu c_qN (x) a_q + mu (c_qN . a_q) I +
+   lambda a_q (x) c_qN, built when the material is set (extra device memory:
+   |S| d^2 doubles per face).  Results equal the per-point form up to
+   rounding; the neo-Hookean law always uses the per-point form. */
+int hofv_set_contraction(hofv_ctx* ctx, int on);
+
 /* Boundary data and sources, DEVICE arrays copied into the context (any may
    be NULL = zero):
      u_bq  [n_disp][Q][dim]  prescribed displacement at displacement-face Gauss points

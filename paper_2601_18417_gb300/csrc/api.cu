@@ -12,6 +12,12 @@
 
 #include "hofv_internal.cuh"
 
+#define TRY(x)                 \
+  do {                         \
+    int rc_ = (x);             \
+    if (rc_ != 0) return rc_;  \
+  } while (0)
+
 namespace hofv {
 
 int fail(hofv_ctx* c, int code, const std::string& msg) {
@@ -54,6 +60,7 @@ DevMesh dev_mesh(const hofv_ctx* c) {
   m.cst = c->d_cst;
   m.cex = c->d_cex;
   m.cface = c->d_cface;
+  m.tco = (c->contract && c->tco_valid && c->mat.law == HOFV_LAW_LINEAR) ? c->d_tco : nullptr;
   return m;
 }
 
@@ -99,6 +106,8 @@ static void free_built(hofv_ctx* c) {
   c->d_fst = c->d_cst = c->d_fstar = c->d_cface = nullptr;
   c->d_fco = c->d_gco = c->d_cex = c->d_fstab = nullptr;
   c->d_ubq = c->d_ubf = c->d_tbq = c->d_body = c->d_src = nullptr;
+  c->d_tco = c->d_gflux = nullptr;
+  c->tco_valid = false;
   c->d_ustar = c->d_flux = c->d_w = c->d_red = c->d_scal = nullptr;
   c->d_count = nullptr;
   c->d_aj_diag = c->d_aj_off = nullptr;
@@ -114,11 +123,46 @@ static void free_built(hofv_ctx* c) {
   c->built = false;
 }
 
+// contracted linear-elastic face matrices for the current material
+static int build_contraction(hofv_ctx* c) {
+  if (!c->contract || !c->have_mat || c->mat.law != HOFV_LAW_LINEAR || !c->built) return 0;
+  const int64_t count = std::max<int64_t>(c->nftile, 1) * c->S * kTile * c->dim * c->dim;
+  if (!c->d_tco) TRY(dev_alloc(c, &c->d_tco, count));
+  if (!c->d_gflux) TRY(dev_alloc(c, &c->d_gflux, std::max<int64_t>(c->nfd, 1) * c->dim));
+  DevMesh m = dev_mesh(c);
+  launch_build_tco(m, c->mat.mu, c->mat.lam, c->d_tco, c->stream);
+  HOFV_CUDA(c, cudaGetLastError());
+  HOFV_CUDA(c, cudaStreamSynchronize(c->stream));
+  c->tco_valid = true;
+  return 0;
+}
+
+int refresh_source(hofv_ctx* c) {
+  if (!c->built) return 0;
+  if (c->contract && c->tco_valid && c->have_mat && c->mat.law == HOFV_LAW_LINEAR)
+    launch_ghost_flux(dev_mesh(c), c->mat.mu, c->mat.lam, c->d_ubq, c->d_gflux, c->stream);
+  launch_source(c, c->stream);
+  HOFV_CUDA(c, cudaGetLastError());
+  HOFV_CUDA(c, cudaStreamSynchronize(c->stream));
+  return 0;
+}
+
 }  // namespace hofv
 
 using namespace hofv;
 
 extern "C" {
+
+int hofv_set_contraction(hofv_ctx* c, int on) {
+  if (!c) return HOFV_EINVAL;
+  c->contract = on != 0;
+  if (!c->contract) {
+    c->tco_valid = false;
+    return refresh_source(c);
+  }
+  TRY(build_contraction(c));
+  return refresh_source(c);
+}
 
 const char* hofv_version(void) { return "hofv 0.1 (sm_103a)"; }
 
@@ -295,11 +339,6 @@ int hofv_set_scheme(hofv_ctx* c, int p, int n_plus, int q1, double k_weight, dou
   return HOFV_OK;
 }
 
-#define TRY(x)                 \
-  do {                         \
-    int rc_ = (x);             \
-    if (rc_ != 0) return rc_;  \
-  } while (0)
 
 int hofv_build_stencils(hofv_ctx* c) {
   if (!c) return HOFV_EINVAL;
@@ -452,6 +491,8 @@ int hofv_build_stencils(hofv_ctx* c) {
   HOFV_CUDA(c, cudaDeviceSynchronize());
   c->src_dirty = false;
   c->built = true;
+  c->tco_valid = false;
+  TRY(build_contraction(c));
   c->setup_seconds =
       std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   return HOFV_OK;
@@ -539,6 +580,11 @@ int hofv_set_material(hofv_ctx* c, int law, double mu, double lambda) {
   c->mat.kbar = 2.0 * mu + lambda;
   c->mat.alpha = c->alpha;
   c->have_mat = true;
+  c->tco_valid = false;
+  if (c->built) {
+    TRY(build_contraction(c));
+    TRY(refresh_source(c));
+  }
   return HOFV_OK;
 }
 
@@ -559,9 +605,7 @@ int hofv_set_bc(hofv_ctx* c, const double* ubq, const double* ubf, const double*
   TRY(put(c->d_ubf, ubf, c->nfd * d));
   TRY(put(c->d_tbq, tbq, c->nft * c->Q * d));
   TRY(put(c->d_body, body, c->nc * d));
-  launch_source(c, c->stream);
-  HOFV_CUDA(c, cudaGetLastError());
-  HOFV_CUDA(c, cudaStreamSynchronize(c->stream));
+  TRY(refresh_source(c));
   return HOFV_OK;
 }
 

@@ -37,6 +37,8 @@ struct DevMesh {
   const int32_t* cst;     // [nctile][S][kTile]
   const double* cex;      // [nctile][S][kTile][nlf]
   const int32_t* cface;   // [nc][nlf]  +(f+1) owner, -(f+1) neighbour, 0 traction
+  const double* tco;      // [nftile][S][kTile][dim][dim] contracted linear-elastic
+                          // face matrices, or nullptr (then the per-point form is used)
 };
 
 struct Material {
@@ -98,6 +100,11 @@ struct hofv_ctx {
   double* d_tbq = nullptr;          // [nft][Q][dim]
   double* d_body = nullptr;         // [dim][nc]
   double* d_src = nullptr;          // [dim][nc]  body + traction-face fluxes
+  // contracted linear-elastic form (per face and stencil cell d x d matrices)
+  bool contract = false;            // requested by the caller
+  bool tco_valid = false;           // d_tco holds the matrices for the current mu, lambda
+  double* d_tco = nullptr;
+  double* d_gflux = nullptr;        // [nfd][dim] ghost-node flux (constant per load step)
   bool src_dirty = true;
   // ---- scratch for the residual ----
   double* d_ustar = nullptr;        // [nc][nlf][dim]
@@ -177,6 +184,14 @@ void launch_residual(const DevMesh& m, const Material& mat, const double* u, con
                      double* flux, const double* ubq, const double* ubf, const double* src,
                      cudaStream_t st, cudaEvent_t* ev = nullptr);
 void launch_source(const hofv_ctx* c, cudaStream_t st);
+void launch_build_tco(const DevMesh& m, double mu, double lam, double* tco, cudaStream_t st);
+void launch_ghost_flux(const DevMesh& m, double mu, double lam, const double* ubq, double* gflux,
+                       cudaStream_t st);
+void launch_tflux(const DevMesh& m, const double* tco, double alpha_kbar, const double* w,
+                  const double* ustar, const double* ubf, double* flux, cudaStream_t st);
+// recompute the constant cell source (body, traction faces and, for the
+// contracted linear form, the ghost-node fluxes)
+int refresh_source(hofv_ctx* c);
 // out[cell] = sum over the cell's internal/displacement faces of |flux_f|
 void launch_flux_scale(const DevMesh& m, const double* flux, double* out, cudaStream_t st);
 

@@ -240,6 +240,12 @@ __global__ void k_cell(DevMesh m, const double* __restrict__ flux, const double*
   }
 }
 
+template <int DIM>
+__global__ void __launch_bounds__(32 * DIM)
+    k_tflux(DevMesh m, const double* __restrict__ tco, double alpha_kbar,
+            const double* __restrict__ w, const double* __restrict__ ustar,
+            const double* __restrict__ ubf, double* __restrict__ flux);
+
 template <int DIM, int LAW>
 static void residual_impl(const DevMesh& m, const Material& mat, const double* w,
                           const double* d_eps, const double* R0, double* out, double* ustar,
@@ -249,8 +255,14 @@ static void residual_impl(const DevMesh& m, const Material& mat, const double* w
   k_ustar<DIM><<<(unsigned)m.nctile, 32 * 2 * DIM, 0, st>>>(m, w, ustar);
   if (ev) cudaEventRecord(ev[1], st);
   if (m.nftile > 0) {
-    const size_t smem = sizeof(double) * kTile * (m.R * DIM + m.Q * DIM);
-    k_flux<DIM, LAW><<<(unsigned)m.nftile, kTile * m.R, smem, st>>>(m, mat, w, ustar, ubq, ubf, flux);
+    if (LAW == HOFV_LAW_LINEAR && m.tco) {
+      k_tflux<DIM><<<(unsigned)m.nftile, 32 * DIM, 0, st>>>(m, m.tco, mat.alpha * mat.kbar, w,
+                                                            ustar, ubf, flux);
+    } else {
+      const size_t smem = sizeof(double) * kTile * (m.R * DIM + m.Q * DIM);
+      k_flux<DIM, LAW><<<(unsigned)m.nftile, kTile * m.R, smem, st>>>(m, mat, w, ustar, ubq, ubf,
+                                                                      flux);
+    }
   }
   if (ev) cudaEventRecord(ev[2], st);
   k_cell<DIM><<<(unsigned)((m.nc + 255) / 256), 256, 0, st>>>(m, flux, src, R0, d_eps, out);
@@ -281,11 +293,17 @@ void launch_residual(const DevMesh& m, const Material& mat, const double* w, con
 __global__ void k_source(int dim, int nlf, int Q, int64_t nc, int64_t nfi, int64_t nfd,
                          const int64_t* __restrict__ cf, const int32_t* __restrict__ ftag,
                          const double* __restrict__ aq, const double* __restrict__ tbq,
-                         const double* __restrict__ body, double* __restrict__ src) {
+                         const double* __restrict__ body, const double* __restrict__ gflux,
+                         double* __restrict__ src) {
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= nc) return;
   for (int j = 0; j < dim; ++j) {
     double s = body ? body[j * nc + c] : 0.0;
+    if (gflux)
+      for (int lf = 0; lf < nlf; ++lf) {
+        const int64_t f = cf[c * nlf + lf];
+        if (ftag[f] == 0) s += gflux[(f - nfi) * dim + j];
+      }
     if (tbq) {
       for (int lf = 0; lf < nlf; ++lf) {
         const int64_t f = cf[c * nlf + lf];
@@ -305,7 +323,10 @@ __global__ void k_source(int dim, int nlf, int Q, int64_t nc, int64_t nfi, int64
 void launch_source(const hofv_ctx* c, cudaStream_t st) {
   k_source<<<(unsigned)((c->nc + 127) / 128), 128, 0, st>>>(
       c->dim, c->nlf, c->Q, c->nc, c->nfi, c->nfd, c->d_cf, c->d_ftag, c->d_aq,
-      c->nft > 0 ? c->d_tbq : nullptr, c->d_body, c->d_src);
+      c->nft > 0 ? c->d_tbq : nullptr, c->d_body,
+      (c->contract && c->tco_valid && c->mat.law == HOFV_LAW_LINEAR && c->nfd > 0) ? c->d_gflux
+                                                                                  : nullptr,
+      c->d_src);
 }
 
 }  // namespace hofv
@@ -338,4 +359,141 @@ void launch_flux_scale(const DevMesh& m, const double* flux, double* out, cudaSt
   else
     k_flux_scale<3><<<(unsigned)((m.nc + 255) / 256), 256, 0, st>>>(m, flux, out);
 }
+}  // namespace hofv
+
+// ---------------------------------------------------------------------
+// Linear elasticity with the law and the face quadrature folded into the
+// coefficients (an exact re-association of eq. divStressDiscret for Hooke's
+// law): with sigma = mu (G + G^T) + lambda tr(G) I and G = sum_N c_N (x) u_N,
+//   flux_i = sum_N sum_k T_N[i][k] u_N[k],
+//   T_N[i][k] = sum_q mu c_qN,i a_q,k + mu (c_qN . a_q) delta_ik + lambda a_q,i c_qN,k.
+// One d x d matrix per face and stencil cell replaces Q d coefficients and
+// the per-point law: d^2 FMAs per cell instead of Q d^2.  The ghost node of
+// a displacement face only multiplies prescribed data, so its part is a
+// constant folded into the cell source.
+// ---------------------------------------------------------------------
+namespace hofv {
+
+// tco[tile][N][fi][i][k] from fco[tile][N][fi][q*d + i] and aq
+template <int DIM>
+__global__ void k_build_tco(DevMesh m, double mu, double lam, double* __restrict__ tco) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;  // (tile, N, fi)
+  const int64_t total = m.nftile * m.S * kTile;
+  if (e >= total) return;
+  const int fi = (int)(e % kTile);
+  const int64_t tile = e / ((int64_t)m.S * kTile);
+  const int64_t f = tile * kTile + fi;
+  double T[DIM][DIM];
+#pragma unroll
+  for (int i = 0; i < DIM; ++i)
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) T[i][k] = 0.0;
+  if (f < m.nfid) {
+    const double* co = m.fco + e * m.R;
+    for (int q = 0; q < m.Q; ++q) {
+      double c[DIM], a[DIM], ca = 0.0;
+#pragma unroll
+      for (int i = 0; i < DIM; ++i) {
+        c[i] = co[q * DIM + i];
+        a[i] = m.aq[(f * m.Q + q) * 3 + i];
+        ca += c[i] * a[i];
+      }
+#pragma unroll
+      for (int i = 0; i < DIM; ++i)
+#pragma unroll
+        for (int k = 0; k < DIM; ++k)
+          T[i][k] += mu * c[i] * a[k] + lam * a[i] * c[k] + (i == k ? mu * ca : 0.0);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < DIM; ++i)
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) tco[(e * DIM + i) * DIM + k] = T[i][k];
+}
+
+// ghost-node flux of each displacement face: sum_q Tg_q u_bq (constant data)
+template <int DIM>
+__global__ void k_ghost_flux(DevMesh m, double mu, double lam, const double* __restrict__ ubq,
+                             double* __restrict__ gflux) {
+  const int64_t fd = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (fd >= m.nfd) return;
+  const int64_t f = m.nfi + fd;
+  double out[DIM];
+#pragma unroll
+  for (int i = 0; i < DIM; ++i) out[i] = 0.0;
+  for (int q = 0; q < m.Q; ++q) {
+    double c[DIM], a[DIM], u[DIM], ca = 0.0, cu = 0.0, au = 0.0;
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) {
+      c[i] = m.gco[fd * m.R + q * DIM + i];
+      a[i] = m.aq[(f * m.Q + q) * 3 + i];
+      u[i] = ubq[(fd * m.Q + q) * DIM + i];
+      ca += c[i] * a[i];
+      cu += c[i] * u[i];
+      au += a[i] * u[i];
+    }
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) out[i] += mu * c[i] * au + mu * ca * u[i] + lam * a[i] * cu;
+  }
+#pragma unroll
+  for (int i = 0; i < DIM; ++i) gflux[fd * DIM + i] = out[i];
+}
+
+// face fluxes from the contracted matrices: thread (face, row i), 32 faces
+// per block; every FP64 instruction runs with full warps (32 d threads)
+template <int DIM>
+__global__ void __launch_bounds__(32 * DIM)
+    k_tflux(DevMesh m, const double* __restrict__ tco, double alpha_kbar,
+            const double* __restrict__ w, const double* __restrict__ ustar,
+            const double* __restrict__ ubf, double* __restrict__ flux) {
+  const int64_t tile = blockIdx.x;
+  const int it = threadIdx.x;  // fi * DIM + i
+  const int fi = it / DIM, i = it % DIM;
+  const int64_t f = tile * kTile + fi;
+  const int S = m.S;
+  const int64_t nc = m.nc;
+  const int32_t* __restrict__ st = m.fst + tile * S * kTile + fi;
+  const double* __restrict__ tc = tco + tile * (int64_t)S * kTile * DIM * DIM + it * DIM;
+  double acc = 0.0;
+#pragma unroll 4
+  for (int n = 0; n < S; ++n) {
+    const int32_t id = __ldg(st + n * kTile);
+    const double* t = tc + (int64_t)n * kTile * DIM * DIM;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) acc = fma(__ldg(t + k), __ldg(w + k * nc + id), acc);
+  }
+  if (f < m.nfid) {
+    const int32_t sp = m.fstar[2 * f], sn = m.fstar[2 * f + 1];
+    const double other = sn >= 0 ? ustar[(int64_t)sn * DIM + i] : ubf[(f - m.nfi) * DIM + i];
+    flux[f * DIM + i] = fma(alpha_kbar * m.fstab[f], other - ustar[(int64_t)sp * DIM + i], acc);
+  }
+}
+
+void launch_build_tco(const DevMesh& m, double mu, double lam, double* tco, cudaStream_t st) {
+  const int64_t total = m.nftile * m.S * kTile;
+  if (total == 0) return;
+  if (m.dim == 2)
+    k_build_tco<2><<<(unsigned)((total + 127) / 128), 128, 0, st>>>(m, mu, lam, tco);
+  else
+    k_build_tco<3><<<(unsigned)((total + 127) / 128), 128, 0, st>>>(m, mu, lam, tco);
+}
+
+void launch_ghost_flux(const DevMesh& m, double mu, double lam, const double* ubq, double* gflux,
+                       cudaStream_t st) {
+  if (m.nfd == 0) return;
+  if (m.dim == 2)
+    k_ghost_flux<2><<<(unsigned)((m.nfd + 127) / 128), 128, 0, st>>>(m, mu, lam, ubq, gflux);
+  else
+    k_ghost_flux<3><<<(unsigned)((m.nfd + 127) / 128), 128, 0, st>>>(m, mu, lam, ubq, gflux);
+}
+
+void launch_tflux(const DevMesh& m, const double* tco, double alpha_kbar, const double* w,
+                  const double* ustar, const double* ubf, double* flux, cudaStream_t st) {
+  if (m.nftile == 0) return;
+  if (m.dim == 2)
+    k_tflux<2><<<(unsigned)m.nftile, 32 * 2, 0, st>>>(m, tco, alpha_kbar, w, ustar, ubf, flux);
+  else
+    k_tflux<3><<<(unsigned)m.nftile, 32 * 3, 0, st>>>(m, tco, alpha_kbar, w, ustar, ubf, flux);
+}
+
 }  // namespace hofv

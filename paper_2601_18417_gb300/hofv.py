@@ -100,6 +100,7 @@ SIGNATURES = {
     "hofv_residual_timed": (_I, [_P, _P, _P, _P]),
     "hofv_residual_noalloc": (_I, [_P, _P, _P]),
     "hofv_force_scale": (_I, [_P, _P, C.POINTER(_D)]),
+    "hofv_set_contraction": (_I, [_P, _I]),
     "hofv_gnn_init": (_I, [_P, C.c_uint64, _D]),
     "hofv_gnn_num_params": (_I, [_P, C.POINTER(_I64)]),
     "hofv_gnn_get_params": (_I, [_P, _P, _I64]),
@@ -220,6 +221,9 @@ class Context:
 
     def set_material(self, law, mu, lam):
         return self._check(self._L.hofv_set_material(self.h, law, mu, lam))
+
+    def set_contraction(self, on=True):
+        return self._check(self._L.hofv_set_contraction(self.h, int(bool(on))))
 
     def set_bc(self, u_bq=None, u_bf=None, t_bq=None, body=None):
         args = [_dev(t) for t in (u_bq, u_bf, t_bq, body)]

@@ -218,3 +218,54 @@ def test_newton_solution_matches_oracle_direct_solve(name):
     ug = u.cpu().numpy()
     rel = np.linalg.norm(ug - u_orc) / np.linalg.norm(u_orc)
     assert rel < 1e-8, (rel, st)
+
+
+@pytest.mark.parametrize("name", ["quad-p2", "quad-p3-jit", "quad-p3-block", "hex-p3", "hex-p1-jit"])
+def test_contracted_linear_residual_parity(name):
+    """Linear law with the quadrature and law folded into per-cell face
+    matrices: same residual as the oracle's per-point form (1e-12 F_s), incl.
+    the displacement-face ghost node (constant source) and traction faces."""
+    import torch
+    pb, ctx = problem(name)
+    ctx.set_contraction(True)
+    try:
+        for seed in (0, 1):
+            u = smooth_u(pb, seed, amp=1.0)
+            R_orc = H.residual(pb, u)
+            ud = H.to_dev(u)
+            Rd = torch.empty_like(ud)
+            ctx.residual(ud, Rd)
+            torch.cuda.synchronize()
+            err = np.abs(Rd.cpu().numpy() - R_orc).max()
+            assert err <= 1e-12 * _fs(pb, u), (err, _fs(pb, u))
+        # a new material rebuilds the matrices
+        ctx.set_material(0, 2.0 * pb.mu, 0.5 * pb.lam)
+        u = smooth_u(pb, 2, amp=1.0)
+        R_orc = pb.orc.residual(0, 2.0 * pb.mu, 0.5 * pb.lam, u, pb.ubq, pb.ubf, pb.tbq, pb.body)
+        ud = H.to_dev(u)
+        Rd = torch.empty_like(ud)
+        ctx.residual(ud, Rd)
+        torch.cuda.synchronize()
+        Fs = H.force_scale(pb.orc, 0, 2.0 * pb.mu, 0.5 * pb.lam, u, pb.ubq, pb.ubf, pb.tbq)
+        assert np.abs(Rd.cpu().numpy() - R_orc).max() <= 1e-12 * Fs
+    finally:
+        ctx.set_material(pb.law, pb.mu, pb.lam)
+        ctx.set_contraction(False)
+
+
+def test_contracted_newton_matches_oracle_direct_solve():
+    import scipy.sparse.linalg as spla
+    import torch
+    pb, ctx = problem("quad-p3-jit")
+    J, R0 = H.probe_jacobian(pb)
+    u_orc = spla.spsolve(J.tocsc(), -R0.ravel()).reshape(pb.dim, -1)
+    ctx.set_contraction(True)
+    try:
+        u = torch.zeros((pb.dim, pb.orc.nc), dtype=torch.float64, device="cuda:0")
+        st = ctx.newton_solve(u, rtol=1e-12, max_newton=6, restart=60, max_krylov=2000,
+                              precond=hofv.PC_AJ32, inner_iters=40)
+        assert st["status"] == 0, st
+        rel = np.linalg.norm(u.cpu().numpy() - u_orc) / np.linalg.norm(u_orc)
+        assert rel < 1e-8, rel
+    finally:
+        ctx.set_contraction(False)
