@@ -51,13 +51,17 @@ def dist_env():
 
 def measured_traffic(workload):
     """DRAM bytes per k_flux launch from the committed ncu capture, or None
-    when the face-flux source changed since the capture."""
+    when the face-flux kernel's source (the law and the kernel) changed since
+    the capture."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "ncu_k_flux_traffic.txt")
     src = os.path.join(ROOT, "paper_2601_18417_gb300", "csrc", "residual.cu")
     if not os.path.exists(path):
         return None
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    text = open(src).read()
+    lo = text.find("// laws: traction t = T a")
+    hi = text.find("// cell assembly")
+    h = hashlib.sha256(text[lo:hi].encode()).hexdigest()[:16]
     for line in open(path):
         parts = line.split()
         if len(parts) == 3 and not line.startswith("#") and parts[0] == workload:
