@@ -499,8 +499,10 @@ def run_learned(args):
         sols = {}
         variants = (("plain_fp64_aj", hofv.PC_AJ64, 1, steps), ("fp32_aj", hofv.PC_AJ32, 1, steps),
                     ("learned", hofv.PC_GNN, 1, steps),
-                    ("learned_no_judge", hofv.PC_GNN, 0, min(steps, 2)))
+                    ("learned_no_judge", hofv.PC_GNN, 0, min(steps, 2) if name == held.name else 0))
         for label, pc, judge, nsteps in variants:
+            if nsteps == 0:
+                continue
             if time.perf_counter() - t_start > args.budget_s:
                 res[label] = {"skipped": "time budget"}
                 continue
