@@ -49,6 +49,21 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(ms, device=None):
+    """Step time of the slowest rank (all ranks get it)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(cells_per_rank, world_size, ms_max):
+    """Whole-job throughput of independent replicas (weak scaling): all
+    ranks' cells per second at the slowest rank's step time, in Mcell/s."""
+    return world_size * cells_per_rank / (ms_max * 1e-3) / 1e6
+
+
 def measured_traffic(workload):
     """DRAM bytes per k_flux launch from the committed ncu capture, or None
     when the face-flux kernel's source (the law and the kernel) changed since
@@ -280,11 +295,8 @@ def run_hofv(args):
         kt.append(ctx.residual_timed(u, Ru))
     clocks = clk.stop() if clk else None
     if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = ws * nc / (ms * 1e-3) / 1e6
+        ms = max_over_ranks(ms, dev)
+    value = replica_value(nc, ws, ms)
     kt = np.array(kt)
     flux_ms = float(kt[:, 1].mean())
     res_ms = float(kt.sum(axis=1).mean())
