@@ -319,6 +319,15 @@ int hofv_arnoldi_step(hofv_ctx* ctx, const double* u, const double* Ru, int kind
    before any stream capture.  u, R: DEVICE [dim][n_cells]. */
 int hofv_residual_noalloc(hofv_ctx* ctx, const double* u, double* R);
 
+/* Self-test of the bounded waits: the approximate-Jacobian solve runs as one
+   cooperative launch whose blocks meet at grid barriers; each wait gives up
+   after a bounded number of polls, latches an error flag and returns, and
+   the host reports HOFV_ECUDA at its next synchronisation.  This launches
+   two blocks that wait for a third arrival that never comes; on return
+   *timed_out (HOST) is 1 when the wait ran out and was latched, and the
+   flag has been cleared so the context stays usable.  Synchronises. */
+int hofv_selftest_barrier(hofv_ctx* ctx, int32_t* timed_out);
+
 /* hofv_residual with each of its three kernels timed by CUDA events on the
    context stream: ms[0] stabilisation extrapolation (cell-ordered), ms[1]
    face fluxes, ms[2] cell assembly (HOST array of 3).  Synchronises. */

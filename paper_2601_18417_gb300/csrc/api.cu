@@ -1192,3 +1192,11 @@ int check_pc_barrier(hofv_ctx* c) {
   return 0;
 }
 }  // namespace hofv
+
+extern "C" int hofv_selftest_barrier(hofv_ctx* c, int32_t* timed_out) {
+  if (!c || !timed_out) return HOFV_EINVAL;
+  int t = 0;
+  TRY(barrier_selftest(c, &t));
+  *timed_out = t;
+  return HOFV_OK;
+}

@@ -217,6 +217,8 @@ int aj_precondition(hofv_ctx* c, int kind, int iters, const double* v, double* z
 // error of a timed-out persistent-CG grid barrier since the last check
 // (reads the flag: call after a stream synchronisation), then clears it
 int check_pc_barrier(hofv_ctx* c);
+// bounded-wait self-test of the grid barrier (see hofv_selftest_barrier)
+int barrier_selftest(hofv_ctx* c, int* timed_out);
 
 // ---- learned preconditioner (gnn.cu) ----
 int gnn_apply(hofv_ctx* c, const double* v, const double* z_aj, double* z);

@@ -10,76 +10,11 @@
 #include <stdlib.h>
 
 #include "hofv_internal.cuh"
+#include "reduce.cuh"
 
 namespace hofv {
 
 constexpr int kRedThreads = 256;
-
-__device__ __forceinline__ double block_sum(double v, double* sh) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0) sh[wid] = v;
-  __syncthreads();
-  double s = 0.0;
-  if (threadIdx.x == 0) {
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += sh[i];
-  }
-  __syncthreads();
-  return s;  // valid in thread 0
-}
-
-// Block sum in the precision of the values (FP32 stays on the FP32 pipe);
-// the per-warp results are added by warp 0 in double.  Valid in thread 0.
-// FP64 warp instructions cost 16 cycles of the SM's FP64 pipe on this GPU,
-// so FP64 reductions are kept to one warp wherever possible.
-template <typename T>
-__device__ __forceinline__ double block_sum_t(T v, double* sh) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0) sh[wid] = (double)v;
-  __syncthreads();
-  double s = 0.0;
-  if (wid == 0) {
-    s = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  }
-  __syncthreads();
-  return s;
-}
-
-// Sum of partials red[0..nb) by warp 0 of the block (fixed order: lane l adds
-// partials l, l+32, ..., then a fixed shuffle tree), accumulated in A.
-// Valid in thread 0.
-template <typename A = double>
-__device__ __forceinline__ double warp0_sum(const double* red, unsigned int nb) {
-  A s = (A)0;
-  if (threadIdx.x < 32) {
-    for (unsigned int b = threadIdx.x; b < nb; b += 32) s += (A)__ldcg(red + b);
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  }
-  return (double)s;
-}
-
-// Returns true in thread 0 of the block that finished last.
-__device__ __forceinline__ bool last_block(unsigned int* count, unsigned int nblocks) {
-  __shared__ bool is_last;
-  __threadfence();
-  if (threadIdx.x == 0) {
-    const unsigned int t = atomicAdd(count, 1u);
-    is_last = (t == nblocks - 1);
-  }
-  __syncthreads();
-  return is_last;
-}
-
-// Sum of partials red[0..nb) by the whole (last) block: thread t adds
-// partials t, t + blockDim, ... in order, then a fixed-shape tree.  The
-// result (valid in thread 0) does not depend on which block finished last.
-__device__ __forceinline__ double final_sum(const double* red, unsigned int nb, double* sh) {
-  double s = 0.0;
-  for (unsigned int b = threadIdx.x; b < nb; b += blockDim.x) s += __ldcg(red + b);
-  return block_sum(s, sh);
-}
 
 // out[k] = x_k . y for k = blockIdx.y; x_k = X + k * ldx
 __global__ void k_mdot(const double* __restrict__ X, int64_t ldx, const double* __restrict__ y,
@@ -398,7 +333,8 @@ struct GridBarrier {
   int* err;
 };
 
-__device__ __forceinline__ bool grid_barrier(const GridBarrier& gb, unsigned int nblocks) {
+__device__ __forceinline__ bool grid_barrier(const GridBarrier& gb, unsigned int nblocks,
+                                             unsigned int spin_limit = kBarrierSpinLimit) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -414,7 +350,7 @@ __device__ __forceinline__ bool grid_barrier(const GridBarrier& gb, unsigned int
     } else {
       unsigned int spins = 0;
       while (*vgen == g) {
-        if (++spins > kBarrierSpinLimit || *verr) {
+        if (++spins > spin_limit || *verr) {
           ok = 0;
           break;
         }
@@ -646,6 +582,28 @@ static void cg_run(hofv_ctx* c, const T* diag, const T* invd, const T* off, T* w
                                                      s[(i - 1) & 1], x, p, red, cnt, sc);
   k_cg_finish<T, DIM><<<(unsigned)((nc + 255) / 256), 256, 0, st>>>(nc, invd, r[(iters - 1) & 1], x,
                                                                      p, sc, zout);
+}
+
+// Two co-resident blocks wait at a barrier that expects one more arrival
+// than exists: the wait must run out and latch the error flag.
+__global__ void k_barrier_probe(GridBarrier gb, unsigned int spin_limit) {
+  grid_barrier(gb, gridDim.x + 1, spin_limit);
+}
+
+int barrier_selftest(hofv_ctx* c, int* timed_out) {
+  *timed_out = 0;
+  if (!c->d_bar) return fail(c, HOFV_ESTATE, "hofv_build_stencils must come first");
+  GridBarrier gb{c->d_bar, c->d_bar + 1, reinterpret_cast<int*>(c->d_bar + 2)};
+  unsigned int limit = 1u << 14;
+  void* args[] = {&gb, &limit};
+  HOFV_CUDA(c, cudaLaunchCooperativeKernel((const void*)k_barrier_probe, dim3(2), dim3(32), args,
+                                           0, c->stream));
+  HOFV_CUDA(c, cudaStreamSynchronize(c->stream));
+  int err = 0;
+  HOFV_CUDA(c, cudaMemcpy(&err, c->d_bar + 2, sizeof(int), cudaMemcpyDeviceToHost));
+  *timed_out = err != 0;
+  HOFV_CUDA(c, cudaMemset(c->d_bar, 0, 4 * sizeof(unsigned int)));
+  return 0;
 }
 
 int aj_precondition(hofv_ctx* c, int kind, int iters, const double* v, double* z) {

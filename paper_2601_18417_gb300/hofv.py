@@ -101,6 +101,7 @@ SIGNATURES = {
     "hofv_residual_noalloc": (_I, [_P, _P, _P]),
     "hofv_force_scale": (_I, [_P, _P, C.POINTER(_D)]),
     "hofv_set_contraction": (_I, [_P, _I]),
+    "hofv_selftest_barrier": (_I, [_P, C.POINTER(C.c_int32)]),
     "hofv_gnn_init": (_I, [_P, C.c_uint64, _D]),
     "hofv_gnn_num_params": (_I, [_P, C.POINTER(_I64)]),
     "hofv_gnn_get_params": (_I, [_P, _P, _I64]),
@@ -221,6 +222,11 @@ class Context:
 
     def set_material(self, law, mu, lam):
         return self._check(self._L.hofv_set_material(self.h, law, mu, lam))
+
+    def selftest_barrier(self):
+        t = C.c_int32(0)
+        self._check(self._L.hofv_selftest_barrier(self.h, C.byref(t)))
+        return bool(t.value)
 
     def set_contraction(self, on=True):
         return self._check(self._L.hofv_set_contraction(self.h, int(bool(on))))
