@@ -39,7 +39,8 @@ if ROOT not in sys.path:
 
 METRIC = "residual evals/s (Mcell/s, % HBM roofline); JFNK time to 1e-8, learned vs plain"
 KRYLOV_J = 15          # Arnoldi index of the timed step (16 basis vectors)
-INNER_ITERS = 20       # approximate-Jacobian CG iterations per preconditioner apply
+INNER_ITERS = 20       # approximate-Jacobian CG iterations per preconditioner apply (Jacobi CG)
+MG_INNER = 1           # multigrid-preconditioned CG iterations per apply (the timed step)
 
 
 def dist_env():
@@ -268,10 +269,11 @@ def run_hofv(args):
     Z = torch.zeros((J + 1, n), dtype=torch.float64, device=dev)
     v_host = torch.empty(n, dtype=torch.float64).pin_memory()
     v_host.copy_(V[J].cpu())
-    pc = hofv.PC_AJ32
+    pc, inner = hofv.PC_AJMG, MG_INNER
+    mg = ctx.mg_info()  # builds the multigrid hierarchy outside the timed region
 
     def step():
-        ctx.arnoldi_step(u, Ru, pc, INNER_ITERS, V, Z, J)
+        ctx.arnoldi_step(u, Ru, pc, inner, V, Z, J)
 
     for _ in range(args.warmup):
         step()
@@ -289,6 +291,16 @@ def run_hofv(args):
     e1.record(s)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
+    # the same step with the Jacobi-preconditioned CG inner solve, for comparison
+    for _ in range(3):
+        ctx.arnoldi_step(u, Ru, hofv.PC_AJ32, INNER_ITERS, V, Z, J)
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record(s)
+    for _ in range(max(args.steps // 5, 10)):
+        ctx.arnoldi_step(u, Ru, hofv.PC_AJ32, INNER_ITERS, V, Z, J)
+    a1.record(s)
+    torch.cuda.synchronize()
+    ms_jacobi = a0.elapsed_time(a1) / max(args.steps // 5, 10)
     # per-kernel residual timing for the roofline (same stream, CUDA events)
     kt = []
     for _ in range(max(args.steps, 10)):
@@ -368,22 +380,26 @@ def run_hofv(args):
             uu = torch.zeros_like(u)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            st = ctx.newton_solve(uu, rtol=1e-8, precond=hofv.PC_AJ32, inner_iters=40,
+            st = ctx.newton_solve(uu, rtol=1e-8, precond=hofv.PC_AJMG, inner_iters=MG_INNER,
                                   restart=30, max_krylov=3000)
             torch.cuda.synchronize()
-            contracted["solve_fp32_aj_inner40"] = {
+            contracted["solve_fp32_aj_mg"] = {
                 "seconds": time.perf_counter() - t0, "status": st["status"],
                 "newton": st["newton_iters"], "krylov": st["krylov_iters"]}
         ctx.set_contraction(False)
-    # per step: persistent AJ CG (1) + norm (1) + Jv (norm, eps, axpy, 3 residual kernels)
-    # + CGS2 (2 multi-dots, 2 multi-axpys) + norm + scale
-    launches = 1 + 1 + 6 + 4 + 2
+    # per step: multigrid CG (start, 4 per non-coarsest level + 1 coarse per
+    # V-cycle, r.z, spmv, output) + norm (1) + Jv (norm, eps, axpy, 3 residual
+    # kernels) + CGS2 (2 multi-dots, 2 multi-axpys) + norm + scale
+    launches = (1 + MG_INNER * (4 * (mg["levels"] - 1) + 1 + 2) + (MG_INNER - 1) + 1) \
+        + 1 + 6 + 4 + 2
     solve = None
     if rank == 0 and not args.no_solve:
         solve = {}
         for name_, kind, inner in (("plain_fp64_aj", hofv.PC_AJ64, INNER_ITERS),
                                    ("fp32_aj", hofv.PC_AJ32, INNER_ITERS),
-                                   ("fp32_aj_inner40", hofv.PC_AJ32, 40)):
+                                   ("fp32_aj_inner40", hofv.PC_AJ32, 40),
+                                   ("fp32_aj_mg", hofv.PC_AJMG, MG_INNER),
+                                   ("fp32_aj_mg2", hofv.PC_AJMG, 2)):
             uu = torch.zeros_like(u)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -392,7 +408,8 @@ def run_hofv(args):
             torch.cuda.synchronize()
             dt = time.perf_counter() - t0
             err = float((uu.cpu().numpy() - u_ex).std() / max(np.abs(u_ex).std(), 1e-300))
-            solve[name_] = {"seconds": dt, "status": st["status"], "newton": st["newton_iters"],
+            solve[name_] = {"seconds": dt, "precond": kind, "inner_iters": inner,
+                            "status": st["status"], "newton": st["newton_iters"],
                             "krylov": st["krylov_iters"], "r_final_over_r0":
                             st["r_final"] / max(st["r0"], 1e-300),
                             "rel_error_vs_manufactured": err}
@@ -411,14 +428,19 @@ def run_hofv(args):
                            "gauss_per_face": lay.q_face,
                            "law": "linear" if wl.law == 0 else "neo-Hookean",
                            "step": f"one flexible Arnoldi step: AJ FP32 preconditioner "
-                                   f"({INNER_ITERS} CG its) + forward-difference Jv (1 FP64 "
-                                   f"residual) + 2x classical Gram-Schmidt on {J + 1} vectors",
+                                   f"({MG_INNER} CG it. with a {mg['levels']}-level "
+                                   f"aggregation-multigrid V-cycle) + forward-difference Jv "
+                                   f"(1 FP64 residual) + 2x classical Gram-Schmidt on {J + 1} "
+                                   f"vectors",
                            "l2": "inputs larger than L2 (coefficients "
                                  f"{rbytes / 1e9:.2f} GB per residual)",
                            "parallelism": "replicas" if ws > 1 else "single GPU"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches * args.steps, "clocks": clocks,
-                "setup_s": setup_s, "solve": solve, "contracted": contracted, "impl": "hofv"}
+                "setup_s": setup_s, "multigrid": mg,
+                "step_ms_jacobi_cg": {"inner_iters": INNER_ITERS, "ms_per_step": ms_jacobi,
+                                      "value": nc / (ms_jacobi * 1e-3) / 1e6},
+                "solve": solve, "contracted": contracted, "impl": "hofv"}
         print(json.dumps(line))
     ctx.close()
     if ws > 1:
@@ -509,10 +531,13 @@ def run_learned(args):
         wl, mesh, ctx, lay, setup_s, _, _ = build_workload(name)
         res = {"cells": lay.n_cells, "setup_s": setup_s}
         sols = {}
-        variants = (("plain_fp64_aj", hofv.PC_AJ64, 1, steps), ("fp32_aj", hofv.PC_AJ32, 1, steps),
-                    ("learned", hofv.PC_GNN, 1, steps),
-                    ("learned_no_judge", hofv.PC_GNN, 0, min(steps, 2) if name == held.name else 0))
-        for label, pc, judge, nsteps in variants:
+        variants = (("plain_fp64_aj", hofv.PC_AJ64, 1, steps, INNER_ITERS),
+                    ("fp32_aj", hofv.PC_AJ32, 1, steps, INNER_ITERS),
+                    ("fp32_aj_mg", hofv.PC_AJMG, 1, steps, 2),
+                    ("learned", hofv.PC_GNN, 1, steps, INNER_ITERS),
+                    ("learned_no_judge", hofv.PC_GNN, 0, min(steps, 2) if name == held.name else 0,
+                     INNER_ITERS))
+        for label, pc, judge, nsteps, inner in variants:
             if nsteps == 0:
                 continue
             if time.perf_counter() - t_start > args.budget_s:
@@ -520,7 +545,8 @@ def run_learned(args):
                 continue
             if pc == hofv.PC_GNN:
                 ctx.gnn_load(wpath)
-            capped = dict(opts, max_krylov=600 if judge else 300, max_newton=12 if judge else 6)
+            capped = dict(opts, max_krylov=600 if judge else 300, max_newton=12 if judge else 6,
+                          inner_iters=inner)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             u, st = block_load_steps(ctx, wl, lay, nsteps, precond=pc, gnn_judge=judge, **capped)
@@ -528,7 +554,7 @@ def run_learned(args):
             sols[label] = u
             print(f"[learned] {name} {label}: {res[label]}", file=sys.stderr, flush=True)
         ref = sols.get("plain_fp64_aj")
-        for label in ("fp32_aj", "learned"):
+        for label in ("fp32_aj", "fp32_aj_mg", "learned"):
             if ref is not None and label in sols:
                 res[label]["rel_diff_vs_plain"] = float((sols[label] - ref).norm() / ref.norm())
         result["eval"][name] = res

@@ -57,6 +57,7 @@ extern "C" {
 #define HOFV_PC_AJ64 0   /* compact approximate Jacobian, FP64 inner solve */
 #define HOFV_PC_AJ32 1   /* same operator stored and applied in FP32 */
 #define HOFV_PC_GNN 2    /* learned graph network on top of AJ32 */
+#define HOFV_PC_AJMG 3   /* same operator (FP32), CG with an algebraic-multigrid V-cycle */
 
 /* point sets for hofv_get_points */
 #define HOFV_PTS_CELL_CENTROID 0   /* [n_cells][dim] */
@@ -215,9 +216,12 @@ int hofv_jvp(hofv_ctx* ctx, const double* u, const double* Ru, const double* v,
 
 /* z ~= P^{-1} v with the compact approximate Jacobian P (Sec. 4.1) applied
    to every displacement component: HOFV_PC_AJ64 / AJ32 run `inner_iters`
-   Jacobi-preconditioned CG iterations in FP64 / FP32; HOFV_PC_GNN adds the
-   learned correction (needs hofv_gnn_load or hofv_gnn_train first).
-   v, z: DEVICE [dim][n_cells]. */
+   Jacobi-preconditioned CG iterations in FP64 / FP32; HOFV_PC_AJMG runs
+   `inner_iters` FP32 CG iterations preconditioned by one V-cycle of
+   smoothed-aggregation multigrid on P (hierarchy built on first use, once
+   per mesh; the paper leaves the inner solve of P to its linear-algebra
+   library); HOFV_PC_GNN adds the learned correction (needs hofv_gnn_load or
+   hofv_gnn_train first).  v, z: DEVICE [dim][n_cells]. */
 int hofv_precondition(hofv_ctx* ctx, int kind, int inner_iters, const double* v, double* z);
 
 /* Newton-Krylov solve of R(u) = 0 from the DEVICE vector u (updated in
@@ -318,6 +322,13 @@ int hofv_arnoldi_step(hofv_ctx* ctx, const double* u, const double* Ru, int kind
    resolves the array's address (cudaGetSymbolAddress) and should come
    before any stream capture.  u, R: DEVICE [dim][n_cells]. */
 int hofv_residual_noalloc(hofv_ctx* ctx, const double* u, double* R);
+
+/* The multigrid hierarchy of HOFV_PC_AJMG (built here if not yet built):
+   number of levels, the cell count of the first min(levels, max_sizes)
+   levels into sizes (HOST), stored non-zeros over all levels, and the host
+   seconds its construction took.  Synchronises. */
+int hofv_mg_info(hofv_ctx* ctx, int32_t* levels, int64_t* sizes, int32_t max_sizes,
+                 int64_t* nnz, double* setup_seconds);
 
 /* Self-test of the bounded waits: the approximate-Jacobian solve runs as one
    cooperative launch whose blocks meet at grid barriers; each wait gives up

@@ -96,6 +96,7 @@ static void gauss_rule(int n, double* x, double* w) {
 
 static void free_built(hofv_ctx* c) {
   gnn_release(c);
+  mg_release(c);
   for (void* p : c->allocs) cudaFree(p);
   c->allocs.clear();
   c->device_bytes = 0;
@@ -693,6 +694,8 @@ int hofv_precondition(hofv_ctx* c, int kind, int iters, const double* v, double*
     case HOFV_PC_AJ64:
     case HOFV_PC_AJ32:
       return aj_precondition(c, kind, iters, v, z);
+    case HOFV_PC_AJMG:
+      return mg_precondition(c, iters, v, z);
     case HOFV_PC_GNN: {
       if (!c->gnn) return fail(c, HOFV_ESTATE, "no learned preconditioner loaded");
       TRY(aj_precondition(c, HOFV_PC_AJ32, iters, v, z));
@@ -758,6 +761,7 @@ static int apply_pc(hofv_ctx* c, const hofv_solve_opts& o, const double* v, doub
     TRY(aj_precondition(c, HOFV_PC_AJ32, o.inner_iters, v, z));
     return gnn_apply(c, v, z, z);
   }
+  if (o.precond == HOFV_PC_AJMG) return mg_precondition(c, o.inner_iters, v, z);
   return aj_precondition(c, o.precond == HOFV_PC_AJ64 ? HOFV_PC_AJ64 : HOFV_PC_AJ32, o.inner_iters, v,
                          z);
 }
@@ -914,7 +918,8 @@ extern "C" int hofv_newton_solve(hofv_ctx* c, double* u, const hofv_solve_opts* 
   hofv_solve_opts o;
   hofv_default_opts(&o);
   if (opts) o = *opts;
-  if (o.restart < 1 || o.restart > 100 || o.max_krylov < 1 || o.max_newton < 0)
+  if (o.restart < 1 || o.restart > 100 || o.max_krylov < 1 || o.max_newton < 0 ||
+      o.precond < HOFV_PC_NONE || o.precond > HOFV_PC_AJMG)
     return fail(c, HOFV_EINVAL, "bad solver options");
   hofv_stats st;
   memset(&st, 0, sizeof(st));
@@ -1113,7 +1118,8 @@ extern "C" int hofv_arnoldi_step(hofv_ctx* c, const double* u, const double* Ru,
   if (!u || !Ru || !V || !Z || !h) return fail(c, HOFV_EINVAL, "null argument");
   const int64_t n = c->nc * c->dim;
   if (j < 0 || j > 99 || ld < n) return fail(c, HOFV_EINVAL, "bad Arnoldi index or leading dimension");
-  if (kind != HOFV_PC_NONE && kind != HOFV_PC_AJ64 && kind != HOFV_PC_AJ32 && kind != HOFV_PC_GNN)
+  if (kind != HOFV_PC_NONE && kind != HOFV_PC_AJ64 && kind != HOFV_PC_AJ32 && kind != HOFV_PC_GNN &&
+      kind != HOFV_PC_AJMG)
     return fail(c, HOFV_EINVAL, "unknown preconditioner");
   if (kind == HOFV_PC_GNN && !c->gnn) return fail(c, HOFV_ESTATE, "no learned preconditioner loaded");
   TRY(ensure_krylov(c, 1));
@@ -1198,5 +1204,13 @@ extern "C" int hofv_selftest_barrier(hofv_ctx* c, int32_t* timed_out) {
   int t = 0;
   TRY(barrier_selftest(c, &t));
   *timed_out = t;
+  return HOFV_OK;
+}
+
+extern "C" int hofv_mg_info(hofv_ctx* c, int32_t* levels, int64_t* sizes, int32_t max_sizes,
+                            int64_t* nnz, double* setup_seconds) {
+  if (!c || !levels || !nnz || !setup_seconds || (max_sizes > 0 && !sizes)) return HOFV_EINVAL;
+  if (!c->built) return hofv::fail(c, HOFV_ESTATE, "hofv_build_stencils must come first");
+  TRY(hofv::mg_info(c, levels, sizes, max_sizes, nnz, setup_seconds));
   return HOFV_OK;
 }

@@ -134,6 +134,8 @@ struct hofv_ctx {
   double* d_h = nullptr;            // [m+2] projections
   // ---- learned preconditioner ----
   void* gnn = nullptr;
+  // ---- multigrid hierarchy of the approximate Jacobian ----
+  void* mg = nullptr;
   double aj_rate = -1.0;            // mean per-iteration residual reduction of the last AJ cycle
   int64_t device_bytes = 0;
   std::vector<void*> allocs;
@@ -219,6 +221,12 @@ int aj_precondition(hofv_ctx* c, int kind, int iters, const double* v, double* z
 int check_pc_barrier(hofv_ctx* c);
 // bounded-wait self-test of the grid barrier (see hofv_selftest_barrier)
 int barrier_selftest(hofv_ctx* c, int* timed_out);
+
+// ---- multigrid inner solve of the approximate Jacobian (multigrid.cu) ----
+int mg_precondition(hofv_ctx* c, int iters, const double* v, double* z);
+int mg_info(hofv_ctx* c, int32_t* levels, int64_t* sizes, int max_sizes, int64_t* nnz,
+            double* setup_s);
+void mg_release(hofv_ctx* c);
 
 // ---- learned preconditioner (gnn.cu) ----
 int gnn_apply(hofv_ctx* c, const double* v, const double* z_aj, double* z);

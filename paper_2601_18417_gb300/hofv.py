@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libhofv.so")
 OK, WNOTCONV = 0, 1
 EINVAL, ENOMEM, ECUDA, EILLCOND, ENAN, ENOTSUP, ESTATE = -1, -2, -3, -4, -5, -6, -7
 LAW_LINEAR, LAW_NEOHOOKEAN = 0, 1
-PC_NONE, PC_AJ64, PC_AJ32, PC_GNN = -1, 0, 1, 2
+PC_NONE, PC_AJ64, PC_AJ32, PC_GNN, PC_AJMG = -1, 0, 1, 2, 3
 PTS_CELL_CENTROID, PTS_DISP_QP, PTS_DISP_CENTRE, PTS_TRAC_QP, PTS_CELL_QP = 0, 1, 2, 3, 4
 PTS_FACE_CENTRE, PTS_FACE_QP, PTS_FACE_AREA, PTS_CELL_VOLUME = 5, 6, 7, 8
 
@@ -102,6 +102,8 @@ SIGNATURES = {
     "hofv_force_scale": (_I, [_P, _P, C.POINTER(_D)]),
     "hofv_set_contraction": (_I, [_P, _I]),
     "hofv_selftest_barrier": (_I, [_P, C.POINTER(C.c_int32)]),
+    "hofv_mg_info": (_I, [_P, C.POINTER(C.c_int32), _P, C.c_int32, C.POINTER(C.c_int64),
+                          C.POINTER(C.c_double)]),
     "hofv_gnn_init": (_I, [_P, C.c_uint64, _D]),
     "hofv_gnn_num_params": (_I, [_P, C.POINTER(_I64)]),
     "hofv_gnn_get_params": (_I, [_P, _P, _I64]),
@@ -222,6 +224,17 @@ class Context:
 
     def set_material(self, law, mu, lam):
         return self._check(self._L.hofv_set_material(self.h, law, mu, lam))
+
+    def mg_info(self):
+        """Multigrid hierarchy of PC_AJMG: level sizes, non-zeros, set-up s."""
+        lv = C.c_int32(0)
+        sizes = np.zeros(32, np.int64)
+        nnz = C.c_int64(0)
+        sec = C.c_double(0.0)
+        self._check(self._L.hofv_mg_info(self.h, C.byref(lv), _ptr(sizes), sizes.size,
+                                         C.byref(nnz), C.byref(sec)))
+        return {"levels": lv.value, "sizes": sizes[: lv.value].tolist(), "nnz": nnz.value,
+                "setup_s": sec.value}
 
     def selftest_barrier(self):
         t = C.c_int32(0)
