@@ -40,7 +40,7 @@ if ROOT not in sys.path:
 METRIC = "residual evals/s (Mcell/s, % HBM roofline); JFNK time to 1e-8, learned vs plain"
 KRYLOV_J = 15          # Arnoldi index of the timed step (16 basis vectors)
 INNER_ITERS = 20       # approximate-Jacobian CG iterations per preconditioner apply (Jacobi CG)
-MG_INNER = 1           # multigrid-preconditioned CG iterations per apply (the timed step)
+MG_INNER = 1           # multigrid applications per preconditioner apply (1: one V-cycle)
 
 
 def dist_env():
@@ -387,11 +387,11 @@ def run_hofv(args):
                 "seconds": time.perf_counter() - t0, "status": st["status"],
                 "newton": st["newton_iters"], "krylov": st["krylov_iters"]}
         ctx.set_contraction(False)
-    # per step: multigrid CG (start, 4 per non-coarsest level + 1 coarse per
-    # V-cycle, r.z, spmv, output) + norm (1) + Jv (norm, eps, axpy, 3 residual
-    # kernels) + CGS2 (2 multi-dots, 2 multi-axpys) + norm + scale
-    launches = (1 + MG_INNER * (4 * (mg["levels"] - 1) + 1 + 2) + (MG_INNER - 1) + 1) \
-        + 1 + 6 + 4 + 2
+    # per step: the preconditioner (one V-cycle: 4 launches per level above the
+    # coarsest, 1 on it) + norm (1) + Jv (norm, eps, axpy, 3 residual kernels)
+    # + CGS2 (2 multi-dots, 2 multi-axpys) + norm + scale
+    assert MG_INNER == 1 and mg["levels"] > 1
+    launches = (4 * (mg["levels"] - 1) + 1) + 1 + 6 + 4 + 2
     solve = None
     if rank == 0 and not args.no_solve:
         solve = {}
@@ -428,7 +428,7 @@ def run_hofv(args):
                            "gauss_per_face": lay.q_face,
                            "law": "linear" if wl.law == 0 else "neo-Hookean",
                            "step": f"one flexible Arnoldi step: AJ FP32 preconditioner "
-                                   f"({MG_INNER} CG it. with a {mg['levels']}-level "
+                                   f"(one {mg['levels']}-level "
                                    f"aggregation-multigrid V-cycle) + forward-difference Jv "
                                    f"(1 FP64 residual) + 2x classical Gram-Schmidt on {J + 1} "
                                    f"vectors",

@@ -216,11 +216,11 @@ int hofv_jvp(hofv_ctx* ctx, const double* u, const double* Ru, const double* v,
 
 /* z ~= P^{-1} v with the compact approximate Jacobian P (Sec. 4.1) applied
    to every displacement component: HOFV_PC_AJ64 / AJ32 run `inner_iters`
-   Jacobi-preconditioned CG iterations in FP64 / FP32; HOFV_PC_AJMG runs
-   `inner_iters` FP32 CG iterations preconditioned by one V-cycle of
-   smoothed-aggregation multigrid on P (hierarchy built on first use, once
-   per mesh; the paper leaves the inner solve of P to its linear-algebra
-   library); HOFV_PC_GNN adds the learned correction (needs hofv_gnn_load or
+   Jacobi-preconditioned CG iterations in FP64 / FP32; HOFV_PC_AJMG applies
+   one V-cycle of smoothed-aggregation multigrid on P (FP32) when
+   inner_iters <= 1, else runs `inner_iters` CG iterations preconditioned by
+   that V-cycle (hierarchy built on first use, once per mesh; the paper
+   leaves the inner solve of P to its linear-algebra library); HOFV_PC_GNN adds the learned correction (needs hofv_gnn_load or
    hofv_gnn_train first).  v, z: DEVICE [dim][n_cells]. */
 int hofv_precondition(hofv_ctx* ctx, int kind, int inner_iters, const double* v, double* z);
 

@@ -19,8 +19,9 @@
 //
 // The hierarchy is built once per mesh on the host (it depends on the
 // geometry only: B is stored with Kbar = 1) and lives on the device in
-// CSR form.  Every kernel handles all displacement components at once, so
-// the matrices are read once per application.  Reductions are
+// CSR form: one thread per row for short rows, one warp per row for long
+// ones.  Every kernel handles all displacement components at once, so the
+// matrices are read once per application.  Reductions are
 // deterministic (fixed-order partial sums, last-block finalisation).
 #include <math.h>
 #include <stdint.h>
@@ -41,6 +42,8 @@ constexpr int64_t kCoarsest = 600;   // stop coarsening at or below this many ce
 constexpr int64_t kDenseMax = 1500;  // largest coarsest level inverted densely; a larger
                                      // one (coarsening stalled) gets Jacobi sweeps
 constexpr int kCoarseSweeps = 8;
+constexpr int64_t kWarpRowNnz = 12;  // mean entries per row above which one warp takes a row
+constexpr int kRedBlocks = 304;      // blocks of the CG reductions (2 per SM)
 constexpr int kMaxLevels = 16;
 constexpr double kTheta0 = 0.08;     // strength threshold on the finest level
 constexpr double kThetaC = 0.02;     // on coarser levels, whose stencils spread each
@@ -293,6 +296,10 @@ struct Level {
   // prolongation from the next level (rows: this level) and its transpose
   int32_t *prp = nullptr, *pci = nullptr, *rrp = nullptr, *rci = nullptr;
   float *pva = nullptr, *rva = nullptr;
+  int64_t nnz = 0, pnnz = 0, rnnz = 0;
+  // long rows (coarse operators, restrictions) go one warp per row, so that
+  // levels with few rows still spread over the whole GPU
+  bool a_warp = false, p_warp = false, r_warp = false;
   float *x = nullptr, *r = nullptr, *b = nullptr, *y = nullptr;  // [dim][n] work
 };
 
@@ -339,26 +346,35 @@ unsigned grid_for(int64_t n) {
 
 // ---- V-cycle kernels (all components per thread, component stride n) ----
 
+// b as stored (float), or as the caller's FP64 right-hand side times a scale
+template <typename TB>
+__device__ __forceinline__ float ldb(const TB* b, int64_t k, double bs) {
+  if constexpr (sizeof(TB) == 8)
+    return (float)(b[k] * bs);
+  else
+    return b[k];
+}
+
 // x = W b (W = omega D^-1), r = b - B x
-template <int DIM>
+template <int DIM, typename TB = float>
 __global__ void k_pre(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                       const float* __restrict__ va, const float* __restrict__ dg,
-                      const float* __restrict__ dinv, const float* __restrict__ b, float* x,
-                      float* r) {
+                      const float* __restrict__ dinv, const TB* __restrict__ b, double bs,
+                      float* x, float* r) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const float wi = dinv[i], di = dg[i];
     float bi[DIM], s[DIM];
 #pragma unroll
     for (int j = 0; j < DIM; ++j) {
-      bi[j] = b[j * n + i];
+      bi[j] = ldb(b, j * n + i, bs);
       s[j] = di * wi * bi[j];
     }
     for (int32_t k = rp[i]; k < rp[i + 1]; ++k) {
       const int32_t c = ci[k];
       const float a = va[k] * dinv[c];
 #pragma unroll
-      for (int j = 0; j < DIM; ++j) s[j] += a * b[j * n + c];
+      for (int j = 0; j < DIM; ++j) s[j] += a * ldb(b, j * n + c, bs);
     }
 #pragma unroll
     for (int j = 0; j < DIM; ++j) {
@@ -390,11 +406,11 @@ __global__ void k_csr_apply(int64_t nrow, int64_t nin, const int32_t* __restrict
 }
 
 // y = x + W (b - B x)
-template <int DIM>
+template <int DIM, typename TB = float, typename TY = float>
 __global__ void k_post(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                        const float* __restrict__ va, const float* __restrict__ dg,
-                       const float* __restrict__ dinv, const float* __restrict__ b,
-                       const float* __restrict__ x, float* y) {
+                       const float* __restrict__ dinv, const TB* __restrict__ b, double bs,
+                       const float* __restrict__ x, TY* y) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const float wi = dinv[i], di = dg[i];
@@ -402,7 +418,7 @@ __global__ void k_post(int64_t n, const int32_t* __restrict__ rp, const int32_t*
 #pragma unroll
     for (int j = 0; j < DIM; ++j) {
       xi[j] = x[j * n + i];
-      s[j] = b[j * n + i] - di * xi[j];
+      s[j] = ldb(b, j * n + i, bs) - di * xi[j];
     }
     for (int32_t k = rp[i]; k < rp[i + 1]; ++k) {
       const int32_t c = ci[k];
@@ -411,7 +427,7 @@ __global__ void k_post(int64_t n, const int32_t* __restrict__ rp, const int32_t*
       for (int j = 0; j < DIM; ++j) s[j] -= a * x[j * n + c];
     }
 #pragma unroll
-    for (int j = 0; j < DIM; ++j) y[j * n + i] = xi[j] + wi * s[j];
+    for (int j = 0; j < DIM; ++j) y[j * n + i] = (TY)(xi[j] + wi * s[j]);
   }
 }
 
@@ -438,35 +454,157 @@ __global__ void k_dense(int64_t m, const float* __restrict__ inv, const float* _
   }
 }
 
+// ---- the same operations with one warp per row ----
+template <int DIM>
+__device__ __forceinline__ void warp_reduce(float (&s)[DIM]) {
+#pragma unroll
+  for (int j = 0; j < DIM; ++j)
+    for (int o = 16; o > 0; o >>= 1) s[j] += __shfl_xor_sync(0xffffffffu, s[j], o);
+}
+
+// x = W b, r = b - B x
+template <int DIM>
+__global__ void k_pre_w(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                        const float* __restrict__ va, const float* __restrict__ dg,
+                        const float* __restrict__ dinv, const float* __restrict__ b, float* x,
+                        float* r) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < n; i += nw) {
+    float s[DIM];
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) s[j] = 0.0f;
+    for (int32_t k = rp[i] + lane; k < rp[i + 1]; k += 32) {
+      const int32_t c = ci[k];
+      const float a = va[k] * dinv[c];
+#pragma unroll
+      for (int j = 0; j < DIM; ++j) s[j] += a * b[j * n + c];
+    }
+    warp_reduce<DIM>(s);
+    if (lane == 0) {
+      const float wi = dinv[i], di = dg[i];
+#pragma unroll
+      for (int j = 0; j < DIM; ++j) {
+        const float bi = b[j * n + i];
+        x[j * n + i] = wi * bi;
+        r[j * n + i] = bi - (di * wi * bi + s[j]);
+      }
+    }
+  }
+}
+
+// out = M in, or out += M in
+template <int DIM, bool ADD>
+__global__ void k_csr_apply_w(int64_t nrow, int64_t nin, const int32_t* __restrict__ rp,
+                              const int32_t* __restrict__ ci, const float* __restrict__ va,
+                              const float* __restrict__ in, float* out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < nrow; i += nw) {
+    float s[DIM];
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) s[j] = 0.0f;
+    for (int32_t k = rp[i] + lane; k < rp[i + 1]; k += 32) {
+      const int32_t c = ci[k];
+      const float a = va[k];
+#pragma unroll
+      for (int j = 0; j < DIM; ++j) s[j] += a * in[j * nin + c];
+    }
+    warp_reduce<DIM>(s);
+    if (lane == 0) {
+#pragma unroll
+      for (int j = 0; j < DIM; ++j) out[j * nrow + i] = ADD ? out[j * nrow + i] + s[j] : s[j];
+    }
+  }
+}
+
+// y = x + W (b - B x)
+template <int DIM>
+__global__ void k_post_w(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                         const float* __restrict__ va, const float* __restrict__ dg,
+                         const float* __restrict__ dinv, const float* __restrict__ b,
+                         const float* __restrict__ x, float* y) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < n; i += nw) {
+    float s[DIM];
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) s[j] = 0.0f;
+    for (int32_t k = rp[i] + lane; k < rp[i + 1]; k += 32) {
+      const int32_t c = ci[k];
+      const float a = va[k];
+#pragma unroll
+      for (int j = 0; j < DIM; ++j) s[j] += a * x[j * n + c];
+    }
+    warp_reduce<DIM>(s);
+    if (lane == 0) {
+      const float wi = dinv[i], di = dg[i];
+#pragma unroll
+      for (int j = 0; j < DIM; ++j) {
+        const float xi = x[j * n + i];
+        y[j * n + i] = xi + wi * (b[j * n + i] - di * xi - s[j]);
+      }
+    }
+  }
+}
+
+unsigned grid_warps(int64_t rows) {
+  return (unsigned)std::max<int64_t>(
+      1, std::min<int64_t>((rows * 32 + kThreads - 1) / kThreads, 8192));
+}
+
+template <int DIM>
+void pre(const Level& L, const float* b, float* x, float* r, cudaStream_t st) {
+  if (L.a_warp)
+    k_pre_w<DIM><<<grid_warps(L.n), kThreads, 0, st>>>(L.n, L.rp, L.ci, L.va, L.dg, L.dinv, b, x, r);
+  else
+    k_pre<DIM><<<grid_for(L.n), kThreads, 0, st>>>(L.n, L.rp, L.ci, L.va, L.dg, L.dinv, b, 1.0, x,
+                                                   r);
+}
+
+template <int DIM>
+void post(const Level& L, const float* b, const float* x, float* y, cudaStream_t st) {
+  if (L.a_warp)
+    k_post_w<DIM><<<grid_warps(L.n), kThreads, 0, st>>>(L.n, L.rp, L.ci, L.va, L.dg, L.dinv, b, x,
+                                                        y);
+  else
+    k_post<DIM><<<grid_for(L.n), kThreads, 0, st>>>(L.n, L.rp, L.ci, L.va, L.dg, L.dinv, b, 1.0, x,
+                                                    y);
+}
+
+template <int DIM, bool ADD>
+void apply(bool warp, int64_t nrow, int64_t nin, const int32_t* rp, const int32_t* ci,
+           const float* va, const float* in, float* out, cudaStream_t st) {
+  if (warp)
+    k_csr_apply_w<DIM, ADD><<<grid_warps(nrow), kThreads, 0, st>>>(nrow, nin, rp, ci, va, in, out);
+  else
+    k_csr_apply<DIM, ADD><<<grid_for(nrow), kThreads, 0, st>>>(nrow, nin, rp, ci, va, in, out);
+}
+
 template <int DIM>
 void vcycle(const Mg& g, int l, const float* b, float* out, cudaStream_t st) {
   const Level& L = g.L[l];
   if (l + 1 == (int)g.L.size()) {
     if (g.inv) {
-      const int64_t threads = L.n * 32;
-      k_dense<DIM><<<(unsigned)((threads + kThreads - 1) / kThreads), kThreads, 0, st>>>(
-          L.n, g.inv, b, out);
+      k_dense<DIM><<<grid_warps(L.n), kThreads, 0, st>>>(L.n, g.inv, b, out);
       return;
     }
     // damped Jacobi sweeps from zero (a symmetric operator)
-    k_pre<DIM><<<grid_for(L.n), kThreads, 0, st>>>(L.n, L.rp, L.ci, L.va, L.dg, L.dinv, b, L.x, L.r);
+    pre<DIM>(L, b, L.x, L.r, st);
     float* src = L.x;
     for (int s = 1; s < kCoarseSweeps; ++s) {
       float* dst = s + 1 == kCoarseSweeps ? out : (src == L.x ? L.r : L.x);
-      k_post<DIM><<<grid_for(L.n), kThreads, 0, st>>>(L.n, L.rp, L.ci, L.va, L.dg, L.dinv, b, src,
-                                                      dst);
+      post<DIM>(L, b, src, dst, st);
       src = dst;
     }
     return;
   }
   const Level& C = g.L[l + 1];
-  k_pre<DIM><<<grid_for(L.n), kThreads, 0, st>>>(L.n, L.rp, L.ci, L.va, L.dg, L.dinv, b, L.x, L.r);
-  k_csr_apply<DIM, false><<<grid_for(C.n), kThreads, 0, st>>>(C.n, L.n, L.rrp, L.rci, L.rva, L.r,
-                                                              C.b);
+  pre<DIM>(L, b, L.x, L.r, st);
+  apply<DIM, false>(L.r_warp, C.n, L.n, L.rrp, L.rci, L.rva, L.r, C.b, st);
   vcycle<DIM>(g, l + 1, C.b, C.y, st);
-  k_csr_apply<DIM, true><<<grid_for(L.n), kThreads, 0, st>>>(L.n, C.n, L.prp, L.pci, L.pva, C.y,
-                                                             L.x);
-  k_post<DIM><<<grid_for(L.n), kThreads, 0, st>>>(L.n, L.rp, L.ci, L.va, L.dg, L.dinv, b, L.x, out);
+  apply<DIM, true>(L.p_warp, L.n, C.n, L.prp, L.pci, L.pva, C.y, L.x, st);
+  post<DIM>(L, b, L.x, out, st);
 }
 
 // ---- conjugate-gradient kernels on level 0 ----
@@ -594,8 +732,11 @@ __global__ void k_cg_out(int64_t n, const float* __restrict__ p, const float* __
 }
 
 // ---------------------------------------------------------------- build
-int upload_level(hofv_ctx* c, Level& L, const HostCsr& A, int dim) {
+// the finest level stays one thread per row: the CG kernels read it directly
+int upload_level(hofv_ctx* c, Level& L, const HostCsr& A, int dim, bool finest) {
   L.n = A.n;
+  L.nnz = (int64_t)A.ci.size();
+  L.a_warp = !finest && L.nnz > kWarpRowNnz * A.n;
   if (A.ci.size() >= (size_t)INT32_MAX) return fail(c, HOFV_EINVAL, "multigrid level too large");
   double rho = 0.0;
   for (int64_t i = 0; i < A.n; ++i) {
@@ -659,7 +800,7 @@ int build_levels(hofv_ctx* c, Mg* g, HostCsr A, int dim, int64_t n) {
   for (int l = 0; l < kMaxLevels; ++l) {
     g->L.emplace_back();
     Level& L = g->L.back();
-    MG_TRY(upload_level(c, L, A, dim));
+    MG_TRY(upload_level(c, L, A, dim, l == 0));
     g->nnz_total += (int64_t)A.ci.size() + A.n;
     if (A.n <= kCoarsest || l + 1 == kMaxLevels) break;
     std::vector<int32_t> agg;
@@ -669,6 +810,10 @@ int build_levels(hofv_ctx* c, Mg* g, HostCsr A, int dim, int64_t n) {
     const HostMat R = transpose(P);
     HostCsr Ac = galerkin(A, P, R);
     if ((int64_t)Ac.ci.size() > 400 * Ac.n) break;  // coarse operator too dense
+    L.pnnz = (int64_t)P.ci.size();
+    L.rnnz = (int64_t)R.ci.size();
+    L.p_warp = L.pnnz > kWarpRowNnz * P.nr;
+    L.r_warp = L.rnnz > kWarpRowNnz * R.nr;
     if (upload(c, &L.prp, to32(P.rp)) || upload(c, &L.pci, P.ci) || upload(c, &L.pva, tof(P.va)) ||
         upload(c, &L.rrp, to32(R.rp)) || upload(c, &L.rci, R.ci) || upload(c, &L.rva, tof(R.va)))
       return HOFV_ENOMEM;
@@ -682,7 +827,8 @@ int build_levels(hofv_ctx* c, Mg* g, HostCsr A, int dim, int64_t n) {
     MG_TRY(upload(c, &g->inv, inv));
   }
   const size_t nv = (size_t)dim * n;
-  g->blocks = (int)std::min<int64_t>((n + kThreads - 1) / kThreads, 1216);
+  // few blocks for the CG reductions: the last block adds one partial per block
+  g->blocks = (int)std::min<int64_t>((n + kThreads - 1) / kThreads, kRedBlocks);
   if (dev_alloc(c, &g->x, nv) || dev_alloc(c, &g->r, nv) || dev_alloc(c, &g->z, nv) ||
       dev_alloc(c, &g->p0, nv) || dev_alloc(c, &g->p1, nv) || dev_alloc(c, &g->q, nv) ||
       dev_alloc(c, &g->part, (size_t)2 * dim * g->blocks) || dev_alloc(c, &g->cnt, 4) ||
@@ -699,6 +845,21 @@ void run(hofv_ctx* c, Mg& g, int iters, const double* v, double* zout) {
   const int64_t n = c->nc;
   const Level& L = g.L[0];
   const unsigned gb = (unsigned)g.blocks;
+  if (iters == 1 && g.L.size() > 1) {
+    // one V-cycle applied to b = -v / Kbar, read and written in FP64 by the
+    // finest level's smoothers (the flexible outer solver absorbs the
+    // missing CG step length: it only scales z)
+    const Level& C = g.L[1];
+    const double bs = -1.0 / c->mat.kbar;
+    k_pre<DIM, double><<<grid_for(n), kThreads, 0, st>>>(n, L.rp, L.ci, L.va, L.dg, L.dinv, v, bs,
+                                                         L.x, L.r);
+    apply<DIM, false>(L.r_warp, C.n, n, L.rrp, L.rci, L.rva, L.r, C.b, st);
+    vcycle<DIM>(g, 1, C.b, C.y, st);
+    apply<DIM, true>(L.p_warp, n, C.n, L.prp, L.pci, L.pva, C.y, L.x, st);
+    k_post<DIM, double, double><<<grid_for(n), kThreads, 0, st>>>(n, L.rp, L.ci, L.va, L.dg,
+                                                                  L.dinv, v, bs, L.x, zout);
+    return;
+  }
   k_cg_start<DIM><<<grid_for(DIM * n), kThreads, 0, st>>>(n, v, 1.0 / c->mat.kbar, g.r, g.x);
   float* p[2] = {g.p0, g.p1};
   for (int it = 0; it < iters; ++it) {

@@ -47,6 +47,7 @@ template <typename A = double>
 __device__ __forceinline__ double warp0_sum(const double* red, unsigned int nb) {
   A s = (A)0;
   if (threadIdx.x < 32) {
+#pragma unroll 8
     for (unsigned int b = threadIdx.x; b < nb; b += 32) s += (A)__ldcg(red + b);
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   }
