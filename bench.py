@@ -537,8 +537,9 @@ def run_learned(args):
                     ("learned", hofv.PC_GNN, 1, steps, INNER_ITERS),
                     ("learned_no_judge", hofv.PC_GNN, 0, min(steps, 2) if name == held.name else 0,
                      INNER_ITERS))
+        only = [x for x in (args.eval_variants.split(",") if name != held.name else []) if x]
         for label, pc, judge, nsteps, inner in variants:
-            if nsteps == 0:
+            if nsteps == 0 or (only and label not in only):
                 continue
             if time.perf_counter() - t_start > args.budget_s:
                 res[label] = {"skipped": "time budget"}
@@ -593,6 +594,68 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_pc_sweep(args):
+    """Preconditioner applications on one workload: CUDA-event time per apply
+    and the relative residual |P z - v| / |v| of the approximate-Jacobian
+    system it leaves (P assembled on the host from the library's own
+    coefficients), for the Jacobi-CG and multigrid inner solves; then time to
+    1e-8 with each (linear law: one solve from u = 0; neo-Hookean block: the
+    first 3 load steps)."""
+    import scipy.sparse as sp
+    import torch
+
+    from paper_2601_18417_gb300 import build as B
+    from paper_2601_18417_gb300 import hofv
+    B.build()
+    wl, mesh, ctx, lay, setup_s, u_ex, field = build_workload(args.workload)
+    t0 = time.perf_counter()
+    mg = ctx.mg_info()
+    mg["first_call_wall_s"] = time.perf_counter() - t0
+    diag, off = ctx.get_aj()
+    own, nei, _, _ = ctx.get_faces()
+    ni, nc, d = lay.n_internal, lay.n_cells, wl.dim
+    A = sp.csr_matrix((np.concatenate([diag, off, off]),
+                       (np.concatenate([np.arange(nc), own[:ni], nei[:ni]]),
+                        np.concatenate([np.arange(nc), nei[:ni], own[:ni]]))), shape=(nc, nc))
+    kbar = 2 * wl.mu + wl.lam
+    v = torch.as_tensor(np.random.default_rng(0).standard_normal((d, nc)), device="cuda:0")
+    z = torch.empty_like(v)
+    vh = v.cpu().numpy()
+    s = torch.cuda.current_stream()
+    out = {"mode": "pc-sweep", "workload": wl.name, "cells": nc, "multigrid": mg, "apply": [],
+           "solve": []}
+    for kind, its in ((hofv.PC_AJ64, 20), (hofv.PC_AJ32, 20), (hofv.PC_AJ32, 40),
+                      (hofv.PC_AJMG, 1), (hofv.PC_AJMG, 2), (hofv.PC_AJMG, 4)):
+        for _ in range(3):
+            ctx.precondition(kind, its, v, z)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(20):
+            ctx.precondition(kind, its, v, z)
+        e1.record(s)
+        torch.cuda.synchronize()
+        zh = z.cpu().numpy()
+        rel = max(float(np.linalg.norm(kbar * (A @ zh[j]) - vh[j]) / np.linalg.norm(vh[j]))
+                  for j in range(d))
+        out["apply"].append({"precond": kind, "inner_iters": its,
+                             "ms": e0.elapsed_time(e1) / 20, "rel_residual": rel})
+    for kind, its in ((hofv.PC_AJ64, INNER_ITERS), (hofv.PC_AJ32, INNER_ITERS),
+                      (hofv.PC_AJMG, 1), (hofv.PC_AJMG, 2)):
+        opts = dict(rtol=1e-8, precond=kind, inner_iters=its, restart=30, max_krylov=3000)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        if wl.law == 0:
+            u = torch.zeros((d, nc), dtype=torch.float64, device="cuda:0")
+            st = [ctx.newton_solve(u, **opts)]
+        else:
+            u, st = block_load_steps(ctx, wl, lay, 3, **opts)
+        res = summarize(st, time.perf_counter() - t0)
+        res.update({"precond": kind, "inner_iters": its})
+        out["solve"].append(res)
+    ctx.close()
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -608,10 +671,14 @@ def main():
     ap.add_argument("--train-workload", default="hex64j-p2-nh")
     ap.add_argument("--eval-workload", default="")
     ap.add_argument("--eval-steps", type=int, default=10)
+    ap.add_argument("--eval-variants", default="",
+                    help="comma list of variants to run on --eval-workload (default: all)")
     ap.add_argument("--epochs", type=int, default=40)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--record", type=int, default=2, help="1: Newton pairs, 2: + Krylov pairs")
+    ap.add_argument("--pc-sweep", action="store_true",
+                    help="time each preconditioner's apply and solve on --workload")
     ap.add_argument("--budget-s", type=float, default=420.0,
                     help="wall-clock budget of the learned comparison; later variants are skipped")
     args = ap.parse_args()
@@ -621,6 +688,8 @@ def main():
         run_reference(args)
     elif args.learned:
         run_learned(args)
+    elif args.pc_sweep:
+        run_pc_sweep(args)
     else:
         run_hofv(args)
 
