@@ -639,6 +639,9 @@ def run_pc_sweep(args):
                   for j in range(d))
         out["apply"].append({"precond": kind, "inner_iters": its,
                              "ms": e0.elapsed_time(e1) / 20, "rel_residual": rel})
+    # untimed: loads the solver's kernels and allocates its Krylov storage
+    ctx.newton_solve(torch.zeros((d, nc), dtype=torch.float64, device="cuda:0"), max_newton=1,
+                     max_krylov=2, restart=30)
     for kind, its in ((hofv.PC_AJ64, INNER_ITERS), (hofv.PC_AJ32, INNER_ITERS),
                       (hofv.PC_AJMG, 1), (hofv.PC_AJMG, 2)):
         opts = dict(rtol=1e-8, precond=kind, inner_iters=its, restart=30, max_krylov=3000)
