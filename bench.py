@@ -291,6 +291,18 @@ def run_hofv(args):
     e1.record(s)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
+    # the same step launched kernel by kernel instead of as one CUDA graph
+    os.environ["HOFV_GRAPHS"] = "0"
+    for _ in range(3):
+        step()
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record(s)
+    for _ in range(max(args.steps // 5, 10)):
+        step()
+    g1.record(s)
+    torch.cuda.synchronize()
+    os.environ.pop("HOFV_GRAPHS", None)
+    ms_direct = g0.elapsed_time(g1) / max(args.steps // 5, 10)
     # the same step with the Jacobi-preconditioned CG inner solve, for comparison
     for _ in range(3):
         ctx.arnoldi_step(u, Ru, hofv.PC_AJ32, INNER_ITERS, V, Z, J)
@@ -431,13 +443,15 @@ def run_hofv(args):
                                    f"(one {mg['levels']}-level "
                                    f"aggregation-multigrid V-cycle) + forward-difference Jv "
                                    f"(1 FP64 residual) + 2x classical Gram-Schmidt on {J + 1} "
-                                   f"vectors",
+                                   f"vectors; device part replayed as one CUDA graph",
                            "l2": "inputs larger than L2 (coefficients "
                                  f"{rbytes / 1e9:.2f} GB per residual)",
                            "parallelism": "replicas" if ws > 1 else "single GPU"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches * args.steps, "clocks": clocks,
                 "setup_s": setup_s, "multigrid": mg,
+                "step_ms_no_graph": {"ms_per_step": ms_direct,
+                                     "value": nc / (ms_direct * 1e-3) / 1e6},
                 "step_ms_jacobi_cg": {"inner_iters": INNER_ITERS, "ms_per_step": ms_jacobi,
                                       "value": nc / (ms_jacobi * 1e-3) / 1e6},
                 "solve": solve, "contracted": contracted, "impl": "hofv"}

@@ -94,7 +94,16 @@ static void gauss_rule(int n, double* x, double* w) {
   }
 }
 
+static void graphs_clear(hofv_ctx* c);
+
+// kernel arguments baked into captured graphs change: drop the graphs
+static void invalidate_graphs(hofv_ctx* c) {
+  c->gen++;
+  graphs_clear(c);
+}
+
 static void free_built(hofv_ctx* c) {
+  invalidate_graphs(c);
   gnn_release(c);
   mg_release(c);
   for (void* p : c->allocs) cudaFree(p);
@@ -156,6 +165,7 @@ extern "C" {
 
 int hofv_set_contraction(hofv_ctx* c, int on) {
   if (!c) return HOFV_EINVAL;
+  invalidate_graphs(c);
   c->contract = on != 0;
   if (!c->contract) {
     c->tco_valid = false;
@@ -186,6 +196,7 @@ void hofv_destroy(hofv_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   else cudaDeviceSynchronize();
   free_built(c);
+  if (c->cap) cudaStreamDestroy(c->cap);
   delete c;
 }
 
@@ -195,6 +206,7 @@ int hofv_set_mesh(hofv_ctx* c, int dim, int64_t nn, const double* xyz, int64_t n
                   const int64_t* cell_nodes, int64_t nb, const int64_t* bface_nodes,
                   const int32_t* bface_tag) {
   if (!c) return HOFV_EINVAL;
+  invalidate_graphs(c);
   if (dim != 2 && dim != 3) return fail(c, HOFV_EINVAL, "dim must be 2 or 3");
   if (nn <= 0 || nc <= 0 || !xyz || !cell_nodes || nb < 0 || (nb > 0 && (!bface_nodes || !bface_tag)))
     return fail(c, HOFV_EINVAL, "empty mesh or null array");
@@ -316,6 +328,7 @@ int hofv_set_mesh(hofv_ctx* c, int dim, int64_t nn, const double* xyz, int64_t n
 
 int hofv_set_scheme(hofv_ctx* c, int p, int n_plus, int q1, double k_weight, double alpha) {
   if (!c) return HOFV_EINVAL;
+  invalidate_graphs(c);
   if (!c->have_mesh) return fail(c, HOFV_ESTATE, "hofv_set_mesh must come first");
   if (p < 1 || p > 3) return fail(c, HOFV_EINVAL, "p must be 1..3");
   if (q1 < 1 || q1 > 4 || (c->dim == 3 && q1 > 3))
@@ -574,6 +587,7 @@ int hofv_set_material(hofv_ctx* c, int law, double mu, double lambda) {
   if (!c) return HOFV_EINVAL;
   if (law != HOFV_LAW_LINEAR && law != HOFV_LAW_NEOHOOKEAN) return fail(c, HOFV_EINVAL, "unknown law");
   if (!(mu > 0) || !(lambda > -2.0 * mu / 3.0)) return fail(c, HOFV_EINVAL, "bad material constants");
+  invalidate_graphs(c);
   c->mat.law = law;
   c->mat.mu = mu;
   c->mat.lam = lambda;
@@ -727,6 +741,118 @@ void hofv_default_opts(hofv_solve_opts* o) {
 
 namespace hofv {
 
+// ---------------------------------------------------------------------
+// The device part of one flexible Arnoldi step, z_j = M v_j, w = J z_j,
+// w -= V (V^T w) twice, |w| (and, for the stand-alone step, v_{j+1} =
+// w / |w|), is 20-30 kernel launches whose arguments stay the same for a
+// given basis index j as long as the mesh, scheme, material and buffers do.
+// It is captured once per such key into a CUDA graph and replayed with one
+// launch; a change of any of them (the context's generation) drops the
+// graphs.  Captured only for the preconditioners made of plain kernel
+// launches (none, multigrid); capture happens on a private stream, so the
+// caller's stream may be the legacy default stream.
+// ---------------------------------------------------------------------
+struct ArnoldiKey {
+  uint64_t gen;
+  int kind, inner, j, with_unorm, with_scale;
+  const double *u, *Ru, *V, *Z, *w, *dh;
+  int64_t ld, dstride;
+  bool operator==(const ArnoldiKey& o) const {
+    return gen == o.gen && kind == o.kind && inner == o.inner && j == o.j &&
+           with_unorm == o.with_unorm && with_scale == o.with_scale && u == o.u && Ru == o.Ru &&
+           V == o.V && Z == o.Z && w == o.w && dh == o.dh && ld == o.ld && dstride == o.dstride;
+  }
+};
+struct GraphCache {
+  std::vector<std::pair<ArnoldiKey, cudaGraphExec_t>> items;
+  bool broken = false;  // a capture failed once: launch directly from then on
+};
+constexpr size_t kMaxGraphs = 128;
+
+static void graphs_clear(hofv_ctx* c) {
+  GraphCache* g = static_cast<GraphCache*>(c->graphs);
+  if (!g) return;
+  for (auto& it : g->items) cudaGraphExecDestroy(it.second);
+  delete g;
+  c->graphs = nullptr;
+}
+
+static int apply_pc(hofv_ctx* c, const hofv_solve_opts& o, const double* v, double* z,
+                    hofv_stats* st);
+static int arnoldi_launch(hofv_ctx* c, const hofv_solve_opts& o, const ArnoldiKey& k,
+                          hofv_stats* st) {
+  const int64_t n = c->nc * c->dim;
+  double* V = const_cast<double*>(k.V);
+  double* Z = const_cast<double*>(k.Z);
+  double* w = const_cast<double*>(k.w);
+  double* dh = const_cast<double*>(k.dh);
+  double* Vj = V + (int64_t)k.j * k.ld;
+  double* Zj = Z + (int64_t)k.j * k.ld;
+  const int nv = k.j + 1;
+  TRY(apply_pc(c, o, Vj, Zj, st));
+  if (k.with_unorm) launch_norm2(k.u, n, c->d_red, c->d_count, c->d_scal + 0, c->red_blocks, c->stream);
+  TRY(jvp_impl(c, k.u, k.Ru, Zj, w));
+  launch_dots(V, k.ld, w, nv, n, c->d_red, c->d_count, dh, c->red_blocks, c->stream, 0);
+  launch_multi_axpy(w, V, dh, nv, n, k.ld, c->stream);
+  launch_dots(V, k.ld, w, nv, n, c->d_red, c->d_count, dh + k.dstride, c->red_blocks, c->stream, 0);
+  launch_multi_axpy(w, V, dh + k.dstride, nv, n, k.ld, c->stream);
+  launch_norm2(w, n, c->d_red, c->d_count, dh + 2 * k.dstride, c->red_blocks, c->stream);
+  if (k.with_scale)
+    launch_scale_copy(V + (int64_t)(k.j + 1) * k.ld, w, dh + 2 * k.dstride, 1, n, c->stream);
+  HOFV_CUDA(c, cudaGetLastError());
+  return 0;
+}
+
+static bool graphs_enabled() {
+  const char* e = getenv("HOFV_GRAPHS");
+  return !(e && e[0] == '0');
+}
+
+static int arnoldi_device(hofv_ctx* c, const hofv_solve_opts& o, const ArnoldiKey& k,
+                          hofv_stats* st) {
+  const bool graphable = (o.precond == HOFV_PC_NONE || o.precond == HOFV_PC_AJMG) &&
+                         graphs_enabled();
+  GraphCache* g = static_cast<GraphCache*>(c->graphs);
+  if (!graphable || (g && g->broken)) return arnoldi_launch(c, o, k, st);
+  if (!g) c->graphs = g = new GraphCache();
+  for (auto& it : g->items) {
+    if (it.first == k) {
+      st->precond_applies++;
+      HOFV_CUDA(c, cudaGraphLaunch(it.second, c->stream));
+      return 0;
+    }
+  }
+  if (o.precond == HOFV_PC_AJMG) TRY(mg_ensure(c));  // synchronising set-up, outside capture
+  if (!c->cap) HOFV_CUDA(c, cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+  if (g->items.size() >= kMaxGraphs) {
+    for (auto& it : g->items) cudaGraphExecDestroy(it.second);
+    g->items.clear();
+  }
+  cudaStream_t user = c->stream;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal);
+  int rc = 0;
+  if (e == cudaSuccess) {
+    c->stream = c->cap;
+    hofv_stats dummy = *st;
+    rc = arnoldi_launch(c, o, k, &dummy);
+    c->stream = user;
+    e = cudaStreamEndCapture(c->cap, &graph);
+  }
+  if (e == cudaSuccess && rc == 0) e = cudaGraphInstantiate(&exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (e != cudaSuccess || rc != 0 || !exec) {
+    cudaGetLastError();  // clear the capture error and launch directly from now on
+    g->broken = true;
+    return arnoldi_launch(c, o, k, st);
+  }
+  g->items.emplace_back(k, exec);
+  st->precond_applies++;
+  HOFV_CUDA(c, cudaGraphLaunch(exec, c->stream));
+  return 0;
+}
+
 // host-side FGMRES state for one linear solve J x = b
 struct Fgmres {
   std::vector<double> H;   // [(m+1) x m] column-major
@@ -816,19 +942,26 @@ static int fgmres(hofv_ctx* c, const hofv_solve_opts& o, const double* u, const 
     for (; j < m && total < max_it; ++j) {
       double* Vj = V + (int64_t)j * n;
       double* Zj = Z + (int64_t)j * n;
-      TRY(apply_pc(c, oc, Vj, Zj, st));
-      TRY(jvp_impl(c, u, Ru, Zj, w));
-      st->residual_evals++;
       // (J z, z) is an exact pair of the inverse Jacobian: keep a few from
       // the Krylov space as training data for the learned preconditioner
-      if (o.record_pairs >= 2 && !cycle_gnn && (j == 0 || j == 3 || j == 8 || j == 15 || j == 24))
+      const bool rec =
+          o.record_pairs >= 2 && !cycle_gnn && (j == 0 || j == 3 || j == 8 || j == 15 || j == 24);
+      if (rec) {
+        TRY(apply_pc(c, oc, Vj, Zj, st));
+        TRY(jvp_impl(c, u, Ru, Zj, w));
         TRY(hofv_gnn_record(c, w, Zj));
-      // classical Gram-Schmidt, twice
-      launch_dots(V, n, w, j + 1, n, c->d_red, c->d_count, dh, c->red_blocks, c->stream, 0);
-      launch_multi_axpy(w, V, dh, j + 1, n, n, c->stream);
-      launch_dots(V, n, w, j + 1, n, c->d_red, c->d_count, dh + (m + 2), c->red_blocks, c->stream, 0);
-      launch_multi_axpy(w, V, dh + (m + 2), j + 1, n, n, c->stream);
-      launch_norm2(w, n, c->d_red, c->d_count, dh + 2 * (m + 2), c->red_blocks, c->stream);
+        // classical Gram-Schmidt, twice
+        launch_dots(V, n, w, j + 1, n, c->d_red, c->d_count, dh, c->red_blocks, c->stream, 0);
+        launch_multi_axpy(w, V, dh, j + 1, n, n, c->stream);
+        launch_dots(V, n, w, j + 1, n, c->d_red, c->d_count, dh + (m + 2), c->red_blocks, c->stream, 0);
+        launch_multi_axpy(w, V, dh + (m + 2), j + 1, n, n, c->stream);
+        launch_norm2(w, n, c->d_red, c->d_count, dh + 2 * (m + 2), c->red_blocks, c->stream);
+      } else {
+        const ArnoldiKey key{c->gen, oc.precond, oc.inner_iters, j, 0, 0, u, Ru, V, Z, w, dh,
+                             n, m + 2};
+        TRY(arnoldi_device(c, oc, key, st));
+      }
+      st->residual_evals++;
       HOFV_CUDA(c, cudaMemcpyAsync(F.hbuf.data(), dh, sizeof(double) * 2 * (m + 2),
                                    cudaMemcpyDeviceToHost, c->stream));
       double hn = 0.0;
@@ -1133,16 +1266,9 @@ extern "C" int hofv_arnoldi_step(hofv_ctx* c, const double* u, const double* Ru,
   o.inner_iters = inner_iters;
   hofv_stats st;
   memset(&st, 0, sizeof(st));
-  TRY(apply_pc(c, o, Vj, Zj, &st));
-  launch_norm2(u, n, c->d_red, c->d_count, c->d_scal + 0, c->red_blocks, c->stream);
-  TRY(jvp_impl(c, u, Ru, Zj, w));
   const int k = j + 1;
-  launch_dots(V, ld, w, k, n, c->d_red, c->d_count, dh, c->red_blocks, c->stream, 0);
-  launch_multi_axpy(w, V, dh, k, n, ld, c->stream);
-  launch_dots(V, ld, w, k, n, c->d_red, c->d_count, dh + k, c->red_blocks, c->stream, 0);
-  launch_multi_axpy(w, V, dh + k, k, n, ld, c->stream);
-  launch_norm2(w, n, c->d_red, c->d_count, dh + 2 * k, c->red_blocks, c->stream);
-  launch_scale_copy(V + (int64_t)(j + 1) * ld, w, dh + 2 * k, 1, n, c->stream);
+  const ArnoldiKey key{c->gen, kind, inner_iters, j, 1, 1, u, Ru, V, Z, w, dh, ld, k};
+  TRY(arnoldi_device(c, o, key, &st));
   std::vector<double> hb((size_t)(2 * k + 1));
   HOFV_CUDA(c, cudaMemcpyAsync(hb.data(), dh, sizeof(double) * hb.size(), cudaMemcpyDeviceToHost,
                                c->stream));

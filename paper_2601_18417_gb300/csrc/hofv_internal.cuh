@@ -136,6 +136,10 @@ struct hofv_ctx {
   void* gnn = nullptr;
   // ---- multigrid hierarchy of the approximate Jacobian ----
   void* mg = nullptr;
+  // ---- CUDA graphs of the device part of an Arnoldi step ----
+  uint64_t gen = 1;                 // bumped by every call that changes kernel arguments
+  void* graphs = nullptr;           // cache of instantiated graphs (api.cu)
+  cudaStream_t cap = nullptr;       // private stream used only for capturing
   double aj_rate = -1.0;            // mean per-iteration residual reduction of the last AJ cycle
   int64_t device_bytes = 0;
   std::vector<void*> allocs;
@@ -224,6 +228,8 @@ int barrier_selftest(hofv_ctx* c, int* timed_out);
 
 // ---- multigrid inner solve of the approximate Jacobian (multigrid.cu) ----
 int mg_precondition(hofv_ctx* c, int iters, const double* v, double* z);
+// builds the hierarchy if it does not exist yet (synchronises)
+int mg_ensure(hofv_ctx* c);
 int mg_info(hofv_ctx* c, int32_t* levels, int64_t* sizes, int max_sizes, int64_t* nnz,
             double* setup_s);
 void mg_release(hofv_ctx* c);

@@ -879,6 +879,8 @@ void run(hofv_ctx* c, Mg& g, int iters, const double* v, double* zout) {
 
 }  // namespace
 
+int mg_ensure(hofv_ctx* c) { return c->mg ? 0 : build(c); }
+
 int mg_precondition(hofv_ctx* c, int iters, const double* v, double* z) {
   if (!c->mg) {
     const int rc = build(c);
