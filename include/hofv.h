@@ -186,6 +186,41 @@ int hofv_set_material(hofv_ctx* ctx, int law, double mu, double lambda);
    rounding; the neo-Hookean law always uses the per-point form. */
 int hofv_set_contraction(hofv_ctx* ctx, int on);
 
+/* Inertia term for dynamics (eq. inertiaTerm; BDF2 of the appendix on time
+   integration): the residual becomes R(u) - int_Omega rho u_tt dOmega with
+   the acceleration of every cell Gauss point
+     a = (3 v^{t+1} - 4 v^t + v^{t-1}) / (2 dt),
+     v^{t+1} = (3 u^{t+1} - 4 u^t + u^{t-1}) / (2 dt),
+   and the point values extrapolated from the cell centroid with the Taylor
+   terms of the cell fit (as in eq. alphaJump).  rho is constant, so the sum
+   over the Gauss points reduces to cell averages ubar = u_P + sum_N m_N u_N
+   of the fit; one_point = 1 uses the centroid alone (ubar = u_P, one
+   integration point per cell), 0 the cell's q_per_dir^d Gauss points.
+   rho > 0 and dt > 0 enable the term; rho = 0 disables it.  The compact
+   approximate Jacobian gains -rho Omega_P 9/(4 dt^2) on its diagonal.  The
+   history starts at rest (zero) until hofv_set_history.  HOFV_ESTATE before
+   hofv_build_stencils. */
+int hofv_set_inertia(hofv_ctx* ctx, double rho, double dt, int one_point);
+
+/* History of the current time step: displacements u^t, u^{t-1} (DEVICE
+   [dim][n_cells], cell centroid values; u_tm1 NULL = u_t) and cell-average
+   velocities v^t, v^{t-1} (DEVICE [dim][n_cells] as returned by
+   hofv_bdf2_velocity; NULL = zero).  Folded into the constant source of
+   the residual.  HOFV_ESTATE unless the inertia term is enabled. */
+int hofv_set_history(hofv_ctx* ctx, const double* u_t, const double* u_tm1, const double* v_t,
+                     const double* v_tm1);
+
+/* Cell-average velocity after a solved step, v^{t+1} = (3 ubar^{t+1} -
+   4 ubar^t + ubar^{t-1}) / (2 dt) (u_tm1 NULL = u_t).  DEVICE [dim][n_cells]
+   vectors; enqueued on the context stream. */
+int hofv_bdf2_velocity(hofv_ctx* ctx, const double* u_tp1, const double* u_t, const double* u_tm1,
+                       double* v_out);
+
+/* Cell averages of the cell least-squares fit over each cell's Gauss points,
+   ubar = u_P + sum_N m_N u_N (the weights are computed on first use).
+   DEVICE [dim][n_cells]. */
+int hofv_cell_average(hofv_ctx* ctx, const double* u, double* ubar);
+
 /* Boundary data and sources, DEVICE arrays copied into the context (any may
    be NULL = zero):
      u_bq  [n_disp][Q][dim]  prescribed displacement at displacement-face Gauss points

@@ -61,6 +61,9 @@ DevMesh dev_mesh(const hofv_ctx* c) {
   m.cex = c->d_cex;
   m.cface = c->d_cface;
   m.tco = (c->contract && c->tco_valid && c->mat.law == HOFV_LAW_LINEAR) ? c->d_tco : nullptr;
+  m.mscale = c->inertia ? c->d_mscale : nullptr;
+  m.cmass = (c->inertia && !c->one_point) ? c->d_cmass : nullptr;
+  m.inert = c->d_inert;
   return m;
 }
 
@@ -118,6 +121,9 @@ static void free_built(hofv_ctx* c) {
   c->d_ubq = c->d_ubf = c->d_tbq = c->d_body = c->d_src = nullptr;
   c->d_tco = c->d_gflux = nullptr;
   c->tco_valid = false;
+  c->inertia = false;
+  c->hist_set = false;
+  c->d_cmass = c->d_mscale = c->d_inert = c->d_hist = nullptr;
   c->d_ustar = c->d_flux = c->d_w = c->d_red = c->d_scal = nullptr;
   c->d_count = nullptr;
   c->d_aj_diag = c->d_aj_off = nullptr;
@@ -152,6 +158,9 @@ int refresh_source(hofv_ctx* c) {
   if (c->contract && c->tco_valid && c->have_mat && c->mat.law == HOFV_LAW_LINEAR)
     launch_ghost_flux(dev_mesh(c), c->mat.mu, c->mat.lam, c->d_ubq, c->d_gflux, c->stream);
   launch_source(c, c->stream);
+  if (c->inertia)  // history part of the BDF2 acceleration, a constant per time step
+    launch_combine4(c->nc * c->dim, 1.0, c->d_src, 1.0, c->d_hist, 0.0, nullptr, 0.0, nullptr,
+                    c->d_src, c->stream);
   HOFV_CUDA(c, cudaGetLastError());
   HOFV_CUDA(c, cudaStreamSynchronize(c->stream));
   return 0;
@@ -599,6 +608,10 @@ int hofv_set_material(hofv_ctx* c, int law, double mu, double lambda) {
   if (c->built) {
     TRY(build_contraction(c));
     TRY(refresh_source(c));
+    if (c->inertia) {  // the inertia diagonal of the AJ is scaled by 1 / Kbar
+      TRY(run_aj_rows(c));
+      mg_drop(c);
+    }
   }
   return HOFV_OK;
 }
@@ -1338,5 +1351,105 @@ extern "C" int hofv_mg_info(hofv_ctx* c, int32_t* levels, int64_t* sizes, int32_
   if (!c || !levels || !nnz || !setup_seconds || (max_sizes > 0 && !sizes)) return HOFV_EINVAL;
   if (!c->built) return hofv::fail(c, HOFV_ESTATE, "hofv_build_stencils must come first");
   TRY(hofv::mg_info(c, levels, sizes, max_sizes, nnz, setup_seconds));
+  return HOFV_OK;
+}
+
+// ---------------------------------------------------------------------
+// inertia term with BDF2 in time (eq. inertiaTerm, App. time integration)
+// ---------------------------------------------------------------------
+// cell-average weights of the cell fit, computed on first use
+static int ensure_cmass(hofv_ctx* c) {
+  if (c->d_cmass) return 0;
+  const size_t count = (size_t)c->nctile * c->S * kTile;
+  TRY(dev_alloc(c, &c->d_cmass, count));
+  HOFV_CUDA(c, cudaMemsetAsync(c->d_cmass, 0, sizeof(double) * count, c->stream));
+  return run_cell_mass(c);
+}
+
+extern "C" int hofv_set_inertia(hofv_ctx* c, double rho, double dt, int one_point) {
+  if (!c) return HOFV_EINVAL;
+  if (!c->built) return hofv::fail(c, HOFV_ESTATE, "hofv_build_stencils must come first");
+  if (!(rho >= 0.0) || (rho > 0.0 && !(dt > 0.0)) || !std::isfinite(rho) || !std::isfinite(dt))
+    return hofv::fail(c, HOFV_EINVAL, "bad density or time step");
+  invalidate_graphs(c);
+  const int64_t n = c->nc * c->dim;
+  if (rho == 0.0) {
+    c->inertia = false;
+    c->hist_set = false;
+  } else {
+    if (!c->d_mscale) {
+      TRY(dev_alloc(c, &c->d_mscale, c->nc));
+      TRY(dev_alloc(c, &c->d_inert, n));
+      TRY(dev_alloc(c, &c->d_hist, n));
+    }
+    if (!one_point) TRY(ensure_cmass(c));
+    const double c2 = 9.0 / (4.0 * dt * dt);
+    c->rho = rho;
+    c->dt = dt;
+    c->one_point = one_point ? 1 : 0;
+    c->inertia = true;
+    c->hist_set = false;
+    launch_combine4(c->nc, -rho * c2, c->d_vol, 0.0, nullptr, 0.0, nullptr, 0.0, nullptr,
+                    c->d_mscale, c->stream);
+    HOFV_CUDA(c, cudaMemsetAsync(c->d_hist, 0, sizeof(double) * n, c->stream));
+  }
+  TRY(refresh_source(c));
+  TRY(run_aj_rows(c));
+  mg_drop(c);
+  return HOFV_OK;
+}
+
+static const double* avg_weights(hofv_ctx* c) { return c->one_point ? nullptr : c->d_cmass; }
+
+extern "C" int hofv_set_history(hofv_ctx* c, const double* u_t, const double* u_tm1,
+                                const double* v_t, const double* v_tm1) {
+  if (!c) return HOFV_EINVAL;
+  if (!c->inertia) return hofv::fail(c, HOFV_ESTATE, "hofv_set_inertia must come first");
+  if (!u_t) return hofv::fail(c, HOFV_EINVAL, "null displacement");
+  if (!u_tm1) u_tm1 = u_t;
+  DevMesh m = dev_mesh(c);
+  m.cmass = avg_weights(c);
+  const int64_t n = c->nc * c->dim;
+  const double dt = c->dt;
+  launch_cell_average(m, u_t, c->d_inert, c->stream);
+  launch_cell_average(m, u_tm1, c->d_hist, c->stream);
+  // h / c2 with h = (-12 ubar^t + 3 ubar^{t-1}) / (4 dt^2) + (-4 v^t + v^{t-1}) / (2 dt)
+  launch_combine4(n, -4.0 / 3.0, c->d_inert, 1.0 / 3.0, c->d_hist, -8.0 * dt / 9.0, v_t,
+                  2.0 * dt / 9.0, v_tm1, c->d_hist, c->stream);
+  launch_scale_rows(c->dim, c->nc, c->d_mscale, c->d_hist, c->stream);
+  c->hist_set = true;
+  TRY(refresh_source(c));
+  return HOFV_OK;
+}
+
+extern "C" int hofv_bdf2_velocity(hofv_ctx* c, const double* u_tp1, const double* u_t,
+                                  const double* u_tm1, double* v_out) {
+  if (!c) return HOFV_EINVAL;
+  if (!c->inertia) return hofv::fail(c, HOFV_ESTATE, "hofv_set_inertia must come first");
+  if (!u_tp1 || !u_t || !v_out) return hofv::fail(c, HOFV_EINVAL, "null vector");
+  if (!u_tm1) u_tm1 = u_t;
+  DevMesh m = dev_mesh(c);
+  m.cmass = avg_weights(c);
+  const int64_t n = c->nc * c->dim;
+  const double k = 1.0 / (2.0 * c->dt);
+  launch_cell_average(m, u_tp1, v_out, c->stream);
+  launch_cell_average(m, u_t, c->d_inert, c->stream);
+  launch_combine4(n, 3.0 * k, v_out, -4.0 * k, c->d_inert, 0.0, nullptr, 0.0, nullptr, v_out,
+                  c->stream);
+  launch_cell_average(m, u_tm1, c->d_inert, c->stream);
+  launch_combine4(n, 1.0, v_out, k, c->d_inert, 0.0, nullptr, 0.0, nullptr, v_out, c->stream);
+  HOFV_CUDA(c, cudaGetLastError());
+  return HOFV_OK;
+}
+
+extern "C" int hofv_cell_average(hofv_ctx* c, const double* u, double* ubar) {
+  if (!c) return HOFV_EINVAL;
+  if (!c->built) return hofv::fail(c, HOFV_ESTATE, "hofv_build_stencils must come first");
+  if (!u || !ubar) return hofv::fail(c, HOFV_EINVAL, "null vector");
+  TRY(ensure_cmass(c));
+  DevMesh m = dev_mesh(c);
+  m.cmass = c->d_cmass;
+  launch_cell_average(m, u, ubar, c->stream);
+  HOFV_CUDA(c, cudaGetLastError());
   return HOFV_OK;
 }

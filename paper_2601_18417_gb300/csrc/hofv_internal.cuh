@@ -39,6 +39,10 @@ struct DevMesh {
   const int32_t* cface;   // [nc][nlf]  +(f+1) owner, -(f+1) neighbour, 0 traction
   const double* tco;      // [nftile][S][kTile][dim][dim] contracted linear-elastic
                           // face matrices, or nullptr (then the per-point form is used)
+  // inertia (BDF2): R_P -= rho Omega_P c2 ubar_P(u), ubar_P = u_P + sum_N cmass_N u_N
+  const double* mscale;   // [nc] -rho Omega_P c2, or nullptr (no inertia term)
+  const double* cmass;    // [nctile][S][kTile] cell-average weights, or nullptr (ubar = u_P)
+  double* inert;          // [dim][nc] scratch: the inertia term of the current call
 };
 
 struct Material {
@@ -136,6 +140,15 @@ struct hofv_ctx {
   void* gnn = nullptr;
   // ---- multigrid hierarchy of the approximate Jacobian ----
   void* mg = nullptr;
+  // ---- inertia term, BDF2 in time (App. time integration) ----
+  bool inertia = false;
+  double rho = 0.0, dt = 0.0;
+  int one_point = 0;
+  double* d_cmass = nullptr;        // cell-average weights over the cell stencil
+  double* d_mscale = nullptr;       // [nc] -rho Omega c2
+  double* d_inert = nullptr;        // [dim][nc] scratch
+  double* d_hist = nullptr;         // [dim][nc] -rho Omega (history part of the acceleration)
+  bool hist_set = false;
   // ---- CUDA graphs of the device part of an Arnoldi step ----
   uint64_t gen = 1;                 // bumped by every call that changes kernel arguments
   void* graphs = nullptr;           // cache of instantiated graphs (api.cu)
@@ -181,6 +194,10 @@ int run_stencils(hofv_ctx* c, const std::vector<int64_t>& bucket_start,
                  double bs);
 int run_lsq(hofv_ctx* c);
 int run_face_aux(hofv_ctx* c);
+// cell-average weights of the cell fit over the cell's Gauss points
+int run_cell_mass(hofv_ctx* c);
+// rebuild the approximate Jacobian rows, with the inertia diagonal if enabled
+int run_aj_rows(hofv_ctx* c);
 
 // ---- residual kernels (residual.cu) ----
 // R = residual(w) where w = u (+ eps * v when v != nullptr, eps read from
@@ -198,6 +215,13 @@ void launch_tflux(const DevMesh& m, const double* tco, double alpha_kbar, const 
 // recompute the constant cell source (body, traction faces and, for the
 // contracted linear form, the ghost-node fluxes)
 int refresh_source(hofv_ctx* c);
+// ubar[j][c] = u_P + sum_N cmass_N u_N (u_P alone when m.cmass is null)
+void launch_cell_average(const DevMesh& m, const double* u, double* ubar, cudaStream_t st);
+// out = a * x + b * y + g * z + e * w (component vectors [dim][nc]; null terms skipped)
+void launch_combine4(int64_t n, double a, const double* x, double b, const double* y, double g,
+                     const double* z, double e, const double* w, double* out, cudaStream_t st);
+// out[j][c] *= s[c]
+void launch_scale_rows(int dim, int64_t nc, const double* s, double* out, cudaStream_t st);
 // out[cell] = sum over the cell's internal/displacement faces of |flux_f|
 void launch_flux_scale(const DevMesh& m, const double* flux, double* out, cudaStream_t st);
 
@@ -233,6 +257,8 @@ int mg_ensure(hofv_ctx* c);
 int mg_info(hofv_ctx* c, int32_t* levels, int64_t* sizes, int max_sizes, int64_t* nnz,
             double* setup_s);
 void mg_release(hofv_ctx* c);
+// frees the hierarchy's device memory too (the approximate Jacobian changed)
+void mg_drop(hofv_ctx* c);
 
 // ---- learned preconditioner (gnn.cu) ----
 int gnn_apply(hofv_ctx* c, const double* v, const double* z_aj, double* z);

@@ -315,6 +315,7 @@ struct Mg {
   int blocks = 0;
   double setup_s = 0.0;
   int64_t nnz_total = 0;
+  std::vector<void*> mem;     // device allocations of the hierarchy
 };
 
 Mg* get(hofv_ctx* c) { return static_cast<Mg*>(c->mg); }
@@ -785,9 +786,12 @@ int build(hofv_ctx* c) {
     A.rp[i + 1] = (int64_t)A.ci.size();
   }
   Mg* g = new Mg();
+  const size_t mark = c->allocs.size();
   const int rc = build_levels(c, g, std::move(A), dim, n);
+  g->mem.assign(c->allocs.begin() + mark, c->allocs.end());
   if (rc) {
-    delete g;  // its device buffers stay on the context's list until it is freed
+    for (void* p : g->mem) dev_free(c, p);
+    delete g;
     return rc;
   }
   g->setup_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -913,6 +917,14 @@ int mg_info(hofv_ctx* c, int32_t* levels, int64_t* sizes, int max_sizes, int64_t
 // device memory of the hierarchy is owned by the context's allocation list
 void mg_release(hofv_ctx* c) {
   delete get(c);
+  c->mg = nullptr;
+}
+
+void mg_drop(hofv_ctx* c) {
+  Mg* g = get(c);
+  if (!g) return;
+  for (void* p : g->mem) dev_free(c, p);
+  delete g;
   c->mg = nullptr;
 }
 

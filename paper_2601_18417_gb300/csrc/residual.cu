@@ -16,6 +16,8 @@
 // All arithmetic is FP64.  Every FP64 instruction of the gradient phase runs
 // with all 32 lanes busy: a tile's (face, row) pairs are laid out so that
 // consecutive threads own consecutive coefficient rows.
+#include <algorithm>
+
 #include "hofv_internal.cuh"
 
 namespace hofv {
@@ -48,6 +50,74 @@ __global__ void __launch_bounds__(32 * 2 * DIM)
 #pragma unroll
     for (int j = 0; j < DIM; ++j) ustar[(cell * NLF + (it % NLF)) * DIM + j] = w[j * nc + cell] + acc[j];
   }
+}
+
+// ---------------------------------------------------------------------
+// inertia: cell average of the cell fit over the cell's Gauss points,
+// ubar_P = u_P + sum_N cmass_N u_N (eq. inertiaTerm with the Taylor
+// extrapolation of eq. alphaJump; u_P alone for one point per cell), and,
+// scaled, the u-dependent part -rho Omega_P c2 ubar_P of the BDF2 term
+// ---------------------------------------------------------------------
+template <int DIM, bool SCALE>
+__global__ void k_cell_avg(DevMesh m, const double* __restrict__ w, double* __restrict__ out) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= m.nc) return;
+  const int64_t nc = m.nc;
+  double acc[DIM];
+#pragma unroll
+  for (int j = 0; j < DIM; ++j) acc[j] = w[j * nc + c];
+  if (m.cmass) {
+    const int64_t tile = c / kTile, ci = c % kTile;
+    const int32_t* __restrict__ st = m.cst + tile * m.S * kTile + ci;
+    const double* __restrict__ e = m.cmass + tile * m.S * kTile + ci;
+    for (int n = 0; n < m.S; ++n) {
+      const int32_t id = __ldg(st + n * kTile);
+      const double en = __ldg(e + n * kTile);
+#pragma unroll
+      for (int j = 0; j < DIM; ++j) acc[j] = fma(en, __ldg(w + j * nc + id), acc[j]);
+    }
+  }
+  const double sc = SCALE ? m.mscale[c] : 1.0;
+#pragma unroll
+  for (int j = 0; j < DIM; ++j) out[j * nc + c] = SCALE ? sc * acc[j] : acc[j];
+}
+
+void launch_cell_average(const DevMesh& m, const double* u, double* ubar, cudaStream_t st) {
+  const unsigned g = (unsigned)((m.nc + 127) / 128);
+  if (m.dim == 2)
+    k_cell_avg<2, false><<<g, 128, 0, st>>>(m, u, ubar);
+  else
+    k_cell_avg<3, false><<<g, 128, 0, st>>>(m, u, ubar);
+}
+
+__global__ void k_combine4(int64_t n, double a, const double* __restrict__ x, double b,
+                           const double* __restrict__ y, double g, const double* __restrict__ z,
+                           double e, const double* __restrict__ w, double* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    if (x) s += a * x[i];
+    if (y) s += b * y[i];
+    if (z) s += g * z[i];
+    if (w) s += e * w[i];
+    out[i] = s;
+  }
+}
+
+void launch_combine4(int64_t n, double a, const double* x, double b, const double* y, double g,
+                     const double* z, double e, const double* w, double* out, cudaStream_t st) {
+  k_combine4<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, st>>>(n, a, x, b, y, g,
+                                                                                 z, e, w, out);
+}
+
+__global__ void k_scale_rows(int dim, int64_t nc, const double* __restrict__ s, double* out) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  for (int j = 0; j < dim; ++j) out[j * nc + c] *= s[c];
+}
+
+void launch_scale_rows(int dim, int64_t nc, const double* s, double* out, cudaStream_t st) {
+  k_scale_rows<<<(unsigned)((nc + 255) / 256), 256, 0, st>>>(dim, nc, s, out);
 }
 
 // ---------------------------------------------------------------------
@@ -230,6 +300,10 @@ __global__ void k_cell(DevMesh m, const double* __restrict__ flux, const double*
       r[j] = code > 0 ? r[j] + v : r[j] - v;
     }
   }
+  if (m.mscale) {
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) r[j] += m.inert[j * m.nc + c];
+  }
   if (R0) {
     const double ie = 1.0 / d_eps[0];
 #pragma unroll
@@ -265,6 +339,8 @@ static void residual_impl(const DevMesh& m, const Material& mat, const double* w
     }
   }
   if (ev) cudaEventRecord(ev[2], st);
+  if (m.mscale)
+    k_cell_avg<DIM, true><<<(unsigned)((m.nc + 127) / 128), 128, 0, st>>>(m, w, m.inert);
   k_cell<DIM><<<(unsigned)((m.nc + 255) / 256), 256, 0, st>>>(m, flux, src, R0, d_eps, out);
   if (ev) cudaEventRecord(ev[3], st);
 }

@@ -214,6 +214,12 @@ struct LsqParams {
   double* cex;
   unsigned long long* cond_bits;
   int* status;
+  // cell averages over the cell Gauss points (inertia term)
+  int QC;
+  const double* cqx;   // [nc][QC][3]
+  const double* cqw;   // [nc][QC]
+  const double* vol;   // [nc]
+  double* cmass;       // tiled like cst
 };
 
 // Factorise the system of one reference point.  Each lane owns rows
@@ -409,7 +415,46 @@ __global__ void k_lsq_cells(LsqParams P) {
   }
 }
 
-int run_lsq(hofv_ctx* c) {
+
+// Cell-average weights of the cell fit: the Taylor extrapolation of
+// eq. (alphaJump) from the centroid to every cell Gauss point, averaged with
+// the Gauss weights, ubar_P = u_P + sum_N cmass_N u_N (eq. inertiaTerm).
+__global__ void k_lsq_cell_mass(LsqParams P) {
+  extern __shared__ double sm[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int per = P.Nt * P.NR + 2 * kMaxNt;
+  double* A = sm + wib * per;
+  double* v0 = A + P.Nt * P.NR;
+  double* beta = v0 + kMaxNt;
+  const int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
+  if (c >= P.nc) return;
+  const int64_t tile = c / kTile, ci = c % kTile;
+  int32_t nodes[kMaxS];
+  for (int n = 0; n < P.S; ++n) nodes[n] = P.cst[(tile * P.S + n) * kTile + ci];
+  double xt[3];
+  for (int a = 0; a < 3; ++a) xt[a] = P.xc[3 * c + a];
+  double sw[4];
+  const double h = lsq_factor(P, xt, nodes, P.S, A, v0, beta, sw, lane);
+  double g[kMaxNt];
+  for (int t = 0; t < P.Nt; ++t) g[t] = 0.0;
+  const double iv = 1.0 / P.vol[c];
+  for (int q = 0; q < P.QC; ++q) {
+    double X[3] = {0, 0, 0}, b[kMaxNt];
+    for (int a = 0; a < P.dim; ++a) X[a] = (P.cqx[(c * P.QC + q) * 3 + a] - xt[a]) / h;
+    taylor_basis(P.dim, P.p, X, b);
+    const double wq = P.cqw[c * P.QC + q] * iv;
+    for (int t = 1; t < P.Nt; ++t) g[t] = fma(wq, b[t], g[t]);  // u_P enters directly
+  }
+  double z[4];
+  lsq_functional(P, P.S, A, v0, beta, sw, g, z, lane);
+  const int nown = (P.NR + 31) / 32;
+  for (int o = 0; o < nown; ++o) {
+    const int r = lane + 32 * o;
+    if (r < P.S) P.cmass[(tile * P.S + r) * kTile + ci] = z[o];
+  }
+}
+
+static LsqParams lsq_params(hofv_ctx* c) {
   LsqParams P;
   P.dim = c->dim;
   P.p = c->p;
@@ -432,13 +477,25 @@ int run_lsq(hofv_ctx* c) {
   P.fco = c->d_fco;
   P.gco = c->d_gco;
   P.cex = c->d_cex;
+  P.cf = c->d_cf;
+  P.QC = c->QC;
+  P.cqx = c->d_cqx;
+  P.cqw = c->d_cqw;
+  P.vol = c->d_vol;
+  P.cmass = c->d_cmass;
+  P.cond_bits = nullptr;
+  P.status = nullptr;
+  return P;
+}
+
+int run_lsq(hofv_ctx* c) {
+  LsqParams P = lsq_params(c);
   unsigned long long* d_cond = nullptr;
   int* d_status = nullptr;
   HOFV_CUDA(c, cudaMalloc(&d_cond, sizeof(unsigned long long)));
   HOFV_CUDA(c, cudaMalloc(&d_status, sizeof(int)));
   HOFV_CUDA(c, cudaMemsetAsync(d_cond, 0, sizeof(unsigned long long), c->stream));
   HOFV_CUDA(c, cudaMemsetAsync(d_status, 0, sizeof(int), c->stream));
-  P.cf = c->d_cf;
   P.cond_bits = d_cond;
   P.status = d_status;
   const int warps = 4;
@@ -535,6 +592,31 @@ __global__ void k_aj_rows(int nlf, int64_t nc, const int32_t* __restrict__ cface
   invd32[c] = (float)(-1.0 / dg);
 }
 
+int run_cell_mass(hofv_ctx* c) {
+  LsqParams P = lsq_params(c);
+  const int warps = 4;
+  const size_t smem = sizeof(double) * warps * (P.Nt * P.NR + 2 * kMaxNt);
+  HOFV_CUDA(c, cudaFuncSetAttribute(k_lsq_cell_mass, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
+  k_lsq_cell_mass<<<(unsigned)((c->nc + warps - 1) / warps), 32 * warps, smem, c->stream>>>(P);
+  HOFV_CUDA(c, cudaGetLastError());
+  HOFV_CUDA(c, cudaStreamSynchronize(c->stream));
+  return 0;
+}
+
+// inertia on the approximate Jacobian's diagonal: -rho Omega c2 / Kbar
+// (the operator is stored with Kbar = 1)
+__global__ void k_aj_mass(int64_t nc, const double* __restrict__ mscale, double inv_kbar,
+                          double* diag, float* diag32, double* invd, float* invd32) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  const double dg = diag[c] + mscale[c] * inv_kbar;
+  diag[c] = dg;
+  diag32[c] = (float)dg;
+  invd[c] = -1.0 / dg;
+  invd32[c] = (float)(-1.0 / dg);
+}
+
 int run_face_aux(hofv_ctx* c) {
   const int T = 128;
   if (c->nfid > 0) {
@@ -543,10 +625,21 @@ int run_face_aux(hofv_ctx* c) {
         c->d_nrm, c->d_gam, c->d_fstar, c->d_fstab);
     HOFV_CUDA(c, cudaGetLastError());
   }
+  return run_aj_rows(c);
+}
+
+int run_aj_rows(hofv_ctx* c) {
+  const int T = 128;
   k_aj_rows<<<(unsigned)((c->nc + T - 1) / T), T, 0, c->stream>>>(
       c->nlf, c->nc, c->d_cface, c->d_fown, c->d_fnei, c->nfi, c->d_fstab, c->d_aj_diag,
       c->d_aj_col, c->d_aj_off, c->d_aj_diag32, c->d_aj_off32, c->d_aj_invd, c->d_aj_invd32);
   HOFV_CUDA(c, cudaGetLastError());
+  if (c->inertia && c->have_mat) {
+    k_aj_mass<<<(unsigned)((c->nc + T - 1) / T), T, 0, c->stream>>>(
+        c->nc, c->d_mscale, 1.0 / c->mat.kbar, c->d_aj_diag, c->d_aj_diag32, c->d_aj_invd,
+        c->d_aj_invd32);
+    HOFV_CUDA(c, cudaGetLastError());
+  }
   HOFV_CUDA(c, cudaStreamSynchronize(c->stream));
   return 0;
 }

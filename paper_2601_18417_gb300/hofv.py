@@ -102,6 +102,10 @@ SIGNATURES = {
     "hofv_force_scale": (_I, [_P, _P, C.POINTER(_D)]),
     "hofv_set_contraction": (_I, [_P, _I]),
     "hofv_selftest_barrier": (_I, [_P, C.POINTER(C.c_int32)]),
+    "hofv_set_inertia": (_I, [_P, C.c_double, C.c_double, _I]),
+    "hofv_set_history": (_I, [_P, _P, _P, _P, _P]),
+    "hofv_bdf2_velocity": (_I, [_P, _P, _P, _P, _P]),
+    "hofv_cell_average": (_I, [_P, _P, _P]),
     "hofv_mg_info": (_I, [_P, C.POINTER(C.c_int32), _P, C.c_int32, C.POINTER(C.c_int64),
                           C.POINTER(C.c_double)]),
     "hofv_gnn_init": (_I, [_P, C.c_uint64, _D]),
@@ -224,6 +228,21 @@ class Context:
 
     def set_material(self, law, mu, lam):
         return self._check(self._L.hofv_set_material(self.h, law, mu, lam))
+
+    # ---- dynamics (BDF2 inertia term) ------------------------------------
+    def set_inertia(self, rho, dt, one_point=False):
+        return self._check(self._L.hofv_set_inertia(self.h, rho, dt, int(bool(one_point))))
+
+    def set_history(self, u_t, u_tm1=None, v_t=None, v_tm1=None):
+        args = [_dev(t) for t in (u_t, u_tm1, v_t, v_tm1)]
+        return self._check(self._L.hofv_set_history(self.h, *[_ptr(a) for a in args]))
+
+    def bdf2_velocity(self, u_tp1, u_t, u_tm1, v_out):
+        return self._check(self._L.hofv_bdf2_velocity(self.h, _ptr(_dev(u_tp1)), _ptr(_dev(u_t)),
+                                                      _ptr(_dev(u_tm1)), _ptr(_dev(v_out))))
+
+    def cell_average(self, u, ubar):
+        return self._check(self._L.hofv_cell_average(self.h, _ptr(_dev(u)), _ptr(_dev(ubar))))
 
     def mg_info(self):
         """Multigrid hierarchy of PC_AJMG: level sizes, non-zeros, set-up s."""
