@@ -673,6 +673,61 @@ def run_pc_sweep(args):
     print(json.dumps(out))
 
 
+def run_dynamics(args):
+    """Implicit dynamics with the BDF2 inertia term: the neo-Hookean block
+    (or any block workload) starts at rest and its top face is driven down
+    along the load schedule, one BDF2 time step per load increment; each step
+    is a Newton-Krylov solve to 1e-8 from a predictor.  Reported per
+    preconditioner: wall time per step and Newton / Krylov counts."""
+    import torch
+
+    from paper_2601_18417_gb300 import build as B
+    from paper_2601_18417_gb300 import hofv
+    from paper_2601_18417_gb300 import inputs as I
+    B.build()
+    wl, mesh, ctx, lay, setup_s, _, _ = build_workload(args.workload)
+    if wl.problem != "block":
+        raise SystemExit("--dynamics needs a block workload")
+    d, nc = wl.dim, lay.n_cells
+    dev = torch.device("cuda", 0)
+    T = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)  # noqa
+    xq = ctx.get_points(hofv.PTS_DISP_QP)
+    xb = ctx.get_points(hofv.PTS_DISP_CENTRE)
+    on_top = np.abs(xb[:, d - 1] - 1.0) < 1e-9
+    xc = T(ctx.get_points(hofv.PTS_CELL_CENTROID))
+    out = {"mode": "dynamics", "workload": wl.name, "cells": nc, "rho": args.rho, "dt": args.dt,
+           "time_steps": args.dyn_steps, "setup_s": setup_s, "variants": {}}
+    for label, pc, inner in (("fp32_aj_mg", hofv.PC_AJMG, 2), ("fp32_aj", hofv.PC_AJ32, INNER_ITERS)):
+        ctx.set_inertia(args.rho, args.dt, 0)
+        u_m1 = torch.zeros((d, nc), dtype=torch.float64, device=dev)
+        u_0 = torch.zeros_like(u_m1)
+        v_m1 = torch.zeros_like(u_m1)
+        v_0 = torch.zeros_like(u_m1)
+        stats = []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for s in range(1, args.dyn_steps + 1):
+            top = I.block_top_displacement(s, wl.load_steps, d)
+            ctx.set_bc(T(np.where(on_top[:, None, None], top, 0.0) * np.ones_like(xq)),
+                       T(np.where(on_top[:, None], top, 0.0) * np.ones_like(xb)), None, None)
+            ctx.set_history(u_0, u_m1, v_0, v_m1)
+            inc = T(I.block_top_displacement(1, wl.load_steps, d))
+            u = u_0 + inc[:, None] * xc[:, d - 1][None, :]
+            stats.append(ctx.newton_solve(u, rtol=1e-8, precond=pc, inner_iters=inner,
+                                          restart=30, max_krylov=3000))
+            v = torch.empty_like(u)
+            ctx.bdf2_velocity(u, u_0, u_m1, v)
+            u_m1, u_0, v_m1, v_0 = u_0, u, v_0, v
+        torch.cuda.synchronize()
+        res = summarize(stats, time.perf_counter() - t0)
+        res["seconds_per_step"] = res["seconds"] / args.dyn_steps
+        res["max_velocity"] = float(v_0.abs().max())
+        out["variants"][label] = res
+        print(f"[dynamics] {label}: {res}", file=sys.stderr, flush=True)
+    ctx.close()
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -694,6 +749,11 @@ def main():
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--record", type=int, default=2, help="1: Newton pairs, 2: + Krylov pairs")
+    ap.add_argument("--dynamics", action="store_true",
+                    help="implicit BDF2 dynamics of a block workload")
+    ap.add_argument("--rho", type=float, default=1000.0)
+    ap.add_argument("--dt", type=float, default=1e-3)
+    ap.add_argument("--dyn-steps", type=int, default=10)
     ap.add_argument("--pc-sweep", action="store_true",
                     help="time each preconditioner's apply and solve on --workload")
     ap.add_argument("--budget-s", type=float, default=420.0,
@@ -707,6 +767,8 @@ def main():
         run_learned(args)
     elif args.pc_sweep:
         run_pc_sweep(args)
+    elif args.dynamics:
+        run_dynamics(args)
     else:
         run_hofv(args)
 
