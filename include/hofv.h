@@ -58,6 +58,7 @@ extern "C" {
 #define HOFV_PC_AJ32 1   /* same operator stored and applied in FP32 */
 #define HOFV_PC_GNN 2    /* learned graph network on top of AJ32 */
 #define HOFV_PC_AJMG 3   /* same operator (FP32), CG with an algebraic-multigrid V-cycle */
+#define HOFV_PC_NEJ 4    /* near-exact Jacobian (linear law), inner GMRES with AJMG */
 
 /* point sets for hofv_get_points */
 #define HOFV_PTS_CELL_CENTROID 0   /* [n_cells][dim] */
@@ -186,6 +187,16 @@ int hofv_set_material(hofv_ctx* ctx, int law, double mu, double lambda);
    rounding; the neo-Hookean law always uses the per-point form. */
 int hofv_set_contraction(hofv_ctx* ctx, int on);
 
+/* y = J_NEJ x with the near-exact Jacobian of the appendix on the
+   near-exact-Jacobian preconditioner: the Jacobian of the face fluxes of
+   the linear-elastic law without the stabilisation term (ghost-node and
+   traction contributions are constants and drop out).  Assembled on first
+   use (and after a material change) as block CSR with d x d FP32 blocks,
+   columns = the union of each cell's face stencils; products accumulate in
+   FP32.  x, y: DEVICE [dim][n_cells].  HOFV_ENOTSUP for the neo-Hookean
+   law. */
+int hofv_nej_apply(hofv_ctx* ctx, const double* x, double* y);
+
 /* Inertia term for dynamics (eq. inertiaTerm; BDF2 of the appendix on time
    integration): the residual becomes R(u) - int_Omega rho u_tt dOmega with
    the acceleration of every cell Gauss point
@@ -255,7 +266,10 @@ int hofv_jvp(hofv_ctx* ctx, const double* u, const double* Ru, const double* v,
    one V-cycle of smoothed-aggregation multigrid on P (FP32) when
    inner_iters <= 1, else runs `inner_iters` CG iterations preconditioned by
    that V-cycle (hierarchy built on first use, once per mesh; the paper
-   leaves the inner solve of P to its linear-algebra library); HOFV_PC_GNN adds the learned correction (needs hofv_gnn_load or
+   leaves the inner solve of P to its linear-algebra library); HOFV_PC_NEJ
+   approximates the inverse of the near-exact Jacobian instead (linear law
+   only, HOFV_ENOTSUP otherwise; see hofv_nej_apply) by `inner_iters` GMRES
+   iterations right-preconditioned by one AJMG V-cycle; HOFV_PC_GNN adds the learned correction (needs hofv_gnn_load or
    hofv_gnn_train first).  v, z: DEVICE [dim][n_cells]. */
 int hofv_precondition(hofv_ctx* ctx, int kind, int inner_iters, const double* v, double* z);
 

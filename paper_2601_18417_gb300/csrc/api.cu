@@ -109,6 +109,7 @@ static void free_built(hofv_ctx* c) {
   invalidate_graphs(c);
   gnn_release(c);
   mg_release(c);
+  nej_release(c);
   for (void* p : c->allocs) cudaFree(p);
   c->allocs.clear();
   c->device_bytes = 0;
@@ -147,6 +148,21 @@ static int build_contraction(hofv_ctx* c) {
   if (!c->d_gflux) TRY(dev_alloc(c, &c->d_gflux, std::max<int64_t>(c->nfd, 1) * c->dim));
   DevMesh m = dev_mesh(c);
   launch_build_tco(m, c->mat.mu, c->mat.lam, c->d_tco, c->stream);
+  HOFV_CUDA(c, cudaGetLastError());
+  HOFV_CUDA(c, cudaStreamSynchronize(c->stream));
+  c->tco_valid = true;
+  return 0;
+}
+
+// the contracted matrices for the current material, whether or not the
+// residual uses the contracted form (the near-exact Jacobian is made of them)
+int ensure_tco(hofv_ctx* c) {
+  if (c->tco_valid) return 0;
+  if (!c->have_mat || c->mat.law != HOFV_LAW_LINEAR || !c->built)
+    return fail(c, HOFV_ESTATE, "linear-elastic material and stencils must be set first");
+  const int64_t count = std::max<int64_t>(c->nftile, 1) * c->S * kTile * c->dim * c->dim;
+  if (!c->d_tco) TRY(dev_alloc(c, &c->d_tco, count));
+  launch_build_tco(dev_mesh(c), c->mat.mu, c->mat.lam, c->d_tco, c->stream);
   HOFV_CUDA(c, cudaGetLastError());
   HOFV_CUDA(c, cudaStreamSynchronize(c->stream));
   c->tco_valid = true;
@@ -723,6 +739,8 @@ int hofv_precondition(hofv_ctx* c, int kind, int iters, const double* v, double*
       return aj_precondition(c, kind, iters, v, z);
     case HOFV_PC_AJMG:
       return mg_precondition(c, iters, v, z);
+    case HOFV_PC_NEJ:
+      return nej_precondition(c, iters, v, z);
     case HOFV_PC_GNN: {
       if (!c->gnn) return fail(c, HOFV_ESTATE, "no learned preconditioner loaded");
       TRY(aj_precondition(c, HOFV_PC_AJ32, iters, v, z));
@@ -901,6 +919,7 @@ static int apply_pc(hofv_ctx* c, const hofv_solve_opts& o, const double* v, doub
     return gnn_apply(c, v, z, z);
   }
   if (o.precond == HOFV_PC_AJMG) return mg_precondition(c, o.inner_iters, v, z);
+  if (o.precond == HOFV_PC_NEJ) return nej_precondition(c, o.inner_iters, v, z);
   return aj_precondition(c, o.precond == HOFV_PC_AJ64 ? HOFV_PC_AJ64 : HOFV_PC_AJ32, o.inner_iters, v,
                          z);
 }
@@ -1065,7 +1084,7 @@ extern "C" int hofv_newton_solve(hofv_ctx* c, double* u, const hofv_solve_opts* 
   hofv_default_opts(&o);
   if (opts) o = *opts;
   if (o.restart < 1 || o.restart > 100 || o.max_krylov < 1 || o.max_newton < 0 ||
-      o.precond < HOFV_PC_NONE || o.precond > HOFV_PC_AJMG)
+      o.precond < HOFV_PC_NONE || o.precond > HOFV_PC_NEJ)
     return fail(c, HOFV_EINVAL, "bad solver options");
   hofv_stats st;
   memset(&st, 0, sizeof(st));
@@ -1265,7 +1284,7 @@ extern "C" int hofv_arnoldi_step(hofv_ctx* c, const double* u, const double* Ru,
   const int64_t n = c->nc * c->dim;
   if (j < 0 || j > 99 || ld < n) return fail(c, HOFV_EINVAL, "bad Arnoldi index or leading dimension");
   if (kind != HOFV_PC_NONE && kind != HOFV_PC_AJ64 && kind != HOFV_PC_AJ32 && kind != HOFV_PC_GNN &&
-      kind != HOFV_PC_AJMG)
+      kind != HOFV_PC_AJMG && kind != HOFV_PC_NEJ)
     return fail(c, HOFV_EINVAL, "unknown preconditioner");
   if (kind == HOFV_PC_GNN && !c->gnn) return fail(c, HOFV_ESTATE, "no learned preconditioner loaded");
   TRY(ensure_krylov(c, 1));
@@ -1451,5 +1470,13 @@ extern "C" int hofv_cell_average(hofv_ctx* c, const double* u, double* ubar) {
   m.cmass = c->d_cmass;
   launch_cell_average(m, u, ubar, c->stream);
   HOFV_CUDA(c, cudaGetLastError());
+  return HOFV_OK;
+}
+
+extern "C" int hofv_nej_apply(hofv_ctx* c, const double* x, double* y) {
+  if (!c) return HOFV_EINVAL;
+  if (!c->built || !c->have_mat) return hofv::fail(c, HOFV_ESTATE, "stencils and material must be set first");
+  if (!x || !y) return hofv::fail(c, HOFV_EINVAL, "null vector");
+  TRY(hofv::nej_apply(c, x, y));
   return HOFV_OK;
 }

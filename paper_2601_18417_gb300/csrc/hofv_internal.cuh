@@ -149,6 +149,8 @@ struct hofv_ctx {
   double* d_inert = nullptr;        // [dim][nc] scratch
   double* d_hist = nullptr;         // [dim][nc] -rho Omega (history part of the acceleration)
   bool hist_set = false;
+  // ---- near-exact Jacobian preconditioner (nej.cu) ----
+  void* nej = nullptr;
   // ---- CUDA graphs of the device part of an Arnoldi step ----
   uint64_t gen = 1;                 // bumped by every call that changes kernel arguments
   void* graphs = nullptr;           // cache of instantiated graphs (api.cu)
@@ -259,6 +261,14 @@ int mg_info(hofv_ctx* c, int32_t* levels, int64_t* sizes, int max_sizes, int64_t
 void mg_release(hofv_ctx* c);
 // frees the hierarchy's device memory too (the approximate Jacobian changed)
 void mg_drop(hofv_ctx* c);
+
+// ---- near-exact Jacobian (nej.cu) ----
+// contracted linear-elastic matrices for the current material (api.cu)
+int ensure_tco(hofv_ctx* c);
+int nej_ensure(hofv_ctx* c);
+int nej_apply(hofv_ctx* c, const double* x, double* y);
+int nej_precondition(hofv_ctx* c, int iters, const double* v, double* z);
+void nej_release(hofv_ctx* c);
 
 // ---- learned preconditioner (gnn.cu) ----
 int gnn_apply(hofv_ctx* c, const double* v, const double* z_aj, double* z);

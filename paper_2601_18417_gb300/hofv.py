@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libhofv.so")
 OK, WNOTCONV = 0, 1
 EINVAL, ENOMEM, ECUDA, EILLCOND, ENAN, ENOTSUP, ESTATE = -1, -2, -3, -4, -5, -6, -7
 LAW_LINEAR, LAW_NEOHOOKEAN = 0, 1
-PC_NONE, PC_AJ64, PC_AJ32, PC_GNN, PC_AJMG = -1, 0, 1, 2, 3
+PC_NONE, PC_AJ64, PC_AJ32, PC_GNN, PC_AJMG, PC_NEJ = -1, 0, 1, 2, 3, 4
 PTS_CELL_CENTROID, PTS_DISP_QP, PTS_DISP_CENTRE, PTS_TRAC_QP, PTS_CELL_QP = 0, 1, 2, 3, 4
 PTS_FACE_CENTRE, PTS_FACE_QP, PTS_FACE_AREA, PTS_CELL_VOLUME = 5, 6, 7, 8
 
@@ -102,6 +102,7 @@ SIGNATURES = {
     "hofv_force_scale": (_I, [_P, _P, C.POINTER(_D)]),
     "hofv_set_contraction": (_I, [_P, _I]),
     "hofv_selftest_barrier": (_I, [_P, C.POINTER(C.c_int32)]),
+    "hofv_nej_apply": (_I, [_P, _P, _P]),
     "hofv_set_inertia": (_I, [_P, C.c_double, C.c_double, _I]),
     "hofv_set_history": (_I, [_P, _P, _P, _P, _P]),
     "hofv_bdf2_velocity": (_I, [_P, _P, _P, _P, _P]),
@@ -228,6 +229,10 @@ class Context:
 
     def set_material(self, law, mu, lam):
         return self._check(self._L.hofv_set_material(self.h, law, mu, lam))
+
+    def nej_apply(self, x, y):
+        """y = near-exact Jacobian times x (linear law)."""
+        return self._check(self._L.hofv_nej_apply(self.h, _ptr(_dev(x)), _ptr(_dev(y))))
 
     # ---- dynamics (BDF2 inertia term) ------------------------------------
     def set_inertia(self, rho, dt, one_point=False):
