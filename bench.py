@@ -411,7 +411,10 @@ def run_hofv(args):
                                    ("fp32_aj", hofv.PC_AJ32, INNER_ITERS),
                                    ("fp32_aj_inner40", hofv.PC_AJ32, 40),
                                    ("fp32_aj_mg", hofv.PC_AJMG, MG_INNER),
-                                   ("fp32_aj_mg2", hofv.PC_AJMG, 2)):
+                                   ("fp32_aj_mg2", hofv.PC_AJMG, 2),
+                                   ("fp32_nej6", hofv.PC_NEJ, 6)):
+            if kind == hofv.PC_NEJ and wl.law != 0:
+                continue
             uu = torch.zeros_like(u)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -657,7 +660,9 @@ def run_pc_sweep(args):
     ctx.newton_solve(torch.zeros((d, nc), dtype=torch.float64, device="cuda:0"), max_newton=1,
                      max_krylov=2, restart=30)
     for kind, its in ((hofv.PC_AJ64, INNER_ITERS), (hofv.PC_AJ32, INNER_ITERS),
-                      (hofv.PC_AJMG, 1), (hofv.PC_AJMG, 2)):
+                      (hofv.PC_AJMG, 1), (hofv.PC_AJMG, 2), (hofv.PC_NEJ, 4), (hofv.PC_NEJ, 8)):
+        if kind == hofv.PC_NEJ and wl.law != 0:
+            continue
         opts = dict(rtol=1e-8, precond=kind, inner_iters=its, restart=30, max_krylov=3000)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
