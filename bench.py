@@ -101,7 +101,7 @@ def build_workload(name, device=0):
     from paper_2601_18417_gb300 import hofv
     from paper_2601_18417_gb300 import inputs as I
     wl = I.WORKLOADS[name]
-    mesh = I.structured_mesh(wl.dim, wl.n, jitter=wl.jitter, seed=wl.mesh_seed)
+    mesh = I.structured_mesh(wl.dim, wl.n, length=wl.length, jitter=wl.jitter, seed=wl.mesh_seed)
     tags = I.side_tags(wl.problem, wl.dim)[mesh.bface_side]
     ctx = hofv.Context(device)
     ctx.set_mesh(mesh, tags)
@@ -647,7 +647,7 @@ def run_pc_sweep(args):
     vh = v.cpu().numpy()
     s = torch.cuda.current_stream()
     out = {"mode": "pc-sweep", "workload": wl.name, "cells": nc, "multigrid": mg, "apply": [],
-           "solve": []}
+           "solve": [], "rtol": args.rtol, "setup_s": setup_s}
     for kind, its in ((hofv.PC_AJ64, 20), (hofv.PC_AJ32, 20), (hofv.PC_AJ32, 40),
                       (hofv.PC_AJMG, 1), (hofv.PC_AJMG, 2), (hofv.PC_AJMG, 4)):
         for _ in range(3):
@@ -676,7 +676,7 @@ def run_pc_sweep(args):
                       (hofv.PC_AJMG, 1), (hofv.PC_AJMG, 2), (hofv.PC_NEJ, 4), (hofv.PC_NEJ, 8)):
         if kind == hofv.PC_NEJ and wl.law != 0:
             continue
-        opts = dict(rtol=1e-8, precond=kind, inner_iters=its, restart=30, max_krylov=3000)
+        opts = dict(rtol=args.rtol, precond=kind, inner_iters=its, restart=30, max_krylov=3000)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         if wl.law == 0:
@@ -772,6 +772,8 @@ def main():
     ap.add_argument("--rho", type=float, default=1000.0)
     ap.add_argument("--dt", type=float, default=1e-3)
     ap.add_argument("--dyn-steps", type=int, default=10)
+    ap.add_argument("--rtol", type=float, default=1e-8,
+                    help="relative residual tolerance of the --pc-sweep solves")
     ap.add_argument("--pc-sweep", action="store_true",
                     help="time each preconditioner's apply and solve on --workload")
     ap.add_argument("--budget-s", type=float, default=420.0,

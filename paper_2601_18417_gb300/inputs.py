@@ -422,6 +422,7 @@ class Workload:
     load_steps: int = 1
     alpha: float = 0.1
     k_weight: float = 6.0
+    length: float = 1.0      # edge of the square / cube
 
     @property
     def n_cells(self) -> int:
@@ -454,6 +455,10 @@ WORKLOADS = {
                               "mms-trig3d", 1239),
     "hex32j-p3-nh": Workload("hex32j-p3-nh", 3, 32, 3, 65, 3, 0.20, 1, 1e6, 4e6, "block",
                              1240, load_steps=10),
+    # the paper's largest regular-hex manufactured-solution mesh (Table 1): 45^3 hexes on a
+    # 0.2 m cube, E=200 GPa, nu=0.3, cubic LSQ, 3x3 Gauss pts/face
+    "hex45-p3-trig": Workload("hex45-p3-trig", 3, 45, 3, 65, 3, 0.0, 0, _MU_S, _LAM_S,
+                              "mms-trig3d", 1241, length=0.2),
     # 3-D neo-Hookean block mu=1 MPa lambda=4 MPa, 64^3 hexes jittered 20 %, quadratic LSQ
     "hex64j-p2-nh": Workload("hex64j-p2-nh", 3, 64, 2, 55, 2, 0.20, 1, 1e6, 4e6, "block",
                              1237, load_steps=10),
