@@ -341,7 +341,8 @@ __device__ void record_cond(const LsqParams& P, const double* A, int lane) {
     mn = fmin(mn, r);
   }
   const double est = mn > 0.0 ? (mx / mn) * (mx / mn) : 1e300;
-  if (!(mn > 0.0)) atomicExch(P.status, 2);
+  // rank-deficient stencil (e.g. collinear centroids): cond(M) above ~1e24
+  if (!(mn > 1e-12 * mx)) atomicExch(P.status, 2);
   atomicMax(P.cond_bits, (unsigned long long)__double_as_longlong(est));
 }
 

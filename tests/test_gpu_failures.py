@@ -121,6 +121,27 @@ def test_bad_scheme_and_material_parameters():
     ctx.close()
 
 
+def test_degenerate_stencil_is_reported():
+    """A one-cell-thick strip has collinear centroids: the least-squares fit
+    cannot determine derivatives across it, and set-up must say so."""
+    n = 24
+    xs = np.arange(n + 1) / n
+    xyz = np.array([[x, y] for y in (0.0, 1.0 / n) for x in xs])
+    top = n + 1
+    cells = np.array([[i, i + 1, i + 1 + top, i + top] for i in range(n)], np.int64)
+    bfaces = ([[i, i + 1] for i in range(n)] + [[i + 1 + top, i + top] for i in range(n)]
+              + [[top, 0], [n, n + top]])
+    side = [2] * n + [3] * n + [0, 1]
+    mesh = I.Mesh(2, n, xyz, cells, np.array(bfaces, np.int64), np.array(side, np.int64))
+    ctx = hofv.Context(0)
+    ctx.set_mesh(mesh, np.zeros(len(bfaces), np.int32))
+    ctx.set_scheme(1, 4, 1)
+    with pytest.raises(hofv.HofvError) as e:
+        ctx.build_stencils()
+    assert _code(e) == hofv.EILLCOND
+    ctx.close()
+
+
 def test_non_finite_state_is_reported_and_leaves_the_context_usable():
     import torch
     pb = _problem()
