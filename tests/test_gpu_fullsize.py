@@ -107,3 +107,62 @@ def test_full_size_arnoldi_step_properties():
     fd = (R1 - Ru).reshape(-1) / eps
     assert float((w - fd).norm() / fd.norm()) < 1e-6
     ctx.close()
+
+
+@pytest.mark.parametrize("name", ["quad512j-p3-mixed", "hex96-p3-trig"])
+def test_full_size_nej_product_on_sampled_cells(name):
+    """The near-exact Jacobian at the benchmark sizes: rows of J_NEJ x at a
+    sample of cells against the oracle's unstabilised residual (alpha = 0,
+    zero boundary data: exactly J_NEJ x) evaluated at those cells alone."""
+    import torch
+    wl, mesh, ctx, lay, setup_s, u_ex, field = bench.build_workload(name)
+    rng = np.random.default_rng(11)
+    x = rng.standard_normal((wl.dim, lay.n_cells))
+    y = torch.empty((wl.dim, lay.n_cells), dtype=torch.float64, device="cuda:0")
+    ctx.nej_apply(torch.as_tensor(x, device="cuda:0"), y)
+    torch.cuda.synchronize()
+    cells = sample_cells(wl.n, wl.dim)
+    o = oracle.OracleMesh(mesh, I.side_tags(wl.problem, wl.dim), p=wl.p, n_plus=wl.n_plus,
+                          q1=wl.q1, k_weight=wl.k_weight, alpha=0.0)
+    o.prepare(cells)
+    ref = o.residual(wl.law, wl.mu, wl.lam, x, cells=cells)
+    got = y.cpu().numpy()[:, cells]
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-5
+    ctx.close()
+
+
+def test_full_size_dynamic_residual_on_sampled_cells():
+    """The inertia term at 512^2: sampled rows of the dynamic residual
+    against the oracle's point-by-point BDF2 term."""
+    import torch
+
+    from oracle import dynamics as D
+    wl, mesh, ctx, lay, setup_s, u_ex, field = bench.build_workload("quad512j-p3-mixed")
+    xc = ctx.get_points(hofv.PTS_CELL_CENTROID)
+    u = state(wl, xc, u_ex)
+    u_t, u_tm1 = 0.9 * u, 0.7 * u
+    rho, dt = 7800.0, 1e-6
+    ctx.set_inertia(rho, dt, 0)
+    ctx.set_history(torch.as_tensor(u_t, device="cuda:0"), torch.as_tensor(u_tm1, device="cuda:0"),
+                    None, None)
+    R = torch.empty((wl.dim, lay.n_cells), dtype=torch.float64, device="cuda:0")
+    ctx.residual(torch.as_tensor(u, device="cuda:0"), R)
+    torch.cuda.synchronize()
+    cells = sample_cells(wl.n, wl.dim)
+    o = oracle.OracleMesh(mesh, I.side_tags(wl.problem, wl.dim), p=wl.p, n_plus=wl.n_plus,
+                          q1=wl.q1, k_weight=wl.k_weight, alpha=wl.alpha)
+    o.prepare(cells)
+    ubq = field.value(o.xq[o.disp_faces()])
+    ubf = field.value(o.xf[o.disp_faces()])
+    body = o.integrate_cells(field.body_force(o.cell_qp, wl.mu, wl.lam))
+    tbq = np.zeros((max(o.nft, 1), o.Q, wl.dim))
+    R_static = o.residual(wl.law, wl.mu, wl.lam, u, ubq, ubf, tbq, body, cells=cells)
+    uq = [D.point_values(o, v, cells)[0] for v in (u, u_t, u_tm1)]
+    _, wq = D.point_values(o, u, cells)
+    zero = np.zeros_like(uq[0])
+    term = D.inertia(rho, D.bdf2_acceleration(uq[0], uq[1], uq[2], zero, zero, dt), wq)
+    ref = R_static - term
+    scale = np.abs(term).max()
+    err = np.abs(R.cpu().numpy()[:, cells] - ref).max()
+    assert err <= 1e-12 * scale, (err, scale)
+    ctx.close()
