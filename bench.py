@@ -672,6 +672,13 @@ def run_pc_sweep(args):
         ctx.nej_apply(v, z)
         torch.cuda.synchronize()
         out["nej_setup_s"] = time.perf_counter() - t0
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(20):
+            ctx.nej_apply(v, z)
+        e1.record(s)
+        torch.cuda.synchronize()
+        out["nej_apply_ms"] = e0.elapsed_time(e1) / 20
     for kind, its in ((hofv.PC_AJ64, INNER_ITERS), (hofv.PC_AJ32, INNER_ITERS),
                       (hofv.PC_AJMG, 1), (hofv.PC_AJMG, 2), (hofv.PC_NEJ, 4), (hofv.PC_NEJ, 8)):
         if kind == hofv.PC_NEJ and wl.law != 0:
