@@ -116,9 +116,9 @@ class OracleMesh:
             raise ValueError(f"oracle rejected the scheme ({rc})")
         if L.orc_geometry(self.h) != 0:
             raise RuntimeError("geometry failed")
-        cnt = np.zeros(8, dtype=np.int64)
+        cnt = np.zeros(9, dtype=np.int64)
         L.orc_counts(self.h, _p(cnt))
-        (self.nf, self.nfi, self.nfd, self.nft, self.nc, self.Q, self.S, self.QC) = (
+        (self.nf, self.nfi, self.nfd, self.nft, self.nc, self.Q, self.S, self.QC, self.nfy) = (
             int(v) for v in cnt)
         self.p, self.n_plus, self.q1 = p, n_plus, q1
         self.nlf = 2 * self.dim
@@ -320,5 +320,8 @@ class OracleMesh:
     def disp_faces(self):
         return np.arange(self.nfi, self.nfi + self.nfd)
 
+    def symm_faces(self):
+        return np.arange(self.nfi + self.nfd, self.nfi + self.nfd + self.nfy)
+
     def trac_faces(self):
-        return np.arange(self.nfi + self.nfd, self.nf)
+        return np.arange(self.nfi + self.nfd + self.nfy, self.nf)

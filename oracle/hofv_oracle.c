@@ -21,8 +21,8 @@
  *   grad[i][j] = d u_j / d x_i  (the paper writes grad u = sum c (x) u);
  *   vectors are component-major: u[j*n_cells + cell];
  *   internal faces are ordered by (owner, owner local face), owner < neighbour;
- *   boundary faces follow: displacement faces then traction faces, each in
- *   input order; local faces are x-, x+, y-, y+ (, z-, z+).
+ *   boundary faces follow: displacement, symmetry, then traction faces, each
+ *   in input order; local faces are x-, x+, y-, y+ (, z-, z+).
  *
  * Readings of the paper taken here (the paper is silent or its setting differs):
  *   - faces are bilinear patches with tensor Gauss-Legendre points; each point
@@ -52,9 +52,9 @@ typedef struct {
   double *x;       /* [nn][3] */
   int64_t *cn;     /* [nc][nv] */
   /* faces */
-  int64_t nf, nfi, nfd, nft;
+  int64_t nf, nfi, nfd, nfy, nft;
   int64_t *fown, *fnei;
-  int *flf, *ftag; /* owner local face; -1 internal, 0 disp, 1 traction */
+  int *flf, *ftag; /* owner local face; -1 internal, 0 disp, 1 traction, 2 symmetry */
   int64_t *fnodes; /* [nf][nfv] in the owner's outward order */
   int64_t *cf;     /* [nc][nlf] face id of each local face */
   /* scheme */
@@ -214,18 +214,19 @@ orc_mesh* orc_create(int dim, int64_t nn, const double* xyz, int64_t nc,
   for (int64_t i = 0; i < nrec; ++i)
     if (partner[i] < 0) ++nbound;
   if (nbound != nb) ok = 0;
-  int64_t nfd = 0, nft = 0;
+  int64_t nfd = 0, nft = 0, nfy = 0;
   for (int64_t b = 0; b < nb; ++b) {
     if (bface_tag[b] == 0) ++nfd;
     else if (bface_tag[b] == 1) ++nft;
+    else if (bface_tag[b] == 2) ++nfy;
     else ok = 0;
   }
   if (!ok) {
     free(rec); free(partner); free(bown); orc_free(m);
     return NULL;
   }
-  m->nfi = nfi; m->nfd = nfd; m->nft = nft;
-  m->nf = nfi + nfd + nft;
+  m->nfi = nfi; m->nfd = nfd; m->nfy = nfy; m->nft = nft;
+  m->nf = nfi + nfd + nfy + nft;
   m->fown = (int64_t*)malloc(sizeof(int64_t) * m->nf);
   m->fnei = (int64_t*)malloc(sizeof(int64_t) * m->nf);
   m->flf = (int*)malloc(sizeof(int) * m->nf);
@@ -242,9 +243,11 @@ orc_mesh* orc_create(int dim, int64_t nn, const double* xyz, int64_t nc,
         ++f;
       }
     }
-  for (int tag = 0; tag <= 1; ++tag)
+  static const int ORDER[3] = {0, 2, 1};  /* displacement, symmetry, traction */
+  for (int o = 0; o < 3; ++o)
     for (int64_t b = 0; b < nb; ++b)
-      if (bface_tag[b] == tag) {
+      if (bface_tag[b] == ORDER[o]) {
+        int tag = ORDER[o];
         int64_t id = bown[b];
         m->fown[f] = id / m->nlf; m->fnei[f] = -1; m->flf[f] = (int)(id % m->nlf);
         m->ftag[f] = tag; m->cf[id] = f;
@@ -276,7 +279,7 @@ void orc_free(orc_mesh* m) {
 
 void orc_counts(const orc_mesh* m, int64_t* out) {
   out[0] = m->nf; out[1] = m->nfi; out[2] = m->nfd; out[3] = m->nft;
-  out[4] = m->nc; out[5] = m->Q; out[6] = m->S; out[7] = m->QC;
+  out[4] = m->nc; out[5] = m->Q; out[6] = m->S; out[7] = m->QC; out[8] = m->nfy;
 }
 
 int orc_set_scheme(orc_mesh* m, int p, int nplus, int q1, double kw, double alpha) {
@@ -586,9 +589,9 @@ int orc_stencil_bruteforce(const orc_mesh* m, const double* xr, int64_t* out) {
   return 0;
 }
 
-static int stencil_search(const orc_mesh* m, const buckets* B, const double* xr,
-                          int64_t* out) {
-  int d = m->dim, S = m->S;
+static int stencil_search_n(const orc_mesh* m, const buckets* B, const double* xr, int S,
+                            int64_t* out) {
+  int d = m->dim;
   int ib[3] = {0, 0, 0};
   for (int a = 0; a < d; ++a) {
     int i = (int)floor((xr[a] - B->lo[a]) / B->bs);
@@ -640,6 +643,25 @@ static int stencil_search(const orc_mesh* m, const buckets* B, const double* xr,
   }
   free(cs);
   return -1;
+}
+
+static int stencil_search(const orc_mesh* m, const buckets* B, const double* xr,
+                          int64_t* out) {
+  return stencil_search_n(m, B, xr, m->S, out);
+}
+
+/* mirror image of x in the plane of face f (its centre and unit normal) */
+static void mirror_point(const orc_mesh* m, int64_t f, const double* x, double* y) {
+  double dn = 0;
+  for (int a = 0; a < 3; ++a) dn += (x[a] - m->xf[3 * f + a]) * m->nrm[3 * f + a];
+  for (int a = 0; a < 3; ++a) y[a] = x[a] - 2.0 * dn * m->nrm[3 * f + a];
+}
+
+/* R v = v - 2 n (n . v), the reflection across the plane of face f */
+static void reflect(const orc_mesh* m, int64_t f, const double* v, double* w) {
+  double dn = 0;
+  for (int a = 0; a < m->dim; ++a) dn += v[a] * m->nrm[3 * f + a];
+  for (int a = 0; a < m->dim; ++a) w[a] = v[a] - 2.0 * dn * m->nrm[3 * f + a];
 }
 
 /* ------------------------------------------------------------------ */
@@ -701,14 +723,14 @@ static int ld_solve(int n, ld* M, int ncol, ld* B) {
    basis [1,0,...] and unit weight.  Abar is written [Nt][ncol] with
    ncol = S + ghost, in the scaled basis; *h_out receives h = 2 r_s and
    *cond_out the 1-norm condition number of M. */
-static int reconstruct(const orc_mesh* m, const double* xt, const int64_t* st, int ghost,
-                       double* Abar, double* h_out, double* cond_out) {
+static int reconstruct_pts(const orc_mesh* m, const double* xt, const double* pts, int ghost,
+                           double* Abar, double* h_out, double* cond_out) {
   int d = m->dim, S = m->S, Nt = m->Nt, ncol = S + ghost;
   double rs = 0.0;
   for (int i = 0; i < S; ++i) {
     double s = 0;
     for (int a = 0; a < d; ++a) {
-      double e = m->xc[3 * st[i] + a] - xt[a];
+      double e = pts[3 * i + a] - xt[a];
       s += e * e;
     }
     s = sqrt(s);
@@ -723,7 +745,7 @@ static int reconstruct(const orc_mesh* m, const double* xt, const int64_t* st, i
   for (int i = 0; i < S; ++i) {
     double dd = 0;
     for (int a = 0; a < d; ++a) {
-      X[a] = (m->xc[3 * st[i] + a] - xt[a]) / h;
+      X[a] = (pts[3 * i + a] - xt[a]) / h;
       dd += X[a] * X[a];
     }
     /* eq. (weightFunc) with dtilde = |xt - x_N| / d_s */
@@ -772,6 +794,17 @@ static int reconstruct(const orc_mesh* m, const double* xt, const int64_t* st, i
   return rc;
 }
 
+/* the same for stencil cells given by id (their centroids) */
+static int reconstruct(const orc_mesh* m, const double* xt, const int64_t* st, int ghost,
+                       double* Abar, double* h_out, double* cond_out) {
+  double* pts = (double*)malloc(sizeof(double) * 3 * m->S);
+  for (int i = 0; i < m->S; ++i)
+    for (int a = 0; a < 3; ++a) pts[3 * i + a] = m->xc[3 * st[i] + a];
+  int rc = reconstruct_pts(m, xt, pts, ghost, Abar, h_out, cond_out);
+  free(pts);
+  return rc;
+}
+
 /* ------------------------------------------------------------------ */
 /* prepare stencils and coefficients for a subset of cells              */
 /* ------------------------------------------------------------------ */
@@ -811,17 +844,29 @@ int orc_prepare(orc_mesh* m, int64_t nsub, const int64_t* cells) {
   buckets B;
   build_buckets(m, &B);
   double* Abar = (double*)malloc(sizeof(double) * Nt * (S + 1));
+  double* pts = (double*)malloc(sizeof(double) * 3 * S);
   int rc = 0;
   for (int64_t f = 0; f < m->nf && rc == 0; ++f) {
     int64_t sl = m->fslot[f];
     if (sl < 0) continue;
     int64_t* st = m->fst + sl * S;
-    if (stencil_search(m, &B, m->xf + 3 * f, st)) { rc = -3; break; }
     int ghost = m->ftag[f] == 0;
+    /* symmetry face (Sec. 3.5.2): the ceil(S/2) nearest cells and the mirror
+       images of the floor(S/2) nearest of them; slot half + k holds the
+       source cell of mirror k */
+    int half = m->ftag[f] == 2 ? (S + 1) / 2 : S;
+    if (stencil_search_n(m, &B, m->xf + 3 * f, half, st)) { rc = -3; break; }
+    for (int k = 0; k < S - half; ++k) st[half + k] = st[k];
+    for (int i = 0; i < S; ++i) {
+      if (i < half)
+        for (int a = 0; a < 3; ++a) pts[3 * i + a] = m->xc[3 * st[i] + a];
+      else
+        mirror_point(m, f, m->xc + 3 * st[i], pts + 3 * i);
+    }
     for (int q = 0; q < Q; ++q) {
       double h;
-      if (reconstruct(m, m->xq + (f * Q + q) * 3, st, ghost, Abar, &h,
-                      &m->fcond[sl * Q + q])) { rc = -4; break; }
+      if (reconstruct_pts(m, m->xq + (f * Q + q) * 3, pts, ghost, Abar, &h,
+                          &m->fcond[sl * Q + q])) { rc = -4; break; }
       int ncol = S + ghost;
       /* gradient rows of Abar, rescaled from the scaled basis (App. B) */
       for (int i = 0; i < ncol; ++i)
@@ -851,6 +896,7 @@ int orc_prepare(orc_mesh* m, int64_t nsub, const int64_t* cells) {
     }
   }
   free(Abar);
+  free(pts);
   free_buckets(&B);
   return rc;
 }
@@ -962,7 +1008,7 @@ static void face_flux(const orc_mesh* m, int64_t f, int law, double mu, double l
   int64_t nc = m->nc;
   for (int a = 0; a < 3; ++a) flux[a] = 0.0;
   if (m->ftag[f] == 1) {
-    int64_t b = f - m->nfi - m->nfd;
+    int64_t b = f - m->nfi - m->nfd - m->nfy;
     for (int q = 0; q < Q; ++q) {
       const double* a = m->aq + (f * Q + q) * 3;
       double mag = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
@@ -973,12 +1019,21 @@ static void face_flux(const orc_mesh* m, int64_t f, int law, double mu, double l
   int64_t sl = m->fslot[f];
   const int64_t* st = m->fst + sl * S;
   int64_t bd = m->ftag[f] == 0 ? f - m->nfi : -1;
+  int sym = m->ftag[f] == 2;
+  int half = sym ? (S + 1) / 2 : S;
   for (int q = 0; q < Q; ++q) {
     double G[3][3] = {{0}};
     const double* co = m->fco + (sl * Q + q) * (S + 1) * 3;
-    for (int i = 0; i < S; ++i)
+    for (int i = 0; i < S; ++i) {
+      double un[3] = {0, 0, 0}, w[3];
+      for (int j = 0; j < d; ++j) un[j] = u[j * nc + st[i]];
+      if (i >= half) {  /* mirrored node: the reflected state R u_N */
+        reflect(m, f, un, w);
+        for (int j = 0; j < d; ++j) un[j] = w[j];
+      }
       for (int a = 0; a < d; ++a)
-        for (int j = 0; j < d; ++j) G[a][j] += co[i * 3 + a] * u[j * nc + st[i]];
+        for (int j = 0; j < d; ++j) G[a][j] += co[i * 3 + a] * un[j];
+    }
     if (bd >= 0)
       for (int a = 0; a < d; ++a)
         for (int j = 0; j < d; ++j) G[a][j] += co[S * 3 + a] * ubq[(bd * Q + q) * d + j];
@@ -1001,7 +1056,11 @@ static void face_flux(const orc_mesh* m, int64_t f, int law, double mu, double l
     uP[j] = s;
   }
   double dvec[3] = {0, 0, 0}, other[3];
-  if (bd < 0) {
+  if (sym) {
+    /* the other side of a symmetry face is the mirror of this one */
+    reflect(m, f, uP, other);
+    for (int a = 0; a < d; ++a) dvec[a] = m->xf[3 * f + a] - m->xc[3 * P + a];
+  } else if (bd < 0) {
     int64_t N = m->fnei[f];
     int64_t cn_ = m->cslot[N];
     int lfN = -1;
@@ -1076,7 +1135,7 @@ void orc_integrate_cells(const orc_mesh* m, const double* fq, double* b) {
 void orc_aj(const orc_mesh* m, double Kbar, double* diag, double* off) {
   int d = m->dim;
   for (int64_t c = 0; c < m->nc; ++c) diag[c] = 0.0;
-  for (int64_t f = 0; f < m->nfi + m->nfd; ++f) {
+  for (int64_t f = 0; f < m->nfi + m->nfd + m->nfy; ++f) {
     int64_t P = m->fown[f];
     double dv[3] = {0, 0, 0}, dn = 0, dl = 0;
     for (int a = 0; a < d; ++a) {
