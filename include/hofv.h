@@ -85,6 +85,7 @@ typedef struct {
                            scaled, weighted LSQ matrix W^1/2 Q^T seen at set-up */
   double setup_seconds; /* wall time of hofv_build_stencils */
   int64_t device_bytes; /* device memory held by the context */
+  int64_t n_symm;       /* symmetry faces (after the displacement faces) */
 } hofv_layout;
 
 typedef struct {
@@ -142,9 +143,15 @@ const char* hofv_version(void);
      cell_nodes  [n_cells][2^dim]
      bface_nodes [n_bfaces][2^(dim-1)]   every boundary face exactly once
      bface_tag   [n_bfaces]  0 = prescribed displacement, 1 = prescribed
-                             traction (2 = symmetry: HOFV_ENOTSUP)
-   Face sets of Sec. 3.1.  Errors: EINVAL if a boundary face is missing,
-   duplicated or not on the boundary. */
+                             traction, 2 = symmetry (a plane of mirror
+                             symmetry: zero normal displacement and shear
+                             traction; Sec. 3.5.2-3.5.3)
+   Face sets of Sec. 3.1; faces are numbered internal, displacement,
+   symmetry, traction.  A symmetry face's stencil holds the ceil(S/2) cells
+   nearest its centre and the mirror images of the floor(S/2) nearest of
+   them, whose values are the reflected states (I - 2 n n) u.  Errors:
+   EINVAL if a boundary face is missing, duplicated or not on the boundary,
+   or a tag is unknown. */
 int hofv_set_mesh(hofv_ctx* ctx, int dim, int64_t n_nodes, const double* xyz,
                   int64_t n_cells, const int64_t* cell_nodes, int64_t n_bfaces,
                   const int64_t* bface_nodes, const int32_t* bface_tag);

@@ -61,6 +61,14 @@ DevMesh dev_mesh(const hofv_ctx* c) {
   m.cex = c->d_cex;
   m.cface = c->d_cface;
   m.tco = (c->contract && c->tco_valid && c->mat.law == HOFV_LAW_LINEAR) ? c->d_tco : nullptr;
+  m.nfy = c->nfy;
+  m.ng = c->ng;
+  m.wst = c->nc + c->ng;
+  m.gsrc = c->d_gsrc;
+  m.gface = c->d_gface;
+  m.nrm = c->d_nrm;
+  m.wext = c->d_wext;
+  m.ubfw = c->d_ubf;
   m.mscale = c->inertia ? c->d_mscale : nullptr;
   m.cmass = (c->inertia && !c->one_point) ? c->d_cmass : nullptr;
   m.inert = c->d_inert;
@@ -122,6 +130,10 @@ static void free_built(hofv_ctx* c) {
   c->d_ubq = c->d_ubf = c->d_tbq = c->d_body = c->d_src = nullptr;
   c->d_tco = c->d_gflux = nullptr;
   c->tco_valid = false;
+  c->d_xce = c->d_wext = nullptr;
+  c->d_gsrc = c->d_gface = nullptr;
+  c->ng = 0;
+  c->gsrc_host.clear();
   c->inertia = false;
   c->hist_set = false;
   c->d_cmass = c->d_mscale = c->d_inert = c->d_hist = nullptr;
@@ -253,8 +265,7 @@ int hofv_set_mesh(hofv_ctx* c, int dim, int64_t nn, const double* xyz, int64_t n
   for (int64_t i = 0; i < nc * c->nv; ++i)
     if (c->cn[i] < 0 || c->cn[i] >= nn) return fail(c, HOFV_EINVAL, "cell node id out of range");
   for (int64_t b = 0; b < nb; ++b) {
-    if (bface_tag[b] == 2) return fail(c, HOFV_ENOTSUP, "symmetry boundaries are not supported");
-    if (bface_tag[b] != 0 && bface_tag[b] != 1) return fail(c, HOFV_EINVAL, "bad boundary tag");
+    if (bface_tag[b] < 0 || bface_tag[b] > 2) return fail(c, HOFV_EINVAL, "bad boundary tag");
   }
   // local faces keyed by their sorted node ids
   const int nlf = c->nlf, nfv = c->nfv;
@@ -303,14 +314,16 @@ int hofv_set_mesh(hofv_ctx* c, int dim, int64_t nn, const double* xyz, int64_t n
     seen[itr->id] = 1;
     bown[b] = itr->id;
   }
-  int64_t nfi = 0, nfd = 0, nft = 0;
+  int64_t nfi = 0, nfd = 0, nft = 0, nfy = 0;
   for (int64_t i = 0; i < nc * nlf; ++i) nfi += partner[i] > i;
-  for (int64_t b = 0; b < nb; ++b) (bface_tag[b] == 0 ? nfd : nft)++;
+  for (int64_t b = 0; b < nb; ++b)
+    (bface_tag[b] == 0 ? nfd : bface_tag[b] == 1 ? nft : nfy)++;
   c->nfi = nfi;
   c->nfd = nfd;
+  c->nfy = nfy;
   c->nft = nft;
-  c->nfid = nfi + nfd;
-  c->nf = nfi + nfd + nft;
+  c->nfid = nfi + nfd + nfy;  // faces with a stencil and a flux
+  c->nf = nfi + nfd + nfy + nft;
   c->fown.assign(c->nf, -1);
   c->fnei.assign(c->nf, -1);
   c->flf.assign(c->nf, 0);
@@ -329,7 +342,7 @@ int hofv_set_mesh(hofv_ctx* c, int dim, int64_t nn, const double* xyz, int64_t n
         ++f;
       }
     }
-  for (int tag = 0; tag <= 1; ++tag)
+  for (int tag : {0, 2, 1})  // displacement, symmetry, traction
     for (int64_t b = 0; b < nb; ++b)
       if (bface_tag[b] == tag) {
         const int64_t id = bown[b];
@@ -487,7 +500,9 @@ int hofv_build_stencils(hofv_ctx* c) {
   const int64_t nfco = std::max<int64_t>(c->nftile, 1) * c->S * kTile * R;
   TRY(dev_alloc(c, &c->d_fco, nfco));
   HOFV_CUDA(c, cudaMemset(c->d_fco, 0, sizeof(double) * nfco));
-  TRY(dev_alloc(c, &c->d_gco, std::max<int64_t>(c->nfd, 1) * R));
+  TRY(dev_alloc(c, &c->d_gco, std::max<int64_t>(c->nfd + c->nfy, 1) * R));
+  HOFV_CUDA(c, cudaMemset(c->d_gco, 0, sizeof(double) * std::max<int64_t>(c->nfd + c->nfy, 1) * R));
+  TRY(run_ghosts(c));
   const int64_t ncex = c->nctile * c->S * kTile * nlf;
   TRY(dev_alloc(c, &c->d_cex, ncex));
   HOFV_CUDA(c, cudaMemset(c->d_cex, 0, sizeof(double) * ncex));
@@ -506,19 +521,22 @@ int hofv_build_stencils(hofv_ctx* c) {
   TRY(dev_alloc(c, &c->d_aj_invd32, nc));
   TRY(run_face_aux(c));
   // ---- boundary data, sources and scratch ----
-  TRY(dev_alloc(c, &c->d_ubq, std::max<int64_t>(c->nfd, 1) * c->Q * d));
-  TRY(dev_alloc(c, &c->d_ubf, std::max<int64_t>(c->nfd, 1) * d));
+  // displacement-face data, then (library-owned) symmetry-face slots
+  const int64_t nfb = std::max<int64_t>(c->nfd + c->nfy, 1);
+  TRY(dev_alloc(c, &c->d_ubq, nfb * c->Q * d));
+  TRY(dev_alloc(c, &c->d_ubf, nfb * d));
   TRY(dev_alloc(c, &c->d_tbq, std::max<int64_t>(c->nft, 1) * c->Q * d));
   TRY(dev_alloc(c, &c->d_body, nc * d));
   TRY(dev_alloc(c, &c->d_src, nc * d));
-  HOFV_CUDA(c, cudaMemset(c->d_ubq, 0, sizeof(double) * std::max<int64_t>(c->nfd, 1) * c->Q * d));
-  HOFV_CUDA(c, cudaMemset(c->d_ubf, 0, sizeof(double) * std::max<int64_t>(c->nfd, 1) * d));
+  HOFV_CUDA(c, cudaMemset(c->d_ubq, 0, sizeof(double) * nfb * c->Q * d));
+  HOFV_CUDA(c, cudaMemset(c->d_ubf, 0, sizeof(double) * nfb * d));
   HOFV_CUDA(c, cudaMemset(c->d_tbq, 0, sizeof(double) * std::max<int64_t>(c->nft, 1) * c->Q * d));
   HOFV_CUDA(c, cudaMemset(c->d_body, 0, sizeof(double) * nc * d));
   HOFV_CUDA(c, cudaMemset(c->d_src, 0, sizeof(double) * nc * d));
   TRY(dev_alloc(c, &c->d_ustar, nc * nlf * d));
   TRY(dev_alloc(c, &c->d_flux, std::max<int64_t>(c->nfid, 1) * d));
   TRY(dev_alloc(c, &c->d_w, nc * d));
+  if (c->ng > 0) TRY(dev_alloc(c, &c->d_wext, (nc + c->ng) * d));
   c->red_blocks = 4 * 152;
   TRY(dev_alloc(c, &c->d_red, (int64_t)c->red_blocks * 128));
   TRY(dev_alloc(c, &c->d_count, 256));
@@ -551,6 +569,7 @@ int hofv_get_layout(const hofv_ctx* c, hofv_layout* out) {
   out->n_internal = c->nfi;
   out->n_disp = c->nfd;
   out->n_trac = c->nft;
+  out->n_symm = c->nfy;
   out->max_cond = c->max_cond;
   out->setup_seconds = c->setup_seconds;
   out->device_bytes = c->device_bytes;
@@ -598,7 +617,7 @@ int hofv_get_points(hofv_ctx* c, int kind, double* out) {
       TRY(fetch(kind == HOFV_PTS_FACE_AREA ? c->d_aq : c->d_xq, c->nf * Q * 3));
       int64_t f0 = 0, nfx = c->nf;
       if (kind == HOFV_PTS_DISP_QP) { f0 = c->nfi; nfx = c->nfd; }
-      if (kind == HOFV_PTS_TRAC_QP) { f0 = c->nfi + c->nfd; nfx = c->nft; }
+      if (kind == HOFV_PTS_TRAC_QP) { f0 = c->nfi + c->nfd + c->nfy; nfx = c->nft; }
       for (int64_t i = 0; i < nfx * Q; ++i)
         for (int a = 0; a < d; ++a) out[i * d + a] = buf[3 * (f0 * Q + i) + a];
       return 0;
@@ -1201,15 +1220,17 @@ int hofv_get_face_data(hofv_ctx* c, int64_t first, int64_t count, int32_t* stenc
     co.resize((size_t)(t1 - t0) * S * kTile * R);
     HOFV_CUDA(c, cudaMemcpy(co.data(), c->d_fco + t0 * S * kTile * R, sizeof(double) * co.size(),
                             cudaMemcpyDeviceToHost));
-    if (c->nfd > 0) {
-      gc.resize((size_t)c->nfd * R);
+    if (c->nfd + c->nfy > 0) {
+      gc.resize((size_t)(c->nfd + c->nfy) * R);
       HOFV_CUDA(c, cudaMemcpy(gc.data(), c->d_gco, sizeof(double) * gc.size(), cudaMemcpyDeviceToHost));
     }
   }
   for (int64_t f = first; f < hi; ++f) {
     const int64_t t = f / kTile - t0, fi = f % kTile, o = f - first;
     for (int nn = 0; nn < S; ++nn) {
-      if (stencil) stencil[o * S + nn] = st[(t * S + nn) * kTile + fi];
+      int32_t id = st[(t * S + nn) * kTile + fi];
+      if (id >= c->nc) id = c->gsrc_host[id - c->nc];  // a mirror node: report its source cell
+      if (stencil) stencil[o * S + nn] = id;
       if (coef)
         for (int q = 0; q < Q; ++q)
           for (int i = 0; i < d; ++i)

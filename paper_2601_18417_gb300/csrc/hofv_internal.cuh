@@ -39,6 +39,16 @@ struct DevMesh {
   const int32_t* cface;   // [nc][nlf]  +(f+1) owner, -(f+1) neighbour, 0 traction
   const double* tco;      // [nftile][S][kTile][dim][dim] contracted linear-elastic
                           // face matrices, or nullptr (then the per-point form is used)
+  // symmetry faces [nfi + nfd, nfid): their stencils end in mirror images of
+  // cells ("ghosts", ids nc + g); the state is then read from an extended
+  // copy [dim][wst] holding the reflected values R u_src after the cells
+  int64_t nfy, ng, wst;   // symmetry faces, ghosts, stride of the state read
+  const int32_t* gsrc;    // [ng] source cell of each ghost
+  const int32_t* gface;   // [ng] symmetry face whose plane mirrors it
+  const double* nrm;      // [nf][3] unit face normals
+  double* wext;           // [dim][nc + ng] extended state (scratch), or nullptr
+  double* ubfw;           // [nfd + nfy][dim] face-centre values; the symmetry
+                          // slots are rewritten by each residual call
   // inertia (BDF2): R_P -= rho Omega_P c2 ubar_P(u), ubar_P = u_P + sum_N cmass_N u_N
   const double* mscale;   // [nc] -rho Omega_P c2, or nullptr (no inertia term)
   const double* cmass;    // [nctile][S][kTile] cell-average weights, or nullptr (ubar = u_P)
@@ -63,6 +73,7 @@ struct hofv_ctx {
   std::vector<double> x;            // [nn][3]
   std::vector<int64_t> cn;          // [nc][nv]
   int64_t nf = 0, nfi = 0, nfd = 0, nft = 0, nfid = 0;
+  int64_t nfy = 0;                  // symmetry faces, after the displacement faces
   std::vector<int64_t> fown, fnei;
   std::vector<int32_t> flf, ftag;
   std::vector<int32_t> fnodes;      // [nf][nfv]
@@ -140,6 +151,13 @@ struct hofv_ctx {
   void* gnn = nullptr;
   // ---- multigrid hierarchy of the approximate Jacobian ----
   void* mg = nullptr;
+  // ---- symmetry faces: mirrored stencil nodes ----
+  int64_t ng = 0;                   // ghosts = nfy * floor(S / 2)
+  double* d_xce = nullptr;          // [nc + ng][3] centroids and ghost positions
+  int32_t* d_gsrc = nullptr;        // [ng]
+  int32_t* d_gface = nullptr;       // [ng]
+  double* d_wext = nullptr;         // [dim][nc + ng]
+  std::vector<int32_t> gsrc_host;
   // ---- inertia term, BDF2 in time (App. time integration) ----
   bool inertia = false;
   double rho = 0.0, dt = 0.0;
@@ -195,6 +213,8 @@ int run_stencils(hofv_ctx* c, const std::vector<int64_t>& bucket_start,
                  const std::vector<int32_t>& bucket_items, const int nb[3], const double lo[3],
                  double bs);
 int run_lsq(hofv_ctx* c);
+// ghost (mirrored) stencil nodes of the symmetry faces: sources, planes, positions
+int run_ghosts(hofv_ctx* c);
 int run_face_aux(hofv_ctx* c);
 // cell-average weights of the cell fit over the cell's Gauss points
 int run_cell_mass(hofv_ctx* c);

@@ -231,6 +231,8 @@ int ensure_inner(hofv_ctx* c, Nej* g, int k) {
 int nej_ensure(hofv_ctx* c) {
   if (c->mat.law != HOFV_LAW_LINEAR)
     return fail(c, HOFV_ENOTSUP, "the near-exact Jacobian is built for the linear-elastic law");
+  if (c->nfy > 0)
+    return fail(c, HOFV_ENOTSUP, "the near-exact Jacobian does not take symmetry faces");
   NEJ_TRY(ensure_tco(c));
   Nej* g = get(c);
   if (!g) {

@@ -38,17 +38,17 @@ __global__ void __launch_bounds__(32 * 2 * DIM)
   double acc[DIM];
 #pragma unroll
   for (int j = 0; j < DIM; ++j) acc[j] = 0.0;
-  const int64_t nc = m.nc;
+  const int64_t ws = m.wst;  // stride of the state read
 #pragma unroll 4
   for (int n = 0; n < m.S; ++n) {
     const int32_t id = __ldg(st + n * kTile);
     const double e = __ldg(ex + (int64_t)n * kTile * NLF);
 #pragma unroll
-    for (int j = 0; j < DIM; ++j) acc[j] = fma(e, __ldg(w + j * nc + id), acc[j]);
+    for (int j = 0; j < DIM; ++j) acc[j] = fma(e, __ldg(w + j * ws + id), acc[j]);
   }
-  if (cell < nc) {
+  if (cell < m.nc) {
 #pragma unroll
-    for (int j = 0; j < DIM; ++j) ustar[(cell * NLF + (it % NLF)) * DIM + j] = w[j * nc + cell] + acc[j];
+    for (int j = 0; j < DIM; ++j) ustar[(cell * NLF + (it % NLF)) * DIM + j] = w[j * ws + cell] + acc[j];
   }
 }
 
@@ -59,13 +59,14 @@ __global__ void __launch_bounds__(32 * 2 * DIM)
 // scaled, the u-dependent part -rho Omega_P c2 ubar_P of the BDF2 term
 // ---------------------------------------------------------------------
 template <int DIM, bool SCALE>
-__global__ void k_cell_avg(DevMesh m, const double* __restrict__ w, double* __restrict__ out) {
+__global__ void k_cell_avg(DevMesh m, const double* __restrict__ w, int64_t ws,
+                           double* __restrict__ out) {
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= m.nc) return;
   const int64_t nc = m.nc;
   double acc[DIM];
 #pragma unroll
-  for (int j = 0; j < DIM; ++j) acc[j] = w[j * nc + c];
+  for (int j = 0; j < DIM; ++j) acc[j] = w[j * ws + c];
   if (m.cmass) {
     const int64_t tile = c / kTile, ci = c % kTile;
     const int32_t* __restrict__ st = m.cst + tile * m.S * kTile + ci;
@@ -74,7 +75,7 @@ __global__ void k_cell_avg(DevMesh m, const double* __restrict__ w, double* __re
       const int32_t id = __ldg(st + n * kTile);
       const double en = __ldg(e + n * kTile);
 #pragma unroll
-      for (int j = 0; j < DIM; ++j) acc[j] = fma(en, __ldg(w + j * nc + id), acc[j]);
+      for (int j = 0; j < DIM; ++j) acc[j] = fma(en, __ldg(w + j * ws + id), acc[j]);
     }
   }
   const double sc = SCALE ? m.mscale[c] : 1.0;
@@ -85,9 +86,9 @@ __global__ void k_cell_avg(DevMesh m, const double* __restrict__ w, double* __re
 void launch_cell_average(const DevMesh& m, const double* u, double* ubar, cudaStream_t st) {
   const unsigned g = (unsigned)((m.nc + 127) / 128);
   if (m.dim == 2)
-    k_cell_avg<2, false><<<g, 128, 0, st>>>(m, u, ubar);
+    k_cell_avg<2, false><<<g, 128, 0, st>>>(m, u, m.nc, ubar);
   else
-    k_cell_avg<3, false><<<g, 128, 0, st>>>(m, u, ubar);
+    k_cell_avg<3, false><<<g, 128, 0, st>>>(m, u, m.nc, ubar);
 }
 
 __global__ void k_combine4(int64_t n, double a, const double* __restrict__ x, double b,
@@ -210,7 +211,7 @@ __global__ void __launch_bounds__(DIM == 3 ? 864 : 256)
   double* Ts = sm + kTile * R * DIM;      // [32][Q][DIM]
   const int64_t tile = blockIdx.x;
   const int it = threadIdx.x;
-  const int64_t nc = m.nc;
+  const int64_t nc = m.wst;  // stride of the state read
   // (1) gradient rows: thread (fi, r) accumulates sum_N c_{r,N} u_N
   {
     const int fi = it / R, r = it % R;
@@ -320,13 +321,60 @@ __global__ void __launch_bounds__(32 * DIM)
             const double* __restrict__ w, const double* __restrict__ ustar,
             const double* __restrict__ ubf, double* __restrict__ flux);
 
+// ---------------------------------------------------------------------
+// symmetry faces (Sec. 3.5.3): the state extended by the ghosts' reflected
+// values R u_src = u - 2 n (n . u), and, after the stabilisation
+// extrapolation, the mirror R u*_P of each symmetry face's own value as the
+// value beyond the face (its jump then penalises the normal component only)
+// ---------------------------------------------------------------------
+template <int DIM>
+__global__ void k_extend(DevMesh m, const double* __restrict__ w, double* __restrict__ wext) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t nc = m.nc, ws = m.wst;
+  if (i < nc) {
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) wext[j * ws + i] = w[j * nc + i];
+  } else if (i < ws) {
+    const int64_t g = i - nc;
+    const int32_t src = m.gsrc[g];
+    const double* n = m.nrm + 3 * (int64_t)m.gface[g];
+    double u[DIM], un = 0.0;
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) {
+      u[j] = w[j * nc + src];
+      un += n[j] * u[j];
+    }
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) wext[j * ws + i] = u[j] - 2.0 * un * n[j];
+  }
+}
+
+template <int DIM>
+__global__ void k_sym_other(DevMesh m, const double* __restrict__ ustar) {
+  const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (b >= m.nfy) return;
+  const int64_t f = m.nfi + m.nfd + b;
+  const double* us = ustar + (int64_t)m.fstar[2 * f] * DIM;
+  const double* n = m.nrm + 3 * f;
+  double un = 0.0;
+#pragma unroll
+  for (int j = 0; j < DIM; ++j) un += n[j] * us[j];
+#pragma unroll
+  for (int j = 0; j < DIM; ++j) m.ubfw[(f - m.nfi) * DIM + j] = us[j] - 2.0 * un * n[j];
+}
+
 template <int DIM, int LAW>
 static void residual_impl(const DevMesh& m, const Material& mat, const double* w,
                           const double* d_eps, const double* R0, double* out, double* ustar,
                           double* flux, const double* ubq, const double* ubf, const double* src,
                           cudaStream_t st, cudaEvent_t* ev) {
   if (ev) cudaEventRecord(ev[0], st);
+  if (m.ng > 0) {
+    k_extend<DIM><<<(unsigned)((m.wst + 255) / 256), 256, 0, st>>>(m, w, m.wext);
+    w = m.wext;
+  }
   k_ustar<DIM><<<(unsigned)m.nctile, 32 * 2 * DIM, 0, st>>>(m, w, ustar);
+  if (m.nfy > 0) k_sym_other<DIM><<<(unsigned)((m.nfy + 127) / 128), 128, 0, st>>>(m, ustar);
   if (ev) cudaEventRecord(ev[1], st);
   if (m.nftile > 0) {
     if (LAW == HOFV_LAW_LINEAR && m.tco) {
@@ -340,7 +388,7 @@ static void residual_impl(const DevMesh& m, const Material& mat, const double* w
   }
   if (ev) cudaEventRecord(ev[2], st);
   if (m.mscale)
-    k_cell_avg<DIM, true><<<(unsigned)((m.nc + 127) / 128), 128, 0, st>>>(m, w, m.inert);
+    k_cell_avg<DIM, true><<<(unsigned)((m.nc + 127) / 128), 128, 0, st>>>(m, w, m.wst, m.inert);
   k_cell<DIM><<<(unsigned)((m.nc + 255) / 256), 256, 0, st>>>(m, flux, src, R0, d_eps, out);
   if (ev) cudaEventRecord(ev[3], st);
 }
@@ -398,7 +446,7 @@ __global__ void k_source(int dim, int nlf, int Q, int64_t nc, int64_t nfi, int64
 
 void launch_source(const hofv_ctx* c, cudaStream_t st) {
   k_source<<<(unsigned)((c->nc + 127) / 128), 128, 0, st>>>(
-      c->dim, c->nlf, c->Q, c->nc, c->nfi, c->nfd, c->d_cf, c->d_ftag, c->d_aq,
+      c->dim, c->nlf, c->Q, c->nc, c->nfi, c->nfd + c->nfy, c->d_cf, c->d_ftag, c->d_aq,
       c->nft > 0 ? c->d_tbq : nullptr, c->d_body,
       (c->contract && c->tco_valid && c->mat.law == HOFV_LAW_LINEAR && c->nfd > 0) ? c->d_gflux
                                                                                   : nullptr,
@@ -527,7 +575,7 @@ __global__ void __launch_bounds__(32 * DIM)
   const int fi = it / DIM, i = it % DIM;
   const int64_t f = tile * kTile + fi;
   const int S = m.S;
-  const int64_t nc = m.nc;
+  const int64_t nc = m.wst;  // stride of the state read
   const int32_t* __restrict__ st = m.fst + tile * S * kTile + fi;
   const double* __restrict__ tc = tco + tile * (int64_t)S * kTile * DIM * DIM + it * DIM;
   double acc = 0.0;

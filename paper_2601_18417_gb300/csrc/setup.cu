@@ -37,14 +37,18 @@ __device__ __forceinline__ long long dist_key(int dim, const double* __restrict_
   return (long long)floor(__dadd_rn(__dmul_rn(d2, scale), 0.5));
 }
 
-__global__ void k_stencils(int dim, int S, int64_t nq_face, int64_t nq_cell, int64_t nfid,
-                           const double* __restrict__ xf, const double* __restrict__ xc,
-                           Buckets B, double scale, int32_t* fst, int32_t* cst, int* status) {
+__global__ void k_stencils(int dim, int S_full, int64_t nq_face, int64_t nq_cell, int64_t nfid,
+                           int64_t nsym0, int64_t nc, const double* __restrict__ xf,
+                           const double* __restrict__ xc, Buckets B, double scale, int32_t* fst,
+                           int32_t* cst, int* status) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= nq_face + nq_cell) return;
   double xr[3];
   const bool is_face = t < nq_face;
   const int64_t id = is_face ? t : t - nq_face;
+  // a symmetry face searches ceil(S/2) cells; mirrors fill the other slots
+  const bool sym = is_face && id >= nsym0;
+  const int S = sym ? (S_full + 1) / 2 : S_full;
   for (int a = 0; a < 3; ++a) xr[a] = is_face ? xf[3 * id + a] : xc[3 * id + a];
   long long key[kMaxS];
   int32_t idx[kMaxS];
@@ -112,7 +116,50 @@ __global__ void k_stencils(int dim, int S, int64_t nq_face, int64_t nq_cell, int
   }
   const int64_t tile = id / kTile, li = id % kTile;
   int32_t* out = is_face ? fst : cst;
-  for (int n = 0; n < S; ++n) out[(tile * S + n) * kTile + li] = idx[n];
+  for (int n = 0; n < S; ++n) out[(tile * S_full + n) * kTile + li] = idx[n];
+  if (sym) {
+    const int half2 = S_full / 2;
+    for (int k = 0; k < half2; ++k)
+      out[(tile * S_full + S + k) * kTile + li] = (int32_t)(nc + (id - nsym0) * half2 + k);
+  }
+}
+
+// ghosts of the symmetry faces: ghost g = b * floor(S/2) + k mirrors the k-th
+// nearest cell of symmetry face b in that face's plane
+__global__ void k_ghosts(int64_t ng, int half2, int S, int64_t nc, int64_t nsym0,
+                         const int32_t* __restrict__ fst, const double* __restrict__ xf,
+                         const double* __restrict__ nrm, const double* __restrict__ xc,
+                         int32_t* gsrc, int32_t* gface, double* xce) {
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= ng) return;
+  const int64_t f = nsym0 + g / half2;
+  const int k = (int)(g % half2);
+  const int32_t src = fst[((f / kTile) * S + k) * kTile + f % kTile];
+  gsrc[g] = src;
+  gface[g] = (int32_t)f;
+  double dn = 0.0;
+  for (int a = 0; a < 3; ++a) dn += (xc[3 * (int64_t)src + a] - xf[3 * f + a]) * nrm[3 * f + a];
+  for (int a = 0; a < 3; ++a) xce[3 * (nc + g) + a] = xc[3 * (int64_t)src + a] - 2.0 * dn * nrm[3 * f + a];
+}
+
+int run_ghosts(hofv_ctx* c) {
+  const int half2 = c->S / 2;
+  c->ng = c->nfy * half2;
+  if (c->ng == 0) return 0;
+  if (dev_alloc(c, &c->d_gsrc, c->ng) || dev_alloc(c, &c->d_gface, c->ng) ||
+      dev_alloc(c, &c->d_xce, (c->nc + c->ng) * 3))
+    return HOFV_ENOMEM;
+  HOFV_CUDA(c, cudaMemcpyAsync(c->d_xce, c->d_xc, sizeof(double) * c->nc * 3,
+                               cudaMemcpyDeviceToDevice, c->stream));
+  k_ghosts<<<(unsigned)((c->ng + 127) / 128), 128, 0, c->stream>>>(
+      c->ng, half2, c->S, c->nc, c->nfi + c->nfd, c->d_fst, c->d_xf, c->d_nrm, c->d_xc, c->d_gsrc,
+      c->d_gface, c->d_xce);
+  HOFV_CUDA(c, cudaGetLastError());
+  c->gsrc_host.resize(c->ng);
+  HOFV_CUDA(c, cudaMemcpyAsync(c->gsrc_host.data(), c->d_gsrc, sizeof(int32_t) * c->ng,
+                               cudaMemcpyDeviceToHost, c->stream));
+  HOFV_CUDA(c, cudaStreamSynchronize(c->stream));
+  return 0;
 }
 
 int run_stencils(hofv_ctx* c, const std::vector<int64_t>& bstart,
@@ -142,8 +189,8 @@ int run_stencils(hofv_ctx* c, const std::vector<int64_t>& bstart,
   const int64_t nq = c->nfid + c->nc;
   const int T = 64;
   k_stencils<<<(unsigned)((nq + T - 1) / T), T, 0, c->stream>>>(
-      c->dim, c->S, c->nfid, c->nc, c->nfid, c->d_xf, c->d_xc, B, scale, c->d_fst, c->d_cst,
-      d_status);
+      c->dim, c->S, c->nfid, c->nc, c->nfid, c->nfi + c->nfd, c->nc, c->d_xf, c->d_xc, B, scale,
+      c->d_fst, c->d_cst, d_status);
   HOFV_CUDA(c, cudaGetLastError());
   int status = 0;
   HOFV_CUDA(c, cudaMemcpyAsync(&status, d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
@@ -203,6 +250,7 @@ struct LsqParams {
   int dim, p, S, Nt, NR, nlf, Q, R;
   double k2, ek;
   int64_t nfid, nfi, nc;
+  int64_t nfde;        // displacement faces end (ghost node for f in [nfi, nfde))
   const double* xq;    // [nf][Q][3]
   const double* xf;    // [nf][3]
   const double* xc;    // [nc][3]
@@ -360,7 +408,7 @@ __global__ void k_lsq_faces(LsqParams P) {
   const int64_t tile = f / kTile, fi = f % kTile;
   int32_t nodes[kMaxS];
   for (int n = 0; n < P.S; ++n) nodes[n] = P.fst[(tile * P.S + n) * kTile + fi];
-  const bool ghost = f >= P.nfi;
+  const bool ghost = f >= P.nfi && f < P.nfde;
   const int nrow = P.S + (ghost ? 1 : 0);
   double xt[3];
   for (int a = 0; a < 3; ++a) xt[a] = P.xq[(f * P.Q + q) * 3 + a];
@@ -469,10 +517,11 @@ static LsqParams lsq_params(hofv_ctx* c) {
   P.ek = exp(-P.k2);
   P.nfid = c->nfid;
   P.nfi = c->nfi;
+  P.nfde = c->nfi + c->nfd;
   P.nc = c->nc;
   P.xq = c->d_xq;
   P.xf = c->d_xf;
-  P.xc = c->d_xc;
+  P.xc = c->ng > 0 ? c->d_xce : c->d_xc;  // with the mirrored positions of the ghosts
   P.fst = c->d_fst;
   P.cst = c->d_cst;
   P.fco = c->d_fco;

@@ -35,7 +35,7 @@ class Layout(C.Structure):
                 ("q_face", C.c_int32), ("q_cell", C.c_int32), ("n_cells", C.c_int64),
                 ("n_faces", C.c_int64), ("n_internal", C.c_int64), ("n_disp", C.c_int64),
                 ("n_trac", C.c_int64), ("max_cond", C.c_double), ("setup_seconds", C.c_double),
-                ("device_bytes", C.c_int64)]
+                ("device_bytes", C.c_int64), ("n_symm", C.c_int64)]
 
 
 class SolveOpts(C.Structure):

@@ -80,8 +80,8 @@ def test_malformed_meshes_are_rejected():
     ok = np.zeros(nb, np.int32)
     assert _mesh_status(mesh, ok) == 0
     sym = ok.copy()
-    sym[3] = 2
-    assert _mesh_status(mesh, sym) == hofv.ENOTSUP
+    sym[3] = 2  # symmetry faces are accepted
+    assert _mesh_status(mesh, sym) == 0
     bad = ok.copy()
     bad[0] = 7
     assert _mesh_status(mesh, bad) == hofv.EINVAL
