@@ -1309,8 +1309,6 @@ extern "C" int hofv_arnoldi_step(hofv_ctx* c, const double* u, const double* Ru,
     return fail(c, HOFV_EINVAL, "unknown preconditioner");
   if (kind == HOFV_PC_GNN && !c->gnn) return fail(c, HOFV_ESTATE, "no learned preconditioner loaded");
   TRY(ensure_krylov(c, 1));
-  double* Vj = V + (int64_t)j * ld;
-  double* Zj = Z + (int64_t)j * ld;
   double* w = c->d_kvec;
   double* dh = c->d_h;
   hofv_solve_opts o;
