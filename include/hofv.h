@@ -18,11 +18,14 @@
  *     device, owned by the caller; the library never frees them.  The
  *     library owns mesh, stencil, coefficient, preconditioner and Krylov
  *     storage, allocated by the set-up calls; the evaluation calls
- *     (residual, jvp, precondition) allocate nothing.
+ *     (residual, jvp, precondition) allocate nothing, except that the first
+ *     use of a preconditioner builds its data (multigrid hierarchy,
+ *     near-exact Jacobian) and the first Arnoldi step of a kind captures
+ *     its CUDA graph.
  *   - Asynchrony: evaluation calls enqueue work on the context stream and
  *     return; set-up calls and hofv_newton_solve synchronise that stream.
  *   - Faces: internal faces first, ordered by (owner, owner local face) with
- *     owner < neighbour; then displacement faces, then traction faces, each
+ *     owner < neighbour; then displacement, symmetry and traction faces, each
  *     in the order of the boundary-face list given to hofv_set_mesh.  Local
  *     faces of a cell are x-, x+, y-, y+ (, z-, z+) of its reference element.
  *   - Gradients: grad[i][j] = d u_j / d x_i, the paper's sum of c (x) u
@@ -99,7 +102,8 @@ typedef struct {
   int32_t max_krylov;      /* Krylov iterations per Newton step (default 300) */
   double eta_max;          /* forcing term cap (default 1e-2) */
   int32_t precond;         /* HOFV_PC_* (default HOFV_PC_AJ32) */
-  int32_t inner_iters;     /* AJ inner CG iterations per apply (default 30) */
+  int32_t inner_iters;     /* inner iterations per apply (default 30): CG for AJ64/AJ32,
+                              V-cycles (1) or multigrid-CG for AJMG, GMRES for NEJ */
   int32_t line_search_max; /* backtracking halvings (default 10) */
   int32_t verbose;         /* 1: one line per Newton step on stderr */
   int32_t record_pairs;    /* 1: keep (-R(u_k), du_k) of every Newton step as a training
@@ -201,7 +205,7 @@ int hofv_set_contraction(hofv_ctx* ctx, int on);
    use (and after a material change) as block CSR with d x d FP32 blocks,
    columns = the union of each cell's face stencils; products accumulate in
    FP32.  x, y: DEVICE [dim][n_cells].  HOFV_ENOTSUP for the neo-Hookean
-   law. */
+   law and for meshes with symmetry faces. */
 int hofv_nej_apply(hofv_ctx* ctx, const double* x, double* y);
 
 /* Inertia term for dynamics (eq. inertiaTerm; BDF2 of the appendix on time
