@@ -5,8 +5,9 @@
 // same scalar operator B = D - O, a graph Laplacian of the cell adjacency
 // with face weights Gamma_f / |d . n| and the displacement faces on the
 // diagonal.  The paper leaves the solution of P z = v to its linear-algebra
-// library.  Here it is solved by FP32 conjugate gradients preconditioned by
-// one symmetric V-cycle of smoothed-aggregation algebraic multigrid:
+// library.  Here it is approximated by one symmetric V-cycle of
+// smoothed-aggregation algebraic multigrid in FP32 (inner_iters = 1), or by
+// FP32 conjugate gradients preconditioned by that V-cycle (inner_iters > 1):
 //
 //   * aggregation (three greedy passes over the strong connections),
 //     tentative piecewise-constant prolongator, smoothed by one damped
@@ -17,10 +18,11 @@
 //   * one damped Jacobi sweep before and after the coarse correction (same
 //     weights, so the V-cycle is a symmetric operator and CG may use it).
 //
-// The hierarchy is built once per mesh on the host (it depends on the
-// geometry only: B is stored with Kbar = 1) and lives on the device in
-// CSR form: one thread per row for short rows, one warp per row for long
-// ones.  Every kernel handles all displacement components at once, so the
+// The hierarchy is built on first use on the host from B (stored with
+// Kbar = 1, so it depends on the geometry only, plus the mass diagonal when
+// the inertia term is on; it is rebuilt when that changes) and lives on the
+// device in CSR form: one thread per row for short rows, one warp per row
+// for long ones.  Every kernel handles all displacement components at once, so the
 // matrices are read once per application.  Reductions are
 // deterministic (fixed-order partial sums, last-block finalisation).
 #include <math.h>
