@@ -12,6 +12,11 @@
 //   k_cell  : cell-ordered, fixed face order (no atomics):
 //             R_P = sum_f +-flux_f + source_P (eq. divStressDiscret +
 //             eq. bodyTerm); optional epilogue (R - R0) / eps for Jv.
+//   k_tflux : the linear law in contracted form, flux_f = sum_N T_N u_N
+//             (replaces k_flux when enabled)
+//   k_extend, k_sym_other : symmetry faces (reflected ghost values, mirrored
+//             stabilisation value), only when the mesh has symmetry faces
+//   k_cell_avg : inertia term of the BDF2 dynamics, only when enabled
 //
 // All arithmetic is FP64.  Every FP64 instruction of the gradient phase runs
 // with all 32 lanes busy: a tile's (face, row) pairs are laid out so that
