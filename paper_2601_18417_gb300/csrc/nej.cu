@@ -11,8 +11,7 @@
 // columns are the union of the face stencils of P.
 //
 // Storage: block CSR with d x d FP32 blocks (assembled in FP64 in a fixed
-// face order, one warp per row: deterministic), columns sorted per row, the
-// block entries stored entry-major for coalesced reads.  The
+// face order, one warp per row: deterministic), columns sorted per row.  The
 // preconditioner applies NEJ^-1 approximately by `inner` iterations of GMRES
 // right-preconditioned by one multigrid V-cycle of the compact approximate
 // Jacobian; the outer flexible GMRES absorbs the inexactness.
@@ -33,7 +32,7 @@ struct Nej {
   int64_t nnzb = 0;
   int32_t* rp = nullptr;       // [nc + 1]
   int32_t* col = nullptr;      // [nnzb]
-  float* val = nullptr;        // [d * d][nnzb], entry-major
+  float* val = nullptr;        // [nnzb][d][d]
   // inner GMRES storage
   int kmax = 0;
   double *V = nullptr, *Z = nullptr, *w = nullptr, *h = nullptr, *y = nullptr;
@@ -91,20 +90,15 @@ __global__ void k_nej_assemble(int64_t nc, int nlf, int S, const int32_t* __rest
   }
 }
 
-// FP64 blocks [nnzb][dd] -> FP32 entries [dd][nnzb]: entry q of consecutive
-// blocks is contiguous, so the lanes of a warp (consecutive blocks of a row)
-// read it in one coalesced access
-__global__ void k_to_float(int64_t nnzb, int dd, const double* __restrict__ x,
-                           float* __restrict__ y) {
-  const int64_t n = nnzb * dd;
+__global__ void k_to_float(int64_t n, const double* __restrict__ x, float* __restrict__ y) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
-    y[(i % dd) * nnzb + i / dd] = (float)x[i];
+    y[i] = (float)x[i];
 }
 
-// y = NEJ x, one warp per block row, FP32 blocks (entry-major), FP64 vectors
+// y = NEJ x, one warp per block row, FP32 blocks, FP64 vectors
 template <int DIM>
-__global__ void k_nej_spmv(int64_t nc, int64_t nnzb, const int32_t* __restrict__ rp,
+__global__ void k_nej_spmv(int64_t nc, const int32_t* __restrict__ rp,
                            const int32_t* __restrict__ col, const float* __restrict__ val,
                            const double* __restrict__ x, double* __restrict__ y) {
   const int lane = threadIdx.x & 31;
@@ -118,10 +112,11 @@ __global__ void k_nej_spmv(int64_t nc, int64_t nnzb, const int32_t* __restrict__
       float xn[DIM];
 #pragma unroll
       for (int j = 0; j < DIM; ++j) xn[j] = (float)x[j * nc + N];
+      const float* B = val + (int64_t)k * DIM * DIM;
 #pragma unroll
       for (int i = 0; i < DIM; ++i)
 #pragma unroll
-        for (int j = 0; j < DIM; ++j) s[i] = fmaf(val[(i * DIM + j) * nnzb + k], xn[j], s[i]);
+        for (int j = 0; j < DIM; ++j) s[i] = fmaf(B[i * DIM + j], xn[j], s[i]);
     }
 #pragma unroll
     for (int i = 0; i < DIM; ++i)
@@ -206,7 +201,7 @@ int assemble(hofv_ctx* c, Nej* g) {
     k_nej_assemble<3><<<grid, 256, 0, c->stream>>>(c->nc, c->nlf, c->S, c->d_cface, c->nfid,
                                                    c->d_fst, c->d_tco, g->rp, g->col, v64);
   k_to_float<<<(unsigned)std::min<size_t>((nv + 255) / 256, 65535), 256, 0, c->stream>>>(
-      g->nnzb, d * d, v64, g->val);
+      (int64_t)nv, v64, g->val);
   HOFV_CUDA(c, cudaGetLastError());
   HOFV_CUDA(c, cudaStreamSynchronize(c->stream));
   dev_free(c, v64);
@@ -259,11 +254,9 @@ int nej_apply(hofv_ctx* c, const double* x, double* y) {
   NEJ_TRY(nej_ensure(c));
   Nej* g = get(c);
   if (c->dim == 2)
-    k_nej_spmv<2><<<warps_grid(c->nc), 256, 0, c->stream>>>(c->nc, g->nnzb, g->rp, g->col, g->val,
-                                                            x, y);
+    k_nej_spmv<2><<<warps_grid(c->nc), 256, 0, c->stream>>>(c->nc, g->rp, g->col, g->val, x, y);
   else
-    k_nej_spmv<3><<<warps_grid(c->nc), 256, 0, c->stream>>>(c->nc, g->nnzb, g->rp, g->col, g->val,
-                                                            x, y);
+    k_nej_spmv<3><<<warps_grid(c->nc), 256, 0, c->stream>>>(c->nc, g->rp, g->col, g->val, x, y);
   HOFV_CUDA(c, cudaGetLastError());
   return 0;
 }
