@@ -5,18 +5,16 @@ Default (N=1): the 2-D, 512 x 512 jittered quad workload with cubic
 least-squares reconstruction (3 Gauss points per face), linear elasticity,
 the paper's mixed manufactured field.  One timed step is one flexible-GMRES
 Arnoldi step of the JFNK solver -- the approximate-Jacobian preconditioner
-(one FP32 multigrid V-cycle), the forward-difference Jacobian-vector product
-(one FP64 residual evaluation), classical Gram-Schmidt against 16 basis
-vectors (a second pass where the first lost orthogonality) and the
-normalisation -- i.e. one pass over every kernel of the hot path.
+(FP32 inner CG), the forward-difference Jacobian-vector product (one FP64
+residual evaluation), two Gram-Schmidt passes against 16 basis vectors and
+the normalisation -- i.e. one pass over every kernel of the hot path.
 ``value`` counts residual evaluations: cells x evaluations / s (Mcell/s).
 
 Also reported on the same JSON line: the roofline of the dominant kernel
 (face fluxes, FP64-ALU bound on this GPU), the oracle timed on the host
 cores on a bounded sample, an end-to-end number through the public API with
-host buffers, the same step with the Jacobi-CG inner solve and without the
-CUDA graph, the contracted linear form, the time to a 1e-8 residual
-reduction with every preconditioner, clocks sampled during the timed region.
+host buffers, the time to a 1e-8 residual reduction for the FP64 and FP32
+approximate-Jacobian preconditioners, clocks sampled during the timed region.
 
 ``--impl reference`` times the CPU oracle as it stands (the only reference
 available: the paper ships no code) on the same workload.
@@ -403,10 +401,9 @@ def run_hofv(args):
         ctx.set_contraction(False)
     # per step: the preconditioner (one V-cycle: 4 launches per level above the
     # coarsest, 1 on it) + norm (1) + Jv (norm, eps, axpy, 3 residual kernels)
-    # + Gram-Schmidt (2 norms, 2 multi-dots, 2 multi-axpys, the second pair
-    # returning at once when no reorthogonalisation is needed) + norm + scale
+    # + CGS2 (2 multi-dots, 2 multi-axpys) + norm + scale
     assert MG_INNER == 1 and mg["levels"] > 1
-    launches = (4 * (mg["levels"] - 1) + 1) + 1 + 6 + 6 + 2
+    launches = (4 * (mg["levels"] - 1) + 1) + 1 + 6 + 4 + 2
     solve = None
     if rank == 0 and not args.no_solve:
         solve = {}
@@ -455,9 +452,8 @@ def run_hofv(args):
                            "step": f"one flexible Arnoldi step: AJ FP32 preconditioner "
                                    f"(one {mg['levels']}-level "
                                    f"aggregation-multigrid V-cycle) + forward-difference Jv "
-                                   f"(1 FP64 residual) + classical Gram-Schmidt on {J + 1} "
-                                   f"vectors with a second pass where needed; device part "
-                                   f"replayed as one CUDA graph",
+                                   f"(1 FP64 residual) + 2x classical Gram-Schmidt on {J + 1} "
+                                   f"vectors; device part replayed as one CUDA graph",
                            "l2": "inputs larger than L2 (coefficients "
                                  f"{rbytes / 1e9:.2f} GB per residual)",
                            "parallelism": "replicas" if ws > 1 else "single GPU"},

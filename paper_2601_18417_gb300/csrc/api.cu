@@ -842,17 +842,10 @@ static int arnoldi_launch(hofv_ctx* c, const hofv_solve_opts& o, const ArnoldiKe
   TRY(apply_pc(c, o, Vj, Zj, st));
   if (k.with_unorm) launch_norm2(k.u, n, c->d_red, c->d_count, c->d_scal + 0, c->red_blocks, c->stream);
   TRY(jvp_impl(c, k.u, k.Ru, Zj, w));
-  // classical Gram-Schmidt with a second pass only where the first lost
-  // orthogonality (the test of Daniel, Gragg, Kaufman & Stewart)
-  double* n0 = dh + 3 * k.dstride;
-  double* n1 = n0 + 1;
-  launch_norm2(w, n, c->d_red, c->d_count, n0, c->red_blocks, c->stream);
   launch_dots(V, k.ld, w, nv, n, c->d_red, c->d_count, dh, c->red_blocks, c->stream, 0);
   launch_multi_axpy(w, V, dh, nv, n, k.ld, c->stream);
-  launch_norm2(w, n, c->d_red, c->d_count, n1, c->red_blocks, c->stream);
-  launch_dots_reorth(V, k.ld, w, nv, n, c->d_red, c->d_count, dh + k.dstride, c->red_blocks, n0, n1,
-                     c->stream);
-  launch_multi_axpy_reorth(w, V, dh + k.dstride, nv, n, k.ld, n0, n1, c->stream);
+  launch_dots(V, k.ld, w, nv, n, c->d_red, c->d_count, dh + k.dstride, c->red_blocks, c->stream, 0);
+  launch_multi_axpy(w, V, dh + k.dstride, nv, n, k.ld, c->stream);
   launch_norm2(w, n, c->d_red, c->d_count, dh + 2 * k.dstride, c->red_blocks, c->stream);
   if (k.with_scale)
     launch_scale_copy(V + (int64_t)(k.j + 1) * k.ld, w, dh + 2 * k.dstride, 1, n, c->stream);

@@ -262,14 +262,6 @@ void launch_scale_copy(double* y, const double* x, const double* s, int invert, 
                        cudaStream_t st);
 void launch_multi_axpy(double* w, const double* V, const double* coef, int k, int64_t n,
                        int64_t ld, cudaStream_t st);
-// the second Gram-Schmidt pass: skipped on the device (dots written as zero,
-// no update) unless the first pass shrank w below |w0| / sqrt(2), with the
-// norms before (n0) and after (n1) the first pass read from device memory
-void launch_dots_reorth(const double* X, int64_t ldx, const double* y, int nvec, int64_t n,
-                        double* red, unsigned int* count, double* out, int blocks,
-                        const double* n0, const double* n1, cudaStream_t st);
-void launch_multi_axpy_reorth(double* w, const double* V, const double* coef, int k, int64_t n,
-                              int64_t ld, const double* n0, const double* n1, cudaStream_t st);
 void launch_combine(double* x, const double* Z, const double* y, int k, int64_t n, int64_t ld,
                     cudaStream_t st);
 void launch_axpby(double* y, double a, const double* x, double b, int64_t n, cudaStream_t st);

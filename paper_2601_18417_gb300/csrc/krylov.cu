@@ -17,24 +17,10 @@ namespace hofv {
 constexpr int kRedThreads = 256;
 
 // out[k] = x_k . y for k = blockIdx.y; x_k = X + k * ldx
-// Gram-Schmidt reorthogonalisation test (Daniel, Gragg, Kaufman & Stewart):
-// a second pass is needed only when the first one removed more than this
-// fraction of the vector, |w1| <= |w0| / sqrt(2)
-constexpr double kReorth = 0.70710678118654752;
-
-__device__ __forceinline__ bool skip_pass(const double* n0, const double* n1) {
-  return n0 && n1[0] > kReorth * n0[0];
-}
-
 __global__ void k_mdot(const double* __restrict__ X, int64_t ldx, const double* __restrict__ y,
-                       int64_t n, double* red, unsigned int* count, double* out, int mode,
-                       const double* n0 = nullptr, const double* n1 = nullptr) {
+                       int64_t n, double* red, unsigned int* count, double* out, int mode) {
   __shared__ double sh[32];
   const int k = blockIdx.y;
-  if (skip_pass(n0, n1)) {  // every block takes the same branch
-    if (blockIdx.x == 0 && threadIdx.x == 0) out[k] = 0.0;
-    return;
-  }
   const double* x = X + k * ldx;
   double s = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -63,14 +49,6 @@ void launch_dots(const double* X, int64_t ldx, const double* y, int nvec, int64_
 void launch_norm2(const double* x, int64_t n, double* red, unsigned int* count, double* out,
                   int blocks, cudaStream_t st) {
   launch_dots(x, 0, x, 1, n, red, count, out, blocks, st, 1);
-}
-
-void launch_dots_reorth(const double* X, int64_t ldx, const double* y, int nvec, int64_t n,
-                        double* red, unsigned int* count, double* out, int blocks,
-                        const double* n0, const double* n1, cudaStream_t st) {
-  blocks = (int)std::min<int64_t>(std::max(blocks / 4, 1), (n + kRedThreads - 1) / kRedThreads);
-  dim3 grid((unsigned)blocks, (unsigned)nvec);
-  k_mdot<<<grid, kRedThreads, 0, st>>>(X, ldx, y, n, red, count, out, 0, n0, n1);
 }
 
 // eps = sqrt(2^-52) (1 + ||u||) / ||v||  (0 if v = 0)
@@ -113,9 +91,7 @@ void launch_scale_copy(double* y, const double* x, const double* s, int invert, 
 
 // w -= sum_k coef[k] V_k  (coef on the device)
 __global__ void k_multi_axpy(double* __restrict__ w, const double* __restrict__ V,
-                             const double* __restrict__ coef, int k, int64_t n, int64_t ld,
-                             const double* n0 = nullptr, const double* n1 = nullptr) {
-  if (skip_pass(n0, n1)) return;
+                             const double* __restrict__ coef, int k, int64_t n, int64_t ld) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     double s = w[i];
@@ -127,12 +103,6 @@ void launch_multi_axpy(double* w, const double* V, const double* coef, int k, in
                        int64_t ld, cudaStream_t st) {
   k_multi_axpy<<<(unsigned)std::min<int64_t>((n + 255) / 256, 8192), 256, 0, st>>>(w, V, coef, k,
                                                                                  n, ld);
-}
-
-void launch_multi_axpy_reorth(double* w, const double* V, const double* coef, int k, int64_t n,
-                              int64_t ld, const double* n0, const double* n1, cudaStream_t st) {
-  k_multi_axpy<<<(unsigned)std::min<int64_t>((n + 255) / 256, 8192), 256, 0, st>>>(
-      w, V, coef, k, n, ld, n0, n1);
 }
 
 // x += sum_k y[k] Z_k  (y on the device)
