@@ -44,6 +44,8 @@ def lib():
         P, I64, D = C.c_void_p, C.c_int64, C.c_double
         L.orc_create.restype = P
         L.orc_create.argtypes = [C.c_int, I64, P, I64, P, I64, P, P]
+        L.orc_create_cells.restype = P
+        L.orc_create_cells.argtypes = [C.c_int, C.c_int, I64, P, I64, P, I64, P, P]
         L.orc_free.argtypes = [P]
         L.orc_counts.argtypes = [P, P]
         L.orc_set_scheme.argtypes = [P, C.c_int, C.c_int, C.c_int, D, D]
@@ -107,8 +109,9 @@ class OracleMesh:
         tags = np.ascontiguousarray(np.asarray(tags_per_side, np.int32)[mesh.bface_side])
         self.bface_tag = tags
         self._keep = (xyz, cn, bn, tags)
-        self.h = L.orc_create(self.dim, xyz.shape[0], _p(xyz), cn.shape[0], _p(cn),
-                              bn.shape[0], _p(bn), _p(tags))
+        self.simplex = bool(getattr(mesh, "simplex", False))
+        self.h = L.orc_create_cells(self.dim, int(self.simplex), xyz.shape[0], _p(xyz),
+                                    cn.shape[0], _p(cn), bn.shape[0], _p(bn), _p(tags))
         if not self.h:
             raise ValueError("oracle rejected the mesh")
         rc = L.orc_set_scheme(self.h, p, n_plus, q1, k_weight, alpha)
@@ -121,7 +124,7 @@ class OracleMesh:
         (self.nf, self.nfi, self.nfd, self.nft, self.nc, self.Q, self.S, self.QC, self.nfy) = (
             int(v) for v in cnt)
         self.p, self.n_plus, self.q1 = p, n_plus, q1
-        self.nlf = 2 * self.dim
+        self.nlf = self.dim + 1 if self.simplex else 2 * self.dim
         self._subset = None
 
     def __del__(self):

@@ -22,11 +22,16 @@
  *   vectors are component-major: u[j*n_cells + cell];
  *   internal faces are ordered by (owner, owner local face), owner < neighbour;
  *   boundary faces follow: displacement, symmetry, then traction faces, each
- *   in input order; local faces are x-, x+, y-, y+ (, z-, z+).
+ *   in input order; local faces of a quad / hex are x-, x+, y-, y+ (, z-,
+ *   z+), local face k of a triangle joins nodes k and k+1 mod 3, local face
+ *   k of a tetrahedron lies opposite node 3 - k.
  *
  * Readings of the paper taken here (the paper is silent or its setting differs):
  *   - faces are bilinear patches with tensor Gauss-Legendre points; each point
  *     carries its own vector area (the paper fan-triangulates planar faces);
+ *     a triangular face is the patch with a repeated corner and a triangle
+ *     or tetrahedron cell the collapsed square / cube (Duffy's map), so the
+ *     same tensor rules serve unstructured simplex meshes;
  *   - stencil ties are broken by a quantised squared distance (quantum
  *     2^-24 of the squared reference cell size) then by cell id;
  *   - the reconstruction is solved from the normal equations, eq. (maQw), in
@@ -47,7 +52,7 @@ typedef long double ld;
 /* mesh object                                                         */
 /* ------------------------------------------------------------------ */
 typedef struct {
-  int dim, nv, nlf, nfv;
+  int dim, simplex, nv, nlf, nfv;
   int64_t nn, nc, nb;
   double *x;       /* [nn][3] */
   int64_t *cn;     /* [nc][nv] */
@@ -85,8 +90,38 @@ static const int QUAD_LF[4][2] = {{3, 0}, {1, 2}, {0, 1}, {2, 3}};
 static const int HEX_LF[6][4] = {{0, 4, 7, 3}, {1, 2, 6, 5}, {0, 1, 5, 4},
                                  {3, 7, 6, 2}, {0, 3, 2, 1}, {4, 5, 6, 7}};
 
+/* local faces of a triangle (nodes counter-clockwise) and of a tetrahedron
+   (positive orientation: (x1-x0) . ((x2-x0) x (x3-x0)) > 0), outward order;
+   local face k of a tetrahedron is the one opposite node 3 - k */
+static const int TRI_LF[3][2] = {{0, 1}, {1, 2}, {2, 0}};
+static const int TET_LF[4][3] = {{0, 2, 1}, {0, 1, 3}, {0, 3, 2}, {1, 2, 3}};
+
 static int lf_node(const orc_mesh* m, int lf, int k) {
+  if (m->simplex) return m->dim == 2 ? TRI_LF[lf][k] : TET_LF[lf][k];
   return m->dim == 2 ? QUAD_LF[lf][k] : HEX_LF[lf][k];
+}
+
+/* corner coordinates [4][3] of a face for face_quadrature: a triangle is
+   the bilinear patch whose fourth corner coincides with its first, i.e.
+   the collapsed square of Duffy's transformation */
+static void face_corners(const orc_mesh* m, const int64_t* nodes, double* corner) {
+  for (int k = 0; k < m->nfv; ++k)
+    for (int a = 0; a < 3; ++a) corner[3 * k + a] = m->x[3 * nodes[k] + a];
+  if (m->dim == 3 && m->nfv == 3)
+    for (int a = 0; a < 3; ++a) corner[9 + a] = corner[a];
+}
+
+/* node ids of the bilinear / trilinear map of cell c: a quad or hex as
+   given; a triangle or tetrahedron as the degenerate quad (0,1,2,0) or hex
+   (0,1,2,0, 0,1,3,0), which is the collapsed-cube (Duffy) map
+   x = x0 + s (x1 - x0) + s t (x2 - x1) [+ s t r (x3 - x2)] */
+static void cell_map_nodes(const orc_mesh* m, int64_t c, int64_t* out) {
+  static const int TRI_MAP[4] = {0, 1, 2, 0};
+  static const int TET_MAP[8] = {0, 1, 2, 0, 0, 1, 3, 0};
+  const int64_t* cn = m->cn + c * m->nv;
+  int n = m->dim == 2 ? 4 : 8;
+  for (int k = 0; k < n; ++k)
+    out[k] = !m->simplex ? cn[k] : cn[m->dim == 2 ? TRI_MAP[k] : TET_MAP[k]];
 }
 
 /* ------------------------------------------------------------------ */
@@ -152,15 +187,17 @@ static void sorted_key(const int64_t* nodes, int n, int64_t* key) {
 
 void orc_free(orc_mesh* m);
 
-orc_mesh* orc_create(int dim, int64_t nn, const double* xyz, int64_t nc,
-                     const int64_t* cell_nodes, int64_t nb,
-                     const int64_t* bface_nodes, const int* bface_tag) {
+/* simplex = 0: quads / hexes; 1: triangles / tetrahedra */
+orc_mesh* orc_create_cells(int dim, int simplex, int64_t nn, const double* xyz, int64_t nc,
+                           const int64_t* cell_nodes, int64_t nb,
+                           const int64_t* bface_nodes, const int* bface_tag) {
   if (dim != 2 && dim != 3) return NULL;
   orc_mesh* m = (orc_mesh*)calloc(1, sizeof(orc_mesh));
   m->dim = dim;
-  m->nv = dim == 2 ? 4 : 8;
-  m->nlf = 2 * dim;
-  m->nfv = dim == 2 ? 2 : 4;
+  m->simplex = simplex ? 1 : 0;
+  m->nv = simplex ? dim + 1 : (dim == 2 ? 4 : 8);
+  m->nlf = simplex ? dim + 1 : 2 * dim;
+  m->nfv = simplex ? dim : (dim == 2 ? 2 : 4);
   m->nn = nn; m->nc = nc; m->nb = nb;
   m->x = (double*)calloc((size_t)nn * 3, sizeof(double));
   for (int64_t i = 0; i < nn; ++i)
@@ -258,6 +295,12 @@ orc_mesh* orc_create(int dim, int64_t nn, const double* xyz, int64_t nc,
       m->fnodes[f * m->nfv + k] = m->cn[m->fown[f] * m->nv + lf_node(m, m->flf[f], k)];
   free(rec); free(partner); free(bown);
   return m;
+}
+
+orc_mesh* orc_create(int dim, int64_t nn, const double* xyz, int64_t nc,
+                     const int64_t* cell_nodes, int64_t nb,
+                     const int64_t* bface_nodes, const int* bface_tag) {
+  return orc_create_cells(dim, 0, nn, xyz, nc, cell_nodes, nb, bface_nodes, bface_tag);
 }
 
 void orc_free_subset(orc_mesh* m) {
@@ -361,8 +404,7 @@ int orc_geometry(orc_mesh* m) {
   double corner[12], xq[16 * 3], aq[16 * 3];
   /* faces */
   for (int64_t f = 0; f < m->nf; ++f) {
-    for (int k = 0; k < nfv; ++k)
-      for (int a = 0; a < 3; ++a) corner[3 * k + a] = m->x[3 * m->fnodes[f * nfv + k] + a];
+    face_corners(m, m->fnodes + f * nfv, corner);
     face_quadrature(m, corner, m->xq + f * Q * 3, m->aq + f * Q * 3);
     double G = 0, A[3] = {0, 0, 0}, X[3] = {0, 0, 0};
     for (int q = 0; q < Q; ++q) {
@@ -386,9 +428,9 @@ int orc_geometry(orc_mesh* m) {
   for (int64_t c = 0; c < m->nc; ++c) {
     double V = 0, M2[3] = {0, 0, 0};
     for (int lf = 0; lf < m->nlf; ++lf) {
-      for (int k = 0; k < nfv; ++k)
-        for (int a = 0; a < 3; ++a)
-          corner[3 * k + a] = m->x[3 * m->cn[c * m->nv + lf_node(m, lf, k)] + a];
+      int64_t fn[4];
+      for (int k = 0; k < nfv; ++k) fn[k] = m->cn[c * m->nv + lf_node(m, lf, k)];
+      face_corners(m, fn, corner);
       face_quadrature(m, corner, xq, aq);
       for (int q = 0; q < Q; ++q)
         for (int a = 0; a < d; ++a) {
@@ -402,7 +444,8 @@ int orc_geometry(orc_mesh* m) {
     /* cell quadrature for volume integrals (tensor Gauss on the
        bilinear / trilinear map), eq. (bodyTerm) */
     int n = m->q1;
-    const int64_t* cn = m->cn + c * m->nv;
+    int64_t cn[8];
+    cell_map_nodes(m, c, cn);
     if (d == 2) {
       static const double R2[4][2] = {{0, 0}, {1, 0}, {1, 1}, {0, 1}};
       for (int a = 0; a < n; ++a)

@@ -18,6 +18,7 @@ and the block-compression loading used for the neo-Hookean runs; the dataclass
 from __future__ import annotations
 
 import dataclasses
+import itertools
 import math
 
 import numpy as np
@@ -59,12 +60,16 @@ def normal(seed: int, n: int, stream: int = 0) -> np.ndarray:
 
 @dataclasses.dataclass
 class Mesh:
-    """Unstructured description of a structured quad (d=2) or hex (d=3) grid.
+    """Unstructured description of a grid of quads (d=2) or hexes (d=3), or
+    of triangles / tetrahedra (simplex=True) on the same nodes.
 
     xyz          [n_nodes, d] node coordinates
     cell_nodes   [n_cells, 2**d] node ids; quads counter-clockwise, hexes with
-                 the bottom face (z-) counter-clockwise seen from +z, then top
-    bface_nodes  [n_bfaces, 2**(d-1)] node ids of boundary faces, outward order
+                 the bottom face (z-) counter-clockwise seen from +z, then top;
+                 simplex meshes: [n_cells, d+1], triangles counter-clockwise,
+                 tetrahedra positively oriented
+    bface_nodes  [n_bfaces, 2**(d-1)] (simplex: [n_bfaces, d]) node ids of
+                 boundary faces, outward order
     bface_side   [n_bfaces] domain side: 0 x-, 1 x+, 2 y-, 3 y+, 4 z-, 5 z+
     """
 
@@ -75,6 +80,7 @@ class Mesh:
     bface_nodes: np.ndarray
     bface_side: np.ndarray
     length: float = 1.0
+    simplex: bool = False
 
     @property
     def n_cells(self) -> int:
@@ -141,6 +147,87 @@ def structured_mesh(dim: int, n: int, length: float = 1.0, jitter: float = 0.0,
                 cell_nodes=np.ascontiguousarray(cell_nodes.astype(np.int64)),
                 bface_nodes=np.ascontiguousarray(np.concatenate(faces).astype(np.int64)),
                 bface_side=np.concatenate(sides).astype(np.int32), length=length)
+
+
+# local faces of a triangle / tetrahedron in outward node order (a
+# tetrahedron's face k lies opposite its node 3 - k)
+SIMPLEX_LOCAL_FACES = {2: ((0, 1), (1, 2), (2, 0)),
+                       3: ((0, 2, 1), (0, 1, 3), (0, 3, 2), (1, 2, 3))}
+
+
+def _signed_measure(xyz: np.ndarray, cells: np.ndarray) -> np.ndarray:
+    x0 = xyz[cells[:, 0]]
+    E = np.stack([xyz[cells[:, k]] - x0 for k in range(1, cells.shape[1])], axis=1)
+    return np.linalg.det(E)
+
+
+def simplex_mesh(dim: int, n: int, length: float = 1.0, jitter: float = 0.0,
+                 seed: int = 0) -> Mesh:
+    """Triangles (2 n^2) or tetrahedra (6 n^3) on the nodes of
+    structured_mesh(dim, n, length, jitter, seed).  Each square is cut along
+    one of its diagonals, picked by a seeded coin per square; each cube is cut
+    into the six tetrahedra of its Kuhn (Freudenthal) subdivision, the paths
+    from its (0,0,0) corner to its (1,1,1) corner along the edges, which
+    meet conformingly across neighbouring cubes.  Every cell is positively
+    oriented (raises if the jitter inverted one); boundary faces are the cell
+    faces that no other cell shares, ordered by domain side and then by cell,
+    in outward order."""
+    base = structured_mesh(dim, n, length, jitter, seed)
+    cn = base.cell_nodes
+    if dim == 2:
+        flip = uniform(seed, cn.shape[0], stream=11) < 0.5
+        t0 = np.where(flip[:, None], cn[:, [0, 1, 3]], cn[:, [0, 1, 2]])
+        t1 = np.where(flip[:, None], cn[:, [1, 2, 3]], cn[:, [0, 2, 3]])
+        cells = np.stack([t0, t1], axis=1).reshape(-1, 3)
+    elif dim == 3:
+        corner = {(0, 0, 0): 0, (1, 0, 0): 1, (1, 1, 0): 2, (0, 1, 0): 3,
+                  (0, 0, 1): 4, (1, 0, 1): 5, (1, 1, 1): 6, (0, 1, 1): 7}
+        paths = []
+        for perm in itertools.permutations(range(3)):
+            r = [0, 0, 0]
+            path = [corner[tuple(r)]]
+            for ax in perm:
+                r[ax] = 1
+                path.append(corner[tuple(r)])
+            paths.append(path)
+        cells = cn[:, paths].reshape(-1, 4)
+    else:
+        raise ValueError("dim must be 2 or 3")
+    # orientation from the unjittered grid, then checked on the jittered one
+    grid = structured_mesh(dim, n, length, 0.0, seed).xyz
+    neg = _signed_measure(grid, cells) < 0
+    cells[neg, 1], cells[neg, 2] = cells[neg, 2].copy(), cells[neg, 1].copy()
+    if np.any(_signed_measure(base.xyz, cells) <= 0):
+        raise ValueError("jitter inverted a simplex; lower it")
+    # boundary faces: local faces met once
+    lfs = np.asarray(SIMPLEX_LOCAL_FACES[dim])
+    fn = cells[:, lfs]                                   # [nc, d+1, d]
+    keys = np.sort(fn, axis=2).reshape(-1, dim)
+    _, inv, cnt = np.unique(keys, axis=0, return_inverse=True, return_counts=True)
+    once = cnt[inv.ravel()] == 1
+    bnodes = fn.reshape(-1, dim)[once]
+    m = n + 1
+    ijk = np.stack([(bnodes // m ** a) % m for a in range(dim)], axis=-1)   # [nb, d, dim]
+    side = np.full(bnodes.shape[0], -1, np.int64)
+    for a in range(dim):
+        side = np.where(np.all(ijk[:, :, a] == 0, axis=1), 2 * a, side)
+        side = np.where(np.all(ijk[:, :, a] == n, axis=1), 2 * a + 1, side)
+    if np.any(side < 0):
+        raise AssertionError("boundary face off the domain sides")
+    order = np.argsort(side, kind="stable")
+    return Mesh(dim=dim, n=n, xyz=base.xyz, cell_nodes=np.ascontiguousarray(cells.astype(np.int64)),
+                bface_nodes=np.ascontiguousarray(bnodes[order].astype(np.int64)),
+                bface_side=side[order].astype(np.int32), length=length, simplex=True)
+
+
+def make_mesh(dim: int, n: int, length: float = 1.0, jitter: float = 0.0, seed: int = 0,
+              cells: str = "tensor") -> Mesh:
+    """structured_mesh (cells="tensor") or simplex_mesh (cells="simplex")."""
+    if cells == "simplex":
+        return simplex_mesh(dim, n, length, jitter, seed)
+    if cells != "tensor":
+        raise ValueError("cells must be 'tensor' or 'simplex'")
+    return structured_mesh(dim, n, length, jitter, seed)
 
 
 # --------------------------------------------------------------------------

@@ -71,10 +71,10 @@ def bc_from_field(orc: oracle.OracleMesh, field, mu, lam, with_body=True):
 
 def make_problem(dim, n, p, q1, n_plus=None, jitter=0.0, seed=0, field=None,
                  tags=None, law=0, mu=1.0, lam=1.5, prepare=True, cells=None,
-                 alpha=0.1, with_body=True):
+                 alpha=0.1, with_body=True, kind="tensor"):
     if n_plus is None:
         n_plus = 10 if dim == 2 else {1: 45, 2: 55, 3: 65}[p]
-    mesh = I.structured_mesh(dim, n, jitter=jitter, seed=seed)
+    mesh = I.make_mesh(dim, n, jitter=jitter, seed=seed, cells=kind)
     if tags is None:
         tags = np.zeros(2 * dim, np.int32)
     orc = oracle.OracleMesh(mesh, tags, p=p, n_plus=n_plus, q1=q1, alpha=alpha)
@@ -108,11 +108,13 @@ def probe_jacobian(pb: Problem, K: int | None = None):
     if K is None:
         K = min(n, 12)
     idx = np.arange(nc)
-    ij = np.stack(np.unravel_index(idx, (n,) * d)[::-1], axis=1)  # (i, j[, k])
+    per = nc // n ** d  # cells per grid square / cube (simplex meshes: 2 or 6)
+    ij = np.stack(np.unravel_index(idx // per, (n,) * d)[::-1], axis=1)  # (i, j[, k])
     color = np.zeros(nc, np.int64)
     for a in range(d):
         color = color * K + (ij[:, a] % K)
-    ncol = K ** d
+    color = color * per + idx % per
+    ncol = K ** d * per
     u0 = np.zeros((d, nc))
     R0 = residual(pb, u0)
     rows, cols, vals = [], [], []
