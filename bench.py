@@ -101,7 +101,7 @@ def build_workload(name, device=0):
     from paper_2601_18417_gb300 import hofv
     from paper_2601_18417_gb300 import inputs as I
     wl = I.WORKLOADS[name]
-    mesh = I.structured_mesh(wl.dim, wl.n, length=wl.length, jitter=wl.jitter, seed=wl.mesh_seed)
+    mesh = wl.mesh()
     tags = I.side_tags(wl.problem, wl.dim)[mesh.bface_side]
     ctx = hofv.Context(device)
     ctx.set_mesh(mesh, tags)
@@ -146,7 +146,7 @@ def algorithmic_counts(wl, lay):
     bytes_face = 8 * R * S + 4 * S + 8 * Q * 3 + 8 + 8 + 8 * d + 2 * 8 * d
     bytes_ = nfid * bytes_face + lay.n_disp * (8 * R + 8 * Q * d + 8 * d) + 8 * d * lay.n_cells
     # the whole residual (u* prepass + fluxes + assembly), for the HBM view
-    nlf = 2 * d
+    nlf = d + 1 if wl.cells == "simplex" else 2 * d
     res_bytes = bytes_ + lay.n_cells * (8 * nlf * S + 4 * S + 8 * d + 8 * nlf * d * 2
                                         + 8 * d * 2 + 4 * nlf)
     return flops, bytes_, res_bytes
@@ -598,7 +598,7 @@ def run_reference(args):
     from paper_2601_18417_gb300 import inputs as I
     oracle.build()
     wl = I.WORKLOADS[args.workload]
-    mesh = I.structured_mesh(wl.dim, wl.n, jitter=wl.jitter, seed=wl.mesh_seed)
+    mesh = wl.mesh()
     per = max(1.0, args.cpu_budget / max(args.steps + args.warmup, 1))
     for _ in range(args.warmup):
         oracle_baseline(wl, mesh, budget_s=per)

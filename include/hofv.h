@@ -27,7 +27,9 @@
  *   - Faces: internal faces first, ordered by (owner, owner local face) with
  *     owner < neighbour; then displacement, symmetry and traction faces, each
  *     in the order of the boundary-face list given to hofv_set_mesh.  Local
- *     faces of a cell are x-, x+, y-, y+ (, z-, z+) of its reference element.
+ *     faces of a quad / hex are x-, x+, y-, y+ (, z-, z+) of its reference
+ *     element; local face k of a triangle runs from node k to node k+1 mod 3,
+ *     and local face k of a tetrahedron is the face opposite node 3 - k.
  *   - Gradients: grad[i][j] = d u_j / d x_i, the paper's sum of c (x) u
  *     (Sec. 3.5.4, eq. faceQuadGrad).
  */
@@ -159,6 +161,26 @@ const char* hofv_version(void);
 int hofv_set_mesh(hofv_ctx* ctx, int dim, int64_t n_nodes, const double* xyz,
                   int64_t n_cells, const int64_t* cell_nodes, int64_t n_bfaces,
                   const int64_t* bface_nodes, const int32_t* bface_tag);
+
+/* cell kinds for hofv_set_mesh_cells */
+#define HOFV_CELL_TENSOR 0   /* quadrilaterals (dim 2) / hexahedra (dim 3) */
+#define HOFV_CELL_SIMPLEX 1  /* triangles (dim 2) / tetrahedra (dim 3) */
+
+/* hofv_set_mesh for a given cell kind; HOFV_CELL_TENSOR is hofv_set_mesh.
+   HOFV_CELL_SIMPLEX takes unstructured triangles (counter-clockwise) or
+   tetrahedra (positively oriented: (x1-x0) . ((x2-x0) x (x3-x0)) > 0) with
+     cell_nodes  [n_cells][dim + 1]
+     bface_nodes [n_bfaces][dim]
+   Their faces are straight edges or flat triangles; the face rule keeps
+   q_per_dir^(dim-1) points, a triangle being the bilinear patch with a
+   repeated corner (the collapsed square of Duffy's transformation), and the
+   cell rule keeps q_per_dir^dim points on the collapsed square / cube.
+   Every other call works unchanged on such meshes.  Errors as
+   hofv_set_mesh; EINVAL for an unknown cell_kind. */
+int hofv_set_mesh_cells(hofv_ctx* ctx, int dim, int cell_kind, int64_t n_nodes,
+                        const double* xyz, int64_t n_cells, const int64_t* cell_nodes,
+                        int64_t n_bfaces, const int64_t* bface_nodes,
+                        const int32_t* bface_tag);
 
 /* Scheme (Sec. 3.5): reconstruction degree p in 1..3, surplus stencil nodes
    n_plus (|S| = N_t + n_plus; the paper uses 10 in 2-D and 45/55/65 in 3-D),

@@ -75,10 +75,19 @@ DevMesh dev_mesh(const hofv_ctx* c) {
   return m;
 }
 
-// local faces of the reference quad / hex as node positions, outward order
+// local faces of the reference quad / hex and of the triangle /
+// tetrahedron as node positions, outward order (face k of a tetrahedron lies
+// opposite its node 3 - k)
 static const int kQuadLF[4][2] = {{3, 0}, {1, 2}, {0, 1}, {2, 3}};
 static const int kHexLF[6][4] = {{0, 4, 7, 3}, {1, 2, 6, 5}, {0, 1, 5, 4},
                                  {3, 7, 6, 2}, {0, 3, 2, 1}, {4, 5, 6, 7}};
+static const int kTriLF[3][2] = {{0, 1}, {1, 2}, {2, 0}};
+static const int kTetLF[4][3] = {{0, 2, 1}, {0, 1, 3}, {0, 3, 2}, {1, 2, 3}};
+
+static int lf_node(const hofv_ctx* c, int lf, int k) {
+  if (c->simplex) return c->dim == 2 ? kTriLF[lf][k] : kTetLF[lf][k];
+  return c->dim == 2 ? kQuadLF[lf][k] : kHexLF[lf][k];
+}
 
 // Gauss-Legendre rule on [0, 1] (closed forms of the 1..4 point rules on
 // [-1, 1], mapped by x = (t + 1) / 2, w = c / 2)
@@ -242,9 +251,18 @@ const char* hofv_last_error(const hofv_ctx* c) { return c ? c->err.c_str() : "nu
 int hofv_set_mesh(hofv_ctx* c, int dim, int64_t nn, const double* xyz, int64_t nc,
                   const int64_t* cell_nodes, int64_t nb, const int64_t* bface_nodes,
                   const int32_t* bface_tag) {
+  return hofv_set_mesh_cells(c, dim, HOFV_CELL_TENSOR, nn, xyz, nc, cell_nodes, nb, bface_nodes,
+                             bface_tag);
+}
+
+int hofv_set_mesh_cells(hofv_ctx* c, int dim, int cell_kind, int64_t nn, const double* xyz,
+                        int64_t nc, const int64_t* cell_nodes, int64_t nb,
+                        const int64_t* bface_nodes, const int32_t* bface_tag) {
   if (!c) return HOFV_EINVAL;
   invalidate_graphs(c);
   if (dim != 2 && dim != 3) return fail(c, HOFV_EINVAL, "dim must be 2 or 3");
+  if (cell_kind != HOFV_CELL_TENSOR && cell_kind != HOFV_CELL_SIMPLEX)
+    return fail(c, HOFV_EINVAL, "cell_kind must be HOFV_CELL_TENSOR or HOFV_CELL_SIMPLEX");
   if (nn <= 0 || nc <= 0 || !xyz || !cell_nodes || nb < 0 || (nb > 0 && (!bface_nodes || !bface_tag)))
     return fail(c, HOFV_EINVAL, "empty mesh or null array");
   if (nn >= (int64_t)1 << 31 || nc >= (int64_t)1 << 30)
@@ -252,9 +270,10 @@ int hofv_set_mesh(hofv_ctx* c, int dim, int64_t nn, const double* xyz, int64_t n
   free_built(c);
   c->have_mesh = false;
   c->dim = dim;
-  c->nv = dim == 2 ? 4 : 8;
-  c->nlf = 2 * dim;
-  c->nfv = dim == 2 ? 2 : 4;
+  c->simplex = cell_kind == HOFV_CELL_SIMPLEX;
+  c->nv = c->simplex ? dim + 1 : (dim == 2 ? 4 : 8);
+  c->nlf = c->simplex ? dim + 1 : 2 * dim;
+  c->nfv = c->simplex ? dim : (dim == 2 ? 2 : 4);
   c->nn = nn;
   c->nc = nc;
   c->nb = nb;
@@ -264,6 +283,18 @@ int hofv_set_mesh(hofv_ctx* c, int dim, int64_t nn, const double* xyz, int64_t n
   c->cn.assign(cell_nodes, cell_nodes + nc * c->nv);
   for (int64_t i = 0; i < nc * c->nv; ++i)
     if (c->cn[i] < 0 || c->cn[i] >= nn) return fail(c, HOFV_EINVAL, "cell node id out of range");
+  if (c->simplex)
+    for (int64_t cell = 0; cell < nc; ++cell) {
+      const int64_t* v = &c->cn[cell * c->nv];
+      double e[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+      for (int k = 1; k <= dim; ++k)
+        for (int a = 0; a < dim; ++a) e[k - 1][a] = c->x[3 * v[k] + a] - c->x[3 * v[0] + a];
+      const double det = dim == 2 ? e[0][0] * e[1][1] - e[0][1] * e[1][0]
+                                  : e[0][0] * (e[1][1] * e[2][2] - e[1][2] * e[2][1]) -
+                                        e[0][1] * (e[1][0] * e[2][2] - e[1][2] * e[2][0]) +
+                                        e[0][2] * (e[1][0] * e[2][1] - e[1][1] * e[2][0]);
+      if (!(det > 0)) return fail(c, HOFV_EINVAL, "simplex cell not positively oriented");
+    }
   for (int64_t b = 0; b < nb; ++b) {
     if (bface_tag[b] < 0 || bface_tag[b] > 2) return fail(c, HOFV_EINVAL, "bad boundary tag");
   }
@@ -284,7 +315,7 @@ int hofv_set_mesh(hofv_ctx* c, int dim, int64_t nn, const double* xyz, int64_t n
     for (int lf = 0; lf < nlf; ++lf) {
       int64_t nodes[4];
       for (int k = 0; k < nfv; ++k)
-        nodes[k] = c->cn[cell * c->nv + (dim == 2 ? kQuadLF[lf][k] : kHexLF[lf][k])];
+        nodes[k] = c->cn[cell * c->nv + lf_node(c, lf, k)];
       recs[cell * nlf + lf] = {make_key(nodes), cell * nlf + lf};
     }
   std::sort(recs.begin(), recs.end(), [](const Rec& a, const Rec& b) {
@@ -357,7 +388,7 @@ int hofv_set_mesh(hofv_ctx* c, int dim, int64_t nn, const double* xyz, int64_t n
     for (int k = 0; k < nfv; ++k) {
       const int lf = c->flf[f];
       c->fnodes[f * nfv + k] =
-          (int32_t)c->cn[c->fown[f] * c->nv + (dim == 2 ? kQuadLF[lf][k] : kHexLF[lf][k])];
+          (int32_t)c->cn[c->fown[f] * c->nv + lf_node(c, lf, k)];
     }
   c->have_mesh = true;
   c->built = false;

@@ -2,7 +2,11 @@
 // (arXiv 2601.18417, Sec. 3.1-3.3): Gauss points and vector-area elements of
 // straight edges (2-D) and bilinear faces (3-D), face areas, normals and
 // centres, cell volumes and centroids by the divergence theorem, and cell
-// Gauss points of the bilinear / trilinear map.
+// Gauss points of the bilinear / trilinear map.  Triangles and tetrahedra
+// use the same tensor rules on the collapsed square / cube (Duffy's
+// transformation): a triangular face is the bilinear patch (a, b, c, a), a
+// triangle cell the bilinear map of (0, 1, 2, 0) and a tetrahedron the
+// trilinear map of (0, 1, 2, 0, 0, 1, 3, 0).
 //
 // This unit is compiled without FMA contraction and evaluates every
 // expression in a fixed order, so that face centres and centroids -- which
@@ -22,6 +26,16 @@ struct Gauss {
 __constant__ int c_quad_lf[4][2] = {{3, 0}, {1, 2}, {0, 1}, {2, 3}};
 __constant__ int c_hex_lf[6][4] = {{0, 4, 7, 3}, {1, 2, 6, 5}, {0, 1, 5, 4},
                                    {3, 7, 6, 2}, {0, 3, 2, 1}, {4, 5, 6, 7}};
+__constant__ int c_tri_lf[3][2] = {{0, 1}, {1, 2}, {2, 0}};
+__constant__ int c_tet_lf[4][3] = {{0, 2, 1}, {0, 1, 3}, {0, 3, 2}, {1, 2, 3}};
+// cell node of each corner of the collapsed reference square / cube
+__constant__ int c_tri_map[4] = {0, 1, 2, 0};
+__constant__ int c_tet_map[8] = {0, 1, 2, 0, 0, 1, 3, 0};
+
+__device__ __forceinline__ int local_face_node(int dim, bool simplex, int lf, int k) {
+  if (simplex) return dim == 2 ? c_tri_lf[lf][k] : c_tet_lf[lf][k];
+  return dim == 2 ? c_quad_lf[lf][k] : c_hex_lf[lf][k];
+}
 
 // Gauss points and vector-area elements of one face.  corner: [nfv][3] in
 // outward order; faces are straight edges (2-D) or bilinear patches (3-D).
@@ -66,6 +80,8 @@ __global__ void k_face_geometry(int dim, int nfv, int Q, int64_t nf, Gauss g,
   double corner[12];
   for (int k = 0; k < nfv; ++k)
     for (int a = 0; a < 3; ++a) corner[3 * k + a] = x[3 * (int64_t)fnodes[f * nfv + k] + a];
+  if (dim == 3 && nfv == 3)
+    for (int a = 0; a < 3; ++a) corner[9 + a] = corner[a];
   double pq[3 * kMaxQ], pa[3 * kMaxQ];
   face_points(dim, g, corner, pq, pa);
   double G = 0, A[3] = {0, 0, 0}, X[3] = {0, 0, 0};
@@ -90,8 +106,8 @@ __global__ void k_face_geometry(int dim, int nfv, int Q, int64_t nf, Gauss g,
 
 // volume and centroid from the divergence theorem over the cell's own
 // outward faces; Gauss points of the bilinear / trilinear cell map
-__global__ void k_cell_geometry(int dim, int nv, int nlf, int nfv, int Q, int QC, int64_t nc,
-                                Gauss g, const double* __restrict__ x,
+__global__ void k_cell_geometry(int dim, bool simplex, int nv, int nlf, int nfv, int Q, int QC,
+                                int64_t nc, Gauss g, const double* __restrict__ x,
                                 const int32_t* __restrict__ cnodes, double* xc, double* vol,
                                 double* cqx, double* cqw) {
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -103,9 +119,11 @@ __global__ void k_cell_geometry(int dim, int nv, int nlf, int nfv, int Q, int QC
   for (int lf = 0; lf < nlf; ++lf) {
     double corner[12];
     for (int k = 0; k < nfv; ++k) {
-      const int node = dim == 2 ? c_quad_lf[lf][k] : c_hex_lf[lf][k];
+      const int node = local_face_node(dim, simplex, lf, k);
       for (int a = 0; a < 3; ++a) corner[3 * k + a] = cx[node][a];
     }
+    if (dim == 3 && nfv == 3)
+      for (int a = 0; a < 3; ++a) corner[9 + a] = corner[a];
     double pq[3 * kMaxQ], pa[3 * kMaxQ];
     face_points(dim, g, corner, pq, pa);
     for (int q = 0; q < Q; ++q)
@@ -117,6 +135,14 @@ __global__ void k_cell_geometry(int dim, int nv, int nlf, int nfv, int Q, int QC
   V /= dim;
   vol[c] = V;
   for (int a = 0; a < 3; ++a) xc[3 * c + a] = a < dim ? M2[a] / (2.0 * V) : 0.0;
+  if (simplex) {  // corners of the collapsed square / cube
+    double s[8][3];
+    const int nm = dim == 2 ? 4 : 8;
+    for (int k = 0; k < nm; ++k)
+      for (int a = 0; a < 3; ++a) s[k][a] = cx[dim == 2 ? c_tri_map[k] : c_tet_map[k]][a];
+    for (int k = 0; k < nm; ++k)
+      for (int a = 0; a < 3; ++a) cx[k][a] = s[k][a];
+  }
   const int n = g.n;
   if (dim == 2) {
     for (int a = 0; a < n; ++a)
@@ -189,7 +215,7 @@ int run_geometry(hofv_ctx* c) {
       c->d_gam);
   HOFV_CUDA(c, cudaGetLastError());
   k_cell_geometry<<<(unsigned)((c->nc + T - 1) / T), T, 0, c->stream>>>(
-      c->dim, c->nv, c->nlf, c->nfv, c->Q, c->QC, c->nc, g, c->d_x, c->d_cnodes, c->d_xc,
+      c->dim, c->simplex != 0, c->nv, c->nlf, c->nfv, c->Q, c->QC, c->nc, g, c->d_x, c->d_cnodes, c->d_xc,
       c->d_vol, c->d_cqx, c->d_cqw);
   HOFV_CUDA(c, cudaGetLastError());
   HOFV_CUDA(c, cudaStreamSynchronize(c->stream));

@@ -69,6 +69,7 @@ struct hofv_ctx {
   // ---- mesh (host) ----
   bool have_mesh = false, have_scheme = false, built = false, have_mat = false;
   int dim = 0, nv = 0, nlf = 0, nfv = 0;
+  bool simplex = false;            // triangles / tetrahedra instead of quads / hexes
   int64_t nn = 0, nc = 0, nb = 0;
   std::vector<double> x;            // [nn][3]
   std::vector<int64_t> cn;          // [nc][nv]

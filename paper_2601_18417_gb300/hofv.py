@@ -20,6 +20,7 @@ OK, WNOTCONV = 0, 1
 EINVAL, ENOMEM, ECUDA, EILLCOND, ENAN, ENOTSUP, ESTATE = -1, -2, -3, -4, -5, -6, -7
 LAW_LINEAR, LAW_NEOHOOKEAN = 0, 1
 PC_NONE, PC_AJ64, PC_AJ32, PC_GNN, PC_AJMG, PC_NEJ = -1, 0, 1, 2, 3, 4
+CELL_TENSOR, CELL_SIMPLEX = 0, 1
 PTS_CELL_CENTROID, PTS_DISP_QP, PTS_DISP_CENTRE, PTS_TRAC_QP, PTS_CELL_QP = 0, 1, 2, 3, 4
 PTS_FACE_CENTRE, PTS_FACE_QP, PTS_FACE_AREA, PTS_CELL_VOLUME = 5, 6, 7, 8
 
@@ -80,6 +81,7 @@ SIGNATURES = {
     "hofv_last_error": (C.c_char_p, [_P]),
     "hofv_version": (C.c_char_p, []),
     "hofv_set_mesh": (_I, [_P, _I, _I64, _P, _I64, _P, _I64, _P, _P]),
+    "hofv_set_mesh_cells": (_I, [_P, _I, _I, _I64, _P, _I64, _P, _I64, _P, _P]),
     "hofv_set_scheme": (_I, [_P, _I, _I, _I, _D, _D]),
     "hofv_build_stencils": (_I, [_P]),
     "hofv_get_layout": (_I, [_P, C.POINTER(Layout)]),
@@ -198,9 +200,10 @@ class Context:
         bn = np.ascontiguousarray(mesh.bface_nodes, np.int64)
         tag = np.ascontiguousarray(bface_tag, np.int32)
         self.dim = mesh.dim
-        return self._check(self._L.hofv_set_mesh(self.h, mesh.dim, xyz.shape[0], _ptr(xyz),
-                                                 cn.shape[0], _ptr(cn), bn.shape[0], _ptr(bn),
-                                                 _ptr(tag)))
+        kind = CELL_SIMPLEX if getattr(mesh, "simplex", False) else CELL_TENSOR
+        return self._check(self._L.hofv_set_mesh_cells(self.h, mesh.dim, kind, xyz.shape[0],
+                                                       _ptr(xyz), cn.shape[0], _ptr(cn),
+                                                       bn.shape[0], _ptr(bn), _ptr(tag)))
 
     def set_scheme(self, p, n_plus, q_per_dir, k_weight=6.0, alpha=0.1):
         return self._check(self._L.hofv_set_scheme(self.h, p, n_plus, q_per_dir, k_weight, alpha))

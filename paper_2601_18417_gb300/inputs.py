@@ -510,10 +510,16 @@ class Workload:
     alpha: float = 0.1
     k_weight: float = 6.0
     length: float = 1.0      # edge of the square / cube
+    cells: str = "tensor"    # "tensor" (quads / hexes) or "simplex" (triangles / tetrahedra)
 
     @property
     def n_cells(self) -> int:
-        return self.n ** self.dim
+        per = (2 if self.dim == 2 else 6) if self.cells == "simplex" else 1
+        return per * self.n ** self.dim
+
+    def mesh(self) -> Mesh:
+        return make_mesh(self.dim, self.n, length=self.length, jitter=self.jitter,
+                         seed=self.mesh_seed, cells=self.cells)
 
     @property
     def n_t(self) -> int:
@@ -549,6 +555,12 @@ WORKLOADS = {
     # 3-D neo-Hookean block mu=1 MPa lambda=4 MPa, 64^3 hexes jittered 20 %, quadratic LSQ
     "hex64j-p2-nh": Workload("hex64j-p2-nh", 3, 64, 2, 55, 2, 0.20, 1, 1e6, 4e6, "block",
                              1237, load_steps=10),
+    # unstructured simplex meshes: 2 x 512^2 jittered triangles, cubic LSQ (the 2-D
+    # mixed field); 6 x 32^3 jittered tetrahedra, quadratic LSQ (the 3-D field)
+    "tri512j-p3-mixed": Workload("tri512j-p3-mixed", 2, 512, 3, 10, 3, 0.15, 0, _MU_S, _LAM_S,
+                                 "mms-mixed2d", 1242, cells="simplex"),
+    "tet32j-p2-trig": Workload("tet32j-p2-trig", 3, 32, 2, 55, 2, 0.1, 0, _MU_1G, _LAM_1G,
+                               "mms-trig3d", 1243, cells="simplex"),
     # 3-D neo-Hookean, 128^3 jittered hexes, cubic LSQ
     "hex128j-p3-nh": Workload("hex128j-p3-nh", 3, 128, 3, 65, 3, 0.20, 1, 1e6, 4e6, "block",
                               1238, load_steps=10),
