@@ -436,8 +436,9 @@ int hofv_get_face_data(hofv_ctx* ctx, int64_t first, int64_t count, int32_t* ste
                        double* coef);
 
 /* Cell data for cells [first, first + count) to HOST arrays (any may be NULL):
-     stencil [count][S] int32;  ext [count][2 dim][S] weights e with
-     u*_{f,P} = u_P + sum_N e_N u_N (eq. alphaJump). */
+     stencil [count][S] int32;  ext [count][F][S] weights e with
+     u*_{f,P} = u_P + sum_N e_N u_N (eq. alphaJump); F = faces per cell
+     (2 dim for quads / hexes, dim + 1 for triangles / tetrahedra). */
 int hofv_get_cell_data(hofv_ctx* ctx, int64_t first, int64_t count, int32_t* stencil,
                        double* ext);
 

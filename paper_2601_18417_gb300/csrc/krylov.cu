@@ -169,14 +169,13 @@ __device__ __forceinline__ void cg_finalize(const double* red, unsigned int nb, 
 }
 
 // r0 = b = -v/Kbar, w0 = B D^{-1} r0; x = p = 0, s_{-1} = 0; alpha0 = gamma0/delta0
-template <typename T, int DIM>
+template <typename T, int DIM, int NLF>
 __global__ void k_cg_init(int64_t nc, const double* __restrict__ v, double inv_kbar,
                           const T* __restrict__ diag, const T* __restrict__ invd,
                           const int32_t* __restrict__ col,
                           const T* __restrict__ off, T* __restrict__ r0, T* __restrict__ w0,
                           T* __restrict__ sm1, T* __restrict__ x, T* __restrict__ p, double* red,
                           unsigned int* count, double* sc) {
-  constexpr int NLF = 2 * DIM;
   __shared__ double sh[32];
   T pg[DIM], pd[DIM];  // per-thread partials in the vector precision
 #pragma unroll
@@ -230,7 +229,7 @@ __global__ void k_cg_init(int64_t nc, const double* __restrict__ v, double inv_k
 //   s_{i-1} = w_{i-1} + beta s_{i-2};  r_i = r_{i-1} - alpha s_{i-1}
 //   p_{i-1} = u_{i-1} + beta p_{i-2};  x += alpha p_{i-1}
 //   w_i = B u_i, u_i = D^{-1} r_i;  partial (r_i, u_i), (w_i, u_i)
-template <typename T, int DIM>
+template <typename T, int DIM, int NLF>
 __global__ void k_cg_iter(int64_t nc, const T* __restrict__ diag, const T* __restrict__ invd,
                           const int32_t* __restrict__ col,
                           const T* __restrict__ off, const T* __restrict__ r_old,
@@ -238,7 +237,6 @@ __global__ void k_cg_iter(int64_t nc, const T* __restrict__ diag, const T* __res
                           T* __restrict__ r_new, T* __restrict__ w_new, T* __restrict__ s_new,
                           T* __restrict__ x, T* __restrict__ p, double* red, unsigned int* count,
                           double* sc) {
-  constexpr int NLF = 2 * DIM;
   __shared__ double sh[32];
   T alpha[DIM], beta[DIM];
   T pg[DIM], pd[DIM];  // per-thread partials in the vector precision
@@ -367,14 +365,13 @@ __device__ __forceinline__ bool grid_barrier(const GridBarrier& gb, unsigned int
 
 constexpr int kPersistThreads = 1024;
 
-template <typename T, int DIM>
+template <typename T, int DIM, int NLF>
 __global__ void __launch_bounds__(kPersistThreads)
     k_cg_persist(int64_t nc, int iters, const double* __restrict__ v, double inv_kbar,
                  const T* __restrict__ diag, const T* __restrict__ invd,
                  const int32_t* __restrict__ col, const T* __restrict__ off, T* x, T* p, T* r0,
                  T* r1, T* w0, T* w1, T* s0, T* s1, double* part, GridBarrier gb,
                  double* __restrict__ zout) {
-  constexpr int NLF = 2 * DIM;
   __shared__ double sh[32];
   __shared__ double s_sc[3 * DIM];  // gamma_prev, alpha, beta
   __shared__ T s_ab[2 * DIM];       // alpha, beta in the vector precision
@@ -518,18 +515,18 @@ __global__ void __launch_bounds__(kPersistThreads)
   }
 }
 
-template <typename T, int DIM>
+template <typename T, int DIM, int NLF>
 static bool cg_persist_run(hofv_ctx* c, const T* diag, const T* invd, const T* off, T* work,
                            int iters, const double* v, double* zout) {
-  static int max_blocks[2][2] = {{-1, -1}, {-1, -1}};
-  int& mb = max_blocks[sizeof(T) == 8][DIM == 3];
+  static int max_blocks[2][2][2] = {{{-1, -1}, {-1, -1}}, {{-1, -1}, {-1, -1}}};
+  int& mb = max_blocks[sizeof(T) == 8][DIM == 3][NLF == 2 * DIM];
   if (mb < 0) {
     int per_sm = 0, dev = 0, nsm = 0, coop = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (!coop ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg_persist<T, DIM>,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg_persist<T, DIM, NLF>,
                                                       kPersistThreads, 0) != cudaSuccess)
       per_sm = 0;
     mb = std::min(per_sm, 1) * nsm;
@@ -550,7 +547,7 @@ static bool cg_persist_run(hofv_ctx* c, const T* diag, const T* invd, const T* o
   void* args[] = {&nc_, &iters_, (void*)&v, &inv_kbar, (void*)&diag, (void*)&invd,
                   (void*)&c->d_aj_col, (void*)&off, &x, &p, &r0, &r1, &w0, &w1, &s0, &s1, &part,
                   &gb, &zout};
-  const cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_cg_persist<T, DIM>, dim3(mb),
+  const cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_cg_persist<T, DIM, NLF>, dim3(mb),
                                                     dim3(kPersistThreads), args, 0, c->stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -559,7 +556,7 @@ static bool cg_persist_run(hofv_ctx* c, const T* diag, const T* invd, const T* o
   return true;
 }
 
-template <typename T, int DIM>
+template <typename T, int DIM, int NLF>
 static void cg_run(hofv_ctx* c, const T* diag, const T* invd, const T* off, T* work, int iters,
                    const double* v, double* zout) {
   const int64_t nc = c->nc, n = DIM * nc;
@@ -574,10 +571,10 @@ static void cg_run(hofv_ctx* c, const T* diag, const T* invd, const T* off, T* w
   double* sc = c->d_scal + 32;  // slots 32..40
   cudaStream_t st = c->stream;
   if (iters < 1) iters = 1;
-  k_cg_init<T, DIM><<<blocks, kRedThreads, 0, st>>>(nc, v, 1.0 / c->mat.kbar, diag, invd, c->d_aj_col,
+  k_cg_init<T, DIM, NLF><<<blocks, kRedThreads, 0, st>>>(nc, v, 1.0 / c->mat.kbar, diag, invd, c->d_aj_col,
                                                    off, r[0], w[0], s[1], x, p, red, cnt, sc);
   for (int i = 1; i < iters; ++i)
-    k_cg_iter<T, DIM><<<blocks, kRedThreads, 0, st>>>(nc, diag, invd, c->d_aj_col, off, r[(i - 1) & 1],
+    k_cg_iter<T, DIM, NLF><<<blocks, kRedThreads, 0, st>>>(nc, diag, invd, c->d_aj_col, off, r[(i - 1) & 1],
                                                      w[(i - 1) & 1], s[i & 1], r[i & 1], w[i & 1],
                                                      s[(i - 1) & 1], x, p, red, cnt, sc);
   k_cg_finish<T, DIM><<<(unsigned)((nc + 255) / 256), 256, 0, st>>>(nc, invd, r[(iters - 1) & 1], x,
@@ -606,31 +603,36 @@ int barrier_selftest(hofv_ctx* c, int* timed_out) {
   return 0;
 }
 
-int aj_precondition(hofv_ctx* c, int kind, int iters, const double* v, double* z) {
-  bool done = false;
-  if (kind == HOFV_PC_AJ64)
-    done = c->dim == 2
-               ? cg_persist_run<double, 2>(c, c->d_aj_diag, c->d_aj_invd, c->d_aj_off, c->d_cg64, iters, v, z)
-               : cg_persist_run<double, 3>(c, c->d_aj_diag, c->d_aj_invd, c->d_aj_off, c->d_cg64, iters, v, z);
-  else
-    done = c->dim == 2
-               ? cg_persist_run<float, 2>(c, c->d_aj_diag32, c->d_aj_invd32, c->d_aj_off32, c->d_cg32, iters, v, z)
-               : cg_persist_run<float, 3>(c, c->d_aj_diag32, c->d_aj_invd32, c->d_aj_off32, c->d_cg32, iters, v, z);
-  if (done) {
-    HOFV_CUDA(c, cudaGetLastError());
-    return 0;
-  }
-  if (kind == HOFV_PC_AJ64) {
-    if (c->dim == 2)
-      cg_run<double, 2>(c, c->d_aj_diag, c->d_aj_invd, c->d_aj_off, c->d_cg64, iters, v, z);
-    else
-      cg_run<double, 3>(c, c->d_aj_diag, c->d_aj_invd, c->d_aj_off, c->d_cg64, iters, v, z);
+// the persistent cooperative solve when it fits on the device, else one
+// launch per iteration; NLF = faces per cell (4 / 6 for quads / hexes,
+// 3 / 4 for triangles / tetrahedra)
+template <typename T, int DIM, int NLF>
+static void aj_run(hofv_ctx* c, const T* diag, const T* invd, const T* off, T* work, int iters,
+                   const double* v, double* z) {
+  if (!cg_persist_run<T, DIM, NLF>(c, diag, invd, off, work, iters, v, z))
+    cg_run<T, DIM, NLF>(c, diag, invd, off, work, iters, v, z);
+}
+
+template <typename T>
+static void aj_dispatch(hofv_ctx* c, const T* diag, const T* invd, const T* off, T* work, int iters,
+                        const double* v, double* z) {
+  const bool simplex = c->nlf == c->dim + 1;
+  if (c->dim == 2) {
+    if (simplex) aj_run<T, 2, 3>(c, diag, invd, off, work, iters, v, z);
+    else aj_run<T, 2, 4>(c, diag, invd, off, work, iters, v, z);
   } else {
-    if (c->dim == 2)
-      cg_run<float, 2>(c, c->d_aj_diag32, c->d_aj_invd32, c->d_aj_off32, c->d_cg32, iters, v, z);
-    else
-      cg_run<float, 3>(c, c->d_aj_diag32, c->d_aj_invd32, c->d_aj_off32, c->d_cg32, iters, v, z);
+    if (simplex) aj_run<T, 3, 4>(c, diag, invd, off, work, iters, v, z);
+    else aj_run<T, 3, 6>(c, diag, invd, off, work, iters, v, z);
   }
+}
+
+int aj_precondition(hofv_ctx* c, int kind, int iters, const double* v, double* z) {
+  if (c->nlf != 2 * c->dim && c->nlf != c->dim + 1)
+    return fail(c, HOFV_ENOTSUP, "cell shape without an approximate-Jacobian kernel");
+  if (kind == HOFV_PC_AJ64)
+    aj_dispatch<double>(c, c->d_aj_diag, c->d_aj_invd, c->d_aj_off, c->d_cg64, iters, v, z);
+  else
+    aj_dispatch<float>(c, c->d_aj_diag32, c->d_aj_invd32, c->d_aj_off32, c->d_cg32, iters, v, z);
   HOFV_CUDA(c, cudaGetLastError());
   return 0;
 }

@@ -30,10 +30,10 @@ namespace hofv {
 // ---------------------------------------------------------------------
 // stabilisation extrapolation: one thread per (cell, local face)
 // ---------------------------------------------------------------------
-template <int DIM>
-__global__ void __launch_bounds__(32 * 2 * DIM)
+// NLF = faces per cell: 4 / 6 for quads / hexes, 3 / 4 for triangles / tetrahedra
+template <int DIM, int NLF>
+__global__ void __launch_bounds__(32 * NLF)
     k_ustar(DevMesh m, const double* __restrict__ w, double* __restrict__ ustar) {
-  constexpr int NLF = 2 * DIM;
   const int64_t tile = blockIdx.x;
   const int it = threadIdx.x;            // ci * NLF + lf
   const int ci = it / NLF;
@@ -285,11 +285,10 @@ __global__ void __launch_bounds__(DIM == 3 ? 864 : 256)
 // ---------------------------------------------------------------------
 // cell assembly; out = R, or (R - R0) * inv_eps when R0 != nullptr
 // ---------------------------------------------------------------------
-template <int DIM>
+template <int DIM, int NLF>
 __global__ void k_cell(DevMesh m, const double* __restrict__ flux, const double* __restrict__ src,
                        const double* __restrict__ R0, const double* __restrict__ d_eps,
                        double* __restrict__ out) {
-  constexpr int NLF = 2 * DIM;
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= m.nc) return;
   double r[DIM];
@@ -378,7 +377,11 @@ static void residual_impl(const DevMesh& m, const Material& mat, const double* w
     k_extend<DIM><<<(unsigned)((m.wst + 255) / 256), 256, 0, st>>>(m, w, m.wext);
     w = m.wext;
   }
-  k_ustar<DIM><<<(unsigned)m.nctile, 32 * 2 * DIM, 0, st>>>(m, w, ustar);
+  const bool simplex = m.nlf == DIM + 1;
+  if (simplex)
+    k_ustar<DIM, DIM + 1><<<(unsigned)m.nctile, 32 * (DIM + 1), 0, st>>>(m, w, ustar);
+  else
+    k_ustar<DIM, 2 * DIM><<<(unsigned)m.nctile, 32 * 2 * DIM, 0, st>>>(m, w, ustar);
   if (m.nfy > 0) k_sym_other<DIM><<<(unsigned)((m.nfy + 127) / 128), 128, 0, st>>>(m, ustar);
   if (ev) cudaEventRecord(ev[1], st);
   if (m.nftile > 0) {
@@ -394,7 +397,12 @@ static void residual_impl(const DevMesh& m, const Material& mat, const double* w
   if (ev) cudaEventRecord(ev[2], st);
   if (m.mscale)
     k_cell_avg<DIM, true><<<(unsigned)((m.nc + 127) / 128), 128, 0, st>>>(m, w, m.wst, m.inert);
-  k_cell<DIM><<<(unsigned)((m.nc + 255) / 256), 256, 0, st>>>(m, flux, src, R0, d_eps, out);
+  if (simplex)
+    k_cell<DIM, DIM + 1><<<(unsigned)((m.nc + 255) / 256), 256, 0, st>>>(m, flux, src, R0, d_eps,
+                                                                         out);
+  else
+    k_cell<DIM, 2 * DIM><<<(unsigned)((m.nc + 255) / 256), 256, 0, st>>>(m, flux, src, R0, d_eps,
+                                                                         out);
   if (ev) cudaEventRecord(ev[3], st);
 }
 
@@ -463,9 +471,8 @@ void launch_source(const hofv_ctx* c, cudaStream_t st) {
 namespace hofv {
 // per-cell sum of |flux_f| over the cell's internal and displacement faces
 // (the force scale F_s = max over cells), from the last residual's fluxes
-template <int DIM>
+template <int DIM, int NLF>
 __global__ void k_flux_scale(DevMesh m, const double* __restrict__ flux, double* __restrict__ out) {
-  constexpr int NLF = 2 * DIM;
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= m.nc) return;
   double s = 0.0;
@@ -483,10 +490,15 @@ __global__ void k_flux_scale(DevMesh m, const double* __restrict__ flux, double*
 }
 
 void launch_flux_scale(const DevMesh& m, const double* flux, double* out, cudaStream_t st) {
-  if (m.dim == 2)
-    k_flux_scale<2><<<(unsigned)((m.nc + 255) / 256), 256, 0, st>>>(m, flux, out);
+  const unsigned grid = (unsigned)((m.nc + 255) / 256);
+  if (m.dim == 2 && m.nlf == 3)
+    k_flux_scale<2, 3><<<grid, 256, 0, st>>>(m, flux, out);
+  else if (m.dim == 2)
+    k_flux_scale<2, 4><<<grid, 256, 0, st>>>(m, flux, out);
+  else if (m.nlf == 4)
+    k_flux_scale<3, 4><<<grid, 256, 0, st>>>(m, flux, out);
   else
-    k_flux_scale<3><<<(unsigned)((m.nc + 255) / 256), 256, 0, st>>>(m, flux, out);
+    k_flux_scale<3, 6><<<grid, 256, 0, st>>>(m, flux, out);
 }
 }  // namespace hofv
 

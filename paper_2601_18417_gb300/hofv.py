@@ -201,6 +201,7 @@ class Context:
         tag = np.ascontiguousarray(bface_tag, np.int32)
         self.dim = mesh.dim
         kind = CELL_SIMPLEX if getattr(mesh, "simplex", False) else CELL_TENSOR
+        self.faces_per_cell = mesh.dim + 1 if kind == CELL_SIMPLEX else 2 * mesh.dim
         return self._check(self._L.hofv_set_mesh_cells(self.h, mesh.dim, kind, xyz.shape[0],
                                                        _ptr(xyz), cn.shape[0], _ptr(cn),
                                                        bn.shape[0], _ptr(bn), _ptr(tag)))
@@ -390,7 +391,7 @@ class Context:
     def get_cell_data(self, first, count, ext=True):
         lay = self.layout
         st = np.zeros((count, lay.stencil), np.int32)
-        ex = np.zeros((count, 2 * lay.dim, lay.stencil)) if ext else None
+        ex = np.zeros((count, self.faces_per_cell, lay.stencil)) if ext else None
         self._check(self._L.hofv_get_cell_data(self.h, first, count, _ptr(st), _ptr(ex)))
         return st, ex
 
