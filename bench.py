@@ -136,6 +136,14 @@ def build_workload(name, device=0):
     return wl, mesh, ctx, lay, setup_s, u_ex, field
 
 
+def mesh_label(wl):
+    if wl.cells == "simplex":
+        shape = ("2 x {n}^2 triangles" if wl.dim == 2 else "6 x {n}^3 tetrahedra").format(n=wl.n)
+    else:
+        shape = f"{wl.n}^{wl.dim} {'quads' if wl.dim == 2 else 'hexes'}"
+    return f"{shape}, {int(round(wl.jitter * 100))}% node jitter"
+
+
 def algorithmic_counts(wl, lay):
     """Per residual launch of the face-flux kernel: FP64 flops of the
     gradient contraction and the minimum bytes it must move."""
@@ -444,8 +452,7 @@ def run_hofv(args):
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64", "data": "synthetic",
                 "config": {"workload": wl.name,
-                           "mesh": f"{wl.n}^{wl.dim} {'quads' if wl.dim == 2 else 'hexes'}, "
-                                   f"{int(wl.jitter * 100)}% node jitter",
+                           "mesh": mesh_label(wl),
                            "cells": nc, "p": wl.p, "stencil": lay.stencil,
                            "gauss_per_face": lay.q_face,
                            "law": "linear" if wl.law == 0 else "neo-Hookean",
