@@ -46,6 +46,8 @@ def lib():
         L.orc_create.argtypes = [C.c_int, I64, P, I64, P, I64, P, P]
         L.orc_create_cells.restype = P
         L.orc_create_cells.argtypes = [C.c_int, C.c_int, I64, P, I64, P, I64, P, P]
+        L.orc_create_poly.restype = P
+        L.orc_create_poly.argtypes = [I64, P, I64, P, P, I64, P, P]
         L.orc_free.argtypes = [P]
         L.orc_counts.argtypes = [P, P]
         L.orc_set_scheme.argtypes = [P, C.c_int, C.c_int, C.c_int, D, D]
@@ -110,8 +112,15 @@ class OracleMesh:
         self.bface_tag = tags
         self._keep = (xyz, cn, bn, tags)
         self.simplex = bool(getattr(mesh, "simplex", False))
-        self.h = L.orc_create_cells(self.dim, int(self.simplex), xyz.shape[0], _p(xyz),
-                                    cn.shape[0], _p(cn), bn.shape[0], _p(bn), _p(tags))
+        self.polygon = getattr(mesh, "cell_ptr", None) is not None
+        if self.polygon:
+            ptr = np.ascontiguousarray(mesh.cell_ptr, dtype=np.int64)
+            self._keep += (ptr,)
+            self.h = L.orc_create_poly(xyz.shape[0], _p(xyz), ptr.shape[0] - 1, _p(ptr), _p(cn),
+                                       bn.shape[0], _p(bn), _p(tags))
+        else:
+            self.h = L.orc_create_cells(self.dim, int(self.simplex), xyz.shape[0], _p(xyz),
+                                        cn.shape[0], _p(cn), bn.shape[0], _p(bn), _p(tags))
         if not self.h:
             raise ValueError("oracle rejected the mesh")
         rc = L.orc_set_scheme(self.h, p, n_plus, q1, k_weight, alpha)
@@ -124,7 +133,8 @@ class OracleMesh:
         (self.nf, self.nfi, self.nfd, self.nft, self.nc, self.Q, self.S, self.QC, self.nfy) = (
             int(v) for v in cnt)
         self.p, self.n_plus, self.q1 = p, n_plus, q1
-        self.nlf = self.dim + 1 if self.simplex else 2 * self.dim
+        # faces per cell; polygons keep 8 slots, -1 past a cell's last side
+        self.nlf = 8 if self.polygon else self.dim + 1 if self.simplex else 2 * self.dim
         self._subset = None
 
     def __del__(self):

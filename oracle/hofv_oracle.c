@@ -24,14 +24,16 @@
  *   boundary faces follow: displacement, symmetry, then traction faces, each
  *   in input order; local faces of a quad / hex are x-, x+, y-, y+ (, z-,
  *   z+), local face k of a triangle joins nodes k and k+1 mod 3, local face
- *   k of a tetrahedron lies opposite node 3 - k.
+ *   k of a tetrahedron lies opposite node 3 - k, local face k of a polygon
+ *   joins corners k and k+1 (8 slots per polygon, -1 past its last side).
  *
  * Readings of the paper taken here (the paper is silent or its setting differs):
  *   - faces are bilinear patches with tensor Gauss-Legendre points; each point
  *     carries its own vector area (the paper fan-triangulates planar faces);
  *     a triangular face is the patch with a repeated corner and a triangle
  *     or tetrahedron cell the collapsed square / cube (Duffy's map), so the
- *     same tensor rules serve unstructured simplex meshes;
+ *     same tensor rules serve unstructured simplex meshes; a polygon cell is
+ *     the fan of triangles from its corners' average, each so collapsed;
  *   - stencil ties are broken by a quantised squared distance (quantum
  *     2^-24 of the squared reference cell size) then by cell id;
  *   - the reconstruction is solved from the normal equations, eq. (maQw), in
@@ -52,10 +54,11 @@ typedef long double ld;
 /* mesh object                                                         */
 /* ------------------------------------------------------------------ */
 typedef struct {
-  int dim, simplex, nv, nlf, nfv;
+  int dim, simplex, poly, nv, nlf, nfv;
   int64_t nn, nc, nb;
   double *x;       /* [nn][3] */
-  int64_t *cn;     /* [nc][nv] */
+  int64_t *cn;     /* [nc][nv]; polygons: corners, -1 past the last */
+  int *cnv;        /* polygons: [nc] number of corners (= sides) */
   /* faces */
   int64_t nf, nfi, nfd, nfy, nft;
   int64_t *fown, *fnei;
@@ -99,6 +102,20 @@ static const int TET_LF[4][3] = {{0, 2, 1}, {0, 1, 3}, {0, 3, 2}, {1, 2, 3}};
 static int lf_node(const orc_mesh* m, int lf, int k) {
   if (m->simplex) return m->dim == 2 ? TRI_LF[lf][k] : TET_LF[lf][k];
   return m->dim == 2 ? QUAD_LF[lf][k] : HEX_LF[lf][k];
+}
+
+/* a polygon has as many local faces as corners; local face k runs from
+   corner k to corner k+1.  Slots past the last side hold no face. */
+#define POLY_MAX_SIDES 8
+
+static int face_exists(const orc_mesh* m, int64_t c, int lf) {
+  return !m->poly || lf < m->cnv[c];
+}
+
+/* node k of local face lf of cell c (the face must exist) */
+static int64_t cell_face_node(const orc_mesh* m, int64_t c, int lf, int k) {
+  if (m->poly) return m->cn[c * m->nv + (lf + k) % m->cnv[c]];
+  return m->cn[c * m->nv + lf_node(m, lf, k)];
 }
 
 /* corner coordinates [4][3] of a face for face_quadrature: a triangle is
@@ -187,48 +204,39 @@ static void sorted_key(const int64_t* nodes, int n, int64_t* key) {
 
 void orc_free(orc_mesh* m);
 
-/* simplex = 0: quads / hexes; 1: triangles / tetrahedra */
-orc_mesh* orc_create_cells(int dim, int simplex, int64_t nn, const double* xyz, int64_t nc,
-                           const int64_t* cell_nodes, int64_t nb,
-                           const int64_t* bface_nodes, const int* bface_tag) {
-  if (dim != 2 && dim != 3) return NULL;
-  orc_mesh* m = (orc_mesh*)calloc(1, sizeof(orc_mesh));
-  m->dim = dim;
-  m->simplex = simplex ? 1 : 0;
-  m->nv = simplex ? dim + 1 : (dim == 2 ? 4 : 8);
-  m->nlf = simplex ? dim + 1 : 2 * dim;
-  m->nfv = simplex ? dim : (dim == 2 ? 2 : 4);
-  m->nn = nn; m->nc = nc; m->nb = nb;
-  m->x = (double*)calloc((size_t)nn * 3, sizeof(double));
-  for (int64_t i = 0; i < nn; ++i)
-    for (int a = 0; a < dim; ++a) m->x[3 * i + a] = xyz[dim * i + a];
-  m->cn = (int64_t*)malloc(sizeof(int64_t) * nc * m->nv);
-  memcpy(m->cn, cell_nodes, sizeof(int64_t) * nc * m->nv);
-
+/* faces of the mesh from the cells' local faces: equal node sets pair up
+   into internal faces, the rest must be the boundary list */
+static orc_mesh* build_faces(orc_mesh* m, int64_t nb, const int64_t* bface_nodes,
+                             const int* bface_tag) {
+  int64_t nc = m->nc, nslot = nc * m->nlf, nrec = 0;
+  for (int64_t c = 0; c < nc; ++c)
+    for (int lf = 0; lf < m->nlf; ++lf) nrec += face_exists(m, c, lf);
   /* every local face of every cell, sorted by its node set */
-  int64_t nrec = nc * m->nlf;
-  face_rec* rec = (face_rec*)malloc(sizeof(face_rec) * nrec);
+  face_rec* rec = (face_rec*)malloc(sizeof(face_rec) * (nrec > 0 ? nrec : 1));
+  int64_t r_ = 0;
   for (int64_t c = 0; c < nc; ++c)
     for (int lf = 0; lf < m->nlf; ++lf) {
+      if (!face_exists(m, c, lf)) continue;
       int64_t nodes[4];
-      for (int k = 0; k < m->nfv; ++k) nodes[k] = m->cn[c * m->nv + lf_node(m, lf, k)];
-      face_rec* r = &rec[c * m->nlf + lf];
+      for (int k = 0; k < m->nfv; ++k) nodes[k] = cell_face_node(m, c, lf, k);
+      face_rec* r = &rec[r_++];
       sorted_key(nodes, m->nfv, r->key);
       r->cell = c;
       r->lf = lf;
     }
   qsort(rec, nrec, sizeof(face_rec), cmp_rec);
-  /* partner of each local face: pairs of equal keys are internal faces */
-  int64_t* partner = (int64_t*)malloc(sizeof(int64_t) * nrec); /* indexed c*nlf+lf */
-  for (int64_t i = 0; i < nrec; ++i) partner[rec[i].cell * m->nlf + rec[i].lf] = -1;
+  /* partner of each local face slot c*nlf+lf: pairs of equal keys are internal faces */
+  int64_t* partner = (int64_t*)malloc(sizeof(int64_t) * nslot);
+  for (int64_t i = 0; i < nslot; ++i) partner[i] = -1;
+  int ok = 1;
   for (int64_t i = 0; i + 1 < nrec; ++i)
     if (cmp_key(rec[i].key, rec[i + 1].key) == 0) {
+      if (i + 2 < nrec && cmp_key(rec[i].key, rec[i + 2].key) == 0) ok = 0;
       partner[rec[i].cell * m->nlf + rec[i].lf] = rec[i + 1].cell * m->nlf + rec[i + 1].lf;
       partner[rec[i + 1].cell * m->nlf + rec[i + 1].lf] = rec[i].cell * m->nlf + rec[i].lf;
     }
   /* boundary faces: find the owning local face of each */
   int64_t* bown = (int64_t*)malloc(sizeof(int64_t) * (nb > 0 ? nb : 1));
-  int ok = 1;
   for (int64_t b = 0; b < nb && ok; ++b) {
     face_rec q;
     sorted_key(bface_nodes + b * m->nfv, m->nfv, q.key);
@@ -244,12 +252,12 @@ orc_mesh* orc_create_cells(int dim, int simplex, int64_t nn, const double* xyz, 
     if (partner[id] >= 0) { ok = 0; break; }
     bown[b] = id;
   }
-  int64_t nfi = 0;
-  for (int64_t i = 0; i < nrec; ++i)
+  int64_t nfi = 0, nbound = 0;
+  for (int64_t i = 0; i < nslot; ++i) {
+    if (!face_exists(m, i / m->nlf, (int)(i % m->nlf))) continue;
     if (partner[i] > i) ++nfi;
-  int64_t nbound = 0;
-  for (int64_t i = 0; i < nrec; ++i)
     if (partner[i] < 0) ++nbound;
+  }
   if (nbound != nb) ok = 0;
   int64_t nfd = 0, nft = 0, nfy = 0;
   for (int64_t b = 0; b < nb; ++b) {
@@ -269,7 +277,8 @@ orc_mesh* orc_create_cells(int dim, int simplex, int64_t nn, const double* xyz, 
   m->flf = (int*)malloc(sizeof(int) * m->nf);
   m->ftag = (int*)malloc(sizeof(int) * m->nf);
   m->fnodes = (int64_t*)malloc(sizeof(int64_t) * m->nf * m->nfv);
-  m->cf = (int64_t*)malloc(sizeof(int64_t) * nc * m->nlf);
+  m->cf = (int64_t*)malloc(sizeof(int64_t) * nslot);
+  for (int64_t i = 0; i < nslot; ++i) m->cf[i] = -1;
   int64_t f = 0;
   for (int64_t c = 0; c < nc; ++c)
     for (int lf = 0; lf < m->nlf; ++lf) {
@@ -292,9 +301,57 @@ orc_mesh* orc_create_cells(int dim, int simplex, int64_t nn, const double* xyz, 
       }
   for (f = 0; f < m->nf; ++f)
     for (int k = 0; k < m->nfv; ++k)
-      m->fnodes[f * m->nfv + k] = m->cn[m->fown[f] * m->nv + lf_node(m, m->flf[f], k)];
+      m->fnodes[f * m->nfv + k] = cell_face_node(m, m->fown[f], m->flf[f], k);
   free(rec); free(partner); free(bown);
   return m;
+}
+
+/* simplex = 0: quads / hexes; 1: triangles / tetrahedra */
+orc_mesh* orc_create_cells(int dim, int simplex, int64_t nn, const double* xyz, int64_t nc,
+                           const int64_t* cell_nodes, int64_t nb,
+                           const int64_t* bface_nodes, const int* bface_tag) {
+  if (dim != 2 && dim != 3) return NULL;
+  orc_mesh* m = (orc_mesh*)calloc(1, sizeof(orc_mesh));
+  m->dim = dim;
+  m->simplex = simplex ? 1 : 0;
+  m->nv = simplex ? dim + 1 : (dim == 2 ? 4 : 8);
+  m->nlf = simplex ? dim + 1 : 2 * dim;
+  m->nfv = simplex ? dim : (dim == 2 ? 2 : 4);
+  m->nn = nn; m->nc = nc; m->nb = nb;
+  m->x = (double*)calloc((size_t)nn * 3, sizeof(double));
+  for (int64_t i = 0; i < nn; ++i)
+    for (int a = 0; a < dim; ++a) m->x[3 * i + a] = xyz[dim * i + a];
+  m->cn = (int64_t*)malloc(sizeof(int64_t) * nc * m->nv);
+  memcpy(m->cn, cell_nodes, sizeof(int64_t) * nc * m->nv);
+  return build_faces(m, nb, bface_nodes, bface_tag);
+}
+
+/* 2-D polygons (counter-clockwise corners, 3..POLY_MAX_SIDES of them):
+   cell c has corners cell_nodes[cell_ptr[c] .. cell_ptr[c+1]) */
+orc_mesh* orc_create_poly(int64_t nn, const double* xyz, int64_t nc, const int64_t* cell_ptr,
+                          const int64_t* cell_nodes, int64_t nb, const int64_t* bface_nodes,
+                          const int* bface_tag) {
+  for (int64_t c = 0; c < nc; ++c) {
+    int64_t k = cell_ptr[c + 1] - cell_ptr[c];
+    if (k < 3 || k > POLY_MAX_SIDES) return NULL;
+  }
+  orc_mesh* m = (orc_mesh*)calloc(1, sizeof(orc_mesh));
+  m->dim = 2;
+  m->poly = 1;
+  m->nv = m->nlf = POLY_MAX_SIDES;
+  m->nfv = 2;
+  m->nn = nn; m->nc = nc; m->nb = nb;
+  m->x = (double*)calloc((size_t)nn * 3, sizeof(double));
+  for (int64_t i = 0; i < nn; ++i)
+    for (int a = 0; a < 2; ++a) m->x[3 * i + a] = xyz[2 * i + a];
+  m->cn = (int64_t*)malloc(sizeof(int64_t) * nc * m->nv);
+  m->cnv = (int*)malloc(sizeof(int) * nc);
+  for (int64_t c = 0; c < nc; ++c) {
+    m->cnv[c] = (int)(cell_ptr[c + 1] - cell_ptr[c]);
+    for (int k = 0; k < m->nv; ++k)
+      m->cn[c * m->nv + k] = k < m->cnv[c] ? cell_nodes[cell_ptr[c] + k] : -1;
+  }
+  return build_faces(m, nb, bface_nodes, bface_tag);
 }
 
 orc_mesh* orc_create(int dim, int64_t nn, const double* xyz, int64_t nc,
@@ -313,7 +370,7 @@ void orc_free_subset(orc_mesh* m) {
 
 void orc_free(orc_mesh* m) {
   if (!m) return;
-  free(m->x); free(m->cn); free(m->fown); free(m->fnei); free(m->flf); free(m->ftag);
+  free(m->x); free(m->cn); free(m->cnv); free(m->fown); free(m->fnei); free(m->flf); free(m->ftag);
   free(m->fnodes); free(m->cf); free(m->xc); free(m->vol); free(m->xq); free(m->aq);
   free(m->xf); free(m->nrm); free(m->gam); free(m->cqx); free(m->cqw);
   orc_free_subset(m);
@@ -333,7 +390,7 @@ int orc_set_scheme(orc_mesh* m, int p, int nplus, int q1, double kw, double alph
   m->Nt = nt;
   m->S = nt + nplus;
   m->Q = m->dim == 2 ? q1 : q1 * q1;
-  m->QC = m->dim == 2 ? q1 * q1 : q1 * q1 * q1;
+  m->QC = m->poly ? m->nlf * q1 * q1 : m->dim == 2 ? q1 * q1 : q1 * q1 * q1;
   if (m->S > m->nc) return -2;
   orc_gauss_legendre(q1, m->gl_x, m->gl_w);
   m->have_scheme = 1;
@@ -387,6 +444,33 @@ static void face_quadrature(const orc_mesh* m, const double* corner /*[nfv][3]*/
     }
 }
 
+/* Gauss points and weights of the bilinear map of the quad with corners
+   P (counter-clockwise; a repeated corner collapses it to a triangle) */
+static void quad_rule(const orc_mesh* m, const double P[4][2], double* cqx, double* cqw) {
+  static const double R2[4][2] = {{0, 0}, {1, 0}, {1, 1}, {0, 1}};
+  int n = m->q1;
+  for (int a = 0; a < n; ++a)
+    for (int b = 0; b < n; ++b) {
+      double s[2] = {m->gl_x[a], m->gl_x[b]};
+      double X2[3] = {0, 0, 0}, J[2][2] = {{0, 0}, {0, 0}};
+      for (int k = 0; k < 4; ++k) {
+        double f0 = R2[k][0] ? s[0] : 1 - s[0], f1 = R2[k][1] ? s[1] : 1 - s[1];
+        double d0 = R2[k][0] ? 1 : -1, d1 = R2[k][1] ? 1 : -1;
+        double N = f0 * f1, dN0 = d0 * f1, dN1 = f0 * d1;
+        for (int e = 0; e < 2; ++e) {
+          double xv = P[k][e];
+          X2[e] += N * xv;
+          J[e][0] += dN0 * xv;
+          J[e][1] += dN1 * xv;
+        }
+      }
+      double det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+      int q = a * n + b;
+      for (int e = 0; e < 3; ++e) cqx[q * 3 + e] = X2[e];
+      cqw[q] = m->gl_w[a] * m->gl_w[b] * fabs(det);
+    }
+}
+
 int orc_geometry(orc_mesh* m) {
   if (!m->have_scheme) return -1;
   int d = m->dim, Q = m->Q, nfv = m->nfv;
@@ -428,8 +512,9 @@ int orc_geometry(orc_mesh* m) {
   for (int64_t c = 0; c < m->nc; ++c) {
     double V = 0, M2[3] = {0, 0, 0};
     for (int lf = 0; lf < m->nlf; ++lf) {
+      if (!face_exists(m, c, lf)) continue;
       int64_t fn[4];
-      for (int k = 0; k < nfv; ++k) fn[k] = m->cn[c * m->nv + lf_node(m, lf, k)];
+      for (int k = 0; k < nfv; ++k) fn[k] = cell_face_node(m, c, lf, k);
       face_corners(m, fn, corner);
       face_quadrature(m, corner, xq, aq);
       for (int q = 0; q < Q; ++q)
@@ -445,30 +530,37 @@ int orc_geometry(orc_mesh* m) {
        bilinear / trilinear map), eq. (bodyTerm) */
     int n = m->q1;
     int64_t cn[8];
-    cell_map_nodes(m, c, cn);
-    if (d == 2) {
-      static const double R2[4][2] = {{0, 0}, {1, 0}, {1, 1}, {0, 1}};
-      for (int a = 0; a < n; ++a)
-        for (int b = 0; b < n; ++b) {
-          double s[2] = {m->gl_x[a], m->gl_x[b]};
-          double X2[3] = {0, 0, 0}, J[2][2] = {{0, 0}, {0, 0}};
-          for (int k = 0; k < 4; ++k) {
-            double f0 = R2[k][0] ? s[0] : 1 - s[0], f1 = R2[k][1] ? s[1] : 1 - s[1];
-            double d0 = R2[k][0] ? 1 : -1, d1 = R2[k][1] ? 1 : -1;
-            double N = f0 * f1, dN0 = d0 * f1, dN1 = f0 * d1;
-            for (int e = 0; e < 2; ++e) {
-              double xv = m->x[3 * cn[k] + e];
-              X2[e] += N * xv;
-              J[e][0] += dN0 * xv;
-              J[e][1] += dN1 * xv;
-            }
+    if (m->poly) {
+      /* fan of triangles (xbar, corner t, corner t+1) from the corners'
+         average, each on the collapsed square; unused slots weigh zero */
+      double xb[2] = {0, 0};
+      int k = m->cnv[c];
+      for (int t = 0; t < k; ++t)
+        for (int e = 0; e < 2; ++e) xb[e] += m->x[3 * m->cn[c * m->nv + t] + e];
+      for (int e = 0; e < 2; ++e) xb[e] /= k;
+      for (int t = 0; t < m->nlf; ++t) {
+        double* qx = m->cqx + (c * m->QC + t * n * n) * 3;
+        double* qw = m->cqw + c * m->QC + t * n * n;
+        if (t >= k) {
+          for (int q = 0; q < n * n; ++q) {
+            qx[3 * q] = xb[0]; qx[3 * q + 1] = xb[1]; qx[3 * q + 2] = 0.0;
+            qw[q] = 0.0;
           }
-          double det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
-          int q = a * n + b;
-          for (int e = 0; e < 3; ++e) m->cqx[(c * m->QC + q) * 3 + e] = X2[e];
-          m->cqw[c * m->QC + q] = m->gl_w[a] * m->gl_w[b] * fabs(det);
+          continue;
         }
+        const double* v0 = m->x + 3 * m->cn[c * m->nv + t];
+        const double* v1 = m->x + 3 * m->cn[c * m->nv + (t + 1) % k];
+        double P4[4][2] = {{xb[0], xb[1]}, {v0[0], v0[1]}, {v1[0], v1[1]}, {xb[0], xb[1]}};
+        quad_rule(m, P4, qx, qw);
+      }
+    } else if (d == 2) {
+      cell_map_nodes(m, c, cn);
+      double P4[4][2];
+      for (int k = 0; k < 4; ++k)
+        for (int e = 0; e < 2; ++e) P4[k][e] = m->x[3 * cn[k] + e];
+      quad_rule(m, P4, m->cqx + c * m->QC * 3, m->cqw + c * m->QC);
     } else {
+      cell_map_nodes(m, c, cn);
       static const double R3[8][3] = {{0, 0, 0}, {1, 0, 0}, {1, 1, 0}, {0, 1, 0},
                                       {0, 0, 1}, {1, 0, 1}, {1, 1, 1}, {0, 1, 1}};
       for (int a = 0; a < n; ++a)
@@ -869,7 +961,7 @@ int orc_prepare(orc_mesh* m, int64_t nsub, const int64_t* cells) {
     if (m->cslot[c] < 0) m->cslot[c] = ncs++;
     for (int lf = 0; lf < nlf; ++lf) {
       int64_t f = m->cf[c * nlf + lf];
-      if (m->ftag[f] == 1) continue;
+      if (f < 0 || m->ftag[f] == 1) continue;
       if (m->fslot[f] < 0) m->fslot[f] = nfs++;
       if (m->ftag[f] < 0) {
         int64_t o = m->fown[f] == c ? m->fnei[f] : m->fown[f];
@@ -928,6 +1020,7 @@ int orc_prepare(orc_mesh* m, int64_t nsub, const int64_t* cells) {
        of order 1..p evaluated at d_Pf, applied to the derivative rows */
     for (int lf = 0; lf < nlf; ++lf) {
       int64_t f = m->cf[c * nlf + lf];
+      if (f < 0) continue;  /* polygon slot past its last side */
       double X[3] = {0, 0, 0}, g[20];
       for (int a = 0; a < d; ++a) X[a] = (m->xf[3 * f + a] - m->xc[3 * c + a]) / h;
       taylor_basis(d, m->p, X, g);
@@ -1138,6 +1231,7 @@ int orc_residual(const orc_mesh* m, int law, double mu, double lam, const double
     double r[3] = {0, 0, 0}, fl[3];
     for (int lf = 0; lf < nlf; ++lf) {
       int64_t f = m->cf[c * nlf + lf];
+      if (f < 0) continue;
       face_flux(m, f, law, mu, lam, u, ubq, ubf, tbq, fl);
       double sg = m->fown[f] == c ? 1.0 : -1.0;
       for (int j = 0; j < d; ++j) r[j] += sg * fl[j];

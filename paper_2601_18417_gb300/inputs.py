@@ -71,6 +71,8 @@ class Mesh:
     bface_nodes  [n_bfaces, 2**(d-1)] (simplex: [n_bfaces, d]) node ids of
                  boundary faces, outward order
     bface_side   [n_bfaces] domain side: 0 x-, 1 x+, 2 y-, 3 y+, 4 z-, 5 z+
+    cell_ptr     polygon meshes (d = 2) only: [n_cells + 1] offsets into the
+                 flat cell_nodes, each polygon counter-clockwise
     """
 
     dim: int
@@ -81,9 +83,12 @@ class Mesh:
     bface_side: np.ndarray
     length: float = 1.0
     simplex: bool = False
+    cell_ptr: np.ndarray | None = None   # polygon meshes: cell c is cell_nodes[ptr[c]:ptr[c+1]]
 
     @property
     def n_cells(self) -> int:
+        if self.cell_ptr is not None:
+            return int(self.cell_ptr.shape[0] - 1)
         return int(self.cell_nodes.shape[0])
 
     @property
@@ -220,13 +225,78 @@ def simplex_mesh(dim: int, n: int, length: float = 1.0, jitter: float = 0.0,
                 bface_side=side[order].astype(np.int32), length=length, simplex=True)
 
 
+def polygon_mesh(n: int, length: float = 1.0, jitter: float = 0.0, seed: int = 0) -> Mesh:
+    """Polygonal cells: the dual of simplex_mesh(2, n, ...), built the way a
+    dual mesh generator builds it.  Each node of the triangle mesh becomes a
+    cell whose corners are the centroids of its triangles, in turn around
+    it; a node on the boundary also keeps itself and the midpoints of its two
+    boundary edges as corners, so the dual covers the square exactly.
+    Interior cells have 4 to 8 sides (one per triangle at the node).  Every
+    fan triangle from a cell's vertex average to one of its sides is checked
+    to be positively oriented (raises otherwise)."""
+    tri = simplex_mesh(2, n, length, jitter, seed)
+    X, T = tri.xyz, tri.cell_nodes
+    nn, nt = X.shape[0], T.shape[0]
+    cent = X[T].mean(axis=1)
+    bn = tri.bface_nodes                          # [nb, 2], outward (counter-clockwise)
+    mid = 0.5 * (X[bn[:, 0]] + X[bn[:, 1]])
+    bnodes = np.unique(bn.ravel())
+    # dual node ids: triangle centroids, boundary-edge midpoints, boundary nodes
+    mid0, bn0 = nt, nt + bn.shape[0]
+    bnode_id = np.full(nn, -1, np.int64)
+    bnode_id[bnodes] = bn0 + np.arange(bnodes.size)
+    xyz = np.concatenate([cent, mid, X[bnodes]])
+    around = [[] for _ in range(nn)]
+    for t in range(nt):
+        for v in T[t]:
+            around[v].append(t)
+    bedges = [[] for _ in range(nn)]
+    for e, (a, b) in enumerate(bn):
+        bedges[a].append(e)
+        bedges[b].append(e)
+    ptr, flat = [0], []
+    for v in range(nn):
+        ids = [t for t in around[v]] + [mid0 + e for e in bedges[v]]
+        if bnode_id[v] >= 0:
+            ids.append(int(bnode_id[v]))
+        P = xyz[ids]
+        c = P.mean(axis=0)
+        ang = np.arctan2(P[:, 1] - c[1], P[:, 0] - c[0])
+        ids = [ids[k] for k in np.argsort(ang, kind="stable")]
+        flat.extend(ids)
+        ptr.append(len(flat))
+    ptr = np.asarray(ptr, np.int64)
+    flat = np.asarray(flat, np.int64)
+    for v in range(nn):
+        poly = xyz[flat[ptr[v]:ptr[v + 1]]]
+        c = poly.mean(axis=0)
+        e0, e1 = poly - c, np.roll(poly, -1, axis=0) - c
+        if np.any(e0[:, 0] * e1[:, 1] - e0[:, 1] * e1[:, 0] <= 0):
+            raise ValueError("a dual cell is not star-shaped about its vertex average")
+    # boundary faces: the halves of each boundary edge, (a, mid) for cell a and
+    # (mid, b) for cell b, on the edge's domain side
+    faces, sides = [], []
+    for e, (a, b) in enumerate(bn):
+        faces.append((bnode_id[a], mid0 + e))
+        faces.append((mid0 + e, bnode_id[b]))
+        sides += [tri.bface_side[e]] * 2
+    return Mesh(dim=2, n=n, xyz=np.ascontiguousarray(xyz), cell_nodes=flat,
+                bface_nodes=np.asarray(faces, np.int64), bface_side=np.asarray(sides, np.int32),
+                length=length, cell_ptr=ptr)
+
+
 def make_mesh(dim: int, n: int, length: float = 1.0, jitter: float = 0.0, seed: int = 0,
               cells: str = "tensor") -> Mesh:
-    """structured_mesh (cells="tensor") or simplex_mesh (cells="simplex")."""
+    """structured_mesh (cells="tensor"), simplex_mesh (cells="simplex") or,
+    in 2-D, polygon_mesh (cells="polygon", (n + 1)^2 cells)."""
     if cells == "simplex":
         return simplex_mesh(dim, n, length, jitter, seed)
+    if cells == "polygon":
+        if dim != 2:
+            raise ValueError("polygon meshes are two-dimensional")
+        return polygon_mesh(n, length, jitter, seed)
     if cells != "tensor":
-        raise ValueError("cells must be 'tensor' or 'simplex'")
+        raise ValueError("cells must be 'tensor', 'simplex' or 'polygon'")
     return structured_mesh(dim, n, length, jitter, seed)
 
 

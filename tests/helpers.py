@@ -90,8 +90,8 @@ def force_scale(orc: oracle.OracleMesh, law, mu, lam, u, ubq, ubf, tbq):
     """F_s = max over cells of the sum over its faces of |flux_f|."""
     fl = orc.face_fluxes(law, mu, lam, u, ubq, ubf, tbq)
     mag = np.linalg.norm(fl, axis=1)
-    cf = orc.cell_faces()
-    return float(np.max(mag[cf].sum(axis=1)))
+    cf = orc.cell_faces()  # -1 marks a polygon slot past its last side
+    return float(np.max(np.where(cf >= 0, mag[np.maximum(cf, 0)], 0.0).sum(axis=1)))
 
 
 def residual(pb: Problem, u, cells=None):
@@ -108,8 +108,11 @@ def probe_jacobian(pb: Problem, K: int | None = None):
     if K is None:
         K = min(n, 12)
     idx = np.arange(nc)
-    per = nc // n ** d  # cells per grid square / cube (simplex meshes: 2 or 6)
-    ij = np.stack(np.unravel_index(idx // per, (n,) * d)[::-1], axis=1)  # (i, j[, k])
+    if pb.mesh.cell_ptr is not None:  # polygon dual: one cell per grid node
+        per, g = 1, n + 1
+    else:  # cells per grid square / cube (simplex meshes: 2 or 6)
+        per, g = nc // n ** d, n
+    ij = np.stack(np.unravel_index(idx // per, (g,) * d)[::-1], axis=1)  # (i, j[, k])
     color = np.zeros(nc, np.int64)
     for a in range(d):
         color = color * K + (ij[:, a] % K)
