@@ -137,6 +137,9 @@ def build_workload(name, device=0):
 
 
 def mesh_label(wl):
+    if wl.cells == "polygon":
+        return (f"{wl.n + 1}^2 polygons (dual of 2 x {wl.n}^2 triangles), "
+                f"{int(round(wl.jitter * 100))}% node jitter")
     if wl.cells == "simplex":
         shape = ("2 x {n}^2 triangles" if wl.dim == 2 else "6 x {n}^3 tetrahedra").format(n=wl.n)
     else:
@@ -154,7 +157,7 @@ def algorithmic_counts(wl, lay):
     bytes_face = 8 * R * S + 4 * S + 8 * Q * 3 + 8 + 8 + 8 * d + 2 * 8 * d
     bytes_ = nfid * bytes_face + lay.n_disp * (8 * R + 8 * Q * d + 8 * d) + 8 * d * lay.n_cells
     # the whole residual (u* prepass + fluxes + assembly), for the HBM view
-    nlf = d + 1 if wl.cells == "simplex" else 2 * d
+    nlf = {"simplex": d + 1, "polygon": 8}.get(wl.cells, 2 * d)
     res_bytes = bytes_ + lay.n_cells * (8 * nlf * S + 4 * S + 8 * d + 8 * nlf * d * 2
                                         + 8 * d * 2 + 4 * nlf)
     return flops, bytes_, res_bytes

@@ -29,7 +29,8 @@
  *     in the order of the boundary-face list given to hofv_set_mesh.  Local
  *     faces of a quad / hex are x-, x+, y-, y+ (, z-, z+) of its reference
  *     element; local face k of a triangle runs from node k to node k+1 mod 3,
- *     and local face k of a tetrahedron is the face opposite node 3 - k.
+ *     local face k of a tetrahedron is the face opposite node 3 - k, and
+ *     local face k of a polygon runs from its corner k to corner k+1.
  *   - Gradients: grad[i][j] = d u_j / d x_i, the paper's sum of c (x) u
  *     (Sec. 3.5.4, eq. faceQuadGrad).
  */
@@ -181,6 +182,26 @@ int hofv_set_mesh_cells(hofv_ctx* ctx, int dim, int cell_kind, int64_t n_nodes,
                         const double* xyz, int64_t n_cells, const int64_t* cell_nodes,
                         int64_t n_bfaces, const int64_t* bface_nodes,
                         const int32_t* bface_tag);
+
+/* hofv_set_mesh for a 2-D mesh of polygons with 3 to 8 corners each, e.g.
+   the dual of a triangle mesh.  HOST arrays, copied in:
+     xyz         [n_nodes][2]
+     cell_ptr    [n_cells + 1], cell_ptr[0] = 0; cell c has the corners
+                 cell_nodes[cell_ptr[c] .. cell_ptr[c+1]), counter-clockwise
+     bface_nodes [n_bfaces][2], bface_tag [n_bfaces] as hofv_set_mesh
+   Local face k of a cell runs from its corner k to corner k+1; every cell
+   keeps 8 face slots (ext rows of hofv_get_cell_data), those past its last
+   side holding no face.  Faces are straight edges with q_per_dir Gauss
+   points; the cell rule is the fan of triangles from the corners' average
+   to each side, q_per_dir^2 points on each (collapsed square), 8 q_per_dir^2
+   points per cell with zero weights past the last side.  Errors as
+   hofv_set_mesh; EINVAL for a polygon with fewer than 3 or more than 8
+   corners, or one that is not counter-clockwise and star-shaped about its
+   corners' average. */
+int hofv_set_mesh_polygons(hofv_ctx* ctx, int64_t n_nodes, const double* xyz, int64_t n_cells,
+                           const int64_t* cell_ptr, const int64_t* cell_nodes,
+                           int64_t n_bfaces, const int64_t* bface_nodes,
+                           const int32_t* bface_tag);
 
 /* Scheme (Sec. 3.5): reconstruction degree p in 1..3, surplus stencil nodes
    n_plus (|S| = N_t + n_plus; the paper uses 10 in 2-D and 45/55/65 in 3-D),
@@ -438,7 +459,8 @@ int hofv_get_face_data(hofv_ctx* ctx, int64_t first, int64_t count, int32_t* ste
 /* Cell data for cells [first, first + count) to HOST arrays (any may be NULL):
      stencil [count][S] int32;  ext [count][F][S] weights e with
      u*_{f,P} = u_P + sum_N e_N u_N (eq. alphaJump); F = faces per cell
-     (2 dim for quads / hexes, dim + 1 for triangles / tetrahedra). */
+     (2 dim for quads / hexes, dim + 1 for triangles / tetrahedra, 8 slots
+     for polygons, zero rows past a polygon's last side). */
 int hofv_get_cell_data(hofv_ctx* ctx, int64_t first, int64_t count, int32_t* stencil,
                        double* ext);
 

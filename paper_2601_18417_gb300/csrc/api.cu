@@ -89,6 +89,17 @@ static int lf_node(const hofv_ctx* c, int lf, int k) {
   return c->dim == 2 ? kQuadLF[lf][k] : kHexLF[lf][k];
 }
 
+// a polygon has one local face per side, from corner k to corner k+1;
+// slots past its last side hold no face
+static bool face_exists(const hofv_ctx* c, int64_t cell, int lf) {
+  return !c->poly || lf < c->cnv[cell];
+}
+
+static int64_t cell_face_node(const hofv_ctx* c, int64_t cell, int lf, int k) {
+  if (c->poly) return c->cn[cell * c->nv + (lf + k) % c->cnv[cell]];
+  return c->cn[cell * c->nv + lf_node(c, lf, k)];
+}
+
 // Gauss-Legendre rule on [0, 1] (closed forms of the 1..4 point rules on
 // [-1, 1], mapped by x = (t + 1) / 2, w = c / 2)
 static void gauss_rule(int n, double* x, double* w) {
@@ -248,57 +259,15 @@ void hofv_destroy(hofv_ctx* c) {
 
 const char* hofv_last_error(const hofv_ctx* c) { return c ? c->err.c_str() : "null context"; }
 
-int hofv_set_mesh(hofv_ctx* c, int dim, int64_t nn, const double* xyz, int64_t nc,
-                  const int64_t* cell_nodes, int64_t nb, const int64_t* bface_nodes,
-                  const int32_t* bface_tag) {
-  return hofv_set_mesh_cells(c, dim, HOFV_CELL_TENSOR, nn, xyz, nc, cell_nodes, nb, bface_nodes,
-                             bface_tag);
-}
-
-int hofv_set_mesh_cells(hofv_ctx* c, int dim, int cell_kind, int64_t nn, const double* xyz,
-                        int64_t nc, const int64_t* cell_nodes, int64_t nb,
-                        const int64_t* bface_nodes, const int32_t* bface_tag) {
-  if (!c) return HOFV_EINVAL;
-  invalidate_graphs(c);
-  if (dim != 2 && dim != 3) return fail(c, HOFV_EINVAL, "dim must be 2 or 3");
-  if (cell_kind != HOFV_CELL_TENSOR && cell_kind != HOFV_CELL_SIMPLEX)
-    return fail(c, HOFV_EINVAL, "cell_kind must be HOFV_CELL_TENSOR or HOFV_CELL_SIMPLEX");
-  if (nn <= 0 || nc <= 0 || !xyz || !cell_nodes || nb < 0 || (nb > 0 && (!bface_nodes || !bface_tag)))
-    return fail(c, HOFV_EINVAL, "empty mesh or null array");
-  if (nn >= (int64_t)1 << 31 || nc >= (int64_t)1 << 30)
-    return fail(c, HOFV_EINVAL, "mesh too large for 32-bit ids");
-  free_built(c);
-  c->have_mesh = false;
-  c->dim = dim;
-  c->simplex = cell_kind == HOFV_CELL_SIMPLEX;
-  c->nv = c->simplex ? dim + 1 : (dim == 2 ? 4 : 8);
-  c->nlf = c->simplex ? dim + 1 : 2 * dim;
-  c->nfv = c->simplex ? dim : (dim == 2 ? 2 : 4);
-  c->nn = nn;
-  c->nc = nc;
-  c->nb = nb;
-  c->x.assign((size_t)nn * 3, 0.0);
-  for (int64_t i = 0; i < nn; ++i)
-    for (int a = 0; a < dim; ++a) c->x[3 * i + a] = xyz[dim * i + a];
-  c->cn.assign(cell_nodes, cell_nodes + nc * c->nv);
-  for (int64_t i = 0; i < nc * c->nv; ++i)
-    if (c->cn[i] < 0 || c->cn[i] >= nn) return fail(c, HOFV_EINVAL, "cell node id out of range");
-  if (c->simplex)
-    for (int64_t cell = 0; cell < nc; ++cell) {
-      const int64_t* v = &c->cn[cell * c->nv];
-      double e[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-      for (int k = 1; k <= dim; ++k)
-        for (int a = 0; a < dim; ++a) e[k - 1][a] = c->x[3 * v[k] + a] - c->x[3 * v[0] + a];
-      const double det = dim == 2 ? e[0][0] * e[1][1] - e[0][1] * e[1][0]
-                                  : e[0][0] * (e[1][1] * e[2][2] - e[1][2] * e[2][1]) -
-                                        e[0][1] * (e[1][0] * e[2][2] - e[1][2] * e[2][0]) +
-                                        e[0][2] * (e[1][0] * e[2][1] - e[1][1] * e[2][0]);
-      if (!(det > 0)) return fail(c, HOFV_EINVAL, "simplex cell not positively oriented");
-    }
+// faces from the cells' local faces: equal node sets pair up into internal
+// faces, the rest must be exactly the boundary list
+static int build_faces(hofv_ctx* c, int64_t nb, const int64_t* bface_nodes,
+                       const int32_t* bface_tag) {
   for (int64_t b = 0; b < nb; ++b) {
     if (bface_tag[b] < 0 || bface_tag[b] > 2) return fail(c, HOFV_EINVAL, "bad boundary tag");
   }
   // local faces keyed by their sorted node ids
+  const int64_t nc = c->nc;
   const int nlf = c->nlf, nfv = c->nfv;
   struct Rec {
     std::array<int64_t, 4> key;
@@ -310,13 +279,14 @@ int hofv_set_mesh_cells(hofv_ctx* c, int dim, int cell_kind, int64_t nn, const d
     std::sort(k.begin(), k.begin() + nfv);
     return k;
   };
-  std::vector<Rec> recs((size_t)nc * nlf);
+  std::vector<Rec> recs;
+  recs.reserve((size_t)nc * nlf);
   for (int64_t cell = 0; cell < nc; ++cell)
     for (int lf = 0; lf < nlf; ++lf) {
+      if (!face_exists(c, cell, lf)) continue;
       int64_t nodes[4];
-      for (int k = 0; k < nfv; ++k)
-        nodes[k] = c->cn[cell * c->nv + lf_node(c, lf, k)];
-      recs[cell * nlf + lf] = {make_key(nodes), cell * nlf + lf};
+      for (int k = 0; k < nfv; ++k) nodes[k] = cell_face_node(c, cell, lf, k);
+      recs.push_back({make_key(nodes), cell * nlf + lf});
     }
   std::sort(recs.begin(), recs.end(), [](const Rec& a, const Rec& b) {
     return a.key != b.key ? a.key < b.key : a.id < b.id;
@@ -330,7 +300,7 @@ int hofv_set_mesh_cells(hofv_ctx* c, int dim, int cell_kind, int64_t nn, const d
       partner[recs[i + 1].id] = recs[i].id;
     }
   int64_t nbound = 0;
-  for (int64_t i = 0; i < nc * nlf; ++i) nbound += partner[i] < 0;
+  for (int64_t i = 0; i < nc * nlf; ++i) nbound += partner[i] < 0 && face_exists(c, i / nlf, (int)(i % nlf));
   if (nbound != nb) return fail(c, HOFV_EINVAL, "boundary face list does not match the mesh boundary");
   std::vector<int64_t> bown((size_t)nb);
   std::vector<char> seen((size_t)nc * nlf, 0);
@@ -387,12 +357,118 @@ int hofv_set_mesh_cells(hofv_ctx* c, int dim, int cell_kind, int64_t nn, const d
   for (f = 0; f < c->nf; ++f)
     for (int k = 0; k < nfv; ++k) {
       const int lf = c->flf[f];
-      c->fnodes[f * nfv + k] =
-          (int32_t)c->cn[c->fown[f] * c->nv + lf_node(c, lf, k)];
+      c->fnodes[f * nfv + k] = (int32_t)cell_face_node(c, c->fown[f], lf, k);
     }
   c->have_mesh = true;
   c->built = false;
   return HOFV_OK;
+}
+
+int hofv_set_mesh(hofv_ctx* c, int dim, int64_t nn, const double* xyz, int64_t nc,
+                  const int64_t* cell_nodes, int64_t nb, const int64_t* bface_nodes,
+                  const int32_t* bface_tag) {
+  return hofv_set_mesh_cells(c, dim, HOFV_CELL_TENSOR, nn, xyz, nc, cell_nodes, nb, bface_nodes,
+                             bface_tag);
+}
+
+int hofv_set_mesh_cells(hofv_ctx* c, int dim, int cell_kind, int64_t nn, const double* xyz,
+                        int64_t nc, const int64_t* cell_nodes, int64_t nb,
+                        const int64_t* bface_nodes, const int32_t* bface_tag) {
+  if (!c) return HOFV_EINVAL;
+  invalidate_graphs(c);
+  if (dim != 2 && dim != 3) return fail(c, HOFV_EINVAL, "dim must be 2 or 3");
+  if (cell_kind != HOFV_CELL_TENSOR && cell_kind != HOFV_CELL_SIMPLEX)
+    return fail(c, HOFV_EINVAL, "cell_kind must be HOFV_CELL_TENSOR or HOFV_CELL_SIMPLEX");
+  if (nn <= 0 || nc <= 0 || !xyz || !cell_nodes || nb < 0 || (nb > 0 && (!bface_nodes || !bface_tag)))
+    return fail(c, HOFV_EINVAL, "empty mesh or null array");
+  if (nn >= (int64_t)1 << 31 || nc >= (int64_t)1 << 30)
+    return fail(c, HOFV_EINVAL, "mesh too large for 32-bit ids");
+  free_built(c);
+  c->have_mesh = false;
+  c->dim = dim;
+  c->poly = false;
+  c->cnv.clear();
+  c->simplex = cell_kind == HOFV_CELL_SIMPLEX;
+  c->nv = c->simplex ? dim + 1 : (dim == 2 ? 4 : 8);
+  c->nlf = c->simplex ? dim + 1 : 2 * dim;
+  c->nfv = c->simplex ? dim : (dim == 2 ? 2 : 4);
+  c->nn = nn;
+  c->nc = nc;
+  c->nb = nb;
+  c->x.assign((size_t)nn * 3, 0.0);
+  for (int64_t i = 0; i < nn; ++i)
+    for (int a = 0; a < dim; ++a) c->x[3 * i + a] = xyz[dim * i + a];
+  c->cn.assign(cell_nodes, cell_nodes + nc * c->nv);
+  for (int64_t i = 0; i < nc * c->nv; ++i)
+    if (c->cn[i] < 0 || c->cn[i] >= nn) return fail(c, HOFV_EINVAL, "cell node id out of range");
+  if (c->simplex)
+    for (int64_t cell = 0; cell < nc; ++cell) {
+      const int64_t* v = &c->cn[cell * c->nv];
+      double e[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+      for (int k = 1; k <= dim; ++k)
+        for (int a = 0; a < dim; ++a) e[k - 1][a] = c->x[3 * v[k] + a] - c->x[3 * v[0] + a];
+      const double det = dim == 2 ? e[0][0] * e[1][1] - e[0][1] * e[1][0]
+                                  : e[0][0] * (e[1][1] * e[2][2] - e[1][2] * e[2][1]) -
+                                        e[0][1] * (e[1][0] * e[2][2] - e[1][2] * e[2][0]) +
+                                        e[0][2] * (e[1][0] * e[2][1] - e[1][1] * e[2][0]);
+      if (!(det > 0)) return fail(c, HOFV_EINVAL, "simplex cell not positively oriented");
+    }
+  return build_faces(c, nb, bface_nodes, bface_tag);
+}
+
+int hofv_set_mesh_polygons(hofv_ctx* c, int64_t nn, const double* xyz, int64_t nc,
+                           const int64_t* cell_ptr, const int64_t* cell_nodes, int64_t nb,
+                           const int64_t* bface_nodes, const int32_t* bface_tag) {
+  if (!c) return HOFV_EINVAL;
+  invalidate_graphs(c);
+  if (nn <= 0 || nc <= 0 || !xyz || !cell_ptr || !cell_nodes || nb < 0 ||
+      (nb > 0 && (!bface_nodes || !bface_tag)))
+    return fail(c, HOFV_EINVAL, "empty mesh or null array");
+  if (nn >= (int64_t)1 << 31 || nc >= (int64_t)1 << 30)
+    return fail(c, HOFV_EINVAL, "mesh too large for 32-bit ids");
+  if (cell_ptr[0] != 0) return fail(c, HOFV_EINVAL, "cell_ptr[0] must be 0");
+  for (int64_t cell = 0; cell < nc; ++cell) {
+    const int64_t k = cell_ptr[cell + 1] - cell_ptr[cell];
+    if (k < 3 || k > kPolyMaxSides)
+      return fail(c, HOFV_EINVAL, "a polygon must have 3 to 8 corners");
+  }
+  free_built(c);
+  c->have_mesh = false;
+  c->dim = 2;
+  c->simplex = false;
+  c->poly = true;
+  c->nv = c->nlf = kPolyMaxSides;
+  c->nfv = 2;
+  c->nn = nn;
+  c->nc = nc;
+  c->nb = nb;
+  c->x.assign((size_t)nn * 3, 0.0);
+  for (int64_t i = 0; i < nn; ++i)
+    for (int a = 0; a < 2; ++a) c->x[3 * i + a] = xyz[2 * i + a];
+  c->cn.assign((size_t)nc * c->nv, -1);
+  c->cnv.assign((size_t)nc, 0);
+  for (int64_t cell = 0; cell < nc; ++cell) {
+    const int64_t k = cell_ptr[cell + 1] - cell_ptr[cell];
+    c->cnv[cell] = (int32_t)k;
+    for (int64_t j = 0; j < k; ++j) {
+      const int64_t v = cell_nodes[cell_ptr[cell] + j];
+      if (v < 0 || v >= nn) return fail(c, HOFV_EINVAL, "cell node id out of range");
+      c->cn[cell * c->nv + j] = v;
+    }
+    // every fan triangle (corner average, corner j, corner j+1) positively oriented
+    double xb[2] = {0, 0};
+    for (int64_t j = 0; j < k; ++j)
+      for (int a = 0; a < 2; ++a) xb[a] += c->x[3 * c->cn[cell * c->nv + j] + a];
+    for (int a = 0; a < 2; ++a) xb[a] /= (double)k;
+    for (int64_t j = 0; j < k; ++j) {
+      const double* p0 = &c->x[3 * c->cn[cell * c->nv + j]];
+      const double* p1 = &c->x[3 * c->cn[cell * c->nv + (j + 1) % k]];
+      const double cr = (p0[0] - xb[0]) * (p1[1] - xb[1]) - (p0[1] - xb[1]) * (p1[0] - xb[0]);
+      if (!(cr > 0))
+        return fail(c, HOFV_EINVAL, "polygon not counter-clockwise and star-shaped about its corners' average");
+    }
+  }
+  return build_faces(c, nb, bface_nodes, bface_tag);
 }
 
 int hofv_set_scheme(hofv_ctx* c, int p, int n_plus, int q1, double k_weight, double alpha) {
@@ -414,7 +490,7 @@ int hofv_set_scheme(hofv_ctx* c, int p, int n_plus, int q1, double k_weight, dou
   c->Nt = nt;
   c->S = nt + n_plus;
   c->Q = c->dim == 2 ? q1 : q1 * q1;
-  c->QC = c->dim == 2 ? q1 * q1 : q1 * q1 * q1;
+  c->QC = c->poly ? c->nlf * q1 * q1 : c->dim == 2 ? q1 * q1 : q1 * q1 * q1;
   c->kw = k_weight;
   c->alpha = alpha;
   gauss_rule(q1, c->gl_x, c->gl_w);
@@ -457,8 +533,8 @@ int hofv_build_stencils(hofv_ctx* c) {
   HOFV_CUDA(c, cudaMemcpy(c->d_fnei, tmp32.data(), sizeof(int32_t) * nf, cudaMemcpyHostToDevice));
   for (int64_t cell = 0; cell < nc; ++cell)
     for (int lf = 0; lf < nlf; ++lf) {
-      const int64_t f = c->cf[cell * nlf + lf];
-      tmp32[cell * nlf + lf] = c->ftag[f] == 1 ? 0 : (c->fown[f] == cell ? (int32_t)(f + 1) : -(int32_t)(f + 1));
+      const int64_t f = c->cf[cell * nlf + lf];  // -1: polygon slot without a face
+      tmp32[cell * nlf + lf] = f < 0 || c->ftag[f] == 1 ? 0 : (c->fown[f] == cell ? (int32_t)(f + 1) : -(int32_t)(f + 1));
     }
   HOFV_CUDA(c, cudaMemcpy(c->d_cface, tmp32.data(), sizeof(int32_t) * nc * nlf, cudaMemcpyHostToDevice));
   std::vector<int32_t>().swap(tmp32);

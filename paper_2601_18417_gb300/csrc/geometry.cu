@@ -6,7 +6,8 @@
 // use the same tensor rules on the collapsed square / cube (Duffy's
 // transformation): a triangular face is the bilinear patch (a, b, c, a), a
 // triangle cell the bilinear map of (0, 1, 2, 0) and a tetrahedron the
-// trilinear map of (0, 1, 2, 0, 0, 1, 3, 0).
+// trilinear map of (0, 1, 2, 0, 0, 1, 3, 0).  A polygon's cell rule is the
+// fan of such collapsed triangles from its corners' average.
 //
 // This unit is compiled without FMA contraction and evaluates every
 // expression in a fixed order, so that face centres and centroids -- which
@@ -104,22 +105,58 @@ __global__ void k_face_geometry(int dim, int nfv, int Q, int64_t nf, Gauss g,
   }
 }
 
+// Gauss points and weights of the bilinear map of the quad with corners P
+// (counter-clockwise; a repeated corner collapses it to a triangle)
+__device__ void quad_cell_points(const Gauss& g, const double (*P)[3], double* cqx, double* cqw) {
+  const int n = g.n;
+  for (int a = 0; a < n; ++a)
+    for (int b = 0; b < n; ++b) {
+      const double s = g.x[a], t = g.x[b];
+      const double N[4] = {(1 - s) * (1 - t), s * (1 - t), s * t, (1 - s) * t};
+      const double Ns[4] = {-(1 - t), 1 - t, t, -t};
+      const double Nt[4] = {-(1 - s), -s, s, 1 - s};
+      double X[2] = {0, 0}, J00 = 0, J01 = 0, J10 = 0, J11 = 0;
+      for (int k = 0; k < 4; ++k) {
+        X[0] += N[k] * P[k][0];
+        X[1] += N[k] * P[k][1];
+        J00 += Ns[k] * P[k][0];
+        J01 += Nt[k] * P[k][0];
+        J10 += Ns[k] * P[k][1];
+        J11 += Nt[k] * P[k][1];
+      }
+      const int q = a * n + b;
+      cqx[q * 3 + 0] = X[0];
+      cqx[q * 3 + 1] = X[1];
+      cqx[q * 3 + 2] = 0.0;
+      cqw[q] = g.w[a] * g.w[b] * fabs(J00 * J11 - J01 * J10);
+    }
+}
+
 // volume and centroid from the divergence theorem over the cell's own
-// outward faces; Gauss points of the bilinear / trilinear cell map
-__global__ void k_cell_geometry(int dim, bool simplex, int nv, int nlf, int nfv, int Q, int QC,
-                                int64_t nc, Gauss g, const double* __restrict__ x,
+// outward faces; Gauss points of the bilinear / trilinear cell map.  A
+// polygon (poly: corners padded with -1 up to nv) uses its sides as faces
+// and, for the cell rule, the fan of collapsed triangles from its corners'
+// average, one block of n^2 points per slot (zero weight past the last side).
+__global__ void k_cell_geometry(int dim, bool simplex, bool poly, int nv, int nlf, int nfv, int Q,
+                                int QC, int64_t nc, Gauss g, const double* __restrict__ x,
                                 const int32_t* __restrict__ cnodes, double* xc, double* vol,
                                 double* cqx, double* cqw) {
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= nc) return;
+  int nk = nv;  // corners present
+  if (poly) {
+    nk = 0;
+    while (nk < nv && cnodes[c * nv + nk] >= 0) ++nk;
+  }
   double cx[8][3];
-  for (int k = 0; k < nv; ++k)
+  for (int k = 0; k < nk; ++k)
     for (int a = 0; a < 3; ++a) cx[k][a] = x[3 * (int64_t)cnodes[c * nv + k] + a];
   double V = 0, M2[3] = {0, 0, 0};
-  for (int lf = 0; lf < nlf; ++lf) {
+  const int nfaces = poly ? nk : nlf;
+  for (int lf = 0; lf < nfaces; ++lf) {
     double corner[12];
     for (int k = 0; k < nfv; ++k) {
-      const int node = local_face_node(dim, simplex, lf, k);
+      const int node = poly ? (lf + k) % nk : local_face_node(dim, simplex, lf, k);
       for (int a = 0; a < 3; ++a) corner[3 * k + a] = cx[node][a];
     }
     if (dim == 3 && nfv == 3)
@@ -135,6 +172,31 @@ __global__ void k_cell_geometry(int dim, bool simplex, int nv, int nlf, int nfv,
   V /= dim;
   vol[c] = V;
   for (int a = 0; a < 3; ++a) xc[3 * c + a] = a < dim ? M2[a] / (2.0 * V) : 0.0;
+  const int n = g.n;
+  if (poly) {
+    double xb[3] = {0, 0, 0};
+    for (int k = 0; k < nk; ++k)
+      for (int a = 0; a < 2; ++a) xb[a] += cx[k][a];
+    for (int a = 0; a < 2; ++a) xb[a] /= nk;
+    for (int t = 0; t < nlf; ++t) {
+      double* qx = cqx + (c * QC + t * n * n) * 3;
+      double* qw = cqw + c * QC + t * n * n;
+      if (t >= nk) {
+        for (int q = 0; q < n * n; ++q) {
+          for (int a = 0; a < 3; ++a) qx[3 * q + a] = xb[a];
+          qw[q] = 0.0;
+        }
+        continue;
+      }
+      const int t1 = (t + 1) % nk;
+      const double P[4][3] = {{xb[0], xb[1], 0.0},
+                              {cx[t][0], cx[t][1], 0.0},
+                              {cx[t1][0], cx[t1][1], 0.0},
+                              {xb[0], xb[1], 0.0}};
+      quad_cell_points(g, P, qx, qw);
+    }
+    return;
+  }
   if (simplex) {  // corners of the collapsed square / cube
     double s[8][3];
     const int nm = dim == 2 ? 4 : 8;
@@ -143,29 +205,8 @@ __global__ void k_cell_geometry(int dim, bool simplex, int nv, int nlf, int nfv,
     for (int k = 0; k < nm; ++k)
       for (int a = 0; a < 3; ++a) cx[k][a] = s[k][a];
   }
-  const int n = g.n;
   if (dim == 2) {
-    for (int a = 0; a < n; ++a)
-      for (int b = 0; b < n; ++b) {
-        const double s = g.x[a], t = g.x[b];
-        const double N[4] = {(1 - s) * (1 - t), s * (1 - t), s * t, (1 - s) * t};
-        const double Ns[4] = {-(1 - t), 1 - t, t, -t};
-        const double Nt[4] = {-(1 - s), -s, s, 1 - s};
-        double X[2] = {0, 0}, J00 = 0, J01 = 0, J10 = 0, J11 = 0;
-        for (int k = 0; k < 4; ++k) {
-          X[0] += N[k] * cx[k][0];
-          X[1] += N[k] * cx[k][1];
-          J00 += Ns[k] * cx[k][0];
-          J01 += Nt[k] * cx[k][0];
-          J10 += Ns[k] * cx[k][1];
-          J11 += Nt[k] * cx[k][1];
-        }
-        const int q = a * n + b;
-        cqx[(c * QC + q) * 3 + 0] = X[0];
-        cqx[(c * QC + q) * 3 + 1] = X[1];
-        cqx[(c * QC + q) * 3 + 2] = 0.0;
-        cqw[c * QC + q] = g.w[a] * g.w[b] * fabs(J00 * J11 - J01 * J10);
-      }
+    quad_cell_points(g, cx, cqx + c * QC * 3, cqw + c * QC);
     return;
   }
   const int R3[8][3] = {{0, 0, 0}, {1, 0, 0}, {1, 1, 0}, {0, 1, 0},
@@ -215,7 +256,7 @@ int run_geometry(hofv_ctx* c) {
       c->d_gam);
   HOFV_CUDA(c, cudaGetLastError());
   k_cell_geometry<<<(unsigned)((c->nc + T - 1) / T), T, 0, c->stream>>>(
-      c->dim, c->simplex != 0, c->nv, c->nlf, c->nfv, c->Q, c->QC, c->nc, g, c->d_x, c->d_cnodes, c->d_xc,
+      c->dim, c->simplex, c->poly, c->nv, c->nlf, c->nfv, c->Q, c->QC, c->nc, g, c->d_x, c->d_cnodes, c->d_xc,
       c->d_vol, c->d_cqx, c->d_cqw);
   HOFV_CUDA(c, cudaGetLastError());
   HOFV_CUDA(c, cudaStreamSynchronize(c->stream));

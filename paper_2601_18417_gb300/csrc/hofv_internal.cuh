@@ -17,6 +17,7 @@ constexpr int kMaxS = 128;       // largest supported stencil (+ ghost)
 constexpr int kMaxNt = 20;       // Taylor terms of a cubic in 3-D
 constexpr int kMaxQ = 16;        // Gauss points per face (4 x 4)
 constexpr int kMaxQC = 64;       // Gauss points per cell (4^3)
+constexpr int kPolyMaxSides = 8; // face slots of a polygon cell
 
 // Device-side description of the discretisation used by the residual
 // kernels.  All pointers are device addresses owned by the context.
@@ -70,6 +71,8 @@ struct hofv_ctx {
   bool have_mesh = false, have_scheme = false, built = false, have_mat = false;
   int dim = 0, nv = 0, nlf = 0, nfv = 0;
   bool simplex = false;            // triangles / tetrahedra instead of quads / hexes
+  bool poly = false;               // 2-D polygons: nlf = nv = kPolyMaxSides slots per cell
+  std::vector<int32_t> cnv;        // polygons: [nc] corners (= sides) of each cell
   int64_t nn = 0, nc = 0, nb = 0;
   std::vector<double> x;            // [nn][3]
   std::vector<int64_t> cn;          // [nc][nv]

@@ -518,8 +518,7 @@ __global__ void __launch_bounds__(kPersistThreads)
 template <typename T, int DIM, int NLF>
 static bool cg_persist_run(hofv_ctx* c, const T* diag, const T* invd, const T* off, T* work,
                            int iters, const double* v, double* zout) {
-  static int max_blocks[2][2][2] = {{{-1, -1}, {-1, -1}}, {{-1, -1}, {-1, -1}}};
-  int& mb = max_blocks[sizeof(T) == 8][DIM == 3][NLF == 2 * DIM];
+  static int mb = -1;  // co-resident blocks of this instantiation, found once
   if (mb < 0) {
     int per_sm = 0, dev = 0, nsm = 0, coop = 0;
     cudaGetDevice(&dev);
@@ -605,7 +604,7 @@ int barrier_selftest(hofv_ctx* c, int* timed_out) {
 
 // the persistent cooperative solve when it fits on the device, else one
 // launch per iteration; NLF = faces per cell (4 / 6 for quads / hexes,
-// 3 / 4 for triangles / tetrahedra)
+// 3 / 4 for triangles / tetrahedra, 8 slots for polygons)
 template <typename T, int DIM, int NLF>
 static void aj_run(hofv_ctx* c, const T* diag, const T* invd, const T* off, T* work, int iters,
                    const double* v, double* z) {
@@ -619,6 +618,7 @@ static void aj_dispatch(hofv_ctx* c, const T* diag, const T* invd, const T* off,
   const bool simplex = c->nlf == c->dim + 1;
   if (c->dim == 2) {
     if (simplex) aj_run<T, 2, 3>(c, diag, invd, off, work, iters, v, z);
+    else if (c->poly) aj_run<T, 2, kPolyMaxSides>(c, diag, invd, off, work, iters, v, z);
     else aj_run<T, 2, 4>(c, diag, invd, off, work, iters, v, z);
   } else {
     if (simplex) aj_run<T, 3, 4>(c, diag, invd, off, work, iters, v, z);
@@ -627,7 +627,7 @@ static void aj_dispatch(hofv_ctx* c, const T* diag, const T* invd, const T* off,
 }
 
 int aj_precondition(hofv_ctx* c, int kind, int iters, const double* v, double* z) {
-  if (c->nlf != 2 * c->dim && c->nlf != c->dim + 1)
+  if (c->nlf != 2 * c->dim && c->nlf != c->dim + 1 && !(c->poly && c->nlf == kPolyMaxSides))
     return fail(c, HOFV_ENOTSUP, "cell shape without an approximate-Jacobian kernel");
   if (kind == HOFV_PC_AJ64)
     aj_dispatch<double>(c, c->d_aj_diag, c->d_aj_invd, c->d_aj_off, c->d_cg64, iters, v, z);

@@ -154,7 +154,7 @@ int build_structure(hofv_ctx* c, Nej* g) {
         row.clear();
         for (int lf = 0; lf < nlf; ++lf) {
           const int64_t f = c->cf[P * nlf + lf];
-          if (f >= nfid) continue;
+          if (f < 0 || f >= nfid) continue;
           for (int n = 0; n < S; ++n) row.push_back(stencil(f, n));
         }
         std::sort(row.begin(), row.end());

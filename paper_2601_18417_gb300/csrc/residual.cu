@@ -377,11 +377,16 @@ static void residual_impl(const DevMesh& m, const Material& mat, const double* w
     k_extend<DIM><<<(unsigned)((m.wst + 255) / 256), 256, 0, st>>>(m, w, m.wext);
     w = m.wext;
   }
-  const bool simplex = m.nlf == DIM + 1;
-  if (simplex)
+  // faces per cell: d + 1 (triangles / tetrahedra), 2 d (quads / hexes),
+  // kPolyMaxSides slots (2-D polygons)
+  if (m.nlf == DIM + 1) {
     k_ustar<DIM, DIM + 1><<<(unsigned)m.nctile, 32 * (DIM + 1), 0, st>>>(m, w, ustar);
-  else
+  } else if (m.nlf == 2 * DIM) {
     k_ustar<DIM, 2 * DIM><<<(unsigned)m.nctile, 32 * 2 * DIM, 0, st>>>(m, w, ustar);
+  } else {
+    if constexpr (DIM == 2)
+      k_ustar<2, kPolyMaxSides><<<(unsigned)m.nctile, 32 * kPolyMaxSides, 0, st>>>(m, w, ustar);
+  }
   if (m.nfy > 0) k_sym_other<DIM><<<(unsigned)((m.nfy + 127) / 128), 128, 0, st>>>(m, ustar);
   if (ev) cudaEventRecord(ev[1], st);
   if (m.nftile > 0) {
@@ -397,12 +402,14 @@ static void residual_impl(const DevMesh& m, const Material& mat, const double* w
   if (ev) cudaEventRecord(ev[2], st);
   if (m.mscale)
     k_cell_avg<DIM, true><<<(unsigned)((m.nc + 127) / 128), 128, 0, st>>>(m, w, m.wst, m.inert);
-  if (simplex)
-    k_cell<DIM, DIM + 1><<<(unsigned)((m.nc + 255) / 256), 256, 0, st>>>(m, flux, src, R0, d_eps,
-                                                                         out);
-  else
-    k_cell<DIM, 2 * DIM><<<(unsigned)((m.nc + 255) / 256), 256, 0, st>>>(m, flux, src, R0, d_eps,
-                                                                         out);
+  const unsigned cgrid = (unsigned)((m.nc + 255) / 256);
+  if (m.nlf == DIM + 1) {
+    k_cell<DIM, DIM + 1><<<cgrid, 256, 0, st>>>(m, flux, src, R0, d_eps, out);
+  } else if (m.nlf == 2 * DIM) {
+    k_cell<DIM, 2 * DIM><<<cgrid, 256, 0, st>>>(m, flux, src, R0, d_eps, out);
+  } else {
+    if constexpr (DIM == 2) k_cell<2, kPolyMaxSides><<<cgrid, 256, 0, st>>>(m, flux, src, R0, d_eps, out);
+  }
   if (ev) cudaEventRecord(ev[3], st);
 }
 
@@ -438,13 +445,13 @@ __global__ void k_source(int dim, int nlf, int Q, int64_t nc, int64_t nfi, int64
     double s = body ? body[j * nc + c] : 0.0;
     if (gflux)
       for (int lf = 0; lf < nlf; ++lf) {
-        const int64_t f = cf[c * nlf + lf];
-        if (ftag[f] == 0) s += gflux[(f - nfi) * dim + j];
+        const int64_t f = cf[c * nlf + lf];  // -1: polygon slot without a face
+        if (f >= 0 && ftag[f] == 0) s += gflux[(f - nfi) * dim + j];
       }
     if (tbq) {
       for (int lf = 0; lf < nlf; ++lf) {
         const int64_t f = cf[c * nlf + lf];
-        if (ftag[f] != 1) continue;
+        if (f < 0 || ftag[f] != 1) continue;
         const int64_t b = f - nfi - nfd;
         for (int q = 0; q < Q; ++q) {
           const double* a = aq + (f * Q + q) * 3;
@@ -493,6 +500,8 @@ void launch_flux_scale(const DevMesh& m, const double* flux, double* out, cudaSt
   const unsigned grid = (unsigned)((m.nc + 255) / 256);
   if (m.dim == 2 && m.nlf == 3)
     k_flux_scale<2, 3><<<grid, 256, 0, st>>>(m, flux, out);
+  else if (m.dim == 2 && m.nlf == kPolyMaxSides)
+    k_flux_scale<2, kPolyMaxSides><<<grid, 256, 0, st>>>(m, flux, out);
   else if (m.dim == 2)
     k_flux_scale<2, 4><<<grid, 256, 0, st>>>(m, flux, out);
   else if (m.nlf == 4)

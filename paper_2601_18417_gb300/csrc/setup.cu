@@ -451,6 +451,7 @@ __global__ void k_lsq_cells(LsqParams P) {
   const int nown = (P.NR + 31) / 32;
   for (int lf = 0; lf < P.nlf; ++lf) {
     const int64_t f = P.cf[c * P.nlf + lf];
+    if (f < 0) continue;  // polygon slot without a face: its weights stay zero
     double X[3] = {0, 0, 0}, g[kMaxNt];
     for (int a = 0; a < P.dim; ++a) X[a] = (P.xf[3 * f + a] - xt[a]) / h;
     taylor_basis(P.dim, P.p, X, g);

@@ -21,6 +21,7 @@ EINVAL, ENOMEM, ECUDA, EILLCOND, ENAN, ENOTSUP, ESTATE = -1, -2, -3, -4, -5, -6,
 LAW_LINEAR, LAW_NEOHOOKEAN = 0, 1
 PC_NONE, PC_AJ64, PC_AJ32, PC_GNN, PC_AJMG, PC_NEJ = -1, 0, 1, 2, 3, 4
 CELL_TENSOR, CELL_SIMPLEX = 0, 1
+POLY_SLOTS = 8  # face slots of a polygon cell
 PTS_CELL_CENTROID, PTS_DISP_QP, PTS_DISP_CENTRE, PTS_TRAC_QP, PTS_CELL_QP = 0, 1, 2, 3, 4
 PTS_FACE_CENTRE, PTS_FACE_QP, PTS_FACE_AREA, PTS_CELL_VOLUME = 5, 6, 7, 8
 
@@ -82,6 +83,7 @@ SIGNATURES = {
     "hofv_version": (C.c_char_p, []),
     "hofv_set_mesh": (_I, [_P, _I, _I64, _P, _I64, _P, _I64, _P, _P]),
     "hofv_set_mesh_cells": (_I, [_P, _I, _I, _I64, _P, _I64, _P, _I64, _P, _P]),
+    "hofv_set_mesh_polygons": (_I, [_P, _I64, _P, _I64, _P, _P, _I64, _P, _P]),
     "hofv_set_scheme": (_I, [_P, _I, _I, _I, _D, _D]),
     "hofv_build_stencils": (_I, [_P]),
     "hofv_get_layout": (_I, [_P, C.POINTER(Layout)]),
@@ -200,6 +202,12 @@ class Context:
         bn = np.ascontiguousarray(mesh.bface_nodes, np.int64)
         tag = np.ascontiguousarray(bface_tag, np.int32)
         self.dim = mesh.dim
+        if getattr(mesh, "cell_ptr", None) is not None:  # 2-D polygons
+            ptr = np.ascontiguousarray(mesh.cell_ptr, np.int64)
+            self.faces_per_cell = POLY_SLOTS
+            return self._check(self._L.hofv_set_mesh_polygons(
+                self.h, xyz.shape[0], _ptr(xyz), ptr.shape[0] - 1, _ptr(ptr), _ptr(cn),
+                bn.shape[0], _ptr(bn), _ptr(tag)))
         kind = CELL_SIMPLEX if getattr(mesh, "simplex", False) else CELL_TENSOR
         self.faces_per_cell = mesh.dim + 1 if kind == CELL_SIMPLEX else 2 * mesh.dim
         return self._check(self._L.hofv_set_mesh_cells(self.h, mesh.dim, kind, xyz.shape[0],

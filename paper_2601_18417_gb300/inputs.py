@@ -239,49 +239,41 @@ def polygon_mesh(n: int, length: float = 1.0, jitter: float = 0.0, seed: int = 0
     nn, nt = X.shape[0], T.shape[0]
     cent = X[T].mean(axis=1)
     bn = tri.bface_nodes                          # [nb, 2], outward (counter-clockwise)
+    nbe = bn.shape[0]
     mid = 0.5 * (X[bn[:, 0]] + X[bn[:, 1]])
     bnodes = np.unique(bn.ravel())
     # dual node ids: triangle centroids, boundary-edge midpoints, boundary nodes
-    mid0, bn0 = nt, nt + bn.shape[0]
+    mid0, bn0 = nt, nt + nbe
     bnode_id = np.full(nn, -1, np.int64)
     bnode_id[bnodes] = bn0 + np.arange(bnodes.size)
     xyz = np.concatenate([cent, mid, X[bnodes]])
-    around = [[] for _ in range(nn)]
-    for t in range(nt):
-        for v in T[t]:
-            around[v].append(t)
-    bedges = [[] for _ in range(nn)]
-    for e, (a, b) in enumerate(bn):
-        bedges[a].append(e)
-        bedges[b].append(e)
-    ptr, flat = [0], []
-    for v in range(nn):
-        ids = [t for t in around[v]] + [mid0 + e for e in bedges[v]]
-        if bnode_id[v] >= 0:
-            ids.append(int(bnode_id[v]))
-        P = xyz[ids]
-        c = P.mean(axis=0)
-        ang = np.arctan2(P[:, 1] - c[1], P[:, 0] - c[0])
-        ids = [ids[k] for k in np.argsort(ang, kind="stable")]
-        flat.extend(ids)
-        ptr.append(len(flat))
-    ptr = np.asarray(ptr, np.int64)
-    flat = np.asarray(flat, np.int64)
-    for v in range(nn):
-        poly = xyz[flat[ptr[v]:ptr[v + 1]]]
-        c = poly.mean(axis=0)
-        e0, e1 = poly - c, np.roll(poly, -1, axis=0) - c
-        if np.any(e0[:, 0] * e1[:, 1] - e0[:, 1] * e1[:, 0] <= 0):
-            raise ValueError("a dual cell is not star-shaped about its vertex average")
+    # (cell = triangle-mesh node, corner = dual node) pairs
+    node = np.concatenate([T.ravel(), bn[:, 0], bn[:, 1], bnodes])
+    corner = np.concatenate([np.repeat(np.arange(nt), 3), mid0 + np.arange(nbe),
+                             mid0 + np.arange(nbe), bnode_id[bnodes]])
+    cnt = np.bincount(node, minlength=nn)
+    c = np.stack([np.bincount(node, weights=xyz[corner, a], minlength=nn) for a in range(2)],
+                 axis=1) / cnt[:, None]
+    d = xyz[corner] - c[node]
+    order = np.lexsort((np.arctan2(d[:, 1], d[:, 0]), node))
+    flat = corner[order].astype(np.int64)
+    ptr = np.concatenate([[0], np.cumsum(cnt)]).astype(np.int64)
+    # star-shaped about the corners' average, counter-clockwise
+    nxt = np.arange(flat.size) + 1
+    nxt[ptr[1:] - 1] = ptr[:-1]
+    own = np.repeat(np.arange(nn), cnt)
+    e0 = xyz[flat] - c[own]
+    e1 = xyz[flat[nxt]] - c[own]
+    if np.any(e0[:, 0] * e1[:, 1] - e0[:, 1] * e1[:, 0] <= 0):
+        raise ValueError("a dual cell is not star-shaped about its vertex average")
     # boundary faces: the halves of each boundary edge, (a, mid) for cell a and
     # (mid, b) for cell b, on the edge's domain side
-    faces, sides = [], []
-    for e, (a, b) in enumerate(bn):
-        faces.append((bnode_id[a], mid0 + e))
-        faces.append((mid0 + e, bnode_id[b]))
-        sides += [tri.bface_side[e]] * 2
+    e = np.arange(nbe)
+    faces = np.stack([np.stack([bnode_id[bn[:, 0]], mid0 + e], axis=1),
+                      np.stack([mid0 + e, bnode_id[bn[:, 1]]], axis=1)], axis=1).reshape(-1, 2)
+    sides = np.repeat(tri.bface_side, 2)
     return Mesh(dim=2, n=n, xyz=np.ascontiguousarray(xyz), cell_nodes=flat,
-                bface_nodes=np.asarray(faces, np.int64), bface_side=np.asarray(sides, np.int32),
+                bface_nodes=faces.astype(np.int64), bface_side=sides.astype(np.int32),
                 length=length, cell_ptr=ptr)
 
 
@@ -580,10 +572,13 @@ class Workload:
     alpha: float = 0.1
     k_weight: float = 6.0
     length: float = 1.0      # edge of the square / cube
-    cells: str = "tensor"    # "tensor" (quads / hexes) or "simplex" (triangles / tetrahedra)
+    cells: str = "tensor"    # "tensor" (quads / hexes), "simplex" (triangles / tetrahedra)
+    #                          or "polygon" (2-D dual polygons)
 
     @property
     def n_cells(self) -> int:
+        if self.cells == "polygon":
+            return (self.n + 1) ** 2
         per = (2 if self.dim == 2 else 6) if self.cells == "simplex" else 1
         return per * self.n ** self.dim
 
@@ -631,6 +626,9 @@ WORKLOADS = {
                                  "mms-mixed2d", 1242, cells="simplex"),
     "tet32j-p2-trig": Workload("tet32j-p2-trig", 3, 32, 2, 55, 2, 0.1, 0, _MU_1G, _LAM_1G,
                                "mms-trig3d", 1243, cells="simplex"),
+    # the dual of the 2 x 512^2 triangle mesh: 513^2 polygons of 4-8 sides, cubic LSQ
+    "poly512j-p3-mixed": Workload("poly512j-p3-mixed", 2, 512, 3, 10, 3, 0.15, 0, _MU_S, _LAM_S,
+                                  "mms-mixed2d", 1244, cells="polygon"),
     # 3-D neo-Hookean, 128^3 jittered hexes, cubic LSQ
     "hex128j-p3-nh": Workload("hex128j-p3-nh", 3, 128, 3, 65, 3, 0.20, 1, 1e6, 4e6, "block",
                               1238, load_steps=10),
