@@ -48,6 +48,8 @@ def lib():
         L.orc_create_cells.argtypes = [C.c_int, C.c_int, I64, P, I64, P, I64, P, P]
         L.orc_create_poly.restype = P
         L.orc_create_poly.argtypes = [I64, P, I64, P, P, I64, P, P]
+        L.orc_create_faces.restype = P
+        L.orc_create_faces.argtypes = [I64, P, I64, I64, P, P, P, P, P]
         L.orc_free.argtypes = [P]
         L.orc_counts.argtypes = [P, P]
         L.orc_set_scheme.argtypes = [P, C.c_int, C.c_int, C.c_int, D, D]
@@ -57,6 +59,7 @@ def lib():
         L.orc_get_faces.argtypes = [P, P, P, P, P]
         L.orc_get_cell_faces.argtypes = [P, P]
         L.orc_href_exp.argtypes = [P]
+        L.orc_nlf.argtypes = [P]
         L.orc_prepare.argtypes = [P, I64, P]
         L.orc_face_slot.argtypes = [P, I64]
         L.orc_cell_slot.argtypes = [P, I64]
@@ -105,6 +108,12 @@ class OracleMesh:
         L = lib()
         self.dim = mesh.dim
         self.mesh = mesh
+        self.simplex = self.polygon = False
+        self.polyhedral = hasattr(mesh, "face_ptr")
+        if self.polyhedral:
+            self._init_faces(L, mesh, tags_per_side)
+            self._finish(L, p, n_plus, q1, k_weight, alpha)
+            return
         xyz = np.ascontiguousarray(mesh.xyz, dtype=np.float64)
         cn = np.ascontiguousarray(mesh.cell_nodes, dtype=np.int64)
         bn = np.ascontiguousarray(mesh.bface_nodes, dtype=np.int64)
@@ -123,6 +132,26 @@ class OracleMesh:
                                         cn.shape[0], _p(cn), bn.shape[0], _p(bn), _p(tags))
         if not self.h:
             raise ValueError("oracle rejected the mesh")
+        self._finish(L, p, n_plus, q1, k_weight, alpha)
+
+    def _init_faces(self, L, mesh, tags_per_side):
+        """A face-based polyhedral mesh (inputs.FaceMesh)."""
+        xyz = np.ascontiguousarray(mesh.xyz, dtype=np.float64)
+        ptr = np.ascontiguousarray(mesh.face_ptr, dtype=np.int64)
+        fn = np.ascontiguousarray(mesh.face_nodes, dtype=np.int64)
+        own = np.ascontiguousarray(mesh.owner, dtype=np.int64)
+        nei = np.ascontiguousarray(mesh.neighbour, dtype=np.int64)
+        side = np.asarray(mesh.face_side)
+        tags = np.ascontiguousarray(np.where(side >= 0, np.asarray(tags_per_side, np.int32)[
+            np.maximum(side, 0)], -1).astype(np.int32))
+        self.bface_tag = tags  # per input face, -1 inside
+        self._keep = (xyz, ptr, fn, own, nei, tags)
+        self.h = L.orc_create_faces(xyz.shape[0], _p(xyz), mesh.n_cells, ptr.shape[0] - 1,
+                                    _p(ptr), _p(fn), _p(own), _p(nei), _p(tags))
+        if not self.h:
+            raise ValueError("oracle rejected the mesh")
+
+    def _finish(self, L, p, n_plus, q1, k_weight, alpha):
         rc = L.orc_set_scheme(self.h, p, n_plus, q1, k_weight, alpha)
         if rc != 0:
             raise ValueError(f"oracle rejected the scheme ({rc})")
@@ -133,8 +162,12 @@ class OracleMesh:
         (self.nf, self.nfi, self.nfd, self.nft, self.nc, self.Q, self.S, self.QC, self.nfy) = (
             int(v) for v in cnt)
         self.p, self.n_plus, self.q1 = p, n_plus, q1
-        # faces per cell; polygons keep 8 slots, -1 past a cell's last side
-        self.nlf = 8 if self.polygon else self.dim + 1 if self.simplex else 2 * self.dim
+        # faces per cell; polygons keep 8 slots, -1 past a cell's last side,
+        # polyhedra as many slots as the cell with most faces
+        if self.polyhedral:
+            self.nlf = int(L.orc_nlf(self.h))
+        else:
+            self.nlf = 8 if self.polygon else self.dim + 1 if self.simplex else 2 * self.dim
         self._subset = None
 
     def __del__(self):

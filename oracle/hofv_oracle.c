@@ -33,7 +33,11 @@
  *     a triangular face is the patch with a repeated corner and a triangle
  *     or tetrahedron cell the collapsed square / cube (Duffy's map), so the
  *     same tensor rules serve unstructured simplex meshes; a polygon cell is
- *     the fan of triangles from its corners' average, each so collapsed;
+ *     the fan of triangles from its corners' average, each so collapsed; a
+ *     polyhedron's polygonal face is the fan of triangles from its corners'
+ *     average and its cell rule the fan of tetrahedra from the average of
+ *     its face averages (the paper's fan triangulation and tetrahedral
+ *     decomposition, with collapsed tensor rules instead of Dunavant's);
  *   - stencil ties are broken by a quantised squared distance (quantum
  *     2^-24 of the squared reference cell size) then by cell id;
  *   - the reconstruction is solved from the normal equations, eq. (maQw), in
@@ -54,7 +58,8 @@ typedef long double ld;
 /* mesh object                                                         */
 /* ------------------------------------------------------------------ */
 typedef struct {
-  int dim, simplex, poly, nv, nlf, nfv;
+  int dim, simplex, poly, polyh, nv, nlf, nfv;
+  int maxtets;     /* polyhedra: most fan tetrahedra of one cell */
   int64_t nn, nc, nb;
   double *x;       /* [nn][3] */
   int64_t *cn;     /* [nc][nv]; polygons: corners, -1 past the last */
@@ -63,7 +68,8 @@ typedef struct {
   int64_t nf, nfi, nfd, nfy, nft;
   int64_t *fown, *fnei;
   int *flf, *ftag; /* owner local face; -1 internal, 0 disp, 1 traction, 2 symmetry */
-  int64_t *fnodes; /* [nf][nfv] in the owner's outward order */
+  int64_t *fnodes; /* [nf][nfv] in the owner's outward order (polyhedra: -1 past the last) */
+  int *fcnt;       /* polyhedra: [nf] corners of each face */
   int64_t *cf;     /* [nc][nlf] face id of each local face */
   /* scheme */
   int have_scheme, p, nplus, q1, S, Nt, Q, QC;
@@ -370,7 +376,7 @@ void orc_free_subset(orc_mesh* m) {
 
 void orc_free(orc_mesh* m) {
   if (!m) return;
-  free(m->x); free(m->cn); free(m->cnv); free(m->fown); free(m->fnei); free(m->flf); free(m->ftag);
+  free(m->x); free(m->cn); free(m->cnv); free(m->fcnt); free(m->fown); free(m->fnei); free(m->flf); free(m->ftag);
   free(m->fnodes); free(m->cf); free(m->xc); free(m->vol); free(m->xq); free(m->aq);
   free(m->xf); free(m->nrm); free(m->gam); free(m->cqx); free(m->cqw);
   orc_free_subset(m);
@@ -389,8 +395,9 @@ int orc_set_scheme(orc_mesh* m, int p, int nplus, int q1, double kw, double alph
   for (int i = 1; i <= m->dim; ++i) nt = nt * (p + i) / i;   /* C(d+p, d) */
   m->Nt = nt;
   m->S = nt + nplus;
-  m->Q = m->dim == 2 ? q1 : q1 * q1;
-  m->QC = m->poly ? m->nlf * q1 * q1 : m->dim == 2 ? q1 * q1 : q1 * q1 * q1;
+  m->Q = m->polyh ? m->nfv * q1 * q1 : m->dim == 2 ? q1 : q1 * q1;
+  m->QC = m->polyh ? m->maxtets * q1 * q1 * q1
+        : m->poly ? m->nlf * q1 * q1 : m->dim == 2 ? q1 * q1 : q1 * q1 * q1;
   if (m->S > m->nc) return -2;
   orc_gauss_legendre(q1, m->gl_x, m->gl_w);
   m->have_scheme = 1;
@@ -471,6 +478,61 @@ static void quad_rule(const orc_mesh* m, const double P[4][2], double* cqx, doub
     }
 }
 
+/* Gauss points and weights of the trilinear map of the hex with corners P
+   (repeated corners collapse it to a tetrahedron) */
+static void hex_rule(const orc_mesh* m, const double P[8][3], double* cqx, double* cqw) {
+  static const double R3[8][3] = {{0, 0, 0}, {1, 0, 0}, {1, 1, 0}, {0, 1, 0},
+                                  {0, 0, 1}, {1, 0, 1}, {1, 1, 1}, {0, 1, 1}};
+  int n = m->q1;
+  for (int a = 0; a < n; ++a)
+    for (int b = 0; b < n; ++b)
+      for (int g = 0; g < n; ++g) {
+        double s[3] = {m->gl_x[a], m->gl_x[b], m->gl_x[g]};
+        double X3[3] = {0, 0, 0}, J[3][3] = {{0}};
+        for (int k = 0; k < 8; ++k) {
+          double fct[3], dr[3];
+          for (int e = 0; e < 3; ++e) {
+            fct[e] = R3[k][e] ? s[e] : 1 - s[e];
+            dr[e] = R3[k][e] ? 1 : -1;
+          }
+          double N = fct[0] * fct[1] * fct[2];
+          double dN[3] = {dr[0] * fct[1] * fct[2], fct[0] * dr[1] * fct[2],
+                          fct[0] * fct[1] * dr[2]};
+          for (int e = 0; e < 3; ++e) {
+            double xv = P[k][e];
+            X3[e] += N * xv;
+            for (int r = 0; r < 3; ++r) J[e][r] += dN[r] * xv;
+          }
+        }
+        double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                     J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                     J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+        int q = (a * n + b) * n + g;
+        for (int e = 0; e < 3; ++e) cqx[q * 3 + e] = X3[e];
+        cqw[q] = m->gl_w[a] * m->gl_w[b] * m->gl_w[g] * fabs(det);
+      }
+}
+
+/* reference length for the stencil tie key: a power of two near the mean
+   cell size, from the node bounding box */
+static void set_href(orc_mesh* m) {
+  int d = m->dim;
+  double vbox = 1.0;
+  for (int a = 0; a < d; ++a) {
+    double lo = m->x[a], hi = m->x[a];
+    for (int64_t i = 1; i < m->nn; ++i) {
+      double v = m->x[3 * i + a];
+      if (v < lo) lo = v;
+      if (v > hi) hi = v;
+    }
+    vbox *= (hi - lo);
+  }
+  int e = ilogb(vbox / (double)m->nc);
+  m->href_exp = e >= 0 ? e / d : -((-e + d - 1) / d); /* floor(e / d) */
+}
+
+static int geometry_polyhedra(orc_mesh* m);
+
 int orc_geometry(orc_mesh* m) {
   if (!m->have_scheme) return -1;
   int d = m->dim, Q = m->Q, nfv = m->nfv;
@@ -486,6 +548,7 @@ int orc_geometry(orc_mesh* m) {
   m->cqx = (double*)calloc(m->nc * m->QC * 3, sizeof(double));
   m->cqw = (double*)calloc(m->nc * m->QC, sizeof(double));
   double corner[12], xq[16 * 3], aq[16 * 3];
+  if (m->polyh) return geometry_polyhedra(m);
   /* faces */
   for (int64_t f = 0; f < m->nf; ++f) {
     face_corners(m, m->fnodes + f * nfv, corner);
@@ -561,54 +624,218 @@ int orc_geometry(orc_mesh* m) {
       quad_rule(m, P4, m->cqx + c * m->QC * 3, m->cqw + c * m->QC);
     } else {
       cell_map_nodes(m, c, cn);
-      static const double R3[8][3] = {{0, 0, 0}, {1, 0, 0}, {1, 1, 0}, {0, 1, 0},
-                                      {0, 0, 1}, {1, 0, 1}, {1, 1, 1}, {0, 1, 1}};
-      for (int a = 0; a < n; ++a)
-        for (int b = 0; b < n; ++b)
-          for (int g = 0; g < n; ++g) {
-            double s[3] = {m->gl_x[a], m->gl_x[b], m->gl_x[g]};
-            double X3[3] = {0, 0, 0}, J[3][3] = {{0}};
-            for (int k = 0; k < 8; ++k) {
-              double fct[3], dr[3];
-              for (int e = 0; e < 3; ++e) {
-                fct[e] = R3[k][e] ? s[e] : 1 - s[e];
-                dr[e] = R3[k][e] ? 1 : -1;
-              }
-              double N = fct[0] * fct[1] * fct[2];
-              double dN[3] = {dr[0] * fct[1] * fct[2], fct[0] * dr[1] * fct[2],
-                              fct[0] * fct[1] * dr[2]};
-              for (int e = 0; e < 3; ++e) {
-                double xv = m->x[3 * cn[k] + e];
-                X3[e] += N * xv;
-                for (int r = 0; r < 3; ++r) J[e][r] += dN[r] * xv;
-              }
-            }
-            double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
-                         J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
-                         J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
-            int q = (a * n + b) * n + g;
-            for (int e = 0; e < 3; ++e) m->cqx[(c * m->QC + q) * 3 + e] = X3[e];
-            m->cqw[c * m->QC + q] = m->gl_w[a] * m->gl_w[b] * m->gl_w[g] * fabs(det);
-          }
+      double P8[8][3];
+      for (int k = 0; k < 8; ++k)
+        for (int e = 0; e < 3; ++e) P8[k][e] = m->x[3 * cn[k] + e];
+      hex_rule(m, P8, m->cqx + c * m->QC * 3, m->cqw + c * m->QC);
     }
   }
-  /* reference length for the stencil tie key: a power of two near the mean
-     cell size, from the node bounding box */
-  double vbox = 1.0;
-  for (int a = 0; a < d; ++a) {
-    double lo = m->x[a], hi = m->x[a];
-    for (int64_t i = 1; i < m->nn; ++i) {
-      double v = m->x[3 * i + a];
-      if (v < lo) lo = v;
-      if (v > hi) hi = v;
-    }
-    vbox *= (hi - lo);
-  }
-  int e = ilogb(vbox / (double)m->nc);
-  int q = e >= 0 ? e / d : -((-e + d - 1) / d); /* floor(e / d) */
-  m->href_exp = q;
+  set_href(m);
   m->have_geom = 1;
   return 0;
+}
+
+/* Polyhedra (faces given as polygons): each face is the fan of triangles
+   from its corners' average cbar_f to its sides, each triangle the bilinear
+   patch (cbar_f, v_t, v_t+1, cbar_f) with q1 x q1 points (Q = nfv q1^2, zero
+   area past a face's last side).  Volume and centroid by the divergence
+   theorem over those points, each face counted outward; the cell rule is
+   the fan of tetrahedra (xbar_c, cbar_f, v_t, v_t+1) from the average xbar_c
+   of the cell's face averages, each the collapsed cube (q1^3 points). */
+static int geometry_polyhedra(orc_mesh* m) {
+  int Q = m->Q, n2 = m->q1 * m->q1, n3 = n2 * m->q1;
+  double* cbar = (double*)calloc(m->nf * 3, sizeof(double));
+  for (int64_t f = 0; f < m->nf; ++f) {
+    int k = m->fcnt[f];
+    const int64_t* fn = m->fnodes + f * m->nfv;
+    double* cb = cbar + 3 * f;
+    for (int t = 0; t < k; ++t)
+      for (int e = 0; e < 3; ++e) cb[e] += m->x[3 * fn[t] + e];
+    for (int e = 0; e < 3; ++e) cb[e] /= k;
+    for (int t = 0; t < m->nfv; ++t) {
+      double* xq = m->xq + (f * Q + t * n2) * 3;
+      double* aq = m->aq + (f * Q + t * n2) * 3;
+      if (t >= k) {
+        for (int q = 0; q < n2; ++q)
+          for (int e = 0; e < 3; ++e) { xq[3 * q + e] = cb[e]; aq[3 * q + e] = 0.0; }
+        continue;
+      }
+      double corner[12];
+      for (int e = 0; e < 3; ++e) {
+        corner[e] = cb[e];
+        corner[3 + e] = m->x[3 * fn[t] + e];
+        corner[6 + e] = m->x[3 * fn[(t + 1) % k] + e];
+        corner[9 + e] = cb[e];
+      }
+      face_quadrature(m, corner, xq, aq);
+    }
+    double G = 0, A[3] = {0, 0, 0}, X[3] = {0, 0, 0};
+    for (int q = 0; q < Q; ++q) {
+      const double* a = m->aq + (f * Q + q) * 3;
+      double mag = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+      G += mag;
+      for (int e = 0; e < 3; ++e) {
+        A[e] += a[e];
+        X[e] += mag * m->xq[(f * Q + q) * 3 + e];
+      }
+    }
+    double An = sqrt(A[0] * A[0] + A[1] * A[1] + A[2] * A[2]);
+    m->gam[f] = G;
+    for (int e = 0; e < 3; ++e) {
+      m->xf[3 * f + e] = X[e] / G;
+      m->nrm[3 * f + e] = A[e] / An;
+    }
+  }
+  for (int64_t c = 0; c < m->nc; ++c) {
+    double V = 0, M2[3] = {0, 0, 0}, xb[3] = {0, 0, 0};
+    int nfc = 0;
+    for (int lf = 0; lf < m->nlf; ++lf) {
+      int64_t f = m->cf[c * m->nlf + lf];
+      if (f < 0) continue;
+      double sg = m->fown[f] == c ? 1.0 : -1.0;
+      for (int q = 0; q < Q; ++q)
+        for (int a = 0; a < 3; ++a) {
+          const double xv = m->xq[(f * Q + q) * 3 + a], av = sg * m->aq[(f * Q + q) * 3 + a];
+          V += xv * av;
+          M2[a] += xv * xv * av;
+        }
+      for (int e = 0; e < 3; ++e) xb[e] += cbar[3 * f + e];
+      ++nfc;
+    }
+    V /= 3;
+    m->vol[c] = V;
+    for (int a = 0; a < 3; ++a) m->xc[3 * c + a] = M2[a] / (2.0 * V);
+    for (int e = 0; e < 3; ++e) xb[e] /= nfc;
+    int slot = 0;
+    for (int lf = 0; lf < m->nlf; ++lf) {
+      int64_t f = m->cf[c * m->nlf + lf];
+      if (f < 0) continue;
+      int k = m->fcnt[f];
+      const int64_t* fn = m->fnodes + f * m->nfv;
+      for (int t = 0; t < k; ++t, ++slot) {
+        double P8[8][3];
+        for (int e = 0; e < 3; ++e) {
+          P8[0][e] = P8[3][e] = P8[4][e] = P8[7][e] = xb[e];
+          P8[1][e] = P8[5][e] = cbar[3 * f + e];
+          P8[2][e] = m->x[3 * fn[t] + e];
+          P8[6][e] = m->x[3 * fn[(t + 1) % k] + e];
+        }
+        hex_rule(m, P8, m->cqx + (c * m->QC + slot * n3) * 3, m->cqw + c * m->QC + slot * n3);
+      }
+    }
+    for (; slot < m->maxtets; ++slot)
+      for (int q = 0; q < n3; ++q) {
+        for (int e = 0; e < 3; ++e) m->cqx[(c * m->QC + slot * n3 + q) * 3 + e] = xb[e];
+        m->cqw[c * m->QC + slot * n3 + q] = 0.0;
+      }
+  }
+  free(cbar);
+  set_href(m);
+  m->have_geom = 1;
+  return 0;
+}
+
+/* 3-D polyhedra from a face list (the polyMesh layout): face i has corners
+   face_nodes[face_ptr[i] .. face_ptr[i+1]) (3..8 of them), its normal by the
+   right-hand rule pointing out of owner[i]; neighbour[i] = -1 and
+   face_tag[i] in {0, 1, 2} on the boundary.  A cell's local faces are its
+   faces in input order; internal faces are renumbered by (owner, local face)
+   with owner < neighbour (a face is flipped where needed), boundary faces
+   follow by tag (displacement, symmetry, traction), each in input order. */
+orc_mesh* orc_create_faces(int64_t nn, const double* xyz, int64_t nc, int64_t nfin,
+                           const int64_t* face_ptr, const int64_t* face_nodes,
+                           const int64_t* owner, const int64_t* neighbour, const int* face_tag) {
+  int maxfv = 0;
+  for (int64_t i = 0; i < nfin; ++i) {
+    int64_t k = face_ptr[i + 1] - face_ptr[i];
+    if (k < 3 || k > POLY_MAX_SIDES) return NULL;
+    if (owner[i] < 0 || owner[i] >= nc || neighbour[i] >= nc || neighbour[i] == owner[i]) return NULL;
+    if (neighbour[i] < 0 && (face_tag[i] < 0 || face_tag[i] > 2)) return NULL;
+    if (k > maxfv) maxfv = (int)k;
+  }
+  int* nfc = (int*)calloc(nc, sizeof(int));
+  for (int64_t i = 0; i < nfin; ++i) {
+    nfc[owner[i]]++;
+    if (neighbour[i] >= 0) nfc[neighbour[i]]++;
+  }
+  int maxf = 0;
+  for (int64_t c = 0; c < nc; ++c) {
+    if (nfc[c] < 4) { free(nfc); return NULL; }
+    if (nfc[c] > maxf) maxf = nfc[c];
+  }
+  orc_mesh* m = (orc_mesh*)calloc(1, sizeof(orc_mesh));
+  m->dim = 3;
+  m->polyh = 1;
+  m->nlf = maxf;
+  m->nfv = maxfv;
+  m->nv = 0;
+  m->nn = nn; m->nc = nc;
+  m->x = (double*)calloc((size_t)nn * 3, sizeof(double));
+  for (int64_t i = 0; i < nn * 3; ++i) m->x[i] = xyz[i];
+  /* orientation: owner the lower id */
+  int64_t* own = (int64_t*)malloc(sizeof(int64_t) * nfin);
+  int64_t* nei = (int64_t*)malloc(sizeof(int64_t) * nfin);
+  int* flip = (int*)calloc(nfin, sizeof(int));
+  for (int64_t i = 0; i < nfin; ++i) {
+    own[i] = owner[i]; nei[i] = neighbour[i];
+    if (nei[i] >= 0 && nei[i] < own[i]) { own[i] = neighbour[i]; nei[i] = owner[i]; flip[i] = 1; }
+  }
+  /* local faces: each cell's faces in input order */
+  int* fill = (int*)calloc(nc, sizeof(int));
+  int* lf_own = (int*)malloc(sizeof(int) * nfin);
+  int* lf_nei = (int*)malloc(sizeof(int) * nfin);
+  for (int64_t i = 0; i < nfin; ++i) {
+    lf_own[i] = fill[own[i]]++;
+    lf_nei[i] = nei[i] >= 0 ? fill[nei[i]]++ : -1;
+  }
+  /* canonical order: internal by (owner, local face), then boundary by tag */
+  int64_t nfi = 0, nfd = 0, nfy = 0, nft = 0;
+  for (int64_t i = 0; i < nfin; ++i) {
+    if (nei[i] >= 0) ++nfi;
+    else if (face_tag[i] == 0) ++nfd;
+    else if (face_tag[i] == 2) ++nfy;
+    else ++nft;
+  }
+  m->nfi = nfi; m->nfd = nfd; m->nfy = nfy; m->nft = nft; m->nb = nfd + nfy + nft;
+  m->nf = nfin;
+  int64_t* order = (int64_t*)malloc(sizeof(int64_t) * nfin);
+  int64_t f = 0;
+  for (int64_t c = 0; c < nc; ++c)           /* internal, by owner then local face */
+    for (int64_t i = 0; i < nfin; ++i)
+      if (nei[i] >= 0 && own[i] == c) order[f++] = i;
+  static const int ORDER[3] = {0, 2, 1};
+  for (int o = 0; o < 3; ++o)
+    for (int64_t i = 0; i < nfin; ++i)
+      if (nei[i] < 0 && face_tag[i] == ORDER[o]) order[f++] = i;
+  m->fown = (int64_t*)malloc(sizeof(int64_t) * m->nf);
+  m->fnei = (int64_t*)malloc(sizeof(int64_t) * m->nf);
+  m->flf = (int*)malloc(sizeof(int) * m->nf);
+  m->ftag = (int*)malloc(sizeof(int) * m->nf);
+  m->fcnt = (int*)malloc(sizeof(int) * m->nf);
+  m->fnodes = (int64_t*)malloc(sizeof(int64_t) * m->nf * m->nfv);
+  m->cf = (int64_t*)malloc(sizeof(int64_t) * nc * m->nlf);
+  for (int64_t i = 0; i < nc * m->nlf; ++i) m->cf[i] = -1;
+  for (f = 0; f < m->nf; ++f) {
+    int64_t i = order[f];
+    int k = (int)(face_ptr[i + 1] - face_ptr[i]);
+    m->fown[f] = own[i]; m->fnei[f] = nei[i]; m->flf[f] = lf_own[i];
+    m->ftag[f] = nei[i] >= 0 ? -1 : face_tag[i];
+    m->fcnt[f] = k;
+    for (int t = 0; t < m->nfv; ++t)
+      m->fnodes[f * m->nfv + t] =
+          t < k ? face_nodes[face_ptr[i] + (flip[i] ? k - 1 - t : t)] : -1;
+    m->cf[own[i] * m->nlf + lf_own[i]] = f;
+    if (nei[i] >= 0) m->cf[nei[i] * m->nlf + lf_nei[i]] = f;
+  }
+  m->maxtets = 0;
+  for (int64_t c = 0; c < nc; ++c) {
+    int t = 0;
+    for (int lf = 0; lf < m->nlf; ++lf)
+      if (m->cf[c * m->nlf + lf] >= 0) t += m->fcnt[m->cf[c * m->nlf + lf]];
+    if (t > m->maxtets) m->maxtets = t;
+  }
+  free(nfc); free(own); free(nei); free(flip); free(fill); free(lf_own); free(lf_nei); free(order);
+  return m;
 }
 
 /* accessors ---------------------------------------------------------- */
@@ -636,6 +863,7 @@ void orc_get_cell_faces(const orc_mesh* m, int64_t* cf) {
   memcpy(cf, m->cf, sizeof(int64_t) * m->nc * m->nlf);
 }
 int orc_href_exp(const orc_mesh* m) { return m->href_exp; }
+int orc_nlf(const orc_mesh* m) { return m->nlf; }
 
 /* ------------------------------------------------------------------ */
 /* stencils (Sec. 3.5.2): the |S| cell centroids nearest to the         */

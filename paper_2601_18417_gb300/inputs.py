@@ -1,7 +1,9 @@
 """Seeded synthetic inputs: meshes, manufactured fields and random vectors.
 
 This module holds no arithmetic of the finite-volume method itself.  It builds
-structured quad/hex meshes (optionally with seeded interior-node jitter),
+structured quad/hex meshes (optionally with seeded interior-node jitter), the
+triangle / tetrahedron meshes cut from them, their polygonal duals and those
+duals extruded into polyhedra,
 evaluates closed-form displacement fields together with their exact
 derivatives and the matching body force of linear elasticity, and draws
 seeded random vectors.  Both the CUDA path and the oracle consume these inputs;
@@ -277,18 +279,123 @@ def polygon_mesh(n: int, length: float = 1.0, jitter: float = 0.0, seed: int = 0
                 length=length, cell_ptr=ptr)
 
 
+@dataclasses.dataclass
+class FaceMesh:
+    """Face-based description of a 3-D polyhedral mesh (the layout of a
+    polyMesh): every face once, as a polygon whose normal by the right-hand
+    rule points out of its owner.
+
+    xyz         [n_nodes, 3]
+    face_ptr    [n_faces + 1] offsets into face_nodes (3 to 8 corners a face)
+    face_nodes  flat corner lists
+    owner       [n_faces] owning cell; neighbour [n_faces], -1 on the boundary
+    face_side   [n_faces] domain side 0..5 of a boundary face, -1 inside
+    cell_grid   [n_cells, 3] integer position of each cell in its generator's
+                grid (used to colour cells, not by the method)
+    """
+
+    dim: int
+    n: int
+    xyz: np.ndarray
+    face_ptr: np.ndarray
+    face_nodes: np.ndarray
+    owner: np.ndarray
+    neighbour: np.ndarray
+    face_side: np.ndarray
+    n_cells: int
+    cell_grid: np.ndarray
+    length: float = 1.0
+
+    @property
+    def n_nodes(self) -> int:
+        return int(self.xyz.shape[0])
+
+
+def prism_mesh(n: int, nz: int | None = None, length: float = 1.0, jitter: float = 0.0,
+               seed: int = 0) -> FaceMesh:
+    """Polyhedra: the dual polygons of polygon_mesh(n, ...) extruded through
+    nz layers of the cube [0, length]^3.  A cell has its polygon (4 to 8
+    corners) as bottom and top face and one quadrilateral per side; interior
+    node levels move by U(-jitter, jitter) of the layer height, so top,
+    bottom and side faces are not planar.  Faces are listed bottom to top:
+    the horizontal faces of each level, then the side faces of each layer;
+    an internal face is owned by the lower cell id."""
+    nz = n if nz is None else nz
+    base = polygon_mesh(n, length, jitter, seed)
+    P2, ptr2, cn2 = base.xyz, base.cell_ptr, base.cell_nodes
+    np2, nc2 = P2.shape[0], ptr2.shape[0] - 1
+    hz = length / nz
+    z = np.tile((np.arange(nz + 1) * hz)[:, None], (1, np2))
+    if jitter > 0.0:
+        dz = (2.0 * uniform(seed, (nz + 1) * np2, stream=13) - 1.0).reshape(nz + 1, np2)
+        z[1:nz] += jitter * hz * dz[1:nz]
+    xyz = np.concatenate([np.concatenate([P2, z[k][:, None]], axis=1) for k in range(nz + 1)])
+    nid = lambda p, k: k * np2 + p  # noqa: E731
+    cid = lambda c, k: k * nc2 + c  # noqa: E731
+    # 2-D edges with the cells on their left (counter-clockwise) and right
+    edge_left = {}
+    for c in range(nc2):
+        cs = cn2[ptr2[c]:ptr2[c + 1]]
+        for j in range(cs.size):
+            edge_left[(int(cs[j]), int(cs[(j + 1) % cs.size]))] = c
+    side_of = {}
+    for (a, b), sd in zip(map(tuple, base.bface_nodes), base.bface_side):
+        side_of[(int(a), int(b))] = int(sd)
+    faces, own, nei, side = [], [], [], []
+
+    def add(nodes, o, nb, sd):
+        if nb >= 0 and nb < o:  # owner is the lower id: flip the face
+            o, nb = nb, o
+            nodes = nodes[::-1]
+        faces.append(np.asarray(nodes, np.int64))
+        own.append(o)
+        nei.append(nb)
+        side.append(sd)
+
+    for k in range(nz + 1):          # horizontal faces, normal +z out of the lower cell
+        for c in range(nc2):
+            cs = [nid(int(p), k) for p in cn2[ptr2[c]:ptr2[c + 1]]]
+            if k == 0:
+                add(cs[::-1], cid(c, 0), -1, 4)
+            elif k == nz:
+                add(cs, cid(c, nz - 1), -1, 5)
+            else:
+                add(cs, cid(c, k - 1), cid(c, k), -1)
+    for k in range(nz):              # side faces, out of the cell on the edge's left
+        for (a, b), c in edge_left.items():
+            quad = [nid(a, k), nid(b, k), nid(b, k + 1), nid(a, k + 1)]
+            other = edge_left.get((b, a), -1)
+            if other >= 0:
+                if c < other:
+                    add(quad, cid(c, k), cid(other, k), -1)
+            else:
+                add(quad, cid(c, k), -1, side_of[(a, b)])
+    fptr = np.concatenate([[0], np.cumsum([f.size for f in faces])]).astype(np.int64)
+    grid = np.stack([np.tile(np.arange(nc2) % (n + 1), nz), np.tile(np.arange(nc2) // (n + 1), nz),
+                     np.repeat(np.arange(nz), nc2)], axis=1).astype(np.int64)
+    return FaceMesh(dim=3, n=n, xyz=np.ascontiguousarray(xyz), face_ptr=fptr,
+                    face_nodes=np.concatenate(faces), owner=np.asarray(own, np.int64),
+                    neighbour=np.asarray(nei, np.int64), face_side=np.asarray(side, np.int32),
+                    n_cells=nc2 * nz, cell_grid=grid, length=length)
+
+
 def make_mesh(dim: int, n: int, length: float = 1.0, jitter: float = 0.0, seed: int = 0,
               cells: str = "tensor") -> Mesh:
-    """structured_mesh (cells="tensor"), simplex_mesh (cells="simplex") or,
-    in 2-D, polygon_mesh (cells="polygon", (n + 1)^2 cells)."""
+    """structured_mesh (cells="tensor"), simplex_mesh (cells="simplex"), in
+    2-D polygon_mesh (cells="polygon", (n + 1)^2 cells), in 3-D prism_mesh
+    (cells="polyhedron", (n + 1)^2 n cells)."""
     if cells == "simplex":
         return simplex_mesh(dim, n, length, jitter, seed)
     if cells == "polygon":
         if dim != 2:
             raise ValueError("polygon meshes are two-dimensional")
         return polygon_mesh(n, length, jitter, seed)
+    if cells == "polyhedron":
+        if dim != 3:
+            raise ValueError("polyhedral meshes are three-dimensional")
+        return prism_mesh(n, n, length, jitter, seed)
     if cells != "tensor":
-        raise ValueError("cells must be 'tensor', 'simplex' or 'polygon'")
+        raise ValueError("cells must be 'tensor', 'simplex', 'polygon' or 'polyhedron'")
     return structured_mesh(dim, n, length, jitter, seed)
 
 

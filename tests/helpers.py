@@ -57,7 +57,8 @@ def bc_from_field(orc: oracle.OracleMesh, field, mu, lam, with_body=True):
     if len(tfaces):
         sig = lin_stress(field.grad(xq[tfaces]), mu, lam)
         a = aq[tfaces]
-        n = a / np.linalg.norm(a, axis=-1, keepdims=True)
+        na = np.linalg.norm(a, axis=-1, keepdims=True)  # 0 at a polyhedral face's padding points
+        n = np.divide(a, na, out=np.zeros_like(a), where=na > 0)
         tbq = np.einsum("fqij,fqj->fqi", sig, n)
     else:
         tbq = np.zeros((0, orc.Q, d))
@@ -108,11 +109,14 @@ def probe_jacobian(pb: Problem, K: int | None = None):
     if K is None:
         K = min(n, 12)
     idx = np.arange(nc)
-    if pb.mesh.cell_ptr is not None:  # polygon dual: one cell per grid node
-        per, g = 1, n + 1
-    else:  # cells per grid square / cube (simplex meshes: 2 or 6)
-        per, g = nc // n ** d, n
-    ij = np.stack(np.unravel_index(idx // per, (g,) * d)[::-1], axis=1)  # (i, j[, k])
+    if hasattr(pb.mesh, "cell_grid"):  # polyhedra: the generator's grid position
+        per, ij = 1, pb.mesh.cell_grid
+    else:
+        if getattr(pb.mesh, "cell_ptr", None) is not None:  # polygon dual: one cell per node
+            per, g = 1, n + 1
+        else:  # cells per grid square / cube (simplex meshes: 2 or 6)
+            per, g = nc // n ** d, n
+        ij = np.stack(np.unravel_index(idx // per, (g,) * d)[::-1], axis=1)  # (i, j[, k])
     color = np.zeros(nc, np.int64)
     for a in range(d):
         color = color * K + (ij[:, a] % K)
