@@ -283,100 +283,6 @@ __global__ void __launch_bounds__(DIM == 3 ? 864 : 256)
 }
 
 // ---------------------------------------------------------------------
-// the same three phases for faces with more points than one thread per
-// (face, row) of a 32-face tile allows (polyhedral faces: up to 8 fan
-// triangles of q^2 points, R up to 96): kWideThreads threads walk the rows
-// and points of the tile in strides
-// ---------------------------------------------------------------------
-constexpr int kWideThreads = 768;
-
-template <int DIM, int LAW>
-__global__ void __launch_bounds__(kWideThreads)
-    k_flux_wide(DevMesh m, Material mt, const double* __restrict__ w,
-                const double* __restrict__ ustar, const double* __restrict__ ubq,
-                const double* __restrict__ ubf, double* __restrict__ flux) {
-  extern __shared__ double sm[];
-  const int R = m.R, Q = m.Q, S = m.S;
-  double* Gs = sm;                        // [32][R][DIM]
-  double* Ts = sm + kTile * R * DIM;      // [32][Q][DIM]
-  const int64_t tile = blockIdx.x;
-  const int64_t nc = m.wst;
-  for (int it = threadIdx.x; it < kTile * R; it += blockDim.x) {
-    const int fi = it / R, r = it % R;
-    const int64_t f = tile * kTile + fi;
-    const int32_t* __restrict__ st = m.fst + tile * S * kTile + fi;
-    const double* __restrict__ co = m.fco + tile * (int64_t)S * kTile * R + it;
-    double acc[DIM];
-#pragma unroll
-    for (int j = 0; j < DIM; ++j) acc[j] = 0.0;
-#pragma unroll 4
-    for (int n = 0; n < S; ++n) {
-      const int32_t id = __ldg(st + n * kTile);
-      const double c = __ldg(co + (int64_t)n * kTile * R);
-#pragma unroll
-      for (int j = 0; j < DIM; ++j) acc[j] = fma(c, __ldg(w + j * nc + id), acc[j]);
-    }
-    if (f >= m.nfi && f < m.nfid) {
-      const int64_t fd = f - m.nfi;
-      const double cg = m.gco[fd * R + r];
-      const int q = r / DIM;
-#pragma unroll
-      for (int j = 0; j < DIM; ++j) acc[j] = fma(cg, ubq[(fd * Q + q) * DIM + j], acc[j]);
-    }
-#pragma unroll
-    for (int j = 0; j < DIM; ++j) Gs[(fi * R + r) * DIM + j] = acc[j];
-  }
-  __syncthreads();
-  for (int it = threadIdx.x; it < kTile * Q; it += blockDim.x) {
-    const int fi = it / Q, q = it % Q;
-    const int64_t f = tile * kTile + fi;
-    double t[DIM];
-    if (f < m.nfid) {
-      double G[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-#pragma unroll
-      for (int i = 0; i < DIM; ++i)
-#pragma unroll
-        for (int j = 0; j < DIM; ++j) G[i][j] = Gs[(fi * R + q * DIM + i) * DIM + j];
-      double a[3];
-#pragma unroll
-      for (int k = 0; k < DIM; ++k) a[k] = m.aq[(f * Q + q) * 3 + k];
-      traction<DIM, LAW>(G, a, mt, t);
-    } else {
-#pragma unroll
-      for (int i = 0; i < DIM; ++i) t[i] = 0.0;
-    }
-#pragma unroll
-    for (int i = 0; i < DIM; ++i) Ts[(fi * Q + q) * DIM + i] = t[i];
-  }
-  __syncthreads();
-  for (int it = threadIdx.x; it < kTile * DIM; it += blockDim.x) {
-    const int fi = it / DIM, i = it % DIM;
-    const int64_t f = tile * kTile + fi;
-    if (f < m.nfid) {
-      double s = 0.0;
-      for (int q = 0; q < Q; ++q) s += Ts[(fi * Q + q) * DIM + i];
-      const int32_t sp = m.fstar[2 * f], sn = m.fstar[2 * f + 1];
-      const double other = sn >= 0 ? ustar[(int64_t)sn * DIM + i] : ubf[(f - m.nfi) * DIM + i];
-      const double coef = mt.alpha * mt.kbar * m.fstab[f];
-      flux[f * DIM + i] = fma(coef, other - ustar[(int64_t)sp * DIM + i], s);
-    }
-  }
-}
-
-// dynamic shared memory of k_flux_wide beyond the default 48 KB; set once
-// per process for both laws, before the first launch or capture
-int flux_wide_prepare(int R, int Q, int dim) {
-  if (dim != 3) return 0;
-  const int smem = (int)(sizeof(double) * kTile * (R * 3 + Q * 3));
-  if (cudaFuncSetAttribute(k_flux_wide<3, HOFV_LAW_LINEAR>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
-      cudaFuncSetAttribute(k_flux_wide<3, HOFV_LAW_NEOHOOKEAN>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
-    return -1;
-  return 0;
-}
-
-// ---------------------------------------------------------------------
 // cell assembly; out = R, or (R - R0) * inv_eps when R0 != nullptr
 // ---------------------------------------------------------------------
 template <int DIM, int NLF>
@@ -477,11 +383,9 @@ static void residual_impl(const DevMesh& m, const Material& mat, const double* w
     k_ustar<DIM, DIM + 1><<<(unsigned)m.nctile, 32 * (DIM + 1), 0, st>>>(m, w, ustar);
   } else if (m.nlf == 2 * DIM) {
     k_ustar<DIM, 2 * DIM><<<(unsigned)m.nctile, 32 * 2 * DIM, 0, st>>>(m, w, ustar);
-  } else if constexpr (DIM == 2) {
-    k_ustar<2, kPolyMaxSides><<<(unsigned)m.nctile, 32 * kPolyMaxSides, 0, st>>>(m, w, ustar);
   } else {
-    k_ustar<3, kPolyhedronMaxFaces><<<(unsigned)m.nctile, 32 * kPolyhedronMaxFaces, 0, st>>>(
-        m, w, ustar);
+    if constexpr (DIM == 2)
+      k_ustar<2, kPolyMaxSides><<<(unsigned)m.nctile, 32 * kPolyMaxSides, 0, st>>>(m, w, ustar);
   }
   if (m.nfy > 0) k_sym_other<DIM><<<(unsigned)((m.nfy + 127) / 128), 128, 0, st>>>(m, ustar);
   if (ev) cudaEventRecord(ev[1], st);
@@ -491,14 +395,8 @@ static void residual_impl(const DevMesh& m, const Material& mat, const double* w
                                                             ustar, ubf, flux);
     } else {
       const size_t smem = sizeof(double) * kTile * (m.R * DIM + m.Q * DIM);
-      if (kTile * m.R <= (DIM == 3 ? 864 : 256)) {
-        k_flux<DIM, LAW><<<(unsigned)m.nftile, kTile * m.R, smem, st>>>(m, mat, w, ustar, ubq,
-                                                                        ubf, flux);
-      } else {
-        if constexpr (DIM == 3)
-          k_flux_wide<3, LAW><<<(unsigned)m.nftile, kWideThreads, smem, st>>>(m, mat, w, ustar,
-                                                                              ubq, ubf, flux);
-      }
+      k_flux<DIM, LAW><<<(unsigned)m.nftile, kTile * m.R, smem, st>>>(m, mat, w, ustar, ubq, ubf,
+                                                                      flux);
     }
   }
   if (ev) cudaEventRecord(ev[2], st);
@@ -509,10 +407,8 @@ static void residual_impl(const DevMesh& m, const Material& mat, const double* w
     k_cell<DIM, DIM + 1><<<cgrid, 256, 0, st>>>(m, flux, src, R0, d_eps, out);
   } else if (m.nlf == 2 * DIM) {
     k_cell<DIM, 2 * DIM><<<cgrid, 256, 0, st>>>(m, flux, src, R0, d_eps, out);
-  } else if constexpr (DIM == 2) {
-    k_cell<2, kPolyMaxSides><<<cgrid, 256, 0, st>>>(m, flux, src, R0, d_eps, out);
   } else {
-    k_cell<3, kPolyhedronMaxFaces><<<cgrid, 256, 0, st>>>(m, flux, src, R0, d_eps, out);
+    if constexpr (DIM == 2) k_cell<2, kPolyMaxSides><<<cgrid, 256, 0, st>>>(m, flux, src, R0, d_eps, out);
   }
   if (ev) cudaEventRecord(ev[3], st);
 }
@@ -610,8 +506,6 @@ void launch_flux_scale(const DevMesh& m, const double* flux, double* out, cudaSt
     k_flux_scale<2, 4><<<grid, 256, 0, st>>>(m, flux, out);
   else if (m.nlf == 4)
     k_flux_scale<3, 4><<<grid, 256, 0, st>>>(m, flux, out);
-  else if (m.nlf == kPolyhedronMaxFaces)
-    k_flux_scale<3, kPolyhedronMaxFaces><<<grid, 256, 0, st>>>(m, flux, out);
   else
     k_flux_scale<3, 6><<<grid, 256, 0, st>>>(m, flux, out);
 }
