@@ -72,10 +72,10 @@ def bc_from_field(orc: oracle.OracleMesh, field, mu, lam, with_body=True):
 
 def make_problem(dim, n, p, q1, n_plus=None, jitter=0.0, seed=0, field=None,
                  tags=None, law=0, mu=1.0, lam=1.5, prepare=True, cells=None,
-                 alpha=0.1, with_body=True, kind="tensor"):
+                 alpha=0.1, with_body=True, kind="tensor", length=1.0):
     if n_plus is None:
         n_plus = 10 if dim == 2 else {1: 45, 2: 55, 3: 65}[p]
-    mesh = I.make_mesh(dim, n, jitter=jitter, seed=seed, cells=kind)
+    mesh = I.make_mesh(dim, n, length=length, jitter=jitter, seed=seed, cells=kind)
     if tags is None:
         tags = np.zeros(2 * dim, np.int32)
     orc = oracle.OracleMesh(mesh, tags, p=p, n_plus=n_plus, q1=q1, alpha=alpha)

@@ -75,3 +75,65 @@ def test_gnn_message_weights_are_symmetric():
             if col[i, k] >= 0:
                 W[i, col[i, k]] += w[i, k]
     assert np.allclose(W, W.T, rtol=1e-14)
+
+
+def test_hand_set_network_has_closed_form_output():
+    """A network with hand-set weights on a regular 5 x 5 grid (all sides
+    displacement): W0 copies the 16 features, layer 1 adds relu of the
+    weighted neighbour sum, layers 2-4 are zero, the decoder reads channel 0
+    into the first component and puts a bias of 0.5 on the second.  With
+    Kbar = 1 on a regular 2-D grid a_ij = 1 and D_i = 4 + (boundary sides of
+    cell i) (a displacement side adds Gamma / (h / 2) = 2), so
+    w_ij = 1 / sqrt(D_i D_j) and the output is, written out by hand,
+      z_out[0] = z[0] + s_z (relu(x_i) + relu(sum_j w_ij relu(x_j))),
+      z_out[1] = z[1] + 0.5 s_z,   x = v[0] / s_v,
+    with s_v, s_z the root-mean-square of all entries of v and z."""
+    dim, n = 2, 5
+    mesh = I.structured_mesh(dim, n)
+    o = oracle.OracleMesh(mesh, I.side_tags("mms", dim), p=1, n_plus=10, q1=2)
+    diag, off = o.aj(1.0)
+    own, nei, lf, tag = o.faces()
+    cf = o.cell_faces()
+    col = -np.ones((o.nc, 2 * dim), np.int64)
+    offm = np.zeros((o.nc, 2 * dim))
+    for c in range(o.nc):
+        for k, f in enumerate(cf[c]):
+            if f < o.nfi:
+                col[c, k] = nei[f] if own[f] == c else own[f]
+                offm[c, k] = off[f]
+    col, w = G.graph_from_aj(diag, col, offm)
+    bnd = np.zeros((o.nc, 2))
+    W0, b0, Ws, bs, Wd, bd = (np.zeros((G.H, G.F_IN)), np.zeros(G.H),
+                              [np.zeros((G.H, 2 * G.H)) for _ in range(G.LAYERS)],
+                              [np.zeros(G.H) for _ in range(G.LAYERS)],
+                              np.zeros((dim, G.H)), np.zeros(dim))
+    W0[:G.F_IN, :] = np.eye(G.F_IN)
+    Ws[0][:, G.H:] = np.eye(G.H)
+    Wd[0, 0] = 1.0
+    bd[1] = 0.5
+    parts = [W0.ravel(), b0]
+    for l in range(G.LAYERS):
+        parts += [Ws[l].ravel(), bs[l]]
+    theta = np.concatenate(parts + [Wd.ravel(), bd])
+    assert theta.size == G.n_params(dim)
+    rng = np.random.default_rng(11)
+    v = rng.standard_normal((dim, o.nc))
+    z = rng.standard_normal((dim, o.nc))
+    zout, _ = G.forward(theta, dim, col, w, v, z, bnd)
+    # by hand: grid neighbours and the closed-form degrees
+    sv = np.sqrt(np.mean(v * v))
+    sz = np.sqrt(np.mean(z * z))
+    x = v[0] / sv
+    ij = [(c % n, c // n) for c in range(n * n)]   # the oracle numbers cells like the generator
+    assert np.allclose(o.xc, (np.array(ij) + 0.5) / n, atol=1e-15)
+    Dg = np.array([4 + (i == 0) + (i == n - 1) + (j == 0) + (j == n - 1) for i, j in ij])
+    want0 = np.zeros(o.nc)
+    for c, (i, j) in enumerate(ij):
+        m = 0.0
+        for (a, b) in ((i - 1, j), (i + 1, j), (i, j - 1), (i, j + 1)):
+            if 0 <= a < n and 0 <= b < n:
+                k = a + n * b
+                m += max(x[k], 0.0) / np.sqrt(Dg[c] * Dg[k])
+        want0[c] = z[0, c] + sz * (max(x[c], 0.0) + max(m, 0.0))
+    assert np.allclose(zout[0], want0, rtol=1e-14, atol=1e-14)
+    assert np.allclose(zout[1], z[1] + 0.5 * sz, rtol=1e-15, atol=1e-15)

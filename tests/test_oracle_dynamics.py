@@ -96,3 +96,30 @@ def test_mass_matrix_matches_the_pointwise_sum(one_point):
     uq, wq = D.point_values(o, u, np.arange(o.nc), one_point)
     want = np.einsum("cq,cqj->jc", wq, uq)
     assert np.allclose(np.stack([M @ u[0], M @ u[1]]), want, rtol=1e-11, atol=1e-14)
+
+
+@pytest.mark.parametrize("dim,n,p,jitter", [(2, 8, 2, 0.2), (2, 8, 3, 0.2), (3, 5, 2, 0.0),
+                                            (3, 5, 3, 0.15)])
+def test_total_inertia_equals_the_analytic_domain_integral(dim, n, p, jitter):
+    """On a mesh of the unit square / cube a motion u = A t^2 + B t + C, A of
+    degree <= p, has the acceleration 2 A; summed over all cells the
+    oracle's inertia term must be rho times the exact integral of 2 A over
+    the domain, sum_m 2 A_m prod_a 1 / (e_a + 1) for the monomials x^e of A
+    (the cells tile the domain, whose boundary nodes are not moved).  The
+    q = p point rule is exact for the mapped integrand on jittered quads
+    (degree p + 1 per direction) and on jittered hexes for p = 3 (degree
+    p + 2 <= 2q - 1); for p = 2 hexes the grid is regular (constant
+    Jacobian), since degree 4 per direction exceeds the 2-point rule."""
+    o = _setup(dim, n, p, jitter)
+    t0, dt, rho = 0.3, 0.02, 1.7
+    A, B, u_at = _quadratic_in_time(o, dim, p, t0, dt)
+    cells = np.arange(o.nc)
+    uq = [D.point_values(o, u_at(t0 + s * dt), cells)[0] for s in (1, 0, -1)]
+    _, wq = D.point_values(o, u_at(t0), cells)
+    xq = o.cell_qp
+    vq_t = 2 * A.value(xq) * t0 + B.value(xq)
+    vq_tm1 = 2 * A.value(xq) * (t0 - dt) + B.value(xq)
+    term = D.inertia(rho, D.bdf2_acceleration(uq[0], uq[1], uq[2], vq_t, vq_tm1, dt), wq)
+    exact = rho * sum(2.0 * A.coef[m] / np.prod([e + 1.0 for e in ex])
+                      for m, ex in enumerate(A.exps))
+    assert np.abs(term.sum(axis=1) - exact).max() <= 1e-8 * np.abs(exact).max()

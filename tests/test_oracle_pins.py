@@ -427,3 +427,43 @@ def test_manufactured_solution_rates(p, q1, field, disp_rate, stress_rate):
     rs = math.log2(es[1] / es[2])
     assert rd >= disp_rate, (ed, rd)
     assert rs >= stress_rate, (es, rs)
+
+
+def _gmres_solve(pb):
+    """Solve R(u) = 0 for the (affine) linear-law residual with scipy's GMRES:
+    the oracle's residual as the operator, the oracle's compact approximate
+    Jacobian (Sec. 4.1), factorised, as the preconditioner."""
+    import scipy.sparse.linalg as spla
+    o, d = pb.orc, pb.dim
+    nc = o.nc
+    R0 = H.residual(pb, np.zeros((d, nc)))
+    lu = spla.splu(o.aj_matrix(2 * pb.mu + pb.lam).tocsc())
+    mv = lambda x: (H.residual(pb, x.reshape(d, nc)) - R0).ravel()  # noqa: E731
+    pc = lambda x: np.concatenate([lu.solve(r) for r in x.reshape(d, nc)])  # noqa: E731
+    n = d * nc
+    u, info = spla.gmres(spla.LinearOperator((n, n), matvec=mv), -R0.ravel(),
+                         M=spla.LinearOperator((n, n), matvec=pc), rtol=1e-11, restart=200,
+                         maxiter=2000)
+    assert info == 0
+    assert np.linalg.norm(mv(u) + R0.ravel()) <= 1e-10 * np.linalg.norm(R0)
+    return u.reshape(d, nc)
+
+
+@pytest.mark.parametrize("p,disp_rate,stress_rate", [(2, 1.8, 1.7), (3, 3.7, 2.7)])
+def test_manufactured_solution_rates_3d(p, disp_rate, stress_rate):
+    """Case 1 in 3-D (Sec. 5.1.1): the paper's trigonometric field on its
+    0.2 m cube of hexahedra, N = 8 and 12 cells per side; displacement order
+    >= p + 0.7 for p = 3 (>= 1.8 for p = 2, the paper's observed asymptote)
+    and stress order >= p - 0.3."""
+    field = I.Trig3D(a=(1.0, 1.0, 1.0))
+    ed, es = [], []
+    for n in (8, 12):
+        pb = H.make_problem(3, n, p, p, seed=11, field=field, mu=1.0, lam=1.5, length=0.2)
+        u = _gmres_solve(pb)
+        mag = np.linalg.norm(u, axis=0) - np.linalg.norm(pb.u_exact, axis=0)
+        ed.append(math.sqrt(np.mean(mag ** 2)))
+        es.append(_cell_von_mises_error(pb, u))
+    rd = math.log(ed[0] / ed[1]) / math.log(12 / 8)
+    rs = math.log(es[0] / es[1]) / math.log(12 / 8)
+    assert rd >= disp_rate, (ed, rd)
+    assert rs >= stress_rate, (es, rs)
