@@ -266,6 +266,7 @@ def run_hofv(args):
         import torch.distributed as dist
         dist.barrier()
     wl, mesh, ctx, lay, setup_s, u_ex, field = build_workload(args.workload, local)
+    ctx.set_precision(hofv.PREC_DF64 if args.precision == "df64" else hofv.PREC_FP64)
     d, nc = wl.dim, lay.n_cells
     n = d * nc
     dev = torch.device("cuda", local)
@@ -770,6 +771,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="hofv", choices=["hofv", "reference"])
     ap.add_argument("--workload", default="quad512j-p3-mixed")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "df64"],
+                    help="arithmetic of the gradient contraction (hofv_set_precision)")
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)

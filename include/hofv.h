@@ -66,6 +66,10 @@ extern "C" {
 #define HOFV_PC_AJMG 3   /* same operator (FP32), CG with an algebraic-multigrid V-cycle */
 #define HOFV_PC_NEJ 4    /* near-exact Jacobian (linear law), inner GMRES with AJMG */
 
+/* arithmetic of the gradient contraction (hofv_set_precision) */
+#define HOFV_PREC_FP64 0   /* FP64 fused multiply-adds (default) */
+#define HOFV_PREC_DF64 1   /* double-float pairs on the FP32 pipe, everything else FP64 */
+
 /* point sets for hofv_get_points */
 #define HOFV_PTS_CELL_CENTROID 0   /* [n_cells][dim] */
 #define HOFV_PTS_DISP_QP 1         /* [n_disp][Q][dim]  displacement-face Gauss points */
@@ -241,6 +245,30 @@ int hofv_set_material(hofv_ctx* ctx, int law, double mu, double lambda);
    rounding; the neo-Hookean law always uses the per-point form. */
 int hofv_set_contraction(hofv_ctx* ctx, int on);
 
+/* Arithmetic of the dominant step of the residual, the contraction of the
+   reconstruction coefficients with the stencil values (the displacement
+   gradient at every face Gauss point, eq. faceQuadGrad, and the
+   extrapolated face values of the stabilisation, eq. alphaJump).
+   HOFV_PREC_FP64 (default) uses FP64 fused multiply-adds.  HOFV_PREC_DF64
+   stores each coefficient as a pair of floats (hi, lo), hi + lo its value
+   rounded to 48 significant bits, splits the state the same way, forms each
+   product exactly (TwoProduct by FMA, Dekker 1971) and accumulates with
+   TwoSum and a compensation term (Dot2, Ogita, Rump & Oishi 2005), on the
+   FP32 pipe; each gradient is then converted to FP64 and the law,
+   quadrature, stabilisation jump, assembly and every solver vector stay
+   FP64.  With HOFV_PREC_DF64 hofv_jvp contracts u and v separately and
+   differences the face fluxes of grad u + eps grad v and grad u in FP64,
+   which is R(u + eps v) - R(u) with the rounding of the contraction of u
+   cancelling exactly; it does not read Ru.  Callable at any time: after
+   hofv_build_stencils the coefficient arrays are rewritten in place
+   (synchronises); switching back to FP64 keeps the 48-bit values until the
+   next hofv_build_stencils.  The environment variable HOFV_PRECISION
+   (fp64 / df64) sets the default of new contexts.  EINVAL for an unknown
+   mode. */
+int hofv_set_precision(hofv_ctx* ctx, int prec);
+/* The current HOFV_PREC_* of the context (or EINVAL for NULL). */
+int hofv_get_precision(const hofv_ctx* ctx);
+
 /* y = J_NEJ x with the near-exact Jacobian of the appendix on the
    near-exact-Jacobian preconditioner: the Jacobian of the face fluxes of
    the linear-elastic law without the stabilisation term (ghost-node and
@@ -309,7 +337,8 @@ int hofv_residual(hofv_ctx* ctx, const double* u, double* R);
 /* Jacobian-vector product by forward difference (Sec. 4.1):
    Jv = (R(u + eps v) - R(u)) / eps with
    eps = sqrt(2^-52) (1 + ||u||_2) / ||v||_2 computed on the device.
-   Ru must hold R(u).  u, Ru, v, Jv: DEVICE [dim][n_cells].  eps_used: HOST
+   Ru must hold R(u) (with HOFV_PREC_DF64 it is not read: see
+   hofv_set_precision).  u, Ru, v, Jv: DEVICE [dim][n_cells].  eps_used: HOST
    pointer or NULL; when non-NULL the call synchronises to return eps. */
 int hofv_jvp(hofv_ctx* ctx, const double* u, const double* Ru, const double* v,
              double* Jv, double* eps_used);
@@ -418,12 +447,20 @@ int hofv_arnoldi_step(hofv_ctx* ctx, const double* u, const double* Ru, int kind
    no counterpart: this is a property of the library, not of the method.
    The call allocates nothing: its scratch is one fixed device array of
    32 MiB (4 Mi doubles) compiled into the library and held on every GPU
-   that loads it until exit.  Meshes needing more scratch than that
-   (n_cells * 2 dim * dim + (n_internal + n_disp) * dim doubles) get
-   HOFV_EINVAL.  All calls share the array: calls that overlap on the GPU
-   race and must be serialised by the caller.  The first call on a device
-   resolves the array's address (cudaGetSymbolAddress) and should come
-   before any stream capture.  u, R: DEVICE [dim][n_cells]. */
+   that loads it until exit.  A mesh needs n_cells * F * dim doubles
+   (F = face slots per cell: dim + 1 for triangles / tetrahedra, 2 dim for
+   quads / hexes, 8 for polygons), rounded up to a multiple of 32, plus
+   (n_internal + n_disp + n_symm) * dim, rounded up to 32, plus with
+   HOFV_PREC_DF64 (n_cells + mirror nodes) * 4 (2-D) or 8 (3-D) for the
+   split state; larger meshes get HOFV_EINVAL.  All calls share the array:
+   calls that overlap on the GPU race and must be serialised by the caller.
+   Like every evaluation call it also writes buffers of its own context
+   (extended state and mirrored face values of symmetry faces, the inertia
+   term), so it must be ordered with the context's other evaluation calls
+   issued from other streams.  The first call on a device resolves the
+   array's address (cudaGetSymbolAddress), again after the device's CUDA
+   context has changed (e.g. after cudaDeviceReset); that first call should
+   come before any stream capture.  u, R: DEVICE [dim][n_cells]. */
 int hofv_residual_noalloc(hofv_ctx* ctx, const double* u, double* R);
 
 /* The multigrid hierarchy of HOFV_PC_AJMG (built here if not yet built):

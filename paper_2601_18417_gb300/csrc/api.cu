@@ -72,6 +72,13 @@ DevMesh dev_mesh(const hofv_ctx* c) {
   m.mscale = c->inertia ? c->d_mscale : nullptr;
   m.cmass = (c->inertia && !c->one_point) ? c->d_cmass : nullptr;
   m.inert = c->d_inert;
+  m.prec = c->prec;
+  m.su = c->d_su;
+  m.sv = c->d_sv;
+  m.ustar_v = c->d_ustar_v;
+  m.vext = c->d_vext;
+  m.gcache = c->d_gcache;
+  m.tcache = c->d_tcache;
   return m;
 }
 
@@ -158,6 +165,11 @@ static void free_built(hofv_ctx* c) {
   c->hist_set = false;
   c->d_cmass = c->d_mscale = c->d_inert = c->d_hist = nullptr;
   c->d_ustar = c->d_flux = c->d_w = c->d_red = c->d_scal = nullptr;
+  c->d_su = c->d_sv = nullptr;
+  c->d_ustar_v = c->d_vext = nullptr;
+  c->d_gcache = c->d_tcache = nullptr;
+  c->jv_u = c->jv_R = nullptr;
+  c->jv_cur++;
   c->d_count = nullptr;
   c->d_aj_diag = c->d_aj_off = nullptr;
   c->d_aj_col = nullptr;
@@ -170,6 +182,60 @@ static void free_built(hofv_ctx* c) {
   c->d_V = c->d_Z = c->d_kvec = c->d_h = nullptr;
   c->kry_m = 0;
   c->built = false;
+}
+
+// rewrite the face and cell coefficient arrays as double-float pairs
+// (to_df = 1) or back to doubles (0), in place
+static int coef_format(hofv_ctx* c, int to_df) {
+  const int64_t nfco = std::max<int64_t>(c->nftile, 1) * c->S * kTile * c->Q * c->dim;
+  const int64_t ncex = c->nctile * c->S * kTile * c->nlf;
+  launch_coef_format(c->d_fco, nfco, to_df, c->stream);
+  launch_coef_format(c->d_cex, ncex, to_df, c->stream);
+  HOFV_CUDA(c, cudaGetLastError());
+  HOFV_CUDA(c, cudaStreamSynchronize(c->stream));
+  return 0;
+}
+
+// ---- linearisation cache of the neo-Hookean double-float Jv ----
+static bool jv_uses_cache(const hofv_ctx* c) {
+  return c->prec == HOFV_PREC_DF64 && c->have_mat && c->mat.law == HOFV_LAW_NEOHOOKEAN;
+}
+
+// storage of the cache, allocated by the set-up calls that make it needed
+static int ensure_jv_storage(hofv_ctx* c) {
+  if (!c->built || !jv_uses_cache(c) || c->d_gcache) return 0;
+  const int64_t nf = std::max<int64_t>(c->nftile, 1) * kTile;
+  TRY(dev_alloc(c, &c->d_gcache, nf * c->Q * c->dim * c->dim));
+  TRY(dev_alloc(c, &c->d_tcache, nf * c->Q * c->dim));
+  return 0;
+}
+
+// the cache no longer describes any state (data, material or coefficients
+// changed, or the state it was filled from may have been overwritten)
+static void jv_invalidate(hofv_ctx* c) {
+  c->jv_cur++;
+  c->jv_u = c->jv_R = nullptr;
+}
+
+// a residual evaluation at u: the caller may have changed u in place
+static void jv_touch(hofv_ctx* c, const double* u) {
+  if (u == c->jv_u) jv_invalidate(c);
+}
+
+// gradient rows and tractions at u, for the Jv calls about (u, R(u)) that
+// follow; refilled when (u, Ru) differs from the last fill or after an
+// invalidation.  Host-side check plus, on a miss, one launch sequence:
+// call outside stream capture.
+int ensure_jv_cache(hofv_ctx* c, const double* u, const double* Ru) {
+  if (!jv_uses_cache(c)) return 0;
+  if (c->jv_u == u && c->jv_R == Ru && c->jv_gen == c->jv_cur) return 0;
+  TRY(ensure_jv_storage(c));
+  launch_jv_cache_fill(dev_mesh(c), c->mat, u, c->d_ubq, c->stream);
+  HOFV_CUDA(c, cudaGetLastError());
+  c->jv_u = u;
+  c->jv_R = Ru;
+  c->jv_gen = c->jv_cur;
+  return 0;
 }
 
 // contracted linear-elastic face matrices for the current material
@@ -232,7 +298,23 @@ int hofv_set_contraction(hofv_ctx* c, int on) {
   return refresh_source(c);
 }
 
-const char* hofv_version(void) { return "hofv 0.1 (sm_103a)"; }
+int hofv_set_precision(hofv_ctx* c, int prec) {
+  if (!c) return HOFV_EINVAL;
+  if (prec != HOFV_PREC_FP64 && prec != HOFV_PREC_DF64) return fail(c, HOFV_EINVAL, "unknown precision");
+  if (prec == c->prec) return HOFV_OK;
+  invalidate_graphs(c);
+  jv_invalidate(c);
+  if (c->built) {
+    HOFV_CUDA(c, cudaSetDevice(c->device));
+    TRY(coef_format(c, prec == HOFV_PREC_DF64 ? 1 : 0));
+  }
+  c->prec = prec;
+  return ensure_jv_storage(c);
+}
+
+int hofv_get_precision(const hofv_ctx* c) { return c ? c->prec : HOFV_EINVAL; }
+
+const char* hofv_version(void) { return "hofv 0.2 (sm_103a)"; }
 
 int hofv_create(hofv_ctx** out, int device, void* stream) {
   if (!out) return HOFV_EINVAL;
@@ -243,6 +325,9 @@ int hofv_create(hofv_ctx** out, int device, void* stream) {
   hofv_ctx* c = new hofv_ctx();
   c->device = device;
   c->stream = static_cast<cudaStream_t>(stream);
+  // default arithmetic of the gradient contraction
+  const char* pe = getenv("HOFV_PRECISION");
+  if (pe && (strcmp(pe, "df64") == 0 || strcmp(pe, "DF64") == 0)) c->prec = HOFV_PREC_DF64;
   *out = c;
   return HOFV_OK;
 }
@@ -644,6 +729,17 @@ int hofv_build_stencils(hofv_ctx* c) {
   TRY(dev_alloc(c, &c->d_flux, std::max<int64_t>(c->nfid, 1) * d));
   TRY(dev_alloc(c, &c->d_w, nc * d));
   if (c->ng > 0) TRY(dev_alloc(c, &c->d_wext, (nc + c->ng) * d));
+  // double-float scratch: split state and Jv direction, extrapolated values
+  // of the direction, its extended copy
+  TRY(dev_alloc(c, &c->d_su, (nc + c->ng) * split4(d)));
+  TRY(dev_alloc(c, &c->d_sv, (nc + c->ng) * split4(d)));
+  TRY(dev_alloc(c, &c->d_ustar_v, nc * nlf * d));
+  if (c->ng > 0) TRY(dev_alloc(c, &c->d_vext, (nc + c->ng) * d));
+  {
+    const int e = setup_df_kernels();
+    if (e != 0) return cuda_fail(c, (cudaError_t)e, "cudaFuncSetAttribute(face kernels)");
+  }
+  if (c->prec == HOFV_PREC_DF64) TRY(coef_format(c, 1));
   c->red_blocks = 4 * 152;
   TRY(dev_alloc(c, &c->d_red, (int64_t)c->red_blocks * 128));
   TRY(dev_alloc(c, &c->d_count, 256));
@@ -657,6 +753,7 @@ int hofv_build_stencils(hofv_ctx* c) {
   c->built = true;
   c->tco_valid = false;
   TRY(build_contraction(c));
+  TRY(ensure_jv_storage(c));
   c->setup_seconds =
       std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   return HOFV_OK;
@@ -747,6 +844,8 @@ int hofv_set_material(hofv_ctx* c, int law, double mu, double lambda) {
   c->mat.alpha = c->alpha;
   c->have_mat = true;
   c->tco_valid = false;
+  jv_invalidate(c);
+  TRY(ensure_jv_storage(c));
   if (c->built) {
     TRY(build_contraction(c));
     TRY(refresh_source(c));
@@ -775,6 +874,7 @@ int hofv_set_bc(hofv_ctx* c, const double* ubq, const double* ubf, const double*
   TRY(put(c->d_ubf, ubf, c->nfd * d));
   TRY(put(c->d_tbq, tbq, c->nft * c->Q * d));
   TRY(put(c->d_body, body, c->nc * d));
+  jv_invalidate(c);  // the ghost-node data enter the cached gradients
   TRY(refresh_source(c));
   return HOFV_OK;
 }
@@ -816,6 +916,7 @@ static int check_eval(hofv_ctx* c) {
 int hofv_residual(hofv_ctx* c, const double* u, double* R) {
   TRY(check_eval(c));
   if (!u || !R) return fail(c, HOFV_EINVAL, "null vector");
+  jv_touch(c, u);
   launch_residual(dev_mesh(c), c->mat, u, nullptr, nullptr, nullptr, R, c->d_ustar, c->d_flux,
                   c->d_ubq, c->d_ubf, c->d_src, c->stream);
   HOFV_CUDA(c, cudaGetLastError());
@@ -829,6 +930,11 @@ static int jvp_impl(hofv_ctx* c, const double* u, const double* Ru, const double
   double* sc = c->d_scal;
   launch_norm2(v, n, c->d_red, c->d_count, sc + 1, c->red_blocks, c->stream);
   launch_jv_eps(sc + 0, sc + 1, sc + 2, c->stream);
+  if (c->prec == HOFV_PREC_DF64) {  // the caller made the linearisation cache valid
+    launch_jv_df(dev_mesh(c), c->mat, v, sc + 2, Jv, c->d_flux, c->stream);
+    HOFV_CUDA(c, cudaGetLastError());
+    return 0;
+  }
   launch_waxpy_dev(c->d_w, u, v, sc + 2, 1.0, n, c->stream);
   launch_residual(dev_mesh(c), c->mat, c->d_w, nullptr, sc + 2, Ru, Jv, c->d_ustar, c->d_flux,
                   c->d_ubq, c->d_ubf, c->d_src, c->stream);
@@ -842,6 +948,7 @@ int hofv_jvp(hofv_ctx* c, const double* u, const double* Ru, const double* v, do
   if (!u || !Ru || !v || !Jv) return fail(c, HOFV_EINVAL, "null vector");
   const int64_t n = c->nc * c->dim;
   launch_norm2(u, n, c->d_red, c->d_count, c->d_scal + 0, c->red_blocks, c->stream);
+  TRY(ensure_jv_cache(c, u, Ru));
   TRY(jvp_impl(c, u, Ru, v, Jv));
   if (eps_used) {
     HOFV_CUDA(c, cudaMemcpyAsync(eps_used, c->d_scal + 2, sizeof(double), cudaMemcpyDeviceToHost,
@@ -1080,6 +1187,7 @@ static int fgmres(hofv_ctx* c, const hofv_solve_opts& o, const double* u, const 
   F.hbuf.assign(2 * (m + 2), 0.0);
   HOFV_CUDA(c, cudaMemsetAsync(x, 0, sizeof(double) * n, c->stream));
   HOFV_CUDA(c, cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
+  TRY(ensure_jv_cache(c, u, Ru));
   int total = 0;
   double res = dev_norm(c, r, n);
   const double res0 = res;
@@ -1265,6 +1373,7 @@ extern "C" int hofv_newton_solve(hofv_ctx* c, double* u, const hofv_solve_opts* 
       if (o.verbose >= 2) {
         // true linear residual ||R + J du|| and its FD estimate with a 100x larger step
         double* w = c->d_kvec;
+        TRY(ensure_jv_cache(c, u, R));
         TRY(jvp_impl(c, u, R, du, w));
         launch_axpby(w, 1.0, R, 1.0, n, c->stream);
         const double tr = dev_norm(c, w, n);
@@ -1296,6 +1405,7 @@ extern "C" int hofv_newton_solve(hofv_ctx* c, double* u, const hofv_solve_opts* 
       }
       HOFV_CUDA(c, cudaMemcpyAsync(u, ut, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
       HOFV_CUDA(c, cudaMemcpyAsync(R, Rt, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
+      jv_invalidate(c);  // u moved
       rn = rt;
       st.newton_iters++;
     }
@@ -1306,6 +1416,15 @@ extern "C" int hofv_newton_solve(hofv_ctx* c, double* u, const hofv_solve_opts* 
   st.status = status;
   if (stats) *stats = st;
   return status;
+}
+
+// host copy of a coefficient array held as double-float pairs -> doubles
+static void df_to_double(std::vector<double>& a) {
+  for (double& x : a) {
+    float hl[2];
+    memcpy(hl, &x, sizeof(hl));
+    x = (double)hl[0] + (double)hl[1];
+  }
 }
 
 extern "C" {
@@ -1327,6 +1446,7 @@ int hofv_get_face_data(hofv_ctx* c, int64_t first, int64_t count, int32_t* stenc
     co.resize((size_t)(t1 - t0) * S * kTile * R);
     HOFV_CUDA(c, cudaMemcpy(co.data(), c->d_fco + t0 * S * kTile * R, sizeof(double) * co.size(),
                             cudaMemcpyDeviceToHost));
+    if (c->prec == HOFV_PREC_DF64) df_to_double(co);
     if (c->nfd + c->nfy > 0) {
       gc.resize((size_t)(c->nfd + c->nfy) * R);
       HOFV_CUDA(c, cudaMemcpy(gc.data(), c->d_gco, sizeof(double) * gc.size(), cudaMemcpyDeviceToHost));
@@ -1367,6 +1487,7 @@ int hofv_get_cell_data(hofv_ctx* c, int64_t first, int64_t count, int32_t* stenc
     ex.resize((size_t)(t1 - t0) * S * kTile * nlf);
     HOFV_CUDA(c, cudaMemcpy(ex.data(), c->d_cex + t0 * S * kTile * nlf, sizeof(double) * ex.size(),
                             cudaMemcpyDeviceToHost));
+    if (c->prec == HOFV_PREC_DF64) df_to_double(ex);
   }
   for (int64_t cell = first; cell < hi; ++cell) {
     const int64_t t = cell / kTile - t0, ci = cell % kTile, o = cell - first;
@@ -1426,6 +1547,7 @@ extern "C" int hofv_arnoldi_step(hofv_ctx* c, const double* u, const double* Ru,
   memset(&st, 0, sizeof(st));
   const int k = j + 1;
   const ArnoldiKey key{c->gen, kind, inner_iters, j, 1, 1, u, Ru, V, Z, w, dh, ld, k};
+  TRY(ensure_jv_cache(c, u, Ru));
   TRY(arnoldi_device(c, o, key, &st));
   std::vector<double> hb((size_t)(2 * k + 1));
   HOFV_CUDA(c, cudaMemcpyAsync(hb.data(), dh, sizeof(double) * hb.size(), cudaMemcpyDeviceToHost,
@@ -1441,6 +1563,7 @@ extern "C" int hofv_arnoldi_step(hofv_ctx* c, const double* u, const double* Ru,
 extern "C" int hofv_residual_timed(hofv_ctx* c, const double* u, double* R, float* ms) {
   TRY(check_eval(c));
   if (!u || !R || !ms) return fail(c, HOFV_EINVAL, "null argument");
+  jv_touch(c, u);
   cudaEvent_t ev[4];
   for (int i = 0; i < 4; ++i) HOFV_CUDA(c, cudaEventCreate(&ev[i]));
   launch_residual(dev_mesh(c), c->mat, u, nullptr, nullptr, nullptr, R, c->d_ustar, c->d_flux,
@@ -1456,6 +1579,7 @@ extern "C" int hofv_residual_timed(hofv_ctx* c, const double* u, double* R, floa
 extern "C" int hofv_force_scale(hofv_ctx* c, const double* u, double* fs) {
   TRY(check_eval(c));
   if (!u || !fs) return fail(c, HOFV_EINVAL, "null argument");
+  jv_touch(c, u);
   launch_residual(dev_mesh(c), c->mat, u, nullptr, nullptr, nullptr, c->d_w, c->d_ustar, c->d_flux,
                   c->d_ubq, c->d_ubf, c->d_src, c->stream);
   launch_flux_scale(dev_mesh(c), c->d_flux, c->d_w, c->stream);

@@ -54,7 +54,22 @@ struct DevMesh {
   const double* mscale;   // [nc] -rho Omega_P c2, or nullptr (no inertia term)
   const double* cmass;    // [nctile][S][kTile] cell-average weights, or nullptr (ubar = u_P)
   double* inert;          // [dim][nc] scratch: the inertia term of the current call
+  // gradient contraction precision (HOFV_PREC_*).  With HOFV_PREC_DF64 every
+  // 8-byte slot of fco and cex holds a double-float pair (float hi, float lo),
+  // and the state is split into such pairs before the contraction
+  int prec;
+  float4* su;             // [wst][kSplit4] split state (scratch)
+  float4* sv;             // [wst][kSplit4] split Jv direction (scratch)
+  double* ustar_v;        // [nc][nlf][dim] extrapolated values of the Jv direction (scratch)
+  double* vext;           // [dim][wst] extended Jv direction (symmetry faces; scratch)
+  // linearisation of the neo-Hookean law at u for the double-float Jv:
+  // gradient rows and Gauss-point tractions of every face at u
+  double* gcache;         // [nftile * kTile][R][dim]
+  double* tcache;         // [nftile * kTile][Q][dim]
 };
+
+// float4 slots per cell of a split state: (h0, l0, h1, l1) [, (h2, l2, 0, 0)]
+__host__ __device__ constexpr int split4(int dim) { return dim == 2 ? 1 : 2; }
 
 struct Material {
   int law;
@@ -125,6 +140,19 @@ struct hofv_ctx {
   double* d_tco = nullptr;
   double* d_gflux = nullptr;        // [nfd][dim] ghost-node flux (constant per load step)
   bool src_dirty = true;
+  // ---- gradient contraction precision (HOFV_PREC_*) ----
+  int prec = HOFV_PREC_FP64;
+  float4* d_su = nullptr;           // [nc + ng][split4] split state
+  float4* d_sv = nullptr;           // [nc + ng][split4] split Jv direction
+  double* d_ustar_v = nullptr;      // [nc][nlf][dim]
+  double* d_vext = nullptr;         // [dim][nc + ng]
+  // neo-Hookean double-float Jv: face gradients and tractions at u, valid
+  // for the state / residual pair (jv_u, jv_R) while jv_gen == jv_cur
+  double* d_gcache = nullptr;
+  double* d_tcache = nullptr;
+  const double* jv_u = nullptr;
+  const double* jv_R = nullptr;
+  uint64_t jv_gen = 0, jv_cur = 1;
   // ---- scratch for the residual ----
   double* d_ustar = nullptr;        // [nc][nlf][dim]
   double* d_flux = nullptr;         // [nfid][dim]
@@ -232,6 +260,28 @@ void launch_residual(const DevMesh& m, const Material& mat, const double* u, con
                      const double* d_eps, const double* R0, double* out, double* ustar,
                      double* flux, const double* ubq, const double* ubf, const double* src,
                      cudaStream_t st, cudaEvent_t* ev = nullptr);
+// Jv with HOFV_PREC_DF64 (eps read from *d_eps on the device).  Linear law:
+// the residual is affine, so (R(u + eps v) - R(u)) / eps is evaluated exactly
+// as its homogeneous part at v (no boundary data, no sources).  Neo-Hookean:
+// the face kernels contract v alone and difference the tractions of
+// grad u + eps grad v and grad u in FP64, grad u and its tractions read from
+// the linearisation cache (launch_jv_cache_fill), so the rounding of the
+// double-float contraction of u cancels exactly
+void launch_jv_df(const DevMesh& m, const Material& mat, const double* v, const double* d_eps,
+                  double* out, double* flux, cudaStream_t st);
+// the neo-Hookean linearisation at u for launch_jv_df: face gradient rows
+// (with the ghost-node data) and Gauss-point tractions into m.gcache,
+// m.tcache
+void launch_jv_cache_fill(const DevMesh& m, const Material& mat, const double* u,
+                          const double* ubq, cudaStream_t st);
+// rewrites the n 8-byte slots of a coefficient array in place: to_df != 0
+// turns each double into the double-float pair (float hi, float lo) with
+// hi + lo its value rounded to 48 significant bits; to_df == 0 turns the pairs
+// back into doubles (exactly)
+void launch_coef_format(double* a, int64_t n, int to_df, cudaStream_t st);
+// raises the dynamic shared-memory limit of the double-float face kernels
+// (once per process); 0 or a cudaError_t
+int setup_df_kernels();
 void launch_source(const hofv_ctx* c, cudaStream_t st);
 void launch_build_tco(const DevMesh& m, double mu, double lam, double* tco, cudaStream_t st);
 void launch_ghost_flux(const DevMesh& m, double mu, double lam, const double* ubq, double* gflux,

@@ -22,6 +22,7 @@
 // with all 32 lanes busy: a tile's (face, row) pairs are laid out so that
 // consecutive threads own consecutive coefficient rows.
 #include <algorithm>
+#include <type_traits>
 
 #include "hofv_internal.cuh"
 
@@ -413,10 +414,19 @@ static void residual_impl(const DevMesh& m, const Material& mat, const double* w
   if (ev) cudaEventRecord(ev[3], st);
 }
 
+void launch_residual_df(const DevMesh& m, const Material& mat, const double* w,
+                        const double* d_eps, const double* R0, double* out, double* ustar,
+                        double* flux, const double* ubq, const double* ubf, const double* src,
+                        cudaStream_t st, cudaEvent_t* ev);
+
 void launch_residual(const DevMesh& m, const Material& mat, const double* w, const double* /*v*/,
                      const double* d_eps, const double* R0, double* out, double* ustar,
                      double* flux, const double* ubq, const double* ubf, const double* src,
                      cudaStream_t st, cudaEvent_t* ev) {
+  if (m.prec == HOFV_PREC_DF64) {
+    launch_residual_df(m, mat, w, d_eps, R0, out, ustar, flux, ubq, ubf, src, st, ev);
+    return;
+  }
   if (m.dim == 2) {
     if (mat.law == HOFV_LAW_LINEAR)
       residual_impl<2, 0>(m, mat, w, d_eps, R0, out, ustar, flux, ubq, ubf, src, st, ev);
@@ -544,7 +554,12 @@ __global__ void k_build_tco(DevMesh m, double mu, double lam, double* __restrict
       double c[DIM], a[DIM], ca = 0.0;
 #pragma unroll
       for (int i = 0; i < DIM; ++i) {
-        c[i] = co[q * DIM + i];
+        if (m.prec == HOFV_PREC_DF64) {  // stored as a double-float pair
+          const float2 p = reinterpret_cast<const float2*>(co)[q * DIM + i];
+          c[i] = (double)p.x + (double)p.y;
+        } else {
+          c[i] = co[q * DIM + i];
+        }
         a[i] = m.aq[(f * m.Q + q) * 3 + i];
         ca += c[i] * a[i];
       }
@@ -644,6 +659,507 @@ void launch_tflux(const DevMesh& m, const double* tco, double alpha_kbar, const 
     k_tflux<2><<<(unsigned)m.nftile, 32 * 2, 0, st>>>(m, tco, alpha_kbar, w, ustar, ubf, flux);
   else
     k_tflux<3><<<(unsigned)m.nftile, 32 * 3, 0, st>>>(m, tco, alpha_kbar, w, ustar, ubf, flux);
+}
+
+}  // namespace hofv
+
+
+// =====================================================================
+// Gradient contraction in double-float arithmetic (HOFV_PREC_DF64).
+//
+// GB300 issues FP64 at 2 FMAs per clock per SM and FP32 at 128, while the
+// per-point face kernel does d FP64 FMAs per 8-byte coefficient: it is bound
+// by the FP64 pipe at 20-35 % of HBM.  Here every coefficient is stored as a
+// pair of floats (hi, lo) in the same 8 bytes and the state is split the
+// same way once per call; each product c u is formed as hi*hi exactly
+// (TwoProduct by FMA, Dekker 1971) plus the cross terms, and accumulated by
+// TwoSum with a compensation float (Dot2, Ogita, Rump & Oishi 2005): twelve
+// FP32 instructions per product.  The sum is converted to FP64 for the law,
+// the quadrature, the stabilisation jump and the assembly, which stay FP64.
+//
+// Jv must not difference two residuals contracted separately: each carries
+// an independent rounding of 2^-48 relative, which the division by eps
+// (~1e-8) would amplify.  For the linear law the residual is affine and the
+// difference quotient is evaluated exactly as the homogeneous residual of v
+// (no boundary data or sources).  For the neo-Hookean law the kernels
+// contract v alone and difference the tractions of grad u + eps grad v and
+// grad u in FP64, with grad u and its tractions taken from a cache filled
+// once per linearisation point, so the rounding of grad u cancels exactly.
+//
+// The face kernel runs half a tile (16 faces) per block so that two or more
+// blocks share an SM and the FP32 contraction of one overlaps the FP64 law
+// of another.
+// =====================================================================
+namespace hofv {
+
+constexpr int kFaceBlock = 16;  // faces per block of the double-float face kernel
+
+// modes of the double-float face kernel
+constexpr int kDfResidual = 0;  // flux of u (split a, extrapolated values ua)
+constexpr int kDfHomog = 1;     // linear law: flux of v without ghost data or prescribed values
+constexpr int kDfFill = 2;      // neo-Hookean: gradient rows and tractions of u into the cache
+constexpr int kDfJv = 3;        // neo-Hookean: flux(u + eps v) - flux(u) from the cache
+
+__device__ __forceinline__ void ff_mac(float ch, float cl, float uh, float ul, float& s, float& e) {
+  const float p = __fmul_rn(ch, uh);
+  float r = __fmaf_rn(ch, uh, -p);  // exact rounding error of ch * uh
+  r = __fmaf_rn(ch, ul, r);
+  r = __fmaf_rn(cl, uh, r);
+  const float t = __fadd_rn(s, p);
+  const float z = __fsub_rn(t, s);
+  const float q = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));  // TwoSum error
+  s = t;
+  e = __fadd_rn(e, __fadd_rn(q, r));
+}
+
+__device__ __forceinline__ double ff_value(float s, float e) { return (double)s + (double)e; }
+
+// split state of cell `id`: (h0, l0, h1, l1) [, (h2, l2, 0, 0)]
+template <int DIM>
+__device__ __forceinline__ void ld_split(const float4* __restrict__ p, int32_t id, float (&h)[DIM],
+                                         float (&l)[DIM]) {
+  const float4 a = __ldg(p + (int64_t)id * split4(DIM));
+  h[0] = a.x;
+  l[0] = a.y;
+  h[1] = a.z;
+  l[1] = a.w;
+  if constexpr (DIM == 3) {
+    const float4 b = __ldg(p + (int64_t)id * 2 + 1);
+    h[2] = b.x;
+    l[2] = b.y;
+  }
+}
+
+__device__ __forceinline__ void split_value(double a, float& h, float& l) {
+  h = __double2float_rn(a);
+  l = __double2float_rn(a - (double)h);  // a - h is exact in FP64
+}
+
+// n cells of a state read with stride ws -> split pairs
+template <int DIM>
+__global__ void k_split(int64_t n, int64_t ws, const double* __restrict__ u, float4* __restrict__ su) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float h[3] = {0.f, 0.f, 0.f}, l[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int j = 0; j < DIM; ++j) split_value(u[j * ws + i], h[j], l[j]);
+  su[i * split4(DIM)] = make_float4(h[0], l[0], h[1], l[1]);
+  if constexpr (DIM == 3) su[i * 2 + 1] = make_float4(h[2], l[2], 0.f, 0.f);
+}
+
+__global__ void k_coef_format(double* __restrict__ a, int64_t n, int to_df) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (to_df) {
+      float h, l;
+      split_value(a[i], h, l);
+      const unsigned long long bits =
+          ((unsigned long long)__float_as_uint(l) << 32) | (unsigned long long)__float_as_uint(h);
+      a[i] = __longlong_as_double((long long)bits);
+    } else {
+      const float2 p = reinterpret_cast<const float2*>(a)[i];
+      a[i] = ff_value(p.x, p.y);
+    }
+  }
+}
+
+void launch_coef_format(double* a, int64_t n, int to_df, cudaStream_t st) {
+  if (n <= 0) return;
+  const unsigned g = (unsigned)std::min<int64_t>((n + 255) / 256, 152 * 64);
+  k_coef_format<<<g, 256, 0, st>>>(a, n, to_df);
+}
+
+// stabilisation extrapolation of the state w (split sw), one thread per
+// (cell, local face): out[(cell * NLF + lf) * DIM + j] = w_P + sum_N e_N w_N
+template <int DIM, int NLF>
+__global__ void __launch_bounds__(32 * NLF)
+    k_ustar_df(DevMesh m, const float4* __restrict__ sw, const double* __restrict__ w,
+               double* __restrict__ out) {
+  const int64_t tile = blockIdx.x;
+  const int it = threadIdx.x;  // ci * NLF + lf
+  const int ci = it / NLF;
+  const int64_t cell = tile * kTile + ci;
+  const int32_t* __restrict__ st = m.cst + tile * m.S * kTile + ci;
+  const float2* __restrict__ ex =
+      reinterpret_cast<const float2*>(m.cex) + tile * (int64_t)m.S * kTile * NLF + it;
+  float s[DIM], e[DIM];
+#pragma unroll
+  for (int j = 0; j < DIM; ++j) s[j] = e[j] = 0.f;
+#pragma unroll 4
+  for (int n = 0; n < m.S; ++n) {
+    const int32_t id = __ldg(st + n * kTile);
+    const float2 c = __ldg(ex + (int64_t)n * kTile * NLF);
+    float h[DIM], l[DIM];
+    ld_split<DIM>(sw, id, h, l);
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) ff_mac(c.x, c.y, h[j], l[j], s[j], e[j]);
+  }
+  if (cell < m.nc) {
+    const int64_t ws = m.wst;
+    const int64_t o = (cell * NLF + (it % NLF)) * DIM;
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) out[o + j] = w[j * ws + cell] + ff_value(s[j], e[j]);
+  }
+}
+
+// component i of the mirror (I - 2 n n) x of the extrapolated value x of a
+// symmetry face (the value beyond the face, as k_sym_other)
+template <int DIM>
+__device__ __forceinline__ double mirror_i(const double* x, const double* n, int i) {
+  double un = 0.0;
+#pragma unroll
+  for (int j = 0; j < DIM; ++j) un += n[j] * x[j];
+  return x[i] - 2.0 * un * n[i];
+}
+
+// face fluxes, kFaceBlock faces per block (block b: tile b / 2, half b % 2),
+// blockDim = kFaceBlock * R, the gradient rows in double-float; sw is the
+// split state contracted (u, or v in the Jv modes) and ws its extrapolated
+// values
+template <int DIM, int LAW, int MODE>
+__global__ void __launch_bounds__(DIM == 3 ? kFaceBlock * 27 : kFaceBlock * 8,
+                                 DIM == 3 ? (LAW == HOFV_LAW_LINEAR ? 3 : 2) : (LAW == HOFV_LAW_LINEAR ? 12 : 8))
+    k_flux_df(DevMesh m, Material mt, const float4* __restrict__ sw, const double* __restrict__ ws,
+              const double* __restrict__ ubq, const double* __restrict__ ubf,
+              const double* __restrict__ d_eps, double* __restrict__ flux) {
+  extern __shared__ double sm[];
+  const int R = m.R, Q = m.Q, S = m.S;
+  double* Gs = sm;                          // [16][R][DIM] gradient fed to the law
+  double* Ts = sm + kFaceBlock * R * DIM;   // [16][Q][DIM]
+  const int64_t tile = blockIdx.x >> 1;
+  const int fb = (blockIdx.x & 1) * kFaceBlock;  // first face of the block within its tile
+  const int64_t f0 = tile * kTile + fb;
+  const int it = threadIdx.x;
+  const double eps = MODE == kDfJv ? __ldg(d_eps) : 0.0;
+  // (1) gradient rows: thread (fi, r) accumulates sum_N c_{r,N} w_N
+  {
+    const int fi = it / R, r = it % R;
+    const int64_t f = f0 + fi;
+    const int32_t* __restrict__ st = m.fst + tile * S * kTile + fb + fi;
+    const float2* __restrict__ co =
+        reinterpret_cast<const float2*>(m.fco) + tile * (int64_t)S * kTile * R + fb * R + it;
+    float s[DIM], e[DIM];
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) s[j] = e[j] = 0.f;
+#pragma unroll 4
+    for (int n = 0; n < S; ++n) {
+      const int32_t id = __ldg(st + n * kTile);
+      const float2 c = __ldg(co + (int64_t)n * kTile * R);
+      float h[DIM], l[DIM];
+      ld_split<DIM>(sw, id, h, l);
+#pragma unroll
+      for (int j = 0; j < DIM; ++j) ff_mac(c.x, c.y, h[j], l[j], s[j], e[j]);
+    }
+    double g[DIM];
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) g[j] = ff_value(s[j], e[j]);
+    if (MODE == kDfResidual || MODE == kDfFill) {
+      if (f >= m.nfi && f < m.nfid) {  // ghost node of a displacement face (prescribed data)
+        const int64_t fd = f - m.nfi;
+        const double cg = m.gco[fd * R + r];
+        const int q = r / DIM;
+#pragma unroll
+        for (int j = 0; j < DIM; ++j) g[j] = fma(cg, ubq[(fd * Q + q) * DIM + j], g[j]);
+      }
+    }
+    const int64_t row = (f0 * R + it) * DIM;  // == (f * R + r) * DIM
+    if (MODE == kDfFill) {
+#pragma unroll
+      for (int j = 0; j < DIM; ++j) m.gcache[row + j] = g[j];
+    }
+    if (MODE == kDfJv) {  // grad (u + eps v) = grad u + eps grad v
+#pragma unroll
+      for (int j = 0; j < DIM; ++j) g[j] = fma(eps, g[j], m.gcache[row + j]);
+    }
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) Gs[it * DIM + j] = g[j];
+  }
+  __syncthreads();
+  // (2) law and traction at each Gauss point
+  if (it < kFaceBlock * Q) {
+    const int fi = it / Q, q = it % Q;
+    const int64_t f = f0 + fi;
+    double t[DIM];
+    if (f < m.nfid) {
+      double a[3];
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) a[k] = m.aq[(f * Q + q) * 3 + k];
+      double G[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+#pragma unroll
+      for (int i = 0; i < DIM; ++i)
+#pragma unroll
+        for (int j = 0; j < DIM; ++j) G[i][j] = Gs[(fi * R + q * DIM + i) * DIM + j];
+      traction<DIM, LAW>(G, a, mt, t);
+    } else {
+#pragma unroll
+      for (int i = 0; i < DIM; ++i) t[i] = 0.0;
+    }
+    const int64_t o = (f * Q + q) * DIM;
+    if (MODE == kDfFill) {
+#pragma unroll
+      for (int i = 0; i < DIM; ++i) m.tcache[o + i] = t[i];
+    }
+    if (MODE == kDfJv) {
+#pragma unroll
+      for (int i = 0; i < DIM; ++i) t[i] -= m.tcache[o + i];
+    }
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) Ts[(fi * Q + q) * DIM + i] = t[i];
+  }
+  if (MODE == kDfFill) return;
+  __syncthreads();
+  // (3) quadrature over the face + alpha stabilisation
+  if (it < kFaceBlock * DIM) {
+    const int fi = it / DIM, i = it % DIM;
+    const int64_t f = f0 + fi;
+    if (f < m.nfid) {
+      double s = 0.0;
+      for (int q = 0; q < Q; ++q) s += Ts[(fi * Q + q) * DIM + i];
+      const int32_t sp = m.fstar[2 * f], sn = m.fstar[2 * f + 1];
+      const bool sym = sn < 0 && f >= m.nfi + m.nfd;
+      const double up = ws[(int64_t)sp * DIM + i];
+      // beyond a displacement face: the prescribed value (the homogeneous and
+      // Jv modes differentiate it away)
+      const double other = sn >= 0 ? ws[(int64_t)sn * DIM + i]
+                           : sym   ? mirror_i<DIM>(ws + (int64_t)sp * DIM, m.nrm + 3 * f, i)
+                           : MODE == kDfResidual ? ubf[(f - m.nfi) * DIM + i]
+                                                 : 0.0;
+      // the stabilisation is linear: its difference at u + eps v and u is
+      // eps times its value at v
+      const double coef = mt.alpha * mt.kbar * m.fstab[f] * (MODE == kDfJv ? eps : 1.0);
+      flux[f * DIM + i] = fma(coef, other - up, s);
+    }
+  }
+}
+
+// contracted linear form, homogeneous part at v: sum_N T_N v_N plus the
+// stabilisation of v with zero prescribed values (symmetry faces mirror)
+template <int DIM>
+__global__ void __launch_bounds__(32 * DIM)
+    k_tflux_hom(DevMesh m, const double* __restrict__ tco, double alpha_kbar,
+                const double* __restrict__ v, const double* __restrict__ vstar,
+                double* __restrict__ flux) {
+  const int64_t tile = blockIdx.x;
+  const int it = threadIdx.x;  // fi * DIM + i
+  const int fi = it / DIM, i = it % DIM;
+  const int64_t f = tile * kTile + fi;
+  const int S = m.S;
+  const int64_t ws = m.wst;
+  const int32_t* __restrict__ st = m.fst + tile * S * kTile + fi;
+  const double* __restrict__ tc = tco + tile * (int64_t)S * kTile * DIM * DIM + it * DIM;
+  double acc = 0.0;
+#pragma unroll 4
+  for (int n = 0; n < S; ++n) {
+    const int32_t id = __ldg(st + n * kTile);
+    const double* t = tc + (int64_t)n * kTile * DIM * DIM;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) acc = fma(__ldg(t + k), __ldg(v + k * ws + id), acc);
+  }
+  if (f < m.nfid) {
+    const int32_t sp = m.fstar[2 * f], sn = m.fstar[2 * f + 1];
+    const bool sym = sn < 0 && f >= m.nfi + m.nfd;
+    const double up = vstar[(int64_t)sp * DIM + i];
+    const double other = sn >= 0 ? vstar[(int64_t)sn * DIM + i]
+                         : sym   ? mirror_i<DIM>(vstar + (int64_t)sp * DIM, m.nrm + 3 * f, i)
+                                 : 0.0;
+    flux[f * DIM + i] = fma(alpha_kbar * m.fstab[f], other - up, acc);
+  }
+}
+
+// Jv assembly from face-flux differences: out = sum_f +-dflux_f / eps, plus
+// the inertia term of v (linear, so its difference quotient is exact)
+template <int DIM, int NLF>
+__global__ void k_cell_diff(DevMesh m, const double* __restrict__ flux,
+                            const double* __restrict__ d_eps, double* __restrict__ out) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= m.nc) return;
+  double r[DIM];
+#pragma unroll
+  for (int j = 0; j < DIM; ++j) r[j] = 0.0;
+#pragma unroll
+  for (int lf = 0; lf < NLF; ++lf) {
+    const int32_t code = m.cface[c * NLF + lf];
+    if (code == 0) continue;
+    const int64_t f = (code > 0 ? code : -code) - 1;
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) {
+      const double v = flux[f * DIM + j];
+      r[j] = code > 0 ? r[j] + v : r[j] - v;
+    }
+  }
+  const double ie = 1.0 / d_eps[0];
+#pragma unroll
+  for (int j = 0; j < DIM; ++j)
+    out[j * m.nc + c] = m.mscale ? fma(r[j], ie, m.inert[j * m.nc + c]) : r[j] * ie;
+}
+
+template <int DIM, typename F>
+static void by_faces_per_cell(const DevMesh& m, F&& launch) {
+  if (m.nlf == DIM + 1)
+    launch(std::integral_constant<int, DIM + 1>{});
+  else if (m.nlf == 2 * DIM)
+    launch(std::integral_constant<int, 2 * DIM>{});
+  else if constexpr (DIM == 2)
+    launch(std::integral_constant<int, kPolyMaxSides>{});
+}
+
+template <int DIM>
+static void launch_ustar_df(const DevMesh& m, const float4* sw, const double* w, double* out,
+                            cudaStream_t st) {
+  by_faces_per_cell<DIM>(m, [&](auto nlf) {
+    constexpr int NLF = decltype(nlf)::value;
+    k_ustar_df<DIM, NLF><<<(unsigned)m.nctile, 32 * NLF, 0, st>>>(m, sw, w, out);
+  });
+}
+
+template <int DIM, int LAW, int MODE>
+static void launch_flux_df(const DevMesh& m, const Material& mat, const float4* sw,
+                           const double* ws, const double* ubq, const double* ubf,
+                           const double* d_eps, double* flux, cudaStream_t st) {
+  const size_t smem = sizeof(double) * kFaceBlock * (m.R * DIM + m.Q * DIM);
+  k_flux_df<DIM, LAW, MODE><<<(unsigned)(2 * m.nftile), kFaceBlock * m.R, smem, st>>>(
+      m, mat, sw, ws, ubq, ubf, d_eps, flux);
+}
+
+// the state (extended by the mirror nodes when the mesh has symmetry faces)
+// split into double-float pairs; returns the FP64 state the kernels read
+template <int DIM>
+static const double* split_state(const DevMesh& m, const double* u, double* ext, float4* su,
+                                 cudaStream_t st) {
+  const unsigned g = (unsigned)((m.wst + 255) / 256);
+  if (m.ng > 0) {
+    k_extend<DIM><<<g, 256, 0, st>>>(m, u, ext);
+    u = ext;
+  }
+  k_split<DIM><<<g, 256, 0, st>>>(m.wst, m.wst, u, su);
+  return u;
+}
+
+template <int DIM, int LAW>
+static void residual_impl_df(const DevMesh& m, const Material& mat, const double* w,
+                             const double* d_eps, const double* R0, double* out, double* ustar,
+                             double* flux, const double* ubq, const double* ubf, const double* src,
+                             cudaStream_t st, cudaEvent_t* ev) {
+  if (ev) cudaEventRecord(ev[0], st);
+  w = split_state<DIM>(m, w, m.wext, m.su, st);
+  launch_ustar_df<DIM>(m, m.su, w, ustar, st);
+  if (ev) cudaEventRecord(ev[1], st);
+  if (m.nftile > 0) {
+    if (LAW == HOFV_LAW_LINEAR && m.tco) {
+      if (m.nfy > 0) k_sym_other<DIM><<<(unsigned)((m.nfy + 127) / 128), 128, 0, st>>>(m, ustar);
+      k_tflux<DIM><<<(unsigned)m.nftile, 32 * DIM, 0, st>>>(m, m.tco, mat.alpha * mat.kbar, w,
+                                                            ustar, ubf, flux);
+    } else {
+      launch_flux_df<DIM, LAW, kDfResidual>(m, mat, m.su, ustar, ubq, ubf, nullptr, flux, st);
+    }
+  }
+  if (ev) cudaEventRecord(ev[2], st);
+  if (m.mscale)
+    k_cell_avg<DIM, true><<<(unsigned)((m.nc + 127) / 128), 128, 0, st>>>(m, w, m.wst, m.inert);
+  const unsigned cgrid = (unsigned)((m.nc + 255) / 256);
+  by_faces_per_cell<DIM>(m, [&](auto nlf) {
+    constexpr int NLF = decltype(nlf)::value;
+    k_cell<DIM, NLF><<<cgrid, 256, 0, st>>>(m, flux, src, R0, d_eps, out);
+  });
+  if (ev) cudaEventRecord(ev[3], st);
+}
+
+template <int DIM, int LAW>
+static void jv_impl_df(const DevMesh& m, const Material& mat, const double* v,
+                       const double* d_eps, double* out, double* flux, cudaStream_t st) {
+  v = split_state<DIM>(m, v, m.vext, m.sv, st);
+  launch_ustar_df<DIM>(m, m.sv, v, m.ustar_v, st);
+  if (m.nftile > 0) {
+    if (LAW == HOFV_LAW_LINEAR && m.tco)
+      k_tflux_hom<DIM><<<(unsigned)m.nftile, 32 * DIM, 0, st>>>(m, m.tco, mat.alpha * mat.kbar, v,
+                                                                m.ustar_v, flux);
+    else if (LAW == HOFV_LAW_LINEAR)
+      launch_flux_df<DIM, LAW, kDfHomog>(m, mat, m.sv, m.ustar_v, nullptr, nullptr, nullptr, flux,
+                                         st);
+    else
+      launch_flux_df<DIM, LAW, kDfJv>(m, mat, m.sv, m.ustar_v, nullptr, nullptr, d_eps, flux, st);
+  }
+  if (m.mscale)
+    k_cell_avg<DIM, true><<<(unsigned)((m.nc + 127) / 128), 128, 0, st>>>(m, v, m.wst, m.inert);
+  const unsigned cgrid = (unsigned)((m.nc + 255) / 256);
+  by_faces_per_cell<DIM>(m, [&](auto nlf) {
+    constexpr int NLF = decltype(nlf)::value;
+    if (LAW == HOFV_LAW_LINEAR)  // the homogeneous residual: J v itself
+      k_cell<DIM, NLF><<<cgrid, 256, 0, st>>>(m, flux, nullptr, nullptr, nullptr, out);
+    else
+      k_cell_diff<DIM, NLF><<<cgrid, 256, 0, st>>>(m, flux, d_eps, out);
+  });
+}
+
+void launch_residual_df(const DevMesh& m, const Material& mat, const double* w,
+                        const double* d_eps, const double* R0, double* out, double* ustar,
+                        double* flux, const double* ubq, const double* ubf, const double* src,
+                        cudaStream_t st, cudaEvent_t* ev) {
+  if (m.dim == 2) {
+    if (mat.law == HOFV_LAW_LINEAR)
+      residual_impl_df<2, 0>(m, mat, w, d_eps, R0, out, ustar, flux, ubq, ubf, src, st, ev);
+    else
+      residual_impl_df<2, 1>(m, mat, w, d_eps, R0, out, ustar, flux, ubq, ubf, src, st, ev);
+  } else {
+    if (mat.law == HOFV_LAW_LINEAR)
+      residual_impl_df<3, 0>(m, mat, w, d_eps, R0, out, ustar, flux, ubq, ubf, src, st, ev);
+    else
+      residual_impl_df<3, 1>(m, mat, w, d_eps, R0, out, ustar, flux, ubq, ubf, src, st, ev);
+  }
+}
+
+void launch_jv_df(const DevMesh& m, const Material& mat, const double* v, const double* d_eps,
+                  double* out, double* flux, cudaStream_t st) {
+  if (m.dim == 2) {
+    if (mat.law == HOFV_LAW_LINEAR)
+      jv_impl_df<2, 0>(m, mat, v, d_eps, out, flux, st);
+    else
+      jv_impl_df<2, 1>(m, mat, v, d_eps, out, flux, st);
+  } else {
+    if (mat.law == HOFV_LAW_LINEAR)
+      jv_impl_df<3, 0>(m, mat, v, d_eps, out, flux, st);
+    else
+      jv_impl_df<3, 1>(m, mat, v, d_eps, out, flux, st);
+  }
+}
+
+void launch_jv_cache_fill(const DevMesh& m, const Material& mat, const double* u,
+                          const double* ubq, cudaStream_t st) {
+  if (m.nftile == 0) return;
+  if (m.dim == 2) {
+    const double* w = split_state<2>(m, u, m.wext, m.su, st);
+    (void)w;
+    launch_flux_df<2, 1, kDfFill>(m, mat, m.su, nullptr, ubq, nullptr, nullptr, nullptr, st);
+  } else {
+    const double* w = split_state<3>(m, u, m.wext, m.su, st);
+    (void)w;
+    launch_flux_df<3, 1, kDfFill>(m, mat, m.su, nullptr, ubq, nullptr, nullptr, nullptr, st);
+  }
+}
+
+// the face kernels of 3-D p = 3 may need more than the default 48 KB of
+// dynamic shared memory; set once per process, before any capture
+int setup_df_kernels() {
+  static int rc = -1;
+  if (rc >= 0) return rc;
+  const int bytes = 96 * 1024;
+  cudaError_t e = cudaSuccess;
+  auto set = [&](const void* k) {
+    const cudaError_t r = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (r != cudaSuccess) e = r;
+  };
+  set((const void*)k_flux_df<2, 0, kDfResidual>);
+  set((const void*)k_flux_df<2, 1, kDfResidual>);
+  set((const void*)k_flux_df<3, 0, kDfResidual>);
+  set((const void*)k_flux_df<3, 1, kDfResidual>);
+  set((const void*)k_flux_df<2, 0, kDfHomog>);
+  set((const void*)k_flux_df<3, 0, kDfHomog>);
+  set((const void*)k_flux_df<2, 1, kDfFill>);
+  set((const void*)k_flux_df<3, 1, kDfFill>);
+  set((const void*)k_flux_df<2, 1, kDfJv>);
+  set((const void*)k_flux_df<3, 1, kDfJv>);
+  rc = e == cudaSuccess ? 0 : (int)e;
+  return rc;
 }
 
 }  // namespace hofv

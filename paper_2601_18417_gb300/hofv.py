@@ -20,6 +20,7 @@ OK, WNOTCONV = 0, 1
 EINVAL, ENOMEM, ECUDA, EILLCOND, ENAN, ENOTSUP, ESTATE = -1, -2, -3, -4, -5, -6, -7
 LAW_LINEAR, LAW_NEOHOOKEAN = 0, 1
 PC_NONE, PC_AJ64, PC_AJ32, PC_GNN, PC_AJMG, PC_NEJ = -1, 0, 1, 2, 3, 4
+PREC_FP64, PREC_DF64 = 0, 1
 CELL_TENSOR, CELL_SIMPLEX = 0, 1
 POLY_SLOTS = 8  # face slots of a polygon cell
 PTS_CELL_CENTROID, PTS_DISP_QP, PTS_DISP_CENTRE, PTS_TRAC_QP, PTS_CELL_QP = 0, 1, 2, 3, 4
@@ -105,6 +106,8 @@ SIGNATURES = {
     "hofv_residual_noalloc": (_I, [_P, _P, _P]),
     "hofv_force_scale": (_I, [_P, _P, C.POINTER(_D)]),
     "hofv_set_contraction": (_I, [_P, _I]),
+    "hofv_set_precision": (_I, [_P, _I]),
+    "hofv_get_precision": (_I, [_P]),
     "hofv_selftest_barrier": (_I, [_P, C.POINTER(C.c_int32)]),
     "hofv_nej_apply": (_I, [_P, _P, _P]),
     "hofv_set_inertia": (_I, [_P, C.c_double, C.c_double, _I]),
@@ -279,6 +282,17 @@ class Context:
 
     def set_contraction(self, on=True):
         return self._check(self._L.hofv_set_contraction(self.h, int(bool(on))))
+
+    def set_precision(self, prec):
+        """HOFV_PREC_FP64 or HOFV_PREC_DF64 for the gradient contraction."""
+        return self._check(self._L.hofv_set_precision(self.h, int(prec)))
+
+    @property
+    def precision(self):
+        rc = self._L.hofv_get_precision(self.h)
+        if rc < 0:
+            self._check(rc)
+        return rc
 
     def set_bc(self, u_bq=None, u_bf=None, t_bq=None, body=None):
         args = [_dev(t) for t in (u_bq, u_bf, t_bq, body)]

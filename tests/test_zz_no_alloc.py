@@ -19,19 +19,38 @@ from tests import helpers as H
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("dim,n,p,q1,jit,law", [(2, 37, 3, 3, 0.25, 0), (3, 9, 2, 2, 0.2, 1)])
-def test_noalloc_residual_matches_residual_twice(dim, n, p, q1, jit, law):
+CASES = {
+    # name: (dim, n, p, q1, jitter, law, mesh kind, boundary tags)
+    "quad-p3": (2, 37, 3, 3, 0.25, 0, "tensor", "mms"),
+    "hex-p2-nh": (3, 9, 2, 2, 0.2, 1, "tensor", "block"),
+    "triangles-p3": (2, 14, 3, 3, 0.15, 0, "simplex", "mms"),
+    "tetrahedra-p2": (3, 5, 2, 2, 0.1, 0, "simplex", "mms"),
+    "polygons-p3": (2, 14, 3, 3, 0.15, 0, "polygon", "mms"),
+    "quad-p3-symmetry": (2, 24, 3, 3, 0.2, 0, "tensor", "symmetry"),
+}
+
+
+@pytest.mark.parametrize("prec", [hofv.PREC_FP64, hofv.PREC_DF64])
+@pytest.mark.parametrize("name", list(CASES))
+def test_noalloc_residual_matches_residual_twice(name, prec):
     import torch
-    field = I.Mixed2D() if dim == 2 else None
-    tags = I.side_tags("mms" if dim == 2 else "block", dim)
+    dim, n, p, q1, jit, law, kind, tagkind = CASES[name]
+    field = None if tagkind == "block" else (I.Mixed2D() if dim == 2 else I.Trig3D())
+    if tagkind == "symmetry":  # x- and y- sides are planes of symmetry
+        tags = np.zeros(2 * dim, np.int32)
+        tags[0] = tags[2] = 2
+    else:
+        tags = I.side_tags(tagkind, dim)
     mu, lam = (1.0, 1.5) if law == 0 else (1e6, 4e6)
     pb = H.make_problem(dim, n, p, q1, jitter=jit, seed=9, field=field, tags=tags, law=law,
-                        mu=mu, lam=lam)
+                        mu=mu, lam=lam, kind=kind)
     ctx = H.gpu_context(pb)
+    ctx.set_precision(prec)
     L = hofv.load()
     rng = np.random.default_rng(2)
+    scale = max(np.abs(pb.u_exact).max(), 1e-3)
     for call in range(2):
-        u = pb.u_exact + 1e-3 * rng.standard_normal((dim, pb.orc.nc))
+        u = pb.u_exact + 1e-3 * scale * rng.standard_normal((dim, pb.orc.nc))
         if field is None:
             u = u + I.block_top_displacement(1, 10, dim)[:, None] * pb.orc.xc[:, dim - 1][None, :]
         ud = H.to_dev(u)
