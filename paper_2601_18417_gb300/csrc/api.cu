@@ -79,6 +79,7 @@ DevMesh dev_mesh(const hofv_ctx* c) {
   m.vext = c->d_vext;
   m.gcache = c->d_gcache;
   m.tcache = c->d_tcache;
+  m.kerr = c->d_bar ? c->d_bar + 3 : nullptr;
   return m;
 }
 
@@ -1602,6 +1603,11 @@ int check_pc_barrier(hofv_ctx* c) {
   if (err) {
     HOFV_CUDA(c, cudaMemset(c->d_bar, 0, 4 * sizeof(unsigned int)));
     return fail(c, HOFV_ECUDA, "approximate-Jacobian solve: grid barrier timed out");
+  }
+  HOFV_CUDA(c, cudaMemcpy(&err, c->d_bar + 3, sizeof(int), cudaMemcpyDeviceToHost));
+  if (err) {
+    HOFV_CUDA(c, cudaMemset(c->d_bar + 3, 0, sizeof(unsigned int)));
+    return fail(c, HOFV_ECUDA, "face kernel: a shared-memory copy did not complete in time");
   }
   return 0;
 }

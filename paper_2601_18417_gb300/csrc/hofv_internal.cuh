@@ -66,6 +66,7 @@ struct DevMesh {
   // gradient rows and Gauss-point tractions of every face at u
   double* gcache;         // [nftile * kTile][R][dim]
   double* tcache;         // [nftile * kTile][Q][dim]
+  unsigned int* kerr;     // set to 1 by a face kernel whose bounded wait ran out
 };
 
 // float4 slots per cell of a split state: (h0, l0, h1, l1) [, (h2, l2, 0, 0)]
@@ -280,7 +281,7 @@ void launch_jv_cache_fill(const DevMesh& m, const Material& mat, const double* u
 // back into doubles (exactly)
 void launch_coef_format(double* a, int64_t n, int to_df, cudaStream_t st);
 // raises the dynamic shared-memory limit of the double-float face kernels
-// (once per process); 0 or a cudaError_t
+// (once per process, at set-up); 0 or a cudaError_t
 int setup_df_kernels();
 void launch_source(const hofv_ctx* c, cudaStream_t st);
 void launch_build_tco(const DevMesh& m, double mu, double lam, double* tco, cudaStream_t st);

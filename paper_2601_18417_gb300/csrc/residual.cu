@@ -147,8 +147,10 @@ __device__ __forceinline__ void traction(const double (&G)[3][3], const double* 
     }
   } else {
     // neo-Hookean, eq. (neoHook), first Piola-Kirchhoff P = J sigma F^{-T}
-    // (eq. nanson).  With tau = J sigma = mu dev(bbar) + kappa/2 (J^2-1) I
-    // and F^{-T} = cof(F) / J:  P = tau cof(F) / J.
+    // (eq. nanson).  With B = F F^T, w = cof(F) a and r = J^{-1/3}:
+    //   J sigma = mu J^{-2/3} (B - tr(B)/3 I) + kappa/2 (J^2 - 1) I,
+    //   t = P a = J sigma w / J = alpha B w + beta w,
+    //   alpha = mu r^5,  beta = kappa/2 (J^2 - 1) r^3 - alpha tr(B) / 3.
     double F[3][3];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
@@ -165,40 +167,31 @@ __device__ __forceinline__ void traction(const double (&G)[3][3], const double* 
     C[2][1] = F[0][2] * F[1][0] - F[0][0] * F[1][2];
     C[2][2] = F[0][0] * F[1][1] - F[0][1] * F[1][0];
     const double J = F[0][0] * C[0][0] + F[0][1] * C[0][1] + F[0][2] * C[0][2];
-    // J^{-2/3}; not defined for J <= 0 (an inverted element): NaN, so the
+    // J^{-1/3}; not defined for J <= 0 (an inverted element): NaN, so the
     // caller's finiteness checks reject the state
-    const double jm23 = J > 0.0 ? rcbrt(J * J) : __longlong_as_double(0x7ff8000000000000LL);
-    double b[3][3];
+    const double r = J > 0.0 ? rcbrt(J) : __longlong_as_double(0x7ff8000000000000LL);
+    const double r3 = r * r * r;
+    const double alpha = mt.mu * (r * r) * r3;
+    double B[3][3];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
-      for (int j = i; j < 3; ++j) {
-        const double s = F[i][0] * F[j][0] + F[i][1] * F[j][1] + F[i][2] * F[j][2];
-        b[i][j] = b[j][i] = jm23 * s;
-      }
-    const double tb = (b[0][0] + b[1][1] + b[2][2]) * (1.0 / 3.0);
-    const double pvol = 0.5 * mt.kappa * (J * J - 1.0);
-    double tau[3][3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int j = 0; j < 3; ++j) tau[i][j] = mt.mu * (b[i][j] - (i == j ? tb : 0.0)) + (i == j ? pvol : 0.0);
-    // t = P a = tau (cof(F) a) / J
-    double ca[3];
+      for (int j = i; j < 3; ++j)
+        B[i][j] = B[j][i] = F[i][0] * F[j][0] + F[i][1] * F[j][1] + F[i][2] * F[j][2];
+    const double beta =
+        0.5 * mt.kappa * fma(J, J, -1.0) * r3 - alpha * (B[0][0] + B[1][1] + B[2][2]) * (1.0 / 3.0);
+    double w[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      double s = 0.0;
+      double sk = 0.0;
 #pragma unroll
-      for (int l = 0; l < DIM; ++l) s = fma(C[k][l], a[l], s);
-      ca[k] = s;
+      for (int l = 0; l < DIM; ++l) sk = fma(C[k][l], a[l], sk);
+      w[k] = sk;
     }
-    const double iJ = 1.0 / J;
 #pragma unroll
     for (int i = 0; i < DIM; ++i) {
-      double s = 0.0;
-#pragma unroll
-      for (int k = 0; k < 3; ++k) s = fma(tau[i][k], ca[k], s);
-      t[i] = s * iJ;
+      const double bw = B[i][0] * w[0] + B[i][1] * w[1] + B[i][2] * w[2];
+      t[i] = fma(alpha, bw, beta * w[i]);
     }
   }
 }
@@ -686,13 +679,12 @@ void launch_tflux(const DevMesh& m, const double* tco, double alpha_kbar, const 
 // grad u in FP64, with grad u and its tractions taken from a cache filled
 // once per linearisation point, so the rounding of grad u cancels exactly.
 //
-// The face kernel runs half a tile (16 faces) per block so that two or more
-// blocks share an SM and the FP32 contraction of one overlaps the FP64 law
-// of another.
+// The face kernel keeps several coefficient loads in flight per thread (a
+// register ring) and, in 3-D, runs half a tile per block so that two blocks
+// share an SM and the FP32 contraction of one overlaps the FP64 law of the
+// other.
 // =====================================================================
 namespace hofv {
-
-constexpr int kFaceBlock = 16;  // faces per block of the double-float face kernel
 
 // modes of the double-float face kernel
 constexpr int kDfResidual = 0;  // flux of u (split a, extrapolated values ua)
@@ -812,44 +804,121 @@ __device__ __forceinline__ double mirror_i(const double* x, const double* n, int
   return x[i] - 2.0 * un * n[i];
 }
 
-// face fluxes, kFaceBlock faces per block (block b: tile b / 2, half b % 2),
-// blockDim = kFaceBlock * R, the gradient rows in double-float; sw is the
-// split state contracted (u, or v in the Jv modes) and ws its extrapolated
-// values
-template <int DIM, int LAW, int MODE>
-__global__ void __launch_bounds__(DIM == 3 ? kFaceBlock * 27 : kFaceBlock * 8,
-                                 DIM == 3 ? (LAW == HOFV_LAW_LINEAR ? 3 : 2) : (LAW == HOFV_LAW_LINEAR ? 12 : 8))
+// 16-byte asynchronous copy global -> shared (sm_80 and later), for gathers
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                   static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_all;" ::: "memory");
+}
+
+// Face fluxes, double-float gradient rows.  QD Gauss points per face
+// (R = QD * DIM rows), FPB faces per block (BPT = 32 / FPB blocks per tile),
+// blockDim = FPB * R; sw is the split state contracted (u, or v in the Jv
+// modes) and ws its extrapolated values.
+//
+// The block first gathers the split values of all its faces' stencil cells
+// into shared memory (16-byte asynchronous copies, [S][FPB] entries), so
+// that the contraction reads them from shared memory (the R threads of a
+// face share each entry).  Each thread then streams its coefficient row
+// through a ring of RING registers: the coefficient of slot n + RING is
+// requested when slot n is consumed, keeping RING coalesced 8-byte loads in
+// flight per thread; with R a compile-time constant every ring offset is an
+// immediate.  In 3-D a block takes half a tile so that several blocks share
+// an SM and the FP32 contraction of one overlaps the FP64 law of another.
+template <int DIM>
+struct DfShape {
+  static constexpr int FPB = DIM == 3 ? 16 : 32;   // faces per block
+  static constexpr int RING = DIM == 3 ? 8 : 4;    // coefficient loads in flight per thread
+};
+
+// dynamic shared memory: the gathered cell values, reused after the
+// contraction for the gradients and tractions of phases 2 and 3
+template <int DIM>
+static size_t df_smem_bytes(int S, int R, int Q) {
+  constexpr int FPB = DfShape<DIM>::FPB;
+  const size_t gath = (size_t)S * FPB * split4(DIM) * 16;
+  const size_t law = (size_t)FPB * (R * DIM + Q * DIM) * sizeof(double);
+  return gath > law ? gath : law;
+}
+
+template <int DIM, int LAW, int MODE, int QD>
+__global__ void __launch_bounds__(DfShape<DIM>::FPB * QD * DIM, DIM == 3 ? 2 : 6)
     k_flux_df(DevMesh m, Material mt, const float4* __restrict__ sw, const double* __restrict__ ws,
               const double* __restrict__ ubq, const double* __restrict__ ubf,
               const double* __restrict__ d_eps, double* __restrict__ flux) {
-  extern __shared__ double sm[];
-  const int R = m.R, Q = m.Q, S = m.S;
-  double* Gs = sm;                          // [16][R][DIM] gradient fed to the law
-  double* Ts = sm + kFaceBlock * R * DIM;   // [16][Q][DIM]
-  const int64_t tile = blockIdx.x >> 1;
-  const int fb = (blockIdx.x & 1) * kFaceBlock;  // first face of the block within its tile
+  constexpr int FPB = DfShape<DIM>::FPB, BPT = kTile / FPB, Q = QD, R = QD * DIM;
+  constexpr int kRing = DfShape<DIM>::RING, SP4 = split4(DIM);
+  constexpr int CS = kTile * R;  // coefficient stride between stencil slots
+  extern __shared__ __align__(16) double sm[];
+  const int S = m.S;
+  float4* us = reinterpret_cast<float4*>(sm);  // [S][FPB][SP4] gathered split values
+  double* Gs = sm;                              // [FPB][R][DIM] after the contraction
+  double* Ts = sm + FPB * R * DIM;              // [FPB][Q][DIM]
+  const int64_t tile = blockIdx.x / BPT;
+  const int fb = (blockIdx.x % BPT) * FPB;  // first face of the block within its tile
   const int64_t f0 = tile * kTile + fb;
   const int it = threadIdx.x;
   const double eps = MODE == kDfJv ? __ldg(d_eps) : 0.0;
-  // (1) gradient rows: thread (fi, r) accumulates sum_N c_{r,N} w_N
+  const int fi = it / R, r = it % R;
+  const int64_t f = f0 + fi;
+  const float2* __restrict__ co =
+      reinterpret_cast<const float2*>(m.fco) + tile * (int64_t)S * CS + fb * R + it;
+  // the first coefficients of the ring, then the gather of the cell values
+  float2 cq[kRing];
+#pragma unroll
+  for (int d = 0; d < kRing; ++d) cq[d] = d < S ? __ldg(co + d * CS) : make_float2(0.f, 0.f);
   {
-    const int fi = it / R, r = it % R;
-    const int64_t f = f0 + fi;
-    const int32_t* __restrict__ st = m.fst + tile * S * kTile + fb + fi;
-    const float2* __restrict__ co =
-        reinterpret_cast<const float2*>(m.fco) + tile * (int64_t)S * kTile * R + fb * R + it;
-    float s[DIM], e[DIM];
+    const int32_t* __restrict__ st = m.fst + tile * (int64_t)S * kTile + fb;
+    for (int t = it; t < S * FPB; t += FPB * R) {
+      const int n = t / FPB, fj = t % FPB;
+      const int32_t id = __ldg(st + n * kTile + fj);
 #pragma unroll
-    for (int j = 0; j < DIM; ++j) s[j] = e[j] = 0.f;
-#pragma unroll 4
-    for (int n = 0; n < S; ++n) {
-      const int32_t id = __ldg(st + n * kTile);
-      const float2 c = __ldg(co + (int64_t)n * kTile * R);
-      float h[DIM], l[DIM];
-      ld_split<DIM>(sw, id, h, l);
-#pragma unroll
-      for (int j = 0; j < DIM; ++j) ff_mac(c.x, c.y, h[j], l[j], s[j], e[j]);
+      for (int h = 0; h < SP4; ++h) cp_async16(us + t * SP4 + h, sw + (int64_t)id * SP4 + h);
     }
+    cp_async_wait_all();
+  }
+  __syncthreads();
+  // (1) gradient rows: thread (fi, r) accumulates sum_N c_{r,N} w_N
+  float s[DIM], e[DIM];
+#pragma unroll
+  for (int j = 0; j < DIM; ++j) s[j] = e[j] = 0.f;
+  const float4* __restrict__ uf = us + fi * SP4;
+  auto mac_slot = [&](int n, float2 c) {
+    const float4 a = uf[n * FPB * SP4];
+    ff_mac(c.x, c.y, a.x, a.y, s[0], e[0]);
+    ff_mac(c.x, c.y, a.z, a.w, s[1], e[1]);
+    if constexpr (DIM == 3) {
+      const float4 b = uf[n * FPB * SP4 + 1];
+      ff_mac(c.x, c.y, b.x, b.y, s[2], e[2]);
+    }
+  };
+  int n0 = 0;
+  // steady part: every request in range
+  for (; n0 + 2 * kRing <= S; n0 += kRing) {
+    const float2* cn = co + (n0 + kRing) * CS;
+#pragma unroll
+    for (int d = 0; d < kRing; ++d) {
+      const float2 c = cq[d];
+      cq[d] = __ldg(cn + d * CS);
+      mac_slot(n0 + d, c);
+    }
+  }
+  // the last kRing .. 2 kRing - 1 slots (fewer if S < kRing)
+#pragma unroll
+  for (int d = 0; d < 2 * kRing; ++d) {
+    const int n = n0 + d;
+    if (n < S) {
+      const float2 c = cq[d % kRing];
+      if (n + kRing < S) cq[d % kRing] = __ldg(co + (n + kRing) * CS);
+      mac_slot(n, c);
+    }
+  }
+  __syncthreads();  // the gathered values are overwritten by the gradients below
+  {
     double g[DIM];
 #pragma unroll
     for (int j = 0; j < DIM; ++j) g[j] = ff_value(s[j], e[j]);
@@ -876,25 +945,25 @@ __global__ void __launch_bounds__(DIM == 3 ? kFaceBlock * 27 : kFaceBlock * 8,
   }
   __syncthreads();
   // (2) law and traction at each Gauss point
-  if (it < kFaceBlock * Q) {
-    const int fi = it / Q, q = it % Q;
-    const int64_t f = f0 + fi;
+  if (it < FPB * Q) {
+    const int fj = it / Q, q = it % Q;
+    const int64_t fq = f0 + fj;
     double t[DIM];
-    if (f < m.nfid) {
+    if (fq < m.nfid) {
       double a[3];
 #pragma unroll
-      for (int k = 0; k < DIM; ++k) a[k] = m.aq[(f * Q + q) * 3 + k];
+      for (int k = 0; k < DIM; ++k) a[k] = m.aq[(fq * Q + q) * 3 + k];
       double G[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
 #pragma unroll
       for (int i = 0; i < DIM; ++i)
 #pragma unroll
-        for (int j = 0; j < DIM; ++j) G[i][j] = Gs[(fi * R + q * DIM + i) * DIM + j];
+        for (int j = 0; j < DIM; ++j) G[i][j] = Gs[(fj * R + q * DIM + i) * DIM + j];
       traction<DIM, LAW>(G, a, mt, t);
     } else {
 #pragma unroll
       for (int i = 0; i < DIM; ++i) t[i] = 0.0;
     }
-    const int64_t o = (f * Q + q) * DIM;
+    const int64_t o = (fq * Q + q) * DIM;
     if (MODE == kDfFill) {
 #pragma unroll
       for (int i = 0; i < DIM; ++i) m.tcache[o + i] = t[i];
@@ -904,30 +973,30 @@ __global__ void __launch_bounds__(DIM == 3 ? kFaceBlock * 27 : kFaceBlock * 8,
       for (int i = 0; i < DIM; ++i) t[i] -= m.tcache[o + i];
     }
 #pragma unroll
-    for (int i = 0; i < DIM; ++i) Ts[(fi * Q + q) * DIM + i] = t[i];
+    for (int i = 0; i < DIM; ++i) Ts[(fj * Q + q) * DIM + i] = t[i];
   }
   if (MODE == kDfFill) return;
   __syncthreads();
   // (3) quadrature over the face + alpha stabilisation
-  if (it < kFaceBlock * DIM) {
-    const int fi = it / DIM, i = it % DIM;
-    const int64_t f = f0 + fi;
-    if (f < m.nfid) {
-      double s = 0.0;
-      for (int q = 0; q < Q; ++q) s += Ts[(fi * Q + q) * DIM + i];
-      const int32_t sp = m.fstar[2 * f], sn = m.fstar[2 * f + 1];
-      const bool sym = sn < 0 && f >= m.nfi + m.nfd;
+  if (it < FPB * DIM) {
+    const int fj = it / DIM, i = it % DIM;
+    const int64_t ff = f0 + fj;
+    if (ff < m.nfid) {
+      double acc = 0.0;
+      for (int q = 0; q < Q; ++q) acc += Ts[(fj * Q + q) * DIM + i];
+      const int32_t sp = m.fstar[2 * ff], sn = m.fstar[2 * ff + 1];
+      const bool sym = sn < 0 && ff >= m.nfi + m.nfd;
       const double up = ws[(int64_t)sp * DIM + i];
       // beyond a displacement face: the prescribed value (the homogeneous and
       // Jv modes differentiate it away)
       const double other = sn >= 0 ? ws[(int64_t)sn * DIM + i]
-                           : sym   ? mirror_i<DIM>(ws + (int64_t)sp * DIM, m.nrm + 3 * f, i)
-                           : MODE == kDfResidual ? ubf[(f - m.nfi) * DIM + i]
+                           : sym   ? mirror_i<DIM>(ws + (int64_t)sp * DIM, m.nrm + 3 * ff, i)
+                           : MODE == kDfResidual ? ubf[(ff - m.nfi) * DIM + i]
                                                  : 0.0;
       // the stabilisation is linear: its difference at u + eps v and u is
       // eps times its value at v
-      const double coef = mt.alpha * mt.kbar * m.fstab[f] * (MODE == kDfJv ? eps : 1.0);
-      flux[f * DIM + i] = fma(coef, other - up, s);
+      const double coef = mt.alpha * mt.kbar * m.fstab[ff] * (MODE == kDfJv ? eps : 1.0);
+      flux[ff * DIM + i] = fma(coef, other - up, acc);
     }
   }
 }
@@ -1012,13 +1081,35 @@ static void launch_ustar_df(const DevMesh& m, const float4* sw, const double* w,
   });
 }
 
+template <int DIM, int LAW, int MODE, int QD>
+static void launch_flux_df_q(const DevMesh& m, const Material& mat, const float4* sw,
+                             const double* ws, const double* ubq, const double* ubf,
+                             const double* d_eps, double* flux, cudaStream_t st) {
+  using SH = DfShape<DIM>;
+  const size_t smem = df_smem_bytes<DIM>(m.S, QD * DIM, QD);
+  k_flux_df<DIM, LAW, MODE, QD><<<(unsigned)(m.nftile * (kTile / SH::FPB)), SH::FPB * QD * DIM,
+                                  smem, st>>>(m, mat, sw, ws, ubq, ubf, d_eps, flux);
+}
+
+// Gauss points per face: q^(d-1) for q = 1..4 in 2-D, 1..3 in 3-D
 template <int DIM, int LAW, int MODE>
 static void launch_flux_df(const DevMesh& m, const Material& mat, const float4* sw,
                            const double* ws, const double* ubq, const double* ubf,
                            const double* d_eps, double* flux, cudaStream_t st) {
-  const size_t smem = sizeof(double) * kFaceBlock * (m.R * DIM + m.Q * DIM);
-  k_flux_df<DIM, LAW, MODE><<<(unsigned)(2 * m.nftile), kFaceBlock * m.R, smem, st>>>(
-      m, mat, sw, ws, ubq, ubf, d_eps, flux);
+  if constexpr (DIM == 2) {
+    switch (m.Q) {
+      case 1: return launch_flux_df_q<2, LAW, MODE, 1>(m, mat, sw, ws, ubq, ubf, d_eps, flux, st);
+      case 2: return launch_flux_df_q<2, LAW, MODE, 2>(m, mat, sw, ws, ubq, ubf, d_eps, flux, st);
+      case 3: return launch_flux_df_q<2, LAW, MODE, 3>(m, mat, sw, ws, ubq, ubf, d_eps, flux, st);
+      default: return launch_flux_df_q<2, LAW, MODE, 4>(m, mat, sw, ws, ubq, ubf, d_eps, flux, st);
+    }
+  } else {
+    switch (m.Q) {
+      case 1: return launch_flux_df_q<3, LAW, MODE, 1>(m, mat, sw, ws, ubq, ubf, d_eps, flux, st);
+      case 4: return launch_flux_df_q<3, LAW, MODE, 4>(m, mat, sw, ws, ubq, ubf, d_eps, flux, st);
+      default: return launch_flux_df_q<3, LAW, MODE, 9>(m, mat, sw, ws, ubq, ubf, d_eps, flux, st);
+    }
+  }
 }
 
 // the state (extended by the mirror nodes when the mesh has symmetry faces)
@@ -1123,6 +1214,41 @@ void launch_jv_df(const DevMesh& m, const Material& mat, const double* v, const 
   }
 }
 
+// the face kernels' gathers exceed the default 48 KB of dynamic shared
+// memory for large stencils: raise the limit of every instantiation to what
+// kMaxS stencil cells need, once per process (set-up calls only, never
+// during stream capture)
+template <int DIM, int LAW, int MODE, int QD>
+static void raise_smem(cudaError_t& e) {
+  const cudaError_t r =
+      cudaFuncSetAttribute((const void*)k_flux_df<DIM, LAW, MODE, QD>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)df_smem_bytes<DIM>(kMaxS, QD * DIM, QD));
+  if (r != cudaSuccess) e = r;
+}
+template <int DIM, int QD>
+static void raise_smem_all(cudaError_t& e) {
+  raise_smem<DIM, 0, kDfResidual, QD>(e);
+  raise_smem<DIM, 1, kDfResidual, QD>(e);
+  raise_smem<DIM, 0, kDfHomog, QD>(e);
+  raise_smem<DIM, 1, kDfFill, QD>(e);
+  raise_smem<DIM, 1, kDfJv, QD>(e);
+}
+int setup_df_kernels() {
+  static int rc = -1;
+  if (rc >= 0) return rc;
+  cudaError_t e = cudaSuccess;
+  raise_smem_all<2, 1>(e);
+  raise_smem_all<2, 2>(e);
+  raise_smem_all<2, 3>(e);
+  raise_smem_all<2, 4>(e);
+  raise_smem_all<3, 1>(e);
+  raise_smem_all<3, 4>(e);
+  raise_smem_all<3, 9>(e);
+  rc = e == cudaSuccess ? 0 : (int)e;
+  return rc;
+}
+
 void launch_jv_cache_fill(const DevMesh& m, const Material& mat, const double* u,
                           const double* ubq, cudaStream_t st) {
   if (m.nftile == 0) return;
@@ -1135,31 +1261,6 @@ void launch_jv_cache_fill(const DevMesh& m, const Material& mat, const double* u
     (void)w;
     launch_flux_df<3, 1, kDfFill>(m, mat, m.su, nullptr, ubq, nullptr, nullptr, nullptr, st);
   }
-}
-
-// the face kernels of 3-D p = 3 may need more than the default 48 KB of
-// dynamic shared memory; set once per process, before any capture
-int setup_df_kernels() {
-  static int rc = -1;
-  if (rc >= 0) return rc;
-  const int bytes = 96 * 1024;
-  cudaError_t e = cudaSuccess;
-  auto set = [&](const void* k) {
-    const cudaError_t r = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (r != cudaSuccess) e = r;
-  };
-  set((const void*)k_flux_df<2, 0, kDfResidual>);
-  set((const void*)k_flux_df<2, 1, kDfResidual>);
-  set((const void*)k_flux_df<3, 0, kDfResidual>);
-  set((const void*)k_flux_df<3, 1, kDfResidual>);
-  set((const void*)k_flux_df<2, 0, kDfHomog>);
-  set((const void*)k_flux_df<3, 0, kDfHomog>);
-  set((const void*)k_flux_df<2, 1, kDfFill>);
-  set((const void*)k_flux_df<3, 1, kDfFill>);
-  set((const void*)k_flux_df<2, 1, kDfJv>);
-  set((const void*)k_flux_df<3, 1, kDfJv>);
-  rc = e == cudaSuccess ? 0 : (int)e;
-  return rc;
 }
 
 }  // namespace hofv
