@@ -1,20 +1,28 @@
 #!/usr/bin/env python
 """Benchmark of the high-order FV-JFNK hot path on GB300.
 
-Default (N=1): the 2-D, 512 x 512 jittered quad workload with cubic
-least-squares reconstruction (3 Gauss points per face), linear elasticity,
-the paper's mixed manufactured field.  One timed step is one flexible-GMRES
-Arnoldi step of the JFNK solver -- the approximate-Jacobian preconditioner
-(FP32 inner CG), the forward-difference Jacobian-vector product (one FP64
-residual evaluation), two Gram-Schmidt passes against 16 basis vectors and
-the normalisation -- i.e. one pass over every kernel of the hot path.
+Default (N=1): the largest workload, the 3-D neo-Hookean block of 128^3
+hexahedra jittered by 20 % with cubic least-squares reconstruction (3 x 3
+Gauss points per face, 85-cell stencils, 2.1 M cells, 128 GB of
+reconstruction coefficients), the gradient contraction in double-float
+pairs (hofv_set_precision).  One timed step is one flexible-GMRES Arnoldi
+step of the JFNK solver -- the approximate-Jacobian preconditioner (one
+FP32 aggregation-multigrid V-cycle), the Jacobian-vector product (the
+face kernels contract the Krylov vector; the state's gradients come from
+the linearisation cache), two Gram-Schmidt passes against 16 basis vectors
+and the normalisation -- i.e. one pass over every kernel of the hot path.
 ``value`` counts residual evaluations: cells x evaluations / s (Mcell/s).
 
-Also reported on the same JSON line: the roofline of the dominant kernel
-(face fluxes, FP64-ALU bound on this GPU), the oracle timed on the host
-cores on a bounded sample, an end-to-end number through the public API with
-host buffers, the time to a 1e-8 residual reduction for the FP64 and FP32
-approximate-Jacobian preconditioners, clocks sampled during the timed region.
+Also on the same JSON line: the roofline of the dominant kernel (the
+double-float face kernel against the measured HBM bandwidth, with its FP32
+issue and the FP64 peak measured by the library's probe), the same step
+with the FP64 contraction, the oracle timed on the host cores (one thread
+and all cores) on a bounded sample of the same workload, an end-to-end
+number through the public API with host buffers, clocks sampled during the
+timed sections, time to a 1e-8 residual reduction over all ten load steps
+of the 64^3 neo-Hookean block (plain FP64 against the FP32 preconditioners
+and the double-float contraction), and the 2-D 512^2 linear workload's
+step, roofline and solve times under "c2".
 
 ``--impl reference`` times the CPU oracle as it stands (the only reference
 available: the paper ships no code) on the same workload.
@@ -65,22 +73,31 @@ def replica_value(cells_per_rank, world_size, ms_max):
     return world_size * cells_per_rank / (ms_max * 1e-3) / 1e6
 
 
-def measured_traffic(workload):
-    """DRAM bytes per k_flux launch from the committed ncu capture, or None
-    when the face-flux kernel's source (the law and the kernel) changed since
-    the capture."""
+def kernel_hash():
+    """sha256[:16] of the source of the double-float face kernel and the laws
+    it evaluates (csrc/residual.cu)."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "ncu_k_flux_traffic.txt")
-    src = os.path.join(ROOT, "paper_2601_18417_gb300", "csrc", "residual.cu")
+    text = open(os.path.join(ROOT, "paper_2601_18417_gb300", "csrc", "residual.cu")).read()
+    parts = []
+    for lo, hi in (("// laws: traction t = T a", "// face fluxes, one tile of 32 faces"),
+                   ("// Face fluxes, double-float gradient rows.",
+                    "// contracted linear form, homogeneous part at v")):
+        a, b = text.find(lo), text.find(hi)
+        parts.append(text[a:b] if 0 <= a < b else "")
+    return hashlib.sha256("".join(parts).encode()).hexdigest()[:16]
+
+
+def measured_traffic(workload):
+    """DRAM bytes per launch of the double-float face kernel from the
+    committed ncu summary, or None when the kernel's source changed since the
+    capture (or the workload was not captured)."""
+    path = os.path.join(ROOT, "profiles", "ncu_k_flux_df_traffic.txt")
     if not os.path.exists(path):
         return None
-    text = open(src).read()
-    lo = text.find("// laws: traction t = T a")
-    hi = text.find("// cell assembly")
-    h = hashlib.sha256(text[lo:hi].encode()).hexdigest()[:16]
+    h = kernel_hash()
     for line in open(path):
         parts = line.split()
-        if len(parts) == 3 and not line.startswith("#") and parts[0] == workload:
+        if len(parts) >= 3 and not line.startswith("#") and parts[0] == workload:
             return float(parts[1]) if parts[2] == h else None
     return None
 
@@ -208,68 +225,102 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ oracle baseline
-def oracle_baseline(wl, mesh, budget_s=12.0, sample_cells=2048, seed=3):
-    """The CPU oracle as it stands, single-threaded, on a bounded sample:
-    the residual of `sample_cells` cells of the same workload."""
-    import oracle
-    from paper_2601_18417_gb300 import inputs as I
-    tags = I.side_tags(wl.problem, wl.dim)
-    o = oracle.OracleMesh(mesh, tags, p=wl.p, n_plus=wl.n_plus, q1=wl.q1,
-                          k_weight=wl.k_weight, alpha=wl.alpha)
-    rng = np.random.default_rng(seed)
-    nc = o.nc
-    start = int(rng.integers(0, max(nc - sample_cells, 1)))
-    cells = np.arange(start, min(start + sample_cells, nc))
-    o.prepare(cells)
-    field = I.field_for(wl.problem, wl.dim)
-    xq, xf = o.xq[o.disp_faces()], o.xf[o.disp_faces()]
-    if field is not None:
-        ubq, ubf = field.value(xq), field.value(xf)
-        u = field.value(o.xc).T.copy()
-    else:
-        top = I.block_top_displacement(1, wl.load_steps, wl.dim)
-        on_top = np.abs(xf[:, wl.dim - 1] - 1.0) < 1e-9
-        ubq = np.where(on_top[:, None, None], top, 0.0) * np.ones_like(xq)
-        ubf = np.where(on_top[:, None], top, 0.0) * np.ones_like(xf)
-        u = top[:, None] * o.xc[:, wl.dim - 1][None, :]
-    u = u + 1e-3 * np.abs(u).max() * rng.standard_normal(u.shape)
-    tbq = np.zeros((max(o.nft, 1), o.Q, wl.dim))
-    body = np.zeros((wl.dim, nc))
-    reps = 0
-    t0 = time.perf_counter()
-    while True:
-        o.residual(wl.law, wl.mu, wl.lam, u, ubq, ubf, tbq, body, cells=cells)
-        reps += 1
-        dt = time.perf_counter() - t0
-        if dt >= budget_s:
-            break
-    return {"value": len(cells) * reps / dt / 1e6, "unit": "Mcell/s", "cores": 1,
-            "kind": "oracle",
-            "sample": f"residual of {len(cells)} contiguous cells of the {wl.name} workload, "
-                      f"{reps} evaluations in {dt:.1f} s, single thread"}
+class OracleSample:
+    """The CPU oracle as it stands, prepared once on a bounded sample: the
+    residual of `sample_cells` contiguous cells of the same workload."""
+
+    def __init__(self, wl, mesh, sample_cells, seed=3):
+        import oracle
+        from paper_2601_18417_gb300 import inputs as I
+        self.oracle, self.wl = oracle, wl
+        tags = I.side_tags(wl.problem, wl.dim)
+        o = oracle.OracleMesh(mesh, tags, p=wl.p, n_plus=wl.n_plus, q1=wl.q1,
+                              k_weight=wl.k_weight, alpha=wl.alpha)
+        rng = np.random.default_rng(seed)
+        nc = o.nc
+        start = int(rng.integers(0, max(nc - sample_cells, 1)))
+        self.cells = np.arange(start, min(start + sample_cells, nc))
+        self.ncores = os.cpu_count() or 1
+        oracle.set_threads(self.ncores)
+        o.prepare(self.cells)
+        field = I.field_for(wl.problem, wl.dim)
+        xq, xf = o.xq[o.disp_faces()], o.xf[o.disp_faces()]
+        if field is not None:
+            self.ubq, self.ubf = field.value(xq), field.value(xf)
+            u = field.value(o.xc).T.copy()
+        else:
+            top = I.block_top_displacement(1, wl.load_steps, wl.dim)
+            on_top = np.abs(xf[:, wl.dim - 1] - 1.0) < 1e-9
+            self.ubq = np.where(on_top[:, None, None], top, 0.0) * np.ones_like(xq)
+            self.ubf = np.where(on_top[:, None], top, 0.0) * np.ones_like(xf)
+            u = top[:, None] * o.xc[:, wl.dim - 1][None, :]
+        self.u = u + 1e-3 * np.abs(u).max() * rng.standard_normal(u.shape)
+        self.tbq = np.zeros((max(o.nft, 1), o.Q, wl.dim))
+        self.body = np.zeros((wl.dim, nc))
+        self.o = o
+
+    def run(self, threads, seconds):
+        """Mcell/s of repeated residual evaluations for about `seconds` on
+        `threads` threads, and the thread count in use."""
+        used = self.oracle.set_threads(threads)
+        wl, reps = self.wl, 0
+        t0 = time.perf_counter()
+        while True:
+            self.o.residual(wl.law, wl.mu, wl.lam, self.u, self.ubq, self.ubf, self.tbq,
+                            self.body, cells=self.cells)
+            reps += 1
+            dt = time.perf_counter() - t0
+            if dt >= seconds:
+                break
+        self.oracle.set_threads(self.ncores)
+        return len(self.cells) * reps / dt / 1e6, used
+
+
+def default_sample(wl):
+    return 96 if wl.dim == 3 else 2048
+
+
+def oracle_baseline(wl, mesh, budget_s=12.0, sample_cells=2048, runs=5):
+    """`runs` timed runs of the oracle on one thread and on every host core
+    (OpenMP over cells), each about budget_s / (2 runs) seconds; medians."""
+    smp = OracleSample(wl, mesh, sample_cells)
+    per_run = budget_s / (2 * runs)
+    one = statistics.median(smp.run(1, per_run)[0] for _ in range(runs))
+    res = [smp.run(smp.ncores, per_run) for _ in range(runs)]
+    used = res[0][1]
+    return {"value": statistics.median(r[0] for r in res), "unit": "Mcell/s", "cores": used,
+            "kind": "oracle", "single_thread": one,
+            "sample": f"residual of {len(smp.cells)} contiguous cells of the {wl.name} workload; "
+                      f"median of {runs} runs of {per_run:.1f} s on {used} threads (value) and on "
+                      f"1 thread (single_thread); OpenMP over cells, the arithmetic unchanged"}
 
 
 # ------------------------------------------------------------------ main arm
-def run_hofv(args):
+def event_ms(fn, reps, s):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(s)
+    for _ in range(reps):
+        fn()
+    e1.record(s)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def step_section(args, wl, mesh, ctx, lay, u_ex, precision, rank, ws, peaks_dev, clk_holder):
+    """One workload: the Arnoldi step (CUDA graph and direct launches,
+    multigrid and Jacobi-CG inner solves), per-kernel residual times and the
+    roofline of the face kernel, end to end with host buffers, the step with
+    the other contraction precision."""
     import torch
 
-    from paper_2601_18417_gb300 import build as B
     from paper_2601_18417_gb300 import hofv
-    ws, rank, local = dist_env()
-    if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    torch.cuda.set_device(local)
-    if rank == 0:
-        B.build()
-    if ws > 1:
-        import torch.distributed as dist
-        dist.barrier()
-    wl, mesh, ctx, lay, setup_s, u_ex, field = build_workload(args.workload, local)
-    ctx.set_precision(hofv.PREC_DF64 if args.precision == "df64" else hofv.PREC_FP64)
     d, nc = wl.dim, lay.n_cells
     n = d * nc
-    dev = torch.device("cuda", local)
+    dev = torch.device("cuda", ctx.device)
+    prec = hofv.PREC_DF64 if precision == "df64" else hofv.PREC_FP64
+    ctx.set_precision(prec)
     rng = np.random.default_rng(99)
     amp = np.abs(u_ex).max()
     u = torch.as_tensor(u_ex + 1e-3 * amp * rng.standard_normal(u_ex.shape), device=dev)
@@ -293,72 +344,55 @@ def run_hofv(args):
     if ws > 1:
         import torch.distributed as dist
         dist.barrier()
-    clk = ClockSampler(local) if rank == 0 else None
+    if clk_holder is not None and rank == 0:
+        clk_holder.append(ClockSampler(ctx.device))
     s = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(s)
-    for _ in range(args.steps):
-        step()
-    e1.record(s)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
+    ms = event_ms(step, args.steps, s)
     # the same step launched kernel by kernel instead of as one CUDA graph
     os.environ["HOFV_GRAPHS"] = "0"
     for _ in range(3):
         step()
-    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    g0.record(s)
-    for _ in range(max(args.steps // 5, 10)):
-        step()
-    g1.record(s)
-    torch.cuda.synchronize()
+    small = max(args.steps // 5, 10)
+    ms_direct = event_ms(step, small, s)
     os.environ.pop("HOFV_GRAPHS", None)
-    ms_direct = g0.elapsed_time(g1) / max(args.steps // 5, 10)
-    # the same step with the Jacobi-preconditioned CG inner solve, for comparison
+    # the Jacobi-preconditioned CG inner solve, for comparison
     for _ in range(3):
         ctx.arnoldi_step(u, Ru, hofv.PC_AJ32, INNER_ITERS, V, Z, J)
-    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a0.record(s)
-    for _ in range(max(args.steps // 5, 10)):
-        ctx.arnoldi_step(u, Ru, hofv.PC_AJ32, INNER_ITERS, V, Z, J)
-    a1.record(s)
-    torch.cuda.synchronize()
-    ms_jacobi = a0.elapsed_time(a1) / max(args.steps // 5, 10)
-    # per-kernel residual timing for the roofline (same stream, CUDA events)
-    kt = []
-    for _ in range(max(args.steps, 10)):
-        kt.append(ctx.residual_timed(u, Ru))
-    clocks = clk.stop() if clk else None
-    if ws > 1:
-        ms = max_over_ranks(ms, dev)
-    value = replica_value(nc, ws, ms)
-    kt = np.array(kt)
+    ms_jacobi = event_ms(lambda: ctx.arnoldi_step(u, Ru, hofv.PC_AJ32, INNER_ITERS, V, Z, J),
+                         small, s)
+    # per-kernel residual timing (CUDA events on the library's stream)
+    kt = np.array([ctx.residual_timed(u, Ru) for _ in range(max(args.steps, 10))])
     flux_ms = float(kt[:, 1].mean())
     res_ms = float(kt.sum(axis=1).mean())
     flops, fbytes, rbytes = algorithmic_counts(wl, lay)
     pk, src = peaks()
-    sm_max = float(pk.get("sm_max_mhz", 2070.0))
-    fp64_peak = 152 * 2 * 2 * sm_max * 1e6 / 1e12     # TFLOP/s: 2 DFMA/clk/SM
-    achieved = flops / (flux_ms * 1e-3) / 1e12
-    roofline = {"bound": "alu", "kernel": "k_flux (face gradients + law + quadrature)",
-                "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp64_peak,
-                "peak_source": f"FP64 units x SMs x max clock ({sm_max:.0f} MHz), nominal "
-                               "2 DFMA/clk/SM on GB300",
-                "traffic": measured_traffic(wl.name),
-                "hbm_achieved_gbs": fbytes / (flux_ms * 1e-3) / 1e9,
-                "hbm_peak_gbs": pk["hbm_gbs"], "hbm_peak_source": src,
-                "hbm_frac": fbytes / (flux_ms * 1e-3) / 1e9 / pk["hbm_gbs"],
-                "flux_ms": flux_ms, "residual_ms": res_ms,
-                "residual_mcells": nc / (res_ms * 1e-3) / 1e6,
-                "residual_hbm_frac": rbytes / (res_ms * 1e-3) / 1e9 / pk["hbm_gbs"],
-                "alg_flops_per_launch": flops, "alg_bytes_per_launch": fbytes}
+    hbm = pk["hbm_gbs"]
+    achieved = fbytes / (flux_ms * 1e-3) / 1e9
+    macs = flops / 2.0
+    roofline = {
+        "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+        "frac": achieved / hbm, "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)",
+        "kernel": ("k_flux_df (double-float face gradients + law + quadrature)"
+                   if precision == "df64" else "k_flux (FP64 face gradients + law + quadrature)"),
+        "traffic": measured_traffic(wl.name) if precision == "df64" else None,
+        "alg_bytes_per_launch": fbytes, "flux_ms": flux_ms, "residual_ms": res_ms,
+        "residual_mcells": nc / (res_ms * 1e-3) / 1e6,
+        "residual_hbm_frac": rbytes / (res_ms * 1e-3) / 1e9 / hbm,
+        "gradient_macs_per_launch": macs,
+        "fp64_equivalent_tflops": flops / (flux_ms * 1e-3) / 1e12,
+        "fp64_peak_tflops_measured": peaks_dev["fp64_tflops"],
+        "fp32_peak_tflops_measured": peaks_dev["fp32_tflops"]}
+    if precision == "df64":  # 12 FP32 instructions per double-float product
+        roofline["fp32_tflops_of_contraction"] = 12.0 * macs / (flux_ms * 1e-3) / 1e12
+        roofline["fp32_frac_of_measured"] = roofline["fp32_tflops_of_contraction"] / \
+            peaks_dev["fp32_tflops"]
+    else:
+        roofline["fp64_frac_of_measured"] = roofline["fp64_equivalent_tflops"] / \
+            peaks_dev["fp64_tflops"]
     # end to end through the public API with host buffers
     e2e = None
     if rank == 0:
-        h2d = n * 8
-        d2h = (J + 2) * 8
+        h2d, d2h = n * 8, (J + 2) * 8
         for _ in range(2):
             V[J].copy_(v_host, non_blocking=True)
             step()
@@ -372,112 +406,183 @@ def run_hofv(args):
         e2e_s = (time.perf_counter() - t0) / reps
         e2e = {"value": nc / e2e_s / 1e6, "unit": "Mcell/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
-    # the linear law in contracted form (law and quadrature folded into one
-    # d x d matrix per face and stencil cell), same step and solve
-    contracted = None
-    if rank == 0 and wl.law == 0:
-        ctx.set_contraction(True)
-        kc = np.array([ctx.residual_timed(u, Ru) for _ in range(max(args.steps // 10, 10))])
-        for _ in range(3):
-            step()
-        torch.cuda.synchronize()
-        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        c0.record(s)
-        for _ in range(args.steps):
-            step()
-        c1.record(s)
-        torch.cuda.synchronize()
-        cms = c0.elapsed_time(c1) / args.steps
-        tf_ms = float(kc[:, 1].mean())
-        d_, S_ = wl.dim, lay.stencil
-        nfid = lay.n_internal + lay.n_disp
-        t_flops = 2.0 * nfid * S_ * d_ * d_
-        t_bytes = nfid * (8 * S_ * d_ * d_ + 4 * S_ + 16 + 24 * d_) + 8 * d_ * lay.n_cells
-        contracted = {"step_ms": cms, "value": nc / (cms * 1e-3) / 1e6,
-                      "residual_ms": float(kc.sum(axis=1).mean()),
-                      "residual_mcells": nc / (float(kc.sum(axis=1).mean()) * 1e-3) / 1e6,
-                      "tflux_ms": tf_ms, "tflux_tflops": t_flops / (tf_ms * 1e-3) / 1e12,
-                      "tflux_fp64_frac": t_flops / (tf_ms * 1e-3) / 1e12 / fp64_peak,
-                      "tflux_hbm_gbs": t_bytes / (tf_ms * 1e-3) / 1e9,
-                      "tflux_hbm_frac": t_bytes / (tf_ms * 1e-3) / 1e9 / pk["hbm_gbs"]}
-        if not args.no_solve:
-            uu = torch.zeros_like(u)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            st = ctx.newton_solve(uu, rtol=1e-8, precond=hofv.PC_AJMG, inner_iters=MG_INNER,
-                                  restart=30, max_krylov=3000)
-            torch.cuda.synchronize()
-            contracted["solve_fp32_aj_mg"] = {
-                "seconds": time.perf_counter() - t0, "status": st["status"],
-                "newton": st["newton_iters"], "krylov": st["krylov_iters"]}
-        ctx.set_contraction(False)
+    # the other contraction precision, same step
+    other = "fp64" if precision == "df64" else "df64"
+    ctx.set_precision(hofv.PREC_FP64 if other == "fp64" else hofv.PREC_DF64)
+    ctx.residual(u, Ru)
+    for _ in range(3):
+        step()
+    ms_other = event_ms(step, small, s)
+    ko = np.array([ctx.residual_timed(u, Ru) for _ in range(10)])
+    ctx.set_precision(prec)
+    ctx.residual(u, Ru)
     # per step: the preconditioner (one V-cycle: 4 launches per level above the
-    # coarsest, 1 on it) + norm (1) + Jv (norm, eps, axpy, 3 residual kernels)
-    # + CGS2 (2 multi-dots, 2 multi-axpys) + norm + scale
+    # coarsest, 1 on it) + norm (1) + Jv (norm, eps, split / axpy, 3 residual
+    # kernels) + CGS2 (2 multi-dots, 2 multi-axpys) + norm + scale
     assert MG_INNER == 1 and mg["levels"] > 1
     launches = (4 * (mg["levels"] - 1) + 1) + 1 + 6 + 4 + 2
+    return {"ms": ms, "u": u, "Ru": Ru, "mg": mg, "roofline": roofline, "e2e": e2e,
+            "launches": launches,
+            "step_ms_no_graph": {"ms_per_step": ms_direct, "value": nc / (ms_direct * 1e-3) / 1e6},
+            "step_ms_jacobi_cg": {"inner_iters": INNER_ITERS, "ms_per_step": ms_jacobi,
+                                  "value": nc / (ms_jacobi * 1e-3) / 1e6},
+            f"step_{other}": {"ms_per_step": ms_other, "value": nc / (ms_other * 1e-3) / 1e6,
+                              "flux_ms": float(ko[:, 1].mean()),
+                              "residual_ms": float(ko.sum(axis=1).mean())},
+            "kernel_ms": {"extrapolation": float(kt[:, 0].mean()), "faces": flux_ms,
+                          "cells": float(kt[:, 2].mean())}}
+
+
+def linear_solves(ctx, wl, u, Ru, u_ex):
+    """Time to 1e-8 from u = 0 on a linear workload with each preconditioner."""
+    import torch
+
+    from paper_2601_18417_gb300 import hofv
+    solve = {}
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx.nej_apply(u, Ru)  # near-exact Jacobian set-up outside the timed solves
+    torch.cuda.synchronize()
+    solve["nej_setup_s"] = time.perf_counter() - t0
+    ctx.residual(u, Ru)
+    for name_, kind, inner in (("plain_fp64_aj", hofv.PC_AJ64, INNER_ITERS),
+                               ("fp32_aj", hofv.PC_AJ32, INNER_ITERS),
+                               ("fp32_aj_mg", hofv.PC_AJMG, MG_INNER),
+                               ("fp32_aj_mg2", hofv.PC_AJMG, 2),
+                               ("fp32_nej6", hofv.PC_NEJ, 6)):
+        uu = torch.zeros_like(u)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = ctx.newton_solve(uu, rtol=1e-8, precond=kind, inner_iters=inner,
+                              restart=30, max_krylov=3000)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        err = float((uu.cpu().numpy() - u_ex).std() / max(np.abs(u_ex).std(), 1e-300))
+        solve[name_] = {"seconds": dt, "precond": kind, "inner_iters": inner,
+                        "status": st["status"], "newton": st["newton_iters"],
+                        "krylov": st["krylov_iters"],
+                        "r_final_over_r0": st["r_final"] / max(st["r0"], 1e-300),
+                        "rel_error_vs_manufactured": err}
+    return solve
+
+
+def block_solves(args, device):
+    """All load steps of the 64^3 neo-Hookean block to 1e-8: plain FP64 JFNK
+    (FP64 contraction, FP64 approximate-Jacobian CG) against the FP32
+    multigrid inner solve with the FP64 and the double-float contraction."""
+    import torch
+
+    from paper_2601_18417_gb300 import hofv
+    wl, mesh, ctx, lay, setup_s, _, _ = build_workload(args.block_workload, device)
+    out = {"workload": wl.name, "cells": lay.n_cells, "load_steps": wl.load_steps,
+           "setup_s": setup_s}
+    opts = dict(rtol=1e-8, restart=30, max_krylov=3000, max_newton=20)
+    for label, prec, pc, inner in (("plain_fp64_aj64", hofv.PREC_FP64, hofv.PC_AJ64, INNER_ITERS),
+                                   ("fp64_aj32_mg", hofv.PREC_FP64, hofv.PC_AJMG, 2),
+                                   ("df64_aj32_mg", hofv.PREC_DF64, hofv.PC_AJMG, 2)):
+        ctx.set_precision(prec)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        u, st = block_load_steps(ctx, wl, lay, wl.load_steps, precond=pc, inner_iters=inner,
+                                 **opts)
+        out[label] = summarize(st, time.perf_counter() - t0)
+        out[label]["u"] = u
+    ref = out["plain_fp64_aj64"].pop("u")
+    for label in ("fp64_aj32_mg", "df64_aj32_mg"):
+        uu = out[label].pop("u")
+        out[label]["rel_diff_vs_plain"] = float((uu - ref).norm() / ref.norm())
+    ctx.close()
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_hofv(args):
+    import torch
+
+    from paper_2601_18417_gb300 import build as B
+    from paper_2601_18417_gb300 import hofv
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    if rank == 0:
+        B.build()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    wl, mesh, ctx, lay, setup_s, u_ex, field = build_workload(args.workload, local)
+    peaks_dev = ctx.probe_peaks()
+    nc = lay.n_cells
+    clk = []
+    sec = step_section(args, wl, mesh, ctx, lay, u_ex, args.precision, rank, ws, peaks_dev, clk)
+    clocks = clk[0].stop() if clk else None
+    ms = sec["ms"]
+    if ws > 1:
+        ms = max_over_ranks(ms, torch.device("cuda", local))
+    value = replica_value(nc, ws, ms)
     solve = None
-    if rank == 0 and not args.no_solve:
-        solve = {}
-        if wl.law == 0:  # near-exact Jacobian set-up outside the timed solves
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            ctx.nej_apply(u, Ru)
-            torch.cuda.synchronize()
-            solve["nej_setup_s"] = time.perf_counter() - t0
-            ctx.residual(u, Ru)
-        for name_, kind, inner in (("plain_fp64_aj", hofv.PC_AJ64, INNER_ITERS),
-                                   ("fp32_aj", hofv.PC_AJ32, INNER_ITERS),
-                                   ("fp32_aj_inner40", hofv.PC_AJ32, 40),
-                                   ("fp32_aj_mg", hofv.PC_AJMG, MG_INNER),
-                                   ("fp32_aj_mg2", hofv.PC_AJMG, 2),
-                                   ("fp32_nej6", hofv.PC_NEJ, 6)):
-            if kind == hofv.PC_NEJ and wl.law != 0:
-                continue
-            uu = torch.zeros_like(u)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            st = ctx.newton_solve(uu, rtol=1e-8, precond=kind, inner_iters=inner,
-                                  restart=30, max_krylov=3000)
-            torch.cuda.synchronize()
-            dt = time.perf_counter() - t0
-            err = float((uu.cpu().numpy() - u_ex).std() / max(np.abs(u_ex).std(), 1e-300))
-            solve[name_] = {"seconds": dt, "precond": kind, "inner_iters": inner,
-                            "status": st["status"], "newton": st["newton_iters"],
-                            "krylov": st["krylov_iters"], "r_final_over_r0":
-                            st["r_final"] / max(st["r0"], 1e-300),
-                            "rel_error_vs_manufactured": err}
+    if rank == 0 and not args.no_solve and wl.law == 0:
+        solve = linear_solves(ctx, wl, sec["u"], sec["Ru"], u_ex)
+    ctx.close()
+    del sec["u"], sec["Ru"]
+    torch.cuda.empty_cache()
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = oracle_baseline(wl, mesh, budget_s=args.cpu_budget)
+        cpu = oracle_baseline(wl, mesh, budget_s=args.cpu_budget,
+                              sample_cells=args.cpu_sample or default_sample(wl))
+    block = None
+    if rank == 0 and not args.no_solve and args.block_workload:
+        block = block_solves(args, local)
+    c2 = None
+    if rank == 0 and args.extra_workload and args.extra_workload != args.workload:
+        wl2, mesh2, ctx2, lay2, setup2, u_ex2, _ = build_workload(args.extra_workload, local)
+        sec2 = step_section(args, wl2, mesh2, ctx2, lay2, u_ex2, args.precision, rank, 1,
+                            peaks_dev, None)
+        c2 = {"workload": wl2.name, "mesh": mesh_label(wl2), "cells": lay2.n_cells,
+              "ms_per_step": sec2["ms"], "value": lay2.n_cells / (sec2["ms"] * 1e-3) / 1e6,
+              "roofline": sec2["roofline"], "e2e": sec2["e2e"],
+              "step_ms_no_graph": sec2["step_ms_no_graph"],
+              "step_ms_jacobi_cg": sec2["step_ms_jacobi_cg"], "kernel_ms": sec2["kernel_ms"],
+              [k for k in sec2 if k.startswith("step_fp64") or k.startswith("step_df64")][0]:
+                  sec2[[k for k in sec2 if k.startswith("step_fp64") or
+                        k.startswith("step_df64")][0]],
+              "setup_s": setup2}
+        if not args.no_solve and wl2.law == 0:
+            c2["solve"] = linear_solves(ctx2, wl2, sec2["u"], sec2["Ru"], u_ex2)
+        ctx2.close()
+        torch.cuda.empty_cache()
     if rank == 0:
+        other = [k for k in sec if k.startswith("step_fp64") or k.startswith("step_df64")][0]
         line = {"metric": METRIC, "value": value, "unit": "Mcell/s", "n_gpus": ws,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f64", "data": "synthetic",
+                "dtype": "f64 (gradient contraction double-float)" if args.precision == "df64"
+                         else "f64",
+                "data": "synthetic",
                 "config": {"workload": wl.name,
                            "mesh": mesh_label(wl),
                            "cells": nc, "p": wl.p, "stencil": lay.stencil,
                            "gauss_per_face": lay.q_face,
                            "law": "linear" if wl.law == 0 else "neo-Hookean",
+                           "precision": args.precision,
                            "step": f"one flexible Arnoldi step: AJ FP32 preconditioner "
-                                   f"(one {mg['levels']}-level "
-                                   f"aggregation-multigrid V-cycle) + forward-difference Jv "
-                                   f"(1 FP64 residual) + 2x classical Gram-Schmidt on {J + 1} "
-                                   f"vectors; device part replayed as one CUDA graph",
+                                   f"(one {sec['mg']['levels']}-level "
+                                   f"aggregation-multigrid V-cycle) + Jacobian-vector product "
+                                   f"(one residual pass) + 2x classical Gram-Schmidt on "
+                                   f"{KRYLOV_J + 1} vectors; device part replayed as one CUDA "
+                                   f"graph",
                            "l2": "inputs larger than L2 (coefficients "
-                                 f"{rbytes / 1e9:.2f} GB per residual)",
+                                 f"{algorithmic_counts(wl, lay)[2] / 1e9:.1f} GB per residual)",
                            "parallelism": "replicas" if ws > 1 else "single GPU"},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": launches * args.steps, "clocks": clocks,
-                "setup_s": setup_s, "multigrid": mg,
-                "step_ms_no_graph": {"ms_per_step": ms_direct,
-                                     "value": nc / (ms_direct * 1e-3) / 1e6},
-                "step_ms_jacobi_cg": {"inner_iters": INNER_ITERS, "ms_per_step": ms_jacobi,
-                                      "value": nc / (ms_jacobi * 1e-3) / 1e6},
-                "solve": solve, "contracted": contracted, "impl": "hofv"}
+                "roofline": sec["roofline"], "cpu_baseline": cpu, "e2e": sec["e2e"],
+                "gpu_launches": sec["launches"] * args.steps, "clocks": clocks,
+                "setup_s": setup_s, "multigrid": sec["mg"], "device_peaks": peaks_dev,
+                "step_ms_no_graph": sec["step_ms_no_graph"],
+                "step_ms_jacobi_cg": sec["step_ms_jacobi_cg"], other: sec[other],
+                "kernel_ms": sec["kernel_ms"], "solve": solve, "block_solve": block,
+                "c2": c2, "impl": "hofv"}
         print(json.dumps(line))
-    ctx.close()
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -610,13 +715,15 @@ def run_reference(args):
     oracle.build()
     wl = I.WORKLOADS[args.workload]
     mesh = wl.mesh()
+    smp = OracleSample(wl, mesh, args.cpu_sample or default_sample(wl))
     per = max(1.0, args.cpu_budget / max(args.steps + args.warmup, 1))
     for _ in range(args.warmup):
-        oracle_baseline(wl, mesh, budget_s=per)
-    vals = [oracle_baseline(wl, mesh, budget_s=per) for _ in range(args.steps)]
-    v = statistics.median(x["value"] for x in vals)
-    cpu = dict(vals[-1])
-    cpu["value"] = v
+        smp.run(smp.ncores, per)
+    res = [smp.run(smp.ncores, per) for _ in range(args.steps)]
+    v = statistics.median(r[0] for r in res)
+    cpu = {"value": v, "unit": "Mcell/s", "cores": res[0][1], "kind": "oracle",
+           "sample": f"residual of {len(smp.cells)} contiguous cells of the {wl.name} workload, "
+                     f"median of {args.steps} runs of {per:.1f} s on {res[0][1]} threads"}
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Mcell/s",
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": per * 1e3, "higher_is_better": True, "scaling": "weak",
@@ -770,9 +877,15 @@ def main():
     ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="hofv", choices=["hofv", "reference"])
-    ap.add_argument("--workload", default="quad512j-p3-mixed")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "df64"],
+    ap.add_argument("--workload", default="hex128j-p3-nh")
+    ap.add_argument("--precision", default="df64", choices=["fp64", "df64"],
                     help="arithmetic of the gradient contraction (hofv_set_precision)")
+    ap.add_argument("--extra-workload", default="quad512j-p3-mixed",
+                    help="second workload reported under 'c2' ('' = none)")
+    ap.add_argument("--block-workload", default="hex64j-p2-nh",
+                    help="neo-Hookean block whose load steps are solved to 1e-8 ('' = none)")
+    ap.add_argument("--cpu-sample", type=int, default=0,
+                    help="cells of the oracle's timed sample (0: 96 in 3-D, 2048 in 2-D)")
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)

@@ -21,7 +21,7 @@
  *     (residual, jvp, precondition) allocate nothing, except that the first
  *     use of a preconditioner builds its data (multigrid hierarchy,
  *     near-exact Jacobian) and the first Arnoldi step of a kind captures
- *     its CUDA graph.
+ *     its CUDA graph; hofv_prepare_solver does all of that up front.
  *   - Asynchrony: evaluation calls enqueue work on the context stream and
  *     return; set-up calls and hofv_newton_solve synchronise that stream.
  *   - Faces: internal faces first, ordered by (owner, owner local face) with
@@ -224,6 +224,22 @@ int hofv_set_scheme(hofv_ctx* ctx, int p, int n_plus, int q_per_dir,
    Errors: ESTATE before set_mesh/set_scheme, ENOMEM, EILLCOND. */
 int hofv_build_stencils(hofv_ctx* ctx);
 
+/* Replace the nearest-neighbour stencils (Sec. 3.5.2) by the caller's and
+   recompute everything made from them (reconstruction coefficients, the
+   stabilisation extrapolation weights of eq. alphaJump, the cell averages of
+   the inertia term, the contracted linear-elastic matrices; the near-exact
+   Jacobian is rebuilt on its next use).  HOST int32 cell ids, row-major,
+   copied in:
+     face_stencils [n_internal + n_disp][S]   (NULL: keep the current ones)
+     cell_stencils [n_cells][S]               (NULL: keep the current ones)
+   The order of the ids within a stencil does not matter; the caller keeps
+   them distinct.  Needs hofv_build_stencils first (ESTATE).  Errors: EINVAL
+   for an id outside [0, n_cells), ENOTSUP on meshes with symmetry faces
+   (their stencils hold mirror nodes), EILLCOND when a fit is singular; on
+   any error the previous stencils are restored.  Synchronises. */
+int hofv_set_stencils(hofv_ctx* ctx, const int32_t* face_stencils,
+                      const int32_t* cell_stencils);
+
 int hofv_get_layout(const hofv_ctx* ctx, hofv_layout* out);
 
 /* Copy a point set (HOFV_PTS_*) to the HOST array `out` (layouts above),
@@ -251,15 +267,23 @@ int hofv_set_contraction(hofv_ctx* ctx, int on);
    extrapolated face values of the stabilisation, eq. alphaJump).
    HOFV_PREC_FP64 (default) uses FP64 fused multiply-adds.  HOFV_PREC_DF64
    stores each coefficient as a pair of floats (hi, lo), hi + lo its value
-   rounded to 48 significant bits, splits the state the same way, forms each
-   product exactly (TwoProduct by FMA, Dekker 1971) and accumulates with
-   TwoSum and a compensation term (Dot2, Ogita, Rump & Oishi 2005), on the
-   FP32 pipe; each gradient is then converted to FP64 and the law,
-   quadrature, stabilisation jump, assembly and every solver vector stay
-   FP64.  With HOFV_PREC_DF64 hofv_jvp contracts u and v separately and
-   differences the face fluxes of grad u + eps grad v and grad u in FP64,
-   which is R(u + eps v) - R(u) with the rounding of the contraction of u
-   cancelling exactly; it does not read Ru.  Callable at any time: after
+   rounded to 48 significant bits, splits the state exactly into three
+   floats, and forms each product exactly (TwoProduct by FMA, Dekker 1971)
+   and the sums with TwoSum and a compensation term (Dot2, Ogita, Rump &
+   Oishi 2005) on the FP32 pipe.  The face gradients contract the
+   differences to each face's nearest stencil cell (exact differences of the
+   splits) and add back that cell's value times the FP64 sum of the stored
+   coefficients, so the rounding acts on the local variation of the field
+   and not on its magnitude.  Each gradient is then converted to FP64; the
+   law, quadrature, stabilisation jump, assembly and every solver vector stay
+   FP64.  With HOFV_PREC_DF64, hofv_jvp evaluates the forward difference
+   without differencing two separately rounded residuals: for the linear law
+   the residual is affine and (R(u + eps v) - R(u)) / eps is its
+   homogeneous part at v; for the neo-Hookean law the face kernels contract
+   v alone and difference, in FP64, the tractions at grad u + eps grad v and
+   at grad u, with grad u and its tractions cached per (u, Ru) pair (filled
+   on the first Jv after the state or the data change; hofv_residual at u
+   marks it stale).  Ru is not read.  Callable at any time: after
    hofv_build_stencils the coefficient arrays are rewritten in place
    (synchronises); switching back to FP64 keeps the 48-bit values until the
    next hofv_build_stencils.  The environment variable HOFV_PRECISION
@@ -364,6 +388,41 @@ int hofv_precondition(hofv_ctx* ctx, int kind, int inner_iters, const double* v,
 int hofv_newton_solve(hofv_ctx* ctx, double* u, const hofv_solve_opts* opts,
                       hofv_stats* stats);
 
+/* Everything hofv_newton_solve and hofv_arnoldi_step allocate or build on
+   first use, done now for the options `opts` (NULL = defaults): the Krylov
+   basis of opts->restart vectors, the multigrid hierarchy (HOFV_PC_AJMG,
+   HOFV_PC_NEJ) and the near-exact Jacobian (HOFV_PC_NEJ), the linearisation
+   cache of the double-float neo-Hookean Jv.  After it the evaluation calls
+   and solves with these options allocate nothing (the first Arnoldi step of
+   a kind still captures its CUDA graph).  Synchronises. */
+int hofv_prepare_solver(hofv_ctx* ctx, const hofv_solve_opts* opts);
+
+/* Load incrementation (the paper's load steps of its hyperelastic cases,
+   Sec. 5) with automatic cut-back.  The context's current boundary data
+   (hofv_set_bc) are the data at load factor 0, where u (DEVICE
+   [dim][n_cells], updated in place) is a converged state; the DEVICE arrays
+   u_bq1, u_bf1, t_bq1, body1 (layouts of hofv_set_bc; NULL = unchanged)
+   are the data at factor 1.  The factor advances in n_steps equal
+   increments; the data of each are interpolated linearly and the step is
+   solved by hofv_newton_solve with `opts` from a predictor: u +
+   increment * du_dlambda (DEVICE [dim][n_cells], the state's derivative
+   with respect to the factor as the caller estimates it) when du_dlambda
+   is not NULL, else the secant through the last two converged states.  A
+   step whose solve fails (HOFV_WNOTCONV or HOFV_ENAN) is retried from the
+   last converged state with half the increment, up to max_halvings times
+   in a row; after a success the increment doubles back towards the
+   nominal one.  On return u holds the last converged state and the
+   context's data are those of its load factor; *steps_done (HOST, may be
+   NULL) counts the accepted increments and *stats (HOST, may be NULL)
+   sums the solver counts.  Returns 0 at factor 1, HOFV_WNOTCONV if an
+   increment still failed after max_halvings halvings, or an error.
+   Allocates two copies of the boundary data and three state vectors for
+   the duration of the call; synchronises. */
+int hofv_solve_load_path(hofv_ctx* ctx, double* u, const double* u_bq1, const double* u_bf1,
+                         const double* t_bq1, const double* body1, const double* du_dlambda,
+                         int32_t n_steps, int32_t max_halvings, const hofv_solve_opts* opts,
+                         hofv_stats* stats, int32_t* steps_done);
+
 /* ---- learned preconditioner ---------------------------------------------
    A graph network over the cell adjacency (no counterpart in the paper):
    nodes are cells, neighbours are face neighbours weighted by the
@@ -451,8 +510,8 @@ int hofv_arnoldi_step(hofv_ctx* ctx, const double* u, const double* Ru, int kind
    (F = face slots per cell: dim + 1 for triangles / tetrahedra, 2 dim for
    quads / hexes, 8 for polygons), rounded up to a multiple of 32, plus
    (n_internal + n_disp + n_symm) * dim, rounded up to 32, plus with
-   HOFV_PREC_DF64 (n_cells + mirror nodes) * 4 (2-D) or 8 (3-D) for the
-   split state; larger meshes get HOFV_EINVAL.  All calls share the array:
+   HOFV_PREC_DF64 (n_cells + mirror nodes) * 4 (2-D) or 6 (3-D) for the
+   split state, rounded up to 32; larger meshes get HOFV_EINVAL.  All calls share the array:
    calls that overlap on the GPU race and must be serialised by the caller.
    Like every evaluation call it also writes buffers of its own context
    (extended state and mirrored face values of symmetry faces, the inertia
@@ -483,6 +542,17 @@ int hofv_selftest_barrier(hofv_ctx* ctx, int32_t* timed_out);
    context stream: ms[0] stabilisation extrapolation (cell-ordered), ms[1]
    face fluxes, ms[2] cell assembly (HOST array of 3).  Synchronises. */
 int hofv_residual_timed(hofv_ctx* ctx, const double* u, double* R, float* ms);
+
+/* ---- measurement ----------------------------------------------------------- */
+
+/* Arithmetic peaks of the context's device, measured: FP64 and FP32 fused
+   multiply-add throughput in TFLOP/s (2 flops per FMA) from register-only
+   kernels on every SM, timed with CUDA events on the context stream, and
+   the number of SMs.  The denominators of the benchmark's ALU rooflines;
+   no counterpart in the paper.  Any output pointer may be NULL (that peak
+   is not measured).  Allocates 64 bytes for the duration of the call and
+   synchronises. */
+int hofv_probe_peaks(hofv_ctx* ctx, double* fp64_tflops, double* fp32_tflops, int32_t* sm_count);
 
 /* ---- inspection (tests) -------------------------------------------------- */
 

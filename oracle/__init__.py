@@ -29,7 +29,7 @@ def build(force: bool = False) -> str:
     """Compile the oracle with gcc (no FMA contraction, as the source asks)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".{os.getpid()}.tmp"
-        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
+        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
                "-o", tmp, _SRC, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB)
@@ -76,12 +76,19 @@ def lib():
         L.orc_integrate_cells.argtypes = [P, P, P]
         L.orc_aj.argtypes = [P, D, P, P]
         L.orc_gauss_legendre.argtypes = [C.c_int, P, P]
+        L.orc_set_threads.argtypes = [C.c_int]
         _lib = L
     return _lib
 
 
 def _p(a: np.ndarray | None):
     return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def set_threads(n: int = 0) -> int:
+    """OpenMP threads of the oracle's loops over cells and faces (0 = all
+    cores); returns the count in use."""
+    return int(lib().orc_set_threads(int(n)))
 
 
 def gauss_legendre(n: int) -> tuple[np.ndarray, np.ndarray]:

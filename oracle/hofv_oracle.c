@@ -48,6 +48,9 @@
  * written.
  */
 #include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -1206,19 +1209,31 @@ int orc_prepare(orc_mesh* m, int64_t nsub, const int64_t* cells) {
   m->ccond = (double*)calloc(ncs + 1, sizeof(double));
   buckets B;
   build_buckets(m, &B);
+  int rc = 0;
+  /* faces and cells are independent: OpenMP threads take whole ones */
+#pragma omp parallel
+  {
   double* Abar = (double*)malloc(sizeof(double) * Nt * (S + 1));
   double* pts = (double*)malloc(sizeof(double) * 3 * S);
-  int rc = 0;
-  for (int64_t f = 0; f < m->nf && rc == 0; ++f) {
+#pragma omp for schedule(dynamic, 8)
+  for (int64_t f = 0; f < m->nf; ++f) {
     int64_t sl = m->fslot[f];
     if (sl < 0) continue;
+    int err;
+#pragma omp atomic read
+    err = rc;
+    if (err) continue;
     int64_t* st = m->fst + sl * S;
     int ghost = m->ftag[f] == 0;
     /* symmetry face (Sec. 3.5.2): the ceil(S/2) nearest cells and the mirror
        images of the floor(S/2) nearest of them; slot half + k holds the
        source cell of mirror k */
     int half = m->ftag[f] == 2 ? (S + 1) / 2 : S;
-    if (stencil_search_n(m, &B, m->xf + 3 * f, half, st)) { rc = -3; break; }
+    if (stencil_search_n(m, &B, m->xf + 3 * f, half, st)) {
+#pragma omp atomic write
+      rc = -3;
+      continue;
+    }
     for (int k = 0; k < S - half; ++k) st[half + k] = st[k];
     for (int i = 0; i < S; ++i) {
       if (i < half)
@@ -1229,7 +1244,11 @@ int orc_prepare(orc_mesh* m, int64_t nsub, const int64_t* cells) {
     for (int q = 0; q < Q; ++q) {
       double h;
       if (reconstruct_pts(m, m->xq + (f * Q + q) * 3, pts, ghost, Abar, &h,
-                          &m->fcond[sl * Q + q])) { rc = -4; break; }
+                          &m->fcond[sl * Q + q])) {
+#pragma omp atomic write
+        rc = -4;
+        break;
+      }
       int ncol = S + ghost;
       /* gradient rows of Abar, rescaled from the scaled basis (App. B) */
       for (int i = 0; i < ncol; ++i)
@@ -1237,13 +1256,26 @@ int orc_prepare(orc_mesh* m, int64_t nsub, const int64_t* cells) {
           m->fco[((sl * Q + q) * (S + 1) + i) * 3 + a] = Abar[(1 + a) * ncol + i] / h;
     }
   }
-  for (int64_t c = 0; c < m->nc && rc == 0; ++c) {
+#pragma omp for schedule(dynamic, 8)
+  for (int64_t c = 0; c < m->nc; ++c) {
     int64_t sl = m->cslot[c];
     if (sl < 0) continue;
+    int err;
+#pragma omp atomic read
+    err = rc;
+    if (err) continue;
     int64_t* st = m->cst + sl * S;
-    if (stencil_search(m, &B, m->xc + 3 * c, st)) { rc = -3; break; }
+    if (stencil_search(m, &B, m->xc + 3 * c, st)) {
+#pragma omp atomic write
+      rc = -3;
+      continue;
+    }
     double h;
-    if (reconstruct(m, m->xc + 3 * c, st, 0, Abar, &h, &m->ccond[sl])) { rc = -4; break; }
+    if (reconstruct(m, m->xc + 3 * c, st, 0, Abar, &h, &m->ccond[sl])) {
+#pragma omp atomic write
+      rc = -4;
+      continue;
+    }
     /* extrapolation to each face centre, eq. (alphaJump): the Taylor terms
        of order 1..p evaluated at d_Pf, applied to the derivative rows */
     for (int lf = 0; lf < nlf; ++lf) {
@@ -1261,8 +1293,21 @@ int orc_prepare(orc_mesh* m, int64_t nsub, const int64_t* cells) {
   }
   free(Abar);
   free(pts);
+  }
   free_buckets(&B);
   return rc;
+}
+
+/* threads of the parallel loops (0: OpenMP's default); returns the count in
+   use, 1 when built without OpenMP */
+int orc_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
 }
 
 int orc_face_slot(const orc_mesh* m, int64_t f) { return m->fslot ? (int)m->fslot[f] : -1; }
@@ -1453,9 +1498,13 @@ int orc_residual(const orc_mesh* m, int law, double mu, double lam, const double
                  const double* bsrc, int64_t nsub, const int64_t* cells, double* R) {
   int d = m->dim, nlf = m->nlf;
   int64_t ns = nsub < 0 ? m->nc : nsub;
+  for (int64_t s = 0; s < ns; ++s)
+    if (m->cslot[nsub < 0 ? s : cells[s]] < 0) return -1;
+  /* cells are independent: each thread takes whole cells (OpenMP when built
+     with it; the arithmetic of a cell does not depend on the thread count) */
+#pragma omp parallel for schedule(dynamic, 16)
   for (int64_t s = 0; s < ns; ++s) {
     int64_t c = nsub < 0 ? s : cells[s];
-    if (m->cslot[c] < 0) return -1;
     double r[3] = {0, 0, 0}, fl[3];
     for (int lf = 0; lf < nlf; ++lf) {
       int64_t f = m->cf[c * nlf + lf];
@@ -1473,6 +1522,7 @@ int orc_residual(const orc_mesh* m, int law, double mu, double lam, const double
    face-level quantities); flux [nf][3] filled for prepared faces only */
 int orc_face_fluxes(const orc_mesh* m, int law, double mu, double lam, const double* u,
                     const double* ubq, const double* ubf, const double* tbq, double* flux) {
+#pragma omp parallel for schedule(dynamic, 64)
   for (int64_t f = 0; f < m->nf; ++f) {
     if (m->ftag[f] != 1 && m->fslot[f] < 0) continue;
     face_flux(m, f, law, mu, lam, u, ubq, ubf, tbq, flux + 3 * f);

@@ -80,6 +80,7 @@ DevMesh dev_mesh(const hofv_ctx* c) {
   m.gcache = c->d_gcache;
   m.tcache = c->d_tcache;
   m.kerr = c->d_bar ? c->d_bar + 3 : nullptr;
+  m.fcsum = c->d_fcsum;
   return m;
 }
 
@@ -169,6 +170,7 @@ static void free_built(hofv_ctx* c) {
   c->d_su = c->d_sv = nullptr;
   c->d_ustar_v = c->d_vext = nullptr;
   c->d_gcache = c->d_tcache = nullptr;
+  c->d_fcsum = nullptr;
   c->jv_u = c->jv_R = nullptr;
   c->jv_cur++;
   c->d_count = nullptr;
@@ -192,6 +194,8 @@ static int coef_format(hofv_ctx* c, int to_df) {
   const int64_t ncex = c->nctile * c->S * kTile * c->nlf;
   launch_coef_format(c->d_fco, nfco, to_df, c->stream);
   launch_coef_format(c->d_cex, ncex, to_df, c->stream);
+  c->prec = to_df ? HOFV_PREC_DF64 : HOFV_PREC_FP64;  // the arrays' format from here on
+  if (to_df) launch_row_sums(dev_mesh(c), c->d_fcsum, c->stream);
   HOFV_CUDA(c, cudaGetLastError());
   HOFV_CUDA(c, cudaStreamSynchronize(c->stream));
   return 0;
@@ -325,6 +329,9 @@ int hofv_create(hofv_ctx** out, int device, void* stream) {
   if (cudaSetDevice(device) != cudaSuccess) return HOFV_ECUDA;
   hofv_ctx* c = new hofv_ctx();
   c->device = device;
+  if (cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+      c->sm_count < 1)
+    c->sm_count = 1;
   c->stream = static_cast<cudaStream_t>(stream);
   // default arithmetic of the gradient contraction
   const char* pe = getenv("HOFV_PRECISION");
@@ -735,13 +742,14 @@ int hofv_build_stencils(hofv_ctx* c) {
   TRY(dev_alloc(c, &c->d_su, (nc + c->ng) * split4(d)));
   TRY(dev_alloc(c, &c->d_sv, (nc + c->ng) * split4(d)));
   TRY(dev_alloc(c, &c->d_ustar_v, nc * nlf * d));
+  TRY(dev_alloc(c, &c->d_fcsum, std::max<int64_t>(c->nftile, 1) * kTile * R));
   if (c->ng > 0) TRY(dev_alloc(c, &c->d_vext, (nc + c->ng) * d));
   {
     const int e = setup_df_kernels();
     if (e != 0) return cuda_fail(c, (cudaError_t)e, "cudaFuncSetAttribute(face kernels)");
   }
   if (c->prec == HOFV_PREC_DF64) TRY(coef_format(c, 1));
-  c->red_blocks = 4 * 152;
+  c->red_blocks = 4 * c->sm_count;
   TRY(dev_alloc(c, &c->d_red, (int64_t)c->red_blocks * 128));
   TRY(dev_alloc(c, &c->d_count, 256));
   TRY(dev_alloc(c, &c->d_scal, 256));
@@ -1735,4 +1743,213 @@ extern "C" int hofv_nej_apply(hofv_ctx* c, const double* x, double* y) {
   if (!x || !y) return hofv::fail(c, HOFV_EINVAL, "null vector");
   TRY(hofv::nej_apply(c, x, y));
   return HOFV_OK;
+}
+
+// ---------------------------------------------------------------------
+// caller-supplied stencils, solver preparation, load path
+// ---------------------------------------------------------------------
+namespace hofv {
+
+// tiled stencil arrays [tiles][S][kTile] <-> row-major [count][S]
+static void tile_rows(const int32_t* rows, int64_t count, int S, std::vector<int32_t>& tiled) {
+  const int64_t tiles = (count + kTile - 1) / kTile;
+  tiled.assign((size_t)std::max<int64_t>(tiles, 1) * S * kTile, 0);
+  for (int64_t i = 0; i < count; ++i)
+    for (int n = 0; n < S; ++n)
+      tiled[((i / kTile) * S + n) * kTile + i % kTile] = rows[i * S + n];
+}
+
+// recompute everything derived from the stencils: reconstruction
+// coefficients and stabilisation weights, their double-float form, the cell
+// averages of the inertia term, the contracted matrices; the near-exact
+// Jacobian (built from them) is rebuilt on its next use
+static int rebuild_from_stencils(hofv_ctx* c) {
+  invalidate_graphs(c);
+  jv_invalidate(c);
+  TRY(run_lsq(c));
+  if (c->prec == HOFV_PREC_DF64) TRY(coef_format(c, 1));
+  if (c->d_cmass) TRY(run_cell_mass(c));
+  c->tco_valid = false;
+  nej_release(c);
+  TRY(build_contraction(c));
+  return refresh_source(c);
+}
+
+}  // namespace hofv
+
+extern "C" int hofv_set_stencils(hofv_ctx* c, const int32_t* face_stencils,
+                                 const int32_t* cell_stencils) {
+  if (!c) return HOFV_EINVAL;
+  if (!c->built) return fail(c, HOFV_ESTATE, "hofv_build_stencils must come first");
+  if (c->nfy > 0)
+    return fail(c, HOFV_ENOTSUP, "stencils cannot be replaced on meshes with symmetry faces");
+  const int S = c->S;
+  auto check = [&](const int32_t* rows, int64_t count) -> bool {
+    for (int64_t i = 0; i < count * S; ++i)
+      if (rows[i] < 0 || rows[i] >= c->nc) return false;
+    return true;
+  };
+  if ((face_stencils && !check(face_stencils, c->nfid)) ||
+      (cell_stencils && !check(cell_stencils, c->nc)))
+    return fail(c, HOFV_EINVAL, "stencil cell id out of range");
+  HOFV_CUDA(c, cudaSetDevice(c->device));
+  const size_t nfst = (size_t)std::max<int64_t>(c->nftile, 1) * S * kTile;
+  const size_t ncst = (size_t)c->nctile * S * kTile;
+  std::vector<int32_t> old_f(nfst), old_c(ncst), t;
+  HOFV_CUDA(c, cudaMemcpy(old_f.data(), c->d_fst, sizeof(int32_t) * nfst, cudaMemcpyDeviceToHost));
+  HOFV_CUDA(c, cudaMemcpy(old_c.data(), c->d_cst, sizeof(int32_t) * ncst, cudaMemcpyDeviceToHost));
+  if (face_stencils) {
+    tile_rows(face_stencils, c->nfid, S, t);
+    HOFV_CUDA(c, cudaMemcpy(c->d_fst, t.data(), sizeof(int32_t) * nfst, cudaMemcpyHostToDevice));
+  }
+  if (cell_stencils) {
+    tile_rows(cell_stencils, c->nc, S, t);
+    HOFV_CUDA(c, cudaMemcpy(c->d_cst, t.data(), sizeof(int32_t) * ncst, cudaMemcpyHostToDevice));
+  }
+  const int rc = rebuild_from_stencils(c);
+  if (rc < 0) {  // keep the context usable: back to the previous stencils
+    const std::string msg = c->err;
+    cudaMemcpy(c->d_fst, old_f.data(), sizeof(int32_t) * nfst, cudaMemcpyHostToDevice);
+    cudaMemcpy(c->d_cst, old_c.data(), sizeof(int32_t) * ncst, cudaMemcpyHostToDevice);
+    rebuild_from_stencils(c);
+    return fail(c, rc, msg + " (previous stencils restored)");
+  }
+  return HOFV_OK;
+}
+
+extern "C" int hofv_prepare_solver(hofv_ctx* c, const hofv_solve_opts* opts) {
+  TRY(check_eval(c));
+  hofv_solve_opts o;
+  hofv_default_opts(&o);
+  if (opts) o = *opts;
+  if (o.restart < 1 || o.restart > 100 || o.precond < HOFV_PC_NONE || o.precond > HOFV_PC_NEJ)
+    return fail(c, HOFV_EINVAL, "bad solver options");
+  HOFV_CUDA(c, cudaSetDevice(c->device));
+  TRY(ensure_krylov(c, o.restart));
+  if (o.precond == HOFV_PC_AJMG || o.precond == HOFV_PC_NEJ) TRY(mg_ensure(c));
+  if (o.precond == HOFV_PC_NEJ) {
+    if (c->mat.law != HOFV_LAW_LINEAR)
+      return fail(c, HOFV_ENOTSUP, "the near-exact Jacobian is defined for the linear law");
+    TRY(ensure_tco(c));
+    TRY(nej_prepare(c, o.inner_iters));
+  }
+  TRY(ensure_jv_storage(c));
+  HOFV_CUDA(c, cudaStreamSynchronize(c->stream));
+  return HOFV_OK;
+}
+
+extern "C" int hofv_solve_load_path(hofv_ctx* c, double* u, const double* u_bq1,
+                                    const double* u_bf1, const double* t_bq1, const double* body1,
+                                    const double* du_dlambda, int32_t n_steps,
+                                    int32_t max_halvings, const hofv_solve_opts* opts,
+                                    hofv_stats* stats, int32_t* steps_done) {
+  TRY(check_eval(c));
+  if (!u) return fail(c, HOFV_EINVAL, "null vector");
+  if (n_steps < 1 || n_steps > 1000000 || max_halvings < 0 || max_halvings > 30)
+    return fail(c, HOFV_EINVAL, "bad step count or halving limit");
+  const auto t0 = std::chrono::steady_clock::now();
+  const int d = c->dim;
+  const int64_t n = c->nc * d;
+  // data at load factors 0 (the context's current data) and 1; state before
+  // the increment; previous converged state (secant predictor)
+  const int64_t nbq = c->nfd * c->Q * d, nbf = c->nfd * d, ntq = c->nft * c->Q * d, nbd = n;
+  const int64_t ndat = nbq + nbf + ntq + nbd;
+  double* buf = nullptr;
+  HOFV_CUDA(c, cudaMalloc(&buf, sizeof(double) * (2 * ndat + 3 * n + 1)));
+  double* d0 = buf;
+  double* d1 = buf + ndat;
+  double* u_last = d1 + ndat;   // last converged state
+  double* u_prev = u_last + n;  // the one before (secant predictor)
+  double* u_try = u_prev + n;
+  struct Part { double* ctxp; const double* one; int64_t off, cnt; };
+  const Part parts[4] = {{c->d_ubq, u_bq1, 0, nbq},
+                         {c->d_ubf, u_bf1, nbq, nbf},
+                         {c->d_tbq, t_bq1, nbq + nbf, ntq},
+                         {c->d_body, body1, nbq + nbf + ntq, nbd}};
+  int rc = 0;
+  auto cu = [&](cudaError_t e, const char* what) {
+    if (e != cudaSuccess && rc == 0) rc = cuda_fail(c, e, what);
+  };
+  for (const Part& p : parts) {
+    if (p.cnt <= 0) continue;
+    cu(cudaMemcpyAsync(d0 + p.off, p.ctxp, sizeof(double) * p.cnt, cudaMemcpyDeviceToDevice,
+                       c->stream), "load path: copy of the initial data");
+    cu(cudaMemcpyAsync(d1 + p.off, p.one ? p.one : p.ctxp, sizeof(double) * p.cnt,
+                       cudaMemcpyDeviceToDevice, c->stream), "load path: copy of the final data");
+  }
+  cu(cudaMemcpyAsync(u_last, u, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream),
+     "load path: state copy");
+  auto set_data = [&](double lam) -> int {  // data(lam) = (1 - lam) d0 + lam d1
+    for (const Part& p : parts)
+      if (p.cnt > 0)
+        launch_combine4(p.cnt, 1.0 - lam, d0 + p.off, lam, d1 + p.off, 0.0, nullptr, 0.0, nullptr,
+                        p.ctxp, c->stream);
+    HOFV_CUDA(c, cudaGetLastError());
+    jv_invalidate(c);
+    return refresh_source(c);
+  };
+  hofv_stats tot;
+  memset(&tot, 0, sizeof(tot));
+  const double nominal = 1.0 / n_steps;
+  double lam = 0.0, dlam = nominal, dlam_prev = 0.0;
+  int halvings = 0, accepted = 0;
+  int status = HOFV_OK;
+  while (rc == 0 && lam < 1.0 - 1e-15) {
+    const double step = std::min(dlam, 1.0 - lam);
+    rc = set_data(lam + step);
+    if (rc) break;
+    // predictor: the caller's direction per unit load factor, else the
+    // secant through the last two converged states, else the last state
+    if (du_dlambda)
+      launch_combine4(n, 1.0, u_last, step, du_dlambda, 0.0, nullptr, 0.0, nullptr, u_try,
+                      c->stream);
+    else if (accepted > 0 && dlam_prev > 0.0)
+      launch_combine4(n, 1.0 + step / dlam_prev, u_last, -step / dlam_prev, u_prev, 0.0, nullptr,
+                      0.0, nullptr, u_try, c->stream);
+    else
+      cu(cudaMemcpyAsync(u_try, u_last, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream),
+         "load path: predictor");
+    if (rc) break;
+    hofv_stats st;
+    memset(&st, 0, sizeof(st));
+    const int s = hofv_newton_solve(c, u_try, opts, &st);
+    tot.newton_iters += st.newton_iters;
+    tot.krylov_iters += st.krylov_iters;
+    tot.residual_evals += st.residual_evals;
+    tot.precond_applies += st.precond_applies;
+    tot.gnn_fallbacks += st.gnn_fallbacks;
+    if (accepted == 0 && halvings == 0) tot.r0 = st.r0;
+    tot.r_final = st.r_final;
+    if (s == HOFV_OK) {
+      cu(cudaMemcpyAsync(u_prev, u_last, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream),
+         "load path: state copy");
+      cu(cudaMemcpyAsync(u_last, u_try, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream),
+         "load path: state copy");
+      lam += step;
+      dlam_prev = step;
+      ++accepted;
+      halvings = 0;
+      dlam = std::min(nominal, 2.0 * dlam);  // grow back after a halved increment
+    } else if (s == HOFV_WNOTCONV || s == HOFV_ENAN) {
+      if (halvings >= max_halvings) {
+        status = HOFV_WNOTCONV;
+        fail(c, HOFV_WNOTCONV, "load path: an increment failed after the allowed halvings");
+        break;
+      }
+      ++halvings;
+      dlam = 0.5 * step;
+    } else {
+      rc = s;  // a hard error of the solver
+    }
+  }
+  if (rc == 0 && status != HOFV_OK) rc = set_data(lam);  // the data of the state returned
+  cu(cudaMemcpyAsync(u, u_last, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream),
+     "load path: result copy");
+  cu(cudaStreamSynchronize(c->stream), "load path: synchronisation");
+  cudaFree(buf);
+  if (steps_done) *steps_done = accepted;
+  tot.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  tot.status = rc ? rc : status;
+  if (stats) *stats = tot;
+  return rc ? rc : status;
 }

@@ -615,7 +615,7 @@ int ensure(hofv_ctx* c, Gnn** out) {
   g->off_Wd = o; o += (int64_t)c->dim * GH;
   g->off_bd = o; o += c->dim;
   g->P = o;
-  g->gblocks = 2 * 152;
+  g->gblocks = 2 * c->sm_count;
   HOFV_CUDA(c, cudaFuncSetAttribute(k_gnn_layer_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     kLayerBwdSmem));
   int rc = 0;

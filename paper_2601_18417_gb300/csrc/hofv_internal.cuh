@@ -58,8 +58,8 @@ struct DevMesh {
   // 8-byte slot of fco and cex holds a double-float pair (float hi, float lo),
   // and the state is split into such pairs before the contraction
   int prec;
-  float4* su;             // [wst][kSplit4] split state (scratch)
-  float4* sv;             // [wst][kSplit4] split Jv direction (scratch)
+  float4* su;             // [wst][dim] split state (scratch): (hi, mid, lo, 0) per component
+  float4* sv;             // [wst][dim] split Jv direction (scratch)
   double* ustar_v;        // [nc][nlf][dim] extrapolated values of the Jv direction (scratch)
   double* vext;           // [dim][wst] extended Jv direction (symmetry faces; scratch)
   // linearisation of the neo-Hookean law at u for the double-float Jv:
@@ -67,10 +67,13 @@ struct DevMesh {
   double* gcache;         // [nftile * kTile][R][dim]
   double* tcache;         // [nftile * kTile][Q][dim]
   unsigned int* kerr;     // set to 1 by a face kernel whose bounded wait ran out
+  const double* fcsum;    // [nftile * kTile][R] sums over the stencil of the stored
+                          // (double-float) gradient coefficients of each row
 };
 
-// float4 slots per cell of a split state: (h0, l0, h1, l1) [, (h2, l2, 0, 0)]
-__host__ __device__ constexpr int split4(int dim) { return dim == 2 ? 1 : 2; }
+// float4 slots per cell of a split state: one per component, the value
+// split exactly into three floats (hi, mid, lo, 0), hi + mid + lo = value
+__host__ __device__ constexpr int split4(int dim) { return dim; }
 
 struct Material {
   int law;
@@ -81,6 +84,7 @@ struct Material {
 
 struct hofv_ctx {
   int device = 0;
+  int sm_count = 1;                 // streaming multiprocessors of the device
   cudaStream_t stream = nullptr;
   std::string err;
   // ---- mesh (host) ----
@@ -146,6 +150,7 @@ struct hofv_ctx {
   float4* d_su = nullptr;           // [nc + ng][split4] split state
   float4* d_sv = nullptr;           // [nc + ng][split4] split Jv direction
   double* d_ustar_v = nullptr;      // [nc][nlf][dim]
+  double* d_fcsum = nullptr;        // [nftile * kTile][R] row sums of the stored coefficients
   double* d_vext = nullptr;         // [dim][nc + ng]
   // neo-Hookean double-float Jv: face gradients and tractions at u, valid
   // for the state / residual pair (jv_u, jv_R) while jv_gen == jv_cur
@@ -280,6 +285,9 @@ void launch_jv_cache_fill(const DevMesh& m, const Material& mat, const double* u
 // hi + lo its value rounded to 48 significant bits; to_df == 0 turns the pairs
 // back into doubles (exactly)
 void launch_coef_format(double* a, int64_t n, int to_df, cudaStream_t st);
+// fcsum[f][r] = sum over the stencil slots of the stored coefficient of face
+// f, row r (double-float pairs summed in FP64, in slot order)
+void launch_row_sums(const DevMesh& m, double* fcsum, cudaStream_t st);
 // raises the dynamic shared-memory limit of the double-float face kernels
 // (once per process, at set-up); 0 or a cudaError_t
 int setup_df_kernels();
@@ -343,6 +351,8 @@ int ensure_tco(hofv_ctx* c);
 int nej_ensure(hofv_ctx* c);
 int nej_apply(hofv_ctx* c, const double* x, double* y);
 int nej_precondition(hofv_ctx* c, int iters, const double* v, double* z);
+// the structure, values and inner-solver storage for `iters` inner iterations
+int nej_prepare(hofv_ctx* c, int iters);
 void nej_release(hofv_ctx* c);
 
 // ---- learned preconditioner (gnn.cu) ----

@@ -264,6 +264,11 @@ int nej_apply(hofv_ctx* c, const double* x, double* y) {
 // z ~= NEJ^-1 v: `iters` GMRES iterations from z = 0, right-preconditioned
 // by one multigrid V-cycle of the approximate Jacobian, classical
 // Gram-Schmidt twice, Givens rotations on the host.
+int nej_prepare(hofv_ctx* c, int iters) {
+  NEJ_TRY(nej_ensure(c));
+  return ensure_inner(c, get(c), std::max(1, std::min(iters, 30)));
+}
+
 int nej_precondition(hofv_ctx* c, int iters, const double* v, double* z) {
   NEJ_TRY(nej_ensure(c));
   NEJ_TRY(mg_ensure(c));

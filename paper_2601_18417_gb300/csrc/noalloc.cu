@@ -19,8 +19,8 @@
 //     hexes, 8 for polygons), rounded up to a multiple of 32, plus
 //     (internal + displacement + symmetry faces) * dim for the fluxes,
 //     rounded up to 32, plus, with HOFV_PREC_DF64, (n_cells + mirror nodes)
-//     * 4 (2-D) or 8 (3-D) for the split state.  Larger meshes are rejected
-//     with HOFV_EINVAL.
+//     * 4 (2-D) or 6 (3-D) for the split state, rounded up to 32.  Larger
+//     meshes are rejected with HOFV_EINVAL.
 //   - All calls share the one array: calls whose work overlaps on the GPU
 //     (other streams, other threads, other contexts on the same device) race
 //     on it and must be serialised by the caller.  Like every evaluation

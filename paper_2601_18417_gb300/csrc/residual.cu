@@ -706,19 +706,15 @@ __device__ __forceinline__ void ff_mac(float ch, float cl, float uh, float ul, f
 
 __device__ __forceinline__ double ff_value(float s, float e) { return (double)s + (double)e; }
 
-// split state of cell `id`: (h0, l0, h1, l1) [, (h2, l2, 0, 0)]
+// split state of cell `id` as double-float pairs (hi, mid): 48 bits
 template <int DIM>
 __device__ __forceinline__ void ld_split(const float4* __restrict__ p, int32_t id, float (&h)[DIM],
                                          float (&l)[DIM]) {
-  const float4 a = __ldg(p + (int64_t)id * split4(DIM));
-  h[0] = a.x;
-  l[0] = a.y;
-  h[1] = a.z;
-  l[1] = a.w;
-  if constexpr (DIM == 3) {
-    const float4 b = __ldg(p + (int64_t)id * 2 + 1);
-    h[2] = b.x;
-    l[2] = b.y;
+#pragma unroll
+  for (int j = 0; j < DIM; ++j) {
+    const float4 a = __ldg(p + (int64_t)id * DIM + j);
+    h[j] = a.x;
+    l[j] = a.y;
   }
 }
 
@@ -727,16 +723,41 @@ __device__ __forceinline__ void split_value(double a, float& h, float& l) {
   l = __double2float_rn(a - (double)h);  // a - h is exact in FP64
 }
 
-// n cells of a state read with stride ws -> split pairs
+// a double as hi + mid + lo, three floats, exactly (24 + 24 bits, then the
+// at most 5 remaining significant bits)
+__device__ __forceinline__ float4 split3(double a) {
+  const float h = __double2float_rn(a);
+  const double r = a - (double)h;  // exact
+  const float m = __double2float_rn(r);
+  return make_float4(h, m, __double2float_rn(r - (double)m), 0.f);
+}
+
+// n cells of a state read with stride ws -> three-float splits
 template <int DIM>
 __global__ void k_split(int64_t n, int64_t ws, const double* __restrict__ u, float4* __restrict__ su) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
-  float h[3] = {0.f, 0.f, 0.f}, l[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-  for (int j = 0; j < DIM; ++j) split_value(u[j * ws + i], h[j], l[j]);
-  su[i * split4(DIM)] = make_float4(h[0], l[0], h[1], l[1]);
-  if constexpr (DIM == 3) su[i * 2 + 1] = make_float4(h[2], l[2], 0.f, 0.f);
+  for (int j = 0; j < DIM; ++j) su[i * DIM + j] = split3(u[j * ws + i]);
+}
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float z = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z));
+}
+
+// x - r from their three-float splits as a double-float pair: the high and
+// middle differences exactly (TwoSum), the low parts' difference rounded
+// once (2^-72 of the values), renormalised
+__device__ __forceinline__ float2 diff3(const float4 x, const float4 r) {
+  float s1, e1, s2, e2, h, e3;
+  two_sum(x.x, -r.x, s1, e1);
+  two_sum(x.y, -r.y, s2, e2);
+  two_sum(s1, s2, h, e3);
+  const float l = __fadd_rn(e3, __fadd_rn(e1, __fadd_rn(e2, __fsub_rn(x.z, r.z))));
+  const float dh = __fadd_rn(h, l);
+  return make_float2(dh, __fsub_rn(l, __fsub_rn(dh, h)));
 }
 
 __global__ void k_coef_format(double* __restrict__ a, int64_t n, int to_df) {
@@ -755,9 +776,30 @@ __global__ void k_coef_format(double* __restrict__ a, int64_t n, int to_df) {
   }
 }
 
+// fcsum[f][r] = sum_n of the stored pair of face f, row r, slot n
+__global__ void k_row_sums(DevMesh m, double* __restrict__ fcsum) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;  // (face, row)
+  const int R = m.R;
+  if (e >= m.nftile * kTile * R) return;
+  const int64_t tile = e / (kTile * R);
+  const int k = (int)(e % (kTile * R));  // fi * R + r within the tile
+  const float2* co = reinterpret_cast<const float2*>(m.fco) + tile * (int64_t)m.S * kTile * R + k;
+  double sum = 0.0;
+  for (int n = 0; n < m.S; ++n) {
+    const float2 p = co[(int64_t)n * kTile * R];
+    sum += ff_value(p.x, p.y);
+  }
+  fcsum[e] = sum;
+}
+
+void launch_row_sums(const DevMesh& m, double* fcsum, cudaStream_t st) {
+  const int64_t n = m.nftile * kTile * m.R;
+  if (n > 0) k_row_sums<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(m, fcsum);
+}
+
 void launch_coef_format(double* a, int64_t n, int to_df, cudaStream_t st) {
   if (n <= 0) return;
-  const unsigned g = (unsigned)std::min<int64_t>((n + 255) / 256, 152 * 64);
+  const unsigned g = (unsigned)std::min<int64_t>((n + 255) / 256, int64_t{1} << 16);  // grid-stride
   k_coef_format<<<g, 256, 0, st>>>(a, n, to_df);
 }
 
@@ -817,45 +859,57 @@ __device__ __forceinline__ void cp_async_wait_all() {
 
 // Face fluxes, double-float gradient rows.  QD Gauss points per face
 // (R = QD * DIM rows), FPB faces per block (BPT = 32 / FPB blocks per tile),
-// blockDim = FPB * R; sw is the split state contracted (u, or v in the Jv
-// modes) and ws its extrapolated values.
+// blockDim = FPB * R; sw is the three-float split of the state contracted
+// (u, or v in the Jv modes), wd the same state in FP64 and ws its
+// extrapolated values.
 //
-// The block first gathers the split values of all its faces' stencil cells
-// into shared memory (16-byte asynchronous copies, [S][FPB] entries), so
-// that the contraction reads them from shared memory (the R threads of a
-// face share each entry).  Each thread then streams its coefficient row
-// through a ring of RING registers: the coefficient of slot n + RING is
-// requested when slot n is consumed, keeping RING coalesced 8-byte loads in
-// flight per thread; with R a compile-time constant every ring offset is an
-// immediate.  In 3-D a block takes half a tile so that several blocks share
-// an SM and the FP32 contraction of one overlaps the FP64 law of another.
+// Each gradient is contracted against the differences to a reference cell,
+// the face's nearest stencil cell N0:
+//   sum_N c_N w_N = sum_N c_N (w_N - w_N0) + w_N0 sum_N c_N,
+// an exact identity; the differences are small where the field is smooth,
+// so the 2^-48 relative representation error of the coefficients acts on
+// them and not on |w| (on fine meshes |w| exceeds h |grad w| by orders of
+// magnitude), and the last term is one FP64 product with the FP64 row sum
+// of the stored coefficients.  The block first gathers its faces' stencil
+// cells' splits into shared memory (16-byte asynchronous copies, [S][FPB]
+// entries) and turns each into the double-float difference to its face's
+// reference (exact differences of the splits); the contraction then reads
+// them from shared memory (the R threads of a face share each entry).  Each
+// thread streams its coefficient row through a ring of RING registers: the
+// coefficient of slot n + RING is requested when slot n is consumed, keeping
+// RING coalesced 8-byte loads in flight per thread; with R a compile-time
+// constant every ring offset is an immediate.  In 3-D a block takes half a
+// tile so that two blocks share an SM and the FP32 contraction of one
+// overlaps the FP64 law of the other.
 template <int DIM>
 struct DfShape {
   static constexpr int FPB = DIM == 3 ? 16 : 32;   // faces per block
   static constexpr int RING = DIM == 3 ? 8 : 4;    // coefficient loads in flight per thread
 };
 
-// dynamic shared memory: the gathered cell values, reused after the
-// contraction for the gradients and tractions of phases 2 and 3
+// dynamic shared memory: the gathered cell values and the faces' references,
+// reused after the contraction for the gradients and tractions of phases 2-3
 template <int DIM>
 static size_t df_smem_bytes(int S, int R, int Q) {
   constexpr int FPB = DfShape<DIM>::FPB;
-  const size_t gath = (size_t)S * FPB * split4(DIM) * 16;
+  const size_t gath = (size_t)(S + 1) * FPB * DIM * 16;
   const size_t law = (size_t)FPB * (R * DIM + Q * DIM) * sizeof(double);
   return gath > law ? gath : law;
 }
 
 template <int DIM, int LAW, int MODE, int QD>
 __global__ void __launch_bounds__(DfShape<DIM>::FPB * QD * DIM, DIM == 3 ? 2 : 6)
-    k_flux_df(DevMesh m, Material mt, const float4* __restrict__ sw, const double* __restrict__ ws,
-              const double* __restrict__ ubq, const double* __restrict__ ubf,
-              const double* __restrict__ d_eps, double* __restrict__ flux) {
+    k_flux_df(DevMesh m, Material mt, const float4* __restrict__ sw, const double* __restrict__ wd,
+              const double* __restrict__ ws, const double* __restrict__ ubq,
+              const double* __restrict__ ubf, const double* __restrict__ d_eps,
+              double* __restrict__ flux) {
   constexpr int FPB = DfShape<DIM>::FPB, BPT = kTile / FPB, Q = QD, R = QD * DIM;
-  constexpr int kRing = DfShape<DIM>::RING, SP4 = split4(DIM);
+  constexpr int kRing = DfShape<DIM>::RING;
   constexpr int CS = kTile * R;  // coefficient stride between stencil slots
   extern __shared__ __align__(16) double sm[];
   const int S = m.S;
-  float4* us = reinterpret_cast<float4*>(sm);  // [S][FPB][SP4] gathered split values
+  float4* us = reinterpret_cast<float4*>(sm);  // [S][FPB][DIM] gathered values, then differences
+  float4* ur = us + (size_t)S * FPB * DIM;     // [FPB][DIM] the faces' reference values
   double* Gs = sm;                              // [FPB][R][DIM] after the contraction
   double* Ts = sm + FPB * R * DIM;              // [FPB][Q][DIM]
   const int64_t tile = blockIdx.x / BPT;
@@ -865,35 +919,38 @@ __global__ void __launch_bounds__(DfShape<DIM>::FPB * QD * DIM, DIM == 3 ? 2 : 6
   const double eps = MODE == kDfJv ? __ldg(d_eps) : 0.0;
   const int fi = it / R, r = it % R;
   const int64_t f = f0 + fi;
+  const int32_t* __restrict__ st = m.fst + tile * (int64_t)S * kTile + fb;
   const float2* __restrict__ co =
       reinterpret_cast<const float2*>(m.fco) + tile * (int64_t)S * CS + fb * R + it;
   // the first coefficients of the ring, then the gather of the cell values
   float2 cq[kRing];
 #pragma unroll
   for (int d = 0; d < kRing; ++d) cq[d] = d < S ? __ldg(co + d * CS) : make_float2(0.f, 0.f);
-  {
-    const int32_t* __restrict__ st = m.fst + tile * (int64_t)S * kTile + fb;
-    for (int t = it; t < S * FPB; t += FPB * R) {
-      const int n = t / FPB, fj = t % FPB;
-      const int32_t id = __ldg(st + n * kTile + fj);
+  for (int t = it; t < S * FPB; t += FPB * R) {
+    const int n = t / FPB, fj = t % FPB;
+    const int32_t id = __ldg(st + n * kTile + fj);
 #pragma unroll
-      for (int h = 0; h < SP4; ++h) cp_async16(us + t * SP4 + h, sw + (int64_t)id * SP4 + h);
-    }
-    cp_async_wait_all();
+    for (int h = 0; h < DIM; ++h) cp_async16(us + t * DIM + h, sw + (int64_t)id * DIM + h);
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  for (int t = it; t < FPB * DIM; t += FPB * R) ur[t] = us[t];  // slot 0: the nearest cell
+  __syncthreads();
+  for (int t = it; t < S * FPB * DIM; t += FPB * R) {
+    const float2 dv = diff3(us[t], ur[t % (FPB * DIM)]);
+    us[t] = make_float4(dv.x, dv.y, 0.f, 0.f);
   }
   __syncthreads();
-  // (1) gradient rows: thread (fi, r) accumulates sum_N c_{r,N} w_N
+  // (1) gradient rows: thread (fi, r) accumulates sum_N c_{r,N} (w_N - w_N0)
   float s[DIM], e[DIM];
 #pragma unroll
   for (int j = 0; j < DIM; ++j) s[j] = e[j] = 0.f;
-  const float4* __restrict__ uf = us + fi * SP4;
+  const float4* __restrict__ uf = us + fi * DIM;
   auto mac_slot = [&](int n, float2 c) {
-    const float4 a = uf[n * FPB * SP4];
-    ff_mac(c.x, c.y, a.x, a.y, s[0], e[0]);
-    ff_mac(c.x, c.y, a.z, a.w, s[1], e[1]);
-    if constexpr (DIM == 3) {
-      const float4 b = uf[n * FPB * SP4 + 1];
-      ff_mac(c.x, c.y, b.x, b.y, s[2], e[2]);
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) {
+      const float4 a = uf[n * FPB * DIM + j];
+      ff_mac(c.x, c.y, a.x, a.y, s[j], e[j]);
     }
   };
   int n0 = 0;
@@ -919,9 +976,13 @@ __global__ void __launch_bounds__(DfShape<DIM>::FPB * QD * DIM, DIM == 3 ? 2 : 6
   }
   __syncthreads();  // the gathered values are overwritten by the gradients below
   {
+    // + w_N0 sum_N c_N, in FP64
+    const int32_t id0 = __ldg(st + fi);
+    const int64_t ldw = m.wst;
+    const double cs = m.fcsum[f * R + r];
     double g[DIM];
 #pragma unroll
-    for (int j = 0; j < DIM; ++j) g[j] = ff_value(s[j], e[j]);
+    for (int j = 0; j < DIM; ++j) g[j] = fma(cs, __ldg(wd + j * ldw + id0), ff_value(s[j], e[j]));
     if (MODE == kDfResidual || MODE == kDfFill) {
       if (f >= m.nfi && f < m.nfid) {  // ghost node of a displacement face (prescribed data)
         const int64_t fd = f - m.nfi;
@@ -1083,31 +1144,32 @@ static void launch_ustar_df(const DevMesh& m, const float4* sw, const double* w,
 
 template <int DIM, int LAW, int MODE, int QD>
 static void launch_flux_df_q(const DevMesh& m, const Material& mat, const float4* sw,
-                             const double* ws, const double* ubq, const double* ubf,
-                             const double* d_eps, double* flux, cudaStream_t st) {
+                             const double* wd, const double* ws, const double* ubq,
+                             const double* ubf, const double* d_eps, double* flux,
+                             cudaStream_t st) {
   using SH = DfShape<DIM>;
   const size_t smem = df_smem_bytes<DIM>(m.S, QD * DIM, QD);
   k_flux_df<DIM, LAW, MODE, QD><<<(unsigned)(m.nftile * (kTile / SH::FPB)), SH::FPB * QD * DIM,
-                                  smem, st>>>(m, mat, sw, ws, ubq, ubf, d_eps, flux);
+                                  smem, st>>>(m, mat, sw, wd, ws, ubq, ubf, d_eps, flux);
 }
 
 // Gauss points per face: q^(d-1) for q = 1..4 in 2-D, 1..3 in 3-D
 template <int DIM, int LAW, int MODE>
 static void launch_flux_df(const DevMesh& m, const Material& mat, const float4* sw,
-                           const double* ws, const double* ubq, const double* ubf,
-                           const double* d_eps, double* flux, cudaStream_t st) {
+                           const double* wd, const double* ws, const double* ubq,
+                           const double* ubf, const double* d_eps, double* flux, cudaStream_t st) {
   if constexpr (DIM == 2) {
     switch (m.Q) {
-      case 1: return launch_flux_df_q<2, LAW, MODE, 1>(m, mat, sw, ws, ubq, ubf, d_eps, flux, st);
-      case 2: return launch_flux_df_q<2, LAW, MODE, 2>(m, mat, sw, ws, ubq, ubf, d_eps, flux, st);
-      case 3: return launch_flux_df_q<2, LAW, MODE, 3>(m, mat, sw, ws, ubq, ubf, d_eps, flux, st);
-      default: return launch_flux_df_q<2, LAW, MODE, 4>(m, mat, sw, ws, ubq, ubf, d_eps, flux, st);
+      case 1: return launch_flux_df_q<2, LAW, MODE, 1>(m, mat, sw, wd, ws, ubq, ubf, d_eps, flux, st);
+      case 2: return launch_flux_df_q<2, LAW, MODE, 2>(m, mat, sw, wd, ws, ubq, ubf, d_eps, flux, st);
+      case 3: return launch_flux_df_q<2, LAW, MODE, 3>(m, mat, sw, wd, ws, ubq, ubf, d_eps, flux, st);
+      default: return launch_flux_df_q<2, LAW, MODE, 4>(m, mat, sw, wd, ws, ubq, ubf, d_eps, flux, st);
     }
   } else {
     switch (m.Q) {
-      case 1: return launch_flux_df_q<3, LAW, MODE, 1>(m, mat, sw, ws, ubq, ubf, d_eps, flux, st);
-      case 4: return launch_flux_df_q<3, LAW, MODE, 4>(m, mat, sw, ws, ubq, ubf, d_eps, flux, st);
-      default: return launch_flux_df_q<3, LAW, MODE, 9>(m, mat, sw, ws, ubq, ubf, d_eps, flux, st);
+      case 1: return launch_flux_df_q<3, LAW, MODE, 1>(m, mat, sw, wd, ws, ubq, ubf, d_eps, flux, st);
+      case 4: return launch_flux_df_q<3, LAW, MODE, 4>(m, mat, sw, wd, ws, ubq, ubf, d_eps, flux, st);
+      default: return launch_flux_df_q<3, LAW, MODE, 9>(m, mat, sw, wd, ws, ubq, ubf, d_eps, flux, st);
     }
   }
 }
@@ -1141,7 +1203,7 @@ static void residual_impl_df(const DevMesh& m, const Material& mat, const double
       k_tflux<DIM><<<(unsigned)m.nftile, 32 * DIM, 0, st>>>(m, m.tco, mat.alpha * mat.kbar, w,
                                                             ustar, ubf, flux);
     } else {
-      launch_flux_df<DIM, LAW, kDfResidual>(m, mat, m.su, ustar, ubq, ubf, nullptr, flux, st);
+      launch_flux_df<DIM, LAW, kDfResidual>(m, mat, m.su, w, ustar, ubq, ubf, nullptr, flux, st);
     }
   }
   if (ev) cudaEventRecord(ev[2], st);
@@ -1165,10 +1227,11 @@ static void jv_impl_df(const DevMesh& m, const Material& mat, const double* v,
       k_tflux_hom<DIM><<<(unsigned)m.nftile, 32 * DIM, 0, st>>>(m, m.tco, mat.alpha * mat.kbar, v,
                                                                 m.ustar_v, flux);
     else if (LAW == HOFV_LAW_LINEAR)
-      launch_flux_df<DIM, LAW, kDfHomog>(m, mat, m.sv, m.ustar_v, nullptr, nullptr, nullptr, flux,
-                                         st);
+      launch_flux_df<DIM, LAW, kDfHomog>(m, mat, m.sv, v, m.ustar_v, nullptr, nullptr, nullptr,
+                                         flux, st);
     else
-      launch_flux_df<DIM, LAW, kDfJv>(m, mat, m.sv, m.ustar_v, nullptr, nullptr, d_eps, flux, st);
+      launch_flux_df<DIM, LAW, kDfJv>(m, mat, m.sv, v, m.ustar_v, nullptr, nullptr, d_eps, flux,
+                                      st);
   }
   if (m.mscale)
     k_cell_avg<DIM, true><<<(unsigned)((m.nc + 127) / 128), 128, 0, st>>>(m, v, m.wst, m.inert);
@@ -1254,12 +1317,10 @@ void launch_jv_cache_fill(const DevMesh& m, const Material& mat, const double* u
   if (m.nftile == 0) return;
   if (m.dim == 2) {
     const double* w = split_state<2>(m, u, m.wext, m.su, st);
-    (void)w;
-    launch_flux_df<2, 1, kDfFill>(m, mat, m.su, nullptr, ubq, nullptr, nullptr, nullptr, st);
+    launch_flux_df<2, 1, kDfFill>(m, mat, m.su, w, nullptr, ubq, nullptr, nullptr, nullptr, st);
   } else {
     const double* w = split_state<3>(m, u, m.wext, m.su, st);
-    (void)w;
-    launch_flux_df<3, 1, kDfFill>(m, mat, m.su, nullptr, ubq, nullptr, nullptr, nullptr, st);
+    launch_flux_df<3, 1, kDfFill>(m, mat, m.su, w, nullptr, ubq, nullptr, nullptr, nullptr, st);
   }
 }
 

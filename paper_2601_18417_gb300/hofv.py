@@ -107,6 +107,11 @@ SIGNATURES = {
     "hofv_force_scale": (_I, [_P, _P, C.POINTER(_D)]),
     "hofv_set_contraction": (_I, [_P, _I]),
     "hofv_set_precision": (_I, [_P, _I]),
+    "hofv_probe_peaks": (_I, [_P, C.POINTER(_D), C.POINTER(_D), C.POINTER(C.c_int32)]),
+    "hofv_set_stencils": (_I, [_P, _P, _P]),
+    "hofv_prepare_solver": (_I, [_P, C.POINTER(SolveOpts)]),
+    "hofv_solve_load_path": (_I, [_P, _P, _P, _P, _P, _P, _P, C.c_int32, C.c_int32,
+                                  C.POINTER(SolveOpts), C.POINTER(Stats), C.POINTER(C.c_int32)]),
     "hofv_get_precision": (_I, [_P]),
     "hofv_selftest_barrier": (_I, [_P, C.POINTER(C.c_int32)]),
     "hofv_nej_apply": (_I, [_P, _P, _P]),
@@ -287,6 +292,12 @@ class Context:
         """HOFV_PREC_FP64 or HOFV_PREC_DF64 for the gradient contraction."""
         return self._check(self._L.hofv_set_precision(self.h, int(prec)))
 
+    def probe_peaks(self):
+        """Measured FP64 / FP32 FMA throughput (TFLOP/s) and SM count."""
+        d, f, n = C.c_double(), C.c_double(), C.c_int32()
+        self._check(self._L.hofv_probe_peaks(self.h, C.byref(d), C.byref(f), C.byref(n)))
+        return {"fp64_tflops": d.value, "fp32_tflops": f.value, "sm_count": n.value}
+
     @property
     def precision(self):
         rc = self._L.hofv_get_precision(self.h)
@@ -324,6 +335,37 @@ class Context:
         rc = self._L.hofv_newton_solve(self.h, _ptr(_dev(u)), C.byref(o), C.byref(st))
         self._check(rc, allow_warn=True)
         return st.as_dict()
+
+    def prepare_solver(self, **opts):
+        """Allocate and build up front what a solve with these options uses."""
+        o = SolveOpts()
+        self._L.hofv_default_opts(C.byref(o))
+        for k, v in opts.items():
+            setattr(o, k, v)
+        return self._check(self._L.hofv_prepare_solver(self.h, C.byref(o)))
+
+    def solve_load_path(self, u, n_steps, u_bq1=None, u_bf1=None, t_bq1=None, body1=None,
+                        du_dlambda=None, max_halvings=6, **opts):
+        """hofv_solve_load_path; returns (stats dict, accepted increments)."""
+        o = SolveOpts()
+        self._L.hofv_default_opts(C.byref(o))
+        for k, v in opts.items():
+            setattr(o, k, v)
+        st = Stats()
+        done = C.c_int32(0)
+        args = [_ptr(_dev(a)) if a is not None else None
+                for a in (u_bq1, u_bf1, t_bq1, body1, du_dlambda)]
+        rc = self._L.hofv_solve_load_path(self.h, _ptr(_dev(u)), *args, int(n_steps),
+                                          int(max_halvings), C.byref(o), C.byref(st),
+                                          C.byref(done))
+        self._check(rc, allow_warn=True)
+        return st.as_dict(), done.value
+
+    def set_stencils(self, face_stencils=None, cell_stencils=None):
+        """Replace the stencils (HOST int32 [n_faces_with_stencil][S], [n_cells][S])."""
+        f = None if face_stencils is None else np.ascontiguousarray(face_stencils, np.int32)
+        c = None if cell_stencils is None else np.ascontiguousarray(cell_stencils, np.int32)
+        return self._check(self._L.hofv_set_stencils(self.h, _ptr(f), _ptr(c)))
 
     def arnoldi_step(self, u, Ru, kind, inner_iters, V, Z, j):
         """One flexible Arnoldi step; V [(j+2), n], Z [(j+1), n] CUDA FP64.

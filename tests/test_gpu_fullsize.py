@@ -85,19 +85,52 @@ def test_full_size_residual_on_sampled_cells(name):
     Fs = float(max(np.linalg.norm(fl[cf[c][cf[c] >= 0]], axis=1).sum() for c in cells))
     err = np.abs(Rg[:, cells] - Ro).max()
     assert err <= 1e-12 * Fs, (name, err, Fs, err / Fs)
+    # the double-float contraction the benchmark times, same context
+    ctx.set_precision(hofv.PREC_DF64)
+    ctx.residual(ud, R)
+    err = np.abs(R.cpu().numpy()[:, cells] - Ro).max()
+    assert err <= 1e-12 * Fs, (name, "df64", err, Fs, err / Fs)
     ctx.close()
 
 
-def test_full_size_arnoldi_step_properties():
-    """The benchmark's step on the 512x512 workload: the new basis vector is
+def oracle_sample(wl, mesh, cells, alpha=None):
+    """The oracle prepared on `cells` of a workload, with its boundary data."""
+    o = oracle.OracleMesh(mesh, I.side_tags(wl.problem, wl.dim), p=wl.p, n_plus=wl.n_plus,
+                          q1=wl.q1, k_weight=wl.k_weight,
+                          alpha=wl.alpha if alpha is None else alpha)
+    o.prepare(cells)
+    field = I.field_for(wl.problem, wl.dim)
+    if field is not None:
+        ubq = field.value(o.xq[o.disp_faces()])
+        ubf = field.value(o.xf[o.disp_faces()])
+        body = o.integrate_cells(field.body_force(o.cell_qp, wl.mu, wl.lam))
+    else:
+        top = I.block_top_displacement(1, wl.load_steps, wl.dim)
+        xf = o.xf[o.disp_faces()]
+        on_top = np.abs(xf[:, wl.dim - 1] - 1.0) < 1e-9
+        ubq = np.where(on_top[:, None, None], top, 0.0) * np.ones_like(o.xq[o.disp_faces()])
+        ubf = np.where(on_top[:, None], top, 0.0) * np.ones_like(xf)
+        body = None
+    tbq = np.zeros((max(o.nft, 1), o.Q, wl.dim))
+    return o, (ubq, ubf, tbq, body)
+
+
+@pytest.mark.parametrize("name", ["quad512j-p3-mixed", "hex128j-p3-nh"])
+def test_full_size_arnoldi_step_properties(name):
+    """The benchmark's step as it is timed (double-float contraction, one
+    multigrid V-cycle of the approximate Jacobian): the new basis vector is
     unit length and orthogonal to the previous ones, the Hessenberg column
-    reproduces w = J z_j, and J z_j matches a forward difference formed here
-    from two library residuals with the same step."""
+    reproduces w = J z_j, and J z_j on a sample of cells matches the
+    oracle's Jacobian applied to the same z_j (the exact product of the affine
+    linear-law residual; a central difference of the oracle's residual for
+    neo-Hookean)."""
     import torch
-    wl, mesh, ctx, lay, setup_s, u_ex, field = bench.build_workload("quad512j-p3-mixed")
+    wl, mesh, ctx, lay, setup_s, u_ex, field = bench.build_workload(name)
+    ctx.set_precision(hofv.PREC_DF64)
     n = wl.dim * lay.n_cells
     xc = ctx.get_points(hofv.PTS_CELL_CENTROID)
-    u = torch.as_tensor(state(wl, xc, u_ex), device="cuda:0")
+    u_np = state(wl, xc, u_ex)
+    u = torch.as_tensor(u_np, device="cuda:0")
     Ru = torch.empty_like(u)
     ctx.residual(u, Ru)
     J = bench.KRYLOV_J
@@ -105,17 +138,49 @@ def test_full_size_arnoldi_step_properties():
     V = torch.as_tensor(rng.standard_normal((J + 2, n)), device="cuda:0")
     V[: J + 1] = torch.linalg.qr(V[: J + 1].T)[0].T
     Z = torch.zeros((J + 1, n), dtype=torch.float64, device="cuda:0")
-    h = ctx.arnoldi_step(u, Ru, hofv.PC_AJ32, bench.INNER_ITERS, V, Z, J)
+    h = ctx.arnoldi_step(u, Ru, hofv.PC_AJMG, bench.MG_INNER, V, Z, J)
     torch.cuda.synchronize()
     assert abs(float(V[J + 1].norm()) - 1.0) < 1e-12
     assert float((V[: J + 1] @ V[J + 1]).abs().max()) < 1e-10
-    w = (V[: J + 2].T @ torch.as_tensor(h, device="cuda:0"))
-    z = Z[J]
-    eps = 1.4901161193847656e-08 * (1 + float(u.norm())) / float(z.norm())
-    R1 = torch.empty_like(u)
-    ctx.residual((u.reshape(-1) + eps * z).reshape(u.shape).contiguous(), R1)
-    fd = (R1 - Ru).reshape(-1) / eps
-    assert float((w - fd).norm() / fd.norm()) < 1e-6
+    w = (V[: J + 2].T @ torch.as_tensor(h, device="cuda:0")).reshape(wl.dim, -1)
+    z = Z[J].reshape(wl.dim, -1).cpu().numpy()
+    cells = sample_cells(wl.n, wl.dim)
+    o, (ubq, ubf, tbq, body) = oracle_sample(wl, mesh, cells)
+    if wl.law == 0:
+        ref = o.residual(wl.law, wl.mu, wl.lam, z, cells=cells) - \
+            o.residual(wl.law, wl.mu, wl.lam, np.zeros_like(z), cells=cells)
+    else:
+        hh = 1e-4 * np.abs(u_np).max() / np.abs(z).max()
+        R = lambda x: o.residual(wl.law, wl.mu, wl.lam, x, ubq, ubf, tbq, body,  # noqa: E731
+                                 cells=cells)
+        ref = (R(u_np + hh * z) - R(u_np - hh * z)) / (2 * hh)
+    got = w.cpu().numpy()[:, cells]
+    rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    assert rel < 1e-5, (name, rel)
+    ctx.close()
+
+
+def test_full_size_neo_hookean_load_step_on_sampled_cells():
+    """The 64^3 neo-Hookean block's first load step solved as the benchmark
+    solves it (double-float contraction, multigrid inner solve): the oracle's
+    residual at the GPU solution on a sample of cells is within 1e-8 of the
+    GPU's initial residual norm."""
+    import torch
+    wl, mesh, ctx, lay, setup_s, u_ex, field = bench.build_workload("hex64j-p2-nh")
+    ctx.set_precision(hofv.PREC_DF64)
+    u = torch.as_tensor(u_ex, device="cuda:0")   # the uniform compression of step 1
+    R0 = torch.empty_like(u)
+    ctx.residual(u, R0)
+    r0 = float(R0.norm())
+    st = ctx.newton_solve(u, rtol=1e-10, precond=hofv.PC_AJMG, inner_iters=2, restart=30,
+                          max_krylov=3000, max_newton=20)
+    assert st["status"] == 0, st
+    cells = sample_cells(wl.n, wl.dim, k=60)
+    top_layer = np.arange(wl.n ** 3 - wl.n ** 2, wl.n ** 3, 97)  # cells under the loaded face
+    cells = np.unique(np.concatenate([cells, top_layer])).astype(np.int64)
+    o, (ubq, ubf, tbq, body) = oracle_sample(wl, mesh, cells)
+    Ro = o.residual(wl.law, wl.mu, wl.lam, u.cpu().numpy(), ubq, ubf, tbq, body, cells=cells)
+    assert np.abs(Ro).max() <= 1e-8 * r0, (np.abs(Ro).max(), r0)
     ctx.close()
 
 
