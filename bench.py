@@ -347,7 +347,9 @@ def step_section(args, wl, mesh, ctx, lay, u_ex, precision, rank, ws, peaks_dev,
     if clk_holder is not None and rank == 0:
         clk_holder.append(ClockSampler(ctx.device))
     s = torch.cuda.current_stream()
+    torch.cuda.nvtx.range_push("hofv_timed_steps")  # ncu --nvtx --nvtx-include hofv_timed_steps/
     ms = event_ms(step, args.steps, s)
+    torch.cuda.nvtx.range_pop()
     # the same step launched kernel by kernel instead of as one CUDA graph
     os.environ["HOFV_GRAPHS"] = "0"
     for _ in range(3):
@@ -494,6 +496,27 @@ def block_solves(args, device):
     ctx.close()
     torch.cuda.empty_cache()
     return out
+
+
+def run_residuals(args):
+    """Profiling aid: `args.residuals` residual evaluations of one workload at
+    the benchmark's state, nothing else (a small, fixed launch sequence for
+    ncu captures of the face kernel)."""
+    import torch
+
+    from paper_2601_18417_gb300 import build as B
+    from paper_2601_18417_gb300 import hofv
+    B.build()
+    wl, mesh, ctx, lay, setup_s, u_ex, field = build_workload(args.workload)
+    ctx.set_precision(hofv.PREC_DF64 if args.precision == "df64" else hofv.PREC_FP64)
+    rng = np.random.default_rng(99)
+    u = torch.as_tensor(u_ex + 1e-3 * np.abs(u_ex).max() * rng.standard_normal(u_ex.shape),
+                        device="cuda:0")
+    R = torch.empty_like(u)
+    ms = event_ms(lambda: ctx.residual(u, R), args.residuals, torch.cuda.current_stream())
+    print(json.dumps({"mode": "residuals", "workload": wl.name, "precision": args.precision,
+                      "residuals": args.residuals, "ms_per_residual": ms}))
+    ctx.close()
 
 
 def run_hofv(args):
@@ -886,6 +909,8 @@ def main():
                     help="neo-Hookean block whose load steps are solved to 1e-8 ('' = none)")
     ap.add_argument("--cpu-sample", type=int, default=0,
                     help="cells of the oracle's timed sample (0: 96 in 3-D, 2048 in 2-D)")
+    ap.add_argument("--residuals", type=int, default=0,
+                    help="profiling aid: only this many residual evaluations of --workload")
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
@@ -922,6 +947,8 @@ def main():
         run_pc_sweep(args)
     elif args.dynamics:
         run_dynamics(args)
+    elif args.residuals > 0:
+        run_residuals(args)
     else:
         run_hofv(args)
 
