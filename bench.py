@@ -119,7 +119,11 @@ def build_workload(name, device=0):
     from paper_2601_18417_gb300 import inputs as I
     wl = I.WORKLOADS[name]
     mesh = wl.mesh()
-    tags = I.side_tags(wl.problem, wl.dim)[mesh.bface_side]
+    st = I.side_tags(wl.problem, wl.dim)
+    if hasattr(mesh, "face_ptr"):  # polyhedra given face by face: one tag per face
+        tags = np.where(mesh.face_side >= 0, st[np.maximum(mesh.face_side, 0)], -1).astype(np.int32)
+    else:
+        tags = st[mesh.bface_side]
     ctx = hofv.Context(device)
     ctx.set_mesh(mesh, tags)
     ctx.set_scheme(wl.p, wl.n_plus, wl.q1, wl.k_weight, wl.alpha)
@@ -154,6 +158,9 @@ def build_workload(name, device=0):
 
 
 def mesh_label(wl):
+    if wl.cells == "polyhedron":
+        return (f"{(wl.n + 1) ** 2} x {wl.n} polyhedra (dual polygons of 2 x {wl.n}^2 triangles "
+                f"extruded through {wl.n} layers), {int(round(wl.jitter * 100))}% node jitter")
     if wl.cells == "polygon":
         return (f"{wl.n + 1}^2 polygons (dual of 2 x {wl.n}^2 triangles), "
                 f"{int(round(wl.jitter * 100))}% node jitter")
@@ -174,7 +181,7 @@ def algorithmic_counts(wl, lay):
     bytes_face = 8 * R * S + 4 * S + 8 * Q * 3 + 8 + 8 + 8 * d + 2 * 8 * d
     bytes_ = nfid * bytes_face + lay.n_disp * (8 * R + 8 * Q * d + 8 * d) + 8 * d * lay.n_cells
     # the whole residual (u* prepass + fluxes + assembly), for the HBM view
-    nlf = {"simplex": d + 1, "polygon": 8}.get(wl.cells, 2 * d)
+    nlf = {"simplex": d + 1, "polygon": 8, "polyhedron": 16, "hexfaces": 16}.get(wl.cells, 2 * d)
     res_bytes = bytes_ + lay.n_cells * (8 * nlf * S + 4 * S + 8 * d + 8 * nlf * d * 2
                                         + 8 * d * 2 + 4 * nlf)
     return flops, bytes_, res_bytes
@@ -709,12 +716,15 @@ def run_learned(args):
                 continue
             if pc == hofv.PC_GNN:
                 ctx.gnn_load(wpath)
+            # plain = FP64 throughout; the others contract in the benchmark's precision
+            prec = "fp64" if label == "plain_fp64_aj" else args.precision
+            ctx.set_precision(hofv.PREC_DF64 if prec == "df64" else hofv.PREC_FP64)
             capped = dict(opts, max_krylov=600 if judge else 300, max_newton=12 if judge else 6,
                           inner_iters=inner)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             u, st = block_load_steps(ctx, wl, lay, nsteps, precond=pc, gnn_judge=judge, **capped)
-            res[label] = summarize(st, time.perf_counter() - t0)
+            res[label] = dict(summarize(st, time.perf_counter() - t0), precision=prec)
             sols[label] = u
             print(f"[learned] {name} {label}: {res[label]}", file=sys.stderr, flush=True)
         ref = sols.get("plain_fp64_aj")

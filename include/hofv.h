@@ -207,10 +207,42 @@ int hofv_set_mesh_polygons(hofv_ctx* ctx, int64_t n_nodes, const double* xyz, in
                            int64_t n_bfaces, const int64_t* bface_nodes,
                            const int32_t* bface_tag);
 
+/* hofv_set_mesh for a 3-D mesh of polyhedra given face by face (the layout
+   of a polyMesh; arbitrary convex polyhedra, Sec. 3.1-3.3, with their faces
+   split into triangles and their cells into tetrahedra).  HOST arrays,
+   copied in:
+     xyz        [n_nodes][3]
+     face_ptr   [n_faces + 1], face_ptr[0] = 0; face i has the corners
+                face_nodes[face_ptr[i] .. face_ptr[i+1]) (3 to 8), ordered so
+                that the right-hand-rule normal points out of owner[i]
+     owner      [n_faces] cell ids in [0, n_cells)
+     neighbour  [n_faces] the other cell, -1 for a boundary face
+     face_tag   [n_faces] boundary tag as hofv_set_mesh (read only where
+                neighbour is -1)
+   Each cell needs 4 to 16 faces; its local faces are its faces in input
+   order (16 slots, ext rows of hofv_get_cell_data, empty past its last
+   face).  Faces are renumbered as everywhere: internal faces by (owner,
+   owner's local face) with owner < neighbour (a face whose owner has the
+   higher id is flipped), then displacement, symmetry and traction faces in
+   input order.  A face is the fan of triangles from its corners' average,
+   each the collapsed square with q_per_dir^2 points; a face has 4 corner
+   slots when no face of the mesh has more than 4 corners, else 8, so
+   Q = q_per_dir^2 * slots, and the points of slots past a face's last
+   corner sit at its corners' average with zero area.  A cell's rule is the
+   fan of tetrahedra (its faces' fan triangles joined to the average of its
+   faces' corner averages), each the collapsed cube with q_per_dir^3
+   points.  q_per_dir must be 1 or 2 (hofv_set_scheme).  Errors: EINVAL for
+   a bad count, id or tag. */
+int hofv_set_mesh_faces(hofv_ctx* ctx, int64_t n_nodes, const double* xyz, int64_t n_cells,
+                        int64_t n_faces, const int64_t* face_ptr, const int64_t* face_nodes,
+                        const int64_t* owner, const int64_t* neighbour,
+                        const int32_t* face_tag);
+
 /* Scheme (Sec. 3.5): reconstruction degree p in 1..3, surplus stencil nodes
    n_plus (|S| = N_t + n_plus; the paper uses 10 in 2-D and 45/55/65 in 3-D),
-   Gauss points per face direction q_per_dir in 1..4 (faces are bilinear
-   patches with q_per_dir^(dim-1) tensor Gauss-Legendre points), weight shape
+   Gauss points per face direction q_per_dir in 1..4 in 2-D, 1..3 in 3-D and
+   1..2 on polyhedra (faces are bilinear patches with q_per_dir^(dim-1)
+   tensor Gauss-Legendre points; polyhedral faces fans of them), weight shape
    k_weight (eq. weightFunc, paper: 6) and stabilisation factor alpha
    (eq. alpha, paper: 0.1). */
 int hofv_set_scheme(hofv_ctx* ctx, int p, int n_plus, int q_per_dir,
@@ -567,7 +599,7 @@ int hofv_get_face_data(hofv_ctx* ctx, int64_t first, int64_t count, int32_t* ste
      stencil [count][S] int32;  ext [count][F][S] weights e with
      u*_{f,P} = u_P + sum_N e_N u_N (eq. alphaJump); F = faces per cell
      (2 dim for quads / hexes, dim + 1 for triangles / tetrahedra, 8 slots
-     for polygons, zero rows past a polygon's last side). */
+     for polygons, 16 for polyhedra, zero rows past a cell's last face). */
 int hofv_get_cell_data(hofv_ctx* ctx, int64_t first, int64_t count, int32_t* stencil,
                        double* ext);
 

@@ -480,6 +480,7 @@ int hofv_set_mesh_cells(hofv_ctx* c, int dim, int cell_kind, int64_t nn, const d
   c->have_mesh = false;
   c->dim = dim;
   c->poly = false;
+  c->polyh = false;
   c->cnv.clear();
   c->simplex = cell_kind == HOFV_CELL_SIMPLEX;
   c->nv = c->simplex ? dim + 1 : (dim == 2 ? 4 : 8);
@@ -529,6 +530,7 @@ int hofv_set_mesh_polygons(hofv_ctx* c, int64_t nn, const double* xyz, int64_t n
   c->have_mesh = false;
   c->dim = 2;
   c->simplex = false;
+  c->polyh = false;
   c->poly = true;
   c->nv = c->nlf = kPolyMaxSides;
   c->nfv = 2;
@@ -564,6 +566,130 @@ int hofv_set_mesh_polygons(hofv_ctx* c, int64_t nn, const double* xyz, int64_t n
   return build_faces(c, nb, bface_nodes, bface_tag);
 }
 
+int hofv_set_mesh_faces(hofv_ctx* c, int64_t nn, const double* xyz, int64_t nc, int64_t nf,
+                        const int64_t* face_ptr, const int64_t* face_nodes, const int64_t* owner,
+                        const int64_t* neighbour, const int32_t* face_tag) {
+  if (!c) return HOFV_EINVAL;
+  invalidate_graphs(c);
+  if (nn <= 0 || nc <= 0 || nf <= 0 || !xyz || !face_ptr || !face_nodes || !owner || !neighbour ||
+      !face_tag)
+    return fail(c, HOFV_EINVAL, "empty mesh or null array");
+  if (nn >= (int64_t)1 << 31 || nc >= (int64_t)1 << 30 || nf >= (int64_t)1 << 30)
+    return fail(c, HOFV_EINVAL, "mesh too large for 32-bit ids");
+  if (face_ptr[0] != 0) return fail(c, HOFV_EINVAL, "face_ptr[0] must be 0");
+  int maxfv = 0;
+  for (int64_t i = 0; i < nf; ++i) {
+    const int64_t k = face_ptr[i + 1] - face_ptr[i];
+    if (k < 3 || k > kPolyFaceMaxCorners)
+      return fail(c, HOFV_EINVAL, "a face must have 3 to 8 corners");
+    for (int64_t j = face_ptr[i]; j < face_ptr[i + 1]; ++j)
+      if (face_nodes[j] < 0 || face_nodes[j] >= nn)
+        return fail(c, HOFV_EINVAL, "face node id out of range");
+    if (owner[i] < 0 || owner[i] >= nc || neighbour[i] >= nc || neighbour[i] == owner[i])
+      return fail(c, HOFV_EINVAL, "bad owner or neighbour");
+    if (neighbour[i] < 0 && (face_tag[i] < 0 || face_tag[i] > 2))
+      return fail(c, HOFV_EINVAL, "bad boundary tag");
+    maxfv = std::max(maxfv, (int)k);
+  }
+  std::vector<int> nfc((size_t)nc, 0);
+  for (int64_t i = 0; i < nf; ++i) {
+    ++nfc[owner[i]];
+    if (neighbour[i] >= 0) ++nfc[neighbour[i]];
+  }
+  for (int64_t cell = 0; cell < nc; ++cell)
+    if (nfc[cell] < 4 || nfc[cell] > kPolyhedronMaxFaces)
+      return fail(c, HOFV_EINVAL, "a cell must have 4 to 16 faces");
+  free_built(c);
+  c->have_mesh = false;
+  c->dim = 3;
+  c->simplex = false;
+  c->poly = false;
+  c->polyh = true;
+  c->cnv.clear();
+  c->nv = 0;
+  c->nlf = kPolyhedronMaxFaces;
+  // corner slots of a face: 4 or 8, so that the face kernels see one of a
+  // few point counts (slots past a face's last corner carry zero area)
+  const int nfv = maxfv <= 4 ? 4 : kPolyFaceMaxCorners;
+  c->nfv = nfv;
+  c->nn = nn;
+  c->nc = nc;
+  c->x.assign(xyz, xyz + nn * 3);
+  c->cn.clear();
+  // owner = the lower cell id (the face flipped where the input's owner is
+  // the higher one); a cell's local faces are its faces in input order
+  std::vector<int64_t> own((size_t)nf), nei((size_t)nf);
+  std::vector<char> flip((size_t)nf, 0);
+  std::vector<int> fill((size_t)nc, 0), lfo((size_t)nf), lfn((size_t)nf, -1);
+  int64_t nfi = 0, nfd = 0, nfy = 0, nft = 0;
+  for (int64_t i = 0; i < nf; ++i) {
+    own[i] = owner[i];
+    nei[i] = neighbour[i];
+    if (nei[i] >= 0 && nei[i] < own[i]) {
+      std::swap(own[i], nei[i]);
+      flip[i] = 1;
+    }
+    lfo[i] = fill[own[i]]++;
+    if (nei[i] >= 0) lfn[i] = fill[nei[i]]++;
+    if (nei[i] >= 0) ++nfi;
+    else if (face_tag[i] == 0) ++nfd;
+    else if (face_tag[i] == 2) ++nfy;
+    else ++nft;
+  }
+  // canonical order: internal faces by (owner, owner's local face), then
+  // displacement, symmetry and traction faces in input order
+  std::vector<int64_t> order;
+  order.reserve((size_t)nf);
+  for (int64_t i = 0; i < nf; ++i)
+    if (nei[i] >= 0) order.push_back(i);
+  std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
+    return own[a] != own[b] ? own[a] < own[b] : lfo[a] < lfo[b];
+  });
+  for (int tag : {0, 2, 1})
+    for (int64_t i = 0; i < nf; ++i)
+      if (nei[i] < 0 && face_tag[i] == tag) order.push_back(i);
+  c->nb = nfd + nfy + nft;
+  c->nfi = nfi;
+  c->nfd = nfd;
+  c->nfy = nfy;
+  c->nft = nft;
+  c->nfid = nfi + nfd + nfy;
+  c->nf = nf;
+  c->fown.assign(nf, -1);
+  c->fnei.assign(nf, -1);
+  c->flf.assign(nf, 0);
+  c->ftag.assign(nf, -1);
+  c->cf.assign((size_t)nc * c->nlf, -1);
+  c->fnodes.assign((size_t)nf * nfv, -1);
+  for (int64_t f = 0; f < nf; ++f) {
+    const int64_t i = order[f];
+    const int64_t k = face_ptr[i + 1] - face_ptr[i];
+    c->fown[f] = own[i];
+    c->fnei[f] = nei[i];
+    c->flf[f] = lfo[i];
+    c->ftag[f] = nei[i] >= 0 ? -1 : face_tag[i];
+    for (int64_t t = 0; t < k; ++t)
+      c->fnodes[f * nfv + t] = (int32_t)face_nodes[face_ptr[i] + (flip[i] ? k - 1 - t : t)];
+    c->cf[own[i] * c->nlf + lfo[i]] = f;
+    if (nei[i] >= 0) c->cf[nei[i] * c->nlf + lfn[i]] = f;
+  }
+  c->maxtets = 0;
+  for (int64_t cell = 0; cell < nc; ++cell) {
+    int t = 0;
+    for (int lf = 0; lf < c->nlf; ++lf) {
+      const int64_t f = c->cf[cell * c->nlf + lf];
+      if (f < 0) continue;
+      int k = 0;
+      while (k < nfv && c->fnodes[f * nfv + k] >= 0) ++k;
+      t += k;
+    }
+    c->maxtets = std::max(c->maxtets, t);
+  }
+  c->have_mesh = true;
+  c->built = false;
+  return HOFV_OK;
+}
+
 int hofv_set_scheme(hofv_ctx* c, int p, int n_plus, int q1, double k_weight, double alpha) {
   if (!c) return HOFV_EINVAL;
   invalidate_graphs(c);
@@ -571,6 +697,8 @@ int hofv_set_scheme(hofv_ctx* c, int p, int n_plus, int q1, double k_weight, dou
   if (p < 1 || p > 3) return fail(c, HOFV_EINVAL, "p must be 1..3");
   if (q1 < 1 || q1 > 4 || (c->dim == 3 && q1 > 3))
     return fail(c, HOFV_EINVAL, "q_per_dir must be 1..4 in 2-D and 1..3 in 3-D");
+  if (c->polyh && q1 > 2)
+    return fail(c, HOFV_EINVAL, "q_per_dir must be 1..2 on polyhedra (8 q^2 points a face)");
   if (n_plus < 0 || !(k_weight > 0) || !(alpha >= 0)) return fail(c, HOFV_EINVAL, "bad scheme parameter");
   int nt = 1;
   for (int i = 1; i <= c->dim; ++i) nt = nt * (p + i) / i;
@@ -582,8 +710,10 @@ int hofv_set_scheme(hofv_ctx* c, int p, int n_plus, int q1, double k_weight, dou
   c->q1 = q1;
   c->Nt = nt;
   c->S = nt + n_plus;
-  c->Q = c->dim == 2 ? q1 : q1 * q1;
-  c->QC = c->poly ? c->nlf * q1 * q1 : c->dim == 2 ? q1 * q1 : q1 * q1 * q1;
+  c->Q = c->polyh ? c->nfv * q1 * q1 : c->dim == 2 ? q1 : q1 * q1;
+  c->QC = c->polyh  ? c->maxtets * q1 * q1 * q1
+          : c->poly ? c->nlf * q1 * q1
+          : c->dim == 2 ? q1 * q1 : q1 * q1 * q1;
   c->kw = k_weight;
   c->alpha = alpha;
   gauss_rule(q1, c->gl_x, c->gl_w);
@@ -642,6 +772,11 @@ int hofv_build_stencils(hofv_ctx* c) {
   TRY(dev_alloc(c, &c->d_cqx, nc * c->QC * 3));
   TRY(dev_alloc(c, &c->d_cqw, nc * c->QC));
   TRY(run_geometry(c));
+  // faces with more rows than one thread per (face, row) of a 32-face tile
+  // allows take the strided FP64 face kernel, whose shared memory is raised
+  if (kTile * c->Q * d > (d == 3 ? 864 : 256) &&
+      (d != 3 || c->Q > kPolyFaceMaxCorners * 4 || flux_wide_prepare() != 0))
+    return fail(c, HOFV_ENOTSUP, "too many face points for the face kernel");
   // reference length: power of two near the mean cell size (node bounding box)
   double vbox = 1.0;
   for (int a = 0; a < d; ++a) {

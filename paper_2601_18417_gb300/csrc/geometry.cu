@@ -132,6 +132,39 @@ __device__ void quad_cell_points(const Gauss& g, const double (*P)[3], double* c
     }
 }
 
+// Gauss points and weights of the trilinear map of the hex with corners P
+// (repeated corners collapse it to a tetrahedron)
+__device__ void hex_cell_points(const Gauss& g, const double (*P)[3], double* cqx, double* cqw) {
+  const int n = g.n;
+  const int R3[8][3] = {{0, 0, 0}, {1, 0, 0}, {1, 1, 0}, {0, 1, 0},
+                        {0, 0, 1}, {1, 0, 1}, {1, 1, 1}, {0, 1, 1}};
+  for (int a = 0; a < n; ++a)
+    for (int b = 0; b < n; ++b)
+      for (int e = 0; e < n; ++e) {
+        const double s[3] = {g.x[a], g.x[b], g.x[e]};
+        double X[3] = {0, 0, 0}, J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+        for (int k = 0; k < 8; ++k) {
+          double f[3], dr[3];
+          for (int r = 0; r < 3; ++r) {
+            f[r] = R3[k][r] ? s[r] : 1 - s[r];
+            dr[r] = R3[k][r] ? 1.0 : -1.0;
+          }
+          const double N = f[0] * f[1] * f[2];
+          const double dN[3] = {dr[0] * f[1] * f[2], f[0] * dr[1] * f[2], f[0] * f[1] * dr[2]};
+          for (int r = 0; r < 3; ++r) {
+            X[r] += N * P[k][r];
+            for (int t = 0; t < 3; ++t) J[r][t] += dN[t] * P[k][r];
+          }
+        }
+        const double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                           J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                           J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+        const int q = (a * n + b) * n + e;
+        for (int r = 0; r < 3; ++r) cqx[q * 3 + r] = X[r];
+        cqw[q] = g.w[a] * g.w[b] * g.w[e] * fabs(det);
+      }
+}
+
 // volume and centroid from the divergence theorem over the cell's own
 // outward faces; Gauss points of the bilinear / trilinear cell map.  A
 // polygon (poly: corners padded with -1 up to nv) uses its sides as faces
@@ -209,33 +242,134 @@ __global__ void k_cell_geometry(int dim, bool simplex, bool poly, int nv, int nl
     quad_cell_points(g, cx, cqx + c * QC * 3, cqw + c * QC);
     return;
   }
-  const int R3[8][3] = {{0, 0, 0}, {1, 0, 0}, {1, 1, 0}, {0, 1, 0},
-                        {0, 0, 1}, {1, 0, 1}, {1, 1, 1}, {0, 1, 1}};
-  for (int a = 0; a < n; ++a)
-    for (int b = 0; b < n; ++b)
-      for (int e = 0; e < n; ++e) {
-        const double s[3] = {g.x[a], g.x[b], g.x[e]};
-        double X[3] = {0, 0, 0}, J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-        for (int k = 0; k < 8; ++k) {
-          double f[3], dr[3];
-          for (int r = 0; r < 3; ++r) {
-            f[r] = R3[k][r] ? s[r] : 1 - s[r];
-            dr[r] = R3[k][r] ? 1.0 : -1.0;
-          }
-          const double N = f[0] * f[1] * f[2];
-          const double dN[3] = {dr[0] * f[1] * f[2], f[0] * dr[1] * f[2], f[0] * f[1] * dr[2]};
-          for (int r = 0; r < 3; ++r) {
-            X[r] += N * cx[k][r];
-            for (int t = 0; t < 3; ++t) J[r][t] += dN[t] * cx[k][r];
-          }
-        }
-        const double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
-                           J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
-                           J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
-        const int q = (a * n + b) * n + e;
-        for (int r = 0; r < 3; ++r) cqx[(c * QC + q) * 3 + r] = X[r];
-        cqw[c * QC + q] = g.w[a] * g.w[b] * g.w[e] * fabs(det);
+  hex_cell_points(g, cx, cqx + c * QC * 3, cqw + c * QC);
+}
+
+// ---------------------------------------------------------------------
+// polyhedra given face by face (corners padded with -1 up to nfv): a face
+// is the fan of triangles from its corners' average cb, each the collapsed
+// patch (cb, v_t, v_t+1, cb) with n^2 points (zero area at cb in the slots
+// past its last corner); a cell's volume and centroid come from the
+// divergence theorem over its faces' points, its rule from the fan of
+// tetrahedra (xb, cb_f, v_t, v_t+1), xb the average of its faces' cb.
+// ---------------------------------------------------------------------
+__device__ __forceinline__ int face_corners_fan(const int32_t* __restrict__ fn, int nfv,
+                                                const double* __restrict__ x, double* cb) {
+  int k = 0;
+  while (k < nfv && fn[k] >= 0) ++k;
+  for (int a = 0; a < 3; ++a) cb[a] = 0.0;
+  for (int t = 0; t < k; ++t)
+    for (int a = 0; a < 3; ++a) cb[a] += x[3 * (int64_t)fn[t] + a];
+  for (int a = 0; a < 3; ++a) cb[a] /= k;
+  return k;
+}
+
+__global__ void k_face_geometry_fan(int nfv, int Q, int64_t nf, Gauss g,
+                                    const double* __restrict__ x,
+                                    const int32_t* __restrict__ fnodes, double* xq, double* aq,
+                                    double* xf, double* nrm, double* gam) {
+  const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (f >= nf) return;
+  const int32_t* fn = fnodes + f * nfv;
+  double cb[3];
+  const int k = face_corners_fan(fn, nfv, x, cb);
+  const int n2 = g.n * g.n;
+  double G = 0, A[3] = {0, 0, 0}, X[3] = {0, 0, 0};
+  for (int t = 0; t < nfv; ++t) {
+    double pq[3 * kMaxQ], pa[3 * kMaxQ];
+    if (t < k) {
+      double corner[12];
+      const int32_t v0 = fn[t], v1 = fn[(t + 1) % k];
+      for (int a = 0; a < 3; ++a) {
+        corner[a] = cb[a];
+        corner[3 + a] = x[3 * (int64_t)v0 + a];
+        corner[6 + a] = x[3 * (int64_t)v1 + a];
+        corner[9 + a] = cb[a];
       }
+      face_points(3, g, corner, pq, pa);
+    } else {
+      for (int q = 0; q < n2; ++q)
+        for (int a = 0; a < 3; ++a) {
+          pq[3 * q + a] = cb[a];
+          pa[3 * q + a] = 0.0;
+        }
+    }
+    for (int q = 0; q < n2; ++q) {
+      const double m = sqrt(pa[3 * q] * pa[3 * q] + pa[3 * q + 1] * pa[3 * q + 1] +
+                            pa[3 * q + 2] * pa[3 * q + 2]);
+      G += m;
+      const int64_t o = (f * Q + t * n2 + q) * 3;
+      for (int a = 0; a < 3; ++a) {
+        A[a] += pa[3 * q + a];
+        X[a] += m * pq[3 * q + a];
+        xq[o + a] = pq[3 * q + a];
+        aq[o + a] = pa[3 * q + a];
+      }
+    }
+  }
+  const double An = sqrt(A[0] * A[0] + A[1] * A[1] + A[2] * A[2]);
+  gam[f] = G;
+  for (int a = 0; a < 3; ++a) {
+    xf[3 * f + a] = X[a] / G;
+    nrm[3 * f + a] = A[a] / An;
+  }
+}
+
+__global__ void k_cell_geometry_fan(int nlf, int nfv, int Q, int QC, int maxtets, int64_t nc,
+                                    Gauss g, const double* __restrict__ x,
+                                    const int32_t* __restrict__ fnodes,
+                                    const int64_t* __restrict__ cf,
+                                    const int32_t* __restrict__ fown,
+                                    const double* __restrict__ xq, const double* __restrict__ aq,
+                                    double* xc, double* vol, double* cqx, double* cqw) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  double V = 0, M2[3] = {0, 0, 0}, xb[3] = {0, 0, 0};
+  int nfc = 0;
+  for (int lf = 0; lf < nlf; ++lf) {
+    const int64_t f = cf[c * nlf + lf];
+    if (f < 0) continue;
+    const double sg = fown[f] == c ? 1.0 : -1.0;
+    for (int q = 0; q < Q; ++q)
+      for (int a = 0; a < 3; ++a) {
+        const double xv = xq[(f * Q + q) * 3 + a], av = sg * aq[(f * Q + q) * 3 + a];
+        V += xv * av;
+        M2[a] += xv * xv * av;
+      }
+    double cb[3];
+    face_corners_fan(fnodes + f * nfv, nfv, x, cb);
+    for (int a = 0; a < 3; ++a) xb[a] += cb[a];
+    ++nfc;
+  }
+  V /= 3;
+  vol[c] = V;
+  for (int a = 0; a < 3; ++a) xc[3 * c + a] = M2[a] / (2.0 * V);
+  for (int a = 0; a < 3; ++a) xb[a] /= nfc;
+  const int n3 = g.n * g.n * g.n;
+  int slot = 0;
+  for (int lf = 0; lf < nlf; ++lf) {
+    const int64_t f = cf[c * nlf + lf];
+    if (f < 0) continue;
+    const int32_t* fn = fnodes + f * nfv;
+    double cb[3];
+    const int k = face_corners_fan(fn, nfv, x, cb);
+    for (int t = 0; t < k && slot < maxtets; ++t, ++slot) {
+      const int32_t v0 = fn[t], v1 = fn[(t + 1) % k];
+      double P[8][3];
+      for (int a = 0; a < 3; ++a) {
+        P[0][a] = P[3][a] = P[4][a] = P[7][a] = xb[a];
+        P[1][a] = P[5][a] = cb[a];
+        P[2][a] = x[3 * (int64_t)v0 + a];
+        P[6][a] = x[3 * (int64_t)v1 + a];
+      }
+      hex_cell_points(g, P, cqx + (c * QC + slot * n3) * 3, cqw + c * QC + slot * n3);
+    }
+  }
+  for (; slot < maxtets; ++slot)
+    for (int q = 0; q < n3; ++q) {
+      for (int a = 0; a < 3; ++a) cqx[(c * QC + slot * n3 + q) * 3 + a] = xb[a];
+      cqw[c * QC + slot * n3 + q] = 0.0;
+    }
 }
 
 static Gauss make_gauss(const hofv_ctx* c) {
@@ -251,6 +385,18 @@ static Gauss make_gauss(const hofv_ctx* c) {
 int run_geometry(hofv_ctx* c) {
   Gauss g = make_gauss(c);
   const int T = 128;
+  if (c->polyh) {
+    k_face_geometry_fan<<<(unsigned)((c->nf + T - 1) / T), T, 0, c->stream>>>(
+        c->nfv, c->Q, c->nf, g, c->d_x, c->d_fnodes, c->d_xq, c->d_aq, c->d_xf, c->d_nrm,
+        c->d_gam);
+    HOFV_CUDA(c, cudaGetLastError());
+    k_cell_geometry_fan<<<(unsigned)((c->nc + T - 1) / T), T, 0, c->stream>>>(
+        c->nlf, c->nfv, c->Q, c->QC, c->maxtets, c->nc, g, c->d_x, c->d_fnodes, c->d_cf,
+        c->d_fown, c->d_xq, c->d_aq, c->d_xc, c->d_vol, c->d_cqx, c->d_cqw);
+    HOFV_CUDA(c, cudaGetLastError());
+    HOFV_CUDA(c, cudaStreamSynchronize(c->stream));
+    return 0;
+  }
   k_face_geometry<<<(unsigned)((c->nf + T - 1) / T), T, 0, c->stream>>>(
       c->dim, c->nfv, c->Q, c->nf, g, c->d_x, c->d_fnodes, c->d_xq, c->d_aq, c->d_xf, c->d_nrm,
       c->d_gam);

@@ -18,6 +18,8 @@ constexpr int kMaxNt = 20;       // Taylor terms of a cubic in 3-D
 constexpr int kMaxQ = 16;        // Gauss points per face (4 x 4)
 constexpr int kMaxQC = 64;       // Gauss points per cell (4^3)
 constexpr int kPolyMaxSides = 8; // face slots of a polygon cell
+constexpr int kPolyhedronMaxFaces = 16;  // face slots of a polyhedral cell
+constexpr int kPolyFaceMaxCorners = 8;   // corners of a polyhedral face
 
 // Device-side description of the discretisation used by the residual
 // kernels.  All pointers are device addresses owned by the context.
@@ -93,6 +95,9 @@ struct hofv_ctx {
   bool simplex = false;            // triangles / tetrahedra instead of quads / hexes
   bool poly = false;               // 2-D polygons: nlf = nv = kPolyMaxSides slots per cell
   std::vector<int32_t> cnv;        // polygons: [nc] corners (= sides) of each cell
+  bool polyh = false;              // 3-D polyhedra given face by face: nlf = kPolyhedronMaxFaces
+                                   // slots, nfv = 4 or 8 corner slots a face (-1 past its last)
+  int maxtets = 0;                 // polyhedra: most fan tetrahedra of one cell
   int64_t nn = 0, nc = 0, nb = 0;
   std::vector<double> x;            // [nn][3]
   std::vector<int64_t> cn;          // [nc][nv]
@@ -247,6 +252,7 @@ DevMesh dev_mesh(const hofv_ctx* c);
 
 // ---- set-up kernels (setup.cu) ----
 int run_geometry(hofv_ctx* c);
+int flux_wide_prepare();
 int run_stencils(hofv_ctx* c, const std::vector<int64_t>& bucket_start,
                  const std::vector<int32_t>& bucket_items, const int nb[3], const double lo[3],
                  double bs);

@@ -604,7 +604,7 @@ int barrier_selftest(hofv_ctx* c, int* timed_out) {
 
 // the persistent cooperative solve when it fits on the device, else one
 // launch per iteration; NLF = faces per cell (4 / 6 for quads / hexes,
-// 3 / 4 for triangles / tetrahedra, 8 slots for polygons)
+// 3 / 4 for triangles / tetrahedra, 8 slots for polygons, 16 for polyhedra)
 template <typename T, int DIM, int NLF>
 static void aj_run(hofv_ctx* c, const T* diag, const T* invd, const T* off, T* work, int iters,
                    const double* v, double* z) {
@@ -622,12 +622,14 @@ static void aj_dispatch(hofv_ctx* c, const T* diag, const T* invd, const T* off,
     else aj_run<T, 2, 4>(c, diag, invd, off, work, iters, v, z);
   } else {
     if (simplex) aj_run<T, 3, 4>(c, diag, invd, off, work, iters, v, z);
+    else if (c->polyh) aj_run<T, 3, kPolyhedronMaxFaces>(c, diag, invd, off, work, iters, v, z);
     else aj_run<T, 3, 6>(c, diag, invd, off, work, iters, v, z);
   }
 }
 
 int aj_precondition(hofv_ctx* c, int kind, int iters, const double* v, double* z) {
-  if (c->nlf != 2 * c->dim && c->nlf != c->dim + 1 && !(c->poly && c->nlf == kPolyMaxSides))
+  if (c->nlf != 2 * c->dim && c->nlf != c->dim + 1 && !(c->poly && c->nlf == kPolyMaxSides) &&
+      !(c->polyh && c->nlf == kPolyhedronMaxFaces))
     return fail(c, HOFV_ENOTSUP, "cell shape without an approximate-Jacobian kernel");
   if (kind == HOFV_PC_AJ64)
     aj_dispatch<double>(c, c->d_aj_diag, c->d_aj_invd, c->d_aj_off, c->d_cg64, iters, v, z);

@@ -277,6 +277,102 @@ __global__ void __launch_bounds__(DIM == 3 ? 864 : 256)
 }
 
 // ---------------------------------------------------------------------
+// the same three phases for faces with more points than one thread per
+// (face, row) of a 32-face tile allows (polyhedral faces: up to 8 fan
+// triangles of q^2 points, R up to 96): kWideThreads threads walk the rows
+// and points of the tile in strides
+// ---------------------------------------------------------------------
+constexpr int kWideThreads = 768;
+
+template <int DIM, int LAW>
+__global__ void __launch_bounds__(kWideThreads)
+    k_flux_wide(DevMesh m, Material mt, const double* __restrict__ w,
+                const double* __restrict__ ustar, const double* __restrict__ ubq,
+                const double* __restrict__ ubf, double* __restrict__ flux) {
+  extern __shared__ double sm[];
+  const int R = m.R, Q = m.Q, S = m.S;
+  double* Gs = sm;                        // [32][R][DIM]
+  double* Ts = sm + kTile * R * DIM;      // [32][Q][DIM]
+  const int64_t tile = blockIdx.x;
+  const int64_t nc = m.wst;
+  for (int it = threadIdx.x; it < kTile * R; it += blockDim.x) {
+    const int fi = it / R, r = it % R;
+    const int64_t f = tile * kTile + fi;
+    const int32_t* __restrict__ st = m.fst + tile * S * kTile + fi;
+    const double* __restrict__ co = m.fco + tile * (int64_t)S * kTile * R + it;
+    double acc[DIM];
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) acc[j] = 0.0;
+#pragma unroll 4
+    for (int n = 0; n < S; ++n) {
+      const int32_t id = __ldg(st + n * kTile);
+      const double c = __ldg(co + (int64_t)n * kTile * R);
+#pragma unroll
+      for (int j = 0; j < DIM; ++j) acc[j] = fma(c, __ldg(w + j * nc + id), acc[j]);
+    }
+    if (f >= m.nfi && f < m.nfid) {
+      const int64_t fd = f - m.nfi;
+      const double cg = m.gco[fd * R + r];
+      const int q = r / DIM;
+#pragma unroll
+      for (int j = 0; j < DIM; ++j) acc[j] = fma(cg, ubq[(fd * Q + q) * DIM + j], acc[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) Gs[(fi * R + r) * DIM + j] = acc[j];
+  }
+  __syncthreads();
+  for (int it = threadIdx.x; it < kTile * Q; it += blockDim.x) {
+    const int fi = it / Q, q = it % Q;
+    const int64_t f = tile * kTile + fi;
+    double t[DIM];
+    if (f < m.nfid) {
+      double G[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+#pragma unroll
+      for (int i = 0; i < DIM; ++i)
+#pragma unroll
+        for (int j = 0; j < DIM; ++j) G[i][j] = Gs[(fi * R + q * DIM + i) * DIM + j];
+      double a[3];
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) a[k] = m.aq[(f * Q + q) * 3 + k];
+      traction<DIM, LAW>(G, a, mt, t);
+    } else {
+#pragma unroll
+      for (int i = 0; i < DIM; ++i) t[i] = 0.0;
+    }
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) Ts[(fi * Q + q) * DIM + i] = t[i];
+  }
+  __syncthreads();
+  for (int it = threadIdx.x; it < kTile * DIM; it += blockDim.x) {
+    const int fi = it / DIM, i = it % DIM;
+    const int64_t f = tile * kTile + fi;
+    if (f < m.nfid) {
+      double s = 0.0;
+      for (int q = 0; q < Q; ++q) s += Ts[(fi * Q + q) * DIM + i];
+      const int32_t sp = m.fstar[2 * f], sn = m.fstar[2 * f + 1];
+      const double other = sn >= 0 ? ustar[(int64_t)sn * DIM + i] : ubf[(f - m.nfi) * DIM + i];
+      const double coef = mt.alpha * mt.kbar * m.fstab[f];
+      flux[f * DIM + i] = fma(coef, other - ustar[(int64_t)sp * DIM + i], s);
+    }
+  }
+}
+
+// dynamic shared memory of k_flux_wide beyond the default 48 KB, raised to
+// what the largest polyhedral face (8 fan slots of 2 x 2 points) needs, so
+// that contexts of different point counts never lower it for one another;
+// set for both laws before the first launch or capture
+int flux_wide_prepare() {
+  constexpr int kMaxWideQ = kPolyFaceMaxCorners * 4;
+  const int smem = (int)(sizeof(double) * kTile * (kMaxWideQ * 3 * 3 + kMaxWideQ * 3));
+  if (cudaFuncSetAttribute(k_flux_wide<3, HOFV_LAW_LINEAR>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
+      cudaFuncSetAttribute(k_flux_wide<3, HOFV_LAW_NEOHOOKEAN>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+    return -1;
+  return 0;
+}
+
+// ---------------------------------------------------------------------
 // cell assembly; out = R, or (R - R0) * inv_eps when R0 != nullptr
 // ---------------------------------------------------------------------
 template <int DIM, int NLF>
@@ -361,6 +457,21 @@ __global__ void k_sym_other(DevMesh m, const double* __restrict__ ustar) {
   for (int j = 0; j < DIM; ++j) m.ubfw[(f - m.nfi) * DIM + j] = us[j] - 2.0 * un * n[j];
 }
 
+// faces per cell as a compile-time constant: d + 1 (triangles /
+// tetrahedra), 2 d (quads / hexes), kPolyMaxSides slots (2-D polygons),
+// kPolyhedronMaxFaces slots (3-D polyhedra)
+template <int DIM, typename F>
+static void by_faces_per_cell(const DevMesh& m, F&& launch) {
+  if (m.nlf == DIM + 1)
+    launch(std::integral_constant<int, DIM + 1>{});
+  else if (m.nlf == 2 * DIM)
+    launch(std::integral_constant<int, 2 * DIM>{});
+  else if constexpr (DIM == 2)
+    launch(std::integral_constant<int, kPolyMaxSides>{});
+  else
+    launch(std::integral_constant<int, kPolyhedronMaxFaces>{});
+}
+
 template <int DIM, int LAW>
 static void residual_impl(const DevMesh& m, const Material& mat, const double* w,
                           const double* d_eps, const double* R0, double* out, double* ustar,
@@ -371,16 +482,10 @@ static void residual_impl(const DevMesh& m, const Material& mat, const double* w
     k_extend<DIM><<<(unsigned)((m.wst + 255) / 256), 256, 0, st>>>(m, w, m.wext);
     w = m.wext;
   }
-  // faces per cell: d + 1 (triangles / tetrahedra), 2 d (quads / hexes),
-  // kPolyMaxSides slots (2-D polygons)
-  if (m.nlf == DIM + 1) {
-    k_ustar<DIM, DIM + 1><<<(unsigned)m.nctile, 32 * (DIM + 1), 0, st>>>(m, w, ustar);
-  } else if (m.nlf == 2 * DIM) {
-    k_ustar<DIM, 2 * DIM><<<(unsigned)m.nctile, 32 * 2 * DIM, 0, st>>>(m, w, ustar);
-  } else {
-    if constexpr (DIM == 2)
-      k_ustar<2, kPolyMaxSides><<<(unsigned)m.nctile, 32 * kPolyMaxSides, 0, st>>>(m, w, ustar);
-  }
+  by_faces_per_cell<DIM>(m, [&](auto nlf) {
+    constexpr int NLF = decltype(nlf)::value;
+    k_ustar<DIM, NLF><<<(unsigned)m.nctile, 32 * NLF, 0, st>>>(m, w, ustar);
+  });
   if (m.nfy > 0) k_sym_other<DIM><<<(unsigned)((m.nfy + 127) / 128), 128, 0, st>>>(m, ustar);
   if (ev) cudaEventRecord(ev[1], st);
   if (m.nftile > 0) {
@@ -389,21 +494,23 @@ static void residual_impl(const DevMesh& m, const Material& mat, const double* w
                                                             ustar, ubf, flux);
     } else {
       const size_t smem = sizeof(double) * kTile * (m.R * DIM + m.Q * DIM);
-      k_flux<DIM, LAW><<<(unsigned)m.nftile, kTile * m.R, smem, st>>>(m, mat, w, ustar, ubq, ubf,
-                                                                      flux);
+      if (kTile * m.R <= (DIM == 3 ? 864 : 256)) {
+        k_flux<DIM, LAW><<<(unsigned)m.nftile, kTile * m.R, smem, st>>>(m, mat, w, ustar, ubq,
+                                                                        ubf, flux);
+      } else {
+        k_flux_wide<DIM, LAW><<<(unsigned)m.nftile, kWideThreads, smem, st>>>(m, mat, w, ustar,
+                                                                              ubq, ubf, flux);
+      }
     }
   }
   if (ev) cudaEventRecord(ev[2], st);
   if (m.mscale)
     k_cell_avg<DIM, true><<<(unsigned)((m.nc + 127) / 128), 128, 0, st>>>(m, w, m.wst, m.inert);
   const unsigned cgrid = (unsigned)((m.nc + 255) / 256);
-  if (m.nlf == DIM + 1) {
-    k_cell<DIM, DIM + 1><<<cgrid, 256, 0, st>>>(m, flux, src, R0, d_eps, out);
-  } else if (m.nlf == 2 * DIM) {
-    k_cell<DIM, 2 * DIM><<<cgrid, 256, 0, st>>>(m, flux, src, R0, d_eps, out);
-  } else {
-    if constexpr (DIM == 2) k_cell<2, kPolyMaxSides><<<cgrid, 256, 0, st>>>(m, flux, src, R0, d_eps, out);
-  }
+  by_faces_per_cell<DIM>(m, [&](auto nlf) {
+    constexpr int NLF = decltype(nlf)::value;
+    k_cell<DIM, NLF><<<cgrid, 256, 0, st>>>(m, flux, src, R0, d_eps, out);
+  });
   if (ev) cudaEventRecord(ev[3], st);
 }
 
@@ -509,6 +616,8 @@ void launch_flux_scale(const DevMesh& m, const double* flux, double* out, cudaSt
     k_flux_scale<2, 4><<<grid, 256, 0, st>>>(m, flux, out);
   else if (m.nlf == 4)
     k_flux_scale<3, 4><<<grid, 256, 0, st>>>(m, flux, out);
+  else if (m.nlf == kPolyhedronMaxFaces)
+    k_flux_scale<3, kPolyhedronMaxFaces><<<grid, 256, 0, st>>>(m, flux, out);
   else
     k_flux_scale<3, 6><<<grid, 256, 0, st>>>(m, flux, out);
 }
@@ -878,33 +987,41 @@ __device__ __forceinline__ void cp_async_wait_all() {
 // thread streams its coefficient row through a ring of RING registers: the
 // coefficient of slot n + RING is requested when slot n is consumed, keeping
 // RING coalesced 8-byte loads in flight per thread; with R a compile-time
-// constant every ring offset is an immediate.  In 3-D a block takes half a
-// tile so that two blocks share an SM and the FP32 contraction of one
-// overlaps the FP64 law of the other.
-template <int DIM>
+// constant every ring offset is an immediate.  In 3-D a block takes part of
+// a tile so that several blocks share an SM and the FP32 contraction of one
+// overlaps the FP64 law and the barriers of the others: a quarter tile of 216
+// threads, four blocks an SM, for 3 x 3 points (measured on the 128^3
+// neo-Hookean block: 7 % faster than half tiles two an SM, 10 % slower with
+// eighth tiles), half tiles otherwise; faces with many points (polyhedral
+// fans, R = 48 or 96) take half or quarter tiles of 768 threads, one an SM.
+template <int DIM, int QD>
 struct DfShape {
-  static constexpr int FPB = DIM == 3 ? 16 : 32;   // faces per block
-  static constexpr int RING = DIM == 3 ? 8 : 4;    // coefficient loads in flight per thread
+  static constexpr int FPB = DIM == 2    ? 32
+                             : QD == 9   ? 8
+                             : 16 * QD * DIM <= 768 ? 16 : 8;  // faces per block
+  static constexpr int RING = DIM == 3 ? 8 : 4;  // coefficient loads in flight per thread
+  static constexpr int THREADS = FPB * QD * DIM;
+  static constexpr int MIN_BLOCKS = DIM == 2 ? 6 : QD == 9 ? 4 : (THREADS <= 512 ? 2 : 1);  // per SM
 };
 
 // dynamic shared memory: the gathered cell values and the faces' references,
 // reused after the contraction for the gradients and tractions of phases 2-3
-template <int DIM>
-static size_t df_smem_bytes(int S, int R, int Q) {
-  constexpr int FPB = DfShape<DIM>::FPB;
+template <int DIM, int QD>
+static size_t df_smem_bytes(int S) {
+  constexpr int FPB = DfShape<DIM, QD>::FPB, R = QD * DIM;
   const size_t gath = (size_t)(S + 1) * FPB * DIM * 16;
-  const size_t law = (size_t)FPB * (R * DIM + Q * DIM) * sizeof(double);
+  const size_t law = (size_t)FPB * (R * DIM + QD * DIM) * sizeof(double);
   return gath > law ? gath : law;
 }
 
 template <int DIM, int LAW, int MODE, int QD>
-__global__ void __launch_bounds__(DfShape<DIM>::FPB * QD * DIM, DIM == 3 ? 2 : 6)
+__global__ void __launch_bounds__(DfShape<DIM, QD>::THREADS, DfShape<DIM, QD>::MIN_BLOCKS)
     k_flux_df(DevMesh m, Material mt, const float4* __restrict__ sw, const double* __restrict__ wd,
               const double* __restrict__ ws, const double* __restrict__ ubq,
               const double* __restrict__ ubf, const double* __restrict__ d_eps,
               double* __restrict__ flux) {
-  constexpr int FPB = DfShape<DIM>::FPB, BPT = kTile / FPB, Q = QD, R = QD * DIM;
-  constexpr int kRing = DfShape<DIM>::RING;
+  constexpr int FPB = DfShape<DIM, QD>::FPB, BPT = kTile / FPB, Q = QD, R = QD * DIM;
+  constexpr int kRing = DfShape<DIM, QD>::RING;
   constexpr int CS = kTile * R;  // coefficient stride between stencil slots
   extern __shared__ __align__(16) double sm[];
   const int S = m.S;
@@ -1123,16 +1240,6 @@ __global__ void k_cell_diff(DevMesh m, const double* __restrict__ flux,
     out[j * m.nc + c] = m.mscale ? fma(r[j], ie, m.inert[j * m.nc + c]) : r[j] * ie;
 }
 
-template <int DIM, typename F>
-static void by_faces_per_cell(const DevMesh& m, F&& launch) {
-  if (m.nlf == DIM + 1)
-    launch(std::integral_constant<int, DIM + 1>{});
-  else if (m.nlf == 2 * DIM)
-    launch(std::integral_constant<int, 2 * DIM>{});
-  else if constexpr (DIM == 2)
-    launch(std::integral_constant<int, kPolyMaxSides>{});
-}
-
 template <int DIM>
 static void launch_ustar_df(const DevMesh& m, const float4* sw, const double* w, double* out,
                             cudaStream_t st) {
@@ -1147,13 +1254,14 @@ static void launch_flux_df_q(const DevMesh& m, const Material& mat, const float4
                              const double* wd, const double* ws, const double* ubq,
                              const double* ubf, const double* d_eps, double* flux,
                              cudaStream_t st) {
-  using SH = DfShape<DIM>;
-  const size_t smem = df_smem_bytes<DIM>(m.S, QD * DIM, QD);
-  k_flux_df<DIM, LAW, MODE, QD><<<(unsigned)(m.nftile * (kTile / SH::FPB)), SH::FPB * QD * DIM,
-                                  smem, st>>>(m, mat, sw, wd, ws, ubq, ubf, d_eps, flux);
+  using SH = DfShape<DIM, QD>;
+  const size_t smem = df_smem_bytes<DIM, QD>(m.S);
+  k_flux_df<DIM, LAW, MODE, QD><<<(unsigned)(m.nftile * (kTile / SH::FPB)), SH::THREADS, smem,
+                                  st>>>(m, mat, sw, wd, ws, ubq, ubf, d_eps, flux);
 }
 
-// Gauss points per face: q^(d-1) for q = 1..4 in 2-D, 1..3 in 3-D
+// Gauss points per face: q^(d-1) for q = 1..4 in 2-D, 1..3 in 3-D; on
+// polyhedra 4 or 8 fan slots of q^2 points for q = 1, 2
 template <int DIM, int LAW, int MODE>
 static void launch_flux_df(const DevMesh& m, const Material& mat, const float4* sw,
                            const double* wd, const double* ws, const double* ubq,
@@ -1169,6 +1277,9 @@ static void launch_flux_df(const DevMesh& m, const Material& mat, const float4* 
     switch (m.Q) {
       case 1: return launch_flux_df_q<3, LAW, MODE, 1>(m, mat, sw, wd, ws, ubq, ubf, d_eps, flux, st);
       case 4: return launch_flux_df_q<3, LAW, MODE, 4>(m, mat, sw, wd, ws, ubq, ubf, d_eps, flux, st);
+      case 8: return launch_flux_df_q<3, LAW, MODE, 8>(m, mat, sw, wd, ws, ubq, ubf, d_eps, flux, st);
+      case 16: return launch_flux_df_q<3, LAW, MODE, 16>(m, mat, sw, wd, ws, ubq, ubf, d_eps, flux, st);
+      case 32: return launch_flux_df_q<3, LAW, MODE, 32>(m, mat, sw, wd, ws, ubq, ubf, d_eps, flux, st);
       default: return launch_flux_df_q<3, LAW, MODE, 9>(m, mat, sw, wd, ws, ubq, ubf, d_eps, flux, st);
     }
   }
@@ -1286,7 +1397,7 @@ static void raise_smem(cudaError_t& e) {
   const cudaError_t r =
       cudaFuncSetAttribute((const void*)k_flux_df<DIM, LAW, MODE, QD>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)df_smem_bytes<DIM>(kMaxS, QD * DIM, QD));
+                           (int)df_smem_bytes<DIM, QD>(kMaxS));
   if (r != cudaSuccess) e = r;
 }
 template <int DIM, int QD>
@@ -1308,6 +1419,9 @@ int setup_df_kernels() {
   raise_smem_all<3, 1>(e);
   raise_smem_all<3, 4>(e);
   raise_smem_all<3, 9>(e);
+  raise_smem_all<3, 8>(e);
+  raise_smem_all<3, 16>(e);
+  raise_smem_all<3, 32>(e);
   rc = e == cudaSuccess ? 0 : (int)e;
   return rc;
 }

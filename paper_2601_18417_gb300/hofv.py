@@ -23,6 +23,7 @@ PC_NONE, PC_AJ64, PC_AJ32, PC_GNN, PC_AJMG, PC_NEJ = -1, 0, 1, 2, 3, 4
 PREC_FP64, PREC_DF64 = 0, 1
 CELL_TENSOR, CELL_SIMPLEX = 0, 1
 POLY_SLOTS = 8  # face slots of a polygon cell
+POLYHEDRON_SLOTS = 16  # face slots of a polyhedral cell
 PTS_CELL_CENTROID, PTS_DISP_QP, PTS_DISP_CENTRE, PTS_TRAC_QP, PTS_CELL_QP = 0, 1, 2, 3, 4
 PTS_FACE_CENTRE, PTS_FACE_QP, PTS_FACE_AREA, PTS_CELL_VOLUME = 5, 6, 7, 8
 
@@ -85,6 +86,7 @@ SIGNATURES = {
     "hofv_set_mesh": (_I, [_P, _I, _I64, _P, _I64, _P, _I64, _P, _P]),
     "hofv_set_mesh_cells": (_I, [_P, _I, _I, _I64, _P, _I64, _P, _I64, _P, _P]),
     "hofv_set_mesh_polygons": (_I, [_P, _I64, _P, _I64, _P, _P, _I64, _P, _P]),
+    "hofv_set_mesh_faces": (_I, [_P, _I64, _P, _I64, _I64, _P, _P, _P, _P, _P]),
     "hofv_set_scheme": (_I, [_P, _I, _I, _I, _D, _D]),
     "hofv_build_stencils": (_I, [_P]),
     "hofv_get_layout": (_I, [_P, C.POINTER(Layout)]),
@@ -205,6 +207,11 @@ class Context:
 
     # ---- set-up --------------------------------------------------------
     def set_mesh(self, mesh, bface_tag):
+        """Quads / hexes, simplices (mesh.simplex), 2-D polygons (mesh.cell_ptr)
+        or polyhedra given face by face (mesh.face_ptr; bface_tag then holds
+        one tag per face, read on boundary faces)."""
+        if hasattr(mesh, "face_ptr"):
+            return self._set_mesh_faces(mesh, bface_tag)
         xyz = np.ascontiguousarray(mesh.xyz, np.float64)
         cn = np.ascontiguousarray(mesh.cell_nodes, np.int64)
         bn = np.ascontiguousarray(mesh.bface_nodes, np.int64)
@@ -221,6 +228,19 @@ class Context:
         return self._check(self._L.hofv_set_mesh_cells(self.h, mesh.dim, kind, xyz.shape[0],
                                                        _ptr(xyz), cn.shape[0], _ptr(cn),
                                                        bn.shape[0], _ptr(bn), _ptr(tag)))
+
+    def _set_mesh_faces(self, mesh, face_tag):
+        xyz = np.ascontiguousarray(mesh.xyz, np.float64)
+        ptr = np.ascontiguousarray(mesh.face_ptr, np.int64)
+        fn = np.ascontiguousarray(mesh.face_nodes, np.int64)
+        own = np.ascontiguousarray(mesh.owner, np.int64)
+        nei = np.ascontiguousarray(mesh.neighbour, np.int64)
+        tag = np.ascontiguousarray(face_tag, np.int32)
+        self.dim = 3
+        self.faces_per_cell = POLYHEDRON_SLOTS
+        return self._check(self._L.hofv_set_mesh_faces(
+            self.h, xyz.shape[0], _ptr(xyz), mesh.n_cells, ptr.shape[0] - 1, _ptr(ptr), _ptr(fn),
+            _ptr(own), _ptr(nei), _ptr(tag)))
 
     def set_scheme(self, p, n_plus, q_per_dir, k_weight=6.0, alpha=0.1):
         return self._check(self._L.hofv_set_scheme(self.h, p, n_plus, q_per_dir, k_weight, alpha))

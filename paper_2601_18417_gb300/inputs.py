@@ -379,11 +379,48 @@ def prism_mesh(n: int, nz: int | None = None, length: float = 1.0, jitter: float
                     n_cells=nc2 * nz, cell_grid=grid, length=length)
 
 
+# outward corner order of each local face of a hex (nodes 0-3 the bottom,
+# counter-clockwise seen from +z, 4-7 the top): x-, x+, y-, y+, z-, z+
+_HEX_FACES = ((0, 4, 7, 3), (1, 2, 6, 5), (0, 1, 5, 4), (3, 7, 6, 2), (0, 3, 2, 1), (4, 5, 6, 7))
+
+
+def hex_face_mesh(n: int, length: float = 1.0, jitter: float = 0.0, seed: int = 0) -> FaceMesh:
+    """structured_mesh(3, n, ...) described face by face: every hex face a
+    quadrilateral polygon, owned by the lower cell id, listed in the order
+    cells and their local faces first meet it; boundary faces keep their
+    domain side."""
+    base = structured_mesh(3, n, length, jitter, seed)
+    cn = base.cell_nodes
+    seen = {}
+    faces, own, nei, side = [], [], [], []
+    for c in range(cn.shape[0]):
+        for lf, loc in enumerate(_HEX_FACES):
+            nodes = [int(cn[c, k]) for k in loc]
+            key = tuple(sorted(nodes))
+            if key in seen:
+                nei[seen[key]] = c
+                continue
+            seen[key] = len(faces)
+            faces.append(np.asarray(nodes, np.int64))
+            own.append(c)
+            nei.append(-1)
+            side.append(lf)
+    nei = np.asarray(nei, np.int64)
+    side = np.where(nei >= 0, -1, np.asarray(side)).astype(np.int32)
+    fptr = np.arange(len(faces) + 1, dtype=np.int64) * 4
+    ck, cj, ci = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    grid = np.stack([ci.ravel(), cj.ravel(), ck.ravel()], axis=1).astype(np.int64)
+    return FaceMesh(dim=3, n=n, xyz=base.xyz, face_ptr=fptr, face_nodes=np.concatenate(faces),
+                    owner=np.asarray(own, np.int64), neighbour=nei, face_side=side,
+                    n_cells=cn.shape[0], cell_grid=grid, length=length)
+
+
 def make_mesh(dim: int, n: int, length: float = 1.0, jitter: float = 0.0, seed: int = 0,
               cells: str = "tensor") -> Mesh:
     """structured_mesh (cells="tensor"), simplex_mesh (cells="simplex"), in
     2-D polygon_mesh (cells="polygon", (n + 1)^2 cells), in 3-D prism_mesh
-    (cells="polyhedron", (n + 1)^2 n cells)."""
+    (cells="polyhedron", (n + 1)^2 n cells) and hex_face_mesh (cells="hexfaces",
+    n^3 hexes given face by face)."""
     if cells == "simplex":
         return simplex_mesh(dim, n, length, jitter, seed)
     if cells == "polygon":
@@ -394,8 +431,12 @@ def make_mesh(dim: int, n: int, length: float = 1.0, jitter: float = 0.0, seed: 
         if dim != 3:
             raise ValueError("polyhedral meshes are three-dimensional")
         return prism_mesh(n, n, length, jitter, seed)
+    if cells == "hexfaces":
+        if dim != 3:
+            raise ValueError("hexes given face by face are three-dimensional")
+        return hex_face_mesh(n, length, jitter, seed)
     if cells != "tensor":
-        raise ValueError("cells must be 'tensor', 'simplex', 'polygon' or 'polyhedron'")
+        raise ValueError("cells must be 'tensor', 'simplex', 'polygon', 'polyhedron' or 'hexfaces'")
     return structured_mesh(dim, n, length, jitter, seed)
 
 
@@ -679,13 +720,16 @@ class Workload:
     alpha: float = 0.1
     k_weight: float = 6.0
     length: float = 1.0      # edge of the square / cube
-    cells: str = "tensor"    # "tensor" (quads / hexes), "simplex" (triangles / tetrahedra)
-    #                          or "polygon" (2-D dual polygons)
+    cells: str = "tensor"    # "tensor" (quads / hexes), "simplex" (triangles / tetrahedra),
+    #                          "polygon" (2-D dual polygons), "polyhedron" (extruded dual
+    #                          polygons, given face by face) or "hexfaces"
 
     @property
     def n_cells(self) -> int:
         if self.cells == "polygon":
             return (self.n + 1) ** 2
+        if self.cells == "polyhedron":
+            return (self.n + 1) ** 2 * self.n
         per = (2 if self.dim == 2 else 6) if self.cells == "simplex" else 1
         return per * self.n ** self.dim
 
@@ -736,6 +780,13 @@ WORKLOADS = {
     # the dual of the 2 x 512^2 triangle mesh: 513^2 polygons of 4-8 sides, cubic LSQ
     "poly512j-p3-mixed": Workload("poly512j-p3-mixed", 2, 512, 3, 10, 3, 0.15, 0, _MU_S, _LAM_S,
                                   "mms-mixed2d", 1244, cells="polygon"),
+    # polyhedra: the dual polygons of 2 x 48^2 triangles extruded through 48 layers
+    # (49^2 x 48 cells of 6 to 10 faces, non-planar faces of 4 to 8 corners), quadratic LSQ,
+    # 2 x 2 points per fan triangle
+    "prism48j-p2-trig": Workload("prism48j-p2-trig", 3, 48, 2, 55, 2, 0.1, 0, _MU_1G, _LAM_1G,
+                                 "mms-trig3d", 1245, cells="polyhedron"),
+    "prism16j-p2-trig": Workload("prism16j-p2-trig", 3, 16, 2, 55, 2, 0.1, 0, _MU_1G, _LAM_1G,
+                                 "mms-trig3d", 1246, cells="polyhedron"),
     # 3-D neo-Hookean, 128^3 jittered hexes, cubic LSQ
     "hex128j-p3-nh": Workload("hex128j-p3-nh", 3, 128, 3, 65, 3, 0.20, 1, 1e6, 4e6, "block",
                               1238, load_steps=10),

@@ -184,3 +184,29 @@ def test_polyhedral_mirror_symmetric_polynomial_gives_zero_residual():
     R = H.residual(pb, pb.u_exact)
     Fs = H.force_scale(pb.orc, 0, 1.0, 1.5, pb.u_exact, pb.ubq, pb.ubf, pb.tbq)
     assert np.abs(R).max() <= 1e-11 * Fs, np.abs(R).max() / Fs
+
+
+def test_hexes_given_face_by_face():
+    """The structured hex grid as polyhedra (4-corner faces): planar cells
+    have volume h^3 and their centres as centroids; jittered cells fill the
+    cube (boundary nodes stay on it) and pass the patch test."""
+    n, h = 4, 1.0 / 4
+    mesh = I.hex_face_mesh(n)
+    assert mesh.n_cells == n ** 3 and np.all(np.diff(mesh.face_ptr) == 4)
+    assert np.array_equal(np.bincount(mesh.face_side[mesh.face_side >= 0]), [n * n] * 6)
+    assert int((mesh.neighbour >= 0).sum()) == 3 * n * n * (n - 1)
+    o = oracle.OracleMesh(mesh, np.zeros(6, np.int32), p=1, n_plus=45, q1=2)
+    assert o.Q == 4 * 4
+    assert np.allclose(o.vol, h ** 3, rtol=1e-13, atol=0)
+    ijk = mesh.cell_grid
+    assert np.abs(o.xc - (ijk + 0.5) * h).max() < 1e-14
+    mj = I.hex_face_mesh(n, jitter=0.2, seed=4)
+    oj = oracle.OracleMesh(mj, np.zeros(6, np.int32), p=1, n_plus=45, q1=2)
+    assert math.isclose(oj.vol.sum(), 1.0, rel_tol=1e-13)
+    tags = I.side_tags("block", 3)
+    field = I.Polynomial(3, 2, seed=7, center=np.full(3, 0.5))
+    pb = H.make_problem(3, 5, 2, 2, jitter=0.2, seed=4, field=field, tags=tags, law=0, mu=1.0,
+                        lam=1.5, kind="hexfaces")
+    R = H.residual(pb, pb.u_exact)
+    Fs = H.force_scale(pb.orc, 0, 1.0, 1.5, pb.u_exact, pb.ubq, pb.ubf, pb.tbq)
+    assert np.abs(R).max() < 1e-12 * Fs, (np.abs(R).max(), Fs)
