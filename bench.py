@@ -171,20 +171,47 @@ def mesh_label(wl):
     return f"{shape}, {int(round(wl.jitter * 100))}% node jitter"
 
 
-def algorithmic_counts(wl, lay):
-    """Per residual launch of the face-flux kernel: FP64 flops of the
-    gradient contraction and the minimum bytes it must move."""
-    d, S, Q = wl.dim, lay.stencil, lay.q_face
-    R = Q * d
+def face_points(wl, lay, mesh=None):
+    """Gauss points with area summed over the faces with a flux and over the
+    displacement faces.  Polyhedral faces count their own fan (corners x
+    q^2), not the corner slots the library pads them to."""
     nfid = lay.n_internal + lay.n_disp
-    flops = 2.0 * nfid * R * S * d + 2.0 * lay.n_disp * R * d
-    bytes_face = 8 * R * S + 4 * S + 8 * Q * 3 + 8 + 8 + 8 * d + 2 * 8 * d
-    bytes_ = nfid * bytes_face + lay.n_disp * (8 * R + 8 * Q * d + 8 * d) + 8 * d * lay.n_cells
+    if mesh is None or not hasattr(mesh, "face_ptr"):
+        return nfid * lay.q_face, lay.n_disp * lay.q_face
+    from paper_2601_18417_gb300 import inputs as I
+    tags = I.side_tags(wl.problem, wl.dim)[np.maximum(mesh.face_side, 0)]
+    pts = np.diff(mesh.face_ptr) * wl.q1 ** 2
+    flux = (mesh.neighbour >= 0) | (tags == 0) | (tags == 2)
+    disp = (mesh.neighbour < 0) & (tags == 0)
+    return int(pts[flux].sum()), int(pts[disp].sum())
+
+
+def algorithmic_counts(wl, lay, mesh=None):
+    """Per residual launch of the face-flux kernel: FP64 flops of the
+    gradient contraction and the minimum bytes it must move (per face:
+    Q d rows of |S| coefficients, the stencil ids, the Q vector areas, the
+    stabilisation data and the flux; per displacement face the ghost
+    coefficients and prescribed values)."""
+    d, S = wl.dim, lay.stencil
+    nfid = lay.n_internal + lay.n_disp
+    pf, pd = face_points(wl, lay, mesh)
+    flops = 2.0 * pf * d * S * d + 2.0 * pd * d * d
+    bytes_ = (8 * d * S * pf + 8 * 3 * pf + nfid * (4 * S + 8 + 8 + 8 * d + 2 * 8 * d)
+              + pd * (8 * d + 8 * d) + lay.n_disp * 8 * d + 8 * d * lay.n_cells)
     # the whole residual (u* prepass + fluxes + assembly), for the HBM view
     nlf = {"simplex": d + 1, "polygon": 8, "polyhedron": 16, "hexfaces": 16}.get(wl.cells, 2 * d)
     res_bytes = bytes_ + lay.n_cells * (8 * nlf * S + 4 * S + 8 * d + 8 * nlf * d * 2
                                         + 8 * d * 2 + 4 * nlf)
     return flops, bytes_, res_bytes
+
+
+def contracted_bytes(wl, lay):
+    """Per launch of the contracted face kernel: per face and stencil slot
+    the id and the d x d matrix (8-byte entries), per face the d x d sum over
+    the stencil, the stabilisation data and the flux; the state once."""
+    d, S = wl.dim, lay.stencil
+    nfid = lay.n_internal + lay.n_disp
+    return nfid * (S * (4 + 8 * d * d) + 8 * d * d + 8 + 8 + 8 * d + 2 * 8 * d) + 8 * d * lay.n_cells
 
 
 # ------------------------------------------------------------------ clocks
@@ -373,7 +400,7 @@ def step_section(args, wl, mesh, ctx, lay, u_ex, precision, rank, ws, peaks_dev,
     kt = np.array([ctx.residual_timed(u, Ru) for _ in range(max(args.steps, 10))])
     flux_ms = float(kt[:, 1].mean())
     res_ms = float(kt.sum(axis=1).mean())
-    flops, fbytes, rbytes = algorithmic_counts(wl, lay)
+    flops, fbytes, rbytes = algorithmic_counts(wl, lay, mesh)
     pk, src = peaks()
     hbm = pk["hbm_gbs"]
     achieved = fbytes / (flux_ms * 1e-3) / 1e9
@@ -415,6 +442,28 @@ def step_section(args, wl, mesh, ctx, lay, u_ex, precision, rank, ws, peaks_dev,
         e2e_s = (time.perf_counter() - t0) / reps
         e2e = {"value": nc / e2e_s / 1e6, "unit": "Mcell/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
+    # linear law: the contracted form (face matrices T_N of the law and the
+    # quadrature folded together), same step
+    contracted = None
+    if wl.law == 0:
+        ctx.set_contraction(True)
+        ctx.residual(u, Ru)
+        kc = np.array([ctx.residual_timed(u, Ru) for _ in range(max(args.steps, 10))])
+        for _ in range(3):
+            step()
+        ms_c = event_ms(step, small, s)
+        tflux_ms = float(kc[:, 1].mean())
+        tb = contracted_bytes(wl, lay)
+        contracted = {
+            "kernel": ("k_tflux_df (double-float contracted face matrices)" if precision == "df64"
+                       else "k_tflux (FP64 contracted face matrices)"),
+            "flux_ms": tflux_ms, "alg_bytes_per_launch": tb,
+            "achieved_gbs": tb / (tflux_ms * 1e-3) / 1e9,
+            "frac": tb / (tflux_ms * 1e-3) / 1e9 / hbm,
+            "residual_ms": float(kc.sum(axis=1).mean()),
+            "step_ms": ms_c, "value": nc / (ms_c * 1e-3) / 1e6}
+        ctx.set_contraction(False)
+        ctx.residual(u, Ru)
     # the other contraction precision, same step
     other = "fp64" if precision == "df64" else "df64"
     ctx.set_precision(hofv.PREC_FP64 if other == "fp64" else hofv.PREC_DF64)
@@ -439,7 +488,8 @@ def step_section(args, wl, mesh, ctx, lay, u_ex, precision, rank, ws, peaks_dev,
                               "flux_ms": float(ko[:, 1].mean()),
                               "residual_ms": float(ko.sum(axis=1).mean())},
             "kernel_ms": {"extrapolation": float(kt[:, 0].mean()), "faces": flux_ms,
-                          "cells": float(kt[:, 2].mean())}}
+                          "cells": float(kt[:, 2].mean())},
+            "contracted": contracted}
 
 
 def linear_solves(ctx, wl, u, Ru, u_ex):
@@ -574,6 +624,7 @@ def run_hofv(args):
               "roofline": sec2["roofline"], "e2e": sec2["e2e"],
               "step_ms_no_graph": sec2["step_ms_no_graph"],
               "step_ms_jacobi_cg": sec2["step_ms_jacobi_cg"], "kernel_ms": sec2["kernel_ms"],
+              "contracted": sec2["contracted"],
               [k for k in sec2 if k.startswith("step_fp64") or k.startswith("step_df64")][0]:
                   sec2[[k for k in sec2 if k.startswith("step_fp64") or
                         k.startswith("step_df64")][0]],
@@ -603,14 +654,15 @@ def run_hofv(args):
                                    f"{KRYLOV_J + 1} vectors; device part replayed as one CUDA "
                                    f"graph",
                            "l2": "inputs larger than L2 (coefficients "
-                                 f"{algorithmic_counts(wl, lay)[2] / 1e9:.1f} GB per residual)",
+                                 f"{algorithmic_counts(wl, lay, mesh)[2] / 1e9:.1f} GB per residual)",
                            "parallelism": "replicas" if ws > 1 else "single GPU"},
                 "roofline": sec["roofline"], "cpu_baseline": cpu, "e2e": sec["e2e"],
                 "gpu_launches": sec["launches"] * args.steps, "clocks": clocks,
                 "setup_s": setup_s, "multigrid": sec["mg"], "device_peaks": peaks_dev,
                 "step_ms_no_graph": sec["step_ms_no_graph"],
                 "step_ms_jacobi_cg": sec["step_ms_jacobi_cg"], other: sec[other],
-                "kernel_ms": sec["kernel_ms"], "solve": solve, "block_solve": block,
+                "kernel_ms": sec["kernel_ms"], "contracted": sec["contracted"],
+                "solve": solve, "block_solve": block,
                 "c2": c2, "impl": "hofv"}
         print(json.dumps(line))
     if ws > 1:

@@ -57,10 +57,14 @@ DevMesh dev_mesh(const hofv_ctx* c) {
   m.aq = c->d_aq;
   m.fstar = c->d_fstar;
   m.fstab = c->d_fstab;
+  m.fql = c->d_fql;
   m.cst = c->d_cst;
   m.cex = c->d_cex;
   m.cface = c->d_cface;
   m.tco = (c->contract && c->tco_valid && c->mat.law == HOFV_LAW_LINEAR) ? c->d_tco : nullptr;
+  const bool tdf = m.tco && c->prec == HOFV_PREC_DF64 && c->tdf_gen == c->tco_gen;
+  m.tco_df = tdf ? c->d_tco_df : nullptr;
+  m.tsum = tdf ? c->d_tsum : nullptr;
   m.nfy = c->nfy;
   m.ng = c->ng;
   m.wst = c->nc + c->ng;
@@ -156,8 +160,11 @@ static void free_built(hofv_ctx* c) {
   c->d_cf = nullptr; c->d_ftag = c->d_fown = c->d_fnei = nullptr;
   c->d_fst = c->d_cst = c->d_fstar = c->d_cface = nullptr;
   c->d_fco = c->d_gco = c->d_cex = c->d_fstab = nullptr;
+  c->d_fql = nullptr;
   c->d_ubq = c->d_ubf = c->d_tbq = c->d_body = c->d_src = nullptr;
   c->d_tco = c->d_gflux = nullptr;
+  c->d_tco_df = c->d_tsum = nullptr;
+  c->tdf_gen = -1;
   c->tco_valid = false;
   c->d_xce = c->d_wext = nullptr;
   c->d_gsrc = c->d_gface = nullptr;
@@ -198,6 +205,29 @@ static int coef_format(hofv_ctx* c, int to_df) {
   if (to_df) launch_row_sums(dev_mesh(c), c->d_fcsum, c->stream);
   HOFV_CUDA(c, cudaGetLastError());
   HOFV_CUDA(c, cudaStreamSynchronize(c->stream));
+  return 0;
+}
+
+// the contracted matrices as float pairs with their FP64 sums over the
+// stencil, for the double-float contracted kernel (made when the residual
+// uses the contracted form in double-float mode)
+static int refresh_tco_df(hofv_ctx* c) {
+  if (!(c->contract && c->tco_valid && c->prec == HOFV_PREC_DF64 && c->have_mat &&
+        c->mat.law == HOFV_LAW_LINEAR && c->built) ||
+      c->tdf_gen == c->tco_gen)
+    return 0;
+  const int64_t count = std::max<int64_t>(c->nftile, 1) * c->S * kTile * c->dim * c->dim;
+  if (!c->d_tco_df) TRY(dev_alloc(c, &c->d_tco_df, count));
+  if (!c->d_tsum) TRY(dev_alloc(c, &c->d_tsum, std::max<int64_t>(c->nftile, 1) * kTile * c->dim * c->dim));
+  HOFV_CUDA(c, cudaMemcpyAsync(c->d_tco_df, c->d_tco, sizeof(double) * count,
+                               cudaMemcpyDeviceToDevice, c->stream));
+  launch_coef_format(c->d_tco_df, count, 1, c->stream);
+  DevMesh m = dev_mesh(c);
+  m.tco_df = c->d_tco_df;
+  launch_tco_sums(m, c->d_tsum, c->stream);
+  HOFV_CUDA(c, cudaGetLastError());
+  HOFV_CUDA(c, cudaStreamSynchronize(c->stream));
+  c->tdf_gen = c->tco_gen;
   return 0;
 }
 
@@ -254,7 +284,8 @@ static int build_contraction(hofv_ctx* c) {
   HOFV_CUDA(c, cudaGetLastError());
   HOFV_CUDA(c, cudaStreamSynchronize(c->stream));
   c->tco_valid = true;
-  return 0;
+  c->tco_gen++;
+  return refresh_tco_df(c);
 }
 
 // the contracted matrices for the current material, whether or not the
@@ -269,7 +300,8 @@ int ensure_tco(hofv_ctx* c) {
   HOFV_CUDA(c, cudaGetLastError());
   HOFV_CUDA(c, cudaStreamSynchronize(c->stream));
   c->tco_valid = true;
-  return 0;
+  c->tco_gen++;
+  return refresh_tco_df(c);
 }
 
 int refresh_source(hofv_ctx* c) {
@@ -314,6 +346,7 @@ int hofv_set_precision(hofv_ctx* c, int prec) {
     TRY(coef_format(c, prec == HOFV_PREC_DF64 ? 1 : 0));
   }
   c->prec = prec;
+  TRY(refresh_tco_df(c));
   return ensure_jv_storage(c);
 }
 
@@ -845,6 +878,19 @@ int hofv_build_stencils(hofv_ctx* c) {
   // ---- per-face data and approximate Jacobian ----
   TRY(dev_alloc(c, &c->d_fstar, std::max<int64_t>(c->nfid, 1) * 2));
   TRY(dev_alloc(c, &c->d_fstab, std::max<int64_t>(c->nfid, 1)));
+  if (c->polyh) {
+    // points of each face with area: its corners x q^2 (the fan slots past a
+    // face's last corner carry none); the face kernels skip the other rows
+    const int64_t nfp = std::max<int64_t>(c->nftile, 1) * kTile;
+    std::vector<int32_t> ql((size_t)nfp, 0);
+    for (int64_t f = 0; f < std::min<int64_t>(c->nf, nfp); ++f) {
+      int k = 0;
+      while (k < c->nfv && c->fnodes[f * c->nfv + k] >= 0) ++k;
+      ql[f] = k * c->q1 * c->q1;
+    }
+    TRY(dev_alloc(c, &c->d_fql, nfp));
+    HOFV_CUDA(c, cudaMemcpy(c->d_fql, ql.data(), sizeof(int32_t) * nfp, cudaMemcpyHostToDevice));
+  }
   TRY(dev_alloc(c, &c->d_aj_diag, nc));
   TRY(dev_alloc(c, &c->d_aj_col, nc * nlf));
   TRY(dev_alloc(c, &c->d_aj_off, nc * nlf));

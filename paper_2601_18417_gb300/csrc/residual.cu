@@ -150,7 +150,8 @@ __device__ __forceinline__ void traction(const double (&G)[3][3], const double* 
     // (eq. nanson).  With B = F F^T, w = cof(F) a and r = J^{-1/3}:
     //   J sigma = mu J^{-2/3} (B - tr(B)/3 I) + kappa/2 (J^2 - 1) I,
     //   t = P a = J sigma w / J = alpha B w + beta w,
-    //   alpha = mu r^5,  beta = kappa/2 (J^2 - 1) r^3 - alpha tr(B) / 3.
+    //   alpha = mu r^5,  beta = kappa/2 (J^2 - 1) r^3 - alpha tr(B) / 3,
+    // and since F^T cof(F) = J I, B w = F (F^T w) = J F a.
     double F[3][3];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
@@ -172,26 +173,22 @@ __device__ __forceinline__ void traction(const double (&G)[3][3], const double* 
     const double r = J > 0.0 ? rcbrt(J) : __longlong_as_double(0x7ff8000000000000LL);
     const double r3 = r * r * r;
     const double alpha = mt.mu * (r * r) * r3;
-    double B[3][3];
+    double trB = 0.0;  // tr(F F^T): the squares of F's entries
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
-      for (int j = i; j < 3; ++j)
-        B[i][j] = B[j][i] = F[i][0] * F[j][0] + F[i][1] * F[j][1] + F[i][2] * F[j][2];
-    const double beta =
-        0.5 * mt.kappa * fma(J, J, -1.0) * r3 - alpha * (B[0][0] + B[1][1] + B[2][2]) * (1.0 / 3.0);
-    double w[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      double sk = 0.0;
-#pragma unroll
-      for (int l = 0; l < DIM; ++l) sk = fma(C[k][l], a[l], sk);
-      w[k] = sk;
-    }
+      for (int j = 0; j < 3; ++j) trB = fma(F[i][j], F[i][j], trB);
+    const double beta = 0.5 * mt.kappa * fma(J, J, -1.0) * r3 - alpha * trB * (1.0 / 3.0);
+    const double aJ = alpha * J;
 #pragma unroll
     for (int i = 0; i < DIM; ++i) {
-      const double bw = B[i][0] * w[0] + B[i][1] * w[1] + B[i][2] * w[2];
-      t[i] = fma(alpha, bw, beta * w[i]);
+      double wi = 0.0, fa = 0.0;
+#pragma unroll
+      for (int l = 0; l < DIM; ++l) {
+        wi = fma(C[i][l], a[l], wi);
+        fa = fma(F[i][l], a[l], fa);
+      }
+      t[i] = fma(aJ, fa, beta * wi);
     }
   }
 }
@@ -220,14 +217,17 @@ __global__ void __launch_bounds__(DIM == 3 ? 864 : 256)
     double acc[DIM];
 #pragma unroll
     for (int j = 0; j < DIM; ++j) acc[j] = 0.0;
+    // rows of points without area (polyhedral fan slots past a face's last
+    // corner) are neither read nor formed
+    const bool live = m.fql == nullptr || r < __ldg(m.fql + f) * DIM;
 #pragma unroll 4
-    for (int n = 0; n < S; ++n) {
+    for (int n = 0; n < (live ? S : 0); ++n) {
       const int32_t id = __ldg(st + n * kTile);
       const double c = __ldg(co + (int64_t)n * kTile * R);
 #pragma unroll
       for (int j = 0; j < DIM; ++j) acc[j] = fma(c, __ldg(w + j * nc + id), acc[j]);
     }
-    if (f >= m.nfi && f < m.nfid) {  // ghost node of a displacement face
+    if (live && f >= m.nfi && f < m.nfid) {  // ghost node of a displacement face
       const int64_t fd = f - m.nfi;
       const double cg = m.gco[fd * R + r];
       const int q = r / DIM;
@@ -282,7 +282,7 @@ __global__ void __launch_bounds__(DIM == 3 ? 864 : 256)
 // triangles of q^2 points, R up to 96): kWideThreads threads walk the rows
 // and points of the tile in strides
 // ---------------------------------------------------------------------
-constexpr int kWideThreads = 768;
+constexpr int kWideThreads = 512;
 
 template <int DIM, int LAW>
 __global__ void __launch_bounds__(kWideThreads)
@@ -303,14 +303,17 @@ __global__ void __launch_bounds__(kWideThreads)
     double acc[DIM];
 #pragma unroll
     for (int j = 0; j < DIM; ++j) acc[j] = 0.0;
+    // rows of points without area (polyhedral fan slots past a face's last
+    // corner) are neither read nor formed
+    const bool live = m.fql == nullptr || r < __ldg(m.fql + f) * DIM;
 #pragma unroll 4
-    for (int n = 0; n < S; ++n) {
+    for (int n = 0; n < (live ? S : 0); ++n) {
       const int32_t id = __ldg(st + n * kTile);
       const double c = __ldg(co + (int64_t)n * kTile * R);
 #pragma unroll
       for (int j = 0; j < DIM; ++j) acc[j] = fma(c, __ldg(w + j * nc + id), acc[j]);
     }
-    if (f >= m.nfi && f < m.nfid) {
+    if (live && f >= m.nfi && f < m.nfid) {
       const int64_t fd = f - m.nfi;
       const double cg = m.gco[fd * R + r];
       const int q = r / DIM;
@@ -497,7 +500,7 @@ static void residual_impl(const DevMesh& m, const Material& mat, const double* w
       if (kTile * m.R <= (DIM == 3 ? 864 : 256)) {
         k_flux<DIM, LAW><<<(unsigned)m.nftile, kTile * m.R, smem, st>>>(m, mat, w, ustar, ubq,
                                                                         ubf, flux);
-      } else {
+      } else if constexpr (DIM == 3) {  // set-up admits no wider 2-D face
         k_flux_wide<DIM, LAW><<<(unsigned)m.nftile, kWideThreads, smem, st>>>(m, mat, w, ustar,
                                                                               ubq, ubf, flux);
       }
@@ -983,7 +986,9 @@ __device__ __forceinline__ void cp_async_wait_all() {
 // cells' splits into shared memory (16-byte asynchronous copies, [S][FPB]
 // entries) and turns each into the double-float difference to its face's
 // reference (exact differences of the splits); the contraction then reads
-// them from shared memory (the R threads of a face share each entry).  Each
+// them from shared memory (the R threads of a face share each entry) and
+// skips the reference itself, whose difference is zero: its coefficient
+// enters only through the row sum and is never read.  Each
 // thread streams its coefficient row through a ring of RING registers: the
 // coefficient of slot n + RING is requested when slot n is consumed, keeping
 // RING coalesced 8-byte loads in flight per thread; with R a compile-time
@@ -993,15 +998,19 @@ __device__ __forceinline__ void cp_async_wait_all() {
 // threads, four blocks an SM, for 3 x 3 points (measured on the 128^3
 // neo-Hookean block: 7 % faster than half tiles two an SM, 10 % slower with
 // eighth tiles), half tiles otherwise; faces with many points (polyhedral
-// fans, R = 48 or 96) take half or quarter tiles of 768 threads, one an SM.
+// fans, R = 48 or 96) take quarter or eighth tiles of 384 threads, two an
+// SM.  Rows of points without area (polyhedral fan slots past a face's last
+// corner) load nothing.
 template <int DIM, int QD>
 struct DfShape {
-  static constexpr int FPB = DIM == 2    ? 32
-                             : QD == 9   ? 8
-                             : 16 * QD * DIM <= 768 ? 16 : 8;  // faces per block
+  static constexpr int FPB = DIM == 2  ? 32
+                             : QD == 9  ? 8
+                             : QD == 16 ? 8
+                             : QD == 32 ? 4
+                                        : 16;  // faces per block
   static constexpr int RING = DIM == 3 ? 8 : 4;  // coefficient loads in flight per thread
   static constexpr int THREADS = FPB * QD * DIM;
-  static constexpr int MIN_BLOCKS = DIM == 2 ? 6 : QD == 9 ? 4 : (THREADS <= 512 ? 2 : 1);  // per SM
+  static constexpr int MIN_BLOCKS = DIM == 2 ? 6 : (THREADS <= 256 ? 4 : 2);  // per SM
 };
 
 // dynamic shared memory: the gathered cell values and the faces' references,
@@ -1009,7 +1018,7 @@ struct DfShape {
 template <int DIM, int QD>
 static size_t df_smem_bytes(int S) {
   constexpr int FPB = DfShape<DIM, QD>::FPB, R = QD * DIM;
-  const size_t gath = (size_t)(S + 1) * FPB * DIM * 16;
+  const size_t gath = (size_t)S * FPB * DIM * 16;
   const size_t law = (size_t)FPB * (R * DIM + QD * DIM) * sizeof(double);
   return gath > law ? gath : law;
 }
@@ -1025,8 +1034,9 @@ __global__ void __launch_bounds__(DfShape<DIM, QD>::THREADS, DfShape<DIM, QD>::M
   constexpr int CS = kTile * R;  // coefficient stride between stencil slots
   extern __shared__ __align__(16) double sm[];
   const int S = m.S;
-  float4* us = reinterpret_cast<float4*>(sm);  // [S][FPB][DIM] gathered values, then differences
-  float4* ur = us + (size_t)S * FPB * DIM;     // [FPB][DIM] the faces' reference values
+  // [S][FPB][DIM] gathered values; slots 1.. then hold the differences to
+  // slot 0, the faces' reference cells (whose own difference is zero)
+  float4* us = reinterpret_cast<float4*>(sm);
   double* Gs = sm;                              // [FPB][R][DIM] after the contraction
   double* Ts = sm + FPB * R * DIM;              // [FPB][Q][DIM]
   const int64_t tile = blockIdx.x / BPT;
@@ -1039,10 +1049,17 @@ __global__ void __launch_bounds__(DfShape<DIM, QD>::THREADS, DfShape<DIM, QD>::M
   const int32_t* __restrict__ st = m.fst + tile * (int64_t)S * kTile + fb;
   const float2* __restrict__ co =
       reinterpret_cast<const float2*>(m.fco) + tile * (int64_t)S * CS + fb * R + it;
+  // rows of points without area (polyhedral fan slots past a face's last
+  // corner) read no coefficient and keep a zero gradient
+  const bool live = m.fql == nullptr || r < __ldg(m.fql + f) * DIM;
+  // stencil slots this thread contracts: 1 .. S-1 (slot 0, the reference,
+  // enters only through the row sums)
+  const int SL = live ? S - 1 : 0;
+  co += CS;  // coefficients of slot 1
   // the first coefficients of the ring, then the gather of the cell values
   float2 cq[kRing];
 #pragma unroll
-  for (int d = 0; d < kRing; ++d) cq[d] = d < S ? __ldg(co + d * CS) : make_float2(0.f, 0.f);
+  for (int d = 0; d < kRing; ++d) cq[d] = d < SL ? __ldg(co + d * CS) : make_float2(0.f, 0.f);
   for (int t = it; t < S * FPB; t += FPB * R) {
     const int n = t / FPB, fj = t % FPB;
     const int32_t id = __ldg(st + n * kTile + fj);
@@ -1051,10 +1068,8 @@ __global__ void __launch_bounds__(DfShape<DIM, QD>::THREADS, DfShape<DIM, QD>::M
   }
   cp_async_wait_all();
   __syncthreads();
-  for (int t = it; t < FPB * DIM; t += FPB * R) ur[t] = us[t];  // slot 0: the nearest cell
-  __syncthreads();
-  for (int t = it; t < S * FPB * DIM; t += FPB * R) {
-    const float2 dv = diff3(us[t], ur[t % (FPB * DIM)]);
+  for (int t = FPB * DIM + it; t < S * FPB * DIM; t += FPB * R) {
+    const float2 dv = diff3(us[t], us[t % (FPB * DIM)]);
     us[t] = make_float4(dv.x, dv.y, 0.f, 0.f);
   }
   __syncthreads();
@@ -1062,7 +1077,7 @@ __global__ void __launch_bounds__(DfShape<DIM, QD>::THREADS, DfShape<DIM, QD>::M
   float s[DIM], e[DIM];
 #pragma unroll
   for (int j = 0; j < DIM; ++j) s[j] = e[j] = 0.f;
-  const float4* __restrict__ uf = us + fi * DIM;
+  const float4* __restrict__ uf = us + FPB * DIM + fi * DIM;  // slot 1 of the thread's face
   auto mac_slot = [&](int n, float2 c) {
 #pragma unroll
     for (int j = 0; j < DIM; ++j) {
@@ -1072,7 +1087,7 @@ __global__ void __launch_bounds__(DfShape<DIM, QD>::THREADS, DfShape<DIM, QD>::M
   };
   int n0 = 0;
   // steady part: every request in range
-  for (; n0 + 2 * kRing <= S; n0 += kRing) {
+  for (; n0 + 2 * kRing <= SL; n0 += kRing) {
     const float2* cn = co + (n0 + kRing) * CS;
 #pragma unroll
     for (int d = 0; d < kRing; ++d) {
@@ -1085,9 +1100,9 @@ __global__ void __launch_bounds__(DfShape<DIM, QD>::THREADS, DfShape<DIM, QD>::M
 #pragma unroll
   for (int d = 0; d < 2 * kRing; ++d) {
     const int n = n0 + d;
-    if (n < S) {
+    if (n < SL) {
       const float2 c = cq[d % kRing];
-      if (n + kRing < S) cq[d % kRing] = __ldg(co + (n + kRing) * CS);
+      if (n + kRing < SL) cq[d % kRing] = __ldg(co + (n + kRing) * CS);
       mac_slot(n, c);
     }
   }
@@ -1096,12 +1111,12 @@ __global__ void __launch_bounds__(DfShape<DIM, QD>::THREADS, DfShape<DIM, QD>::M
     // + w_N0 sum_N c_N, in FP64
     const int32_t id0 = __ldg(st + fi);
     const int64_t ldw = m.wst;
-    const double cs = m.fcsum[f * R + r];
+    const double cs = live ? m.fcsum[f * R + r] : 0.0;
     double g[DIM];
 #pragma unroll
     for (int j = 0; j < DIM; ++j) g[j] = fma(cs, __ldg(wd + j * ldw + id0), ff_value(s[j], e[j]));
     if (MODE == kDfResidual || MODE == kDfFill) {
-      if (f >= m.nfi && f < m.nfid) {  // ghost node of a displacement face (prescribed data)
+      if (live && f >= m.nfi && f < m.nfid) {  // ghost node of a displacement face (prescribed data)
         const int64_t fd = f - m.nfi;
         const double cg = m.gco[fd * R + r];
         const int q = r / DIM;
@@ -1213,6 +1228,154 @@ __global__ void __launch_bounds__(32 * DIM)
   }
 }
 
+// Contracted linear form in double-float arithmetic: flux_{f,i} =
+// sum_N sum_k T_{N,ik} (w_N - w_N0)_k + sum_k (sum_N T_{N,ik}) w_N0,k + the
+// stabilisation, with the matrices stored as float pairs (tco_df) and their
+// FP64 sums over the stencil (tsum), N0 the face's first stencil cell (the
+// same exact identity as the per-point kernel).  One block takes one tile of
+// 32 faces.  The block first turns the three-float splits of its faces'
+// stencil cells into double-float differences to the faces' references in
+// shared memory ([S][32][DIM] pairs); then thread (g, face, row i) contracts
+// the stencil slots g, g + G, ... of its row (G = kTdfSplit groups, so that
+// each SM holds enough threads to keep the coefficient stream in flight),
+// and the groups' compensated sums are added in shared memory.  HOM: the
+// homogeneous part of the Jacobian-vector product (no prescribed values).
+constexpr int kTdfSplit = 4;
+
+template <int DIM>
+struct TdfShape {
+  static constexpr int THREADS = kTile * DIM * kTdfSplit;
+  static constexpr int MIN_BLOCKS = DIM == 3 ? 3 : 6;  // per SM
+  static constexpr int RING = 4;  // stencil slots of coefficients in flight per thread
+};
+
+template <int DIM>
+static size_t tdf_smem_bytes(int S) {
+  const size_t diffs = (size_t)S * kTile * DIM * sizeof(float2);
+  const size_t red = (size_t)kTdfSplit * kTile * DIM * sizeof(float2);
+  return diffs > red ? diffs : red;
+}
+
+template <int DIM, bool HOM>
+__global__ void __launch_bounds__(TdfShape<DIM>::THREADS, TdfShape<DIM>::MIN_BLOCKS)
+    k_tflux_df(DevMesh m, double alpha_kbar, const float4* __restrict__ sw,
+               const double* __restrict__ wd, const double* __restrict__ ws,
+               const double* __restrict__ ubf, double* __restrict__ flux) {
+  constexpr int RD = kTile * DIM;        // rows of a tile
+  constexpr int CS = RD * DIM;           // pairs of one stencil slot of a tile
+  constexpr int kRing = TdfShape<DIM>::RING;
+  extern __shared__ __align__(16) double sm[];
+  float2* dv = reinterpret_cast<float2*>(sm);  // [S][32][DIM] differences, then [G][RD] sums
+  const int S = m.S;
+  const int64_t tile = blockIdx.x;
+  const int it = threadIdx.x;
+  const int32_t* __restrict__ st = m.fst + tile * (int64_t)S * kTile;
+  // (1) differences of the split state to each face's reference cell
+  for (int t = it; t < S * RD; t += TdfShape<DIM>::THREADS) {
+    const int n = t / RD, rem = t % RD, fj = rem / DIM, k = rem % DIM;
+    const int32_t id = __ldg(st + n * kTile + fj), id0 = __ldg(st + fj);
+    dv[t] = diff3(__ldg(sw + (int64_t)id * DIM + k), __ldg(sw + (int64_t)id0 * DIM + k));
+  }
+  __syncthreads();
+  // (2) thread (g, row ri = fi * DIM + i): slots g, g + G, ...
+  const int ri = it % RD, g = it / RD, fi = ri / DIM, i = ri % DIM;
+  const float2* __restrict__ tc =
+      reinterpret_cast<const float2*>(m.tco_df) + tile * (int64_t)S * CS + ri * DIM;
+  const float2* __restrict__ df = dv + fi * DIM;
+  float s = 0.f, e = 0.f;
+  float2 cq[kRing][DIM];
+#pragma unroll
+  for (int d = 0; d < kRing; ++d) {
+    const int n = g + d * kTdfSplit;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k)
+      cq[d][k] = n < S ? __ldg(tc + (int64_t)n * CS + k) : make_float2(0.f, 0.f);
+  }
+  for (int n0 = g; n0 < S; n0 += kRing * kTdfSplit) {
+#pragma unroll
+    for (int d = 0; d < kRing; ++d) {
+      const int n = n0 + d * kTdfSplit;
+      if (n < S) {
+        float2 c[DIM];
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) c[k] = cq[d][k];
+        const int nn = n + kRing * kTdfSplit;
+        if (nn < S) {
+#pragma unroll
+          for (int k = 0; k < DIM; ++k) cq[d][k] = __ldg(tc + (int64_t)nn * CS + k);
+        }
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) {
+          const float2 a = df[n * RD + k];
+          ff_mac(c[k].x, c[k].y, a.x, a.y, s, e);
+        }
+      }
+    }
+  }
+  __syncthreads();  // the differences are overwritten by the groups' sums
+  dv[g * RD + ri] = make_float2(s, e);
+  __syncthreads();
+  if (g != 0) return;
+  for (int h = 1; h < kTdfSplit; ++h) {
+    const float2 o = dv[h * RD + ri];
+    float t, r;
+    two_sum(s, o.x, t, r);
+    s = t;
+    e = __fadd_rn(e, __fadd_rn(o.y, r));
+  }
+  const int64_t f = tile * kTile + fi;
+  if (f >= m.nfid) return;
+  // + (sum_N T_N) w_N0 in FP64, then the stabilisation
+  const int32_t id0 = __ldg(st + fi);
+  const int64_t ldw = m.wst;
+  double acc = ff_value(s, e);
+#pragma unroll
+  for (int k = 0; k < DIM; ++k)
+    acc = fma(m.tsum[(f * DIM + i) * DIM + k], __ldg(wd + k * ldw + id0), acc);
+  const int32_t sp = m.fstar[2 * f], sn = m.fstar[2 * f + 1];
+  const bool sym = sn < 0 && f >= m.nfi + m.nfd;
+  const double up = ws[(int64_t)sp * DIM + i];
+  const double other = sn >= 0 ? ws[(int64_t)sn * DIM + i]
+                       : sym   ? mirror_i<DIM>(ws + (int64_t)sp * DIM, m.nrm + 3 * f, i)
+                       : HOM   ? 0.0
+                               : ubf[(f - m.nfi) * DIM + i];
+  flux[f * DIM + i] = fma(alpha_kbar * m.fstab[f], other - up, acc);
+}
+
+// tsum[f][i][k] = sum_N of the stored pair T_{N,ik} of face f
+template <int DIM>
+__global__ void k_tco_sums(DevMesh m, double* __restrict__ tsum) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;  // (face, i, k)
+  if (e >= m.nftile * kTile * DIM * DIM) return;
+  const int64_t tile = e / (kTile * DIM * DIM);
+  const int r = (int)(e % (kTile * DIM * DIM));  // (fi * DIM + i) * DIM + k within the tile
+  const float2* co =
+      reinterpret_cast<const float2*>(m.tco_df) + tile * (int64_t)m.S * kTile * DIM * DIM + r;
+  double sum = 0.0;
+  for (int n = 0; n < m.S; ++n) {
+    const float2 p = co[(int64_t)n * kTile * DIM * DIM];
+    sum += ff_value(p.x, p.y);
+  }
+  tsum[e] = sum;
+}
+
+void launch_tco_sums(const DevMesh& m, double* tsum, cudaStream_t st) {
+  const int64_t n = m.nftile * kTile * m.dim * m.dim;
+  if (n == 0) return;
+  if (m.dim == 2)
+    k_tco_sums<2><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(m, tsum);
+  else
+    k_tco_sums<3><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(m, tsum);
+}
+
+template <int DIM, bool HOM>
+static void launch_tflux_df(const DevMesh& m, double alpha_kbar, const float4* sw,
+                            const double* wd, const double* ws, const double* ubf, double* flux,
+                            cudaStream_t st) {
+  k_tflux_df<DIM, HOM><<<(unsigned)m.nftile, TdfShape<DIM>::THREADS, tdf_smem_bytes<DIM>(m.S),
+                         st>>>(m, alpha_kbar, sw, wd, ws, ubf, flux);
+}
+
 // Jv assembly from face-flux differences: out = sum_f +-dflux_f / eps, plus
 // the inertia term of v (linear, so its difference quotient is exact)
 template <int DIM, int NLF>
@@ -1309,7 +1472,9 @@ static void residual_impl_df(const DevMesh& m, const Material& mat, const double
   launch_ustar_df<DIM>(m, m.su, w, ustar, st);
   if (ev) cudaEventRecord(ev[1], st);
   if (m.nftile > 0) {
-    if (LAW == HOFV_LAW_LINEAR && m.tco) {
+    if (LAW == HOFV_LAW_LINEAR && m.tco && m.tco_df) {
+      launch_tflux_df<DIM, false>(m, mat.alpha * mat.kbar, m.su, w, ustar, ubf, flux, st);
+    } else if (LAW == HOFV_LAW_LINEAR && m.tco) {
       if (m.nfy > 0) k_sym_other<DIM><<<(unsigned)((m.nfy + 127) / 128), 128, 0, st>>>(m, ustar);
       k_tflux<DIM><<<(unsigned)m.nftile, 32 * DIM, 0, st>>>(m, m.tco, mat.alpha * mat.kbar, w,
                                                             ustar, ubf, flux);
@@ -1334,7 +1499,9 @@ static void jv_impl_df(const DevMesh& m, const Material& mat, const double* v,
   v = split_state<DIM>(m, v, m.vext, m.sv, st);
   launch_ustar_df<DIM>(m, m.sv, v, m.ustar_v, st);
   if (m.nftile > 0) {
-    if (LAW == HOFV_LAW_LINEAR && m.tco)
+    if (LAW == HOFV_LAW_LINEAR && m.tco && m.tco_df)
+      launch_tflux_df<DIM, true>(m, mat.alpha * mat.kbar, m.sv, v, m.ustar_v, nullptr, flux, st);
+    else if (LAW == HOFV_LAW_LINEAR && m.tco)
       k_tflux_hom<DIM><<<(unsigned)m.nftile, 32 * DIM, 0, st>>>(m, m.tco, mat.alpha * mat.kbar, v,
                                                                 m.ustar_v, flux);
     else if (LAW == HOFV_LAW_LINEAR)
@@ -1408,10 +1575,21 @@ static void raise_smem_all(cudaError_t& e) {
   raise_smem<DIM, 1, kDfFill, QD>(e);
   raise_smem<DIM, 1, kDfJv, QD>(e);
 }
+template <int DIM, bool HOM>
+static void raise_smem_tdf(cudaError_t& e) {
+  const cudaError_t r = cudaFuncSetAttribute((const void*)k_tflux_df<DIM, HOM>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)tdf_smem_bytes<DIM>(kMaxS));
+  if (r != cudaSuccess) e = r;
+}
 int setup_df_kernels() {
   static int rc = -1;
   if (rc >= 0) return rc;
   cudaError_t e = cudaSuccess;
+  raise_smem_tdf<2, false>(e);
+  raise_smem_tdf<2, true>(e);
+  raise_smem_tdf<3, false>(e);
+  raise_smem_tdf<3, true>(e);
   raise_smem_all<2, 1>(e);
   raise_smem_all<2, 2>(e);
   raise_smem_all<2, 3>(e);

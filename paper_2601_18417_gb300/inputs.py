@@ -785,7 +785,7 @@ WORKLOADS = {
     # 2 x 2 points per fan triangle
     "prism48j-p2-trig": Workload("prism48j-p2-trig", 3, 48, 2, 55, 2, 0.1, 0, _MU_1G, _LAM_1G,
                                  "mms-trig3d", 1245, cells="polyhedron"),
-    "prism16j-p2-trig": Workload("prism16j-p2-trig", 3, 16, 2, 55, 2, 0.1, 0, _MU_1G, _LAM_1G,
+    "prism24j-p2-trig": Workload("prism24j-p2-trig", 3, 24, 2, 55, 2, 0.1, 0, _MU_1G, _LAM_1G,
                                  "mms-trig3d", 1246, cells="polyhedron"),
     # 3-D neo-Hookean, 128^3 jittered hexes, cubic LSQ
     "hex128j-p3-nh": Workload("hex128j-p3-nh", 3, 128, 3, 65, 3, 0.20, 1, 1e6, 4e6, "block",

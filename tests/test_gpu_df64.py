@@ -181,9 +181,11 @@ def test_df64_switching_rewrites_coefficients_in_place():
     ctx.close()
 
 
-def test_df64_symmetry_faces():
+@pytest.mark.parametrize("contract", [False, True])
+def test_df64_symmetry_faces(contract):
     """Symmetry faces (mirrored stencil nodes, reflected states, the mirror
-    of the face's own extrapolated value beyond it): residual and fused Jv."""
+    of the face's own extrapolated value beyond it): residual and fused Jv,
+    per point and in the contracted form (its double-float kernel)."""
     import torch
     for dim, n, p in ((2, 20, 3), (3, 8, 2)):
         tags = np.zeros(2 * dim, np.int32)
@@ -193,6 +195,7 @@ def test_df64_symmetry_faces():
                             lam=1.5)
         ctx = H.gpu_context(pb)
         ctx.set_precision(hofv.PREC_DF64)
+        ctx.set_contraction(contract)
         rng = np.random.default_rng(3)
         u = rng.standard_normal((dim, pb.orc.nc))
         err = np.abs(_residual(ctx, u) - H.residual(pb, u)).max()

@@ -47,7 +47,7 @@ def state(wl, xc, u_ex, seed=1):
 
 @pytest.mark.parametrize("name", ["quad512j-p3-mixed", "hex96-p3-trig", "hex64j-p2-nh",
                                   "hex128j-p3-nh", "tri512j-p3-mixed", "tet32j-p2-trig",
-                                  "poly512j-p3-mixed"])
+                                  "poly512j-p3-mixed", "prism48j-p2-trig"])
 def test_full_size_residual_on_sampled_cells(name):
     import torch
     wl, mesh, ctx, lay, setup_s, u_ex, field = bench.build_workload(name)

@@ -177,13 +177,13 @@ def test_polyhedra_reconstruction_coefficients(name):
 
 
 @pytest.mark.parametrize("name", list(CASES))
-@pytest.mark.parametrize("form", ["fp64", "contracted", "df64"])
+@pytest.mark.parametrize("form", ["fp64", "contracted", "df64", "contracted-df64"])
 def test_polyhedra_residual_parity(name, form):
     pb, ctx = problem(name)
-    if form == "contracted" and pb.law != 0:
+    if form.startswith("contracted") and pb.law != 0:
         pytest.skip("the contracted form is for the linear law")
-    ctx.set_contraction(form == "contracted")
-    ctx.set_precision(hofv.PREC_DF64 if form == "df64" else hofv.PREC_FP64)
+    ctx.set_contraction(form.startswith("contracted"))
+    ctx.set_precision(hofv.PREC_DF64 if form.endswith("df64") else hofv.PREC_FP64)
     try:
         for seed in (0, 1):
             u = smooth_u(pb, seed, amp=1e-2 if pb.law == 1 else 1.0)
@@ -308,7 +308,7 @@ def _sym_problem(name):
 
 
 @pytest.mark.parametrize("name", list(SYM))
-@pytest.mark.parametrize("form", ["fp64", "contracted", "df64"])
+@pytest.mark.parametrize("form", ["fp64", "contracted", "df64", "contracted-df64"])
 def test_polyhedra_symmetry_parity(name, form):
     pb, ctx = _sym_problem(name)
     o = pb.orc
@@ -317,8 +317,8 @@ def test_polyhedra_symmetry_parity(name, form):
     st, _ = ctx.get_face_data(lo, hi - lo, coef=False)
     for k, f in enumerate(range(lo, hi)):
         assert np.array_equal(st[k], o.face_stencil(f)), f
-    ctx.set_contraction(form == "contracted")
-    ctx.set_precision(hofv.PREC_DF64 if form == "df64" else hofv.PREC_FP64)
+    ctx.set_contraction(form.startswith("contracted"))
+    ctx.set_precision(hofv.PREC_DF64 if form.endswith("df64") else hofv.PREC_FP64)
     try:
         u = smooth_u(pb, 2)
         err = np.abs(_gpu_residual(ctx, u) - H.residual(pb, u)).max()
