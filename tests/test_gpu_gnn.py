@@ -30,7 +30,7 @@ def _tensors(theta, dim):
     return [W0, b0] + [x for pair in zip(Ws, bs) for x in pair] + [Wd, bd]
 
 
-@pytest.mark.parametrize("dim,n", [(3, 5), (2, 12)])
+@pytest.mark.parametrize("dim,n", [(3, 5), (2, 12), (3, 12)])
 def test_gnn_forward_and_gradient_match_reference(dim, n):
     import torch
     ctx, o, col, w, bnd = _setup(dim, n)
