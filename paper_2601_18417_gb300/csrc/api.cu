@@ -62,9 +62,6 @@ DevMesh dev_mesh(const hofv_ctx* c) {
   m.cex = c->d_cex;
   m.cface = c->d_cface;
   m.tco = (c->contract && c->tco_valid && c->mat.law == HOFV_LAW_LINEAR) ? c->d_tco : nullptr;
-  const bool tdf = m.tco && c->prec == HOFV_PREC_DF64 && c->tdf_gen == c->tco_gen;
-  m.tco_df = tdf ? c->d_tco_df : nullptr;
-  m.tsum = tdf ? c->d_tsum : nullptr;
   m.nfy = c->nfy;
   m.ng = c->ng;
   m.wst = c->nc + c->ng;
@@ -163,8 +160,6 @@ static void free_built(hofv_ctx* c) {
   c->d_fql = nullptr;
   c->d_ubq = c->d_ubf = c->d_tbq = c->d_body = c->d_src = nullptr;
   c->d_tco = c->d_gflux = nullptr;
-  c->d_tco_df = c->d_tsum = nullptr;
-  c->tdf_gen = -1;
   c->tco_valid = false;
   c->d_xce = c->d_wext = nullptr;
   c->d_gsrc = c->d_gface = nullptr;
@@ -205,29 +200,6 @@ static int coef_format(hofv_ctx* c, int to_df) {
   if (to_df) launch_row_sums(dev_mesh(c), c->d_fcsum, c->stream);
   HOFV_CUDA(c, cudaGetLastError());
   HOFV_CUDA(c, cudaStreamSynchronize(c->stream));
-  return 0;
-}
-
-// the contracted matrices as float pairs with their FP64 sums over the
-// stencil, for the double-float contracted kernel (made when the residual
-// uses the contracted form in double-float mode)
-static int refresh_tco_df(hofv_ctx* c) {
-  if (!(c->contract && c->tco_valid && c->prec == HOFV_PREC_DF64 && c->have_mat &&
-        c->mat.law == HOFV_LAW_LINEAR && c->built) ||
-      c->tdf_gen == c->tco_gen)
-    return 0;
-  const int64_t count = std::max<int64_t>(c->nftile, 1) * c->S * kTile * c->dim * c->dim;
-  if (!c->d_tco_df) TRY(dev_alloc(c, &c->d_tco_df, count));
-  if (!c->d_tsum) TRY(dev_alloc(c, &c->d_tsum, std::max<int64_t>(c->nftile, 1) * kTile * c->dim * c->dim));
-  HOFV_CUDA(c, cudaMemcpyAsync(c->d_tco_df, c->d_tco, sizeof(double) * count,
-                               cudaMemcpyDeviceToDevice, c->stream));
-  launch_coef_format(c->d_tco_df, count, 1, c->stream);
-  DevMesh m = dev_mesh(c);
-  m.tco_df = c->d_tco_df;
-  launch_tco_sums(m, c->d_tsum, c->stream);
-  HOFV_CUDA(c, cudaGetLastError());
-  HOFV_CUDA(c, cudaStreamSynchronize(c->stream));
-  c->tdf_gen = c->tco_gen;
   return 0;
 }
 
@@ -284,8 +256,7 @@ static int build_contraction(hofv_ctx* c) {
   HOFV_CUDA(c, cudaGetLastError());
   HOFV_CUDA(c, cudaStreamSynchronize(c->stream));
   c->tco_valid = true;
-  c->tco_gen++;
-  return refresh_tco_df(c);
+  return 0;
 }
 
 // the contracted matrices for the current material, whether or not the
@@ -300,8 +271,7 @@ int ensure_tco(hofv_ctx* c) {
   HOFV_CUDA(c, cudaGetLastError());
   HOFV_CUDA(c, cudaStreamSynchronize(c->stream));
   c->tco_valid = true;
-  c->tco_gen++;
-  return refresh_tco_df(c);
+  return 0;
 }
 
 int refresh_source(hofv_ctx* c) {
@@ -346,7 +316,6 @@ int hofv_set_precision(hofv_ctx* c, int prec) {
     TRY(coef_format(c, prec == HOFV_PREC_DF64 ? 1 : 0));
   }
   c->prec = prec;
-  TRY(refresh_tco_df(c));
   return ensure_jv_storage(c);
 }
 

@@ -13,11 +13,14 @@
 //   sum_i |z_out_i - delta_i|^2 / sum_i |delta_i|^2
 // over (residual, Newton correction) pairs recorded by the solver.
 //
-// Node-wise GEMMs run on the tensor cores (mma.sync m16n8k16, BF16 inputs,
-// FP32 accumulation) from padded shared-memory tiles of 64 nodes; the
-// message passing is a gather over the symmetric graph, so its transpose in
-// the backward pass is the same gather (no atomics); weight gradients are
-// accumulated per block and reduced in block order (deterministic).
+// The message-passing layers' node-wise GEMMs (K = 128, forward and both
+// backward products) run on the 5th-generation tensor cores: tcgen05.mma
+// with BF16 operands in shared memory and FP32 accumulators in tensor
+// memory, 128 nodes a tile.  The 16-wide encoder keeps warp-level mma.sync
+// m16n8k16 tiles of 64 nodes.  The message passing is a gather over the
+// symmetric graph, so its transpose in the backward pass is the same gather
+// (no atomics); weight gradients are accumulated per block and reduced in
+// block order (deterministic).
 #include <cuda_bf16.h>
 #include <math.h>
 #include <string.h>
@@ -38,9 +41,6 @@ constexpr int GF = 16;          // input features (padded)
 constexpr int GL = 4;           // message-passing layers
 constexpr int GT = 64;          // nodes per tile
 constexpr int GTHREADS = 128;   // 4 warps, 16 nodes each
-constexpr int kLayerBwdSmem = (int)sizeof(__nv_bfloat16) *
-                              (64 * (2 * 64 + 8) + 2 * 64 * (64 + 8) + 64 * (64 + 8) +
-                               64 * (64 + 8) + 2 * 64 * (64 + 8));
 typedef __nv_bfloat16 bf16;
 
 struct Gnn {
@@ -191,81 +191,367 @@ __global__ void __launch_bounds__(GTHREADS)
   }
 }
 
-// gather m_i = sum_k w_ik h_{col_ik} for the tile into smem (bf16), plus the
-// tile's own h, as the 64 x 128 operand [h | m]
-__device__ __forceinline__ void load_hm_tile(int nlf, int64_t n, int64_t base,
-                                             const bf16* __restrict__ h,
-                                             const int32_t* __restrict__ col,
-                                             const float* __restrict__ w, bf16 (*sX)[2 * GH + 8]) {
-  for (int e = threadIdx.x; e < GT * (GH / 8); e += GTHREADS) {
+// ---------------------------------------------------------------------
+// the same layer on the 5th-generation tensor cores: 128 nodes a block, the
+// operands [h | m] (128 x 128) and W (64 x 128) in shared memory in the
+// canonical K-major layout without swizzle (8-row x 16-byte core matrices;
+// K-direction core stride kTcLboA / kTcLboB, row-group stride 128 bytes),
+// one thread issuing eight tcgen05.mma of K = 16 into a 128 x 64 FP32
+// accumulator in tensor memory (64 columns), completion signalled on an
+// mbarrier, and each warp reading its 32 rows back with tcgen05.ld.
+// ---------------------------------------------------------------------
+constexpr int kTcRows = 128;                       // nodes per block (MMA M)
+constexpr int kTcLboA = kTcRows * 16;              // bytes between K-adjacent core matrices of A
+constexpr int kTcLboB = GH * 16;                   // ... of W
+constexpr int kTcSmem = kTcRows * 2 * GH * 2 + GH * 2 * GH * 2;  // A then W, bytes
+constexpr long long kTcSpin = 1LL << 26;           // mbarrier polls before giving up
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// byte offset of element (row, k) of a K-major operand with lbo bytes
+// between K-adjacent core matrices and 128 between row-adjacent ones
+__device__ __forceinline__ int tc_off(int row, int k, int lbo) {
+  return (k >> 3) * lbo + (row >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2;
+}
+
+// shared-memory matrix descriptor: start, leading (K) and stride (row
+// group) byte offsets in 16-byte units, descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+
+__global__ void __launch_bounds__(128)
+    k_gnn_layer_tc(int nlf, int64_t n, int64_t npad, const bf16* __restrict__ hin,
+                   const int32_t* __restrict__ col, const float* __restrict__ w,
+                   const bf16* __restrict__ Wb, const float* __restrict__ b, bf16* aout,
+                   bf16* hout) {
+  extern __shared__ __align__(1024) uint8_t tsm[];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tslot;
+  uint8_t* sA = tsm;
+  uint8_t* sW = tsm + kTcRows * 2 * GH * 2;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int64_t base = (int64_t)blockIdx.x * kTcRows;
+  // [h | m] of the tile's nodes (zero past the last node)
+  for (int e = tid; e < kTcRows * (GH / 8); e += 128) {
     const int r = e / (GH / 8), ch = e % (GH / 8);
     const int64_t i = base + r;
     float mv[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     uint4 own = make_uint4(0, 0, 0, 0);
     if (i < n) {
-      own = *reinterpret_cast<const uint4*>(h + i * GH + ch * 8);
+      own = *reinterpret_cast<const uint4*>(hin + i * GH + ch * 8);
       for (int k = 0; k < nlf; ++k) {
         const int32_t j = col[i * nlf + k];
         if (j < 0) continue;
         const float wk = w[i * nlf + k];
-        const uint4 hv = *reinterpret_cast<const uint4*>(h + (int64_t)j * GH + ch * 8);
+        const uint4 hv = *reinterpret_cast<const uint4*>(hin + (int64_t)j * GH + ch * 8);
         const bf16* hb = reinterpret_cast<const bf16*>(&hv);
 #pragma unroll
         for (int q = 0; q < 8; ++q) mv[q] = fmaf(wk, __bfloat162float(hb[q]), mv[q]);
       }
     }
-    *reinterpret_cast<uint4*>(&sX[r][ch * 8]) = own;
+    *reinterpret_cast<uint4*>(sA + tc_off(r, ch * 8, kTcLboA)) = own;
+    __align__(16) bf16 mb[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) sX[r][GH + ch * 8 + q] = __float2bfloat16_rn(mv[q]);
+    for (int q = 0; q < 8; ++q) mb[q] = __float2bfloat16_rn(mv[q]);
+    *reinterpret_cast<uint4*>(sA + tc_off(r, GH + ch * 8, kTcLboA)) =
+        *reinterpret_cast<const uint4*>(mb);
   }
+  for (int e = tid; e < GH * (2 * GH / 8); e += 128) {
+    const int r = e / (2 * GH / 8), ch = e % (2 * GH / 8);
+    *reinterpret_cast<uint4*>(sW + tc_off(r, ch * 8, kTcLboB)) =
+        *reinterpret_cast<const uint4*>(Wb + r * 2 * GH + ch * 8);
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(
+        smem_addr(&tslot)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  // the generic-proxy stores above become visible to the tensor cores
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tslot;
+  if (tid == 0) {
+    // kind::f16: D FP32, A and B BF16, both K-major, N = 64, M = 128
+    const uint32_t idesc =
+        (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(GH / 8) << 17) | ((uint32_t)(kTcRows / 16) << 24);
+#pragma unroll
+    for (int ks = 0; ks < 2 * GH / 16; ++ks) {
+      const uint64_t ad = tc_desc(smem_addr(sA) + ks * 2 * kTcLboA, kTcLboA, 128);
+      const uint64_t bd = tc_desc(smem_addr(sW) + ks * 2 * kTcLboB, kTcLboB, 128);
+      asm volatile(
+          "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+          "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+          "l"(ad), "l"(bd), "r"(idesc), "r"(ks > 0 ? 1u : 0u));
+    }
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_addr(&mbar)));
+  }
+  uint32_t done = 0;
+  for (long long it = 0; it < kTcSpin && !done; ++it) {
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n"
+        "selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_addr(&mbar)));
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const int r = tid;  // warp w reads rows 32 w .. 32 w + 31 (its lane quadrant)
+  const int64_t row = base + r;
+  float acc[GH];
+  if (done) {
+    uint32_t v[GH];
+    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+        "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32,%33,%34,%35,%36,%37,"
+        "%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,"
+        "%61,%62,%63}, [%64];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+          "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
+          "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
+          "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31]),
+          "=r"(v[32]), "=r"(v[33]), "=r"(v[34]), "=r"(v[35]), "=r"(v[36]), "=r"(v[37]),
+          "=r"(v[38]), "=r"(v[39]), "=r"(v[40]), "=r"(v[41]), "=r"(v[42]), "=r"(v[43]),
+          "=r"(v[44]), "=r"(v[45]), "=r"(v[46]), "=r"(v[47]), "=r"(v[48]), "=r"(v[49]),
+          "=r"(v[50]), "=r"(v[51]), "=r"(v[52]), "=r"(v[53]), "=r"(v[54]), "=r"(v[55]),
+          "=r"(v[56]), "=r"(v[57]), "=r"(v[58]), "=r"(v[59]), "=r"(v[60]), "=r"(v[61]),
+          "=r"(v[62]), "=r"(v[63])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < GH; ++j) acc[j] = __uint_as_float(v[j]);
+  } else {  // the product did not complete: NaN, which the solver rejects
+#pragma unroll
+    for (int j = 0; j < GH; ++j) acc[j] = __int_as_float(0x7fc00000);
+  }
+  if (row < npad) {
+#pragma unroll
+    for (int c8 = 0; c8 < GH / 8; ++c8) {
+      const uint4 hv = *reinterpret_cast<const uint4*>(sA + tc_off(r, c8 * 8, kTcLboA));
+      const bf16* hb = reinterpret_cast<const bf16*>(&hv);
+      __align__(16) bf16 ab[8], ob[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const float pre = acc[c8 * 8 + q] + b[c8 * 8 + q];
+        ab[q] = __float2bfloat16_rn(pre);
+        ob[q] = __float2bfloat16_rn(__bfloat162float(hb[q]) + relu(pre));
+      }
+      *reinterpret_cast<uint4*>(aout + row * GH + c8 * 8) = *reinterpret_cast<const uint4*>(ab);
+      *reinterpret_cast<uint4*>(hout + row * GH + c8 * 8) = *reinterpret_cast<const uint4*>(ob);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem));
 }
 
 // ---------------------------------------------------------------------
-// one message-passing layer: h_out = h_in + relu(W [h_in; m] + b)
+// backward of one layer on the tensor cores, 128 nodes a tile, persistent
+// over tiles:
+//   [dself | dm] (128 nodes x 128) = dpre (128 x 64) W (64 x 128)   (GEMM 1)
+//   dW^T (128 x 64) += X^T (128 x 128 nodes) dpre (128 nodes x 64)   (GEMM 2)
+// with dpre = dh_out where the pre-activation is positive.  Operands in the
+// same canonical K-major layout as the forward: A of GEMM 1 = dpre (rows
+// nodes, K = outputs), B = W^T (rows inputs, K = outputs); A of GEMM 2 = X^T
+// (rows inputs, K = nodes), B = dpre^T (rows outputs, K = nodes).  Tensor
+// memory: columns 0-127 GEMM 1 (per tile), 128-191 GEMM 2 (accumulated over
+// the block's tiles, read once at the end as the block's dW partial).
 // ---------------------------------------------------------------------
-__global__ void __launch_bounds__(GTHREADS)
-    k_gnn_layer(int nlf, int64_t n, const bf16* __restrict__ hin, const int32_t* __restrict__ col,
-                const float* __restrict__ w, const bf16* __restrict__ Wb,
-                const float* __restrict__ b, bf16* aout, bf16* hout) {
-  __shared__ __align__(16) bf16 sX[GT][2 * GH + 8];
-  __shared__ __align__(16) bf16 sW[GH][2 * GH + 8];
-  const int64_t base = (int64_t)blockIdx.x * GT;
-  load_hm_tile(nlf, n, base, hin, col, w, sX);
-  for (int e = threadIdx.x; e < GH * 2 * GH / 8; e += GTHREADS) {
-    const int r = e / (2 * GH / 8), ch = e % (2 * GH / 8);
-    *reinterpret_cast<uint4*>(&sW[r][ch * 8]) = *reinterpret_cast<const uint4*>(Wb + r * 2 * GH + ch * 8);
+constexpr int kTcBwdSmem = 2 * GH * kTcRows * 2     // X^T
+                           + kTcRows * GH * 2       // dpre
+                           + GH * kTcRows * 2       // dpre^T
+                           + 2 * GH * GH * 2;       // W^T
+
+__device__ __forceinline__ void tc_ld64(uint32_t taddr, float* out) {
+  uint32_t v[64];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32,%33,%34,%35,%36,%37,"
+      "%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,"
+      "%61,%62,%63}, [%64];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+        "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
+        "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
+        "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31]),
+        "=r"(v[32]), "=r"(v[33]), "=r"(v[34]), "=r"(v[35]), "=r"(v[36]), "=r"(v[37]),
+        "=r"(v[38]), "=r"(v[39]), "=r"(v[40]), "=r"(v[41]), "=r"(v[42]), "=r"(v[43]),
+        "=r"(v[44]), "=r"(v[45]), "=r"(v[46]), "=r"(v[47]), "=r"(v[48]), "=r"(v[49]),
+        "=r"(v[50]), "=r"(v[51]), "=r"(v[52]), "=r"(v[53]), "=r"(v[54]), "=r"(v[55]),
+        "=r"(v[56]), "=r"(v[57]), "=r"(v[58]), "=r"(v[59]), "=r"(v[60]), "=r"(v[61]),
+        "=r"(v[62]), "=r"(v[63])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 64; ++j) out[j] = __uint_as_float(v[j]);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc,
+                                       uint32_t accumulate) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(accumulate));
+}
+
+// bounded wait for the commit of phase `parity`; 1 when it completed
+__device__ __forceinline__ uint32_t tc_wait(const uint64_t* mbar, uint32_t parity) {
+  uint32_t done = 0;
+  for (long long it = 0; it < kTcSpin && !done; ++it) {
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_addr(mbar)), "r"(parity));
   }
+  return done;
+}
+
+__global__ void __launch_bounds__(128)
+    k_gnn_layer_bwd_tc(int nlf, int64_t n, int64_t ntc, const bf16* __restrict__ hin,
+                       const bf16* __restrict__ a, const int32_t* __restrict__ col,
+                       const float* __restrict__ w, const bf16* __restrict__ Wb,
+                       const float* __restrict__ dh_out, float* dnext, float* dm, float* part,
+                       int part_stride) {
+  extern __shared__ __align__(1024) uint8_t bsm[];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tslot;
+  uint8_t* sXT = bsm;
+  uint8_t* sD = sXT + 2 * GH * kTcRows * 2;
+  uint8_t* sDT = sD + kTcRows * GH * 2;
+  uint8_t* sWT = sDT + GH * kTcRows * 2;
+  constexpr int kLbo128 = kTcRows * 16, kLbo64 = GH * 16;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  // W^T: row i (input feature), K = output o
+  for (int e = tid; e < GH * 2 * GH; e += 128) {
+    const int o = e / (2 * GH), i = e % (2 * GH);
+    *reinterpret_cast<bf16*>(sWT + tc_off(i, o, kLbo128)) = Wb[e];
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(
+        smem_addr(&tslot)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-  const int g = lane >> 2, t = lane & 3;
-  float acc[GH / 8][4];
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tslot;
+  const uint32_t id1 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(2 * GH / 8) << 17) |
+                       ((uint32_t)(kTcRows / 16) << 24);  // M 128, N 128
+  const uint32_t id2 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(GH / 8) << 17) |
+                       ((uint32_t)(kTcRows / 16) << 24);  // M 128, N 64
+  float gb = 0.f;  // db of output feature tid (< 64)
+  uint32_t ok = 1, iter = 0;
+  for (int64_t tile = blockIdx.x; tile < ntc && ok; tile += gridDim.x, ++iter) {
+    const int64_t base = tile * kTcRows;
+    // X^T: [h | m] of the tile's nodes, transposed (rows = input features)
+    for (int e = tid; e < kTcRows * (GH / 8); e += 128) {
+      const int r = e / (GH / 8), ch = e % (GH / 8);
+      const int64_t i = base + r;
+      float mv[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      uint4 own = make_uint4(0, 0, 0, 0);
+      if (i < n) {
+        own = *reinterpret_cast<const uint4*>(hin + i * GH + ch * 8);
+        for (int k = 0; k < nlf; ++k) {
+          const int32_t j = col[i * nlf + k];
+          if (j < 0) continue;
+          const float wk = w[i * nlf + k];
+          const uint4 hv = *reinterpret_cast<const uint4*>(hin + (int64_t)j * GH + ch * 8);
+          const bf16* hb = reinterpret_cast<const bf16*>(&hv);
 #pragma unroll
-  for (int nt = 0; nt < GH / 8; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
+          for (int q = 0; q < 8; ++q) mv[q] = fmaf(wk, __bfloat162float(hb[q]), mv[q]);
+        }
+      }
+      const bf16* ob = reinterpret_cast<const bf16*>(&own);
 #pragma unroll
-  for (int kk = 0; kk < 2 * GH / 16; ++kk) {
-    uint32_t af[4];
-    frag_a(af, &sX[0][0], 2 * GH + 8, wp * 16, kk * 16, lane);
-#pragma unroll
-    for (int nt = 0; nt < GH / 8; ++nt) {
-      uint32_t bfr[2];
-      frag_b(bfr, &sW[0][0], 2 * GH + 8, nt * 8, kk * 16, lane);
-      mma16816(acc[nt], af, bfr);
-    }
-  }
-#pragma unroll
-  for (int nt = 0; nt < GH / 8; ++nt)
-#pragma unroll
-    for (int hh = 0; hh < 2; ++hh) {
-      const int r = wp * 16 + g + 8 * hh;
-      const int64_t row = base + r;
-#pragma unroll
-      for (int cc = 0; cc < 2; ++cc) {
-        const int colm = nt * 8 + 2 * t + cc;
-        const float pre = acc[nt][2 * hh + cc] + b[colm];
-        aout[row * GH + colm] = __float2bfloat16_rn(pre);
-        hout[row * GH + colm] = __float2bfloat16_rn(__bfloat162float(sX[r][colm]) + relu(pre));
+      for (int q = 0; q < 8; ++q) {
+        *reinterpret_cast<bf16*>(sXT + tc_off(ch * 8 + q, r, kLbo128)) = ob[q];
+        *reinterpret_cast<bf16*>(sXT + tc_off(GH + ch * 8 + q, r, kLbo128)) =
+            __float2bfloat16_rn(mv[q]);
       }
     }
+    // dpre and its transpose
+    for (int e = tid; e < kTcRows * GH; e += 128) {
+      const int r = e / GH, f = e % GH;
+      const int64_t i = base + r;
+      float d = 0.f;
+      if (i < n && __bfloat162float(a[i * GH + f]) > 0.f) d = dh_out[i * GH + f];
+      const bf16 db = __float2bfloat16_rn(d);
+      *reinterpret_cast<bf16*>(sD + tc_off(r, f, kLbo128)) = db;
+      *reinterpret_cast<bf16*>(sDT + tc_off(f, r, kLbo64)) = db;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (tid == 0) {
+#pragma unroll
+      for (int ks = 0; ks < GH / 16; ++ks)
+        tc_mma(tmem, tc_desc(smem_addr(sD) + ks * 2 * kLbo128, kLbo128, 128),
+               tc_desc(smem_addr(sWT) + ks * 2 * kLbo128, kLbo128, 128), id1, ks > 0 ? 1u : 0u);
+#pragma unroll
+      for (int ks = 0; ks < kTcRows / 16; ++ks)
+        tc_mma(tmem + 2 * GH, tc_desc(smem_addr(sXT) + ks * 2 * kLbo128, kLbo128, 128),
+               tc_desc(smem_addr(sDT) + ks * 2 * kLbo64, kLbo64, 128), id2,
+               (ks > 0 || iter > 0) ? 1u : 0u);
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              smem_addr(&mbar)));
+    }
+    if (tid < GH)
+      for (int r = 0; r < kTcRows; ++r)
+        gb += __bfloat162float(*reinterpret_cast<const bf16*>(sDT + tc_off(tid, r, kLbo64)));
+    ok = tc_wait(&mbar, iter & 1);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int64_t i = base + tid;  // warp w holds rows 32 w .. 32 w + 31
+    float acc[64];
+    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+    if (ok) tc_ld64(lane_base, acc);
+    if (i < n) {
+      for (int c = 0; c < GH; ++c)
+        dnext[i * GH + c] = ok ? dh_out[i * GH + c] + acc[c] : __int_as_float(0x7fc00000);
+    }
+    if (ok) tc_ld64(lane_base + GH, acc);
+    if (i < n) {
+      for (int c = 0; c < GH; ++c) dm[i * GH + c] = ok ? acc[c] : __int_as_float(0x7fc00000);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();  // operands and tensor-memory columns 0-127 are reused by the next tile
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  }
+  // the block's dW partial: thread tid = input feature i reads dW^T[i][0..63]
+  float* pp = part + (int64_t)blockIdx.x * part_stride;
+  {
+    float acc[64];
+    if (iter > 0 && ok) {
+      tc_ld64(tmem + ((uint32_t)(warp * 32) << 16) + 2 * GH, acc);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 64; ++j) acc[j] = iter > 0 ? __int_as_float(0x7fc00000) : 0.f;
+    }
+    for (int o = 0; o < GH; ++o) pp[o * 2 * GH + tid] = acc[o];
+  }
+  if (tid < GH) pp[GH * 2 * GH + tid] = ok ? gb : __int_as_float(0x7fc00000);
+  if (!ok) tc_wait(&mbar, (iter - 1) & 1);  // a late commit: wait again (bounded) before freeing
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem));
 }
 
 // ---------------------------------------------------------------------
@@ -354,111 +640,6 @@ __global__ void k_gnn_decode_wgrad(int64_t n, int64_t chunk, const bf16* __restr
   part[(int64_t)blockIdx.x * part_stride + e] = s;
 }
 
-// ---------------------------------------------------------------------
-// layer backward, part A (persistent over tiles):
-//   dpre = dh_out * (a > 0)
-//   [dself | dm] = dpre W          -> dnext = dh_out + dself,  dm
-//   dW += dpre^T [h_in | m],  db += sum dpre   (block partials)
-// ---------------------------------------------------------------------
-__global__ void __launch_bounds__(GTHREADS)
-    k_gnn_layer_bwd(int nlf, int64_t n, int64_t ntiles, const bf16* __restrict__ hin,
-                    const bf16* __restrict__ a, const int32_t* __restrict__ col,
-                    const float* __restrict__ w, const bf16* __restrict__ Wb,
-                    const float* __restrict__ dh_out, float* dnext, float* dm, float* part,
-                    int part_stride) {
-  // dynamic shared memory (kLayerBwdSmem bytes):
-  //   sX  [GT][2GH+8]   [h | m], rows = nodes
-  //   sXT [2GH][GT+8]   transposed, rows = features
-  //   sD  [GT][GH+8]    dpre, rows = nodes
-  //   sDT [GH][GT+8]    dpre^T, rows = output features
-  //   sWT [2GH][GH+8]   W^T, rows = input features
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  bf16 (*sX)[2 * GH + 8] = reinterpret_cast<bf16 (*)[2 * GH + 8]>(smem_raw);
-  bf16 (*sXT)[GT + 8] = reinterpret_cast<bf16 (*)[GT + 8]>(&sX[GT][0]);
-  bf16 (*sD)[GH + 8] = reinterpret_cast<bf16 (*)[GH + 8]>(&sXT[2 * GH][0]);
-  bf16 (*sDT)[GT + 8] = reinterpret_cast<bf16 (*)[GT + 8]>(&sD[GT][0]);
-  bf16 (*sWT)[GH + 8] = reinterpret_cast<bf16 (*)[GH + 8]>(&sDT[GH][0]);
-  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-  const int g = lane >> 2, t = lane & 3;
-  for (int e = threadIdx.x; e < GH * 2 * GH; e += GTHREADS) {
-    const int o = e / (2 * GH), i = e % (2 * GH);
-    sWT[i][o] = Wb[e];
-  }
-  float gw[2 * GH / 8][4];  // this warp's 16 output rows x 128 inputs of dW
-#pragma unroll
-  for (int nt = 0; nt < 2 * GH / 8; ++nt) gw[nt][0] = gw[nt][1] = gw[nt][2] = gw[nt][3] = 0.f;
-  float gb = 0.f;           // db for output feature threadIdx.x (< 64)
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int64_t base = tile * GT;
-    __syncthreads();
-    load_hm_tile(nlf, n, base, hin, col, w, sX);
-    for (int e = threadIdx.x; e < GT * GH; e += GTHREADS) {
-      const int r = e / GH, f = e % GH;
-      const int64_t i = base + r;
-      float d = 0.f;
-      if (i < n && __bfloat162float(a[i * GH + f]) > 0.f) d = dh_out[i * GH + f];
-      const bf16 db = __float2bfloat16_rn(d);
-      sD[r][f] = db;
-      sDT[f][r] = db;
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < GT * 2 * GH; e += GTHREADS) {
-      const int r = e / (2 * GH), f = e % (2 * GH);
-      sXT[f][r] = sX[r][f];
-    }
-    if (threadIdx.x < GH)
-      for (int r = 0; r < GT; ++r) gb += __bfloat162float(sDT[threadIdx.x][r]);
-    __syncthreads();
-    // [dself | dm] (16 nodes x 128 per warp) = dpre (16 x 64) x W (64 x 128)
-#pragma unroll
-    for (int nt = 0; nt < 2 * GH / 8; ++nt) {
-      float acc[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-      for (int kk = 0; kk < GH / 16; ++kk) {
-        uint32_t af[4], bfr[2];
-        frag_a(af, &sD[0][0], GH + 8, wp * 16, kk * 16, lane);
-        frag_b(bfr, &sWT[0][0], GH + 8, nt * 8, kk * 16, lane);
-        mma16816(acc, af, bfr);
-      }
-#pragma unroll
-      for (int hh = 0; hh < 2; ++hh) {
-        const int64_t i = base + wp * 16 + g + 8 * hh;
-        if (i >= n) continue;
-#pragma unroll
-        for (int cc = 0; cc < 2; ++cc) {
-          const int colm = nt * 8 + 2 * t + cc;
-          if (colm < GH)
-            dnext[i * GH + colm] = dh_out[i * GH + colm] + acc[2 * hh + cc];
-          else
-            dm[i * GH + colm - GH] = acc[2 * hh + cc];
-        }
-      }
-    }
-    // dW (16 out rows x 128 per warp) += dpre^T (16 x 64 nodes) x X (64 nodes x 128)
-#pragma unroll
-    for (int kk = 0; kk < GT / 16; ++kk) {
-      uint32_t af[4];
-      frag_a(af, &sDT[0][0], GT + 8, wp * 16, kk * 16, lane);
-#pragma unroll
-      for (int nt = 0; nt < 2 * GH / 8; ++nt) {
-        uint32_t bfr[2];
-        frag_b(bfr, &sXT[0][0], GT + 8, nt * 8, kk * 16, lane);
-        mma16816(gw[nt], af, bfr);
-      }
-    }
-  }
-  float* pp = part + (int64_t)blockIdx.x * part_stride;
-#pragma unroll
-  for (int nt = 0; nt < 2 * GH / 8; ++nt)
-#pragma unroll
-    for (int hh = 0; hh < 2; ++hh)
-#pragma unroll
-      for (int cc = 0; cc < 2; ++cc) {
-        const int o = wp * 16 + g + 8 * hh, i = nt * 8 + 2 * t + cc;
-        pp[o * 2 * GH + i] = gw[nt][2 * hh + cc];
-      }
-  if (threadIdx.x < GH) pp[GH * 2 * GH + threadIdx.x] = gb;
-}
 
 // layer backward, part B: dh_in = dnext + sum_k w_ik dm_{col_ik}
 __global__ void k_gnn_gather_dm(int nlf, int64_t n, const int32_t* __restrict__ col,
@@ -616,8 +797,10 @@ int ensure(hofv_ctx* c, Gnn** out) {
   g->off_bd = o; o += c->dim;
   g->P = o;
   g->gblocks = 2 * c->sm_count;
-  HOFV_CUDA(c, cudaFuncSetAttribute(k_gnn_layer_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    kLayerBwdSmem));
+  HOFV_CUDA(c, cudaFuncSetAttribute(k_gnn_layer_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    kTcSmem));
+  HOFV_CUDA(c, cudaFuncSetAttribute(k_gnn_layer_bwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    kTcBwdSmem));
   int rc = 0;
   rc |= galloc(c, g, &g->w, g->n * g->nlf);
   rc |= galloc(c, g, &g->bnd, g->n * 2);
@@ -670,10 +853,12 @@ int forward(hofv_ctx* c, Gnn* g, const double* v, const double* z, double* zout)
   else
     k_gnn_encode<3><<<nt, GTHREADS, 0, st>>>(g->n, v, z, g->bnd, g->scal, g->W0b,
                                              g->theta + g->off_b0, g->x, abuf(g, 0), hbuf(g, 0));
+  const unsigned ntc = (unsigned)((g->n + kTcRows - 1) / kTcRows);
   for (int l = 0; l < GL; ++l)
-    k_gnn_layer<<<nt, GTHREADS, 0, st>>>(g->nlf, g->n, hbuf(g, l), c->d_aj_col, g->w,
-                                         g->Wb + (int64_t)l * GH * 2 * GH, g->theta + g->off_b[l],
-                                         abuf(g, l + 1), hbuf(g, l + 1));
+    k_gnn_layer_tc<<<ntc, 128, kTcSmem, st>>>(g->nlf, g->n, g->npad, hbuf(g, l), c->d_aj_col, g->w,
+                                              g->Wb + (int64_t)l * GH * 2 * GH,
+                                              g->theta + g->off_b[l], abuf(g, l + 1),
+                                              hbuf(g, l + 1));
   if (zout) {
     const unsigned nb = (unsigned)((g->n + 255) / 256);
     if (g->dim == 2)
@@ -716,12 +901,14 @@ int backward(hofv_ctx* c, Gnn* g, const double* z, const double* delta) {
   float* dcur = g->dh0;
   float* dnext = g->dh1;
   const int lb = (int)std::min<int64_t>(g->ntiles, gb);
+  const int64_t ntc = (g->n + kTcRows - 1) / kTcRows;
+  const int lbt = (int)std::min<int64_t>(ntc, gb);
   for (int l = GL - 1; l >= 0; --l) {
-    k_gnn_layer_bwd<<<lb, GTHREADS, kLayerBwdSmem, st>>>(g->nlf, g->n, g->ntiles, hbuf(g, l), abuf(g, l + 1),
-                                             c->d_aj_col, g->w, g->Wb + (int64_t)l * GH * 2 * GH,
-                                             dcur, dnext, g->dm, g->part, kPartStride);
+    k_gnn_layer_bwd_tc<<<lbt, 128, kTcBwdSmem, st>>>(
+        g->nlf, g->n, ntc, hbuf(g, l), abuf(g, l + 1), c->d_aj_col, g->w,
+        g->Wb + (int64_t)l * GH * 2 * GH, dcur, dnext, g->dm, g->part, kPartStride);
     k_gnn_reduce<<<(GH * 2 * GH + GH + 255) / 256, 256, 0, st>>>(
-        lb, kPartStride, GH * 2 * GH + GH, g->part, g->grad, g->off_W[l], g->off_b[l], GH * 2 * GH,
+        lbt, kPartStride, GH * 2 * GH + GH, g->part, g->grad, g->off_W[l], g->off_b[l], GH * 2 * GH,
         nullptr, 0);
     k_gnn_gather_dm<<<(unsigned)((g->n * GH + 255) / 256), 256, 0, st>>>(g->nlf, g->n, c->d_aj_col,
                                                                          g->w, g->dm, dnext);

@@ -44,8 +44,6 @@ struct DevMesh {
   const int32_t* cface;   // [nc][nlf]  +(f+1) owner, -(f+1) neighbour, 0 traction
   const double* tco;      // [nftile][S][kTile][dim][dim] contracted linear-elastic
                           // face matrices, or nullptr (then the per-point form is used)
-  const double* tco_df;   // the same as float pairs (double-float arithmetic), or nullptr
-  const double* tsum;     // [nftile * kTile][dim][dim] FP64 sums over N of the pairs
   // symmetry faces [nfi + nfd, nfid): their stencils end in mirror images of
   // cells ("ghosts", ids nc + g); the state is then read from an extended
   // copy [dim][wst] holding the reflected values R u_src after the cells
@@ -153,9 +151,6 @@ struct hofv_ctx {
   bool contract = false;            // requested by the caller
   bool tco_valid = false;           // d_tco holds the matrices for the current mu, lambda
   double* d_tco = nullptr;
-  double* d_tco_df = nullptr;       // d_tco as float pairs, for the double-float contraction
-  double* d_tsum = nullptr;         // [nftile * kTile][dim][dim] sums over N of those pairs
-  int64_t tco_gen = 0, tdf_gen = -1;  // builds of d_tco; the build d_tco_df was made from
   double* d_gflux = nullptr;        // [nfd][dim] ghost-node flux (constant per load step)
   bool src_dirty = true;
   // ---- gradient contraction precision (HOFV_PREC_*) ----
@@ -302,7 +297,6 @@ void launch_coef_format(double* a, int64_t n, int to_df, cudaStream_t st);
 // fcsum[f][r] = sum over the stencil slots of the stored coefficient of face
 // f, row r (double-float pairs summed in FP64, in slot order)
 void launch_row_sums(const DevMesh& m, double* fcsum, cudaStream_t st);
-void launch_tco_sums(const DevMesh& m, double* tsum, cudaStream_t st);
 // raises the dynamic shared-memory limit of the double-float face kernels
 // (once per process, at set-up); 0 or a cudaError_t
 int setup_df_kernels();

@@ -992,14 +992,17 @@ __device__ __forceinline__ void cp_async_wait_all() {
 // thread streams its coefficient row through a ring of RING registers: the
 // coefficient of slot n + RING is requested when slot n is consumed, keeping
 // RING coalesced 8-byte loads in flight per thread; with R a compile-time
-// constant every ring offset is an immediate.  In 3-D a block takes part of
-// a tile so that several blocks share an SM and the FP32 contraction of one
-// overlaps the FP64 law and the barriers of the others: a quarter tile of 216
-// threads, four blocks an SM, for 3 x 3 points (measured on the 128^3
+// constant every ring offset is an immediate.  Faces come in groups of part
+// of a tile, one thread per (face, row): in 3-D a quarter tile of 216
+// threads for 3 x 3 points, four blocks an SM (measured on the 128^3
 // neo-Hookean block: 7 % faster than half tiles two an SM, 10 % slower with
-// eighth tiles), half tiles otherwise; faces with many points (polyhedral
-// fans, R = 48 or 96) take quarter or eighth tiles of 384 threads, two an
-// SM.  Rows of points without area (polyhedral fan slots past a face's last
+// eighth tiles), half tiles otherwise, and for faces with many points
+// (polyhedral fans, R = 48 or 96) quarter or eighth tiles of 384 threads.
+// A block contracts d groups one after the other (the gradients stay in
+// shared memory) and then evaluates the law at all their Gauss points at
+// once, one point a thread: R = Q d rows a face, so d groups have exactly as
+// many points as the block has threads and the FP64 law runs on full warps.
+// Rows of points without area (polyhedral fan slots past a face's last
 // corner) load nothing.
 template <int DIM, int QD>
 struct DfShape {
@@ -1007,20 +1010,24 @@ struct DfShape {
                              : QD == 9  ? 8
                              : QD == 16 ? 8
                              : QD == 32 ? 4
-                                        : 16;  // faces per block
+                                        : 16;  // faces per group
   static constexpr int RING = DIM == 3 ? 8 : 4;  // coefficient loads in flight per thread
   static constexpr int THREADS = FPB * QD * DIM;
+  // face groups per block: GPB FPB Q = THREADS, so that each thread evaluates
+  // one law (a face's Gauss point) after the block's GPB contractions
+  static constexpr int GPB = DIM;
   static constexpr int MIN_BLOCKS = DIM == 2 ? 6 : (THREADS <= 256 ? 4 : 2);  // per SM
 };
 
-// dynamic shared memory: the gathered cell values and the faces' references,
-// reused after the contraction for the gradients and tractions of phases 2-3
+// dynamic shared memory: the gathered cell values and the faces' references
+// (one group at a time), then the gradients and tractions of all groups
 template <int DIM, int QD>
 static size_t df_smem_bytes(int S) {
-  constexpr int FPB = DfShape<DIM, QD>::FPB, R = QD * DIM;
-  const size_t gath = (size_t)S * FPB * DIM * 16;
-  const size_t law = (size_t)FPB * (R * DIM + QD * DIM) * sizeof(double);
-  return gath > law ? gath : law;
+  using SH = DfShape<DIM, QD>;
+  constexpr int R = QD * DIM;
+  const size_t gath = (size_t)S * SH::FPB * DIM * 16;
+  const size_t law = (size_t)SH::GPB * SH::FPB * (R * DIM + QD * DIM) * sizeof(double);
+  return gath + law;
 }
 
 template <int DIM, int LAW, int MODE, int QD>
@@ -1029,154 +1036,165 @@ __global__ void __launch_bounds__(DfShape<DIM, QD>::THREADS, DfShape<DIM, QD>::M
               const double* __restrict__ ws, const double* __restrict__ ubq,
               const double* __restrict__ ubf, const double* __restrict__ d_eps,
               double* __restrict__ flux) {
-  constexpr int FPB = DfShape<DIM, QD>::FPB, BPT = kTile / FPB, Q = QD, R = QD * DIM;
-  constexpr int kRing = DfShape<DIM, QD>::RING;
+  using SH = DfShape<DIM, QD>;
+  constexpr int FPB = SH::FPB, BPT = kTile / FPB, GPB = SH::GPB, Q = QD, R = QD * DIM;
+  constexpr int kRing = SH::RING;
   constexpr int CS = kTile * R;  // coefficient stride between stencil slots
   extern __shared__ __align__(16) double sm[];
   const int S = m.S;
-  // [S][FPB][DIM] gathered values; slots 1.. then hold the differences to
-  // slot 0, the faces' reference cells (whose own difference is zero)
+  // [S][FPB][DIM] gathered values of one group; slots 1.. then hold the
+  // differences to slot 0, the faces' reference cells (zero difference)
   float4* us = reinterpret_cast<float4*>(sm);
-  double* Gs = sm;                              // [FPB][R][DIM] after the contraction
-  double* Ts = sm + FPB * R * DIM;              // [FPB][Q][DIM]
-  const int64_t tile = blockIdx.x / BPT;
-  const int fb = (blockIdx.x % BPT) * FPB;  // first face of the block within its tile
-  const int64_t f0 = tile * kTile + fb;
+  double* Gs = reinterpret_cast<double*>(us + (size_t)S * FPB * DIM);  // [GPB][FPB][R][DIM]
+  double* Ts = Gs + GPB * FPB * R * DIM;                               // [GPB][FPB][Q][DIM]
+  const int64_t ngroups = m.nftile * BPT;
+  const int64_t g0 = (int64_t)blockIdx.x * GPB;
+  const int ng = (int)(ngroups - g0 < GPB ? ngroups - g0 : GPB);  // the same for every thread
   const int it = threadIdx.x;
   const double eps = MODE == kDfJv ? __ldg(d_eps) : 0.0;
   const int fi = it / R, r = it % R;
-  const int64_t f = f0 + fi;
-  const int32_t* __restrict__ st = m.fst + tile * (int64_t)S * kTile + fb;
-  const float2* __restrict__ co =
-      reinterpret_cast<const float2*>(m.fco) + tile * (int64_t)S * CS + fb * R + it;
-  // rows of points without area (polyhedral fan slots past a face's last
-  // corner) read no coefficient and keep a zero gradient
-  const bool live = m.fql == nullptr || r < __ldg(m.fql + f) * DIM;
-  // stencil slots this thread contracts: 1 .. S-1 (slot 0, the reference,
-  // enters only through the row sums)
-  const int SL = live ? S - 1 : 0;
-  co += CS;  // coefficients of slot 1
-  // the first coefficients of the ring, then the gather of the cell values
   float2 cq[kRing];
+  for (int gi = 0; gi < ng; ++gi) {
+    const int64_t grp = g0 + gi;
+    const int64_t tile = grp / BPT;
+    const int fb = (int)(grp % BPT) * FPB;  // first face of the group within its tile
+    const int64_t f0 = tile * kTile + fb;
+    const int64_t f = f0 + fi;
+    const int32_t* __restrict__ st = m.fst + tile * (int64_t)S * kTile + fb;
+    const float2* __restrict__ co =
+        reinterpret_cast<const float2*>(m.fco) + tile * (int64_t)S * CS + fb * R + it;
+    // rows of points without area (polyhedral fan slots past a face's last
+    // corner) read no coefficient and keep a zero gradient
+    const bool live = m.fql == nullptr || r < __ldg(m.fql + f) * DIM;
+    // stencil slots this thread contracts: 1 .. S-1 (slot 0, the reference,
+    // enters only through the row sums)
+    const int SL = live ? S - 1 : 0;
+    co += CS;  // coefficients of slot 1
+    // the first coefficients of the ring, then the gather of the cell values
 #pragma unroll
-  for (int d = 0; d < kRing; ++d) cq[d] = d < SL ? __ldg(co + d * CS) : make_float2(0.f, 0.f);
-  for (int t = it; t < S * FPB; t += FPB * R) {
-    const int n = t / FPB, fj = t % FPB;
-    const int32_t id = __ldg(st + n * kTile + fj);
+    for (int d = 0; d < kRing; ++d) cq[d] = d < SL ? __ldg(co + d * CS) : make_float2(0.f, 0.f);
+    for (int t = it; t < S * FPB; t += SH::THREADS) {
+      const int n = t / FPB, fj = t % FPB;
+      const int32_t id = __ldg(st + n * kTile + fj);
 #pragma unroll
-    for (int h = 0; h < DIM; ++h) cp_async16(us + t * DIM + h, sw + (int64_t)id * DIM + h);
-  }
-  cp_async_wait_all();
-  __syncthreads();
-  for (int t = FPB * DIM + it; t < S * FPB * DIM; t += FPB * R) {
-    const float2 dv = diff3(us[t], us[t % (FPB * DIM)]);
-    us[t] = make_float4(dv.x, dv.y, 0.f, 0.f);
-  }
-  __syncthreads();
-  // (1) gradient rows: thread (fi, r) accumulates sum_N c_{r,N} (w_N - w_N0)
-  float s[DIM], e[DIM];
-#pragma unroll
-  for (int j = 0; j < DIM; ++j) s[j] = e[j] = 0.f;
-  const float4* __restrict__ uf = us + FPB * DIM + fi * DIM;  // slot 1 of the thread's face
-  auto mac_slot = [&](int n, float2 c) {
-#pragma unroll
-    for (int j = 0; j < DIM; ++j) {
-      const float4 a = uf[n * FPB * DIM + j];
-      ff_mac(c.x, c.y, a.x, a.y, s[j], e[j]);
+      for (int h = 0; h < DIM; ++h) cp_async16(us + t * DIM + h, sw + (int64_t)id * DIM + h);
     }
-  };
-  int n0 = 0;
-  // steady part: every request in range
-  for (; n0 + 2 * kRing <= SL; n0 += kRing) {
-    const float2* cn = co + (n0 + kRing) * CS;
-#pragma unroll
-    for (int d = 0; d < kRing; ++d) {
-      const float2 c = cq[d];
-      cq[d] = __ldg(cn + d * CS);
-      mac_slot(n0 + d, c);
+    cp_async_wait_all();
+    __syncthreads();
+    for (int t = FPB * DIM + it; t < S * FPB * DIM; t += SH::THREADS) {
+      const float2 dv = diff3(us[t], us[t % (FPB * DIM)]);
+      us[t] = make_float4(dv.x, dv.y, 0.f, 0.f);
     }
-  }
-  // the last kRing .. 2 kRing - 1 slots (fewer if S < kRing)
+    __syncthreads();
+    // (1) gradient rows: thread (fi, r) accumulates sum_N c_{r,N} (w_N - w_N0)
+    float s[DIM], e[DIM];
 #pragma unroll
-  for (int d = 0; d < 2 * kRing; ++d) {
-    const int n = n0 + d;
-    if (n < SL) {
-      const float2 c = cq[d % kRing];
-      if (n + kRing < SL) cq[d % kRing] = __ldg(co + (n + kRing) * CS);
-      mac_slot(n, c);
-    }
-  }
-  __syncthreads();  // the gathered values are overwritten by the gradients below
-  {
-    // + w_N0 sum_N c_N, in FP64
-    const int32_t id0 = __ldg(st + fi);
-    const int64_t ldw = m.wst;
-    const double cs = live ? m.fcsum[f * R + r] : 0.0;
-    double g[DIM];
+    for (int j = 0; j < DIM; ++j) s[j] = e[j] = 0.f;
+    const float4* __restrict__ uf = us + FPB * DIM + fi * DIM;  // slot 1 of the thread's face
+    auto mac_slot = [&](int n, float2 c) {
 #pragma unroll
-    for (int j = 0; j < DIM; ++j) g[j] = fma(cs, __ldg(wd + j * ldw + id0), ff_value(s[j], e[j]));
-    if (MODE == kDfResidual || MODE == kDfFill) {
-      if (live && f >= m.nfi && f < m.nfid) {  // ghost node of a displacement face (prescribed data)
-        const int64_t fd = f - m.nfi;
-        const double cg = m.gco[fd * R + r];
-        const int q = r / DIM;
+      for (int j = 0; j < DIM; ++j) {
+        const float4 a = uf[n * FPB * DIM + j];
+        ff_mac(c.x, c.y, a.x, a.y, s[j], e[j]);
+      }
+    };
+    int n0 = 0;
+    // steady part: every request in range
+    for (; n0 + 2 * kRing <= SL; n0 += kRing) {
+      const float2* cn = co + (n0 + kRing) * CS;
 #pragma unroll
-        for (int j = 0; j < DIM; ++j) g[j] = fma(cg, ubq[(fd * Q + q) * DIM + j], g[j]);
+      for (int d = 0; d < kRing; ++d) {
+        const float2 c = cq[d];
+        cq[d] = __ldg(cn + d * CS);
+        mac_slot(n0 + d, c);
       }
     }
-    const int64_t row = (f0 * R + it) * DIM;  // == (f * R + r) * DIM
-    if (MODE == kDfFill) {
+    // the last kRing .. 2 kRing - 1 slots (fewer if S < kRing)
 #pragma unroll
-      for (int j = 0; j < DIM; ++j) m.gcache[row + j] = g[j];
+    for (int d = 0; d < 2 * kRing; ++d) {
+      const int n = n0 + d;
+      if (n < SL) {
+        const float2 c = cq[d % kRing];
+        if (n + kRing < SL) cq[d % kRing] = __ldg(co + (n + kRing) * CS);
+        mac_slot(n, c);
+      }
     }
-    if (MODE == kDfJv) {  // grad (u + eps v) = grad u + eps grad v
+    {
+      // + w_N0 sum_N c_N, in FP64
+      const int32_t id0 = __ldg(st + fi);
+      const int64_t ldw = m.wst;
+      const double cs = live ? m.fcsum[f * R + r] : 0.0;
+      double g[DIM];
 #pragma unroll
-      for (int j = 0; j < DIM; ++j) g[j] = fma(eps, g[j], m.gcache[row + j]);
+      for (int j = 0; j < DIM; ++j) g[j] = fma(cs, __ldg(wd + j * ldw + id0), ff_value(s[j], e[j]));
+      if (MODE == kDfResidual || MODE == kDfFill) {
+        if (live && f >= m.nfi && f < m.nfid) {  // ghost node of a displacement face (prescribed data)
+          const int64_t fd = f - m.nfi;
+          const double cg = m.gco[fd * R + r];
+          const int q = r / DIM;
+#pragma unroll
+          for (int j = 0; j < DIM; ++j) g[j] = fma(cg, ubq[(fd * Q + q) * DIM + j], g[j]);
+        }
+      }
+      const int64_t row = (f0 * R + it) * DIM;  // == (f * R + r) * DIM
+      if (MODE == kDfFill) {
+#pragma unroll
+        for (int j = 0; j < DIM; ++j) m.gcache[row + j] = g[j];
+      }
+      if (MODE == kDfJv) {  // grad (u + eps v) = grad u + eps grad v
+#pragma unroll
+        for (int j = 0; j < DIM; ++j) g[j] = fma(eps, g[j], m.gcache[row + j]);
+      }
+#pragma unroll
+      for (int j = 0; j < DIM; ++j) Gs[(gi * FPB * R + it) * DIM + j] = g[j];
     }
-#pragma unroll
-    for (int j = 0; j < DIM; ++j) Gs[it * DIM + j] = g[j];
+    __syncthreads();  // the next group's gather overwrites the differences
   }
-  __syncthreads();
-  // (2) law and traction at each Gauss point
-  if (it < FPB * Q) {
-    const int fj = it / Q, q = it % Q;
-    const int64_t fq = f0 + fj;
-    double t[DIM];
-    if (fq < m.nfid) {
-      double a[3];
+  // (2) law and traction at each Gauss point of the block's groups, one a thread
+  {
+    const int gi = it / (FPB * Q), rem = it % (FPB * Q), fj = rem / Q, q = rem % Q;
+    if (gi < ng) {
+      const int64_t grp = g0 + gi;
+      const int64_t fq = (grp / BPT) * kTile + (grp % BPT) * FPB + fj;
+      double t[DIM];
+      if (fq < m.nfid) {
+        double a[3];
 #pragma unroll
-      for (int k = 0; k < DIM; ++k) a[k] = m.aq[(fq * Q + q) * 3 + k];
-      double G[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+        for (int k = 0; k < DIM; ++k) a[k] = m.aq[(fq * Q + q) * 3 + k];
+        double G[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+        const double* gq = Gs + ((gi * FPB + fj) * R + q * DIM) * DIM;
 #pragma unroll
-      for (int i = 0; i < DIM; ++i)
+        for (int i = 0; i < DIM; ++i)
 #pragma unroll
-        for (int j = 0; j < DIM; ++j) G[i][j] = Gs[(fj * R + q * DIM + i) * DIM + j];
-      traction<DIM, LAW>(G, a, mt, t);
-    } else {
+          for (int j = 0; j < DIM; ++j) G[i][j] = gq[i * DIM + j];
+        traction<DIM, LAW>(G, a, mt, t);
+      } else {
 #pragma unroll
-      for (int i = 0; i < DIM; ++i) t[i] = 0.0;
+        for (int i = 0; i < DIM; ++i) t[i] = 0.0;
+      }
+      const int64_t o = (fq * Q + q) * DIM;
+      if (MODE == kDfFill) {
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) m.tcache[o + i] = t[i];
+      }
+      if (MODE == kDfJv) {
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) t[i] -= m.tcache[o + i];
+      }
+#pragma unroll
+      for (int i = 0; i < DIM; ++i) Ts[((gi * FPB + fj) * Q + q) * DIM + i] = t[i];
     }
-    const int64_t o = (fq * Q + q) * DIM;
-    if (MODE == kDfFill) {
-#pragma unroll
-      for (int i = 0; i < DIM; ++i) m.tcache[o + i] = t[i];
-    }
-    if (MODE == kDfJv) {
-#pragma unroll
-      for (int i = 0; i < DIM; ++i) t[i] -= m.tcache[o + i];
-    }
-#pragma unroll
-    for (int i = 0; i < DIM; ++i) Ts[(fj * Q + q) * DIM + i] = t[i];
   }
   if (MODE == kDfFill) return;
   __syncthreads();
   // (3) quadrature over the face + alpha stabilisation
-  if (it < FPB * DIM) {
-    const int fj = it / DIM, i = it % DIM;
-    const int64_t ff = f0 + fj;
+  for (int t3 = it; t3 < ng * FPB * DIM; t3 += SH::THREADS) {
+    const int gi = t3 / (FPB * DIM), fj = (t3 / DIM) % FPB, i = t3 % DIM;
+    const int64_t grp = g0 + gi;
+    const int64_t ff = (grp / BPT) * kTile + (grp % BPT) * FPB + fj;
     if (ff < m.nfid) {
       double acc = 0.0;
-      for (int q = 0; q < Q; ++q) acc += Ts[(fj * Q + q) * DIM + i];
+      for (int q = 0; q < Q; ++q) acc += Ts[((gi * FPB + fj) * Q + q) * DIM + i];
       const int32_t sp = m.fstar[2 * ff], sn = m.fstar[2 * ff + 1];
       const bool sym = sn < 0 && ff >= m.nfi + m.nfd;
       const double up = ws[(int64_t)sp * DIM + i];
@@ -1228,154 +1246,6 @@ __global__ void __launch_bounds__(32 * DIM)
   }
 }
 
-// Contracted linear form in double-float arithmetic: flux_{f,i} =
-// sum_N sum_k T_{N,ik} (w_N - w_N0)_k + sum_k (sum_N T_{N,ik}) w_N0,k + the
-// stabilisation, with the matrices stored as float pairs (tco_df) and their
-// FP64 sums over the stencil (tsum), N0 the face's first stencil cell (the
-// same exact identity as the per-point kernel).  One block takes one tile of
-// 32 faces.  The block first turns the three-float splits of its faces'
-// stencil cells into double-float differences to the faces' references in
-// shared memory ([S][32][DIM] pairs); then thread (g, face, row i) contracts
-// the stencil slots g, g + G, ... of its row (G = kTdfSplit groups, so that
-// each SM holds enough threads to keep the coefficient stream in flight),
-// and the groups' compensated sums are added in shared memory.  HOM: the
-// homogeneous part of the Jacobian-vector product (no prescribed values).
-constexpr int kTdfSplit = 4;
-
-template <int DIM>
-struct TdfShape {
-  static constexpr int THREADS = kTile * DIM * kTdfSplit;
-  static constexpr int MIN_BLOCKS = DIM == 3 ? 3 : 6;  // per SM
-  static constexpr int RING = 4;  // stencil slots of coefficients in flight per thread
-};
-
-template <int DIM>
-static size_t tdf_smem_bytes(int S) {
-  const size_t diffs = (size_t)S * kTile * DIM * sizeof(float2);
-  const size_t red = (size_t)kTdfSplit * kTile * DIM * sizeof(float2);
-  return diffs > red ? diffs : red;
-}
-
-template <int DIM, bool HOM>
-__global__ void __launch_bounds__(TdfShape<DIM>::THREADS, TdfShape<DIM>::MIN_BLOCKS)
-    k_tflux_df(DevMesh m, double alpha_kbar, const float4* __restrict__ sw,
-               const double* __restrict__ wd, const double* __restrict__ ws,
-               const double* __restrict__ ubf, double* __restrict__ flux) {
-  constexpr int RD = kTile * DIM;        // rows of a tile
-  constexpr int CS = RD * DIM;           // pairs of one stencil slot of a tile
-  constexpr int kRing = TdfShape<DIM>::RING;
-  extern __shared__ __align__(16) double sm[];
-  float2* dv = reinterpret_cast<float2*>(sm);  // [S][32][DIM] differences, then [G][RD] sums
-  const int S = m.S;
-  const int64_t tile = blockIdx.x;
-  const int it = threadIdx.x;
-  const int32_t* __restrict__ st = m.fst + tile * (int64_t)S * kTile;
-  // (1) differences of the split state to each face's reference cell
-  for (int t = it; t < S * RD; t += TdfShape<DIM>::THREADS) {
-    const int n = t / RD, rem = t % RD, fj = rem / DIM, k = rem % DIM;
-    const int32_t id = __ldg(st + n * kTile + fj), id0 = __ldg(st + fj);
-    dv[t] = diff3(__ldg(sw + (int64_t)id * DIM + k), __ldg(sw + (int64_t)id0 * DIM + k));
-  }
-  __syncthreads();
-  // (2) thread (g, row ri = fi * DIM + i): slots g, g + G, ...
-  const int ri = it % RD, g = it / RD, fi = ri / DIM, i = ri % DIM;
-  const float2* __restrict__ tc =
-      reinterpret_cast<const float2*>(m.tco_df) + tile * (int64_t)S * CS + ri * DIM;
-  const float2* __restrict__ df = dv + fi * DIM;
-  float s = 0.f, e = 0.f;
-  float2 cq[kRing][DIM];
-#pragma unroll
-  for (int d = 0; d < kRing; ++d) {
-    const int n = g + d * kTdfSplit;
-#pragma unroll
-    for (int k = 0; k < DIM; ++k)
-      cq[d][k] = n < S ? __ldg(tc + (int64_t)n * CS + k) : make_float2(0.f, 0.f);
-  }
-  for (int n0 = g; n0 < S; n0 += kRing * kTdfSplit) {
-#pragma unroll
-    for (int d = 0; d < kRing; ++d) {
-      const int n = n0 + d * kTdfSplit;
-      if (n < S) {
-        float2 c[DIM];
-#pragma unroll
-        for (int k = 0; k < DIM; ++k) c[k] = cq[d][k];
-        const int nn = n + kRing * kTdfSplit;
-        if (nn < S) {
-#pragma unroll
-          for (int k = 0; k < DIM; ++k) cq[d][k] = __ldg(tc + (int64_t)nn * CS + k);
-        }
-#pragma unroll
-        for (int k = 0; k < DIM; ++k) {
-          const float2 a = df[n * RD + k];
-          ff_mac(c[k].x, c[k].y, a.x, a.y, s, e);
-        }
-      }
-    }
-  }
-  __syncthreads();  // the differences are overwritten by the groups' sums
-  dv[g * RD + ri] = make_float2(s, e);
-  __syncthreads();
-  if (g != 0) return;
-  for (int h = 1; h < kTdfSplit; ++h) {
-    const float2 o = dv[h * RD + ri];
-    float t, r;
-    two_sum(s, o.x, t, r);
-    s = t;
-    e = __fadd_rn(e, __fadd_rn(o.y, r));
-  }
-  const int64_t f = tile * kTile + fi;
-  if (f >= m.nfid) return;
-  // + (sum_N T_N) w_N0 in FP64, then the stabilisation
-  const int32_t id0 = __ldg(st + fi);
-  const int64_t ldw = m.wst;
-  double acc = ff_value(s, e);
-#pragma unroll
-  for (int k = 0; k < DIM; ++k)
-    acc = fma(m.tsum[(f * DIM + i) * DIM + k], __ldg(wd + k * ldw + id0), acc);
-  const int32_t sp = m.fstar[2 * f], sn = m.fstar[2 * f + 1];
-  const bool sym = sn < 0 && f >= m.nfi + m.nfd;
-  const double up = ws[(int64_t)sp * DIM + i];
-  const double other = sn >= 0 ? ws[(int64_t)sn * DIM + i]
-                       : sym   ? mirror_i<DIM>(ws + (int64_t)sp * DIM, m.nrm + 3 * f, i)
-                       : HOM   ? 0.0
-                               : ubf[(f - m.nfi) * DIM + i];
-  flux[f * DIM + i] = fma(alpha_kbar * m.fstab[f], other - up, acc);
-}
-
-// tsum[f][i][k] = sum_N of the stored pair T_{N,ik} of face f
-template <int DIM>
-__global__ void k_tco_sums(DevMesh m, double* __restrict__ tsum) {
-  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;  // (face, i, k)
-  if (e >= m.nftile * kTile * DIM * DIM) return;
-  const int64_t tile = e / (kTile * DIM * DIM);
-  const int r = (int)(e % (kTile * DIM * DIM));  // (fi * DIM + i) * DIM + k within the tile
-  const float2* co =
-      reinterpret_cast<const float2*>(m.tco_df) + tile * (int64_t)m.S * kTile * DIM * DIM + r;
-  double sum = 0.0;
-  for (int n = 0; n < m.S; ++n) {
-    const float2 p = co[(int64_t)n * kTile * DIM * DIM];
-    sum += ff_value(p.x, p.y);
-  }
-  tsum[e] = sum;
-}
-
-void launch_tco_sums(const DevMesh& m, double* tsum, cudaStream_t st) {
-  const int64_t n = m.nftile * kTile * m.dim * m.dim;
-  if (n == 0) return;
-  if (m.dim == 2)
-    k_tco_sums<2><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(m, tsum);
-  else
-    k_tco_sums<3><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(m, tsum);
-}
-
-template <int DIM, bool HOM>
-static void launch_tflux_df(const DevMesh& m, double alpha_kbar, const float4* sw,
-                            const double* wd, const double* ws, const double* ubf, double* flux,
-                            cudaStream_t st) {
-  k_tflux_df<DIM, HOM><<<(unsigned)m.nftile, TdfShape<DIM>::THREADS, tdf_smem_bytes<DIM>(m.S),
-                         st>>>(m, alpha_kbar, sw, wd, ws, ubf, flux);
-}
-
 // Jv assembly from face-flux differences: out = sum_f +-dflux_f / eps, plus
 // the inertia term of v (linear, so its difference quotient is exact)
 template <int DIM, int NLF>
@@ -1419,7 +1289,8 @@ static void launch_flux_df_q(const DevMesh& m, const Material& mat, const float4
                              cudaStream_t st) {
   using SH = DfShape<DIM, QD>;
   const size_t smem = df_smem_bytes<DIM, QD>(m.S);
-  k_flux_df<DIM, LAW, MODE, QD><<<(unsigned)(m.nftile * (kTile / SH::FPB)), SH::THREADS, smem,
+  const int64_t groups = m.nftile * (kTile / SH::FPB);
+  k_flux_df<DIM, LAW, MODE, QD><<<(unsigned)((groups + SH::GPB - 1) / SH::GPB), SH::THREADS, smem,
                                   st>>>(m, mat, sw, wd, ws, ubq, ubf, d_eps, flux);
 }
 
@@ -1472,9 +1343,7 @@ static void residual_impl_df(const DevMesh& m, const Material& mat, const double
   launch_ustar_df<DIM>(m, m.su, w, ustar, st);
   if (ev) cudaEventRecord(ev[1], st);
   if (m.nftile > 0) {
-    if (LAW == HOFV_LAW_LINEAR && m.tco && m.tco_df) {
-      launch_tflux_df<DIM, false>(m, mat.alpha * mat.kbar, m.su, w, ustar, ubf, flux, st);
-    } else if (LAW == HOFV_LAW_LINEAR && m.tco) {
+    if (LAW == HOFV_LAW_LINEAR && m.tco) {
       if (m.nfy > 0) k_sym_other<DIM><<<(unsigned)((m.nfy + 127) / 128), 128, 0, st>>>(m, ustar);
       k_tflux<DIM><<<(unsigned)m.nftile, 32 * DIM, 0, st>>>(m, m.tco, mat.alpha * mat.kbar, w,
                                                             ustar, ubf, flux);
@@ -1499,9 +1368,7 @@ static void jv_impl_df(const DevMesh& m, const Material& mat, const double* v,
   v = split_state<DIM>(m, v, m.vext, m.sv, st);
   launch_ustar_df<DIM>(m, m.sv, v, m.ustar_v, st);
   if (m.nftile > 0) {
-    if (LAW == HOFV_LAW_LINEAR && m.tco && m.tco_df)
-      launch_tflux_df<DIM, true>(m, mat.alpha * mat.kbar, m.sv, v, m.ustar_v, nullptr, flux, st);
-    else if (LAW == HOFV_LAW_LINEAR && m.tco)
+    if (LAW == HOFV_LAW_LINEAR && m.tco)
       k_tflux_hom<DIM><<<(unsigned)m.nftile, 32 * DIM, 0, st>>>(m, m.tco, mat.alpha * mat.kbar, v,
                                                                 m.ustar_v, flux);
     else if (LAW == HOFV_LAW_LINEAR)
@@ -1575,21 +1442,10 @@ static void raise_smem_all(cudaError_t& e) {
   raise_smem<DIM, 1, kDfFill, QD>(e);
   raise_smem<DIM, 1, kDfJv, QD>(e);
 }
-template <int DIM, bool HOM>
-static void raise_smem_tdf(cudaError_t& e) {
-  const cudaError_t r = cudaFuncSetAttribute((const void*)k_tflux_df<DIM, HOM>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)tdf_smem_bytes<DIM>(kMaxS));
-  if (r != cudaSuccess) e = r;
-}
 int setup_df_kernels() {
   static int rc = -1;
   if (rc >= 0) return rc;
   cudaError_t e = cudaSuccess;
-  raise_smem_tdf<2, false>(e);
-  raise_smem_tdf<2, true>(e);
-  raise_smem_tdf<3, false>(e);
-  raise_smem_tdf<3, true>(e);
   raise_smem_all<2, 1>(e);
   raise_smem_all<2, 2>(e);
   raise_smem_all<2, 3>(e);
