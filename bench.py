@@ -576,6 +576,36 @@ def run_residuals(args):
     ctx.close()
 
 
+def run_gnn_timing(args):
+    """Profiling aid: CUDA-event time of one learned-preconditioner forward
+    pass (encoder, four tensor-core message-passing layers, decoder) and of
+    one forward + backward (loss and gradient) on one workload."""
+    import torch
+
+    from paper_2601_18417_gb300 import build as B
+    B.build()
+    wl, mesh, ctx, lay, setup_s, u_ex, field = build_workload(args.workload)
+    ctx.gnn_init(seed=args.seed, out_scale=0.5)
+    rng = np.random.default_rng(3)
+    shape = (wl.dim, lay.n_cells)
+    v, z = (torch.as_tensor(rng.standard_normal(shape), device="cuda:0") for _ in range(2))
+    zo = torch.empty_like(z)
+    s = torch.cuda.current_stream()
+    for _ in range(3):
+        ctx.gnn_forward(v, z, zo)
+    fwd = event_ms(lambda: ctx.gnn_forward(v, z, zo), 20, s)
+    ctx.gnn_loss_grad(v, z, z)
+    t0 = time.perf_counter()
+    for _ in range(5):
+        ctx.gnn_loss_grad(v, z, z)
+    torch.cuda.synchronize()
+    lg = (time.perf_counter() - t0) / 5 * 1e3
+    print(json.dumps({"mode": "gnn_timing", "workload": wl.name, "cells": lay.n_cells,
+                      "forward_ms": fwd, "loss_and_gradient_ms_host": lg,
+                      "forward_mcells": lay.n_cells / (fwd * 1e-3) / 1e6}))
+    ctx.close()
+
+
 def run_hofv(args):
     import torch
 
@@ -971,6 +1001,8 @@ def main():
                     help="neo-Hookean block whose load steps are solved to 1e-8 ('' = none)")
     ap.add_argument("--cpu-sample", type=int, default=0,
                     help="cells of the oracle's timed sample (0: 96 in 3-D, 2048 in 2-D)")
+    ap.add_argument("--gnn-timing", action="store_true",
+                    help="profiling aid: learned-preconditioner forward / backward times on --workload")
     ap.add_argument("--residuals", type=int, default=0,
                     help="profiling aid: only this many residual evaluations of --workload")
     ap.add_argument("--no-solve", action="store_true")
@@ -1009,6 +1041,8 @@ def main():
         run_pc_sweep(args)
     elif args.dynamics:
         run_dynamics(args)
+    elif args.gnn_timing:
+        run_gnn_timing(args)
     elif args.residuals > 0:
         run_residuals(args)
     else:
