@@ -87,10 +87,12 @@ def kernel_hash():
     return hashlib.sha256("".join(parts).encode()).hexdigest()[:16]
 
 
-def measured_traffic(workload):
-    """DRAM bytes per launch of the double-float face kernel from the
-    committed ncu summary, or None when the kernel's source changed since the
-    capture (or the workload was not captured)."""
+def measured_traffic(workload, mode="residual"):
+    """DRAM bytes per launch of the double-float face kernel (residual or
+    Jv mode) from the committed ncu summary, or None when the kernel's source
+    changed since the capture (or the workload was not captured)."""
+    if mode == "jv":
+        workload = workload + ":jv"
     path = os.path.join(ROOT, "profiles", "ncu_k_flux_df_traffic.txt")
     if not os.path.exists(path):
         return None
@@ -203,6 +205,23 @@ def algorithmic_counts(wl, lay, mesh=None):
     res_bytes = bytes_ + lay.n_cells * (8 * nlf * S + 4 * S + 8 * d + 8 * nlf * d * 2
                                         + 8 * d * 2 + 4 * nlf)
     return flops, bytes_, res_bytes
+
+
+def jv_bytes(wl, lay, mesh=None, precision="df64"):
+    """Per launch of the face kernel in a Jacobian-vector product: in
+    double-float mode the per-point terms of the residual without the ghost
+    data (a product has no prescribed values), plus, for the neo-Hookean law,
+    the cached gradient rows (Q d^2) and tractions (Q d) of the linearisation;
+    in FP64 mode the residual's own bytes."""
+    if precision != "df64":
+        return algorithmic_counts(wl, lay, mesh)[1]
+    d, S = wl.dim, lay.stencil
+    nfid = lay.n_internal + lay.n_disp
+    pf, _ = face_points(wl, lay, mesh)
+    b = 8 * d * S * pf + 8 * 3 * pf + nfid * (4 * S + 8 + 8 + 8 * d + 2 * 8 * d) + 8 * d * lay.n_cells
+    if wl.law == 1:
+        b += pf * (8 * d * d + 8 * d)
+    return b
 
 
 def contracted_bytes(wl, lay):
@@ -401,25 +420,37 @@ def step_section(args, wl, mesh, ctx, lay, u_ex, precision, rank, ws, peaks_dev,
     flux_ms = float(kt[:, 1].mean())
     res_ms = float(kt.sum(axis=1).mean())
     flops, fbytes, rbytes = algorithmic_counts(wl, lay, mesh)
+    # the face kernel as the timed step runs it: in the Jacobian-vector product
+    Jtmp = torch.empty_like(u)
+    kj = np.array([ctx.jvp_timed(u, Ru, V[J], Jtmp) for _ in range(max(args.steps, 10))])
+    jflux_ms = float(kj[:, 1].mean())
+    jb = jv_bytes(wl, lay, mesh, precision)
     pk, src = peaks()
     hbm = pk["hbm_gbs"]
-    achieved = fbytes / (flux_ms * 1e-3) / 1e9
     macs = flops / 2.0
+    name = ("k_flux_df (double-float face gradients + law + quadrature)" if precision == "df64"
+            else "k_flux (FP64 face gradients + law + quadrature)")
     roofline = {
-        "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-        "frac": achieved / hbm, "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)",
-        "kernel": ("k_flux_df (double-float face gradients + law + quadrature)"
-                   if precision == "df64" else "k_flux (FP64 face gradients + law + quadrature)"),
-        "traffic": measured_traffic(wl.name) if precision == "df64" else None,
-        "alg_bytes_per_launch": fbytes, "flux_ms": flux_ms, "residual_ms": res_ms,
-        "residual_mcells": nc / (res_ms * 1e-3) / 1e6,
-        "residual_hbm_frac": rbytes / (res_ms * 1e-3) / 1e9 / hbm,
-        "gradient_macs_per_launch": macs,
-        "fp64_equivalent_tflops": flops / (flux_ms * 1e-3) / 1e12,
+        "bound": "hbm", "achieved": jb / (jflux_ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+        "frac": jb / (jflux_ms * 1e-3) / 1e9 / hbm,
+        "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)",
+        "kernel": name + ", in the Jacobian-vector product of the timed step",
+        "traffic": measured_traffic(wl.name, "jv") if precision == "df64" else None,
+        "alg_bytes_per_launch": jb, "flux_ms": jflux_ms,
+        "jv_ms": float(kj.sum(axis=1).mean()),
+        "fp64_equivalent_tflops": flops / (jflux_ms * 1e-3) / 1e12,
         "fp64_peak_tflops_measured": peaks_dev["fp64_tflops"],
-        "fp32_peak_tflops_measured": peaks_dev["fp32_tflops"]}
+        "fp32_peak_tflops_measured": peaks_dev["fp32_tflops"],
+        "gradient_macs_per_launch": macs,
+        "residual_mode": {
+            "flux_ms": flux_ms, "alg_bytes_per_launch": fbytes,
+            "achieved": fbytes / (flux_ms * 1e-3) / 1e9,
+            "frac": fbytes / (flux_ms * 1e-3) / 1e9 / hbm,
+            "traffic": measured_traffic(wl.name) if precision == "df64" else None,
+            "residual_ms": res_ms, "residual_mcells": nc / (res_ms * 1e-3) / 1e6,
+            "residual_hbm_frac": rbytes / (res_ms * 1e-3) / 1e9 / hbm}}
     if precision == "df64":  # 12 FP32 instructions per double-float product
-        roofline["fp32_tflops_of_contraction"] = 12.0 * macs / (flux_ms * 1e-3) / 1e12
+        roofline["fp32_tflops_of_contraction"] = 12.0 * macs / (jflux_ms * 1e-3) / 1e12
         roofline["fp32_frac_of_measured"] = roofline["fp32_tflops_of_contraction"] / \
             peaks_dev["fp32_tflops"]
     else:
@@ -455,8 +486,7 @@ def step_section(args, wl, mesh, ctx, lay, u_ex, precision, rank, ws, peaks_dev,
         tflux_ms = float(kc[:, 1].mean())
         tb = contracted_bytes(wl, lay)
         contracted = {
-            "kernel": ("k_tflux_df (double-float contracted face matrices)" if precision == "df64"
-                       else "k_tflux (FP64 contracted face matrices)"),
+            "kernel": "k_tflux (FP64 contracted face matrices, in both precisions)",
             "flux_ms": tflux_ms, "alg_bytes_per_launch": tb,
             "achieved_gbs": tb / (tflux_ms * 1e-3) / 1e9,
             "frac": tb / (tflux_ms * 1e-3) / 1e9 / hbm,
@@ -570,9 +600,16 @@ def run_residuals(args):
     u = torch.as_tensor(u_ex + 1e-3 * np.abs(u_ex).max() * rng.standard_normal(u_ex.shape),
                         device="cuda:0")
     R = torch.empty_like(u)
-    ms = event_ms(lambda: ctx.residual(u, R), args.residuals, torch.cuda.current_stream())
-    print(json.dumps({"mode": "residuals", "workload": wl.name, "precision": args.precision,
-                      "residuals": args.residuals, "ms_per_residual": ms}))
+    if args.jv:  # Jacobian-vector products at u instead (the timed step's face kernel)
+        ctx.residual(u, R)
+        v = torch.as_tensor(rng.standard_normal(u_ex.shape), device="cuda:0")
+        Jv = torch.empty_like(u)
+        ms = event_ms(lambda: ctx.jvp(u, R, v, Jv), args.residuals, torch.cuda.current_stream())
+    else:
+        ms = event_ms(lambda: ctx.residual(u, R), args.residuals, torch.cuda.current_stream())
+    print(json.dumps({"mode": "jvps" if args.jv else "residuals", "workload": wl.name,
+                      "precision": args.precision, "evaluations": args.residuals,
+                      "ms_each": ms}))
     ctx.close()
 
 
@@ -1003,6 +1040,8 @@ def main():
                     help="cells of the oracle's timed sample (0: 96 in 3-D, 2048 in 2-D)")
     ap.add_argument("--gnn-timing", action="store_true",
                     help="profiling aid: learned-preconditioner forward / backward times on --workload")
+    ap.add_argument("--jv", action="store_true",
+                    help="with --residuals: Jacobian-vector products instead of residuals")
     ap.add_argument("--residuals", type=int, default=0,
                     help="profiling aid: only this many residual evaluations of --workload")
     ap.add_argument("--no-solve", action="store_true")

@@ -575,6 +575,14 @@ int hofv_selftest_barrier(hofv_ctx* ctx, int32_t* timed_out);
    face fluxes, ms[2] cell assembly (HOST array of 3).  Synchronises. */
 int hofv_residual_timed(hofv_ctx* ctx, const double* u, double* R, float* ms);
 
+/* hofv_jvp (Sec. 4.1) with its kernels timed by CUDA events on the context
+   stream: ms[0] the direction's split and stabilisation extrapolation (or,
+   in FP64 mode, the residual's extrapolation after u + eps v is formed),
+   ms[1] the face fluxes, ms[2] the cell assembly (HOST array of 3).  The
+   same arguments, layouts and errors as hofv_jvp.  Synchronises. */
+int hofv_jvp_timed(hofv_ctx* ctx, const double* u, const double* Ru, const double* v, double* Jv,
+                   float* ms);
+
 /* ---- measurement ----------------------------------------------------------- */
 
 /* Arithmetic peaks of the context's device, measured: FP64 and FP32 fused

@@ -1084,19 +1084,20 @@ int hofv_residual(hofv_ctx* c, const double* u, double* R) {
 
 // Jv with ||u|| already in d_scal[0]: computes ||v||, eps, w = u + eps v and
 // (R(w) - Ru) / eps into Jv.  eps stays in d_scal[2].
-static int jvp_impl(hofv_ctx* c, const double* u, const double* Ru, const double* v, double* Jv) {
+static int jvp_impl(hofv_ctx* c, const double* u, const double* Ru, const double* v, double* Jv,
+                    cudaEvent_t* ev = nullptr) {
   const int64_t n = c->nc * c->dim;
   double* sc = c->d_scal;
   launch_norm2(v, n, c->d_red, c->d_count, sc + 1, c->red_blocks, c->stream);
   launch_jv_eps(sc + 0, sc + 1, sc + 2, c->stream);
   if (c->prec == HOFV_PREC_DF64) {  // the caller made the linearisation cache valid
-    launch_jv_df(dev_mesh(c), c->mat, v, sc + 2, Jv, c->d_flux, c->stream);
+    launch_jv_df(dev_mesh(c), c->mat, v, sc + 2, Jv, c->d_flux, c->stream, ev);
     HOFV_CUDA(c, cudaGetLastError());
     return 0;
   }
   launch_waxpy_dev(c->d_w, u, v, sc + 2, 1.0, n, c->stream);
   launch_residual(dev_mesh(c), c->mat, c->d_w, nullptr, sc + 2, Ru, Jv, c->d_ustar, c->d_flux,
-                  c->d_ubq, c->d_ubf, c->d_src, c->stream);
+                  c->d_ubq, c->d_ubf, c->d_src, c->stream, ev);
   HOFV_CUDA(c, cudaGetLastError());
   return 0;
 }
@@ -1114,6 +1115,25 @@ int hofv_jvp(hofv_ctx* c, const double* u, const double* Ru, const double* v, do
                                  c->stream));
     HOFV_CUDA(c, cudaStreamSynchronize(c->stream));
   }
+  return HOFV_OK;
+}
+
+int hofv_jvp_timed(hofv_ctx* c, const double* u, const double* Ru, const double* v, double* Jv,
+                   float* ms) {
+  TRY(check_eval(c));
+  if (!u || !Ru || !v || !Jv || !ms) return fail(c, HOFV_EINVAL, "null argument");
+  const int64_t n = c->nc * c->dim;
+  launch_norm2(u, n, c->d_red, c->d_count, c->d_scal + 0, c->red_blocks, c->stream);
+  TRY(ensure_jv_cache(c, u, Ru));
+  cudaEvent_t ev[4];
+  for (int i = 0; i < 4; ++i) HOFV_CUDA(c, cudaEventCreate(&ev[i]));
+  const int rc = jvp_impl(c, u, Ru, v, Jv, ev);
+  cudaError_t e = rc == 0 ? cudaEventSynchronize(ev[3]) : cudaSuccess;
+  for (int i = 0; i < 3 && rc == 0 && e == cudaSuccess; ++i)
+    e = cudaEventElapsedTime(&ms[i], ev[i], ev[i + 1]);
+  for (int i = 0; i < 4; ++i) cudaEventDestroy(ev[i]);
+  if (rc != 0) return rc;
+  HOFV_CUDA(c, e);
   return HOFV_OK;
 }
 

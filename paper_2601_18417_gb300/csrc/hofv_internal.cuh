@@ -283,7 +283,7 @@ void launch_residual(const DevMesh& m, const Material& mat, const double* u, con
 // the linearisation cache (launch_jv_cache_fill), so the rounding of the
 // double-float contraction of u cancels exactly
 void launch_jv_df(const DevMesh& m, const Material& mat, const double* v, const double* d_eps,
-                  double* out, double* flux, cudaStream_t st);
+                  double* out, double* flux, cudaStream_t st, cudaEvent_t* ev = nullptr);
 // the neo-Hookean linearisation at u for launch_jv_df: face gradient rows
 // (with the ghost-node data) and Gauss-point tractions into m.gcache,
 // m.tcache

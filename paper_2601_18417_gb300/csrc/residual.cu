@@ -1366,9 +1366,12 @@ static void residual_impl_df(const DevMesh& m, const Material& mat, const double
 
 template <int DIM, int LAW>
 static void jv_impl_df(const DevMesh& m, const Material& mat, const double* v,
-                       const double* d_eps, double* out, double* flux, cudaStream_t st) {
+                       const double* d_eps, double* out, double* flux, cudaStream_t st,
+                       cudaEvent_t* ev) {
+  if (ev) cudaEventRecord(ev[0], st);
   v = split_state<DIM>(m, v, m.vext, m.sv, st);
   launch_ustar_df<DIM>(m, m.sv, v, m.ustar_v, st);
+  if (ev) cudaEventRecord(ev[1], st);
   if (m.nftile > 0) {
     if (LAW == HOFV_LAW_LINEAR && m.tco)
       k_tflux_hom<DIM><<<(unsigned)m.nftile, 32 * DIM, 0, st>>>(m, m.tco, mat.alpha * mat.kbar, v,
@@ -1380,6 +1383,7 @@ static void jv_impl_df(const DevMesh& m, const Material& mat, const double* v,
       launch_flux_df<DIM, LAW, kDfJv>(m, mat, m.sv, v, m.ustar_v, nullptr, nullptr, d_eps, flux,
                                       st);
   }
+  if (ev) cudaEventRecord(ev[2], st);
   if (m.mscale)
     k_cell_avg<DIM, true><<<(unsigned)((m.nc + 127) / 128), 128, 0, st>>>(m, v, m.wst, m.inert);
   const unsigned cgrid = (unsigned)((m.nc + 255) / 256);
@@ -1390,6 +1394,7 @@ static void jv_impl_df(const DevMesh& m, const Material& mat, const double* v,
     else
       k_cell_diff<DIM, NLF><<<cgrid, 256, 0, st>>>(m, flux, d_eps, out);
   });
+  if (ev) cudaEventRecord(ev[3], st);
 }
 
 void launch_residual_df(const DevMesh& m, const Material& mat, const double* w,
@@ -1410,17 +1415,17 @@ void launch_residual_df(const DevMesh& m, const Material& mat, const double* w,
 }
 
 void launch_jv_df(const DevMesh& m, const Material& mat, const double* v, const double* d_eps,
-                  double* out, double* flux, cudaStream_t st) {
+                  double* out, double* flux, cudaStream_t st, cudaEvent_t* ev) {
   if (m.dim == 2) {
     if (mat.law == HOFV_LAW_LINEAR)
-      jv_impl_df<2, 0>(m, mat, v, d_eps, out, flux, st);
+      jv_impl_df<2, 0>(m, mat, v, d_eps, out, flux, st, ev);
     else
-      jv_impl_df<2, 1>(m, mat, v, d_eps, out, flux, st);
+      jv_impl_df<2, 1>(m, mat, v, d_eps, out, flux, st, ev);
   } else {
     if (mat.law == HOFV_LAW_LINEAR)
-      jv_impl_df<3, 0>(m, mat, v, d_eps, out, flux, st);
+      jv_impl_df<3, 0>(m, mat, v, d_eps, out, flux, st, ev);
     else
-      jv_impl_df<3, 1>(m, mat, v, d_eps, out, flux, st);
+      jv_impl_df<3, 1>(m, mat, v, d_eps, out, flux, st, ev);
   }
 }
 

@@ -105,6 +105,7 @@ SIGNATURES = {
     "hofv_get_aj": (_I, [_P, _P, _P]),
     "hofv_arnoldi_step": (_I, [_P, _P, _P, _I, _I, _P, _P, _I64, _I, _P]),
     "hofv_residual_timed": (_I, [_P, _P, _P, _P]),
+    "hofv_jvp_timed": (_I, [_P, _P, _P, _P, _P, _P]),
     "hofv_residual_noalloc": (_I, [_P, _P, _P]),
     "hofv_force_scale": (_I, [_P, _P, C.POINTER(_D)]),
     "hofv_set_contraction": (_I, [_P, _I]),
@@ -410,6 +411,14 @@ class Context:
         """Residual with per-kernel CUDA-event times (ms): u*, flux, cell."""
         ms = (C.c_float * 3)()
         self._check(self._L.hofv_residual_timed(self.h, _ptr(_dev(u)), _ptr(_dev(R)), ms))
+        return [float(x) for x in ms]
+
+    def jvp_timed(self, u, Ru, v, Jv):
+        """Jacobian-vector product with per-kernel CUDA-event times (ms):
+        extrapolation, flux, cell."""
+        ms = (C.c_float * 3)()
+        self._check(self._L.hofv_jvp_timed(self.h, _ptr(_dev(u)), _ptr(_dev(Ru)), _ptr(_dev(v)),
+                                           _ptr(_dev(Jv)), ms))
         return [float(x) for x in ms]
 
     # ---- learned preconditioner -------------------------------------------

@@ -113,6 +113,11 @@ def test_df64_jvp(name):
     assert abs(eps - want) <= 1e-12 * want
     rel = np.linalg.norm(Jv.cpu().numpy() - Jv_ref) / np.linalg.norm(Jv_ref)
     assert rel < bar, rel
+    # the timed variant the benchmark uses: the same product, three kernel times
+    Jt = torch.full_like(ud, float("nan"))
+    ms = ctx.jvp_timed(ud, garbage, vd, Jt)
+    assert np.array_equal(Jt.cpu().numpy(), Jv.cpu().numpy())
+    assert len(ms) == 3 and all(t > 0.0 for t in ms), ms
 
 
 @pytest.mark.parametrize("name", ["quad-p2", "quad-p3-jit"])
