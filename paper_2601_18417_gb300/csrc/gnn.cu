@@ -13,11 +13,11 @@
 //   sum_i |z_out_i - delta_i|^2 / sum_i |delta_i|^2
 // over (residual, Newton correction) pairs recorded by the solver.
 //
-// The message-passing layers' node-wise GEMMs (K = 128, forward and both
-// backward products) run on the 5th-generation tensor cores: tcgen05.mma
-// with BF16 operands in shared memory and FP32 accumulators in tensor
-// memory, 128 nodes a tile.  The 16-wide encoder keeps warp-level mma.sync
-// m16n8k16 tiles of 64 nodes.  The message passing is a gather over the
+// Every node-wise GEMM (the encoder and its weight gradient, the message-
+// passing layers forward and both backward products) runs on the 5th-
+// generation tensor cores: tcgen05.mma with BF16 operands in shared memory
+// and FP32 accumulators in tensor memory, 128 nodes a tile; the decoder
+// (64 -> d) is FP32 FMAs.  The message passing is a gather over the
 // symmetric graph, so its transpose in the backward pass is the same gather
 // (no atomics); weight gradients are accumulated per block and reduced in
 // block order (deterministic).
@@ -39,8 +39,6 @@ namespace {
 constexpr int GH = 64;          // hidden width
 constexpr int GF = 16;          // input features (padded)
 constexpr int GL = 4;           // message-passing layers
-constexpr int GT = 64;          // nodes per tile
-constexpr int GTHREADS = 128;   // 4 warps, 16 nodes each
 typedef __nv_bfloat16 bf16;
 
 struct Gnn {
@@ -84,29 +82,6 @@ int galloc(hofv_ctx* c, Gnn* g, T** p, int64_t count) {
   return 0;
 }
 
-__device__ __forceinline__ void mma16816(float* c, const uint32_t* a, const uint32_t* b) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-      "{%8,%9}, {%0,%1,%2,%3};\n"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
-// A: row-major [rows][lda] bf16 in smem; fragment of rows row0..row0+15, cols k0..k0+15
-__device__ __forceinline__ void frag_a(uint32_t* a, const bf16* A, int lda, int row0, int k0, int lane) {
-  const int g = lane >> 2, t = lane & 3;
-  a[0] = *reinterpret_cast<const uint32_t*>(A + (row0 + g) * lda + k0 + 2 * t);
-  a[1] = *reinterpret_cast<const uint32_t*>(A + (row0 + g + 8) * lda + k0 + 2 * t);
-  a[2] = *reinterpret_cast<const uint32_t*>(A + (row0 + g) * lda + k0 + 2 * t + 8);
-  a[3] = *reinterpret_cast<const uint32_t*>(A + (row0 + g + 8) * lda + k0 + 2 * t + 8);
-}
-// B given as BT: row-major [N][ldb] bf16 (row n holds column n of B over k)
-__device__ __forceinline__ void frag_b(uint32_t* b, const bf16* BT, int ldb, int n0, int k0, int lane) {
-  const int g = lane >> 2, t = lane & 3;
-  b[0] = *reinterpret_cast<const uint32_t*>(BT + (n0 + g) * ldb + k0 + 2 * t);
-  b[1] = *reinterpret_cast<const uint32_t*>(BT + (n0 + g) * ldb + k0 + 2 * t + 8);
-}
-
 __device__ __forceinline__ float relu(float x) { return x > 0.f ? x : 0.f; }
 
 // ---------------------------------------------------------------------
@@ -139,57 +114,6 @@ __global__ void k_gnn_scales(double* scal, double inv_sqrt_count) {
 
 __global__ void k_square(double* x) { x[0] = x[0] * x[0]; }
 
-// ---------------------------------------------------------------------
-// encoder: x (built from v, z) -> h0 = relu(W0 x + b0)
-// ---------------------------------------------------------------------
-template <int DIM>
-__global__ void __launch_bounds__(GTHREADS)
-    k_gnn_encode(int64_t n, const double* __restrict__ v, const double* __restrict__ z,
-                 const float* __restrict__ bnd, const double* __restrict__ scal,
-                 const bf16* __restrict__ W0b, const float* __restrict__ b0, bf16* xg, bf16* a0,
-                 bf16* h0) {
-  __shared__ __align__(16) bf16 sx[GT][GF + 8];
-  __shared__ __align__(16) bf16 sw[GH][GF + 8];
-  const int64_t base = (int64_t)blockIdx.x * GT;
-  const double isv = 1.0 / scal[2], isz = 1.0 / scal[3];
-  for (int e = threadIdx.x; e < GT * GF; e += GTHREADS) {
-    const int r = e / GF, f = e % GF;
-    const int64_t i = base + r;
-    float val = 0.f;
-    if (i < n) {
-      if (f < DIM) val = (float)(v[f * n + i] * isv);
-      else if (f < 2 * DIM) val = (float)(z[(f - DIM) * n + i] * isz);
-      else if (f < 2 * DIM + 2) val = bnd[2 * i + (f - 2 * DIM)];
-    }
-    const bf16 bv = __float2bfloat16_rn(val);
-    sx[r][f] = bv;
-    xg[(base + r) * GF + f] = bv;
-  }
-  for (int e = threadIdx.x; e < GH * GF; e += GTHREADS) sw[e / GF][e % GF] = W0b[e];
-  __syncthreads();
-  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-  uint32_t af[4];
-  frag_a(af, &sx[0][0], GF + 8, wp * 16, 0, lane);
-  const int g = lane >> 2, t = lane & 3;
-#pragma unroll
-  for (int nt = 0; nt < GH / 8; ++nt) {
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
-    uint32_t bfr[2];
-    frag_b(bfr, &sw[0][0], GF + 8, nt * 8, 0, lane);
-    mma16816(acc, af, bfr);
-#pragma unroll
-    for (int hh = 0; hh < 2; ++hh) {
-      const int64_t row = base + wp * 16 + g + 8 * hh;
-#pragma unroll
-      for (int cc = 0; cc < 2; ++cc) {
-        const int colm = nt * 8 + 2 * t + cc;
-        const float pre = acc[2 * hh + cc] + b0[colm];
-        a0[row * GH + colm] = __float2bfloat16_rn(pre);
-        h0[row * GH + colm] = __float2bfloat16_rn(relu(pre));
-      }
-    }
-  }
-}
 
 // ---------------------------------------------------------------------
 // the same layer on the 5th-generation tensor cores: 128 nodes a block, the
@@ -555,6 +479,189 @@ __global__ void __launch_bounds__(128)
 }
 
 // ---------------------------------------------------------------------
+// the encoder on the tensor cores: x (128 nodes x 16 features) times W0^T
+// (16 x 64) as one tcgen05.mma of K = 16 into 64 tensor-memory columns
+// ---------------------------------------------------------------------
+template <int DIM>
+__global__ void __launch_bounds__(128)
+    k_gnn_encode_tc(int64_t n, int64_t npad, const double* __restrict__ v,
+                    const double* __restrict__ z, const float* __restrict__ bnd,
+                    const double* __restrict__ scal, const bf16* __restrict__ W0b,
+                    const float* __restrict__ b0, bf16* xg, bf16* a0, bf16* h0) {
+  __shared__ __align__(1024) uint8_t sx[kTcRows * GF * 2];  // A: rows nodes, K features
+  __shared__ __align__(1024) uint8_t sw[GH * GF * 2];       // B: rows outputs, K features
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tslot;
+  constexpr int kLboX = kTcRows * 16, kLboW = GH * 16;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int64_t base = (int64_t)blockIdx.x * kTcRows;
+  const double isv = 1.0 / scal[2], isz = 1.0 / scal[3];
+  for (int e = tid; e < kTcRows * GF; e += 128) {
+    const int r = e / GF, f = e % GF;
+    const int64_t i = base + r;
+    float val = 0.f;
+    if (i < n) {
+      if (f < DIM) val = (float)(v[f * n + i] * isv);
+      else if (f < 2 * DIM) val = (float)(z[(f - DIM) * n + i] * isz);
+      else if (f < 2 * DIM + 2) val = bnd[2 * i + (f - 2 * DIM)];
+    }
+    const bf16 bv = __float2bfloat16_rn(val);
+    *reinterpret_cast<bf16*>(sx + tc_off(r, f, kLboX)) = bv;
+    if (i < npad) xg[i * GF + f] = bv;
+  }
+  for (int e = tid; e < GH * GF; e += 128)
+    *reinterpret_cast<bf16*>(sw + tc_off(e / GF, e % GF, kLboW)) = W0b[e];
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(
+        smem_addr(&tslot)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tslot;
+  if (tid == 0) {
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(GH / 8) << 17) |
+                           ((uint32_t)(kTcRows / 16) << 24);  // M 128, N 64
+    tc_mma(tmem, tc_desc(smem_addr(sx), kLboX, 128), tc_desc(smem_addr(sw), kLboW, 128), idesc, 0u);
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_addr(&mbar)));
+  }
+  const uint32_t done = tc_wait(&mbar, 0);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  float acc[GH];
+  if (done) {
+    tc_ld64(tmem + ((uint32_t)(warp * 32) << 16), acc);
+  } else {  // the product did not complete: NaN, which the solver rejects
+#pragma unroll
+    for (int j = 0; j < GH; ++j) acc[j] = __int_as_float(0x7fc00000);
+  }
+  const int64_t row = base + tid;
+  if (row < npad) {
+#pragma unroll
+    for (int c8 = 0; c8 < GH / 8; ++c8) {
+      __align__(16) bf16 ab[8], hb[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const float pre = acc[c8 * 8 + q] + b0[c8 * 8 + q];
+        ab[q] = __float2bfloat16_rn(pre);
+        hb[q] = __float2bfloat16_rn(relu(pre));
+      }
+      *reinterpret_cast<uint4*>(a0 + row * GH + c8 * 8) = *reinterpret_cast<const uint4*>(ab);
+      *reinterpret_cast<uint4*>(h0 + row * GH + c8 * 8) = *reinterpret_cast<const uint4*>(hb);
+    }
+  }
+  if (!done) tc_wait(&mbar, 0);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem));
+}
+
+// ---------------------------------------------------------------------
+// encoder backward on the tensor cores (persistent over 128-node tiles):
+// dW0 (64 x 16) += dpre0^T (64 x 128 nodes) x (128 nodes x 16), as an
+// M = 128 product whose rows 64-127 are zero, N = 16, accumulated in 16
+// tensor-memory columns across the block's tiles; db0 from the same dpre0
+// ---------------------------------------------------------------------
+__global__ void __launch_bounds__(128)
+    k_gnn_encode_bwd_tc(int64_t n, int64_t npad, int64_t ntc, const bf16* __restrict__ xg,
+                        const bf16* __restrict__ a0, const float* __restrict__ dh, float* part,
+                        int part_stride) {
+  __shared__ __align__(1024) uint8_t sA[kTcRows * kTcRows * 2];  // dpre0^T, rows 64.. zero
+  __shared__ __align__(1024) uint8_t sB[GF * kTcRows * 2];       // x^T: rows features
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tslot;
+  constexpr int kLboA = kTcRows * 16, kLboB = GF * 16;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  for (int e = tid; e < kTcRows * kTcRows / 8; e += 128)
+    reinterpret_cast<uint4*>(sA)[e] = make_uint4(0, 0, 0, 0);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(
+        smem_addr(&tslot)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tslot;
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(GF / 8) << 17) |
+                         ((uint32_t)(kTcRows / 16) << 24);  // M 128, N 16
+  float gb = 0.f;
+  uint32_t ok = 1, iter = 0;
+  for (int64_t tile = blockIdx.x; tile < ntc && ok; tile += gridDim.x, ++iter) {
+    const int64_t base = tile * kTcRows;
+    for (int e = tid; e < kTcRows * GH; e += 128) {
+      const int r = e / GH, f = e % GH;
+      const int64_t i = base + r;
+      float d = 0.f;
+      if (i < n && __bfloat162float(a0[i * GH + f]) > 0.f) d = dh[i * GH + f];
+      *reinterpret_cast<bf16*>(sA + tc_off(f, r, kLboA)) = __float2bfloat16_rn(d);
+    }
+    for (int e = tid; e < kTcRows * GF; e += 128) {
+      const int r = e / GF, f = e % GF;
+      const int64_t i = base + r;
+      *reinterpret_cast<bf16*>(sB + tc_off(f, r, kLboB)) =
+          i < npad ? xg[i * GF + f] : __float2bfloat16_rn(0.f);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (tid == 0) {
+#pragma unroll
+      for (int ks = 0; ks < kTcRows / 16; ++ks)
+        tc_mma(tmem, tc_desc(smem_addr(sA) + ks * 2 * kLboA, kLboA, 128),
+               tc_desc(smem_addr(sB) + ks * 2 * kLboB, kLboB, 128), idesc,
+               (ks > 0 || iter > 0) ? 1u : 0u);
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              smem_addr(&mbar)));
+    }
+    if (tid < GH)
+      for (int r = 0; r < kTcRows; ++r)
+        gb += __bfloat162float(*reinterpret_cast<const bf16*>(sA + tc_off(tid, r, kLboA)));
+    ok = tc_wait(&mbar, iter & 1);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();  // the operands are rewritten by the next tile
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  float* pp = part + (int64_t)blockIdx.x * part_stride;
+  if (warp < 2) {  // rows 0-63: dW0[o][0..15], o = tid
+    uint32_t v[GF];
+    if (iter > 0 && ok) {
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+          "%14,%15}, [%16];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+            "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+            "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+          : "r"(tmem + ((uint32_t)(warp * 32) << 16)));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    } else {
+#pragma unroll
+      for (int j = 0; j < GF; ++j) v[j] = iter > 0 ? 0x7fc00000u : 0u;
+    }
+#pragma unroll
+    for (int j = 0; j < GF; ++j) pp[tid * GF + j] = __uint_as_float(v[j]);
+    pp[GH * GF + tid] = ok ? gb : __int_as_float(0x7fc00000);
+  }
+  if (!ok) tc_wait(&mbar, (iter - 1) & 1);  // a late commit: wait again (bounded) before freeing
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem));
+}
+
+// ---------------------------------------------------------------------
 // decoder: y = Wd h + bd;  inference: z_out = z + s_z y
 // training: dy = 2 s_z (z + s_z y - delta) / |delta|^2, dh = Wd^T dy,
 // loss and dWd / dbd partials per block
@@ -657,60 +764,6 @@ __global__ void k_gnn_gather_dm(int nlf, int64_t n, const int32_t* __restrict__ 
   dnext[e] = s;
 }
 
-// encoder backward (persistent): dpre0 = dh0 * (a0 > 0); dW0 += dpre0^T x
-__global__ void __launch_bounds__(GTHREADS)
-    k_gnn_encode_bwd(int64_t n, int64_t ntiles, const bf16* __restrict__ xg,
-                     const bf16* __restrict__ a0, const float* __restrict__ dh, float* part,
-                     int part_stride) {
-  __shared__ __align__(16) bf16 sDT[GH][GT + 8];
-  __shared__ __align__(16) bf16 sXT[GF][GT + 8];
-  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-  const int g = lane >> 2, t = lane & 3;
-  float gw[GF / 8][4];
-#pragma unroll
-  for (int nt = 0; nt < GF / 8; ++nt) gw[nt][0] = gw[nt][1] = gw[nt][2] = gw[nt][3] = 0.f;
-  float gb = 0.f;
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int64_t base = tile * GT;
-    __syncthreads();
-    for (int e = threadIdx.x; e < GT * GH; e += GTHREADS) {
-      const int r = e / GH, f = e % GH;
-      const int64_t i = base + r;
-      float d = 0.f;
-      if (i < n && __bfloat162float(a0[i * GH + f]) > 0.f) d = dh[i * GH + f];
-      sDT[f][r] = __float2bfloat16_rn(d);
-    }
-    for (int e = threadIdx.x; e < GT * GF; e += GTHREADS) {
-      const int r = e / GF, f = e % GF;
-      sXT[f][r] = xg[(base + r) * GF + f];
-    }
-    __syncthreads();
-    if (threadIdx.x < GH)
-      for (int r = 0; r < GT; ++r) gb += __bfloat162float(sDT[threadIdx.x][r]);
-#pragma unroll
-    for (int kk = 0; kk < GT / 16; ++kk) {
-      uint32_t af[4];
-      frag_a(af, &sDT[0][0], GT + 8, wp * 16, kk * 16, lane);
-#pragma unroll
-      for (int nt = 0; nt < GF / 8; ++nt) {
-        uint32_t bfr[2];
-        frag_b(bfr, &sXT[0][0], GT + 8, nt * 8, kk * 16, lane);
-        mma16816(gw[nt], af, bfr);
-      }
-    }
-  }
-  float* pp = part + (int64_t)blockIdx.x * part_stride;
-#pragma unroll
-  for (int nt = 0; nt < GF / 8; ++nt)
-#pragma unroll
-    for (int hh = 0; hh < 2; ++hh)
-#pragma unroll
-      for (int cc = 0; cc < 2; ++cc) {
-        const int o = wp * 16 + g + 8 * hh, i = nt * 8 + 2 * t + cc;
-        pp[o * GF + i] = gw[nt][2 * hh + cc];
-      }
-  if (threadIdx.x < GH) pp[GH * GF + threadIdx.x] = gb;
-}
 
 // grad[off + e] += sum over blocks b of part[b][e] (block order), e < count
 __global__ void k_gnn_reduce(int nblocks, int part_stride, int count, const float* __restrict__ part,
@@ -784,8 +837,8 @@ int ensure(hofv_ctx* c, Gnn** out) {
   g->dim = c->dim;
   g->nlf = c->nlf;
   g->n = c->nc;
-  g->ntiles = (c->nc + GT - 1) / GT;
-  g->npad = g->ntiles * GT;
+  g->ntiles = (c->nc + kTcRows - 1) / kTcRows;
+  g->npad = g->ntiles * kTcRows;
   int64_t o = 0;
   g->off_W0 = o; o += GH * GF;
   g->off_b0 = o; o += GH;
@@ -846,14 +899,13 @@ int forward(hofv_ctx* c, Gnn* g, const double* v, const double* z, double* zout)
   launch_norm2(v, nd, c->d_red, c->d_count, g->scal + 0, c->red_blocks, st);
   launch_norm2(z, nd, c->d_red, c->d_count, g->scal + 1, c->red_blocks, st);
   k_gnn_scales<<<1, 1, 0, st>>>(g->scal, 1.0 / sqrt((double)nd));
-  const unsigned nt = (unsigned)g->ntiles;
-  if (g->dim == 2)
-    k_gnn_encode<2><<<nt, GTHREADS, 0, st>>>(g->n, v, z, g->bnd, g->scal, g->W0b,
-                                             g->theta + g->off_b0, g->x, abuf(g, 0), hbuf(g, 0));
-  else
-    k_gnn_encode<3><<<nt, GTHREADS, 0, st>>>(g->n, v, z, g->bnd, g->scal, g->W0b,
-                                             g->theta + g->off_b0, g->x, abuf(g, 0), hbuf(g, 0));
   const unsigned ntc = (unsigned)((g->n + kTcRows - 1) / kTcRows);
+  if (g->dim == 2)
+    k_gnn_encode_tc<2><<<ntc, 128, 0, st>>>(g->n, g->npad, v, z, g->bnd, g->scal, g->W0b,
+                                            g->theta + g->off_b0, g->x, abuf(g, 0), hbuf(g, 0));
+  else
+    k_gnn_encode_tc<3><<<ntc, 128, 0, st>>>(g->n, g->npad, v, z, g->bnd, g->scal, g->W0b,
+                                            g->theta + g->off_b0, g->x, abuf(g, 0), hbuf(g, 0));
   for (int l = 0; l < GL; ++l)
     k_gnn_layer_tc<<<ntc, 128, kTcSmem, st>>>(g->nlf, g->n, g->npad, hbuf(g, l), c->d_aj_col, g->w,
                                               g->Wb + (int64_t)l * GH * 2 * GH,
@@ -900,7 +952,6 @@ int backward(hofv_ctx* c, Gnn* g, const double* z, const double* delta) {
                                                           g->scal + 5, d * GH + d);
   float* dcur = g->dh0;
   float* dnext = g->dh1;
-  const int lb = (int)std::min<int64_t>(g->ntiles, gb);
   const int64_t ntc = (g->n + kTcRows - 1) / kTcRows;
   const int lbt = (int)std::min<int64_t>(ntc, gb);
   for (int l = GL - 1; l >= 0; --l) {
@@ -914,9 +965,9 @@ int backward(hofv_ctx* c, Gnn* g, const double* z, const double* delta) {
                                                                          g->w, g->dm, dnext);
     std::swap(dcur, dnext);
   }
-  k_gnn_encode_bwd<<<lb, GTHREADS, 0, st>>>(g->n, g->ntiles, g->x, abuf(g, 0), dcur, g->part,
+  k_gnn_encode_bwd_tc<<<lbt, 128, 0, st>>>(g->n, g->npad, ntc, g->x, abuf(g, 0), dcur, g->part,
                                             kPartStride);
-  k_gnn_reduce<<<(GH * GF + GH + 255) / 256, 256, 0, st>>>(lb, kPartStride, GH * GF + GH, g->part,
+  k_gnn_reduce<<<(GH * GF + GH + 255) / 256, 256, 0, st>>>(lbt, kPartStride, GH * GF + GH, g->part,
                                                             g->grad, g->off_W0, g->off_b0, GH * GF,
                                                             nullptr, 0);
   HOFV_CUDA(c, cudaGetLastError());
