@@ -484,7 +484,7 @@ __global__ void __launch_bounds__(128)
 // ---------------------------------------------------------------------
 template <int DIM>
 __global__ void __launch_bounds__(128)
-    k_gnn_encode_tc(int64_t n, int64_t npad, const double* __restrict__ v,
+    k_gnn_encode_tc(int64_t n, int64_t npad, int64_t ntc, const double* __restrict__ v,
                     const double* __restrict__ z, const float* __restrict__ bnd,
                     const double* __restrict__ scal, const bf16* __restrict__ W0b,
                     const float* __restrict__ b0, bf16* xg, bf16* a0, bf16* h0) {
@@ -494,24 +494,10 @@ __global__ void __launch_bounds__(128)
   __shared__ uint32_t tslot;
   constexpr int kLboX = kTcRows * 16, kLboW = GH * 16;
   const int tid = threadIdx.x, warp = tid >> 5;
-  const int64_t base = (int64_t)blockIdx.x * kTcRows;
   const double isv = 1.0 / scal[2], isz = 1.0 / scal[3];
-  for (int e = tid; e < kTcRows * GF; e += 128) {
-    const int r = e / GF, f = e % GF;
-    const int64_t i = base + r;
-    float val = 0.f;
-    if (i < n) {
-      if (f < DIM) val = (float)(v[f * n + i] * isv);
-      else if (f < 2 * DIM) val = (float)(z[(f - DIM) * n + i] * isz);
-      else if (f < 2 * DIM + 2) val = bnd[2 * i + (f - 2 * DIM)];
-    }
-    const bf16 bv = __float2bfloat16_rn(val);
-    *reinterpret_cast<bf16*>(sx + tc_off(r, f, kLboX)) = bv;
-    if (i < npad) xg[i * GF + f] = bv;
-  }
   for (int e = tid; e < GH * GF; e += 128)
     *reinterpret_cast<bf16*>(sw + tc_off(e / GF, e % GF, kLboW)) = W0b[e];
-  if (warp == 0) {
+  if (warp == 0) {  // once per block: the grid is a few blocks an SM, persistent over tiles
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(
         smem_addr(&tslot)));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -520,46 +506,77 @@ __global__ void __launch_bounds__(128)
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar)));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tslot;
-  if (tid == 0) {
-    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(GH / 8) << 17) |
-                           ((uint32_t)(kTcRows / 16) << 24);  // M 128, N 64
-    tc_mma(tmem, tc_desc(smem_addr(sx), kLboX, 128), tc_desc(smem_addr(sw), kLboW, 128), idesc, 0u);
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-            smem_addr(&mbar)));
-  }
-  const uint32_t done = tc_wait(&mbar, 0);
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  float acc[GH];
-  if (done) {
-    tc_ld64(tmem + ((uint32_t)(warp * 32) << 16), acc);
-  } else {  // the product did not complete: NaN, which the solver rejects
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(GH / 8) << 17) |
+                         ((uint32_t)(kTcRows / 16) << 24);  // M 128, N 64
+  uint32_t ok = 1, iter = 0;
+  for (int64_t tile = blockIdx.x; tile < ntc && ok; tile += gridDim.x, ++iter) {
+    const int64_t base = tile * kTcRows;
+    // one node per thread: its 16 features
+    {
+      const int r = tid;
+      const int64_t i = base + r;
+      __align__(16) bf16 xb[GF];
 #pragma unroll
-    for (int j = 0; j < GH; ++j) acc[j] = __int_as_float(0x7fc00000);
-  }
-  const int64_t row = base + tid;
-  if (row < npad) {
-#pragma unroll
-    for (int c8 = 0; c8 < GH / 8; ++c8) {
-      __align__(16) bf16 ab[8], hb[8];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const float pre = acc[c8 * 8 + q] + b0[c8 * 8 + q];
-        ab[q] = __float2bfloat16_rn(pre);
-        hb[q] = __float2bfloat16_rn(relu(pre));
+      for (int f = 0; f < GF; ++f) {
+        float val = 0.f;
+        if (i < n) {
+          if (f < DIM) val = (float)(v[f * n + i] * isv);
+          else if (f < 2 * DIM) val = (float)(z[(f - DIM) * n + i] * isz);
+          else if (f < 2 * DIM + 2) val = bnd[2 * i + (f - 2 * DIM)];
+        }
+        xb[f] = __float2bfloat16_rn(val);
       }
-      *reinterpret_cast<uint4*>(a0 + row * GH + c8 * 8) = *reinterpret_cast<const uint4*>(ab);
-      *reinterpret_cast<uint4*>(h0 + row * GH + c8 * 8) = *reinterpret_cast<const uint4*>(hb);
+#pragma unroll
+      for (int c8 = 0; c8 < GF / 8; ++c8) {
+        const uint4 q = reinterpret_cast<const uint4*>(xb)[c8];
+        *reinterpret_cast<uint4*>(sx + tc_off(r, c8 * 8, kLboX)) = q;
+        if (i < npad) *reinterpret_cast<uint4*>(xg + i * GF + c8 * 8) = q;
+      }
     }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (tid == 0) {
+      tc_mma(tmem, tc_desc(smem_addr(sx), kLboX, 128), tc_desc(smem_addr(sw), kLboW, 128), idesc,
+             0u);
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              smem_addr(&mbar)));
+    }
+    ok = tc_wait(&mbar, iter & 1);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    float acc[GH];
+    if (ok) {
+      tc_ld64(tmem + ((uint32_t)(warp * 32) << 16), acc);
+    } else {  // the product did not complete: NaN, which the solver rejects
+#pragma unroll
+      for (int j = 0; j < GH; ++j) acc[j] = __int_as_float(0x7fc00000);
+    }
+    const int64_t row = base + tid;
+    if (row < npad) {
+#pragma unroll
+      for (int c8 = 0; c8 < GH / 8; ++c8) {
+        __align__(16) bf16 ab[8], hb[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const float pre = acc[c8 * 8 + q] + b0[c8 * 8 + q];
+          ab[q] = __float2bfloat16_rn(pre);
+          hb[q] = __float2bfloat16_rn(relu(pre));
+        }
+        *reinterpret_cast<uint4*>(a0 + row * GH + c8 * 8) = *reinterpret_cast<const uint4*>(ab);
+        *reinterpret_cast<uint4*>(h0 + row * GH + c8 * 8) = *reinterpret_cast<const uint4*>(hb);
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();  // the operand and the accumulator are reused by the next tile
   }
-  if (!done) tc_wait(&mbar, 0);
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
+  if (!ok) tc_wait(&mbar, (iter - 1) & 1);  // a late commit: wait again (bounded) before freeing
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem));
 }
 
@@ -900,11 +917,12 @@ int forward(hofv_ctx* c, Gnn* g, const double* v, const double* z, double* zout)
   launch_norm2(z, nd, c->d_red, c->d_count, g->scal + 1, c->red_blocks, st);
   k_gnn_scales<<<1, 1, 0, st>>>(g->scal, 1.0 / sqrt((double)nd));
   const unsigned ntc = (unsigned)((g->n + kTcRows - 1) / kTcRows);
+  const unsigned neb = (unsigned)std::min<int64_t>(ntc, 4 * (int64_t)c->sm_count);
   if (g->dim == 2)
-    k_gnn_encode_tc<2><<<ntc, 128, 0, st>>>(g->n, g->npad, v, z, g->bnd, g->scal, g->W0b,
+    k_gnn_encode_tc<2><<<neb, 128, 0, st>>>(g->n, g->npad, ntc, v, z, g->bnd, g->scal, g->W0b,
                                             g->theta + g->off_b0, g->x, abuf(g, 0), hbuf(g, 0));
   else
-    k_gnn_encode_tc<3><<<ntc, 128, 0, st>>>(g->n, g->npad, v, z, g->bnd, g->scal, g->W0b,
+    k_gnn_encode_tc<3><<<neb, 128, 0, st>>>(g->n, g->npad, ntc, v, z, g->bnd, g->scal, g->W0b,
                                             g->theta + g->off_b0, g->x, abuf(g, 0), hbuf(g, 0));
   for (int l = 0; l < GL; ++l)
     k_gnn_layer_tc<<<ntc, 128, kTcSmem, st>>>(g->nlf, g->n, g->npad, hbuf(g, l), c->d_aj_col, g->w,
