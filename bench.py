@@ -160,6 +160,8 @@ def build_workload(name, device=0):
 
 
 def mesh_label(wl):
+    if wl.cells == "hexfaces":
+        return f"{wl.n}^3 hexes given face by face, {int(round(wl.jitter * 100))}% node jitter"
     if wl.cells == "polyhedron":
         return (f"{(wl.n + 1) ** 2} x {wl.n} polyhedra (dual polygons of 2 x {wl.n}^2 triangles "
                 f"extruded through {wl.n} layers), {int(round(wl.jitter * 100))}% node jitter")

@@ -89,19 +89,22 @@ __device__ __forceinline__ float relu(float x) { return x > 0.f ? x : 0.f; }
 // ---------------------------------------------------------------------
 __global__ void k_gnn_graph(int nlf, int64_t n, int64_t nfi, const double* __restrict__ diag,
                             const int32_t* __restrict__ col, const double* __restrict__ off,
-                            const int32_t* __restrict__ cface, float* w, float* bnd) {
+                            const int32_t* __restrict__ cface, const int64_t* __restrict__ cf,
+                            float* w, float* bnd) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
-  int nd = 0, nt = 0;
+  int nd = 0, nt = 0, nf = 0;  // the cell's faces: displacement (or symmetry), traction, all
   for (int k = 0; k < nlf; ++k) {
     const int32_t j = col[i * nlf + k];
     w[i * nlf + k] = j >= 0 ? (float)(off[i * nlf + k] / sqrt(diag[i] * diag[j])) : 0.f;
+    if (cf[i * nlf + k] < 0) continue;  // a polygon / polyhedron slot without a face
+    ++nf;
     const int32_t code = cface[i * nlf + k];
     if (code == 0) ++nt;
     else if (code > 0 && code - 1 >= nfi) ++nd;
   }
-  bnd[2 * i] = (float)nd / nlf;
-  bnd[2 * i + 1] = (float)nt / nlf;
+  bnd[2 * i] = (float)nd / nf;
+  bnd[2 * i + 1] = (float)nt / nf;
 }
 
 // rms scales from the norms: s = |x| / sqrt(count), 1 when the vector is zero
@@ -900,7 +903,8 @@ int ensure(hofv_ctx* c, Gnn** out) {
   cudaMemsetAsync(g->a, 0, sizeof(bf16) * (GL + 1) * g->npad * GH, c->stream);
   cudaMemsetAsync(g->x, 0, sizeof(bf16) * g->npad * GF, c->stream);
   k_gnn_graph<<<(unsigned)((g->n + 127) / 128), 128, 0, c->stream>>>(
-      g->nlf, g->n, c->nfi, c->d_aj_diag, c->d_aj_col, c->d_aj_off, c->d_cface, g->w, g->bnd);
+      g->nlf, g->n, c->nfi, c->d_aj_diag, c->d_aj_col, c->d_aj_off, c->d_cface, c->d_cf, g->w,
+      g->bnd);
   HOFV_CUDA(c, cudaGetLastError());
   refresh_bf16(c, g);
   HOFV_CUDA(c, cudaStreamSynchronize(c->stream));

@@ -730,6 +730,8 @@ class Workload:
             return (self.n + 1) ** 2
         if self.cells == "polyhedron":
             return (self.n + 1) ** 2 * self.n
+        if self.cells == "hexfaces":
+            return self.n ** 3
         per = (2 if self.dim == 2 else 6) if self.cells == "simplex" else 1
         return per * self.n ** self.dim
 
@@ -787,6 +789,10 @@ WORKLOADS = {
                                  "mms-trig3d", 1245, cells="polyhedron"),
     "prism24j-p2-trig": Workload("prism24j-p2-trig", 3, 24, 2, 55, 2, 0.1, 0, _MU_1G, _LAM_1G,
                                  "mms-trig3d", 1246, cells="polyhedron"),
+    # the 64^3 jittered hexes described face by face (every face 4 corners: the
+    # polyhedral path without padded fan slots), quadratic LSQ
+    "hexf64j-p2-trig": Workload("hexf64j-p2-trig", 3, 64, 2, 55, 2, 0.2, 0, _MU_1G, _LAM_1G,
+                                "mms-trig3d", 1247, cells="hexfaces"),
     # 3-D neo-Hookean, 128^3 jittered hexes, cubic LSQ
     "hex128j-p3-nh": Workload("hex128j-p3-nh", 3, 128, 3, 65, 3, 0.20, 1, 1e6, 4e6, "block",
                               1238, load_steps=10),
