@@ -594,6 +594,16 @@ int hofv_jvp_timed(hofv_ctx* ctx, const double* u, const double* Ru, const doubl
    synchronises. */
 int hofv_probe_peaks(hofv_ctx* ctx, double* fp64_tflops, double* fp32_tflops, int32_t* sm_count);
 
+/* The neo-Hookean law's J^{-1/3} (App. A, eq. neoHook: the isochoric factor
+   J^{-2/3} and the volumetric term use r = J^{-1/3}) as the face kernels
+   evaluate it -- a single-precision estimate corrected once in FP64 by the
+   binomial series of (1 - h)^{-1/3}, h = 1 - J r^3 -- next to CUDA's
+   double-precision rcbrt, for n values J (DEVICE arrays of n doubles; r_own
+   and r_lib DEVICE outputs of n doubles, either may be NULL).  Checks the
+   law's own routine against the library's error bound; no counterpart in
+   the paper.  HOFV_EINVAL for n < 0 or a NULL J with n > 0.  Synchronises. */
+int hofv_probe_inv_cbrt(hofv_ctx* ctx, const double* J, double* r_own, double* r_lib, int64_t n);
+
 /* ---- inspection (tests) -------------------------------------------------- */
 
 /* Face data for faces [first, first + count) to HOST arrays (any may be NULL):

@@ -21,6 +21,22 @@ constexpr int kPolyMaxSides = 8; // face slots of a polygon cell
 constexpr int kPolyhedronMaxFaces = 16;  // face slots of a polyhedral cell
 constexpr int kPolyFaceMaxCorners = 8;   // corners of a polyhedral face
 
+// J^{-1/3} for the neo-Hookean law, with one FP64 correction of a
+// single-precision estimate instead of the full double-precision routine:
+// with r = rcbrtf(J) and h = 1 - J r^3 (|h| ~ 1e-7), J^{-1/3} = r (1 - h)^{-1/3}
+// = r (1 + h/3 + 2 h^2/9 + O(h^3)) (binomial series; one step of
+// Householder's third-order iteration for r^-3 = J), exact to rounding since
+// h^3 ~ 1e-21.  Outside 1e-30 < J < 1e30 (beyond the float range of the
+// estimate) and for J <= 0 it defers to rcbrt (NaN for J <= 0).
+#if defined(__CUDACC__)
+__device__ __forceinline__ double inv_cbrt(double J) {
+  if (!(J > 1e-30 && J < 1e30)) return J > 0.0 ? rcbrt(J) : __longlong_as_double(0x7ff8000000000000LL);
+  const double r = (double)rcbrtf((float)J);
+  const double h = fma(-J, r * r * r, 1.0);
+  return fma(r, h * fma(h, 2.0 / 9.0, 1.0 / 3.0), r);
+}
+#endif
+
 // Device-side description of the discretisation used by the residual
 // kernels.  All pointers are device addresses owned by the context.
 struct DevMesh {

@@ -46,9 +46,29 @@ static int time_fma(hofv_ctx* c, int iters, T* scratch, double* tflops) {
   return 0;
 }
 
+__global__ void k_inv_cbrt(const double* __restrict__ J, double* __restrict__ own,
+                           double* __restrict__ lib, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double x = J[i];
+  if (own) own[i] = inv_cbrt(x);
+  if (lib) lib[i] = rcbrt(x);
+}
+
 }  // namespace hofv
 
 using namespace hofv;
+
+extern "C" int hofv_probe_inv_cbrt(hofv_ctx* c, const double* J, double* r_own, double* r_lib,
+                                   int64_t n) {
+  if (!c || n < 0 || (n > 0 && !J)) return HOFV_EINVAL;
+  if (n == 0) return 0;
+  HOFV_CUDA(c, cudaSetDevice(c->device));
+  k_inv_cbrt<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(J, r_own, r_lib, n);
+  HOFV_CUDA(c, cudaGetLastError());
+  HOFV_CUDA(c, cudaStreamSynchronize(c->stream));
+  return 0;
+}
 
 extern "C" int hofv_probe_peaks(hofv_ctx* c, double* fp64_tflops, double* fp32_tflops,
                                 int32_t* sm_count) {

@@ -170,7 +170,7 @@ __device__ __forceinline__ void traction(const double (&G)[3][3], const double* 
     const double J = F[0][0] * C[0][0] + F[0][1] * C[0][1] + F[0][2] * C[0][2];
     // J^{-1/3}; not defined for J <= 0 (an inverted element): NaN, so the
     // caller's finiteness checks reject the state
-    const double r = J > 0.0 ? rcbrt(J) : __longlong_as_double(0x7ff8000000000000LL);
+    const double r = inv_cbrt(J);
     const double r3 = r * r * r;
     const double alpha = mt.mu * (r * r) * r3;
     double trB = 0.0;  // tr(F F^T): the squares of F's entries
@@ -965,8 +965,22 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
                "l"(src)
                : "memory");
 }
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.commit_group;\ncp.async.wait_all;" ::: "memory");
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(
+                   static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
+               "l"(src)
+               : "memory");
+}
+// n doubles (n even, both ends 16-byte aligned) global -> shared, by the
+// block's nthreads threads
+__device__ __forceinline__ void stage16(double* dst, const double* src, int n, int it, int nthreads) {
+  for (int c = it; c < n / 2; c += nthreads) cp_async16(dst + 2 * c, src + 2 * c);
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// wait until at most N of this thread's committed groups are pending
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
 // Face fluxes, double-float gradient rows.  QD Gauss points per face
@@ -994,10 +1008,13 @@ __device__ __forceinline__ void cp_async_wait_all() {
 // RING coalesced 8-byte loads in flight per thread; with R a compile-time
 // constant every ring offset is an immediate.  Faces come in groups of part
 // of a tile, one thread per (face, row): in 3-D a quarter tile of 216
-// threads for 3 x 3 points, four blocks an SM (measured on the 128^3
-// neo-Hookean block: 7 % faster than half tiles two an SM, 10 % slower with
-// eighth tiles), half tiles otherwise, and for faces with many points
-// (polyhedral fans, R = 48 or 96) quarter or eighth tiles of 384 threads.
+// threads for 3 x 3 points, five blocks an SM (measured on the 128^3
+// neo-Hookean block: quarter tiles 7 % faster than half tiles two an SM,
+// 10 % faster than eighth tiles), half tiles otherwise, and for faces with
+// many points (polyhedral fans, R = 48 or 96) quarter or eighth tiles of 384
+// threads.  In 3-D the operands read after the contraction (row sums,
+// reference values, area vectors, the Jv cache) are copied into shared
+// memory while it runs.
 // A block contracts GPB groups one after the other (the gradients stay in
 // shared memory) and then evaluates the law at all their Gauss points at
 // once: R = Q d rows a face, so d groups have exactly as many points as the
@@ -1011,14 +1028,22 @@ struct DfShape {
                              : QD == 16 ? 8
                              : QD == 32 ? 4
                                         : 16;  // faces per group
-  static constexpr int RING = 8;  // coefficient loads in flight per thread (4 in 2-D: 6 % slower)
+  // coefficient loads in flight per thread (4 in 2-D: 6 % slower; 3 x 3
+  // points: 6, with five blocks an SM, 5 % faster than 8 with four)
+  static constexpr int RING = (DIM == 3 && QD == 9) ? 6 : 8;
   static constexpr int THREADS = FPB * QD * DIM;
   // face groups per block: with GPB = d, GPB FPB Q = THREADS and each thread
   // evaluates one law (a face's Gauss point) after the block's contractions
   // (measured: 9 % faster on the 48-layer prisms, 5 % on 512^2 quads); 3 x 3
   // points keep one group a block (5 % slower with three on the 128^3 block)
   static constexpr int GPB = (DIM == 3 && QD == 9) ? 1 : DIM;
-  static constexpr int MIN_BLOCKS = DIM == 2 ? 6 : (THREADS <= 256 ? 4 : 2);  // per SM
+  static constexpr int MIN_BLOCKS = DIM == 2 ? 6 : (THREADS <= 256 ? 5 : 2);  // per SM
+  // 3-D: the epilogue's and the law's operands (row sums, reference values,
+  // area vectors and, in Jv mode, the cached gradients and tractions) are
+  // copied into shared memory while the contraction runs (a second group of
+  // asynchronous copies, waited for after it), instead of being loaded after
+  // it with their latency exposed
+  static constexpr bool STAGE = DIM == 3;
 };
 
 // dynamic shared memory: the gathered cell values and the faces' references
@@ -1029,7 +1054,8 @@ static size_t df_smem_bytes(int S) {
   constexpr int R = QD * DIM;
   const size_t gath = (size_t)S * SH::FPB * DIM * 16;
   const size_t law = (size_t)SH::GPB * SH::FPB * (R * DIM + QD * DIM) * sizeof(double);
-  return gath + law;
+  const size_t staged = SH::STAGE ? (size_t)SH::GPB * SH::FPB * (QD * 3 + R + DIM) * sizeof(double) : 0;
+  return gath + law + staged;
 }
 
 template <int DIM, int LAW, int MODE, int QD>
@@ -1049,6 +1075,11 @@ __global__ void __launch_bounds__(DfShape<DIM, QD>::THREADS, DfShape<DIM, QD>::M
   float4* us = reinterpret_cast<float4*>(sm);
   double* Gs = reinterpret_cast<double*>(us + (size_t)S * FPB * DIM);  // [GPB][FPB][R][DIM]
   double* Ts = Gs + GPB * FPB * R * DIM;                               // [GPB][FPB][Q][DIM]
+  constexpr bool STG = SH::STAGE;
+  double* As = Ts + GPB * FPB * Q * DIM;  // [GPB][FPB][Q][3] staged area vectors
+  double* Cs = As + GPB * FPB * Q * 3;    // [GPB][FPB][R] staged row sums
+  double* Ws = Cs + GPB * FPB * R;        // [GPB][FPB][DIM] staged reference values
+  const int64_t ldw = m.wst;
   const int64_t ngroups = m.nftile * BPT;
   const int64_t g0 = (int64_t)blockIdx.x * GPB;
   const int ng = (int)(ngroups - g0 < GPB ? ngroups - g0 : GPB);  // the same for every thread
@@ -1080,8 +1111,31 @@ __global__ void __launch_bounds__(DfShape<DIM, QD>::THREADS, DfShape<DIM, QD>::M
       const int32_t id = __ldg(st + n * kTile + fj);
 #pragma unroll
       for (int h = 0; h < DIM; ++h) cp_async16(us + t * DIM + h, sw + (int64_t)id * DIM + h);
+      if (STG && n == 0) {  // the reference cell's FP64 value
+#pragma unroll
+        for (int j = 0; j < DIM; ++j) cp_async8(Ws + (gi * FPB + fj) * DIM + j, wd + j * ldw + id);
+      }
     }
-    cp_async_wait_all();
+    cp_async_commit();
+    if (STG) {
+      // second group, waited for only after the contraction: each thread's
+      // own row sum and (Jv) cached gradient row, and the group's area
+      // vectors and (Jv) cached tractions for the law
+      cp_async8(Cs + gi * FPB * R + it, m.fcsum + f * R + r);
+      if (MODE == kDfJv) {
+#pragma unroll
+        for (int j = 0; j < DIM; ++j)
+          cp_async8(Gs + (gi * FPB * R + it) * DIM + j, m.gcache + (f * R + r) * DIM + j);
+        stage16(Ts + gi * FPB * Q * DIM, m.tcache + f0 * Q * DIM, FPB * Q * DIM, it, SH::THREADS);
+      }
+      // area vectors: faces up to the last one stored
+      const int na = (int)(m.nf - f0 < FPB ? (m.nf - f0 > 0 ? m.nf - f0 : 0) : FPB) * Q * 3;
+      for (int c = it; c < na; c += SH::THREADS) cp_async8(As + gi * FPB * Q * 3 + c, m.aq + f0 * Q * 3 + c);
+      cp_async_commit();
+      cp_async_wait_group<1>();  // the gather
+    } else {
+      cp_async_wait_group<0>();
+    }
     __syncthreads();
     for (int t = FPB * DIM + it; t < S * FPB * DIM; t += SH::THREADS) {
       const float2 dv = diff3(us[t], us[t % (FPB * DIM)]);
@@ -1121,14 +1175,19 @@ __global__ void __launch_bounds__(DfShape<DIM, QD>::THREADS, DfShape<DIM, QD>::M
         mac_slot(n, c);
       }
     }
+    if (STG) cp_async_wait_group<0>();  // this thread's staged operands
     {
       // + w_N0 sum_N c_N, in FP64
-      const int32_t id0 = __ldg(st + fi);
-      const int64_t ldw = m.wst;
-      const double cs = live ? m.fcsum[f * R + r] : 0.0;
+      const double cs = live ? (STG ? Cs[gi * FPB * R + it] : m.fcsum[f * R + r]) : 0.0;
       double g[DIM];
+      if (STG) {
 #pragma unroll
-      for (int j = 0; j < DIM; ++j) g[j] = fma(cs, __ldg(wd + j * ldw + id0), ff_value(s[j], e[j]));
+        for (int j = 0; j < DIM; ++j) g[j] = fma(cs, Ws[(gi * FPB + fi) * DIM + j], ff_value(s[j], e[j]));
+      } else {
+        const int32_t id0 = __ldg(st + fi);
+#pragma unroll
+        for (int j = 0; j < DIM; ++j) g[j] = fma(cs, __ldg(wd + j * ldw + id0), ff_value(s[j], e[j]));
+      }
       if (MODE == kDfResidual || MODE == kDfFill) {
         if (live && f >= m.nfi && f < m.nfid) {  // ghost node of a displacement face (prescribed data)
           const int64_t fd = f - m.nfi;
@@ -1144,8 +1203,9 @@ __global__ void __launch_bounds__(DfShape<DIM, QD>::THREADS, DfShape<DIM, QD>::M
         for (int j = 0; j < DIM; ++j) m.gcache[row + j] = g[j];
       }
       if (MODE == kDfJv) {  // grad (u + eps v) = grad u + eps grad v
+        double* gr = Gs + (gi * FPB * R + it) * DIM;  // staged: this row of the cache
 #pragma unroll
-        for (int j = 0; j < DIM; ++j) g[j] = fma(eps, g[j], m.gcache[row + j]);
+        for (int j = 0; j < DIM; ++j) g[j] = fma(eps, g[j], STG ? gr[j] : m.gcache[row + j]);
       }
 #pragma unroll
       for (int j = 0; j < DIM; ++j) Gs[(gi * FPB * R + it) * DIM + j] = g[j];
@@ -1161,8 +1221,9 @@ __global__ void __launch_bounds__(DfShape<DIM, QD>::THREADS, DfShape<DIM, QD>::M
       double t[DIM];
       if (fq < m.nfid) {
         double a[3];
+        const double* aq = STG ? As + ((gi * FPB + fj) * Q + q) * 3 : m.aq + (fq * Q + q) * 3;
 #pragma unroll
-        for (int k = 0; k < DIM; ++k) a[k] = m.aq[(fq * Q + q) * 3 + k];
+        for (int k = 0; k < DIM; ++k) a[k] = aq[k];
         double G[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
         const double* gq = Gs + ((gi * FPB + fj) * R + q * DIM) * DIM;
 #pragma unroll
@@ -1180,8 +1241,9 @@ __global__ void __launch_bounds__(DfShape<DIM, QD>::THREADS, DfShape<DIM, QD>::M
         for (int i = 0; i < DIM; ++i) m.tcache[o + i] = t[i];
       }
       if (MODE == kDfJv) {
+        const double* tc = STG ? Ts + ((gi * FPB + fj) * Q + q) * DIM : m.tcache + o;  // staged: this point
 #pragma unroll
-        for (int i = 0; i < DIM; ++i) t[i] -= m.tcache[o + i];
+        for (int i = 0; i < DIM; ++i) t[i] -= tc[i];
       }
 #pragma unroll
       for (int i = 0; i < DIM; ++i) Ts[((gi * FPB + fj) * Q + q) * DIM + i] = t[i];

@@ -111,6 +111,7 @@ SIGNATURES = {
     "hofv_set_contraction": (_I, [_P, _I]),
     "hofv_set_precision": (_I, [_P, _I]),
     "hofv_probe_peaks": (_I, [_P, C.POINTER(_D), C.POINTER(_D), C.POINTER(C.c_int32)]),
+    "hofv_probe_inv_cbrt": (_I, [_P, _P, _P, _P, C.c_int64]),
     "hofv_set_stencils": (_I, [_P, _P, _P]),
     "hofv_prepare_solver": (_I, [_P, C.POINTER(SolveOpts)]),
     "hofv_solve_load_path": (_I, [_P, _P, _P, _P, _P, _P, _P, C.c_int32, C.c_int32,
@@ -318,6 +319,11 @@ class Context:
         d, f, n = C.c_double(), C.c_double(), C.c_int32()
         self._check(self._L.hofv_probe_peaks(self.h, C.byref(d), C.byref(f), C.byref(n)))
         return {"fp64_tflops": d.value, "fp32_tflops": f.value, "sm_count": n.value}
+
+    def probe_inv_cbrt(self, J, r_own, r_lib):
+        """The law's J^{-1/3} and CUDA's rcbrt of the device vector J."""
+        self._check(self._L.hofv_probe_inv_cbrt(self.h, _ptr(_dev(J)), _ptr(_dev(r_own)),
+                                                _ptr(_dev(r_lib)), int(J.numel())))
 
     @property
     def precision(self):
