@@ -58,6 +58,8 @@ DevMesh dev_mesh(const hofv_ctx* c) {
   m.fstar = c->d_fstar;
   m.fstab = c->d_fstab;
   m.fql = c->d_fql;
+  m.pgrp = c->d_pgrp;
+  m.npg = c->npg;
   m.cst = c->d_cst;
   m.cex = c->d_cex;
   m.cface = c->d_cface;
@@ -158,6 +160,8 @@ static void free_built(hofv_ctx* c) {
   c->d_fst = c->d_cst = c->d_fstar = c->d_cface = nullptr;
   c->d_fco = c->d_gco = c->d_cex = c->d_fstab = nullptr;
   c->d_fql = nullptr;
+  c->d_pgrp = nullptr;
+  c->npg = 0;
   c->d_ubq = c->d_ubf = c->d_tbq = c->d_body = c->d_src = nullptr;
   c->d_tco = c->d_gflux = nullptr;
   c->tco_valid = false;
@@ -859,6 +863,30 @@ int hofv_build_stencils(hofv_ctx* c) {
     }
     TRY(dev_alloc(c, &c->d_fql, nfp));
     HOFV_CUDA(c, cudaMemcpy(c->d_fql, ql.data(), sizeof(int32_t) * nfp, cudaMemcpyHostToDevice));
+    if (c->Q == 32) {
+      // faces of 8 fan slots (Q = 32): consecutive faces of a tile packed into
+      // groups whose rows with area fill the packed kernel's threads
+      std::vector<int32_t> grp;
+      for (int64_t t0 = 0; t0 < c->nfid; t0 += kTile) {
+        const int64_t t1 = std::min<int64_t>(t0 + kTile, c->nfid);
+        int64_t f = t0;
+        while (f < t1) {
+          int rows = 0, n = 0;
+          while (f + n < t1 && n < kPackMaxFaces && rows + ql[f + n] * c->dim <= kPackThreads) {
+            rows += ql[f + n] * c->dim;
+            ++n;
+          }
+          if (n == 0) return fail(c, HOFV_EINVAL, "a polyhedral face has more points than a packed group");
+          grp.push_back((int32_t)f);
+          grp.push_back(n);
+          f += n;
+        }
+      }
+      c->npg = (int64_t)grp.size() / 2;
+      TRY(dev_alloc(c, &c->d_pgrp, std::max<int64_t>(c->npg, 1) * 2));
+      if (c->npg > 0)
+        HOFV_CUDA(c, cudaMemcpy(c->d_pgrp, grp.data(), sizeof(int32_t) * grp.size(), cudaMemcpyHostToDevice));
+    }
   }
   TRY(dev_alloc(c, &c->d_aj_diag, nc));
   TRY(dev_alloc(c, &c->d_aj_col, nc * nlf));

@@ -20,6 +20,8 @@ constexpr int kMaxQC = 64;       // Gauss points per cell (4^3)
 constexpr int kPolyMaxSides = 8; // face slots of a polygon cell
 constexpr int kPolyhedronMaxFaces = 16;  // face slots of a polyhedral cell
 constexpr int kPolyFaceMaxCorners = 8;   // corners of a polyhedral face
+constexpr int kPackThreads = 384;        // threads (rows with area) of a packed face group
+constexpr int kPackMaxFaces = 8;         // faces of a packed face group
 
 // J^{-1/3} for the neo-Hookean law, with one FP64 correction of a
 // single-precision estimate instead of the full double-precision routine:
@@ -54,6 +56,10 @@ struct DevMesh {
   const double* fstab;    // [nfid]     Gamma_f / |d . n|
   const int32_t* fql;     // [nftile * kTile] points of each face that carry area (polyhedral
                           // fans with fewer corners than slots), or nullptr: all Q
+  const int32_t* pgrp;    // [npg][2] polyhedral faces with 8 fan slots packed by their
+                          // points with area: first face and face count of each group
+                          // (consecutive faces of one tile), or nullptr
+  int64_t npg;            // groups in pgrp
   // cells
   const int32_t* cst;     // [nctile][S][kTile]
   const double* cex;      // [nctile][S][kTile][nlf]
@@ -154,6 +160,8 @@ struct hofv_ctx {
   int32_t* d_fstar = nullptr;
   double* d_fstab = nullptr;
   int32_t* d_fql = nullptr;
+  int32_t* d_pgrp = nullptr;        // packed face groups (polyhedra, 8 fan slots)
+  int64_t npg = 0;
   int32_t* d_cface = nullptr;
   double max_cond = 0.0;
   double setup_seconds = 0.0;

@@ -1012,8 +1012,8 @@ __device__ __forceinline__ void cp_async_wait_group() {
 // neo-Hookean block: quarter tiles 7 % faster than half tiles two an SM,
 // 10 % faster than eighth tiles), half tiles otherwise, and for faces with
 // many points (polyhedral fans, R = 48 or 96) quarter or eighth tiles of 384
-// threads.  In 3-D the operands read after the contraction (row sums,
-// reference values, area vectors, the Jv cache) are copied into shared
+// threads.  For 3 x 3 points the operands read after the contraction (row
+// sums, reference values, area vectors, the Jv cache) are copied into shared
 // memory while it runs.
 // A block contracts GPB groups one after the other (the gradients stay in
 // shared memory) and then evaluates the law at all their Gauss points at
@@ -1038,12 +1038,13 @@ struct DfShape {
   // points keep one group a block (5 % slower with three on the 128^3 block)
   static constexpr int GPB = (DIM == 3 && QD == 9) ? 1 : DIM;
   static constexpr int MIN_BLOCKS = DIM == 2 ? 6 : (THREADS <= 256 ? 5 : 2);  // per SM
-  // 3-D: the epilogue's and the law's operands (row sums, reference values,
-  // area vectors and, in Jv mode, the cached gradients and tractions) are
-  // copied into shared memory while the contraction runs (a second group of
-  // asynchronous copies, waited for after it), instead of being loaded after
-  // it with their latency exposed
-  static constexpr bool STAGE = DIM == 3;
+  // 3 x 3 points: the epilogue's and the law's operands (row sums, reference
+  // values, area vectors and, in Jv mode, the cached gradients and
+  // tractions) are copied into shared memory while the contraction runs (a
+  // second group of asynchronous copies, waited for after it), instead of
+  // being loaded after it with their latency exposed (measured: 5 % faster
+  // on the 128^3 block; 27 % slower with 2 x 2 points, three groups a block)
+  static constexpr bool STAGE = DIM == 3 && QD == 9;
 };
 
 // dynamic shared memory: the gathered cell values and the faces' references
@@ -1276,6 +1277,260 @@ __global__ void __launch_bounds__(DfShape<DIM, QD>::THREADS, DfShape<DIM, QD>::M
   }
 }
 
+// Packed variant for polyhedral faces of 8 fan slots (Q = 32 points, 96
+// rows a face).  The rows of the slots past a face's last corner carry no
+// area; rather than one thread for each row of FPB whole faces, a group here
+// is a run of consecutive faces of one tile whose rows with area fill the
+// block's kPackThreads threads (at most kPackMaxFaces faces; the host builds
+// the runs, DevMesh::pgrp).  Thread it of a group takes the group's it-th
+// row with area, and the gradients, tractions and staged operands are
+// indexed by packed row and packed point.  Everything else is k_flux_df's:
+// reference differences, register ring, staged operands, GPB groups one
+// after the other and then the law at all their points (at most
+// kPackThreads / 3 a group, one a thread), Gauss sums over the points with
+// area in the same order, stabilisation.  The fluxes equal k_flux_df's bit
+// for bit (the padded points add exact zeros there).
+template <int LAW, int MODE>
+__global__ void __launch_bounds__(kPackThreads, 2)
+    k_flux_df_pk(DevMesh m, Material mt, const float4* __restrict__ sw, const double* __restrict__ wd,
+                 const double* __restrict__ ws, const double* __restrict__ ubq,
+                 const double* __restrict__ ubf, const double* __restrict__ d_eps,
+                 double* __restrict__ flux) {
+  constexpr int DIM = 3, Q = 32, R = Q * DIM, PM = kPackMaxFaces, T = kPackThreads, GPB = 3;
+  constexpr int PTS = T / DIM;  // points with area of a group, at most
+  constexpr int kRing = 8;
+  constexpr int CS = kTile * R;  // coefficient stride between stencil slots
+  extern __shared__ __align__(16) double sm[];
+  const int S = m.S;
+  float4* us = reinterpret_cast<float4*>(sm);                         // [S][PM][DIM]
+  double* Gs = reinterpret_cast<double*>(us + (size_t)S * PM * DIM);  // [GPB][T][DIM]
+  double* Ts = Gs + GPB * T * DIM;                                    // [GPB][PTS][DIM]
+  double* As = Ts + GPB * PTS * DIM;                                  // [GPB][PTS][3]
+  double* Cs = As + GPB * PTS * 3;                                    // [T] row sums
+  double* Ws = Cs + T;                                                // [PM][DIM] reference values
+  int* rowp = reinterpret_cast<int*>(Ws + PM * DIM);                  // [GPB][PM + 1] row offsets
+  int* gf = rowp + GPB * (PM + 1);                                    // [GPB][2] first face, faces
+  const int64_t ldw = m.wst;
+  const int64_t g0 = (int64_t)blockIdx.x * GPB;
+  const int ng = (int)(m.npg - g0 < GPB ? m.npg - g0 : GPB);
+  const int it = threadIdx.x;
+  const double eps = MODE == kDfJv ? __ldg(d_eps) : 0.0;
+  if (it < GPB) {  // the block's groups and the prefix sums of their rows with area
+    int fa = 0, na = 0;
+    if (it < ng) {
+      fa = m.pgrp[2 * (g0 + it)];
+      na = m.pgrp[2 * (g0 + it) + 1];
+    }
+    gf[2 * it] = fa;
+    gf[2 * it + 1] = na;
+    int acc = 0;
+    rowp[it * (PM + 1)] = 0;
+    for (int k = 0; k < PM; ++k) {
+      if (k < na) acc += m.fql[fa + k] * DIM;
+      rowp[it * (PM + 1) + k + 1] = acc;
+    }
+  }
+  __syncthreads();
+  float2 cq[kRing];
+  for (int gi = 0; gi < ng; ++gi) {
+    const int f0 = gf[2 * gi], nf = gf[2 * gi + 1];
+    const int* rp = rowp + gi * (PM + 1);
+    const int64_t tile = f0 / kTile;
+    const int fb = f0 % kTile;
+    const int nrows = rp[nf];
+    int fi = 0;  // this thread's face in the group and its row there
+    while (fi + 1 < nf && rp[fi + 1] <= it) ++fi;
+    const bool live = it < nrows;
+    const int r = live ? it - rp[fi] : 0;
+    const int64_t f = f0 + fi;
+    const int32_t* __restrict__ st = m.fst + tile * (int64_t)S * kTile + fb;
+    const float2* __restrict__ co =
+        reinterpret_cast<const float2*>(m.fco) + tile * (int64_t)S * CS + (fb + fi) * R + r + CS;
+    const int SL = live ? S - 1 : 0;
+#pragma unroll
+    for (int d = 0; d < kRing; ++d) cq[d] = d < SL ? __ldg(co + d * CS) : make_float2(0.f, 0.f);
+    for (int t = it; t < S * nf; t += T) {
+      const int n = t / nf, fj = t % nf;
+      const int32_t id = __ldg(st + n * kTile + fj);
+#pragma unroll
+      for (int h = 0; h < DIM; ++h) cp_async16(us + (n * PM + fj) * DIM + h, sw + (int64_t)id * DIM + h);
+      if (n == 0) {
+#pragma unroll
+        for (int j = 0; j < DIM; ++j) cp_async8(Ws + fj * DIM + j, wd + j * ldw + id);
+      }
+    }
+    cp_async_commit();
+    // second group: this thread's row sum and (Jv) cached gradient row, the
+    // group's area vectors and (Jv) cached tractions by packed point
+    if (live) {
+      cp_async8(Cs + it, m.fcsum + f * R + r);
+      if (MODE == kDfJv) {
+#pragma unroll
+        for (int j = 0; j < DIM; ++j)
+          cp_async8(Gs + (gi * T + it) * DIM + j, m.gcache + (f * R + r) * DIM + j);
+      }
+    }
+    if (it < nrows / DIM) {
+      const int p = it;
+      int fj = 0;
+      while (rp[fj + 1] <= p * DIM) ++fj;
+      const int q = p - rp[fj] / DIM;
+      const int64_t o = ((int64_t)(f0 + fj) * Q + q) * 3;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) cp_async8(As + (gi * PTS + p) * 3 + k, m.aq + o + k);
+      if (MODE == kDfJv) {
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) cp_async8(Ts + (gi * PTS + p) * DIM + k, m.tcache + o + k);
+      }
+    }
+    cp_async_commit();
+    cp_async_wait_group<1>();  // the gather
+    __syncthreads();
+    for (int t = it; t < (S - 1) * nf * DIM; t += T) {
+      const int n = 1 + t / (nf * DIM), k = t % (nf * DIM);
+      const int e = n * PM * DIM + k;  // k = fj * DIM + h
+      const float2 dv = diff3(us[e], us[k]);
+      us[e] = make_float4(dv.x, dv.y, 0.f, 0.f);
+    }
+    __syncthreads();
+    float s[DIM], e[DIM];
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) s[j] = e[j] = 0.f;
+    const float4* __restrict__ uf = us + PM * DIM + fi * DIM;  // slot 1 of the thread's face
+    auto mac_slot = [&](int n, float2 c) {
+#pragma unroll
+      for (int j = 0; j < DIM; ++j) {
+        const float4 a = uf[n * PM * DIM + j];
+        ff_mac(c.x, c.y, a.x, a.y, s[j], e[j]);
+      }
+    };
+    int n0 = 0;
+    for (; n0 + 2 * kRing <= SL; n0 += kRing) {
+      const float2* cn = co + (n0 + kRing) * CS;
+#pragma unroll
+      for (int d = 0; d < kRing; ++d) {
+        const float2 c = cq[d];
+        cq[d] = __ldg(cn + d * CS);
+        mac_slot(n0 + d, c);
+      }
+    }
+#pragma unroll
+    for (int d = 0; d < 2 * kRing; ++d) {
+      const int n = n0 + d;
+      if (n < SL) {
+        const float2 c = cq[d % kRing];
+        if (n + kRing < SL) cq[d % kRing] = __ldg(co + (n + kRing) * CS);
+        mac_slot(n, c);
+      }
+    }
+    cp_async_wait_group<0>();
+    {
+      const double cs = live ? Cs[it] : 0.0;
+      double g[DIM];
+#pragma unroll
+      for (int j = 0; j < DIM; ++j) g[j] = fma(cs, Ws[fi * DIM + j], ff_value(s[j], e[j]));
+      if (MODE == kDfResidual || MODE == kDfFill) {
+        if (live && f >= m.nfi && f < m.nfid) {  // ghost node of a displacement face
+          const int64_t fd = f - m.nfi;
+          const double cg = m.gco[fd * R + r];
+          const int q = r / DIM;
+#pragma unroll
+          for (int j = 0; j < DIM; ++j) g[j] = fma(cg, ubq[(fd * Q + q) * DIM + j], g[j]);
+        }
+      }
+      double* gr = Gs + (gi * T + it) * DIM;
+      if (MODE == kDfFill && live) {
+#pragma unroll
+        for (int j = 0; j < DIM; ++j) m.gcache[(f * R + r) * DIM + j] = g[j];
+      }
+      if (MODE == kDfJv) {
+#pragma unroll
+        for (int j = 0; j < DIM; ++j) g[j] = fma(eps, g[j], live ? gr[j] : 0.0);
+      }
+#pragma unroll
+      for (int j = 0; j < DIM; ++j) gr[j] = g[j];
+    }
+    __syncthreads();  // the next group's gather overwrites the differences
+  }
+  // law at each point with area of the block's groups, one a thread
+  {
+    const int gi = it / PTS, p = it % PTS;
+    if (gi < ng) {
+      const int* rp = rowp + gi * (PM + 1);
+      const int nf = gf[2 * gi + 1];
+      if (p < rp[nf] / DIM) {
+        int fj = 0;
+        while (rp[fj + 1] <= p * DIM) ++fj;
+        const int q = p - rp[fj] / DIM;
+        const int64_t fq = gf[2 * gi] + fj;
+        double t[DIM];
+        if (fq < m.nfid) {
+          double a[3];
+#pragma unroll
+          for (int k = 0; k < DIM; ++k) a[k] = As[(gi * PTS + p) * 3 + k];
+          double G[3][3];
+          const double* gq = Gs + (gi * T + rp[fj] + q * DIM) * DIM;
+#pragma unroll
+          for (int i = 0; i < DIM; ++i)
+#pragma unroll
+            for (int j = 0; j < DIM; ++j) G[i][j] = gq[i * DIM + j];
+          traction<DIM, LAW>(G, a, mt, t);
+        } else {
+#pragma unroll
+          for (int i = 0; i < DIM; ++i) t[i] = 0.0;
+        }
+        double* tp = Ts + (gi * PTS + p) * DIM;
+        if (MODE == kDfFill) {
+#pragma unroll
+          for (int i = 0; i < DIM; ++i) m.tcache[(fq * Q + q) * DIM + i] = t[i];
+        }
+        if (MODE == kDfJv) {
+#pragma unroll
+          for (int i = 0; i < DIM; ++i) t[i] -= tp[i];
+        }
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) tp[i] = t[i];
+      }
+    }
+  }
+  if (MODE == kDfFill) return;
+  __syncthreads();
+  // Gauss sums over each face's points with area + alpha stabilisation
+  for (int t3 = it; t3 < ng * PM * DIM; t3 += T) {
+    const int gi = t3 / (PM * DIM), fj = (t3 / DIM) % PM, i = t3 % DIM;
+    const int* rp = rowp + gi * (PM + 1);
+    if (fj >= gf[2 * gi + 1]) continue;
+    const int64_t ff = gf[2 * gi] + fj;
+    if (ff >= m.nfid) continue;
+    double acc = 0.0;
+    for (int p = rp[fj] / DIM; p < rp[fj + 1] / DIM; ++p) acc += Ts[(gi * PTS + p) * DIM + i];
+    const int32_t sp = m.fstar[2 * ff], sn = m.fstar[2 * ff + 1];
+    const bool sym = sn < 0 && ff >= m.nfi + m.nfd;
+    const double up = ws[(int64_t)sp * DIM + i];
+    const double other = sn >= 0 ? ws[(int64_t)sn * DIM + i]
+                         : sym   ? mirror_i<DIM>(ws + (int64_t)sp * DIM, m.nrm + 3 * ff, i)
+                         : MODE == kDfResidual ? ubf[(ff - m.nfi) * DIM + i]
+                                               : 0.0;
+    const double coef = mt.alpha * mt.kbar * m.fstab[ff] * (MODE == kDfJv ? eps : 1.0);
+    flux[ff * DIM + i] = fma(coef, other - up, acc);
+  }
+}
+
+static size_t df_pk_smem_bytes(int S) {
+  constexpr int PM = kPackMaxFaces, T = kPackThreads, GPB = 3, PTS = T / 3;
+  return (size_t)S * PM * 3 * 16 + sizeof(double) * (GPB * T * 3 + GPB * PTS * 3 * 2 + T + PM * 3) +
+         sizeof(int) * (GPB * (PM + 1) + GPB * 2);
+}
+
+template <int LAW, int MODE>
+static void launch_flux_df_pk(const DevMesh& m, const Material& mat, const float4* sw,
+                              const double* wd, const double* ws, const double* ubq,
+                              const double* ubf, const double* d_eps, double* flux, cudaStream_t st) {
+  if (m.npg == 0) return;
+  k_flux_df_pk<LAW, MODE><<<(unsigned)((m.npg + 2) / 3), kPackThreads, df_pk_smem_bytes(m.S), st>>>(
+      m, mat, sw, wd, ws, ubq, ubf, d_eps, flux);
+}
+
 // contracted linear form, homogeneous part at v: sum_N T_N v_N plus the
 // stabilisation of v with zero prescribed values (symmetry faces mirror)
 template <int DIM>
@@ -1377,7 +1632,9 @@ static void launch_flux_df(const DevMesh& m, const Material& mat, const float4* 
       case 4: return launch_flux_df_q<3, LAW, MODE, 4>(m, mat, sw, wd, ws, ubq, ubf, d_eps, flux, st);
       case 8: return launch_flux_df_q<3, LAW, MODE, 8>(m, mat, sw, wd, ws, ubq, ubf, d_eps, flux, st);
       case 16: return launch_flux_df_q<3, LAW, MODE, 16>(m, mat, sw, wd, ws, ubq, ubf, d_eps, flux, st);
-      case 32: return launch_flux_df_q<3, LAW, MODE, 32>(m, mat, sw, wd, ws, ubq, ubf, d_eps, flux, st);
+      case 32:
+        if (m.pgrp) return launch_flux_df_pk<LAW, MODE>(m, mat, sw, wd, ws, ubq, ubf, d_eps, flux, st);
+        return launch_flux_df_q<3, LAW, MODE, 32>(m, mat, sw, wd, ws, ubq, ubf, d_eps, flux, st);
       default: return launch_flux_df_q<3, LAW, MODE, 9>(m, mat, sw, wd, ws, ubq, ubf, d_eps, flux, st);
     }
   }
@@ -1503,6 +1760,13 @@ static void raise_smem(cudaError_t& e) {
                            (int)df_smem_bytes<DIM, QD>(kMaxS));
   if (r != cudaSuccess) e = r;
 }
+template <int LAW, int MODE>
+static void raise_smem_pk(cudaError_t& e) {
+  const cudaError_t r = cudaFuncSetAttribute((const void*)k_flux_df_pk<LAW, MODE>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)df_pk_smem_bytes(kMaxS));
+  if (r != cudaSuccess) e = r;
+}
 template <int DIM, int QD>
 static void raise_smem_all(cudaError_t& e) {
   raise_smem<DIM, 0, kDfResidual, QD>(e);
@@ -1525,6 +1789,11 @@ int setup_df_kernels() {
   raise_smem_all<3, 8>(e);
   raise_smem_all<3, 16>(e);
   raise_smem_all<3, 32>(e);
+  raise_smem_pk<0, kDfResidual>(e);
+  raise_smem_pk<1, kDfResidual>(e);
+  raise_smem_pk<0, kDfHomog>(e);
+  raise_smem_pk<1, kDfFill>(e);
+  raise_smem_pk<1, kDfJv>(e);
   rc = e == cudaSuccess ? 0 : (int)e;
   return rc;
 }
