@@ -430,7 +430,11 @@ def step_section(args, wl, mesh, ctx, lay, u_ex, precision, rank, ws, peaks_dev,
     pk, src = peaks()
     hbm = pk["hbm_gbs"]
     macs = flops / 2.0
-    name = ("k_flux_df (double-float face gradients + law + quadrature)" if precision == "df64"
+    # prisms: faces of 8 fan slots at 2 x 2 points a triangle, run by the packed kernel
+    packed = precision == "df64" and wl.cells == "polyhedron" and wl.q1 == 2
+    name = ("k_flux_df_pk (double-float face gradients + law + quadrature, faces packed by "
+            "their points with area)" if packed else
+            "k_flux_df (double-float face gradients + law + quadrature)" if precision == "df64"
             else "k_flux (FP64 face gradients + law + quadrature)")
     roofline = {
         "bound": "hbm", "achieved": jb / (jflux_ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
