@@ -74,9 +74,11 @@ def replica_value(cells_per_rank, world_size, ms_max):
 
 
 def kernel_hash():
-    """sha256[:16] of the source of the double-float face kernel and the laws
-    it evaluates (csrc/residual.cu)."""
+    """sha256[:16] of the code of the double-float face kernels and the laws
+    they evaluate (csrc/residual.cu), comments and blank lines left out, so
+    that an edit of a comment keeps the recorded ncu traffic valid."""
     import hashlib
+    import re
     text = open(os.path.join(ROOT, "paper_2601_18417_gb300", "csrc", "residual.cu")).read()
     parts = []
     for lo, hi in (("// laws: traction t = T a", "// face fluxes, one tile of 32 faces"),
@@ -84,7 +86,8 @@ def kernel_hash():
                     "// contracted linear form, homogeneous part at v")):
         a, b = text.find(lo), text.find(hi)
         parts.append(text[a:b] if 0 <= a < b else "")
-    return hashlib.sha256("".join(parts).encode()).hexdigest()[:16]
+    code = [re.sub(r"//.*$", "", line).rstrip() for line in "".join(parts).splitlines()]
+    return hashlib.sha256("\n".join(c for c in code if c).encode()).hexdigest()[:16]
 
 
 def measured_traffic(workload, mode="residual"):

@@ -993,10 +993,12 @@ __device__ __forceinline__ void cp_async_wait_group() {
 // the face's nearest stencil cell N0:
 //   sum_N c_N w_N = sum_N c_N (w_N - w_N0) + w_N0 sum_N c_N,
 // an exact identity; the differences are small where the field is smooth,
-// so the 2^-48 relative representation error of the coefficients acts on
-// them and not on |w| (on fine meshes |w| exceeds h |grad w| by orders of
+// so the rounding of the products and sums of the contraction scales with
+// them and not with |w| (on fine meshes |w| exceeds h |grad w| by orders of
 // magnitude), and the last term is one FP64 product with the FP64 row sum
-// of the stored coefficients.  The block first gathers its faces' stencil
+// of the stored coefficients.  The stored pairs differ from the FP64
+// coefficients by up to 2^-48 of each; through the row sum that difference
+// still meets w_N0 itself (the sum of the pairs, not of the originals).  The block first gathers its faces' stencil
 // cells' splits into shared memory (16-byte asynchronous copies, [S][FPB]
 // entries) and turns each into the double-float difference to its face's
 // reference (exact differences of the splits); the contraction then reads
